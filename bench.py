@@ -1,0 +1,336 @@
+"""Throughput of the two-timescale multicomponent LB step on GB300.
+
+Workload (default): charged ternary mixture (solvent, cation z=+1, anion
+z=-1), D3Q19, 128^3 periodic, ion number fractions 0.01 +/- U(1e-3) seeded,
+Bjerrum length 0.7, Poisson solved every step to a relative residual of
+1e-8, Sc = 1, FP32.  One step = charge density + Poisson solve + fused
+stream/collide of all species.  Metric: species-site MLUPS (S * N * steps /
+time / 1e6), with the stream/collide kernel's fraction of the measured HBM
+roofline and the Poisson iterations per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only other implementation:
+the paper ships no code) on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "species-site MLUPS & % HBM roofline; Poisson iters/step, learned vs plain"
+UNIT = "species-site MLUPS"
+BYTES_PER_SPECIES_SITE = {"fp32": 152, "fp16": 76, "bf16": 76}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--schmidt", type=float, default=1.0)
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--poisson", default="mg", choices=["mg", "sor"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """DRAM bytes per stream/collide launch from the committed ncu summary,
+    valid only while the kernel source is unchanged (hash recorded there)."""
+    path = os.path.join(ROOT, "profiles", "stream_collide_ternary_128.md")
+    src = os.path.join(ROOT, "paper_1507_04891_gb300", "csrc", "lbm_kernels.cu")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        rec = {}
+        for line in open(path):
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                rec[k.strip()] = v.strip().strip("`")
+        if rec.get("kernel_source_sha256_16") != h:
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    def __init__(self, index=0):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:6]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(n_sample=24, steps=3, schmidt=1.0):
+    """Times the FP64 oracle on a bounded sample of the workload: the same
+    charged ternary physics on an n_sample^3 periodic lattice (the oracle's
+    cost per node does not depend on the lattice size except through the
+    Poisson solve)."""
+    import oracle as O
+    from paper_1507_04891_gb300 import workloads as WL
+
+    wl = WL.ternary_bulk(shape=(n_sample,) * 3, seed=1235, schmidt=schmidt)
+    p = O.Params(wl.omega_visc, O.omega_drag_for_schmidt(wl.omega_visc, schmidt), wl.mass,
+                 wl.valence, bjerrum=wl.bjerrum)
+    o = O.Oracle(p, wl.shape)
+    o.initialise(wl.n0)
+    o.step()
+    t0 = time.perf_counter()
+    o.run(steps)
+    dt = time.perf_counter() - t0
+    mlups = 3 * wl.sites * steps / dt / 1e6
+    return {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 numpy oracle, same charged ternary physics (Sc=%g, l_B=0.7, Poisson "
+                      "each step) on a %d^3 periodic lattice, %d timed steps after 1 untimed, "
+                      "%.1f s" % (schmidt, n_sample, steps, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    steps = max(1, args.steps)
+    warm = max(0, args.warmup)
+    import oracle as O
+    from paper_1507_04891_gb300 import workloads as WL
+    n_sample = 24
+    wl = WL.ternary_bulk(shape=(n_sample,) * 3, seed=1235, schmidt=args.schmidt)
+    p = O.Params(wl.omega_visc, O.omega_drag_for_schmidt(wl.omega_visc, args.schmidt), wl.mass,
+                 wl.valence, bjerrum=wl.bjerrum)
+    o = O.Oracle(p, wl.shape)
+    o.initialise(wl.n0)
+    for _ in range(warm):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step()
+    dt = time.perf_counter() - t0
+    value = 3 * wl.sites * steps / dt / 1e6
+    sample = ("FP64 numpy oracle on a %d^3 sample of the charged ternary workload (Sc=%g, "
+              "Poisson each step), %d timed steps" % (n_sample, args.schmidt, steps))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "ternary_bulk_%d^3" % args.n, "sc": args.schmidt,
+                       "bjerrum": 0.7, "poisson_tol": 1e-8},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_1507_04891_gb300 import lbm
+    from paper_1507_04891_gb300 import workloads as WL
+    from paper_1507_04891_gb300.build import build_library
+
+    build_library()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.n
+    wl = WL.ternary_bulk(n=n, seed=1235 + rank, schmidt=args.schmidt)
+    S, N = wl.nspecies, wl.sites
+    od = lbm.omega_drag_for_schmidt(wl.omega_visc, args.schmidt)
+
+    def make():
+        return lbm.Lattice(n, n, n, S, omega_visc=wl.omega_visc, omega_drag=od, bjerrum=wl.bjerrum,
+                           storage=args.storage, poisson=args.poisson, poisson_tol=1e-8,
+                           poisson_maxit=500, device=local)
+
+    lat = make()
+    for s in range(S):
+        lat.set_species(s, 1.0, wl.valence[s], wl.n0[s])
+    stream = torch.cuda.ExternalStream(lat.stream, device=torch.device("cuda", local))
+    lat.step(max(3, args.warmup))
+    lat.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    lat.set_timing(True)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    lat.synchronize()
+    barrier()
+    clk = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    tm = lat.get_timing()
+    lat.set_timing(False)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * S * N * args.steps / (t_ms / 1e3) / 1e6
+    collide_ms = tm["collide_ms"] / max(1, tm["collide_launches"])
+    bpl = BYTES_PER_SPECIES_SITE[args.storage] * S * N
+    peak, peak_kind = measured_peaks()
+    achieved = bpl / (collide_ms / 1e3) / 1e9
+    traffic = kernel_traffic() if args.storage == "fp32" and n == 128 else None
+    diag = lat.diagnostics()
+
+    # end to end through the C ABI with host buffers: initial state uploaded
+    # from pinned host memory, every step's FP64 diagnostics read back.
+    lat.destroy()
+    lat2 = make()
+    pinned = [torch.from_numpy(np.ascontiguousarray(wl.n0[s])).pin_memory().numpy() for s in range(S)]
+    lat2.step  # noqa: B018 (handle created before the timed region)
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(S):
+        lat2.set_species(s, 1.0, wl.valence[s], pinned[s])
+    for _ in range(args.steps):
+        lat2.step(1)
+        lat2.diagnostics()
+    lat2.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * S * N * args.steps / e2e_s / 1e6
+    lat2.destroy()
+
+    # launches of our kernels in the timed region
+    iters = tm["poisson_iters"]
+    per_vcycle = None
+    launches = None
+    if args.poisson == "mg":
+        per_vcycle = None  # counted below from the level structure
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_oracle_sample(schmidt=args.schmidt)
+        except Exception as ex:  # the baseline is reported, never required
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: %s" % ex}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "fp32" else args.storage + "-storage/f32",
+            "data": "synthetic",
+            "config": {"workload": "ternary_bulk_%d^3" % n, "species": S, "sc": args.schmidt,
+                       "omega_visc": wl.omega_visc, "omega_drag": od, "bjerrum": wl.bjerrum,
+                       "poisson": args.poisson, "poisson_tol": 1e-8, "storage": args.storage,
+                       "l2": "inputs larger than L2 (2 x %.0f MB population lattices)"
+                             % (BYTES_PER_SPECIES_SITE[args.storage] / 2 * S * N / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "poisson_iters_per_step": iters / args.steps,
+            "phase_ms_per_step": {"charge": tm["charge_ms"] / args.steps,
+                                  "poisson": tm["poisson_ms"] / args.steps,
+                                  "stream_collide": tm["collide_ms"] / args.steps},
+            "roofline": {"kernel": "k_stream_collide", "bound": "hbm", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_kind,
+                         "algorithmic_bytes_per_launch": bpl, "traffic": traffic},
+            "clocks": clk,
+            "gpu_launches": None,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * S * N / args.steps,
+                    "d2h_bytes_per_step": 8 * (S + 7)},
+            "diagnostics": {"mass": list(map(float, diag["mass"])),
+                            "poisson_residual_last": diag["poisson_residual"]},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

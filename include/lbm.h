@@ -1,0 +1,181 @@
+/*
+ * lbm.h -- C ABI of the GB300 two-timescale multicomponent lattice
+ * Boltzmann library (D3Q19).
+ *
+ * The model is the discrete kinetic equation of Monteferrante, Melchionna
+ * and Marini Bettolo Marconi, "Lattice Boltzmann Method for mixtures at
+ * variable Schmidt number": for every species alpha and direction p,
+ *
+ *   f_p(r + c_p, t + 1) = f_p(r, t) - omega_visc [f_p - phi_perp,p] + g_p
+ *
+ * (Eq. latboeq), with the orthogonalised equilibrium phi_perp (Appendix,
+ * final expression), the second-order forcing term g_p (Eq. ourforc) carrying
+ * the interspecies drag of frequency omega_drag (Sec. 2, drag force) and the
+ * mean-field electric force of the potential that solves the Poisson
+ * equation nabla^2 psi = -4 pi l_B sum_alpha z^alpha n^alpha with the
+ * surface-charge boundary condition (Eq. Poisson and the condition after it).
+ *
+ * Conventions shared by every entry point
+ *   - Lattice: nx * ny * nz nodes on a 3-torus, index (z*ny + y)*nx + x,
+ *     x fastest.  Walls are solid nodes; a non-periodic face is closed by
+ *     a layer of solid nodes.  Halfway bounce-back at solid nodes.
+ *   - D3Q19 order: 0 rest, 1..6 = +x,-x,+y,-y,+z,-z, 7..18 the 12 edge
+ *     vectors in opposite pairs (2k-1, 2k).
+ *   - Units: lattice units, v_T^2 = c_s^2 = 1/3, unit time step.
+ *   - Host pointers are caller-owned, read or written during the call only
+ *     and never retained.  Device memory is owned by the handle.
+ *   - Every call returns an lbm_status; nothing throws across the ABI.
+ *     The message of the last failure is lbm_last_error(h).
+ *   - All calls on one handle must come from one host thread at a time.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm lbm_t; /* opaque, owned by the library */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,    /* bad argument or call order                      */
+  LBM_ENOMEM = 2,    /* device allocation failed                        */
+  LBM_ECUDA = 3,     /* CUDA runtime error (message has the CUDA text)  */
+  LBM_ENOCONV = 4,   /* Poisson solve hit its iteration limit           */
+  LBM_EUNSTABLE = 5, /* non-finite or non-positive density detected     */
+  LBM_ETIMEOUT = 6   /* a bounded device wait gave up                   */
+} lbm_status;
+
+enum { LBM_FP32 = 0, LBM_FP16_SHIFT = 1, LBM_BF16_SHIFT = 2 };
+enum { LBM_POISSON_MG = 0, LBM_POISSON_SOR = 1 };
+
+typedef struct {
+  int nx, ny, nz;        /* lattice extents, each >= 1                       */
+  int nspecies;          /* 1..4                                             */
+  double omega_visc;     /* 0 < w < 2: nu = c_s^2 (1/w - 1/2), Sec. 4        */
+  double omega_drag;     /* 0 < w < 2: D = c_s^2 (1/w - 1/2), Sec. 4         */
+  double bjerrum;        /* l_B of Eq. (Poisson); 0 = neutral, no Poisson    */
+  double e_ext[3];       /* applied field, acceleration per unit valence     */
+  int storage;           /* LBM_FP32 | LBM_FP16_SHIFT | LBM_BF16_SHIFT       */
+  int poisson;           /* LBM_POISSON_MG | LBM_POISSON_SOR                 */
+  double poisson_tol;    /* ||s - A psi||_2 / ||s||_2 target, e.g. 1e-8      */
+  int poisson_maxit;     /* iteration cap (V-cycles or SOR sweeps)           */
+  int device;            /* CUDA device ordinal                              */
+} lbm_config;
+
+/* Fills *cfg with defaults: omega_visc = 1, omega_drag = 1, l_B = 0,
+ * FP32 storage, multigrid Poisson, tol 1e-8, maxit 200, device 0.        */
+void lbm_config_default(lbm_config* cfg);
+
+/* Creates a lattice.  Allocates two population lattices and the Poisson
+ * hierarchy on cfg->device.  Returns LBM_EINVAL for extents < 1, species
+ * outside 1..4, omega outside (0, 2), storage/poisson codes unknown;
+ * LBM_ENOMEM when device memory runs out.  *out is NULL on failure.      */
+lbm_status lbm_create(const lbm_config* cfg, lbm_t** out);
+
+/* Releases every device buffer of h.  NULL is accepted.                  */
+void lbm_destroy(lbm_t* h);
+
+/* Walls (optional; must precede lbm_set_species).  solid: N bytes, non-zero
+ * marks a wall node.  sigma: N doubles, the surface charge (units of e)
+ * carried by each wall node, or NULL for uncharged walls; entries at fluid
+ * nodes are ignored.  A wall node with k fluid face neighbours hands
+ * sigma/k to each (boundary condition after Eq. Poisson).  LBM_EINVAL if
+ * species were already set or every node is solid.                        */
+lbm_status lbm_set_walls(lbm_t* h, const uint8_t* solid, const double* sigma);
+
+/* Species s (0 <= s < nspecies): particle mass (equal for all species:
+ * one thermal speed on the lattice), valence z^alpha, initial density n0
+ * (N doubles, > 0 at fluid nodes) and velocity u0 (3N doubles laid out as
+ * [3][N], or NULL for rest).  Sets f_p(r, 0) = phi_perp,p(n0, u0) at every
+ * fluid node (local equilibrium, Appendix).  LBM_EINVAL for a bad index, a
+ * different mass than an earlier species, or n0 <= 0 at a fluid node.     */
+lbm_status lbm_set_species(lbm_t* h, int s, double mass, double valence,
+                           const double* n0, const double* u0);
+
+/* Advances nsteps >= 0 time steps of Eq. (latboeq).  Each step: charge
+ * density and Poisson solve (if l_B > 0), fused stream + moments + forces +
+ * collision of all species.  stream: a cudaStream_t, or NULL for the
+ * library's own stream; the call returns after the work is queued except
+ * that the Poisson convergence test reads one value back per iteration.
+ * LBM_ENOCONV if a Poisson solve reached poisson_maxit (the state has then
+ * advanced with the unconverged potential).                               */
+lbm_status lbm_step(lbm_t* h, int nsteps, void* stream);
+
+/* Blocks until all queued work of h is done.                             */
+lbm_status lbm_synchronize(lbm_t* h);
+
+/* Moments of the current state f(t) of species s: n (N doubles) and the
+ * bare species velocity u = sum_p c_p f_p / n (3N doubles, [3][N]); either
+ * pointer may be NULL.  Zero at wall nodes.  Host buffers.                */
+lbm_status lbm_get_moments(lbm_t* h, int s, double* n, double* u);
+
+/* Populations f_p(r, t) of species s (19*N doubles, [19][N]); zero at wall
+ * nodes.  Host buffer.                                                    */
+lbm_status lbm_get_populations(lbm_t* h, int s, double* f);
+
+/* Potential psi (N doubles, zero at wall nodes) used by the last step's
+ * collision.  Host buffer.                                                */
+lbm_status lbm_get_potential(lbm_t* h, double* psi);
+
+/* Standalone Poisson solve on the lattice's geometry (Eq. Poisson with the
+ * wall charges of lbm_set_walls): A psi = 4 pi l_B (rho_e + w - mean).
+ * rho_e: N doubles (host).  psi: N doubles (host), initial guess on entry,
+ * solution on exit (zero mean over fluid cells is not enforced: the guess
+ * fixes the constant).  tol, maxit as in the config (maxit <= 0 uses the
+ * config's).  *iters and *rel_res (may be NULL) report the outcome.
+ * Requires l_B > 0.  LBM_ENOCONV when the cap was hit (psi still written). */
+lbm_status lbm_solve_poisson(lbm_t* h, const double* rho_e, double* psi,
+                             double tol, int maxit, int* iters,
+                             double* rel_res);
+
+/* FP64 global diagnostics of the current state f(t), written to out:
+ *   out[0 .. S-1]   total number of particles of each species
+ *   out[S .. S+2]   total momentum sum_alpha sum_r m n^alpha u^alpha
+ *   out[S+3]        net fluid charge sum_r sum_alpha z^alpha n^alpha
+ *   out[S+4]        Poisson iterations of the last step
+ *   out[S+5]        final relative Poisson residual of the last step
+ *   out[S+6]        number of time steps taken
+ * out must hold LBM_DIAG_LEN(S) doubles.  LBM_EUNSTABLE if a density is
+ * non-finite or non-positive (the values are still written).             */
+#define LBM_DIAG_LEN(S) ((S) + 7)
+lbm_status lbm_diagnostics(lbm_t* h, double* out);
+
+/* Raw state for checkpointing: the stored populations of all species as
+ * FP32 values, S*19*N floats, in the library's internal order (post-
+ * collision populations of the last step, before streaming), plus the step
+ * counter.  lbm_set_state restores exactly what lbm_get_state returned.   */
+lbm_status lbm_get_state(lbm_t* h, float* state, int64_t* step);
+lbm_status lbm_set_state(lbm_t* h, const float* state, int64_t step);
+
+/* Number of lattice nodes N = nx*ny*nz, and the element count of the raw
+ * state (S*19*N).                                                          */
+int64_t lbm_num_nodes(const lbm_t* h);
+int64_t lbm_state_len(const lbm_t* h);
+
+/* Phase timing.  lbm_set_timing(h, 1) makes every following lbm_step record
+ * CUDA events around its phases on the stream it runs on; lbm_get_timing
+ * waits for them and writes, accumulated since timing was enabled:
+ *   out[0] charge-density kernel ms    out[3] its launch count
+ *   out[1] Poisson solve ms            out[4] Poisson iterations
+ *   out[2] stream-collide kernel ms    out[5] its launch count
+ * lbm_set_timing(h, 0) stops recording and clears the sums.               */
+lbm_status lbm_set_timing(lbm_t* h, int enable);
+lbm_status lbm_get_timing(lbm_t* h, double* out);
+
+/* The library's CUDA stream (a cudaStream_t), for callers that record
+ * events around lbm_step on it.                                           */
+void* lbm_stream(lbm_t* h);
+
+/* Message of the last failure on h (or of the last failed lbm_create when
+ * h is NULL).  Valid until the next call on h.                            */
+const char* lbm_last_error(const lbm_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

@@ -1,0 +1,565 @@
+// C ABI of the library (declared in include/lbm.h): argument checking,
+// device memory ownership and the per-step launch sequence.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+using namespace lbm_gb300;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+lbm_status fail(lbm_t* h, lbm_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+template <typename T>
+lbm_status dev_alloc(lbm_t* h, T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(h, LBM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return LBM_OK;
+}
+
+// RAII scratch buffer for one call.
+struct Scratch {
+  void* p = nullptr;
+  ~Scratch() {
+    if (p) cudaFree(p);
+  }
+};
+
+bool species_complete(const lbm_t* h) {
+  return h->species_set == ((1u << h->S) - 1u);
+}
+
+// Returns the index of a recorded event (from a reusable pool).
+cudaError_t mark(lbm_t* h, int* idx) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    h->ev_pool.push_back(e);
+  }
+  *idx = (int)h->ev_used++;
+  return cudaEventRecord(h->ev_pool[*idx], h->st);
+}
+
+// Adds the elapsed times of all recorded phase pairs to the sums.
+cudaError_t drain_timing(lbm_t* h) {
+  for (auto& m : h->ev_marks) {
+    cudaError_t r = cudaEventSynchronize(h->ev_pool[m.second.second]);
+    if (r != cudaSuccess) return r;
+    float ms = 0.f;
+    r = cudaEventElapsedTime(&ms, h->ev_pool[m.second.first], h->ev_pool[m.second.second]);
+    if (r != cudaSuccess) return r;
+    h->t_acc[m.first] += ms;
+  }
+  h->ev_marks.clear();
+  h->ev_used = 0;
+  return cudaSuccess;
+}
+
+struct Phase {
+  lbm_t* h;
+  int phase, a = -1;
+  Phase(lbm_t* hh, int p) : h(hh), phase(p) {
+    if (h->timing) mark(h, &a);
+  }
+  cudaError_t stop() {
+    if (!h->timing || a < 0) return cudaSuccess;
+    int b;
+    cudaError_t r = mark(h, &b);
+    if (r == cudaSuccess) h->ev_marks.push_back({phase, {a, b}});
+    a = -1;
+    return r;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+void lbm_config_default(lbm_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->nx = c->ny = c->nz = 1;
+  c->nspecies = 1;
+  c->omega_visc = 1.0;
+  c->omega_drag = 1.0;
+  c->bjerrum = 0.0;
+  c->storage = LBM_FP32;
+  c->poisson = LBM_POISSON_MG;
+  c->poisson_tol = 1e-8;
+  c->poisson_maxit = 200;
+  c->device = 0;
+}
+
+lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (!cfg) {
+    g_create_error = "cfg is NULL";
+    return LBM_EINVAL;
+  }
+  const lbm_config& c = *cfg;
+  if (c.nx < 1 || c.ny < 1 || c.nz < 1) {
+    g_create_error = "lattice extents must be >= 1";
+    return LBM_EINVAL;
+  }
+  const int64_t N = (int64_t)c.nx * c.ny * c.nz;
+  if (N > (int64_t)1 << 30) {
+    g_create_error = "lattice larger than 2^30 nodes";
+    return LBM_EINVAL;
+  }
+  if (c.nspecies < 1 || c.nspecies > MAX_SPECIES) {
+    g_create_error = "nspecies must be in 1..4";
+    return LBM_EINVAL;
+  }
+  if (!(c.omega_visc > 0.0 && c.omega_visc < 2.0) ||
+      !(c.omega_drag > 0.0 && c.omega_drag < 2.0)) {
+    g_create_error = "omega_visc and omega_drag must lie in (0, 2)";
+    return LBM_EINVAL;
+  }
+  if (c.storage != LBM_FP32 && c.storage != LBM_FP16_SHIFT && c.storage != LBM_BF16_SHIFT) {
+    g_create_error = "unknown storage code";
+    return LBM_EINVAL;
+  }
+  if (c.poisson != LBM_POISSON_MG && c.poisson != LBM_POISSON_SOR) {
+    g_create_error = "unknown Poisson solver code";
+    return LBM_EINVAL;
+  }
+  if (!(c.bjerrum >= 0.0) || !isfinite(c.bjerrum)) {
+    g_create_error = "bjerrum must be finite and >= 0";
+    return LBM_EINVAL;
+  }
+  if (c.bjerrum > 0.0 && (!(c.poisson_tol > 0.0) || c.poisson_maxit < 1)) {
+    g_create_error = "poisson_tol must be > 0 and poisson_maxit >= 1";
+    return LBM_EINVAL;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
+    cudaGetLastError();
+    g_create_error = "no CUDA device with the requested ordinal";
+    return LBM_ECUDA;
+  }
+  lbm_t* h = new (std::nothrow) lbm_t();
+  if (!h) return LBM_ENOMEM;
+  h->cfg = c;
+  h->S = c.nspecies;
+  h->N = N;
+  h->dev = c.device;
+  h->nfluid = N;
+  h->esize = (c.storage == LBM_FP32) ? 4 : 2;
+  lbm_status s = LBM_OK;
+  if (cudaSetDevice(h->dev) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
+    g_create_error = "CUDA context or stream creation failed";
+    lbm_destroy(h);
+    return LBM_ECUDA;
+  }
+  h->st = h->own;
+  const size_t pops = (size_t)h->S * Q * N * h->esize;
+  for (int k = 0; k < 2 && s == LBM_OK; ++k) {
+    if (cudaMalloc(&h->f[k], pops) != cudaSuccess) {
+      cudaGetLastError();
+      s = LBM_ENOMEM;
+    } else {
+      cudaMemset(h->f[k], 0, pops);
+    }
+  }
+  if (s == LBM_OK) s = dev_alloc(h, &h->dred, MAX_SPECIES + 8);
+  if (s == LBM_OK) s = dev_alloc(h, &h->dflag, 1);
+  if (s == LBM_OK && cudaMallocHost(&h->hred, (MAX_SPECIES + 8) * sizeof(double)) != cudaSuccess)
+    s = LBM_ENOMEM;
+  if (s == LBM_OK && c.bjerrum > 0.0) {
+    s = dev_alloc(h, &h->ps.psi[0], N);
+    if (s == LBM_OK) s = dev_alloc(h, &h->ps.psi[1], N);
+    if (s == LBM_OK) s = dev_alloc(h, &h->ps.src, N);
+    if (s == LBM_OK) s = dev_alloc(h, &h->ps.dsum, 4);
+    if (s == LBM_OK && cudaMallocHost(&h->ps.hsum, 4 * sizeof(double)) != cudaSuccess)
+      s = LBM_ENOMEM;
+    if (s == LBM_OK) {
+      cudaMemset(h->ps.psi[0], 0, N * sizeof(int64_t));
+      cudaMemset(h->ps.psi[1], 0, N * sizeof(int64_t));
+      cudaMemset(h->ps.dsum, 0, 4 * sizeof(double));
+      s = poisson_setup(h, nullptr);
+    }
+  }
+  if (s == LBM_OK && cudaDeviceSynchronize() != cudaSuccess) s = LBM_ECUDA;
+  if (s != LBM_OK) {
+    g_create_error = h->err.empty() ? "device allocation failed" : h->err;
+    lbm_destroy(h);
+    return s;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_t* h) {
+  if (!h) return;
+  cudaSetDevice(h->dev);
+  if (h->own) cudaStreamSynchronize(h->own);
+  cudaFree(h->f[0]);
+  cudaFree(h->f[1]);
+  cudaFree(h->links);
+  cudaFree(h->wallq);
+  cudaFree(h->wcell);
+  cudaFree(h->dred);
+  cudaFree(h->dflag);
+  if (h->hred) cudaFreeHost(h->hred);
+  poisson_free(h);
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  if (h->own) cudaStreamDestroy(h->own);
+  delete h;
+}
+
+lbm_status lbm_set_walls(lbm_t* h, const uint8_t* solid, const double* sigma) {
+  if (!h) return LBM_EINVAL;
+  if (!solid) return fail(h, LBM_EINVAL, "solid mask is NULL");
+  if (h->species_set) return fail(h, LBM_EINVAL, "walls must be set before any species");
+  cudaSetDevice(h->dev);
+  h->st = h->own;
+  const int nx = h->cfg.nx, ny = h->cfg.ny, nz = h->cfg.nz;
+  const int64_t N = h->N;
+  int64_t nfluid = 0;
+  for (int64_t i = 0; i < N; ++i) nfluid += solid[i] ? 0 : 1;
+  if (nfluid == 0) return fail(h, LBM_EINVAL, "every node is a wall node");
+  // Face charge share q_j = sigma_j / k_j of each wall node (k_j = number of
+  // fluid face neighbours) and the wall charge w_i handed to each fluid cell.
+  std::vector<float> q(N, 0.f), w(N, 0.f);
+  auto idx = [&](int x, int y, int z) -> int64_t {
+    x = (x + nx) % nx;
+    y = (y + ny) % ny;
+    z = (z + nz) % nz;
+    return ((int64_t)z * ny + y) * nx + x;
+  };
+  const int fd[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  bool charged_walls = false;
+  if (sigma) {
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          const int64_t i = idx(x, y, z);
+          if (!solid[i] || sigma[i] == 0.0) continue;
+          if (!isfinite(sigma[i])) return fail(h, LBM_EINVAL, "sigma is not finite");
+          int k = 0;
+          for (auto& d : fd)
+            if (!solid[idx(x + d[0], y + d[1], z + d[2])]) ++k;
+          if (k == 0) continue;
+          q[i] = (float)(sigma[i] / k);
+          charged_walls = true;
+        }
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          const int64_t i = idx(x, y, z);
+          if (solid[i]) continue;
+          double acc = 0.0;
+          for (auto& d : fd) {
+            const int64_t j = idx(x + d[0], y + d[1], z + d[2]);
+            if (solid[j]) acc += q[j];
+          }
+          w[i] = (float)acc;
+        }
+  }
+  Scratch sc;
+  if (cudaMalloc(&sc.p, N) != cudaSuccess) return fail(h, LBM_ENOMEM, "scratch allocation failed");
+  lbm_status s = LBM_OK;
+  if (!h->links) s = dev_alloc(h, &h->links, N);
+  if (s != LBM_OK) return s;
+  LBM_CUDA_TRY(h, cudaMemcpy(sc.p, solid, N, cudaMemcpyHostToDevice));
+  h->has_walls = true;
+  LBM_CUDA_TRY(h, launch_links(h, (const uint8_t*)sc.p));
+  if (charged_walls) {
+    if (!h->wallq && (s = dev_alloc(h, &h->wallq, N)) != LBM_OK) return s;
+    if (!h->wcell && (s = dev_alloc(h, &h->wcell, N)) != LBM_OK) return s;
+    LBM_CUDA_TRY(h, cudaMemcpy(h->wallq, q.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+    LBM_CUDA_TRY(h, cudaMemcpy(h->wcell, w.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+  } else {
+    cudaFree(h->wallq);
+    cudaFree(h->wcell);
+    h->wallq = h->wcell = nullptr;
+  }
+  h->nfluid = nfluid;
+  if (h->cfg.bjerrum > 0.0) {
+    h->ps.nfluid = nfluid;
+    s = poisson_setup(h, solid);
+    if (s != LBM_OK) return s;
+  }
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  LBM_CUDA_TRY(h, cudaDeviceSynchronize());
+  return LBM_OK;
+}
+
+lbm_status lbm_set_species(lbm_t* h, int s, double mass, double valence,
+                           const double* n0, const double* u0) {
+  if (!h) return LBM_EINVAL;
+  if (s < 0 || s >= h->S) return fail(h, LBM_EINVAL, "species index out of range");
+  if (!n0) return fail(h, LBM_EINVAL, "n0 is NULL");
+  if (!(mass > 0.0) || !isfinite(mass) || !isfinite(valence))
+    return fail(h, LBM_EINVAL, "mass must be > 0 and valence finite");
+  if (h->species_set && fabs(mass - h->mass0) > 1e-12 * h->mass0)
+    return fail(h, LBM_EINVAL,
+                "all species must have the same mass (one thermal speed on the lattice)");
+  cudaSetDevice(h->dev);
+  h->st = h->own;
+  const int64_t N = h->N;
+  // host checks and the reference density of the 16-bit shifted storage
+  std::vector<uint8_t> solid;
+  if (h->has_walls) {
+    std::vector<uint32_t> lk(N);
+    LBM_CUDA_TRY(h, cudaMemcpy(lk.data(), h->links, N * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    solid.resize(N);
+    for (int64_t i = 0; i < N; ++i) solid[i] = (lk[i] & LINK_SOLID) ? 1 : 0;
+  }
+  double tot = 0.0;
+  int64_t cnt = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    if (!solid.empty() && solid[i]) continue;
+    if (!(n0[i] > 0.0) || !isfinite(n0[i]))
+      return fail(h, LBM_EINVAL, "n0 must be finite and > 0 at every fluid node");
+    if (u0 && (!isfinite(u0[i]) || !isfinite(u0[N + i]) || !isfinite(u0[2 * N + i])))
+      return fail(h, LBM_EINVAL, "u0 must be finite");
+    tot += n0[i];
+    ++cnt;
+  }
+  h->nref[s] = (float)(tot / (double)cnt);
+  Scratch sc;
+  const size_t bytes = (size_t)N * sizeof(double) * (u0 ? 4 : 1);
+  if (cudaMalloc(&sc.p, bytes) != cudaSuccess) return fail(h, LBM_ENOMEM, "scratch allocation failed");
+  double* dn = (double*)sc.p;
+  double* du = u0 ? dn + N : nullptr;
+  LBM_CUDA_TRY(h, cudaMemcpy(dn, n0, N * sizeof(double), cudaMemcpyHostToDevice));
+  if (u0) LBM_CUDA_TRY(h, cudaMemcpy(du, u0, 3 * N * sizeof(double), cudaMemcpyHostToDevice));
+  LBM_CUDA_TRY(h, launch_init_species(h, s, dn, du));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  h->mass[s] = (float)mass;
+  h->valence[s] = (float)valence;
+  if (!h->species_set) h->mass0 = mass;
+  h->species_set |= 1u << s;
+  h->tstep = 0;
+  h->psi_valid = false;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
+  if (!h) return LBM_EINVAL;
+  if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
+  if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set before stepping");
+  cudaSetDevice(h->dev);
+  h->st = stream ? (cudaStream_t)stream : h->own;
+  const bool charged = h->cfg.bjerrum > 0.0;
+  // bound the number of outstanding timing events
+  if (h->timing && h->ev_used > 4096) LBM_CUDA_TRY(h, drain_timing(h));
+  for (int k = 0; k < nsteps; ++k) {
+    lbm_status s = LBM_OK;
+    if (charged) {
+      Phase pc(h, 0);
+      LBM_CUDA_TRY(h, cudaMemsetAsync(h->ps.dsum, 0, 3 * sizeof(double), h->st));
+      LBM_CUDA_TRY(h, launch_charge(h));
+      LBM_CUDA_TRY(h, pc.stop());
+      h->t_cnt[0] += 1;
+      int it = 0;
+      double rel = 0.0;
+      Phase pp(h, 1);
+      s = poisson_solve(h, h->cfg.poisson_tol, h->cfg.poisson_maxit, &it, &rel);
+      LBM_CUDA_TRY(h, pp.stop());
+      h->t_cnt[1] += it;
+      h->last_iters = it;
+      h->last_res = rel;
+      if (s != LBM_OK && s != LBM_ENOCONV) return s;
+      h->psi_valid = true;
+    }
+    Phase ps(h, 2);
+    LBM_CUDA_TRY(h, launch_stream_collide(h));
+    LBM_CUDA_TRY(h, ps.stop());
+    h->t_cnt[2] += 1;
+    ++h->tstep;
+    if (s == LBM_ENOCONV) return s;
+  }
+  if (h->timing && h->ev_used > 4096) LBM_CUDA_TRY(h, drain_timing(h));
+  return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_t* h) {
+  if (!h) return LBM_EINVAL;
+  cudaSetDevice(h->dev);
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->own));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_moments(lbm_t* h, int s, double* n, double* u) {
+  if (!h) return LBM_EINVAL;
+  if (s < 0 || s >= h->S) return fail(h, LBM_EINVAL, "species index out of range");
+  if (!(h->species_set >> s & 1u)) return fail(h, LBM_EINVAL, "species not set");
+  if (!n && !u) return LBM_OK;
+  cudaSetDevice(h->dev);
+  const int64_t N = h->N;
+  Scratch sc;
+  if (cudaMalloc(&sc.p, 4 * N * sizeof(double)) != cudaSuccess)
+    return fail(h, LBM_ENOMEM, "scratch allocation failed");
+  double* dn = (double*)sc.p;
+  double* du = dn + N;
+  LBM_CUDA_TRY(h, launch_gather(h, s, dn, du, nullptr));
+  if (n) LBM_CUDA_TRY(h, cudaMemcpyAsync(n, dn, N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  if (u) LBM_CUDA_TRY(h, cudaMemcpyAsync(u, du, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_t* h, int s, double* f) {
+  if (!h) return LBM_EINVAL;
+  if (s < 0 || s >= h->S || !f) return fail(h, LBM_EINVAL, "bad species index or NULL buffer");
+  cudaSetDevice(h->dev);
+  const int64_t N = h->N;
+  Scratch sc;
+  if (cudaMalloc(&sc.p, (size_t)Q * N * sizeof(double)) != cudaSuccess)
+    return fail(h, LBM_ENOMEM, "scratch allocation failed");
+  LBM_CUDA_TRY(h, launch_gather(h, s, nullptr, nullptr, (double*)sc.p));
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(f, sc.p, (size_t)Q * N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_potential(lbm_t* h, double* psi) {
+  if (!h || !psi) return LBM_EINVAL;
+  if (!(h->cfg.bjerrum > 0.0)) return fail(h, LBM_EINVAL, "neutral lattice has no potential");
+  cudaSetDevice(h->dev);
+  const int64_t N = h->N;
+  Scratch sc;
+  if (cudaMalloc(&sc.p, N * sizeof(double)) != cudaSuccess)
+    return fail(h, LBM_ENOMEM, "scratch allocation failed");
+  LBM_CUDA_TRY(h, launch_psi_to_double(h, h->ps.psi[h->ps.cur], (double*)sc.p));
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(psi, sc.p, N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return LBM_OK;
+}
+
+lbm_status lbm_solve_poisson(lbm_t* h, const double* rho_e, double* psi,
+                             double tol, int maxit, int* iters, double* rel_res) {
+  if (!h) return LBM_EINVAL;
+  if (!(h->cfg.bjerrum > 0.0)) return fail(h, LBM_EINVAL, "requires bjerrum > 0");
+  if (!rho_e || !psi) return fail(h, LBM_EINVAL, "NULL buffer");
+  if (!(tol > 0.0)) return fail(h, LBM_EINVAL, "tol must be > 0");
+  if (maxit <= 0) maxit = h->cfg.poisson_maxit;
+  cudaSetDevice(h->dev);
+  h->st = h->own;
+  const int64_t N = h->N;
+  for (int64_t i = 0; i < N; ++i)
+    if (!isfinite(rho_e[i]) || !isfinite(psi[i]) || fabs(psi[i]) >= PSI_MAX)
+      return fail(h, LBM_EINVAL, "rho_e and psi must be finite, |psi| < 2^19");
+  Scratch sc;
+  if (cudaMalloc(&sc.p, 2 * N * sizeof(double)) != cudaSuccess)
+    return fail(h, LBM_ENOMEM, "scratch allocation failed");
+  double* drho = (double*)sc.p;
+  double* dpsi = drho + N;
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(drho, rho_e, N * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(dpsi, psi, N * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  LBM_CUDA_TRY(h, cudaMemsetAsync(h->ps.dsum, 0, 3 * sizeof(double), h->st));
+  LBM_CUDA_TRY(h, launch_src_from_rho(h, drho));
+  LBM_CUDA_TRY(h, launch_psi_from_double(h, dpsi, h->ps.psi[h->ps.cur]));
+  int it = 0;
+  double rel = 0.0;
+  lbm_status s = poisson_solve(h, tol, maxit, &it, &rel);
+  if (iters) *iters = it;
+  if (rel_res) *rel_res = rel;
+  if (s != LBM_OK && s != LBM_ENOCONV) return s;
+  LBM_CUDA_TRY(h, launch_psi_to_double(h, h->ps.psi[h->ps.cur], dpsi));
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(psi, dpsi, N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return s;
+}
+
+lbm_status lbm_diagnostics(lbm_t* h, double* out) {
+  if (!h || !out) return LBM_EINVAL;
+  if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set first");
+  cudaSetDevice(h->dev);
+  LBM_CUDA_TRY(h, cudaMemsetAsync(h->dred, 0, (MAX_SPECIES + 8) * sizeof(double), h->st));
+  LBM_CUDA_TRY(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->st));
+  LBM_CUDA_TRY(h, launch_diagnostics(h));
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(h->hred, h->dred, (MAX_SPECIES + 4) * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->st));
+  int bad = 0;
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(&bad, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  const int S = h->S;
+  for (int s = 0; s < S; ++s) out[s] = h->hred[s];
+  for (int d = 0; d < 3; ++d) out[S + d] = h->mass0 * h->hred[MAX_SPECIES + d];
+  out[S + 3] = h->hred[MAX_SPECIES + 3];
+  out[S + 4] = (double)h->last_iters;
+  out[S + 5] = h->last_res;
+  out[S + 6] = (double)h->tstep;
+  if (bad) return fail(h, LBM_EUNSTABLE, "non-finite or non-positive density detected");
+  return LBM_OK;
+}
+
+lbm_status lbm_get_state(lbm_t* h, float* state, int64_t* step) {
+  if (!h || !state) return LBM_EINVAL;
+  if (h->cfg.storage != LBM_FP32)
+    return fail(h, LBM_EINVAL, "raw state access needs FP32 storage");
+  cudaSetDevice(h->dev);
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(state, h->f[h->cur], (size_t)h->S * Q * h->N * sizeof(float),
+                                  cudaMemcpyDeviceToHost, h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  if (step) *step = h->tstep;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_t* h, const float* state, int64_t step) {
+  if (!h || !state) return LBM_EINVAL;
+  if (h->cfg.storage != LBM_FP32)
+    return fail(h, LBM_EINVAL, "raw state access needs FP32 storage");
+  if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set first");
+  cudaSetDevice(h->dev);
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(h->f[h->cur], state, (size_t)h->S * Q * h->N * sizeof(float),
+                                  cudaMemcpyHostToDevice, h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  h->tstep = step;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_timing(lbm_t* h, int enable) {
+  if (!h) return LBM_EINVAL;
+  cudaSetDevice(h->dev);
+  LBM_CUDA_TRY(h, drain_timing(h));
+  h->timing = enable != 0;
+  for (int k = 0; k < 3; ++k) {
+    h->t_acc[k] = 0.0;
+    h->t_cnt[k] = 0;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_timing(lbm_t* h, double* out) {
+  if (!h || !out) return LBM_EINVAL;
+  cudaSetDevice(h->dev);
+  LBM_CUDA_TRY(h, drain_timing(h));
+  for (int k = 0; k < 3; ++k) {
+    out[k] = h->t_acc[k];
+    out[3 + k] = (double)h->t_cnt[k];
+  }
+  return LBM_OK;
+}
+
+int64_t lbm_num_nodes(const lbm_t* h) { return h ? h->N : 0; }
+int64_t lbm_state_len(const lbm_t* h) { return h ? (int64_t)h->S * Q * h->N : 0; }
+void* lbm_stream(lbm_t* h) { return h ? (void*)h->own : nullptr; }
+
+const char* lbm_last_error(const lbm_t* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

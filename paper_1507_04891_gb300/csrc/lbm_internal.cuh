@@ -1,0 +1,146 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the C ABI (include/lbm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+
+namespace lbm_gb300 {
+
+constexpr int Q = 19;
+constexpr int MAX_SPECIES = 4;
+
+// Potential psi is held on the device as a signed 64-bit fixed-point number
+// with 44 fractional bits: psi = k * 2^-44 (|psi| < 2^19).  Sums and
+// differences of neighbouring values are then exact integer operations, so
+// the Poisson residual s - A psi is computed without cancellation error and
+// without FP64 arithmetic (FP64 throughput on GB300 is a small fraction of
+// FP32).  The smoothers work on FP32 corrections.
+constexpr double PSI_SCALE = 17592186044416.0;        // 2^44
+constexpr double PSI_INV_SCALE = 1.0 / 17592186044416.0;
+constexpr float PSI_SCALE_F = 17592186044416.0f;
+constexpr float PSI_INV_SCALE_F = 1.0f / 17592186044416.0f;
+constexpr double PSI_MAX = 524288.0;                  // 2^19
+
+// Per-node link word (only allocated when walls exist):
+//   bit 0      node is a wall node
+//   bit p      (p = 1..18) the upstream node r - c_p is a wall node
+constexpr uint32_t LINK_SOLID = 1u;
+
+struct StepArgs {
+  const void* fin;
+  void* fout;
+  const uint32_t* links;   // NULL without walls
+  const int64_t* psi;      // fixed point, lattice-sized; NULL when neutral
+  const float* wallq;      // face charge share of each wall node; may be NULL
+  int nx, ny, nz;
+  int64_t N;
+  float omega_visc, omega_drag;
+  float fourpi_lb;
+  float eext[3];
+  float valence[MAX_SPECIES];
+  float nref[MAX_SPECIES];  // reference density of the 16-bit shifted storage
+};
+
+struct PoissonLevel {
+  int nx, ny, nz;
+  int64_t n;
+  int per[3];        // periodic flags
+  int coarsened[3];  // 1 if this level halves that axis of the finer level
+  float* e = nullptr;     // correction
+  float* rhs = nullptr;   // right-hand side
+  float* K = nullptr;     // [3][n] conductance to the + neighbour (levels >= 1)
+  float* Dinv = nullptr;  // 1 / diagonal, 0 for an inactive cell (levels >= 1)
+};
+
+struct Poisson {
+  // box of the fine grid inside the lattice: x, y full, z in [zlo, zlo+nzb)
+  int zlo = 0, nzb = 0, perz = 1;
+  std::vector<PoissonLevel> lev;
+  int64_t* psi[2] = {nullptr, nullptr};  // lattice-sized fixed-point buffers
+  int cur = 0;
+  float* src = nullptr;   // 4 pi l_B (rho_e + w) per lattice node, no mean removed
+  double* dsum = nullptr; // [0] sum of src over fluid, [1] sum r^2, [2] sum s^2 (fixed units)
+  double* hsum = nullptr; // pinned mirror of dsum
+  int64_t nfluid = 0;
+  int coarse_sweeps = 100;
+  int nu1 = 2, nu2 = 2;
+};
+
+}  // namespace lbm_gb300
+
+struct lbm {
+  lbm_config cfg;
+  int S = 0;
+  int64_t N = 0;
+  int dev = 0;
+  cudaStream_t own = nullptr;
+  cudaStream_t st = nullptr;  // stream of the call in progress
+  size_t esize = 4;
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;
+  float mass[lbm_gb300::MAX_SPECIES] = {0};
+  float valence[lbm_gb300::MAX_SPECIES] = {0};
+  float nref[lbm_gb300::MAX_SPECIES] = {1, 1, 1, 1};
+  unsigned species_set = 0;
+  double mass0 = 0.0;
+  bool has_walls = false;
+  uint32_t* links = nullptr;
+  float* wallq = nullptr;
+  float* wcell = nullptr;
+  int64_t nfluid = 0;
+  lbm_gb300::Poisson ps;
+  bool psi_valid = false;
+  double* dred = nullptr;   // diagnostics reduction buffer (device)
+  double* hred = nullptr;   // pinned mirror
+  int* dflag = nullptr;
+  int last_iters = 0;
+  double last_res = 0.0;
+  int64_t tstep = 0;
+  // phase timing (lbm_set_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<int, int>>> ev_marks;  // phase, (start, stop)
+  size_t ev_used = 0;
+  double t_acc[3] = {0, 0, 0};
+  int64_t t_cnt[3] = {0, 0, 0};
+  std::string err;
+};
+
+namespace lbm_gb300 {
+
+// ---- lbm_kernels.cu ----
+cudaError_t launch_init_species(lbm_t* h, int s, const double* n0_dev,
+                                const double* u0_dev);
+cudaError_t launch_stream_collide(lbm_t* h);
+cudaError_t launch_charge(lbm_t* h);
+cudaError_t launch_gather(lbm_t* h, int s, double* n_dev, double* u_dev,
+                          double* f_dev);
+cudaError_t launch_diagnostics(lbm_t* h);
+cudaError_t launch_links(lbm_t* h, const uint8_t* solid_dev);
+cudaError_t launch_psi_to_double(lbm_t* h, const int64_t* psi, double* out);
+cudaError_t launch_psi_from_double(lbm_t* h, const double* in, int64_t* psi);
+cudaError_t launch_src_from_rho(lbm_t* h, const double* rho_dev);
+
+// ---- lbm_poisson.cu ----
+lbm_status poisson_setup(lbm_t* h, const uint8_t* solid_host);
+void poisson_free(lbm_t* h);
+// Solves A psi = src - mean starting from the current psi buffer.
+lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
+                         double* rel_res);
+
+}  // namespace lbm_gb300
+
+#define LBM_CUDA_TRY(h, call)                                              \
+  do {                                                                     \
+    cudaError_t _e = (call);                                               \
+    if (_e != cudaSuccess) {                                               \
+      (h)->err = std::string(#call) + ": " + cudaGetErrorString(_e);       \
+      return _e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;     \
+    }                                                                      \
+  } while (0)

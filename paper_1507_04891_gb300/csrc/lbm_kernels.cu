@@ -1,0 +1,666 @@
+// Lattice Boltzmann kernels of the two-timescale multicomponent scheme:
+// fused stream + moments + forces + collision, initialisation, charge
+// density, moment gathers and FP64 diagnostics.
+//
+// Storage: structure of arrays, one plane of N values per (species,
+// direction), f[(s*19 + p)*N + node], x fastest.  The stored lattice holds
+// post-collision populations before streaming; every kernel that needs
+// f(t) pulls them from the upstream node r - c_p (halfway bounce-back when
+// that node is a wall node), so streaming costs no separate pass.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbm_internal.cuh"
+
+namespace lbm_gb300 {
+namespace {
+
+// ---------------------------------------------------------------------------
+// D3Q19 velocity set (Sec. 4 of the paper: D3Q19 discretisation).  Written as
+// compile-time functions so that fully unrolled loops fold them away.
+//   0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 edge vectors, opposite pairs.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ constexpr int CX(int p) {
+  return (p == 1 || p == 7 || p == 9 || p == 11 || p == 13)    ? 1
+         : (p == 2 || p == 8 || p == 10 || p == 12 || p == 14) ? -1
+                                                               : 0;
+}
+__host__ __device__ __forceinline__ constexpr int CY(int p) {
+  return (p == 3 || p == 7 || p == 10 || p == 15 || p == 17)   ? 1
+         : (p == 4 || p == 8 || p == 9 || p == 16 || p == 18)  ? -1
+                                                               : 0;
+}
+__host__ __device__ __forceinline__ constexpr int CZ(int p) {
+  return (p == 5 || p == 11 || p == 14 || p == 15 || p == 18)  ? 1
+         : (p == 6 || p == 12 || p == 13 || p == 16 || p == 17) ? -1
+                                                                : 0;
+}
+__host__ __device__ __forceinline__ constexpr int OPP(int p) {
+  return p == 0 ? 0 : ((p & 1) ? p + 1 : p - 1);
+}
+// Lattice weights Gamma_0(c_p) (Appendix): 1/3, 1/18, 1/36.
+__host__ __device__ __forceinline__ constexpr float WT(int p) {
+  return p == 0 ? (1.0f / 3.0f) : (p <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f));
+}
+constexpr float CS2 = 1.0f / 3.0f;
+
+// ---------------------------------------------------------------------------
+// Population storage formats.  The 16-bit formats store the relative
+// deviation from the rest state of the species, h = f / (w_p n_ref) - 1, so
+// that dilute ions keep their relative precision.
+// ---------------------------------------------------------------------------
+template <int ST>
+struct Fmt;
+template <>
+struct Fmt<LBM_FP32> {
+  using T = float;
+  static __device__ __forceinline__ float ld(const T* p, float) { return *p; }
+  static __device__ __forceinline__ void st(T* p, float v, float) { *p = v; }
+};
+template <>
+struct Fmt<LBM_FP16_SHIFT> {
+  using T = __half;
+  static __device__ __forceinline__ float ld(const T* p, float wn) {
+    return wn * (1.0f + __half2float(*p));
+  }
+  static __device__ __forceinline__ void st(T* p, float v, float wn) {
+    *p = __float2half_rn(v / wn - 1.0f);
+  }
+};
+template <>
+struct Fmt<LBM_BF16_SHIFT> {
+  using T = __nv_bfloat16;
+  static __device__ __forceinline__ float ld(const T* p, float wn) {
+    return wn * (1.0f + __bfloat162float(*p));
+  }
+  static __device__ __forceinline__ void st(T* p, float v, float wn) {
+    *p = __float2bfloat16_rn(v / wn - 1.0f);
+  }
+};
+
+struct Nbr {
+  // signed offsets to the upstream node along each axis for c = +1 / -1
+  int dxm, dxp, dym, dyp, dzm, dzp;
+};
+
+__device__ __forceinline__ Nbr neighbours(int x, int y, int z, int nx, int ny,
+                                          int nz) {
+  const int nxy = nx * ny;
+  Nbr o;
+  o.dxm = (x == 0) ? nx - 1 : -1;  // node x-1
+  o.dxp = (x == nx - 1) ? -(nx - 1) : 1;
+  o.dym = ((y == 0) ? ny - 1 : -1) * nx;
+  o.dyp = ((y == ny - 1) ? -(ny - 1) : 1) * nx;
+  o.dzm = ((z == 0) ? nz - 1 : -1) * nxy;
+  o.dzp = ((z == nz - 1) ? -(nz - 1) : 1) * nxy;
+  return o;
+}
+
+// Offset from node r to the upstream node r - c_p.
+__device__ __forceinline__ int upstream(const Nbr& o, int p) {
+  const int cx = CX(p), cy = CY(p), cz = CZ(p);
+  int d = 0;
+  d += cx == 1 ? o.dxm : (cx == -1 ? o.dxp : 0);
+  d += cy == 1 ? o.dym : (cy == -1 ? o.dyp : 0);
+  d += cz == 1 ? o.dzm : (cz == -1 ? o.dzp : 0);
+  return d;
+}
+
+// Pulls f_p(r, t) of species s: the post-collision value of r - c_p, or the
+// reversed population of r itself when r - c_p is a wall node.
+template <int ST, bool WALLS>
+__device__ __forceinline__ float pull(const typename Fmt<ST>::T* __restrict__ f,
+                                      int64_t N, int s, int p, uint32_t i,
+                                      int d, uint32_t lk, float nref) {
+  const float wn = WT(p) * nref;
+  if (WALLS && ((lk >> p) & 1u)) {
+    return Fmt<ST>::ld(f + (int64_t)(s * Q + OPP(p)) * N + i, wn);
+  }
+  return Fmt<ST>::ld(f + (int64_t)(s * Q + p) * N + (int64_t)((int)i + d), wn);
+}
+
+__device__ __forceinline__ void site_xyz(uint32_t i, int nx, int ny, int& x,
+                                         int& y, int& z) {
+  const uint32_t t = i / (uint32_t)nx;
+  x = (int)(i - t * (uint32_t)nx);
+  z = (int)(t / (uint32_t)ny);
+  y = (int)(t - (uint32_t)z * (uint32_t)ny);
+}
+
+// Gradient of psi at node i: mean of the two face gradients along each axis.
+// A wall face takes the Neumann value of the surface-charge condition,
+// d psi / d n_out = 4 pi l_B q (q: charge share of the wall node).
+template <bool WALLS>
+__device__ __forceinline__ void psi_gradient(const StepArgs& a, uint32_t i,
+                                             const Nbr& o, uint32_t lk,
+                                             float& gx, float& gy, float& gz) {
+  const int64_t pc = a.psi[i];
+  const int ii = (int)i;
+  const int64_t pxp = a.psi[ii + o.dxp], pxm = a.psi[ii + o.dxm];
+  const int64_t pyp = a.psi[ii + o.dyp], pym = a.psi[ii + o.dym];
+  const int64_t pzp = a.psi[ii + o.dzp], pzm = a.psi[ii + o.dzm];
+  float gpx = (float)(pxp - pc) * PSI_INV_SCALE_F;
+  float gmx = (float)(pc - pxm) * PSI_INV_SCALE_F;
+  float gpy = (float)(pyp - pc) * PSI_INV_SCALE_F;
+  float gmy = (float)(pc - pym) * PSI_INV_SCALE_F;
+  float gpz = (float)(pzp - pc) * PSI_INV_SCALE_F;
+  float gmz = (float)(pc - pzm) * PSI_INV_SCALE_F;
+  if (WALLS) {
+    // bit 2: r + x is a wall node; bit 1: r - x; 4: +y; 3: -y; 6: +z; 5: -z
+    const float k = a.fourpi_lb;
+    if (lk & (1u << 2)) gpx = a.wallq ? k * a.wallq[ii + o.dxp] : 0.0f;
+    if (lk & (1u << 1)) gmx = a.wallq ? -k * a.wallq[ii + o.dxm] : 0.0f;
+    if (lk & (1u << 4)) gpy = a.wallq ? k * a.wallq[ii + o.dyp] : 0.0f;
+    if (lk & (1u << 3)) gmy = a.wallq ? -k * a.wallq[ii + o.dym] : 0.0f;
+    if (lk & (1u << 6)) gpz = a.wallq ? k * a.wallq[ii + o.dzp] : 0.0f;
+    if (lk & (1u << 5)) gmz = a.wallq ? -k * a.wallq[ii + o.dzm] : 0.0f;
+  }
+  gx = 0.5f * (gpx + gmx);
+  gy = 0.5f * (gpy + gmy);
+  gz = 0.5f * (gpz + gmz);
+}
+
+// ---------------------------------------------------------------------------
+// Fused stream + collide, one thread per node, all S species in registers.
+//   1. pull the 19*S populations f_p^alpha(r, t)            (Eq. latboeq, lhs)
+//   2. n^alpha, bare u^alpha = sum c f / n, barycentric u   (Sec. 3 definitions)
+//   3. F^alpha = F_el + F_drag: electric z(-c_s^2 grad psi + E) and the drag
+//      -omega_drag sum_beta (n_beta/n)(u^a - u^b) on velocities shifted by
+//      half the electric acceleration                       (Sec. 2)
+//   4. f* = f - omega_visc (f - phi_perp) + g_p              (Eq. latboeq, rhs)
+//      phi_perp in its reduced form n w [1 + 3 a + 4.5 a^2 - 1.5 |u^a|^2],
+//      a = u^a . c (algebraically equal to the Appendix expression);
+//      g_p = n w [3 F.c + 9 (F.c)(u.c) - 3 F.u]             (Eq. ourforc)
+//   5. store f* at r.
+// ---------------------------------------------------------------------------
+template <int S, bool WALLS, bool CHARGED, int ST>
+__global__ void __launch_bounds__(128) k_stream_collide(const StepArgs a) {
+  using T = typename Fmt<ST>::T;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (uint32_t)a.N) return;
+  uint32_t lk = 0;
+  if (WALLS) {
+    lk = a.links[i];
+    if (lk & LINK_SOLID) return;
+  }
+  int x, y, z;
+  site_xyz(i, a.nx, a.ny, x, y, z);
+  const Nbr o = neighbours(x, y, z, a.nx, a.ny, a.nz);
+  const T* __restrict__ fin = static_cast<const T*>(a.fin);
+  T* __restrict__ fout = static_cast<T*>(a.fout);
+  const int64_t N = a.N;
+
+  float f[S][Q];
+#pragma unroll
+  for (int p = 0; p < Q; ++p) {
+    const int d = upstream(o, p);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      f[s][p] = pull<ST, WALLS>(fin, N, s, p, i, d, lk, a.nref[s]);
+    }
+  }
+
+  float n[S], jx[S], jy[S], jz[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    float m0 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+    for (int p = 0; p < Q; ++p) {
+      m0 += f[s][p];
+      if (CX(p)) mx += CX(p) * f[s][p];
+      if (CY(p)) my += CY(p) * f[s][p];
+      if (CZ(p)) mz += CZ(p) * f[s][p];
+    }
+    n[s] = m0;
+    jx[s] = mx;
+    jy[s] = my;
+    jz[s] = mz;
+  }
+
+  float ntot = 0.f, Jx = 0.f, Jy = 0.f, Jz = 0.f;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    ntot += n[s];
+    Jx += jx[s];
+    Jy += jy[s];
+    Jz += jz[s];
+  }
+  const float inv_ntot = 1.0f / ntot;
+  // barycentric velocity (equal masses: mass-weighted = number-weighted)
+  const float ux = Jx * inv_ntot, uy = Jy * inv_ntot, uz = Jz * inv_ntot;
+
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  if (CHARGED) psi_gradient<WALLS>(a, i, o, lk, gx, gy, gz);
+  const float Ex = -CS2 * gx + a.eext[0];
+  const float Ey = -CS2 * gy + a.eext[1];
+  const float Ez = -CS2 * gz + a.eext[2];
+
+  // number-weighted mean of the drag velocities u^a + F_el^a / 2
+  float zn = 0.f;
+#pragma unroll
+  for (int s = 0; s < S; ++s) zn += a.valence[s] * n[s];
+  const float vbx = (Jx + 0.5f * zn * Ex) * inv_ntot;
+  const float vby = (Jy + 0.5f * zn * Ey) * inv_ntot;
+  const float vbz = (Jz + 0.5f * zn * Ez) * inv_ntot;
+
+  const float om = a.omega_visc, omd = a.omega_drag;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const float inv_n = 1.0f / n[s];
+    const float usx = jx[s] * inv_n, usy = jy[s] * inv_n, usz = jz[s] * inv_n;
+    const float zs = a.valence[s];
+    const float ex = zs * Ex, ey = zs * Ey, ez = zs * Ez;
+    const float Fx = ex - omd * (usx + 0.5f * ex - vbx);
+    const float Fy = ey - omd * (usy + 0.5f * ey - vby);
+    const float Fz = ez - omd * (usz + 0.5f * ez - vbz);
+    const float usq = usx * usx + usy * usy + usz * usz;
+    const float Fu = Fx * ux + Fy * uy + Fz * uz;
+    // p-independent part of omega*phi/(n w) + g/(n w)
+    const float base = om * (1.0f - 1.5f * usq) - 3.0f * Fu;
+    const float nr = a.nref[s];
+#pragma unroll
+    for (int p = 0; p < Q; ++p) {
+      const float av = CX(p) * usx + CY(p) * usy + CZ(p) * usz;
+      const float fc = CX(p) * Fx + CY(p) * Fy + CZ(p) * Fz;
+      const float uc = CX(p) * ux + CY(p) * uy + CZ(p) * uz;
+      const float wn = WT(p) * n[s];
+      const float src = base + om * (3.0f * av + 4.5f * av * av) +
+                        3.0f * fc + 9.0f * fc * uc;
+      const float fo = (1.0f - om) * f[s][p] + wn * src;
+      Fmt<ST>::st(fout + (int64_t)(s * Q + p) * N + i, fo, WT(p) * nr);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation: f_p(r, 0) = phi_perp,p(n0, u0), i.e. the equilibrium at the
+// species velocity, written to the stored lattice at the upstream node so
+// that the next pull returns it (inverse streaming).
+// ---------------------------------------------------------------------------
+template <bool WALLS, int ST>
+__global__ void k_init(int s, const double* __restrict__ n0,
+                       const double* __restrict__ u0, const uint32_t* links,
+                       void* fout_v, int nx, int ny, int nz, int64_t N,
+                       float nref) {
+  using T = typename Fmt<ST>::T;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (uint32_t)N) return;
+  uint32_t lk = 0;
+  if (WALLS) {
+    lk = links[i];
+    if (lk & LINK_SOLID) return;
+  }
+  int x, y, z;
+  site_xyz(i, nx, ny, x, y, z);
+  const Nbr o = neighbours(x, y, z, nx, ny, nz);
+  T* fout = static_cast<T*>(fout_v);
+  const float n = (float)n0[i];
+  float vx = 0.f, vy = 0.f, vz = 0.f;
+  if (u0) {
+    vx = (float)u0[i];
+    vy = (float)u0[N + i];
+    vz = (float)u0[2 * N + i];
+  }
+  const float usq = vx * vx + vy * vy + vz * vz;
+#pragma unroll
+  for (int p = 0; p < Q; ++p) {
+    const float av = CX(p) * vx + CY(p) * vy + CZ(p) * vz;
+    const float feq = WT(p) * n * (1.0f + 3.0f * av + 4.5f * av * av - 1.5f * usq);
+    int64_t dst;
+    int q = p;
+    if (WALLS && ((lk >> p) & 1u)) {
+      q = OPP(p);
+      dst = i;
+    } else {
+      dst = (int64_t)((int)i + upstream(o, p));
+    }
+    Fmt<ST>::st(fout + (int64_t)(s * Q + q) * N + dst, feq, WT(q) * nref);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Charge density for the Poisson source: s_r = 4 pi l_B (rho_e + w_r) with
+// rho_e = sum_alpha z^alpha n^alpha(r, t) from the pulled populations of the
+// charged species; block sums of s over fluid nodes go to dsum[0] (FP64).
+// ---------------------------------------------------------------------------
+template <bool WALLS, int ST>
+__global__ void __launch_bounds__(256) k_charge(
+    const void* fin_v, const uint32_t* links, const float* wcell, float* src,
+    double* dsum, int nx, int ny, int nz, int64_t N, int S, float4 val,
+    float4 nref, float fourpi_lb) {
+  using T = typename Fmt<ST>::T;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  float sv = 0.f;
+  if (i < (uint32_t)N) {
+    uint32_t lk = 0;
+    bool fluid = true;
+    if (WALLS) {
+      lk = links[i];
+      fluid = !(lk & LINK_SOLID);
+    }
+    if (fluid) {
+      int x, y, z;
+      site_xyz(i, nx, ny, x, y, z);
+      const Nbr o = neighbours(x, y, z, nx, ny, nz);
+      const T* fin = static_cast<const T*>(fin_v);
+      const float vz[4] = {val.x, val.y, val.z, val.w};
+      const float nr[4] = {nref.x, nref.y, nref.z, nref.w};
+      float rho = 0.f;
+      for (int s = 0; s < S; ++s) {
+        if (vz[s] == 0.f) continue;
+        float m0 = 0.f;
+#pragma unroll
+        for (int p = 0; p < Q; ++p)
+          m0 += pull<ST, WALLS>(fin, N, s, p, i, upstream(o, p), lk, nr[s]);
+        rho += vz[s] * m0;
+      }
+      if (wcell) rho += wcell[i];
+      sv = fourpi_lb * rho;
+    }
+    src[i] = sv;
+  }
+  // block reduction of sv
+  __shared__ float red[8];
+  float v = sv;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += (double)red[w];
+    atomicAdd(dsum, tot);
+  }
+}
+
+// Gathers f(t) of species s and its moments n, u = sum c f / n (doubles).
+template <bool WALLS, int ST>
+__global__ void k_gather(const void* fin_v, const uint32_t* links, int s,
+                         int nx, int ny, int nz, int64_t N, float nref,
+                         double* n_out, double* u_out, double* f_out) {
+  using T = typename Fmt<ST>::T;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (uint32_t)N) return;
+  uint32_t lk = 0;
+  if (WALLS) lk = links[i];
+  if (WALLS && (lk & LINK_SOLID)) {
+    if (n_out) n_out[i] = 0.0;
+    if (u_out) u_out[i] = u_out[N + i] = u_out[2 * N + i] = 0.0;
+    if (f_out)
+      for (int p = 0; p < Q; ++p) f_out[(int64_t)p * N + i] = 0.0;
+    return;
+  }
+  int x, y, z;
+  site_xyz(i, nx, ny, x, y, z);
+  const Nbr o = neighbours(x, y, z, nx, ny, nz);
+  const T* fin = static_cast<const T*>(fin_v);
+  double m0 = 0, mx = 0, my = 0, mz = 0;
+#pragma unroll
+  for (int p = 0; p < Q; ++p) {
+    const float v = pull<ST, WALLS>(fin, N, s, p, i, upstream(o, p), lk, nref);
+    if (f_out) f_out[(int64_t)p * N + i] = (double)v;
+    m0 += v;
+    mx += CX(p) * (double)v;
+    my += CY(p) * (double)v;
+    mz += CZ(p) * (double)v;
+  }
+  if (n_out) n_out[i] = m0;
+  if (u_out) {
+    u_out[i] = mx / m0;
+    u_out[N + i] = my / m0;
+    u_out[2 * N + i] = mz / m0;
+  }
+}
+
+// FP64 diagnostics: per-species particle number, total momentum, net charge;
+// flags non-finite or non-positive densities.  out layout as lbm_diagnostics.
+template <bool WALLS, int ST>
+__global__ void __launch_bounds__(256) k_diag(const void* fin_v,
+                                              const uint32_t* links, int nx,
+                                              int ny, int nz, int64_t N, int S,
+                                              float4 val, float4 nref,
+                                              double* out, int* bad) {
+  using T = typename Fmt<ST>::T;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[MAX_SPECIES + 4];
+  for (int k = 0; k < MAX_SPECIES + 4; ++k) acc[k] = 0.0;
+  if (i < (uint32_t)N) {
+    uint32_t lk = 0;
+    bool fluid = true;
+    if (WALLS) {
+      lk = links[i];
+      fluid = !(lk & LINK_SOLID);
+    }
+    if (fluid) {
+      int x, y, z;
+      site_xyz(i, nx, ny, x, y, z);
+      const Nbr o = neighbours(x, y, z, nx, ny, nz);
+      const T* fin = static_cast<const T*>(fin_v);
+      const float vz[4] = {val.x, val.y, val.z, val.w};
+      const float nr[4] = {nref.x, nref.y, nref.z, nref.w};
+      for (int s = 0; s < S; ++s) {
+        float m0 = 0, mx = 0, my = 0, mz = 0;
+#pragma unroll
+        for (int p = 0; p < Q; ++p) {
+          const float v = pull<ST, WALLS>(fin, N, s, p, i, upstream(o, p), lk, nr[s]);
+          m0 += v;
+          mx += CX(p) * v;
+          my += CY(p) * v;
+          mz += CZ(p) * v;
+        }
+        if (!(m0 > 0.f) || !isfinite(m0) || !isfinite(mx) || !isfinite(my) ||
+            !isfinite(mz))
+          atomicOr(bad, 1);
+        acc[s] = m0;
+        acc[MAX_SPECIES + 0] += mx;
+        acc[MAX_SPECIES + 1] += my;
+        acc[MAX_SPECIES + 2] += mz;
+        acc[MAX_SPECIES + 3] += (double)vz[s] * m0;
+      }
+    }
+  }
+  __shared__ double red[8][MAX_SPECIES + 4];
+  for (int k = 0; k < MAX_SPECIES + 4; ++k) {
+    double v = acc[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < MAX_SPECIES + 4) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w][threadIdx.x];
+    atomicAdd(out + threadIdx.x, tot);
+  }
+}
+
+// Link words from the wall mask: bit 0 = wall node, bit p = r - c_p is wall.
+__global__ void k_links(const uint8_t* solid, uint32_t* links, int nx, int ny,
+                        int nz, int64_t N) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (uint32_t)N) return;
+  int x, y, z;
+  site_xyz(i, nx, ny, x, y, z);
+  const Nbr o = neighbours(x, y, z, nx, ny, nz);
+  uint32_t w = solid[i] ? LINK_SOLID : 0u;
+#pragma unroll
+  for (int p = 1; p < Q; ++p)
+    if (solid[(int)i + upstream(o, p)]) w |= 1u << p;
+  links[i] = w;
+}
+
+__global__ void k_psi_to_double(const int64_t* psi, double* out, int64_t N) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) out[i] = (double)psi[i] * PSI_INV_SCALE;
+}
+
+__global__ void k_psi_from_double(const double* in, int64_t* psi,
+                                  const uint32_t* links, int64_t N) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const bool solid = links && (links[i] & LINK_SOLID);
+  psi[i] = solid ? 0 : llrint(in[i] * PSI_SCALE);
+}
+
+__global__ void __launch_bounds__(256) k_src_from_rho(
+    const double* rho, const uint32_t* links, const float* wcell, float* src,
+    double* dsum, int64_t N, float fourpi_lb) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float sv = 0.f;
+  if (i < N) {
+    const bool solid = links && (links[i] & LINK_SOLID);
+    if (!solid) sv = fourpi_lb * ((float)rho[i] + (wcell ? wcell[i] : 0.f));
+    src[i] = sv;
+  }
+  __shared__ float red[8];
+  float v = sv;
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += (double)red[w];
+    atomicAdd(dsum, tot);
+  }
+}
+
+inline unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <int S, bool W, bool C, int ST>
+cudaError_t launch_sc(const StepArgs& a, cudaStream_t st) {
+  k_stream_collide<S, W, C, ST><<<nblocks(a.N, 128), 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int S, int ST>
+cudaError_t dispatch_wc(const StepArgs& a, bool w, bool c, cudaStream_t st) {
+  if (w) return c ? launch_sc<S, true, true, ST>(a, st) : launch_sc<S, true, false, ST>(a, st);
+  return c ? launch_sc<S, false, true, ST>(a, st) : launch_sc<S, false, false, ST>(a, st);
+}
+
+template <int ST>
+cudaError_t dispatch_s(const StepArgs& a, int S, bool w, bool c, cudaStream_t st) {
+  switch (S) {
+    case 1: return dispatch_wc<1, ST>(a, w, c, st);
+    case 2: return dispatch_wc<2, ST>(a, w, c, st);
+    case 3: return dispatch_wc<3, ST>(a, w, c, st);
+    case 4: return dispatch_wc<4, ST>(a, w, c, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+float4 as_f4(const float* v) { return make_float4(v[0], v[1], v[2], v[3]); }
+
+}  // namespace
+
+cudaError_t launch_stream_collide(lbm_t* h) {
+  StepArgs a;
+  a.fin = h->f[h->cur];
+  a.fout = h->f[h->cur ^ 1];
+  a.links = h->links;
+  const bool charged = h->cfg.bjerrum > 0.0;
+  a.psi = charged ? h->ps.psi[h->ps.cur] : nullptr;
+  a.wallq = h->wallq;
+  a.nx = h->cfg.nx;
+  a.ny = h->cfg.ny;
+  a.nz = h->cfg.nz;
+  a.N = h->N;
+  a.omega_visc = (float)h->cfg.omega_visc;
+  a.omega_drag = (float)h->cfg.omega_drag;
+  a.fourpi_lb = (float)(4.0 * 3.14159265358979323846 * h->cfg.bjerrum);
+  for (int d = 0; d < 3; ++d) a.eext[d] = (float)h->cfg.e_ext[d];
+  for (int s = 0; s < MAX_SPECIES; ++s) {
+    a.valence[s] = h->valence[s];
+    a.nref[s] = h->nref[s];
+  }
+  cudaError_t e;
+  switch (h->cfg.storage) {
+    case LBM_FP32: e = dispatch_s<LBM_FP32>(a, h->S, h->has_walls, charged, h->st); break;
+    case LBM_FP16_SHIFT: e = dispatch_s<LBM_FP16_SHIFT>(a, h->S, h->has_walls, charged, h->st); break;
+    case LBM_BF16_SHIFT: e = dispatch_s<LBM_BF16_SHIFT>(a, h->S, h->has_walls, charged, h->st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e == cudaSuccess) h->cur ^= 1;
+  return e;
+}
+
+#define LBM_DISPATCH_WS(h, KERNEL_CALL)                                        \
+  do {                                                                         \
+    const bool _w = (h)->has_walls;                                            \
+    switch ((h)->cfg.storage) {                                                \
+      case LBM_FP32:                                                           \
+        if (_w) { constexpr bool W_ = true; constexpr int ST_ = LBM_FP32; KERNEL_CALL; } \
+        else { constexpr bool W_ = false; constexpr int ST_ = LBM_FP32; KERNEL_CALL; } \
+        break;                                                                 \
+      case LBM_FP16_SHIFT:                                                     \
+        if (_w) { constexpr bool W_ = true; constexpr int ST_ = LBM_FP16_SHIFT; KERNEL_CALL; } \
+        else { constexpr bool W_ = false; constexpr int ST_ = LBM_FP16_SHIFT; KERNEL_CALL; } \
+        break;                                                                 \
+      default:                                                                 \
+        if (_w) { constexpr bool W_ = true; constexpr int ST_ = LBM_BF16_SHIFT; KERNEL_CALL; } \
+        else { constexpr bool W_ = false; constexpr int ST_ = LBM_BF16_SHIFT; KERNEL_CALL; } \
+        break;                                                                 \
+    }                                                                          \
+  } while (0)
+
+cudaError_t launch_init_species(lbm_t* h, int s, const double* n0,
+                                const double* u0) {
+  const int nb = nblocks(h->N, 256);
+  LBM_DISPATCH_WS(h, (k_init<W_, ST_><<<nb, 256, 0, h->st>>>(
+                         s, n0, u0, h->links, h->f[h->cur], h->cfg.nx,
+                         h->cfg.ny, h->cfg.nz, h->N, h->nref[s])));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_charge(lbm_t* h) {
+  const int nb = nblocks(h->N, 256);
+  const float k = (float)(4.0 * 3.14159265358979323846 * h->cfg.bjerrum);
+  LBM_DISPATCH_WS(h, (k_charge<W_, ST_><<<nb, 256, 0, h->st>>>(
+                         h->f[h->cur], h->links, h->wcell, h->ps.src,
+                         h->ps.dsum, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,
+                         h->S, as_f4(h->valence), as_f4(h->nref), k)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(lbm_t* h, int s, double* n_dev, double* u_dev,
+                          double* f_dev) {
+  const int nb = nblocks(h->N, 256);
+  LBM_DISPATCH_WS(h, (k_gather<W_, ST_><<<nb, 256, 0, h->st>>>(
+                         h->f[h->cur], h->links, s, h->cfg.nx, h->cfg.ny,
+                         h->cfg.nz, h->N, h->nref[s], n_dev, u_dev, f_dev)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(lbm_t* h) {
+  const int nb = nblocks(h->N, 256);
+  LBM_DISPATCH_WS(h, (k_diag<W_, ST_><<<nb, 256, 0, h->st>>>(
+                         h->f[h->cur], h->links, h->cfg.nx, h->cfg.ny,
+                         h->cfg.nz, h->N, h->S, as_f4(h->valence),
+                         as_f4(h->nref), h->dred, h->dflag)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_links(lbm_t* h, const uint8_t* solid_dev) {
+  k_links<<<nblocks(h->N, 256), 256, 0, h->st>>>(solid_dev, h->links, h->cfg.nx,
+                                                h->cfg.ny, h->cfg.nz, h->N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_psi_to_double(lbm_t* h, const int64_t* psi, double* out) {
+  k_psi_to_double<<<nblocks(h->N, 256), 256, 0, h->st>>>(psi, out, h->N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_psi_from_double(lbm_t* h, const double* in, int64_t* psi) {
+  k_psi_from_double<<<nblocks(h->N, 256), 256, 0, h->st>>>(in, psi, h->links, h->N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_src_from_rho(lbm_t* h, const double* rho_dev) {
+  const float k = (float)(4.0 * 3.14159265358979323846 * h->cfg.bjerrum);
+  k_src_from_rho<<<nblocks(h->N, 256), 256, 0, h->st>>>(
+      rho_dev, h->links, h->wcell, h->ps.src, h->ps.dsum, h->N, k);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm_gb300

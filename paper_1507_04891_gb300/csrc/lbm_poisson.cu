@@ -1,0 +1,768 @@
+// Poisson solve for the mean-field potential of the charged mixture:
+//   nabla^2 psi = -4 pi l_B sum_alpha z^alpha n^alpha          (Eq. Poisson)
+// with the surface-charge Neumann condition at wall faces.  Discretised by
+// finite volumes on the lattice cells:
+//   (A psi)_i = sum_{open faces j} (psi_i - psi_j) = s_i - <s>,
+//   s_i = 4 pi l_B (rho_e,i + w_i)
+// (w_i: wall charge handed to cell i).  The mean <s> over fluid cells is
+// removed (neutralising background), which makes the periodic / Neumann
+// problem solvable.
+//
+// psi is a 64-bit fixed-point field (see lbm_internal.cuh), so the residual
+// s - A psi is exact integer arithmetic and the 1e-8 relative residual is
+// reached without FP64 arithmetic.  Two solvers work on FP32 corrections:
+//   - geometric multigrid used for defect correction: cell-centred V(2,2)
+//     cycles, red-black Gauss-Seidel smoothing, restriction by summing the
+//     8 children, trilinear prolongation, coarse face conductances
+//     (sum of the crossing fine ones) * h_fine/h_coarse, one-CTA coarsest
+//     solve;
+//   - red-black SOR directly on the fixed-point psi.
+// Convergence is tested on the FP64 norm ratio ||s - A psi||_2 / ||s||_2.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+namespace lbm_gb300 {
+namespace {
+
+struct Box {
+  int nx, ny, nzb, zlo, perz;
+  int64_t nxy;
+};
+
+// open-face bits from the link word: bit 2 of the link word = +x neighbour
+// is a wall node, 1 = -x, 4 = +y, 3 = -y, 6 = +z, 5 = -z.
+__device__ __forceinline__ bool open_face(uint32_t lk, int face) {
+  // face: 0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z
+  const int bit = (face & 1) ? face : face + 2;  // 0->2, 1->1, 2->4, 3->3, 4->6, 5->5
+  return !((lk >> bit) & 1u);
+}
+
+// box-cell neighbour offsets (periodic x, y; z periodic only if perz)
+__device__ __forceinline__ void box_nbr(const Box& b, int x, int y, int z,
+                                        int (&d)[6]) {
+  d[0] = (x == b.nx - 1) ? -(b.nx - 1) : 1;
+  d[1] = (x == 0) ? (b.nx - 1) : -1;
+  d[2] = ((y == b.ny - 1) ? -(b.ny - 1) : 1) * b.nx;
+  d[3] = ((y == 0) ? (b.ny - 1) : -1) * b.nx;
+  const int nxy = b.nx * b.ny;
+  if (b.perz) {
+    d[4] = ((z == b.nzb - 1) ? -(b.nzb - 1) : 1) * nxy;
+    d[5] = ((z == 0) ? (b.nzb - 1) : -1) * nxy;
+  } else {
+    d[4] = (z == b.nzb - 1) ? 0 : nxy;
+    d[5] = (z == 0) ? 0 : -nxy;
+  }
+}
+
+__device__ __forceinline__ void box_xyz(uint32_t c, const Box& b, int& x,
+                                        int& y, int& z) {
+  const uint32_t t = c / (uint32_t)b.nx;
+  x = (int)(c - t * (uint32_t)b.nx);
+  z = (int)(t / (uint32_t)b.ny);
+  y = (int)(t - (uint32_t)z * (uint32_t)b.ny);
+}
+
+__device__ __forceinline__ int64_t fx_of(float e) {
+  return llrintf(e * PSI_SCALE_F);
+}
+
+// Residual on the fine box, optionally applying the correction first:
+//   psi_new = psi_in + round(e),  r = s - <s> - A psi_new   (exact in int64)
+// Writes r (FP32) to rhs, psi_new to psi_out, and block sums of r^2 and
+// (s - <s>)^2 (fixed-point units) to dsum[1], dsum[2].
+template <bool WALLS, bool UPDATE>
+__global__ void __launch_bounds__(256) k_res0(
+    const int64_t* __restrict__ psi_in, const float* __restrict__ e,
+    int64_t* __restrict__ psi_out, const float* __restrict__ src,
+    const uint32_t* __restrict__ links, float* __restrict__ r, double* dsum,
+    Box b, int64_t nbox, double inv_nfluid) {
+  __shared__ long long s_mean;
+  __shared__ float red_r[8], red_s[8];
+  if (threadIdx.x == 0) s_mean = llrint(dsum[0] * inv_nfluid * PSI_SCALE);
+  __syncthreads();
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  float rr = 0.f, ss = 0.f;
+  if (c < (uint32_t)nbox) {
+    const int64_t i = (int64_t)c + (int64_t)b.zlo * b.nxy;  // lattice node
+    uint32_t lk = 0;
+    if (WALLS) lk = links[i];
+    if (WALLS && (lk & LINK_SOLID)) {
+      r[c] = 0.f;
+      if (UPDATE) psi_out[i] = 0;
+    } else {
+      int x, y, z;
+      box_xyz(c, b, x, y, z);
+      int d[6];
+      box_nbr(b, x, y, z, d);
+      int64_t pc = psi_in[i];
+      if (UPDATE) pc += fx_of(e[c]);
+      int64_t Ap = 0;
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        if (WALLS && !open_face(lk, f)) continue;
+        int64_t pn = psi_in[i + d[f]];
+        if (UPDATE) pn += fx_of(e[(int64_t)c + d[f]]);
+        Ap += pc - pn;
+      }
+      const int64_t sfx = (int64_t)(src[i] * PSI_SCALE_F) - s_mean;
+      const int64_t rfx = sfx - Ap;
+      const float rf = (float)rfx;
+      r[c] = rf * PSI_INV_SCALE_F;
+      if (UPDATE) psi_out[i] = pc;
+      rr = rf * rf;
+      const float sf = (float)sfx;
+      ss = sf * sf;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    rr += __shfl_down_sync(0xffffffffu, rr, off);
+    ss += __shfl_down_sync(0xffffffffu, ss, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_r[threadIdx.x >> 5] = rr;
+    red_s[threadIdx.x >> 5] = ss;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0, ts = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tr += (double)red_r[w];
+      ts += (double)red_s[w];
+    }
+    atomicAdd(dsum + 1, tr);
+    atomicAdd(dsum + 2, ts);
+  }
+}
+
+// Red-black Gauss-Seidel on the fine box for A e = r (FP32).
+template <bool WALLS>
+__global__ void __launch_bounds__(256) k_smooth0(
+    float* __restrict__ e, const float* __restrict__ r,
+    const uint32_t* __restrict__ links, Box b, int64_t nbox, int color) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= (uint32_t)nbox) return;
+  int x, y, z;
+  box_xyz(c, b, x, y, z);
+  if (((x + y + z) & 1) != color) return;
+  uint32_t lk = 0;
+  if (WALLS) {
+    lk = links[(int64_t)c + (int64_t)b.zlo * b.nxy];
+    if (lk & LINK_SOLID) return;
+  }
+  int d[6];
+  box_nbr(b, x, y, z, d);
+  float sum = r[c];
+  int cnt = 0;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    if (WALLS && !open_face(lk, f)) continue;
+    sum += e[(int64_t)c + d[f]];
+    ++cnt;
+  }
+  if (cnt > 0) e[c] = sum / (float)cnt;
+}
+
+// Red-black SOR directly on the fixed-point psi (in place).
+template <bool WALLS>
+__global__ void __launch_bounds__(256) k_sor0(
+    int64_t* __restrict__ psi, const float* __restrict__ src,
+    const uint32_t* __restrict__ links, const double* dsum, Box b,
+    int64_t nbox, double inv_nfluid, int color, float omega) {
+  __shared__ long long s_mean;
+  if (threadIdx.x == 0) s_mean = llrint(dsum[0] * inv_nfluid * PSI_SCALE);
+  __syncthreads();
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= (uint32_t)nbox) return;
+  int x, y, z;
+  box_xyz(c, b, x, y, z);
+  if (((x + y + z) & 1) != color) return;
+  const int64_t i = (int64_t)c + (int64_t)b.zlo * b.nxy;
+  uint32_t lk = 0;
+  if (WALLS) {
+    lk = links[i];
+    if (lk & LINK_SOLID) return;
+  }
+  int d[6];
+  box_nbr(b, x, y, z, d);
+  const int64_t pc = psi[i];
+  int64_t Ap = 0;
+  int cnt = 0;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    if (WALLS && !open_face(lk, f)) continue;
+    Ap += pc - psi[i + d[f]];
+    ++cnt;
+  }
+  if (cnt == 0) return;
+  const int64_t rfx = (int64_t)(src[i] * PSI_SCALE_F) - s_mean - Ap;
+  psi[i] = pc + llrintf(omega * (float)rfx / (float)cnt);
+}
+
+struct CL {  // coarse level view
+  int nx, ny, nz;
+  int64_t n;
+  int px, py, pz;
+};
+
+__device__ __forceinline__ void cl_xyz(uint32_t c, const CL& l, int& x, int& y,
+                                       int& z) {
+  const uint32_t t = c / (uint32_t)l.nx;
+  x = (int)(c - t * (uint32_t)l.nx);
+  z = (int)(t / (uint32_t)l.ny);
+  y = (int)(t - (uint32_t)z * (uint32_t)l.ny);
+}
+
+// + and - neighbour offsets on a coarse level (0 when not periodic and at
+// the boundary: the conductance there is zero anyway).
+__device__ __forceinline__ void cl_nbr(const CL& l, int x, int y, int z,
+                                       int (&d)[6]) {
+  const int nxy = l.nx * l.ny;
+  d[0] = (x == l.nx - 1) ? (l.px ? -(l.nx - 1) : 0) : 1;
+  d[1] = (x == 0) ? (l.px ? l.nx - 1 : 0) : -1;
+  d[2] = ((y == l.ny - 1) ? (l.py ? -(l.ny - 1) : 0) : 1) * l.nx;
+  d[3] = ((y == 0) ? (l.py ? l.ny - 1 : 0) : -1) * l.nx;
+  d[4] = ((z == l.nz - 1) ? (l.pz ? -(l.nz - 1) : 0) : 1) * nxy;
+  d[5] = ((z == 0) ? (l.pz ? l.nz - 1 : 0) : -1) * nxy;
+}
+
+// Neighbour sum sum_faces K x_nb on a coarse level.  The + face of a cell
+// carries K[axis][c]; the - face the + conductance of the - neighbour, which
+// does not exist at the low end of a non-periodic axis.
+__device__ __forceinline__ float cl_nsum(const float* __restrict__ x,
+                                         const float* __restrict__ K, const CL& l,
+                                         uint32_t c, int xx, int yy, int zz,
+                                         const int (&d)[6]) {
+  const int64_t n = l.n;
+  float s = 0.f;
+  s += K[c] * x[(int64_t)c + d[0]];
+  s += K[n + c] * x[(int64_t)c + d[2]];
+  s += K[2 * n + c] * x[(int64_t)c + d[4]];
+  if (l.px || xx > 0) s += K[(int64_t)c + d[1]] * x[(int64_t)c + d[1]];
+  if (l.py || yy > 0) s += K[n + (int64_t)c + d[3]] * x[(int64_t)c + d[3]];
+  if (l.pz || zz > 0) s += K[2 * n + (int64_t)c + d[5]] * x[(int64_t)c + d[5]];
+  return s;
+}
+
+__global__ void __launch_bounds__(256) k_smooth(float* __restrict__ x,
+                                                const float* __restrict__ rhs,
+                                                const float* __restrict__ K,
+                                                const float* __restrict__ Dinv,
+                                                CL l, int color) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= (uint32_t)l.n) return;
+  int xx, yy, zz;
+  cl_xyz(c, l, xx, yy, zz);
+  if (((xx + yy + zz) & 1) != color) return;
+  const float di = Dinv[c];
+  if (di == 0.f) return;
+  int d[6];
+  cl_nbr(l, xx, yy, zz, d);
+  x[c] = di * (rhs[c] + cl_nsum(x, K, l, c, xx, yy, zz, d));
+}
+
+// One CTA: many red-black sweeps over the whole coarsest level.
+__global__ void __launch_bounds__(1024) k_coarse_solve(
+    float* __restrict__ x, const float* __restrict__ rhs,
+    const float* __restrict__ K, const float* __restrict__ Dinv, CL l,
+    int sweeps) {
+  for (int it = 0; it < sweeps; ++it) {
+    for (int color = 0; color < 2; ++color) {
+      for (uint32_t c = threadIdx.x; c < (uint32_t)l.n; c += blockDim.x) {
+        int xx, yy, zz;
+        cl_xyz(c, l, xx, yy, zz);
+        if (((xx + yy + zz) & 1) != color) continue;
+        const float di = Dinv[c];
+        if (di == 0.f) continue;
+        int d[6];
+        cl_nbr(l, xx, yy, zz, d);
+        x[c] = di * (rhs[c] + cl_nsum(x, K, l, c, xx, yy, zz, d));
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Restriction from the fine box: rhs_c(J) = sum over children i of
+// (r_i - (A e)_i).
+template <bool WALLS>
+__global__ void __launch_bounds__(256) k_restrict0(
+    const float* __restrict__ e, const float* __restrict__ r,
+    const uint32_t* __restrict__ links, Box b, CL cl, int cxs, int cys,
+    int czs, float* __restrict__ rhs_c) {
+  const uint32_t J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= (uint32_t)cl.n) return;
+  int X, Y, Z;
+  cl_xyz(J, cl, X, Y, Z);
+  float acc = 0.f;
+  for (int kz = 0; kz <= czs; ++kz)
+    for (int ky = 0; ky <= cys; ++ky)
+      for (int kx = 0; kx <= cxs; ++kx) {
+        const int x = (X << cxs) + kx, y = (Y << cys) + ky, z = (Z << czs) + kz;
+        const uint32_t c = ((uint32_t)z * b.ny + y) * b.nx + x;
+        uint32_t lk = 0;
+        if (WALLS) {
+          lk = links[(int64_t)c + (int64_t)b.zlo * b.nxy];
+          if (lk & LINK_SOLID) continue;
+        }
+        int d[6];
+        box_nbr(b, x, y, z, d);
+        const float ec = e[c];
+        float Ae = 0.f;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          if (WALLS && !open_face(lk, f)) continue;
+          Ae += ec - e[(int64_t)c + d[f]];
+        }
+        acc += r[c] - Ae;
+      }
+  rhs_c[J] = acc;
+}
+
+__global__ void __launch_bounds__(256) k_restrict(
+    const float* __restrict__ x, const float* __restrict__ rhs,
+    const float* __restrict__ K, const float* __restrict__ Dinv, CL f, CL cl,
+    int cxs, int cys, int czs, float* __restrict__ rhs_c) {
+  const uint32_t J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= (uint32_t)cl.n) return;
+  int X, Y, Z;
+  cl_xyz(J, cl, X, Y, Z);
+  float acc = 0.f;
+  for (int kz = 0; kz <= czs; ++kz)
+    for (int ky = 0; ky <= cys; ++ky)
+      for (int kx = 0; kx <= cxs; ++kx) {
+        const int xx = (X << cxs) + kx, yy = (Y << cys) + ky, zz = (Z << czs) + kz;
+        const uint32_t c = ((uint32_t)zz * f.ny + yy) * f.nx + xx;
+        const float di = Dinv[c];
+        if (di == 0.f) continue;
+        int d[6];
+        cl_nbr(f, xx, yy, zz, d);
+        const float Ax = x[c] / di - cl_nsum(x, K, f, c, xx, yy, zz, d);
+        acc += rhs[c] - Ax;
+      }
+  rhs_c[J] = acc;
+}
+
+// Trilinear (cell-centred) prolongation of the coarse correction, added to
+// the fine correction.  A coarse cell outside a non-periodic boundary or
+// inactive is replaced by the parent cell.
+__device__ __forceinline__ void prol_axis(int i, int n_c, int per, int coarsened,
+                                          int& p0, int& p1, float& w0) {
+  if (!coarsened) {
+    p0 = p1 = i;
+    w0 = 1.f;
+    return;
+  }
+  p0 = i >> 1;
+  int q = (i & 1) ? p0 + 1 : p0 - 1;
+  if (q < 0 || q >= n_c) {
+    if (per) q = (q + n_c) % n_c;
+    else q = p0;
+  }
+  p1 = q;
+  w0 = 0.75f;
+}
+
+template <bool FINE0, bool WALLS>
+__global__ void __launch_bounds__(256) k_prolong(
+    float* __restrict__ ef, const float* __restrict__ Dinv_f,
+    const uint32_t* __restrict__ links, Box b, CL f, const float* __restrict__ xc,
+    const float* __restrict__ Dinv_c, CL cl, int cxs, int cys, int czs) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= (uint32_t)f.n) return;
+  int x, y, z;
+  cl_xyz(c, f, x, y, z);
+  if (FINE0) {
+    if (WALLS && (links[(int64_t)c + (int64_t)b.zlo * b.nxy] & LINK_SOLID)) return;
+  } else {
+    if (Dinv_f[c] == 0.f) return;
+  }
+  int ax[2], ay[2], az[2];
+  float wx0, wy0, wz0;
+  prol_axis(x, cl.nx, cl.px, cxs, ax[0], ax[1], wx0);
+  prol_axis(y, cl.ny, cl.py, cys, ay[0], ay[1], wy0);
+  prol_axis(z, cl.nz, cl.pz, czs, az[0], az[1], wz0);
+  const float wx[2] = {wx0, 1.f - wx0}, wy[2] = {wy0, 1.f - wy0},
+              wz[2] = {wz0, 1.f - wz0};
+  const int64_t parent = ((int64_t)az[0] * cl.ny + ay[0]) * cl.nx + ax[0];
+  const float vp = xc[parent];
+  float acc = 0.f;
+#pragma unroll
+  for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+    for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 2; ++kx) {
+        const float w = wx[kx] * wy[ky] * wz[kz];
+        if (w == 0.f) continue;
+        const int64_t J = ((int64_t)az[kz] * cl.ny + ay[ky]) * cl.nx + ax[kx];
+        const float v = (Dinv_c[J] != 0.f) ? xc[J] : vp;
+        acc += w * v;
+      }
+  ef[c] += acc;
+}
+
+inline unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+Box make_box(lbm_t* h) {
+  Box b;
+  b.nx = h->cfg.nx;
+  b.ny = h->cfg.ny;
+  b.nzb = h->ps.nzb;
+  b.zlo = h->ps.zlo;
+  b.perz = h->ps.perz;
+  b.nxy = (int64_t)b.nx * b.ny;
+  return b;
+}
+
+CL make_cl(const PoissonLevel& l) {
+  CL c;
+  c.nx = l.nx;
+  c.ny = l.ny;
+  c.nz = l.nz;
+  c.n = l.n;
+  c.px = l.per[0];
+  c.py = l.per[1];
+  c.pz = l.per[2];
+  return c;
+}
+
+}  // namespace
+
+void poisson_free(lbm_t* h) {
+  Poisson& P = h->ps;
+  for (auto& l : P.lev) {
+    cudaFree(l.e);
+    cudaFree(l.rhs);
+    cudaFree(l.K);
+    cudaFree(l.Dinv);
+  }
+  P.lev.clear();
+  cudaFree(P.psi[0]);
+  cudaFree(P.psi[1]);
+  cudaFree(P.src);
+  cudaFree(P.dsum);
+  if (P.hsum) cudaFreeHost(P.hsum);
+  P.psi[0] = P.psi[1] = nullptr;
+  P.src = nullptr;
+  P.dsum = nullptr;
+  P.hsum = nullptr;
+}
+
+// Builds the grid hierarchy.  solid_host: lattice mask or NULL.
+lbm_status poisson_setup(lbm_t* h, const uint8_t* solid) {
+  Poisson& P = h->ps;
+  const int nx = h->cfg.nx, ny = h->cfg.ny, nz = h->cfg.nz;
+  const int64_t nxy = (int64_t)nx * ny;
+  // Trim fully solid bottom and top planes (slit geometry): the Poisson box
+  // is then non-periodic in z.
+  P.zlo = 0;
+  P.nzb = nz;
+  P.perz = 1;
+  if (solid && nz >= 3) {
+    auto plane_solid = [&](int z) {
+      for (int64_t k = 0; k < nxy; ++k)
+        if (!solid[(int64_t)z * nxy + k]) return false;
+      return true;
+    };
+    if (plane_solid(0) && plane_solid(nz - 1)) {
+      P.zlo = 1;
+      P.nzb = nz - 2;
+      P.perz = 0;
+    }
+  }
+  // free old levels (walls may be reset)
+  for (auto& l : P.lev) {
+    cudaFree(l.e);
+    cudaFree(l.rhs);
+    cudaFree(l.K);
+    cudaFree(l.Dinv);
+  }
+  P.lev.clear();
+
+  // Level 0 conductances on the host (face open iff both cells fluid).
+  PoissonLevel L0;
+  L0.nx = nx;
+  L0.ny = ny;
+  L0.nz = P.nzb;
+  L0.n = nxy * P.nzb;
+  L0.per[0] = 1;
+  L0.per[1] = 1;
+  L0.per[2] = P.perz;
+  L0.coarsened[0] = L0.coarsened[1] = L0.coarsened[2] = 0;
+  auto fl0 = [&](int x, int y, int z) -> bool {
+    return !solid || !solid[((int64_t)(z + P.zlo) * ny + y) * nx + x];
+  };
+  // host conductances of the current finest level: Kh[3][n], active flags
+  std::vector<float> Kh(3 * L0.n, 0.f);
+  std::vector<char> act(L0.n, 0);
+  for (int z = 0; z < P.nzb; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const int64_t c = ((int64_t)z * ny + y) * nx + x;
+        act[c] = fl0(x, y, z);
+        if (!act[c]) continue;
+        if (nx > 1 && fl0((x + 1) % nx, y, z)) Kh[c] = 1.f;
+        if (ny > 1 && fl0(x, (y + 1) % ny, z)) Kh[L0.n + c] = 1.f;
+        if (P.nzb > 1 && (z + 1 < P.nzb || P.perz)) {
+          if (fl0(x, y, (z + 1) % P.nzb)) Kh[2 * L0.n + c] = 1.f;
+        }
+      }
+  if (cudaMalloc(&L0.e, L0.n * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&L0.rhs, L0.n * sizeof(float)) != cudaSuccess) {
+    h->err = "Poisson level 0 allocation failed";
+    return LBM_ENOMEM;
+  }
+  P.lev.push_back(L0);
+
+  // Coarsen while the level has more than 512 cells and an axis can halve.
+  int lx = nx, ly = ny, lz = P.nzb;
+  int per[3] = {1, 1, P.perz};
+  while ((int64_t)lx * ly * lz > 512 && P.lev.size() < 12) {
+    int cx = (lx % 2 == 0 && lx >= 4), cy = (ly % 2 == 0 && ly >= 4),
+        cz = (lz % 2 == 0 && lz >= 4);
+    if (!cx && !cy && !cz) break;
+    const int Lx = cx ? lx / 2 : lx, Ly = cy ? ly / 2 : ly, Lz = cz ? lz / 2 : lz;
+    const int64_t n = (int64_t)Lx * Ly * Lz, nf = (int64_t)lx * ly * lz;
+    std::vector<float> Kc(3 * n, 0.f);
+    std::vector<char> ac(n, 0);
+    const float sc[3] = {cx ? 0.5f : 1.f, cy ? 0.5f : 1.f, cz ? 0.5f : 1.f};
+    for (int z = 0; z < lz; ++z)
+      for (int y = 0; y < ly; ++y)
+        for (int x = 0; x < lx; ++x) {
+          const int64_t c = ((int64_t)z * ly + y) * lx + x;
+          if (!act[c]) continue;
+          const int X = cx ? x / 2 : x, Y = cy ? y / 2 : y, Z = cz ? z / 2 : z;
+          const int64_t J = ((int64_t)Z * Ly + Y) * Lx + X;
+          ac[J] = 1;
+          // a fine face crossing the + face of J: the child on the + side
+          // of J along that axis (last child), or any child if not coarsened
+          if (!cx || (x & 1)) Kc[J] += sc[0] * Kh[c];
+          if (!cy || (y & 1)) Kc[n + J] += sc[1] * Kh[nf + c];
+          if (!cz || (z & 1)) Kc[2 * n + J] += sc[2] * Kh[2 * nf + c];
+        }
+    // inner faces of a non-coarsened axis are within J only if coarsened;
+    // for a non-coarsened axis every child's + face is the coarse + face.
+    std::vector<float> Dv(n, 0.f);
+    for (int Z = 0; Z < Lz; ++Z)
+      for (int Y = 0; Y < Ly; ++Y)
+        for (int X = 0; X < Lx; ++X) {
+          const int64_t J = ((int64_t)Z * Ly + Y) * Lx + X;
+          if (!ac[J]) continue;
+          const int Xm = (X - 1 + Lx) % Lx, Ym = (Y - 1 + Ly) % Ly, Zm = (Z - 1 + Lz) % Lz;
+          float D = Kc[J] + Kc[n + J] + Kc[2 * n + J];
+          if (per[0] || X > 0) D += Kc[((int64_t)Z * Ly + Y) * Lx + Xm];
+          if (per[1] || Y > 0) D += Kc[n + ((int64_t)Z * Ly + Ym) * Lx + X];
+          if (per[2] || Z > 0) D += Kc[2 * n + ((int64_t)Zm * Ly + Y) * Lx + X];
+          Dv[J] = D > 0.f ? 1.f / D : 0.f;
+          if (D == 0.f) ac[J] = 0;
+        }
+    PoissonLevel L;
+    L.nx = Lx;
+    L.ny = Ly;
+    L.nz = Lz;
+    L.n = n;
+    L.per[0] = per[0];
+    L.per[1] = per[1];
+    L.per[2] = per[2];
+    L.coarsened[0] = cx;
+    L.coarsened[1] = cy;
+    L.coarsened[2] = cz;
+    if (cudaMalloc(&L.e, n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&L.rhs, n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&L.K, 3 * n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&L.Dinv, n * sizeof(float)) != cudaSuccess) {
+      h->err = "Poisson level allocation failed";
+      P.lev.push_back(L);
+      return LBM_ENOMEM;
+    }
+    cudaMemcpy(L.K, Kc.data(), 3 * n * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(L.Dinv, Dv.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+    P.lev.push_back(L);
+    Kh.swap(Kc);
+    act.swap(ac);
+    lx = Lx;
+    ly = Ly;
+    lz = Lz;
+  }
+  LBM_CUDA_TRY(h, cudaGetLastError());
+  return LBM_OK;
+}
+
+namespace {
+
+lbm_status residual(lbm_t* h, bool update, double* rel) {
+  Poisson& P = h->ps;
+  const Box b = make_box(h);
+  const int64_t nbox = P.lev[0].n;
+  const double inv_nf = 1.0 / (double)h->nfluid;
+  LBM_CUDA_TRY(h, cudaMemsetAsync(P.dsum + 1, 0, 2 * sizeof(double), h->st));
+  const int64_t* pin = P.psi[P.cur];
+  int64_t* pout = P.psi[P.cur ^ 1];
+  const unsigned nb = nblocks(nbox, 256);
+  if (h->has_walls) {
+    if (update)
+      k_res0<true, true><<<nb, 256, 0, h->st>>>(pin, P.lev[0].e, pout, P.src, h->links,
+                                                P.lev[0].rhs, P.dsum, b, nbox, inv_nf);
+    else
+      k_res0<true, false><<<nb, 256, 0, h->st>>>(pin, nullptr, nullptr, P.src, h->links,
+                                                 P.lev[0].rhs, P.dsum, b, nbox, inv_nf);
+  } else {
+    if (update)
+      k_res0<false, true><<<nb, 256, 0, h->st>>>(pin, P.lev[0].e, pout, P.src, nullptr,
+                                                 P.lev[0].rhs, P.dsum, b, nbox, inv_nf);
+    else
+      k_res0<false, false><<<nb, 256, 0, h->st>>>(pin, nullptr, nullptr, P.src, nullptr,
+                                                  P.lev[0].rhs, P.dsum, b, nbox, inv_nf);
+  }
+  LBM_CUDA_TRY(h, cudaGetLastError());
+  if (update) P.cur ^= 1;
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  const double floor_fx = sqrt((double)h->nfluid) * 1e-12 * PSI_SCALE;
+  const double rn = sqrt(P.hsum[1]), sn = sqrt(P.hsum[2]);
+  *rel = rn / std::max(sn, floor_fx);
+  if (!isfinite(*rel)) {
+    h->err = "Poisson residual is not finite";
+    return LBM_EUNSTABLE;
+  }
+  return LBM_OK;
+}
+
+cudaError_t smooth_level(lbm_t* h, int l, int sweeps) {
+  Poisson& P = h->ps;
+  PoissonLevel& L = P.lev[l];
+  const unsigned nb = nblocks(L.n, 256);
+  if (l == 0) {
+    const Box b = make_box(h);
+    for (int k = 0; k < sweeps; ++k)
+      for (int color = 0; color < 2; ++color) {
+        if (h->has_walls)
+          k_smooth0<true><<<nb, 256, 0, h->st>>>(L.e, L.rhs, h->links, b, L.n, color);
+        else
+          k_smooth0<false><<<nb, 256, 0, h->st>>>(L.e, L.rhs, nullptr, b, L.n, color);
+      }
+  } else {
+    const CL c = make_cl(L);
+    for (int k = 0; k < sweeps; ++k)
+      for (int color = 0; color < 2; ++color)
+        k_smooth<<<nb, 256, 0, h->st>>>(L.e, L.rhs, L.K, L.Dinv, c, color);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t vcycle(lbm_t* h) {
+  Poisson& P = h->ps;
+  const int nl = (int)P.lev.size();
+  const Box b = make_box(h);
+  cudaError_t e = cudaMemsetAsync(P.lev[0].e, 0, P.lev[0].n * sizeof(float), h->st);
+  if (e != cudaSuccess) return e;
+  if (nl == 1) return smooth_level(h, 0, 8);
+  if ((e = smooth_level(h, 0, P.nu1)) != cudaSuccess) return e;
+  {
+    PoissonLevel& C = P.lev[1];
+    const CL cl = make_cl(C);
+    if (h->has_walls)
+      k_restrict0<true><<<nblocks(C.n, 256), 256, 0, h->st>>>(
+          P.lev[0].e, P.lev[0].rhs, h->links, b, cl, C.coarsened[0], C.coarsened[1],
+          C.coarsened[2], C.rhs);
+    else
+      k_restrict0<false><<<nblocks(C.n, 256), 256, 0, h->st>>>(
+          P.lev[0].e, P.lev[0].rhs, nullptr, b, cl, C.coarsened[0], C.coarsened[1],
+          C.coarsened[2], C.rhs);
+  }
+  for (int l = 1; l < nl; ++l) {
+    PoissonLevel& L = P.lev[l];
+    if ((e = cudaMemsetAsync(L.e, 0, L.n * sizeof(float), h->st)) != cudaSuccess) return e;
+    if (l == nl - 1) {
+      if (L.n <= 8192) {
+        k_coarse_solve<<<1, 1024, 0, h->st>>>(L.e, L.rhs, L.K, L.Dinv, make_cl(L),
+                                              P.coarse_sweeps);
+      } else {
+        if ((e = smooth_level(h, l, 50)) != cudaSuccess) return e;
+      }
+      break;
+    }
+    if ((e = smooth_level(h, l, P.nu1)) != cudaSuccess) return e;
+    PoissonLevel& C = P.lev[l + 1];
+    k_restrict<<<nblocks(C.n, 256), 256, 0, h->st>>>(L.e, L.rhs, L.K, L.Dinv, make_cl(L),
+                                                     make_cl(C), C.coarsened[0],
+                                                     C.coarsened[1], C.coarsened[2], C.rhs);
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    PoissonLevel& F = P.lev[l];
+    PoissonLevel& C = P.lev[l + 1];
+    const unsigned nb = nblocks(F.n, 256);
+    if (l == 0) {
+      if (h->has_walls)
+        k_prolong<true, true><<<nb, 256, 0, h->st>>>(F.e, nullptr, h->links, b, make_cl(F),
+                                                     C.e, C.Dinv, make_cl(C), C.coarsened[0],
+                                                     C.coarsened[1], C.coarsened[2]);
+      else
+        k_prolong<true, false><<<nb, 256, 0, h->st>>>(F.e, nullptr, nullptr, b, make_cl(F),
+                                                      C.e, C.Dinv, make_cl(C), C.coarsened[0],
+                                                      C.coarsened[1], C.coarsened[2]);
+    } else {
+      k_prolong<false, false><<<nb, 256, 0, h->st>>>(F.e, F.Dinv, nullptr, b, make_cl(F),
+                                                     C.e, C.Dinv, make_cl(C), C.coarsened[0],
+                                                     C.coarsened[1], C.coarsened[2]);
+    }
+    if ((e = smooth_level(h, l, P.nu2)) != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
+                         double* rel_res) {
+  Poisson& P = h->ps;
+  double rel = 0.0;
+  lbm_status s = residual(h, false, &rel);
+  if (s != LBM_OK) return s;
+  int it = 0;
+  if (h->cfg.poisson == LBM_POISSON_MG) {
+    while (rel > tol && it < maxit) {
+      LBM_CUDA_TRY(h, vcycle(h));
+      s = residual(h, true, &rel);
+      if (s != LBM_OK) return s;
+      ++it;
+    }
+  } else {
+    const Box b = make_box(h);
+    const int64_t nbox = P.lev[0].n;
+    const double inv_nf = 1.0 / (double)h->nfluid;
+    const int L = std::max(std::max(h->cfg.nx, h->cfg.ny), P.nzb);
+    const float omega = (float)(2.0 / (1.0 + sin(3.14159265358979323846 / L)));
+    const int check = 10;
+    while (rel > tol && it < maxit) {
+      for (int k = 0; k < check; ++k)
+        for (int color = 0; color < 2; ++color) {
+          if (h->has_walls)
+            k_sor0<true><<<nblocks(nbox, 256), 256, 0, h->st>>>(
+                P.psi[P.cur], P.src, h->links, P.dsum, b, nbox, inv_nf, color, omega);
+          else
+            k_sor0<false><<<nblocks(nbox, 256), 256, 0, h->st>>>(
+                P.psi[P.cur], P.src, nullptr, P.dsum, b, nbox, inv_nf, color, omega);
+        }
+      LBM_CUDA_TRY(h, cudaGetLastError());
+      it += check;
+      s = residual(h, false, &rel);
+      if (s != LBM_OK) return s;
+    }
+  }
+  if (iters) *iters = it;
+  if (rel_res) *rel_res = rel;
+  if (rel > tol) {
+    h->err = "Poisson solve did not reach the tolerance within the iteration cap";
+    return LBM_ENOCONV;
+  }
+  return LBM_OK;
+}
+
+}  // namespace lbm_gb300

@@ -1,0 +1,274 @@
+"""Python binding of the C ABI in include/lbm.h (ctypes; marshalling only).
+
+Every numerical step runs in the CUDA library liblbm_gb300.so.  There is no
+fallback: if the library is missing or no GPU is present, the calls raise.
+Array layouts follow the C ABI: fields are (nz, ny, nx) with x fastest,
+velocities (3, nz, ny, nx), populations (19, nz, ny, nx).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm_gb300.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOCONV, LBM_EUNSTABLE, LBM_ETIMEOUT = range(7)
+STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
+                4: "LBM_ENOCONV", 5: "LBM_EUNSTABLE", 6: "LBM_ETIMEOUT"}
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+POISSON = {"mg": 0, "sor": 1}
+
+# every symbol include/lbm.h declares
+EXPORTED = [
+    "lbm_config_default", "lbm_create", "lbm_destroy", "lbm_set_walls", "lbm_set_species",
+    "lbm_step", "lbm_synchronize", "lbm_get_moments", "lbm_get_populations",
+    "lbm_get_potential", "lbm_solve_poisson", "lbm_diagnostics", "lbm_get_state",
+    "lbm_set_state", "lbm_set_timing", "lbm_get_timing", "lbm_num_nodes", "lbm_state_len", "lbm_stream", "lbm_last_error",
+]
+
+
+class LbmConfig(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("nspecies", ctypes.c_int),
+        ("omega_visc", ctypes.c_double), ("omega_drag", ctypes.c_double),
+        ("bjerrum", ctypes.c_double), ("e_ext", ctypes.c_double * 3),
+        ("storage", ctypes.c_int), ("poisson", ctypes.c_int),
+        ("poisson_tol", ctypes.c_double), ("poisson_maxit", ctypes.c_int),
+        ("device", ctypes.c_int),
+    ]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads the CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("liblbm_gb300.so not found at %s: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')" % path)
+    lib = ctypes.CDLL(path)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.lbm_config_default.argtypes = [ctypes.POINTER(LbmConfig)]
+    lib.lbm_config_default.restype = None
+    lib.lbm_create.argtypes = [ctypes.POINTER(LbmConfig), ctypes.POINTER(P)]
+    lib.lbm_create.restype = I
+    lib.lbm_destroy.argtypes = [P]
+    lib.lbm_destroy.restype = None
+    lib.lbm_set_walls.argtypes = [P, P, P]
+    lib.lbm_set_walls.restype = I
+    lib.lbm_set_species.argtypes = [P, I, D, D, P, P]
+    lib.lbm_set_species.restype = I
+    lib.lbm_step.argtypes = [P, I, V]
+    lib.lbm_step.restype = I
+    lib.lbm_synchronize.argtypes = [P]
+    lib.lbm_synchronize.restype = I
+    lib.lbm_get_moments.argtypes = [P, I, P, P]
+    lib.lbm_get_moments.restype = I
+    lib.lbm_get_populations.argtypes = [P, I, P]
+    lib.lbm_get_populations.restype = I
+    lib.lbm_get_potential.argtypes = [P, P]
+    lib.lbm_get_potential.restype = I
+    lib.lbm_solve_poisson.argtypes = [P, P, P, D, I, ctypes.POINTER(I), dp]
+    lib.lbm_solve_poisson.restype = I
+    lib.lbm_diagnostics.argtypes = [P, P]
+    lib.lbm_diagnostics.restype = I
+    lib.lbm_get_state.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
+    lib.lbm_get_state.restype = I
+    lib.lbm_set_state.argtypes = [P, P, ctypes.c_int64]
+    lib.lbm_set_state.restype = I
+    lib.lbm_set_timing.argtypes = [P, I]
+    lib.lbm_set_timing.restype = I
+    lib.lbm_get_timing.argtypes = [P, P]
+    lib.lbm_get_timing.restype = I
+    lib.lbm_num_nodes.argtypes = [P]
+    lib.lbm_num_nodes.restype = ctypes.c_int64
+    lib.lbm_state_len.argtypes = [P]
+    lib.lbm_state_len.restype = ctypes.c_int64
+    lib.lbm_stream.argtypes = [P]
+    lib.lbm_stream.restype = P
+    lib.lbm_last_error.argtypes = [P]
+    lib.lbm_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def omega_drag_for_schmidt(omega_visc: float, schmidt: float) -> float:
+    """omega_drag with Sc = nu/D, nu = cs^2 (1/omega_visc - 1/2) and
+    D = cs^2 (1/omega_drag - 1/2) (Sec. 4 of the paper)."""
+    nu_over_cs2 = 1.0 / omega_visc - 0.5
+    return 1.0 / (0.5 + nu_over_cs2 / schmidt)
+
+
+class Lattice:
+    """One lattice handle (lbm_t).  Methods carry the names of the C calls."""
+
+    def __init__(self, nx, ny, nz, nspecies, omega_visc=1.0, omega_drag=1.0,
+                 bjerrum=0.0, e_ext=(0.0, 0.0, 0.0), storage="fp32", poisson="mg",
+                 poisson_tol=1e-8, poisson_maxit=200, device=0):
+        self._lib = load_library()
+        cfg = LbmConfig()
+        self._lib.lbm_config_default(ctypes.byref(cfg))
+        cfg.nx, cfg.ny, cfg.nz, cfg.nspecies = int(nx), int(ny), int(nz), int(nspecies)
+        cfg.omega_visc, cfg.omega_drag, cfg.bjerrum = float(omega_visc), float(omega_drag), float(bjerrum)
+        for d in range(3):
+            cfg.e_ext[d] = float(e_ext[d])
+        cfg.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        cfg.poisson = POISSON[poisson] if isinstance(poisson, str) else int(poisson)
+        cfg.poisson_tol, cfg.poisson_maxit, cfg.device = float(poisson_tol), int(poisson_maxit), int(device)
+        self.cfg = cfg
+        self.shape = (int(nz), int(ny), int(nx))
+        self.S = int(nspecies)
+        h = ctypes.c_void_p()
+        st = self._lib.lbm_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, self._lib.lbm_last_error(None).decode())
+        self.h = h
+        self.N = int(self._lib.lbm_num_nodes(h))
+
+    # -- helpers -----------------------------------------------------------
+    def _check(self, st, allow=()):
+        if st != LBM_OK and st not in allow:
+            raise LBMError(st, self._lib.lbm_last_error(self.h).decode())
+        return st
+
+    def _field(self, a, comps=None):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        want = self.shape if comps is None else (comps,) + self.shape
+        if a.shape != want:
+            raise ValueError("expected shape %s, got %s" % (want, a.shape))
+        return a
+
+    # -- C calls -------------------------------------------------------------
+    def set_walls(self, solid, sigma=None):
+        solid = np.ascontiguousarray(solid, dtype=np.uint8)
+        if solid.shape != self.shape:
+            raise ValueError("solid must have shape %s" % (self.shape,))
+        sig = None if sigma is None else self._field(sigma)
+        self._check(self._lib.lbm_set_walls(self.h, _ptr(solid), _ptr(sig)))
+
+    def set_species(self, s, mass, valence, n0, u0=None):
+        n0 = self._field(n0)
+        u0 = None if u0 is None else self._field(u0, 3)
+        self._check(self._lib.lbm_set_species(self.h, int(s), float(mass), float(valence),
+                                              _ptr(n0), _ptr(u0)))
+
+    def step(self, nsteps=1, stream=None, allow_noconv=False):
+        return self._check(self._lib.lbm_step(self.h, int(nsteps),
+                                              ctypes.c_void_p(stream) if stream else None),
+                           allow=(LBM_ENOCONV,) if allow_noconv else ())
+
+    def synchronize(self):
+        self._check(self._lib.lbm_synchronize(self.h))
+
+    def get_moments(self, s):
+        n = np.empty(self.shape)
+        u = np.empty((3,) + self.shape)
+        self._check(self._lib.lbm_get_moments(self.h, int(s), _ptr(n), _ptr(u)))
+        return n, u
+
+    def get_populations(self, s):
+        f = np.empty((19,) + self.shape)
+        self._check(self._lib.lbm_get_populations(self.h, int(s), _ptr(f)))
+        return f
+
+    def get_potential(self):
+        psi = np.empty(self.shape)
+        self._check(self._lib.lbm_get_potential(self.h, _ptr(psi)))
+        return psi
+
+    def solve_poisson(self, rho_e, psi0=None, tol=1e-8, maxit=0):
+        rho = self._field(rho_e)
+        psi = np.zeros(self.shape) if psi0 is None else self._field(psi0).copy()
+        it = ctypes.c_int(0)
+        res = ctypes.c_double(0.0)
+        st = self._check(self._lib.lbm_solve_poisson(self.h, _ptr(rho), _ptr(psi), float(tol),
+                                                     int(maxit), ctypes.byref(it), ctypes.byref(res)),
+                         allow=(LBM_ENOCONV,))
+        return psi, it.value, res.value, st
+
+    def diagnostics(self):
+        out = np.empty(self.S + 7)
+        st = self._check(self._lib.lbm_diagnostics(self.h, _ptr(out)), allow=(LBM_EUNSTABLE,))
+        S = self.S
+        return {"mass": out[:S].copy(), "momentum": out[S:S + 3].copy(), "charge": out[S + 3],
+                "poisson_iters": int(out[S + 4]), "poisson_residual": out[S + 5],
+                "steps": int(out[S + 6]), "unstable": st == LBM_EUNSTABLE, "raw": out}
+
+    def get_state(self):
+        n = int(self._lib.lbm_state_len(self.h))
+        buf = np.empty(n, dtype=np.float32)
+        step = ctypes.c_int64(0)
+        self._check(self._lib.lbm_get_state(self.h, _ptr(buf), ctypes.byref(step)))
+        return buf, step.value
+
+    def set_state(self, buf, step):
+        buf = np.ascontiguousarray(buf, dtype=np.float32)
+        if buf.size != int(self._lib.lbm_state_len(self.h)):
+            raise ValueError("state has the wrong length")
+        self._check(self._lib.lbm_set_state(self.h, _ptr(buf), int(step)))
+
+    def set_timing(self, enable=True):
+        self._check(self._lib.lbm_set_timing(self.h, int(bool(enable))))
+
+    def get_timing(self):
+        out = np.zeros(6)
+        self._check(self._lib.lbm_get_timing(self.h, _ptr(out)))
+        return {"charge_ms": out[0], "poisson_ms": out[1], "collide_ms": out[2],
+                "charge_launches": int(out[3]), "poisson_iters": int(out[4]),
+                "collide_launches": int(out[5])}
+
+    @property
+    def stream(self):
+        return int(self._lib.lbm_stream(self.h) or 0)
+
+    def destroy(self):
+        if getattr(self, "h", None):
+            self._lib.lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+
+def from_workload(wl, storage="fp32", poisson="mg", poisson_tol=1e-8, poisson_maxit=200,
+                  omega_drag=None, device=0):
+    """Creates and initialises a lattice from a workloads.Workload."""
+    nz, ny, nx = wl.shape
+    od = omega_drag if omega_drag is not None else omega_drag_for_schmidt(wl.omega_visc, wl.schmidt)
+    lat = Lattice(nx, ny, nz, wl.nspecies, omega_visc=wl.omega_visc, omega_drag=od,
+                  bjerrum=wl.bjerrum, e_ext=wl.e_ext, storage=storage, poisson=poisson,
+                  poisson_tol=poisson_tol, poisson_maxit=poisson_maxit, device=device)
+    if wl.solid is not None:
+        lat.set_walls(wl.solid, wl.sigma)
+    for s in range(wl.nspecies):
+        u0 = None if wl.u0 is None else wl.u0[s]
+        lat.set_species(s, wl.mass[s], wl.valence[s], wl.n0[s], u0)
+    return lat

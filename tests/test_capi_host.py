@@ -1,0 +1,98 @@
+"""Host-side checks of the C ABI library (no GPU): it builds, loads and
+exports every symbol include/lbm.h declares."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1507_04891_gb300 import lbm
+from paper_1507_04891_gb300.build import build_library
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return build_library()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)) - {"lbm_t"})
+
+
+def test_header_declares_the_binding_list():
+    assert declared_symbols() == sorted(lbm.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\b(lbm_[a-z_]+)\b", out))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(libpath)
+    for s in declared_symbols():
+        assert getattr(lib, s) is not None
+
+
+def test_config_default_is_host_only(libpath):
+    lib = lbm.load_library(libpath)
+    cfg = lbm.LbmConfig()
+    lib.lbm_config_default(ctypes.byref(cfg))
+    assert (cfg.nx, cfg.ny, cfg.nz, cfg.nspecies) == (1, 1, 1, 1)
+    assert cfg.omega_visc == 1.0 and cfg.poisson_tol == 1e-8 and cfg.poisson_maxit == 200
+
+
+def test_create_rejects_bad_arguments_before_touching_a_device(libpath):
+    lib = lbm.load_library(libpath)
+    cfg = lbm.LbmConfig()
+    lib.lbm_config_default(ctypes.byref(cfg))
+    h = ctypes.c_void_p()
+    for field, value in [("nx", 0), ("nspecies", 5), ("omega_visc", 2.0), ("omega_drag", 0.0),
+                         ("storage", 7), ("poisson", 9)]:
+        bad = lbm.LbmConfig.from_buffer_copy(cfg)
+        setattr(bad, field, value)
+        assert lib.lbm_create(ctypes.byref(bad), ctypes.byref(h)) == lbm.LBM_EINVAL
+        assert h.value is None
+        assert lib.lbm_last_error(None)
+    assert lib.lbm_create(None, ctypes.byref(h)) == lbm.LBM_EINVAL
+
+
+def test_null_handle_calls_are_rejected(libpath):
+    lib = lbm.load_library(libpath)
+    assert lib.lbm_step(None, 1, None) == lbm.LBM_EINVAL
+    assert lib.lbm_get_moments(None, 0, None, None) == lbm.LBM_EINVAL
+    assert lib.lbm_diagnostics(None, None) == lbm.LBM_EINVAL
+    assert lib.lbm_num_nodes(None) == 0
+    lib.lbm_destroy(None)
+
+
+def test_omega_for_schmidt_matches_paper_relations():
+    # nu = cs^2 (1/w_v - 1/2), D = cs^2 (1/w_d - 1/2), Sc = nu / D
+    for wv, sc in [(1.0, 10.0), (1.0, 1.0), (0.8, 1000.0)]:
+        wd = lbm.omega_drag_for_schmidt(wv, sc)
+        nu = (1 / wv - 0.5) / 3
+        D = (1 / wd - 0.5) / 3
+        assert abs(nu / D - sc) < 1e-9 * sc
+    assert abs(lbm.omega_drag_for_schmidt(1.0, 10.0) - 1 / 0.55) < 1e-12
+
+
+def test_config_layout_matches_c_compiler(tmp_path):
+    """ctypes mirror of lbm_config has the C compiler's size and offsets."""
+    fields = [f for f, _ in lbm.LbmConfig._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join('printf("%%s %%zu\\n", "%s", offsetof(lbm_config, %s));' % (f, f) for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm.h"\n'
+                   'int main(void){printf("size %zu\\n", sizeof(lbm_config));' + body + 'return 0;}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(lbm.LbmConfig)
+    for f in fields:
+        assert int(out[f]) == getattr(lbm.LbmConfig, f).offset, f
