@@ -162,7 +162,9 @@ int64_t lbm_state_len(const lbm_t* h);
  *   out[0] charge-density kernel ms    out[3] its launch count
  *   out[1] Poisson solve ms            out[4] Poisson iterations
  *   out[2] stream-collide kernel ms    out[5] its launch count
- * lbm_set_timing(h, 0) stops recording and clears the sums.               */
+ *   out[6] kernels the library launched (all kinds)
+ * out must hold 7 doubles.  lbm_set_timing(h, 0) stops recording and
+ * clears the sums.                                                        */
 lbm_status lbm_set_timing(lbm_t* h, int enable);
 lbm_status lbm_get_timing(lbm_t* h, double* out);
 

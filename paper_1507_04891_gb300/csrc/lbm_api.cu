@@ -536,6 +536,7 @@ lbm_status lbm_set_timing(lbm_t* h, int enable) {
   cudaSetDevice(h->dev);
   LBM_CUDA_TRY(h, drain_timing(h));
   h->timing = enable != 0;
+  h->launches = 0;
   for (int k = 0; k < 3; ++k) {
     h->t_acc[k] = 0.0;
     h->t_cnt[k] = 0;
@@ -551,6 +552,7 @@ lbm_status lbm_get_timing(lbm_t* h, double* out) {
     out[k] = h->t_acc[k];
     out[3 + k] = (double)h->t_cnt[k];
   }
+  out[6] = (double)h->launches;
   return LBM_OK;
 }
 

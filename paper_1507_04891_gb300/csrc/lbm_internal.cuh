@@ -64,11 +64,12 @@ struct Poisson {
   std::vector<PoissonLevel> lev;
   int64_t* psi[2] = {nullptr, nullptr};  // lattice-sized fixed-point buffers
   int cur = 0;
-  float* src = nullptr;   // 4 pi l_B (rho_e + w) per lattice node, no mean removed
-  double* dsum = nullptr; // [0] sum of src over fluid, [1] sum r^2, [2] sum s^2 (fixed units)
+  int64_t* src = nullptr; // 4 pi l_B (rho_e + w) per lattice node (fixed point), no mean removed
+  double* dsum = nullptr; // [0] sum of src over fluid, [1] sum r^2, [2] sum s^2 (fixed-point units)
   double* hsum = nullptr; // pinned mirror of dsum
   int64_t nfluid = 0;
-  int coarse_sweeps = 100;
+  int coarse_sweeps = 40;
+  int last_cycles = 0;   // V-cycles of the previous solve
   int nu1 = 2, nu2 = 2;
 };
 
@@ -109,6 +110,7 @@ struct lbm {
   size_t ev_used = 0;
   double t_acc[3] = {0, 0, 0};
   int64_t t_cnt[3] = {0, 0, 0};
+  int64_t launches = 0;  // kernels launched since timing was (re)set
   std::string err;
 };
 

@@ -160,6 +160,21 @@ __device__ __forceinline__ void psi_gradient(const StepArgs& a, uint32_t i,
   gz = 0.5f * (gpz + gmz);
 }
 
+// Block sum of 64-bit integers (exact), added to *out as one FP64 value per
+// block (a block's sum is far below 2^53, so the conversion is exact).
+__device__ __forceinline__ void block_sum_to(long long v, double* out) {
+  __shared__ long long red[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    atomicAdd(out, (double)tot);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Fused stream + collide, one thread per node, all S species in registers.
 //   1. pull the 19*S populations f_p^alpha(r, t)            (Eq. latboeq, lhs)
@@ -258,8 +273,13 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs a) {
     // p-independent part of omega*phi/(n w) + g/(n w)
     const float base = om * (1.0f - 1.5f * usq) - 3.0f * Fu;
     const float nr = a.nref[s];
+    // moving populations first; the rest population then takes
+    // f*_0 = n - sum_{p>0} f*_p, which holds exactly in real arithmetic
+    // (phi_perp carries mass n, g_p none) and keeps FP32 rounding of the
+    // weights from drifting the species mass.
+    float moved = 0.f;
 #pragma unroll
-    for (int p = 0; p < Q; ++p) {
+    for (int p = 1; p < Q; ++p) {
       const float av = CX(p) * usx + CY(p) * usy + CZ(p) * usz;
       const float fc = CX(p) * Fx + CY(p) * Fy + CZ(p) * Fz;
       const float uc = CX(p) * ux + CY(p) * uy + CZ(p) * uz;
@@ -267,8 +287,10 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs a) {
       const float src = base + om * (3.0f * av + 4.5f * av * av) +
                         3.0f * fc + 9.0f * fc * uc;
       const float fo = (1.0f - om) * f[s][p] + wn * src;
+      moved += fo;
       Fmt<ST>::st(fout + (int64_t)(s * Q + p) * N + i, fo, WT(p) * nr);
     }
+    Fmt<ST>::st(fout + (int64_t)(s * Q) * N + i, n[s] - moved, WT(0) * nr);
   }
 }
 
@@ -325,12 +347,12 @@ __global__ void k_init(int s, const double* __restrict__ n0,
 // ---------------------------------------------------------------------------
 template <bool WALLS, int ST>
 __global__ void __launch_bounds__(256) k_charge(
-    const void* fin_v, const uint32_t* links, const float* wcell, float* src,
+    const void* fin_v, const uint32_t* links, const float* wcell, int64_t* src,
     double* dsum, int nx, int ny, int nz, int64_t N, int S, float4 val,
     float4 nref, float fourpi_lb) {
   using T = typename Fmt<ST>::T;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  float sv = 0.f;
+  long long sv = 0;
   if (i < (uint32_t)N) {
     uint32_t lk = 0;
     bool fluid = true;
@@ -355,22 +377,12 @@ __global__ void __launch_bounds__(256) k_charge(
         rho += vz[s] * m0;
       }
       if (wcell) rho += wcell[i];
-      sv = fourpi_lb * rho;
+      // exact conversion: a float times a power of two, to a 64-bit integer
+      sv = (long long)(fourpi_lb * rho * PSI_SCALE_F);
     }
     src[i] = sv;
   }
-  // block reduction of sv
-  __shared__ float red[8];
-  float v = sv;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += (double)red[w];
-    atomicAdd(dsum, tot);
-  }
+  block_sum_to(sv, dsum);
 }
 
 // Gathers f(t) of species s and its moments n, u = sum c f / n (doubles).
@@ -503,25 +515,16 @@ __global__ void k_psi_from_double(const double* in, int64_t* psi,
 }
 
 __global__ void __launch_bounds__(256) k_src_from_rho(
-    const double* rho, const uint32_t* links, const float* wcell, float* src,
-    double* dsum, int64_t N, float fourpi_lb) {
+    const double* rho, const uint32_t* links, const float* wcell, int64_t* src,
+    double* dsum, int64_t N, double fourpi_lb) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  float sv = 0.f;
+  long long sv = 0;
   if (i < N) {
     const bool solid = links && (links[i] & LINK_SOLID);
-    if (!solid) sv = fourpi_lb * ((float)rho[i] + (wcell ? wcell[i] : 0.f));
+    if (!solid) sv = llrint(fourpi_lb * (rho[i] + (wcell ? (double)wcell[i] : 0.0)) * PSI_SCALE);
     src[i] = sv;
   }
-  __shared__ float red[8];
-  float v = sv;
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += (double)red[w];
-    atomicAdd(dsum, tot);
-  }
+  block_sum_to(sv, dsum);
 }
 
 inline unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -580,7 +583,10 @@ cudaError_t launch_stream_collide(lbm_t* h) {
     case LBM_BF16_SHIFT: e = dispatch_s<LBM_BF16_SHIFT>(a, h->S, h->has_walls, charged, h->st); break;
     default: return cudaErrorInvalidValue;
   }
-  if (e == cudaSuccess) h->cur ^= 1;
+  if (e == cudaSuccess) {
+    h->cur ^= 1;
+    ++h->launches;
+  }
   return e;
 }
 
@@ -609,6 +615,7 @@ cudaError_t launch_init_species(lbm_t* h, int s, const double* n0,
   LBM_DISPATCH_WS(h, (k_init<W_, ST_><<<nb, 256, 0, h->st>>>(
                          s, n0, u0, h->links, h->f[h->cur], h->cfg.nx,
                          h->cfg.ny, h->cfg.nz, h->N, h->nref[s])));
+  ++h->launches;
   return cudaGetLastError();
 }
 
@@ -619,6 +626,7 @@ cudaError_t launch_charge(lbm_t* h) {
                          h->f[h->cur], h->links, h->wcell, h->ps.src,
                          h->ps.dsum, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,
                          h->S, as_f4(h->valence), as_f4(h->nref), k)));
+  ++h->launches;
   return cudaGetLastError();
 }
 
@@ -628,6 +636,7 @@ cudaError_t launch_gather(lbm_t* h, int s, double* n_dev, double* u_dev,
   LBM_DISPATCH_WS(h, (k_gather<W_, ST_><<<nb, 256, 0, h->st>>>(
                          h->f[h->cur], h->links, s, h->cfg.nx, h->cfg.ny,
                          h->cfg.nz, h->N, h->nref[s], n_dev, u_dev, f_dev)));
+  ++h->launches;
   return cudaGetLastError();
 }
 
@@ -637,29 +646,34 @@ cudaError_t launch_diagnostics(lbm_t* h) {
                          h->f[h->cur], h->links, h->cfg.nx, h->cfg.ny,
                          h->cfg.nz, h->N, h->S, as_f4(h->valence),
                          as_f4(h->nref), h->dred, h->dflag)));
+  ++h->launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_links(lbm_t* h, const uint8_t* solid_dev) {
   k_links<<<nblocks(h->N, 256), 256, 0, h->st>>>(solid_dev, h->links, h->cfg.nx,
                                                 h->cfg.ny, h->cfg.nz, h->N);
+  ++h->launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_psi_to_double(lbm_t* h, const int64_t* psi, double* out) {
   k_psi_to_double<<<nblocks(h->N, 256), 256, 0, h->st>>>(psi, out, h->N);
+  ++h->launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_psi_from_double(lbm_t* h, const double* in, int64_t* psi) {
   k_psi_from_double<<<nblocks(h->N, 256), 256, 0, h->st>>>(in, psi, h->links, h->N);
+  ++h->launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_src_from_rho(lbm_t* h, const double* rho_dev) {
-  const float k = (float)(4.0 * 3.14159265358979323846 * h->cfg.bjerrum);
+  const double k = 4.0 * 3.14159265358979323846 * h->cfg.bjerrum;
   k_src_from_rho<<<nblocks(h->N, 256), 256, 0, h->st>>>(
       rho_dev, h->links, h->wcell, h->ps.src, h->ps.dsum, h->N, k);
+  ++h->launches;
   return cudaGetLastError();
 }
 

@@ -77,12 +77,12 @@ __device__ __forceinline__ int64_t fx_of(float e) {
 template <bool WALLS, bool UPDATE>
 __global__ void __launch_bounds__(256) k_res0(
     const int64_t* __restrict__ psi_in, const float* __restrict__ e,
-    int64_t* __restrict__ psi_out, const float* __restrict__ src,
+    int64_t* __restrict__ psi_out, const int64_t* __restrict__ src,
     const uint32_t* __restrict__ links, float* __restrict__ r, double* dsum,
     Box b, int64_t nbox, double inv_nfluid) {
   __shared__ long long s_mean;
   __shared__ float red_r[8], red_s[8];
-  if (threadIdx.x == 0) s_mean = llrint(dsum[0] * inv_nfluid * PSI_SCALE);
+  if (threadIdx.x == 0) s_mean = llrint(dsum[0] * inv_nfluid);
   __syncthreads();
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   float rr = 0.f, ss = 0.f;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) k_res0(
         if (UPDATE) pn += fx_of(e[(int64_t)c + d[f]]);
         Ap += pc - pn;
       }
-      const int64_t sfx = (int64_t)(src[i] * PSI_SCALE_F) - s_mean;
+      const int64_t sfx = src[i] - s_mean;
       const int64_t rfx = sfx - Ap;
       const float rf = (float)rfx;
       r[c] = rf * PSI_INV_SCALE_F;
@@ -139,16 +139,42 @@ __global__ void __launch_bounds__(256) k_res0(
   }
 }
 
+// Cell of colour `color` handled by thread t when the x extent is even:
+// every x row holds nx/2 cells of each colour.  With an odd x extent every
+// thread takes one cell and skips the other colour.
+__device__ __forceinline__ bool rb_cell(uint32_t t, int nx, int ny, int64_t n,
+                                        int color, bool compact, uint32_t& c,
+                                        int& x, int& y, int& z) {
+  if (compact) {
+    const uint32_t half = (uint32_t)nx >> 1;
+    if (t >= (uint32_t)(n >> 1)) return false;
+    const uint32_t row = t / half;
+    const uint32_t k = t - row * half;
+    z = (int)(row / (uint32_t)ny);
+    y = (int)(row - (uint32_t)z * (uint32_t)ny);
+    x = (int)(2 * k) + ((y + z + color) & 1);
+    c = row * (uint32_t)nx + (uint32_t)x;
+    return true;
+  }
+  if (t >= (uint32_t)n) return false;
+  c = t;
+  const uint32_t q = t / (uint32_t)nx;
+  x = (int)(t - q * (uint32_t)nx);
+  z = (int)(q / (uint32_t)ny);
+  y = (int)(q - (uint32_t)z * (uint32_t)ny);
+  return ((x + y + z) & 1) == color;
+}
+
 // Red-black Gauss-Seidel on the fine box for A e = r (FP32).
 template <bool WALLS>
 __global__ void __launch_bounds__(256) k_smooth0(
     float* __restrict__ e, const float* __restrict__ r,
-    const uint32_t* __restrict__ links, Box b, int64_t nbox, int color) {
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= (uint32_t)nbox) return;
+    const uint32_t* __restrict__ links, Box b, int64_t nbox, int color,
+    int compact) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t c;
   int x, y, z;
-  box_xyz(c, b, x, y, z);
-  if (((x + y + z) & 1) != color) return;
+  if (!rb_cell(t, b.nx, b.ny, nbox, color, compact, c, x, y, z)) return;
   uint32_t lk = 0;
   if (WALLS) {
     lk = links[(int64_t)c + (int64_t)b.zlo * b.nxy];
@@ -170,11 +196,11 @@ __global__ void __launch_bounds__(256) k_smooth0(
 // Red-black SOR directly on the fixed-point psi (in place).
 template <bool WALLS>
 __global__ void __launch_bounds__(256) k_sor0(
-    int64_t* __restrict__ psi, const float* __restrict__ src,
+    int64_t* __restrict__ psi, const int64_t* __restrict__ src,
     const uint32_t* __restrict__ links, const double* dsum, Box b,
     int64_t nbox, double inv_nfluid, int color, float omega) {
   __shared__ long long s_mean;
-  if (threadIdx.x == 0) s_mean = llrint(dsum[0] * inv_nfluid * PSI_SCALE);
+  if (threadIdx.x == 0) s_mean = llrint(dsum[0] * inv_nfluid);
   __syncthreads();
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= (uint32_t)nbox) return;
@@ -199,7 +225,7 @@ __global__ void __launch_bounds__(256) k_sor0(
     ++cnt;
   }
   if (cnt == 0) return;
-  const int64_t rfx = (int64_t)(src[i] * PSI_SCALE_F) - s_mean - Ap;
+  const int64_t rfx = src[i] - s_mean - Ap;
   psi[i] = pc + llrintf(omega * (float)rfx / (float)cnt);
 }
 
@@ -248,21 +274,26 @@ __device__ __forceinline__ float cl_nsum(const float* __restrict__ x,
   return s;
 }
 
-__global__ void __launch_bounds__(256) k_smooth(float* __restrict__ x,
-                                                const float* __restrict__ rhs,
-                                                const float* __restrict__ K,
-                                                const float* __restrict__ Dinv,
-                                                CL l, int color) {
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= (uint32_t)l.n) return;
-  int xx, yy, zz;
-  cl_xyz(c, l, xx, yy, zz);
-  if (((xx + yy + zz) & 1) != color) return;
+__device__ __forceinline__ void gs_cell(float* x, const float* rhs, const float* K,
+                                        const float* Dinv, const CL& l, uint32_t c,
+                                        int xx, int yy, int zz) {
   const float di = Dinv[c];
   if (di == 0.f) return;
   int d[6];
   cl_nbr(l, xx, yy, zz, d);
   x[c] = di * (rhs[c] + cl_nsum(x, K, l, c, xx, yy, zz, d));
+}
+
+__global__ void __launch_bounds__(256) k_smooth(float* __restrict__ x,
+                                                const float* __restrict__ rhs,
+                                                const float* __restrict__ K,
+                                                const float* __restrict__ Dinv,
+                                                CL l, int color, int compact) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t c;
+  int xx, yy, zz;
+  if (!rb_cell(t, l.nx, l.ny, l.n, color, compact, c, xx, yy, zz)) return;
+  gs_cell(x, rhs, K, Dinv, l, c, xx, yy, zz);
 }
 
 // One CTA: many red-black sweeps over the whole coarsest level.
@@ -406,6 +437,144 @@ __global__ void __launch_bounds__(256) k_prolong(
   ef[c] += acc;
 }
 
+// Restricted residual of one coarse cell J: sum over its children i of
+// (rhs_i - (A x)_i) on the finer level f.
+__device__ __forceinline__ float restrict_cell(const float* x, const float* rhs,
+                                              const float* K, const float* Dinv,
+                                              const CL& f, int X, int Y, int Z,
+                                              int cxs, int cys, int czs) {
+  float acc = 0.f;
+  for (int kz = 0; kz <= czs; ++kz)
+    for (int ky = 0; ky <= cys; ++ky)
+      for (int kx = 0; kx <= cxs; ++kx) {
+        const int xx = (X << cxs) + kx, yy = (Y << cys) + ky, zz = (Z << czs) + kz;
+        const uint32_t c = ((uint32_t)zz * f.ny + yy) * f.nx + xx;
+        const float di = Dinv[c];
+        if (di == 0.f) continue;
+        int d[6];
+        cl_nbr(f, xx, yy, zz, d);
+        acc += rhs[c] - (x[c] / di - cl_nsum(x, K, f, c, xx, yy, zz, d));
+      }
+  return acc;
+}
+
+// Trilinear interpolation of the coarse correction at fine cell (x, y, z).
+__device__ __forceinline__ float prolong_cell(const float* xc, const float* Dinv_c,
+                                             const CL& cl, int x, int y, int z,
+                                             int cxs, int cys, int czs) {
+  int ax[2], ay[2], az[2];
+  float wx0, wy0, wz0;
+  prol_axis(x, cl.nx, cl.px, cxs, ax[0], ax[1], wx0);
+  prol_axis(y, cl.ny, cl.py, cys, ay[0], ay[1], wy0);
+  prol_axis(z, cl.nz, cl.pz, czs, az[0], az[1], wz0);
+  const float wx[2] = {wx0, 1.f - wx0}, wy[2] = {wy0, 1.f - wy0},
+              wz[2] = {wz0, 1.f - wz0};
+  const int parent = (az[0] * cl.ny + ay[0]) * cl.nx + ax[0];
+  const float vp = xc[parent];
+  float acc = 0.f;
+#pragma unroll
+  for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+    for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 2; ++kx) {
+        const float w = wx[kx] * wy[ky] * wz[kz];
+        if (w == 0.f) continue;
+        const int J = (az[kz] * cl.ny + ay[ky]) * cl.nx + ax[kx];
+        acc += w * ((Dinv_c[J] != 0.f) ? xc[J] : vp);
+      }
+  return acc;
+}
+
+constexpr int SUB_MAX_LEVELS = 8;
+constexpr int64_t SUB_MAX_CELLS = 4096;  // finest level handled in shared memory
+
+struct SubLevel {
+  CL l;
+  int cx, cy, cz;  // halved axes relative to the next finer level
+  const float* K;
+  const float* Dinv;
+};
+struct SubHier {
+  SubLevel lev[SUB_MAX_LEVELS];
+  int nlev;
+  const float* rhs_in;  // right-hand side of the first level (global)
+  float* e_out;         // its correction (global)
+};
+
+// The whole V-cycle below and including a level of at most 4096 cells, in
+// one CTA, every array in shared memory: smoothing, restriction, the
+// coarsest-level sweeps and prolongation, separated by __syncthreads.
+__global__ void __launch_bounds__(1024) k_sub_cycle(const SubHier H, int nu1, int nu2,
+                                                    int sweeps) {
+  extern __shared__ float sm[];
+  float* E[SUB_MAX_LEVELS];
+  float* R[SUB_MAX_LEVELS];
+  float* KK[SUB_MAX_LEVELS];
+  float* DD[SUB_MAX_LEVELS];
+  int off = 0;
+  for (int l = 0; l < H.nlev; ++l) {
+    const int n = (int)H.lev[l].l.n;
+    E[l] = sm + off;
+    off += n;
+    R[l] = sm + off;
+    off += n;
+    KK[l] = sm + off;
+    off += 3 * n;
+    DD[l] = sm + off;
+    off += n;
+  }
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int l = 0; l < H.nlev; ++l) {
+    const int n = (int)H.lev[l].l.n;
+    for (int c = tid; c < n; c += nt) {
+      E[l][c] = 0.f;
+      R[l][c] = l == 0 ? H.rhs_in[c] : 0.f;
+      DD[l][c] = H.lev[l].Dinv[c];
+      KK[l][c] = H.lev[l].K[c];
+      KK[l][n + c] = H.lev[l].K[n + c];
+      KK[l][2 * n + c] = H.lev[l].K[2 * n + c];
+    }
+  }
+  __syncthreads();
+  auto smooth = [&](int l, int count) {
+    const CL& L = H.lev[l].l;
+    for (int k = 0; k < count; ++k)
+      for (int color = 0; color < 2; ++color) {
+        for (int c = tid; c < (int)L.n; c += nt) {
+          int xx, yy, zz;
+          cl_xyz((uint32_t)c, L, xx, yy, zz);
+          if (((xx + yy + zz) & 1) == color) gs_cell(E[l], R[l], KK[l], DD[l], L, c, xx, yy, zz);
+        }
+        __syncthreads();
+      }
+  };
+  for (int l = 0; l + 1 < H.nlev; ++l) {
+    smooth(l, nu1);
+    const SubLevel& C = H.lev[l + 1];
+    for (int J = tid; J < (int)C.l.n; J += nt) {
+      int X, Y, Z;
+      cl_xyz((uint32_t)J, C.l, X, Y, Z);
+      R[l + 1][J] = restrict_cell(E[l], R[l], KK[l], DD[l], H.lev[l].l, X, Y, Z, C.cx, C.cy, C.cz);
+    }
+    __syncthreads();
+  }
+  smooth(H.nlev - 1, H.nlev == 1 ? sweeps : sweeps);
+  for (int l = H.nlev - 2; l >= 0; --l) {
+    const SubLevel& C = H.lev[l + 1];
+    const CL& L = H.lev[l].l;
+    for (int c = tid; c < (int)L.n; c += nt) {
+      if (DD[l][c] == 0.f) continue;
+      int xx, yy, zz;
+      cl_xyz((uint32_t)c, L, xx, yy, zz);
+      E[l][c] += prolong_cell(E[l + 1], DD[l + 1], C.l, xx, yy, zz, C.cx, C.cy, C.cz);
+    }
+    __syncthreads();
+    smooth(l, nu2);
+  }
+  for (int c = tid; c < (int)H.lev[0].l.n; c += nt) H.e_out[c] = E[0][c];
+}
+
 inline unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 Box make_box(lbm_t* h) {
@@ -452,6 +621,11 @@ void poisson_free(lbm_t* h) {
   P.dsum = nullptr;
   P.hsum = nullptr;
 }
+
+namespace {
+int sub_level(const Poisson& P);
+size_t sub_smem(const Poisson& P, int lc);
+}  // namespace
 
 // Builds the grid hierarchy.  solid_host: lattice mask or NULL.
 lbm_status poisson_setup(lbm_t* h, const uint8_t* solid) {
@@ -519,10 +693,10 @@ lbm_status poisson_setup(lbm_t* h, const uint8_t* solid) {
   }
   P.lev.push_back(L0);
 
-  // Coarsen while the level has more than 512 cells and an axis can halve.
+  // Coarsen while the level has more than 64 cells and an axis can halve.
   int lx = nx, ly = ny, lz = P.nzb;
   int per[3] = {1, 1, P.perz};
-  while ((int64_t)lx * ly * lz > 512 && P.lev.size() < 12) {
+  while ((int64_t)lx * ly * lz > 64 && P.lev.size() < 12) {
     int cx = (lx % 2 == 0 && lx >= 4), cy = (ly % 2 == 0 && ly >= 4),
         cz = (lz % 2 == 0 && lz >= 4);
     if (!cx && !cy && !cz) break;
@@ -589,18 +763,34 @@ lbm_status poisson_setup(lbm_t* h, const uint8_t* solid) {
     ly = Ly;
     lz = Lz;
   }
+  const int lc = sub_level(P);
+  if (lc > 0) {
+    // allow the largest dynamic shared memory the device offers, so that
+    // lattices created later with bigger sub-hierarchies also fit
+    int optin = 0;
+    LBM_CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
+    if ((int)sub_smem(P, lc) > optin) {
+      h->err = "coarse Poisson levels exceed the shared memory of one CTA";
+      return LBM_EINVAL;
+    }
+    LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_sub_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         optin));
+  }
   LBM_CUDA_TRY(h, cudaGetLastError());
   return LBM_OK;
 }
 
 namespace {
 
-lbm_status residual(lbm_t* h, bool update, double* rel) {
+// Queues the fine-box residual (optionally applying the pending correction
+// first) and the device-to-host copy of its norms; does not wait.
+cudaError_t residual_launch(lbm_t* h, bool update) {
   Poisson& P = h->ps;
   const Box b = make_box(h);
   const int64_t nbox = P.lev[0].n;
   const double inv_nf = 1.0 / (double)h->nfluid;
-  LBM_CUDA_TRY(h, cudaMemsetAsync(P.dsum + 1, 0, 2 * sizeof(double), h->st));
+  cudaError_t e = cudaMemsetAsync(P.dsum + 1, 0, 2 * sizeof(double), h->st);
+  if (e != cudaSuccess) return e;
   const int64_t* pin = P.psi[P.cur];
   int64_t* pout = P.psi[P.cur ^ 1];
   const unsigned nb = nblocks(nbox, 256);
@@ -619,10 +809,15 @@ lbm_status residual(lbm_t* h, bool update, double* rel) {
       k_res0<false, false><<<nb, 256, 0, h->st>>>(pin, nullptr, nullptr, P.src, nullptr,
                                                   P.lev[0].rhs, P.dsum, b, nbox, inv_nf);
   }
-  LBM_CUDA_TRY(h, cudaGetLastError());
+  ++h->launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (update) P.cur ^= 1;
-  LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double),
-                                  cudaMemcpyDeviceToHost, h->st));
+  return cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+}
+
+// Waits for the last queued residual and returns ||r|| / ||s||.
+lbm_status residual_read(lbm_t* h, double* rel) {
+  Poisson& P = h->ps;
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   const double floor_fx = sqrt((double)h->nfluid) * 1e-12 * PSI_SCALE;
   const double rn = sqrt(P.hsum[1]), sn = sqrt(P.hsum[2]);
@@ -637,22 +832,61 @@ lbm_status residual(lbm_t* h, bool update, double* rel) {
 cudaError_t smooth_level(lbm_t* h, int l, int sweeps) {
   Poisson& P = h->ps;
   PoissonLevel& L = P.lev[l];
-  const unsigned nb = nblocks(L.n, 256);
+  const int compact = (L.nx % 2 == 0) ? 1 : 0;
+  const unsigned nb = nblocks(compact ? L.n / 2 : L.n, 256);
   if (l == 0) {
     const Box b = make_box(h);
     for (int k = 0; k < sweeps; ++k)
       for (int color = 0; color < 2; ++color) {
         if (h->has_walls)
-          k_smooth0<true><<<nb, 256, 0, h->st>>>(L.e, L.rhs, h->links, b, L.n, color);
+          k_smooth0<true><<<nb, 256, 0, h->st>>>(L.e, L.rhs, h->links, b, L.n, color, compact);
         else
-          k_smooth0<false><<<nb, 256, 0, h->st>>>(L.e, L.rhs, nullptr, b, L.n, color);
+          k_smooth0<false><<<nb, 256, 0, h->st>>>(L.e, L.rhs, nullptr, b, L.n, color, compact);
+        ++h->launches;
       }
   } else {
     const CL c = make_cl(L);
     for (int k = 0; k < sweeps; ++k)
-      for (int color = 0; color < 2; ++color)
-        k_smooth<<<nb, 256, 0, h->st>>>(L.e, L.rhs, L.K, L.Dinv, c, color);
+      for (int color = 0; color < 2; ++color) {
+        k_smooth<<<nb, 256, 0, h->st>>>(L.e, L.rhs, L.K, L.Dinv, c, color, compact);
+        ++h->launches;
+      }
   }
+  return cudaGetLastError();
+}
+
+// First level (>= 1) small enough for the shared-memory sub-cycle.
+int sub_level(const Poisson& P) {
+  for (int l = 1; l < (int)P.lev.size(); ++l)
+    if (P.lev[l].n <= SUB_MAX_CELLS && (int)P.lev.size() - l <= SUB_MAX_LEVELS) return l;
+  return -1;
+}
+
+size_t sub_smem(const Poisson& P, int lc) {
+  size_t n = 0;
+  for (int l = lc; l < (int)P.lev.size(); ++l) n += 6 * (size_t)P.lev[l].n;
+  return n * sizeof(float);
+}
+
+cudaError_t launch_sub_cycle(lbm_t* h, int lc) {
+  Poisson& P = h->ps;
+  SubHier H;
+  H.nlev = (int)P.lev.size() - lc;
+  for (int k = 0; k < H.nlev; ++k) {
+    const PoissonLevel& L = P.lev[lc + k];
+    H.lev[k].l = make_cl(L);
+    H.lev[k].cx = L.coarsened[0];
+    H.lev[k].cy = L.coarsened[1];
+    H.lev[k].cz = L.coarsened[2];
+    H.lev[k].K = L.K;
+    H.lev[k].Dinv = L.Dinv;
+  }
+  H.rhs_in = P.lev[lc].rhs;
+  H.e_out = P.lev[lc].e;
+  const size_t smem = sub_smem(P, lc);
+  const int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(64, ((P.lev[lc].n / 2 + 31) / 32) * 32));
+  k_sub_cycle<<<1, threads, smem, h->st>>>(H, P.nu1, P.nu2, P.coarse_sweeps);
+  ++h->launches;
   return cudaGetLastError();
 }
 
@@ -663,6 +897,7 @@ cudaError_t vcycle(lbm_t* h) {
   cudaError_t e = cudaMemsetAsync(P.lev[0].e, 0, P.lev[0].n * sizeof(float), h->st);
   if (e != cudaSuccess) return e;
   if (nl == 1) return smooth_level(h, 0, 8);
+  const int lc = sub_level(P);
   if ((e = smooth_level(h, 0, P.nu1)) != cudaSuccess) return e;
   {
     PoissonLevel& C = P.lev[1];
@@ -675,26 +910,27 @@ cudaError_t vcycle(lbm_t* h) {
       k_restrict0<false><<<nblocks(C.n, 256), 256, 0, h->st>>>(
           P.lev[0].e, P.lev[0].rhs, nullptr, b, cl, C.coarsened[0], C.coarsened[1],
           C.coarsened[2], C.rhs);
+    ++h->launches;
   }
-  for (int l = 1; l < nl; ++l) {
+  const int last = lc > 0 ? lc : nl - 1;  // levels 1..last-1 use grid kernels
+  for (int l = 1; l < last; ++l) {
     PoissonLevel& L = P.lev[l];
     if ((e = cudaMemsetAsync(L.e, 0, L.n * sizeof(float), h->st)) != cudaSuccess) return e;
-    if (l == nl - 1) {
-      if (L.n <= 8192) {
-        k_coarse_solve<<<1, 1024, 0, h->st>>>(L.e, L.rhs, L.K, L.Dinv, make_cl(L),
-                                              P.coarse_sweeps);
-      } else {
-        if ((e = smooth_level(h, l, 50)) != cudaSuccess) return e;
-      }
-      break;
-    }
     if ((e = smooth_level(h, l, P.nu1)) != cudaSuccess) return e;
     PoissonLevel& C = P.lev[l + 1];
     k_restrict<<<nblocks(C.n, 256), 256, 0, h->st>>>(L.e, L.rhs, L.K, L.Dinv, make_cl(L),
                                                      make_cl(C), C.coarsened[0],
                                                      C.coarsened[1], C.coarsened[2], C.rhs);
+    ++h->launches;
   }
-  for (int l = nl - 2; l >= 0; --l) {
+  if (lc > 0) {
+    if ((e = launch_sub_cycle(h, lc)) != cudaSuccess) return e;
+  } else {
+    PoissonLevel& L = P.lev[last];
+    if ((e = cudaMemsetAsync(L.e, 0, L.n * sizeof(float), h->st)) != cudaSuccess) return e;
+    if ((e = smooth_level(h, last, 50)) != cudaSuccess) return e;
+  }
+  for (int l = last - 1; l >= 0; --l) {
     PoissonLevel& F = P.lev[l];
     PoissonLevel& C = P.lev[l + 1];
     const unsigned nb = nblocks(F.n, 256);
@@ -712,6 +948,7 @@ cudaError_t vcycle(lbm_t* h) {
                                                      C.e, C.Dinv, make_cl(C), C.coarsened[0],
                                                      C.coarsened[1], C.coarsened[2]);
     }
+    ++h->launches;
     if ((e = smooth_level(h, l, P.nu2)) != cudaSuccess) return e;
   }
   return cudaGetLastError();
@@ -723,36 +960,56 @@ lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
                          double* rel_res) {
   Poisson& P = h->ps;
   double rel = 0.0;
-  lbm_status s = residual(h, false, &rel);
+  LBM_CUDA_TRY(h, residual_launch(h, false));
+  lbm_status s = residual_read(h, &rel);
   if (s != LBM_OK) return s;
   int it = 0;
   if (h->cfg.poisson == LBM_POISSON_MG) {
+    // The previous solve's cycle count predicts this one (warm start, slowly
+    // varying charge): queue that many cycles minus one before the first
+    // host read-back, then test after every cycle.
+    int batch = std::max(1, P.last_cycles - 1);
     while (rel > tol && it < maxit) {
-      LBM_CUDA_TRY(h, vcycle(h));
-      s = residual(h, true, &rel);
+      const int nb = std::min(batch, maxit - it);
+      for (int k = 0; k < nb; ++k) {
+        LBM_CUDA_TRY(h, vcycle(h));
+        LBM_CUDA_TRY(h, residual_launch(h, true));
+      }
+      it += nb;
+      batch = 1;
+      s = residual_read(h, &rel);
       if (s != LBM_OK) return s;
-      ++it;
     }
+    P.last_cycles = it;
   } else {
     const Box b = make_box(h);
     const int64_t nbox = P.lev[0].n;
     const double inv_nf = 1.0 / (double)h->nfluid;
     const int L = std::max(std::max(h->cfg.nx, h->cfg.ny), P.nzb);
-    const float omega = (float)(2.0 / (1.0 + sin(3.14159265358979323846 / L)));
+    // Red-black ordering is a true two-colouring only when every periodic
+    // extent is even; otherwise same-colour neighbours meet across the wrap
+    // and are updated together, which over-relaxation does not tolerate:
+    // fall back to Gauss-Seidel weights there.
+    const bool odd_wrap = (h->cfg.nx > 1 && (h->cfg.nx & 1)) ||
+                          (h->cfg.ny > 1 && (h->cfg.ny & 1)) ||
+                          (P.perz && P.nzb > 1 && (P.nzb & 1));
+    const float omega =
+        odd_wrap ? 1.0f : (float)(2.0 / (1.0 + sin(3.14159265358979323846 / L)));
     const int check = 10;
     while (rel > tol && it < maxit) {
       for (int k = 0; k < check; ++k)
         for (int color = 0; color < 2; ++color) {
           if (h->has_walls)
-            k_sor0<true><<<nblocks(nbox, 256), 256, 0, h->st>>>(
-                P.psi[P.cur], P.src, h->links, P.dsum, b, nbox, inv_nf, color, omega);
+            { k_sor0<true><<<nblocks(nbox, 256), 256, 0, h->st>>>(
+                P.psi[P.cur], P.src, h->links, P.dsum, b, nbox, inv_nf, color, omega); ++h->launches; }
           else
-            k_sor0<false><<<nblocks(nbox, 256), 256, 0, h->st>>>(
-                P.psi[P.cur], P.src, nullptr, P.dsum, b, nbox, inv_nf, color, omega);
+            { k_sor0<false><<<nblocks(nbox, 256), 256, 0, h->st>>>(
+                P.psi[P.cur], P.src, nullptr, P.dsum, b, nbox, inv_nf, color, omega); ++h->launches; }
         }
       LBM_CUDA_TRY(h, cudaGetLastError());
       it += check;
-      s = residual(h, false, &rel);
+      LBM_CUDA_TRY(h, residual_launch(h, false));
+      s = residual_read(h, &rel);
       if (s != LBM_OK) return s;
     }
   }

@@ -230,11 +230,11 @@ class Lattice:
         self._check(self._lib.lbm_set_timing(self.h, int(bool(enable))))
 
     def get_timing(self):
-        out = np.zeros(6)
+        out = np.zeros(7)
         self._check(self._lib.lbm_get_timing(self.h, _ptr(out)))
         return {"charge_ms": out[0], "poisson_ms": out[1], "collide_ms": out[2],
                 "charge_launches": int(out[3]), "poisson_iters": int(out[4]),
-                "collide_launches": int(out[5])}
+                "collide_launches": int(out[5]), "kernel_launches": int(out[6])}
 
     @property
     def stream(self):
