@@ -170,6 +170,11 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     return LBM_ECUDA;
   }
   h->st = h->own;
+  {
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev) == cudaSuccess && nsm > 0)
+      h->grid_cap = 8 * nsm;
+  }
   const size_t pops = (size_t)h->S * Q * N * h->esize;
   for (int k = 0; k < 2 && s == LBM_OK; ++k) {
     if (cudaMalloc(&h->f[k], pops) != cudaSuccess) {
@@ -215,7 +220,7 @@ void lbm_destroy(lbm_t* h) {
   cudaFree(h->f[1]);
   cudaFree(h->links);
   cudaFree(h->wallq);
-  cudaFree(h->wcell);
+  cudaFree(h->wsrc);
   cudaFree(h->dred);
   cudaFree(h->dflag);
   if (h->hred) cudaFreeHost(h->hred);
@@ -238,7 +243,8 @@ lbm_status lbm_set_walls(lbm_t* h, const uint8_t* solid, const double* sigma) {
   if (nfluid == 0) return fail(h, LBM_EINVAL, "every node is a wall node");
   // Face charge share q_j = sigma_j / k_j of each wall node (k_j = number of
   // fluid face neighbours) and the wall charge w_i handed to each fluid cell.
-  std::vector<float> q(N, 0.f), w(N, 0.f);
+  std::vector<float> q(N, 0.f);
+  std::vector<double> qd(N, 0.0), wd(N, 0.0);
   auto idx = [&](int x, int y, int z) -> int64_t {
     x = (x + nx) % nx;
     y = (y + ny) % ny;
@@ -258,7 +264,8 @@ lbm_status lbm_set_walls(lbm_t* h, const uint8_t* solid, const double* sigma) {
           for (auto& d : fd)
             if (!solid[idx(x + d[0], y + d[1], z + d[2])]) ++k;
           if (k == 0) continue;
-          q[i] = (float)(sigma[i] / k);
+          qd[i] = sigma[i] / k;
+          q[i] = (float)qd[i];
           charged_walls = true;
         }
     for (int z = 0; z < nz; ++z)
@@ -269,9 +276,9 @@ lbm_status lbm_set_walls(lbm_t* h, const uint8_t* solid, const double* sigma) {
           double acc = 0.0;
           for (auto& d : fd) {
             const int64_t j = idx(x + d[0], y + d[1], z + d[2]);
-            if (solid[j]) acc += q[j];
+            if (solid[j]) acc += qd[j];
           }
-          w[i] = (float)acc;
+          wd[i] = acc;
         }
   }
   Scratch sc;
@@ -284,13 +291,17 @@ lbm_status lbm_set_walls(lbm_t* h, const uint8_t* solid, const double* sigma) {
   LBM_CUDA_TRY(h, launch_links(h, (const uint8_t*)sc.p));
   if (charged_walls) {
     if (!h->wallq && (s = dev_alloc(h, &h->wallq, N)) != LBM_OK) return s;
-    if (!h->wcell && (s = dev_alloc(h, &h->wcell, N)) != LBM_OK) return s;
+    if (!h->wsrc && (s = dev_alloc(h, &h->wsrc, N)) != LBM_OK) return s;
+    std::vector<int64_t> wfx(N, 0);
+    const double k4 = 4.0 * 3.14159265358979323846 * h->cfg.bjerrum;
+    for (int64_t i = 0; i < N; ++i) wfx[i] = llrint(k4 * wd[i] * PSI_SCALE);
     LBM_CUDA_TRY(h, cudaMemcpy(h->wallq, q.data(), N * sizeof(float), cudaMemcpyHostToDevice));
-    LBM_CUDA_TRY(h, cudaMemcpy(h->wcell, w.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+    LBM_CUDA_TRY(h, cudaMemcpy(h->wsrc, wfx.data(), N * sizeof(int64_t), cudaMemcpyHostToDevice));
   } else {
     cudaFree(h->wallq);
-    cudaFree(h->wcell);
-    h->wallq = h->wcell = nullptr;
+    cudaFree(h->wsrc);
+    h->wallq = nullptr;
+    h->wsrc = nullptr;
   }
   h->nfluid = nfluid;
   if (h->cfg.bjerrum > 0.0) {

@@ -68,7 +68,7 @@ struct Poisson {
   double* dsum = nullptr; // [0] sum of src over fluid, [1] sum r^2, [2] sum s^2 (fixed-point units)
   double* hsum = nullptr; // pinned mirror of dsum
   int64_t nfluid = 0;
-  int coarse_sweeps = 40;
+  int coarse_sweeps = 16;
   int last_cycles = 0;   // V-cycles of the previous solve
   int nu1 = 2, nu2 = 2;
 };
@@ -93,7 +93,7 @@ struct lbm {
   bool has_walls = false;
   uint32_t* links = nullptr;
   float* wallq = nullptr;
-  float* wcell = nullptr;
+  int64_t* wsrc = nullptr;  // 4 pi l_B w_i in fixed point (wall charge of each fluid cell)
   int64_t nfluid = 0;
   lbm_gb300::Poisson ps;
   bool psi_valid = false;
@@ -110,7 +110,8 @@ struct lbm {
   size_t ev_used = 0;
   double t_acc[3] = {0, 0, 0};
   int64_t t_cnt[3] = {0, 0, 0};
-  int64_t launches = 0;  // kernels launched since timing was (re)set
+  int64_t launches = 0;
+  int grid_cap = 1216;   // CTAs of the grid-stride reduction kernels (8 per SM)  // kernels launched since timing was (re)set
   std::string err;
 };
 

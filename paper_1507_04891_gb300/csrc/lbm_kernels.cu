@@ -7,6 +7,8 @@
 // post-collision populations before streaming; every kernel that needs
 // f(t) pulls them from the upstream node r - c_p (halfway bounce-back when
 // that node is a wall node), so streaming costs no separate pass.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -347,42 +349,44 @@ __global__ void k_init(int s, const double* __restrict__ n0,
 // ---------------------------------------------------------------------------
 template <bool WALLS, int ST>
 __global__ void __launch_bounds__(256) k_charge(
-    const void* fin_v, const uint32_t* links, const float* wcell, int64_t* src,
+    const void* fin_v, const uint32_t* links, const int64_t* wsrc, int64_t* src,
     double* dsum, int nx, int ny, int nz, int64_t N, int S, float4 val,
     float4 nref, float fourpi_lb) {
   using T = typename Fmt<ST>::T;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  long long sv = 0;
-  if (i < (uint32_t)N) {
+  const T* fin = static_cast<const T*>(fin_v);
+  const float vz[4] = {val.x, val.y, val.z, val.w};
+  const float nr[4] = {nref.x, nref.y, nref.z, nref.w};
+  long long acc = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)N;
+       i += gridDim.x * blockDim.x) {
     uint32_t lk = 0;
-    bool fluid = true;
     if (WALLS) {
       lk = links[i];
-      fluid = !(lk & LINK_SOLID);
-    }
-    if (fluid) {
-      int x, y, z;
-      site_xyz(i, nx, ny, x, y, z);
-      const Nbr o = neighbours(x, y, z, nx, ny, nz);
-      const T* fin = static_cast<const T*>(fin_v);
-      const float vz[4] = {val.x, val.y, val.z, val.w};
-      const float nr[4] = {nref.x, nref.y, nref.z, nref.w};
-      float rho = 0.f;
-      for (int s = 0; s < S; ++s) {
-        if (vz[s] == 0.f) continue;
-        float m0 = 0.f;
-#pragma unroll
-        for (int p = 0; p < Q; ++p)
-          m0 += pull<ST, WALLS>(fin, N, s, p, i, upstream(o, p), lk, nr[s]);
-        rho += vz[s] * m0;
+      if (lk & LINK_SOLID) {
+        src[i] = 0;
+        continue;
       }
-      if (wcell) rho += wcell[i];
-      // exact conversion: a float times a power of two, to a 64-bit integer
-      sv = (long long)(fourpi_lb * rho * PSI_SCALE_F);
     }
+    int x, y, z;
+    site_xyz(i, nx, ny, x, y, z);
+    const Nbr o = neighbours(x, y, z, nx, ny, nz);
+    float rho = 0.f;
+    for (int s = 0; s < S; ++s) {
+      if (vz[s] == 0.f) continue;
+      float m0 = 0.f;
+#pragma unroll
+      for (int p = 0; p < Q; ++p)
+        m0 += pull<ST, WALLS>(fin, N, s, p, i, upstream(o, p), lk, nr[s]);
+      rho += vz[s] * m0;
+    }
+    // exact conversion: a float times a power of two, to a 64-bit integer;
+    // the wall charge is already in fixed point
+    long long sv = (long long)(fourpi_lb * rho * PSI_SCALE_F);
+    if (wsrc) sv += wsrc[i];
     src[i] = sv;
+    acc += sv;
   }
-  block_sum_to(sv, dsum);
+  block_sum_to(acc, dsum);
 }
 
 // Gathers f(t) of species s and its moments n, u = sum c f / n (doubles).
@@ -433,10 +437,10 @@ __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
                                               float4 val, float4 nref,
                                               double* out, int* bad) {
   using T = typename Fmt<ST>::T;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[MAX_SPECIES + 4];
   for (int k = 0; k < MAX_SPECIES + 4; ++k) acc[k] = 0.0;
-  if (i < (uint32_t)N) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)N;
+       i += gridDim.x * blockDim.x) {
     uint32_t lk = 0;
     bool fluid = true;
     if (WALLS) {
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
         if (!(m0 > 0.f) || !isfinite(m0) || !isfinite(mx) || !isfinite(my) ||
             !isfinite(mz))
           atomicOr(bad, 1);
-        acc[s] = m0;
+        acc[s] += m0;
         acc[MAX_SPECIES + 0] += mx;
         acc[MAX_SPECIES + 1] += my;
         acc[MAX_SPECIES + 2] += mz;
@@ -515,16 +519,18 @@ __global__ void k_psi_from_double(const double* in, int64_t* psi,
 }
 
 __global__ void __launch_bounds__(256) k_src_from_rho(
-    const double* rho, const uint32_t* links, const float* wcell, int64_t* src,
+    const double* rho, const uint32_t* links, const int64_t* wsrc, int64_t* src,
     double* dsum, int64_t N, double fourpi_lb) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  long long sv = 0;
-  if (i < N) {
+  long long acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
     const bool solid = links && (links[i] & LINK_SOLID);
-    if (!solid) sv = llrint(fourpi_lb * (rho[i] + (wcell ? (double)wcell[i] : 0.0)) * PSI_SCALE);
+    long long sv = 0;
+    if (!solid) sv = llrint(fourpi_lb * rho[i] * PSI_SCALE) + (wsrc ? wsrc[i] : 0);
     src[i] = sv;
+    acc += sv;
   }
-  block_sum_to(sv, dsum);
+  block_sum_to(acc, dsum);
 }
 
 inline unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -620,10 +626,10 @@ cudaError_t launch_init_species(lbm_t* h, int s, const double* n0,
 }
 
 cudaError_t launch_charge(lbm_t* h) {
-  const int nb = nblocks(h->N, 256);
+  const int nb = (int)std::min<int64_t>(nblocks(h->N, 256), h->grid_cap);
   const float k = (float)(4.0 * 3.14159265358979323846 * h->cfg.bjerrum);
   LBM_DISPATCH_WS(h, (k_charge<W_, ST_><<<nb, 256, 0, h->st>>>(
-                         h->f[h->cur], h->links, h->wcell, h->ps.src,
+                         h->f[h->cur], h->links, h->wsrc, h->ps.src,
                          h->ps.dsum, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,
                          h->S, as_f4(h->valence), as_f4(h->nref), k)));
   ++h->launches;
@@ -641,7 +647,7 @@ cudaError_t launch_gather(lbm_t* h, int s, double* n_dev, double* u_dev,
 }
 
 cudaError_t launch_diagnostics(lbm_t* h) {
-  const int nb = nblocks(h->N, 256);
+  const int nb = (int)std::min<int64_t>(nblocks(h->N, 256), h->grid_cap);
   LBM_DISPATCH_WS(h, (k_diag<W_, ST_><<<nb, 256, 0, h->st>>>(
                          h->f[h->cur], h->links, h->cfg.nx, h->cfg.ny,
                          h->cfg.nz, h->N, h->S, as_f4(h->valence),
@@ -671,8 +677,8 @@ cudaError_t launch_psi_from_double(lbm_t* h, const double* in, int64_t* psi) {
 
 cudaError_t launch_src_from_rho(lbm_t* h, const double* rho_dev) {
   const double k = 4.0 * 3.14159265358979323846 * h->cfg.bjerrum;
-  k_src_from_rho<<<nblocks(h->N, 256), 256, 0, h->st>>>(
-      rho_dev, h->links, h->wcell, h->ps.src, h->ps.dsum, h->N, k);
+  k_src_from_rho<<<(unsigned)std::min<int64_t>(nblocks(h->N, 256), h->grid_cap), 256, 0,
+                   h->st>>>(rho_dev, h->links, h->wsrc, h->ps.src, h->ps.dsum, h->N, k);
   ++h->launches;
   return cudaGetLastError();
 }

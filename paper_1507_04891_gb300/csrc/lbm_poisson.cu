@@ -84,39 +84,41 @@ __global__ void __launch_bounds__(256) k_res0(
   __shared__ float red_r[8], red_s[8];
   if (threadIdx.x == 0) s_mean = llrint(dsum[0] * inv_nfluid);
   __syncthreads();
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   float rr = 0.f, ss = 0.f;
-  if (c < (uint32_t)nbox) {
+  // grid-stride loop over a grid capped at a few CTAs per SM: one pair of
+  // FP64 atomics per CTA instead of per 256 cells
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < (uint32_t)nbox;
+       c += gridDim.x * blockDim.x) {
     const int64_t i = (int64_t)c + (int64_t)b.zlo * b.nxy;  // lattice node
     uint32_t lk = 0;
     if (WALLS) lk = links[i];
     if (WALLS && (lk & LINK_SOLID)) {
       r[c] = 0.f;
       if (UPDATE) psi_out[i] = 0;
-    } else {
-      int x, y, z;
-      box_xyz(c, b, x, y, z);
-      int d[6];
-      box_nbr(b, x, y, z, d);
-      int64_t pc = psi_in[i];
-      if (UPDATE) pc += fx_of(e[c]);
-      int64_t Ap = 0;
-#pragma unroll
-      for (int f = 0; f < 6; ++f) {
-        if (WALLS && !open_face(lk, f)) continue;
-        int64_t pn = psi_in[i + d[f]];
-        if (UPDATE) pn += fx_of(e[(int64_t)c + d[f]]);
-        Ap += pc - pn;
-      }
-      const int64_t sfx = src[i] - s_mean;
-      const int64_t rfx = sfx - Ap;
-      const float rf = (float)rfx;
-      r[c] = rf * PSI_INV_SCALE_F;
-      if (UPDATE) psi_out[i] = pc;
-      rr = rf * rf;
-      const float sf = (float)sfx;
-      ss = sf * sf;
+      continue;
     }
+    int x, y, z;
+    box_xyz(c, b, x, y, z);
+    int d[6];
+    box_nbr(b, x, y, z, d);
+    int64_t pc = psi_in[i];
+    if (UPDATE) pc += fx_of(e[c]);
+    int64_t Ap = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      if (WALLS && !open_face(lk, f)) continue;
+      int64_t pn = psi_in[i + d[f]];
+      if (UPDATE) pn += fx_of(e[(int64_t)c + d[f]]);
+      Ap += pc - pn;
+    }
+    const int64_t sfx = src[i] - s_mean;
+    const int64_t rfx = sfx - Ap;
+    const float rf = (float)rfx;
+    r[c] = rf * PSI_INV_SCALE_F;
+    if (UPDATE) psi_out[i] = pc;
+    rr += rf * rf;
+    const float sf = (float)sfx;
+    ss += sf * sf;
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -508,43 +510,54 @@ struct SubHier {
 __global__ void __launch_bounds__(1024) k_sub_cycle(const SubHier H, int nu1, int nu2,
                                                     int sweeps) {
   extern __shared__ float sm[];
-  float* E[SUB_MAX_LEVELS];
-  float* R[SUB_MAX_LEVELS];
-  float* KK[SUB_MAX_LEVELS];
-  float* DD[SUB_MAX_LEVELS];
-  int off = 0;
-  for (int l = 0; l < H.nlev; ++l) {
-    const int n = (int)H.lev[l].l.n;
-    E[l] = sm + off;
-    off += n;
-    R[l] = sm + off;
-    off += n;
-    KK[l] = sm + off;
-    off += 3 * n;
-    DD[l] = sm + off;
-    off += n;
-  }
+  __shared__ int offs[SUB_MAX_LEVELS];
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    int off = 0;
+    for (int l = 0; l < H.nlev; ++l) {
+      offs[l] = off;
+      off += 6 * (int)H.lev[l].l.n;
+    }
+  }
+  __syncthreads();
+  // level l occupies [e | rhs | K (3n) | Dinv] at sm + offs[l]
+  struct Lv {
+    float *e, *r, *K, *D;
+  };
+  auto lv = [&](int l) {
+    const int n = (int)H.lev[l].l.n;
+    Lv v;
+    v.e = sm + offs[l];
+    v.r = v.e + n;
+    v.K = v.r + n;
+    v.D = v.K + 3 * n;
+    return v;
+  };
   for (int l = 0; l < H.nlev; ++l) {
     const int n = (int)H.lev[l].l.n;
+    const Lv v = lv(l);
     for (int c = tid; c < n; c += nt) {
-      E[l][c] = 0.f;
-      R[l][c] = l == 0 ? H.rhs_in[c] : 0.f;
-      DD[l][c] = H.lev[l].Dinv[c];
-      KK[l][c] = H.lev[l].K[c];
-      KK[l][n + c] = H.lev[l].K[n + c];
-      KK[l][2 * n + c] = H.lev[l].K[2 * n + c];
+      v.e[c] = 0.f;
+      v.r[c] = l == 0 ? H.rhs_in[c] : 0.f;
+      v.D[c] = H.lev[l].Dinv[c];
+      v.K[c] = H.lev[l].K[c];
+      v.K[n + c] = H.lev[l].K[n + c];
+      v.K[2 * n + c] = H.lev[l].K[2 * n + c];
     }
   }
   __syncthreads();
   auto smooth = [&](int l, int count) {
-    const CL& L = H.lev[l].l;
+    const CL L = H.lev[l].l;
+    const Lv v = lv(l);
+    const int compact = (L.nx % 2 == 0);
+    const int work = compact ? (int)(L.n >> 1) : (int)L.n;
     for (int k = 0; k < count; ++k)
       for (int color = 0; color < 2; ++color) {
-        for (int c = tid; c < (int)L.n; c += nt) {
+        for (int t = tid; t < work; t += nt) {
+          uint32_t c;
           int xx, yy, zz;
-          cl_xyz((uint32_t)c, L, xx, yy, zz);
-          if (((xx + yy + zz) & 1) == color) gs_cell(E[l], R[l], KK[l], DD[l], L, c, xx, yy, zz);
+          if (rb_cell((uint32_t)t, L.nx, L.ny, L.n, color, compact, c, xx, yy, zz))
+            gs_cell(v.e, v.r, v.K, v.D, L, c, xx, yy, zz);
         }
         __syncthreads();
       }
@@ -552,27 +565,31 @@ __global__ void __launch_bounds__(1024) k_sub_cycle(const SubHier H, int nu1, in
   for (int l = 0; l + 1 < H.nlev; ++l) {
     smooth(l, nu1);
     const SubLevel& C = H.lev[l + 1];
+    const Lv f = lv(l), cv = lv(l + 1);
+    const CL F = H.lev[l].l;
     for (int J = tid; J < (int)C.l.n; J += nt) {
       int X, Y, Z;
       cl_xyz((uint32_t)J, C.l, X, Y, Z);
-      R[l + 1][J] = restrict_cell(E[l], R[l], KK[l], DD[l], H.lev[l].l, X, Y, Z, C.cx, C.cy, C.cz);
+      cv.r[J] = restrict_cell(f.e, f.r, f.K, f.D, F, X, Y, Z, C.cx, C.cy, C.cz);
     }
     __syncthreads();
   }
-  smooth(H.nlev - 1, H.nlev == 1 ? sweeps : sweeps);
+  smooth(H.nlev - 1, sweeps);
   for (int l = H.nlev - 2; l >= 0; --l) {
     const SubLevel& C = H.lev[l + 1];
-    const CL& L = H.lev[l].l;
+    const CL L = H.lev[l].l;
+    const Lv f = lv(l), cv = lv(l + 1);
     for (int c = tid; c < (int)L.n; c += nt) {
-      if (DD[l][c] == 0.f) continue;
+      if (f.D[c] == 0.f) continue;
       int xx, yy, zz;
       cl_xyz((uint32_t)c, L, xx, yy, zz);
-      E[l][c] += prolong_cell(E[l + 1], DD[l + 1], C.l, xx, yy, zz, C.cx, C.cy, C.cz);
+      f.e[c] += prolong_cell(cv.e, cv.D, C.l, xx, yy, zz, C.cx, C.cy, C.cz);
     }
     __syncthreads();
     smooth(l, nu2);
   }
-  for (int c = tid; c < (int)H.lev[0].l.n; c += nt) H.e_out[c] = E[0][c];
+  const Lv v0 = lv(0);
+  for (int c = tid; c < (int)H.lev[0].l.n; c += nt) H.e_out[c] = v0.e[c];
 }
 
 inline unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -793,7 +810,7 @@ cudaError_t residual_launch(lbm_t* h, bool update) {
   if (e != cudaSuccess) return e;
   const int64_t* pin = P.psi[P.cur];
   int64_t* pout = P.psi[P.cur ^ 1];
-  const unsigned nb = nblocks(nbox, 256);
+  const unsigned nb = (unsigned)std::min<int64_t>(nblocks(nbox, 256), h->grid_cap);
   if (h->has_walls) {
     if (update)
       k_res0<true, true><<<nb, 256, 0, h->st>>>(pin, P.lev[0].e, pout, P.src, h->links,
