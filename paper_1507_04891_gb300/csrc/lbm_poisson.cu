@@ -790,8 +790,15 @@ lbm_status poisson_setup(lbm_t* h, const uint8_t* solid) {
       h->err = "coarse Poisson levels exceed the shared memory of one CTA";
       return LBM_EINVAL;
     }
+    cudaFuncAttributes fa;
+    LBM_CUDA_TRY(h, cudaFuncGetAttributes(&fa, k_sub_cycle));
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;
+    if ((int)sub_smem(P, lc) > dyn_max) {
+      h->err = "coarse Poisson levels exceed the shared memory of one CTA";
+      return LBM_EINVAL;
+    }
     LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_sub_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         optin));
+                                         dyn_max));
   }
   LBM_CUDA_TRY(h, cudaGetLastError());
   return LBM_OK;
