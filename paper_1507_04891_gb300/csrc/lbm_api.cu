@@ -193,6 +193,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.psi[1], N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.src, N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.dsum, 4);
+    if (s == LBM_OK) s = dev_alloc(h, &h->ps.part, (size_t)((N + 255) / 256));
     if (s == LBM_OK && cudaMallocHost(&h->ps.hsum, 4 * sizeof(double)) != cudaSuccess)
       s = LBM_ENOMEM;
     if (s == LBM_OK) {

@@ -67,6 +67,7 @@ struct Poisson {
   int64_t* src = nullptr; // 4 pi l_B (rho_e + w) per lattice node (fixed point), no mean removed
   double* dsum = nullptr; // [0] sum of src over fluid, [1] sum r^2, [2] sum s^2 (fixed-point units)
   double* hsum = nullptr; // pinned mirror of dsum
+  long long* part = nullptr; // per-CTA partial sums of the charge kernel
   int64_t nfluid = 0;
   int coarse_sweeps = 16;
   int last_cycles = 0;   // V-cycles of the previous solve

@@ -162,6 +162,20 @@ __device__ __forceinline__ void psi_gradient(const StepArgs& a, uint32_t i,
   gz = 0.5f * (gpz + gmz);
 }
 
+// Block sum of 64-bit integers (exact), written to part[blockIdx.x].
+__device__ __forceinline__ void block_partial(long long v, long long* part) {
+  __shared__ long long red[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    part[blockIdx.x] = tot;
+  }
+}
+
 // Block sum of 64-bit integers (exact), added to *out as one FP64 value per
 // block (a block's sum is far below 2^53, so the conversion is exact).
 __device__ __forceinline__ void block_sum_to(long long v, double* out) {
@@ -350,7 +364,7 @@ __global__ void k_init(int s, const double* __restrict__ n0,
 template <bool WALLS, int ST>
 __global__ void __launch_bounds__(256) k_charge(
     const void* fin_v, const uint32_t* links, const int64_t* wsrc, int64_t* src,
-    double* dsum, int nx, int ny, int nz, int64_t N, int S, float4 val,
+    long long* part, int nx, int ny, int nz, int64_t N, int S, float4 val,
     float4 nref, float fourpi_lb) {
   using T = typename Fmt<ST>::T;
   const T* fin = static_cast<const T*>(fin_v);
@@ -386,7 +400,25 @@ __global__ void __launch_bounds__(256) k_charge(
     src[i] = sv;
     acc += sv;
   }
-  block_sum_to(acc, dsum);
+  block_partial(acc, part);
+}
+
+// Sums the per-CTA partials of k_charge into *out (FP64; each partial is
+// exact in FP64).
+__global__ void __launch_bounds__(1024) k_sum_partials(const long long* part, int n,
+                                                       double* out) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) v += (double)part[k];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    *out = tot;
+  }
 }
 
 // Gathers f(t) of species s and its moments n, u = sum c f / n (doubles).
@@ -626,13 +658,16 @@ cudaError_t launch_init_species(lbm_t* h, int s, const double* n0,
 }
 
 cudaError_t launch_charge(lbm_t* h) {
-  const int nb = (int)std::min<int64_t>(nblocks(h->N, 256), h->grid_cap);
+  // one node per thread (the pulled loads of a node are independent and all
+  // in flight); per-CTA partial sums instead of same-address atomics
+  const int nb = (int)nblocks(h->N, 256);
   const float k = (float)(4.0 * 3.14159265358979323846 * h->cfg.bjerrum);
   LBM_DISPATCH_WS(h, (k_charge<W_, ST_><<<nb, 256, 0, h->st>>>(
                          h->f[h->cur], h->links, h->wsrc, h->ps.src,
-                         h->ps.dsum, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,
+                         h->ps.part, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,
                          h->S, as_f4(h->valence), as_f4(h->nref), k)));
-  ++h->launches;
+  k_sum_partials<<<1, 1024, 0, h->st>>>(h->ps.part, nb, h->ps.dsum);
+  h->launches += 2;
   return cudaGetLastError();
 }
 

@@ -70,14 +70,12 @@ __device__ __forceinline__ int64_t fx_of(float e) {
   return llrintf(e * PSI_SCALE_F);
 }
 
-// Residual on the fine box, optionally applying the correction first:
-//   psi_new = psi_in + round(e),  r = s - <s> - A psi_new   (exact in int64)
-// Writes r (FP32) to rhs, psi_new to psi_out, and block sums of r^2 and
-// (s - <s>)^2 (fixed-point units) to dsum[1], dsum[2].
-template <bool WALLS, bool UPDATE>
+// Residual on the fine box, r = s - <s> - A psi, exact in 64-bit integers.
+// Writes r (FP32) to rhs and block sums of r^2 and (s - <s>)^2 (fixed-point
+// units) to dsum[1], dsum[2].
+template <bool WALLS>
 __global__ void __launch_bounds__(256) k_res0(
-    const int64_t* __restrict__ psi_in, const float* __restrict__ e,
-    int64_t* __restrict__ psi_out, const int64_t* __restrict__ src,
+    const int64_t* __restrict__ psi, const int64_t* __restrict__ src,
     const uint32_t* __restrict__ links, float* __restrict__ r, double* dsum,
     Box b, int64_t nbox, double inv_nfluid) {
   __shared__ long long s_mean;
@@ -94,28 +92,22 @@ __global__ void __launch_bounds__(256) k_res0(
     if (WALLS) lk = links[i];
     if (WALLS && (lk & LINK_SOLID)) {
       r[c] = 0.f;
-      if (UPDATE) psi_out[i] = 0;
       continue;
     }
     int x, y, z;
     box_xyz(c, b, x, y, z);
     int d[6];
     box_nbr(b, x, y, z, d);
-    int64_t pc = psi_in[i];
-    if (UPDATE) pc += fx_of(e[c]);
+    const int64_t pc = psi[i];
     int64_t Ap = 0;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       if (WALLS && !open_face(lk, f)) continue;
-      int64_t pn = psi_in[i + d[f]];
-      if (UPDATE) pn += fx_of(e[(int64_t)c + d[f]]);
-      Ap += pc - pn;
+      Ap += pc - psi[i + d[f]];
     }
     const int64_t sfx = src[i] - s_mean;
-    const int64_t rfx = sfx - Ap;
-    const float rf = (float)rfx;
+    const float rf = (float)(sfx - Ap);
     r[c] = rf * PSI_INV_SCALE_F;
-    if (UPDATE) psi_out[i] = pc;
     rr += rf * rf;
     const float sf = (float)sfx;
     ss += sf * sf;
@@ -167,19 +159,22 @@ __device__ __forceinline__ bool rb_cell(uint32_t t, int nx, int ny, int64_t n,
   return ((x + y + z) & 1) == color;
 }
 
-// Red-black Gauss-Seidel on the fine box for A e = r (FP32).
-template <bool WALLS>
+// Red-black Gauss-Seidel on the fine box for A e = r (FP32).  With APPLY
+// (the last sweep of a V-cycle) each cell also writes its final correction
+// into the other potential buffer: psi_out = psi_in + round(e).
+template <bool WALLS, bool APPLY>
 __global__ void __launch_bounds__(256) k_smooth0(
     float* __restrict__ e, const float* __restrict__ r,
     const uint32_t* __restrict__ links, Box b, int64_t nbox, int color,
-    int compact) {
+    int compact, const int64_t* __restrict__ psi_in, int64_t* __restrict__ psi_out) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t c;
   int x, y, z;
   if (!rb_cell(t, b.nx, b.ny, nbox, color, compact, c, x, y, z)) return;
+  const int64_t i = (int64_t)c + (int64_t)b.zlo * b.nxy;
   uint32_t lk = 0;
   if (WALLS) {
-    lk = links[(int64_t)c + (int64_t)b.zlo * b.nxy];
+    lk = links[i];
     if (lk & LINK_SOLID) return;
   }
   int d[6];
@@ -192,7 +187,12 @@ __global__ void __launch_bounds__(256) k_smooth0(
     sum += e[(int64_t)c + d[f]];
     ++cnt;
   }
-  if (cnt > 0) e[c] = sum / (float)cnt;
+  float ev = e[c];
+  if (cnt > 0) {
+    ev = sum / (float)cnt;
+    e[c] = ev;
+  }
+  if (APPLY) psi_out[i] = psi_in[i] + fx_of(ev);
 }
 
 // Red-black SOR directly on the fixed-point psi (in place).
@@ -632,6 +632,8 @@ void poisson_free(lbm_t* h) {
   cudaFree(P.psi[1]);
   cudaFree(P.src);
   cudaFree(P.dsum);
+  cudaFree(P.part);
+  P.part = nullptr;
   if (P.hsum) cudaFreeHost(P.hsum);
   P.psi[0] = P.psi[1] = nullptr;
   P.src = nullptr;
@@ -806,36 +808,24 @@ lbm_status poisson_setup(lbm_t* h, const uint8_t* solid) {
 
 namespace {
 
-// Queues the fine-box residual (optionally applying the pending correction
-// first) and the device-to-host copy of its norms; does not wait.
-cudaError_t residual_launch(lbm_t* h, bool update) {
+// Queues the fine-box residual of the current potential and the
+// device-to-host copy of its norms; does not wait.
+cudaError_t residual_launch(lbm_t* h) {
   Poisson& P = h->ps;
   const Box b = make_box(h);
   const int64_t nbox = P.lev[0].n;
   const double inv_nf = 1.0 / (double)h->nfluid;
   cudaError_t e = cudaMemsetAsync(P.dsum + 1, 0, 2 * sizeof(double), h->st);
   if (e != cudaSuccess) return e;
-  const int64_t* pin = P.psi[P.cur];
-  int64_t* pout = P.psi[P.cur ^ 1];
   const unsigned nb = (unsigned)std::min<int64_t>(nblocks(nbox, 256), h->grid_cap);
-  if (h->has_walls) {
-    if (update)
-      k_res0<true, true><<<nb, 256, 0, h->st>>>(pin, P.lev[0].e, pout, P.src, h->links,
-                                                P.lev[0].rhs, P.dsum, b, nbox, inv_nf);
-    else
-      k_res0<true, false><<<nb, 256, 0, h->st>>>(pin, nullptr, nullptr, P.src, h->links,
-                                                 P.lev[0].rhs, P.dsum, b, nbox, inv_nf);
-  } else {
-    if (update)
-      k_res0<false, true><<<nb, 256, 0, h->st>>>(pin, P.lev[0].e, pout, P.src, nullptr,
-                                                 P.lev[0].rhs, P.dsum, b, nbox, inv_nf);
-    else
-      k_res0<false, false><<<nb, 256, 0, h->st>>>(pin, nullptr, nullptr, P.src, nullptr,
-                                                  P.lev[0].rhs, P.dsum, b, nbox, inv_nf);
-  }
+  if (h->has_walls)
+    k_res0<true><<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, h->links, P.lev[0].rhs, P.dsum,
+                                        b, nbox, inv_nf);
+  else
+    k_res0<false><<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, nullptr, P.lev[0].rhs, P.dsum,
+                                         b, nbox, inv_nf);
   ++h->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (update) P.cur ^= 1;
   return cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
 }
 
@@ -853,21 +843,36 @@ lbm_status residual_read(lbm_t* h, double* rel) {
   return LBM_OK;
 }
 
-cudaError_t smooth_level(lbm_t* h, int l, int sweeps) {
+cudaError_t smooth_level(lbm_t* h, int l, int sweeps, bool apply = false) {
   Poisson& P = h->ps;
   PoissonLevel& L = P.lev[l];
   const int compact = (L.nx % 2 == 0) ? 1 : 0;
   const unsigned nb = nblocks(compact ? L.n / 2 : L.n, 256);
   if (l == 0) {
     const Box b = make_box(h);
+    const int64_t* pin = P.psi[P.cur];
+    int64_t* pout = P.psi[P.cur ^ 1];
     for (int k = 0; k < sweeps; ++k)
       for (int color = 0; color < 2; ++color) {
-        if (h->has_walls)
-          k_smooth0<true><<<nb, 256, 0, h->st>>>(L.e, L.rhs, h->links, b, L.n, color, compact);
-        else
-          k_smooth0<false><<<nb, 256, 0, h->st>>>(L.e, L.rhs, nullptr, b, L.n, color, compact);
+        const bool last = apply && k == sweeps - 1;
+        if (h->has_walls) {
+          if (last)
+            k_smooth0<true, true><<<nb, 256, 0, h->st>>>(L.e, L.rhs, h->links, b, L.n, color,
+                                                         compact, pin, pout);
+          else
+            k_smooth0<true, false><<<nb, 256, 0, h->st>>>(L.e, L.rhs, h->links, b, L.n, color,
+                                                          compact, pin, pout);
+        } else {
+          if (last)
+            k_smooth0<false, true><<<nb, 256, 0, h->st>>>(L.e, L.rhs, nullptr, b, L.n, color,
+                                                          compact, pin, pout);
+          else
+            k_smooth0<false, false><<<nb, 256, 0, h->st>>>(L.e, L.rhs, nullptr, b, L.n, color,
+                                                           compact, pin, pout);
+        }
         ++h->launches;
       }
+    if (apply) P.cur ^= 1;
   } else {
     const CL c = make_cl(L);
     for (int k = 0; k < sweeps; ++k)
@@ -920,7 +925,7 @@ cudaError_t vcycle(lbm_t* h) {
   const Box b = make_box(h);
   cudaError_t e = cudaMemsetAsync(P.lev[0].e, 0, P.lev[0].n * sizeof(float), h->st);
   if (e != cudaSuccess) return e;
-  if (nl == 1) return smooth_level(h, 0, 8);
+  if (nl == 1) return smooth_level(h, 0, 8, true);
   const int lc = sub_level(P);
   if ((e = smooth_level(h, 0, P.nu1)) != cudaSuccess) return e;
   {
@@ -973,7 +978,7 @@ cudaError_t vcycle(lbm_t* h) {
                                                      C.coarsened[1], C.coarsened[2]);
     }
     ++h->launches;
-    if ((e = smooth_level(h, l, P.nu2)) != cudaSuccess) return e;
+    if ((e = smooth_level(h, l, P.nu2, l == 0)) != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -984,7 +989,7 @@ lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
                          double* rel_res) {
   Poisson& P = h->ps;
   double rel = 0.0;
-  LBM_CUDA_TRY(h, residual_launch(h, false));
+  LBM_CUDA_TRY(h, residual_launch(h));
   lbm_status s = residual_read(h, &rel);
   if (s != LBM_OK) return s;
   int it = 0;
@@ -997,7 +1002,7 @@ lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
       const int nb = std::min(batch, maxit - it);
       for (int k = 0; k < nb; ++k) {
         LBM_CUDA_TRY(h, vcycle(h));
-        LBM_CUDA_TRY(h, residual_launch(h, true));
+        LBM_CUDA_TRY(h, residual_launch(h));
       }
       it += nb;
       batch = 1;
@@ -1032,7 +1037,7 @@ lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
         }
       LBM_CUDA_TRY(h, cudaGetLastError());
       it += check;
-      LBM_CUDA_TRY(h, residual_launch(h, false));
+      LBM_CUDA_TRY(h, residual_launch(h));
       s = residual_read(h, &rel);
       if (s != LBM_OK) return s;
     }
