@@ -472,7 +472,7 @@ lbm_status lbm_solve_poisson(lbm_t* h, const double* rho_e, double* psi,
   const int64_t N = h->N;
   for (int64_t i = 0; i < N; ++i)
     if (!isfinite(rho_e[i]) || !isfinite(psi[i]) || fabs(psi[i]) >= PSI_MAX)
-      return fail(h, LBM_EINVAL, "rho_e and psi must be finite, |psi| < 2^19");
+      return fail(h, LBM_EINVAL, "rho_e and psi must be finite, |psi| < 2048");
   Scratch sc;
   if (cudaMalloc(&sc.p, 2 * N * sizeof(double)) != cudaSuccess)
     return fail(h, LBM_ENOMEM, "scratch allocation failed");

@@ -16,16 +16,18 @@ constexpr int Q = 19;
 constexpr int MAX_SPECIES = 4;
 
 // Potential psi is held on the device as a signed 64-bit fixed-point number
-// with 44 fractional bits: psi = k * 2^-44 (|psi| < 2^19).  Sums and
+// with 52 fractional bits: psi = k * 2^-52 (|psi| < 2^11 = 2048, far beyond
+// any potential of a lattice electrolyte in units of k_B T / e).  Sums and
 // differences of neighbouring values are then exact integer operations, so
 // the Poisson residual s - A psi is computed without cancellation error and
 // without FP64 arithmetic (FP64 throughput on GB300 is a small fraction of
-// FP32).  The smoothers work on FP32 corrections.
-constexpr double PSI_SCALE = 17592186044416.0;        // 2^44
-constexpr double PSI_INV_SCALE = 1.0 / 17592186044416.0;
-constexpr float PSI_SCALE_F = 17592186044416.0f;
-constexpr float PSI_INV_SCALE_F = 1.0f / 17592186044416.0f;
-constexpr double PSI_MAX = 524288.0;                  // 2^19
+// FP32).  The Poisson source s = 4 pi l_B (rho_e + w) uses the same scale
+// (|s| < 2048).  The smoothers work on FP32 corrections.
+constexpr double PSI_SCALE = 4503599627370496.0;        // 2^52
+constexpr double PSI_INV_SCALE = 1.0 / 4503599627370496.0;
+constexpr float PSI_SCALE_F = 4503599627370496.0f;
+constexpr float PSI_INV_SCALE_F = 1.0f / 4503599627370496.0f;
+constexpr double PSI_MAX = 2048.0;                      // 2^11
 
 // Per-node link word (only allocated when walls exist):
 //   bit 0      node is a wall node
@@ -70,7 +72,7 @@ struct Poisson {
   long long* part = nullptr; // per-CTA partial sums of the charge kernel
   int64_t nfluid = 0;
   int coarse_sweeps = 16;
-  int last_cycles = 0;   // V-cycles of the previous solve
+  double conv = 0.15;    // measured residual reduction per V-cycle (last solve)
   int nu1 = 2, nu2 = 2;
 };
 

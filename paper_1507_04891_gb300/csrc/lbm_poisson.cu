@@ -829,17 +829,20 @@ cudaError_t residual_launch(lbm_t* h) {
   return cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
 }
 
-// Waits for the last queued residual and returns ||r|| / ||s||.
-lbm_status residual_read(lbm_t* h, double* rel) {
+// Waits for the last queued residual.  Returns ||r|| / ||s|| in *rel and
+// whether the solve has converged: relative residual <= tol, or a residual
+// at the fixed-point resolution of psi (rms below 2 units of 2^-52), which
+// is all a charge-neutral source of vanishing norm allows.
+lbm_status residual_read(lbm_t* h, double tol, double* rel, bool* done) {
   Poisson& P = h->ps;
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
-  const double floor_fx = sqrt((double)h->nfluid) * 1e-12 * PSI_SCALE;
   const double rn = sqrt(P.hsum[1]), sn = sqrt(P.hsum[2]);
-  *rel = rn / std::max(sn, floor_fx);
-  if (!isfinite(*rel)) {
+  *rel = sn > 0.0 ? rn / sn : (rn > 0.0 ? INFINITY : 0.0);
+  if (!isfinite(rn) || !isfinite(sn)) {
     h->err = "Poisson residual is not finite";
     return LBM_EUNSTABLE;
   }
+  *done = rn <= tol * sn || rn <= 2.0 * sqrt((double)h->nfluid);
   return LBM_OK;
 }
 
@@ -988,17 +991,23 @@ cudaError_t vcycle(lbm_t* h) {
 lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
                          double* rel_res) {
   Poisson& P = h->ps;
-  double rel = 0.0;
+  double rel = 0.0, rel0 = 0.0;
+  bool done = false;
   LBM_CUDA_TRY(h, residual_launch(h));
-  lbm_status s = residual_read(h, &rel);
+  lbm_status s = residual_read(h, tol, &rel, &done);
   if (s != LBM_OK) return s;
+  rel0 = rel;
   int it = 0;
   if (h->cfg.poisson == LBM_POISSON_MG) {
-    // The previous solve's cycle count predicts this one (warm start, slowly
-    // varying charge): queue that many cycles minus one before the first
-    // host read-back, then test after every cycle.
-    int batch = std::max(1, P.last_cycles - 1);
-    while (rel > tol && it < maxit) {
+    // Queue the predicted number of cycles (from the initial residual and
+    // the reduction per cycle measured in the last solve) minus one before
+    // the first host read-back, then test after every cycle.
+    int batch = 1;
+    if (!done && rel0 > 0.0 && isfinite(rel0)) {
+      const double need = std::log(tol / rel0) / std::log(P.conv);
+      batch = std::max(1, std::min(maxit, (int)std::ceil(need) - 1));
+    }
+    while (!done && it < maxit) {
       const int nb = std::min(batch, maxit - it);
       for (int k = 0; k < nb; ++k) {
         LBM_CUDA_TRY(h, vcycle(h));
@@ -1006,10 +1015,11 @@ lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
       }
       it += nb;
       batch = 1;
-      s = residual_read(h, &rel);
+      s = residual_read(h, tol, &rel, &done);
       if (s != LBM_OK) return s;
     }
-    P.last_cycles = it;
+    if (it > 0 && rel > 0.0 && rel0 > 0.0 && isfinite(rel) && rel < rel0)
+      P.conv = std::min(0.6, std::max(0.01, std::pow(rel / rel0, 1.0 / it)));
   } else {
     const Box b = make_box(h);
     const int64_t nbox = P.lev[0].n;
@@ -1025,26 +1035,27 @@ lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
     const float omega =
         odd_wrap ? 1.0f : (float)(2.0 / (1.0 + sin(3.14159265358979323846 / L)));
     const int check = 10;
-    while (rel > tol && it < maxit) {
+    while (!done && it < maxit) {
       for (int k = 0; k < check; ++k)
         for (int color = 0; color < 2; ++color) {
           if (h->has_walls)
-            { k_sor0<true><<<nblocks(nbox, 256), 256, 0, h->st>>>(
-                P.psi[P.cur], P.src, h->links, P.dsum, b, nbox, inv_nf, color, omega); ++h->launches; }
+            k_sor0<true><<<nblocks(nbox, 256), 256, 0, h->st>>>(
+                P.psi[P.cur], P.src, h->links, P.dsum, b, nbox, inv_nf, color, omega);
           else
-            { k_sor0<false><<<nblocks(nbox, 256), 256, 0, h->st>>>(
-                P.psi[P.cur], P.src, nullptr, P.dsum, b, nbox, inv_nf, color, omega); ++h->launches; }
+            k_sor0<false><<<nblocks(nbox, 256), 256, 0, h->st>>>(
+                P.psi[P.cur], P.src, nullptr, P.dsum, b, nbox, inv_nf, color, omega);
+          ++h->launches;
         }
       LBM_CUDA_TRY(h, cudaGetLastError());
       it += check;
       LBM_CUDA_TRY(h, residual_launch(h));
-      s = residual_read(h, &rel);
+      s = residual_read(h, tol, &rel, &done);
       if (s != LBM_OK) return s;
     }
   }
   if (iters) *iters = it;
   if (rel_res) *rel_res = rel;
-  if (rel > tol) {
+  if (!done) {
     h->err = "Poisson solve did not reach the tolerance within the iteration cap";
     return LBM_ENOCONV;
   }
