@@ -47,6 +47,7 @@ struct StepArgs {
   float eext[3];
   float valence[MAX_SPECIES];
   float nref[MAX_SPECIES];  // reference density of the 16-bit shifted storage
+  uint32_t step;            // time step (seeds the stochastic rounding)
 };
 
 struct PoissonLevel {

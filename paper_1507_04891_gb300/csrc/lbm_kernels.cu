@@ -58,7 +58,14 @@ struct Fmt<LBM_FP32> {
   using T = float;
   static __device__ __forceinline__ float ld(const T* p, float) { return *p; }
   static __device__ __forceinline__ void st(T* p, float v, float) { *p = v; }
+  static __device__ __forceinline__ void st_sr(T* p, float v, float, uint32_t) { *p = v; }
 };
+// 16-bit formats: h = f / (w_p n_ref) - 1.  st() rounds to nearest; st_sr()
+// rounds stochastically: random bits are added below the kept mantissa of
+// the FP32 value and the result is truncated toward zero, so the stored
+// value is unbiased.  The per-step change of a slowly diffusing mode is a
+// fraction of one 16-bit ulp of h; round-to-nearest would return the same
+// value every step and freeze the mode.
 template <>
 struct Fmt<LBM_FP16_SHIFT> {
   using T = __half;
@@ -67,6 +74,12 @@ struct Fmt<LBM_FP16_SHIFT> {
   }
   static __device__ __forceinline__ void st(T* p, float v, float wn) {
     *p = __float2half_rn(v / wn - 1.0f);
+  }
+  static __device__ __forceinline__ void st_sr(T* p, float v, float wn, uint32_t rnd) {
+    const float hv = v / wn - 1.0f;
+    // FP16 keeps 10 of the 23 FP32 mantissa bits: dither the 13 dropped bits
+    const float d = __uint_as_float(__float_as_uint(hv) + (rnd >> 19));
+    *p = __float2half_rz(d);
   }
 };
 template <>
@@ -78,7 +91,31 @@ struct Fmt<LBM_BF16_SHIFT> {
   static __device__ __forceinline__ void st(T* p, float v, float wn) {
     *p = __float2bfloat16_rn(v / wn - 1.0f);
   }
+  static __device__ __forceinline__ void st_sr(T* p, float v, float wn, uint32_t rnd) {
+    const float hv = v / wn - 1.0f;
+    // BF16 is the upper half of FP32: dither the 16 dropped bits, truncate
+    const uint32_t b = __float_as_uint(hv) + (rnd >> 16);
+    __nv_bfloat16_raw raw;
+    raw.x = (unsigned short)(b >> 16);
+    *p = __nv_bfloat16(raw);
+  }
 };
+
+// Counter-based random bits for stochastic rounding: one 32-bit mix of the
+// node index and the step per node, then one LCG step per stored value
+// (only the high bits of the LCG state are used).
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+__device__ __forceinline__ uint32_t lcg_next(uint32_t& r) {
+  r = r * 1664525u + 1013904223u;
+  return r;
+}
 
 struct Nbr {
   // signed offsets to the upstream node along each axis for c = +1 / -1
@@ -275,6 +312,8 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs a) {
   const float vbz = (Jz + 0.5f * zn * Ez) * inv_ntot;
 
   const float om = a.omega_visc, omd = a.omega_drag;
+  uint32_t rnd = 0;
+  if (ST != LBM_FP32) rnd = mix32(i * 0x9E3779B9u ^ mix32(a.step));
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const float inv_n = 1.0f / n[s];
@@ -304,9 +343,9 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs a) {
                         3.0f * fc + 9.0f * fc * uc;
       const float fo = (1.0f - om) * f[s][p] + wn * src;
       moved += fo;
-      Fmt<ST>::st(fout + (int64_t)(s * Q + p) * N + i, fo, WT(p) * nr);
+      Fmt<ST>::st_sr(fout + (int64_t)(s * Q + p) * N + i, fo, WT(p) * nr, lcg_next(rnd));
     }
-    Fmt<ST>::st(fout + (int64_t)(s * Q) * N + i, n[s] - moved, WT(0) * nr);
+    Fmt<ST>::st_sr(fout + (int64_t)(s * Q) * N + i, n[s] - moved, WT(0) * nr, lcg_next(rnd));
   }
 }
 
@@ -614,6 +653,7 @@ cudaError_t launch_stream_collide(lbm_t* h) {
     a.valence[s] = h->valence[s];
     a.nref[s] = h->nref[s];
   }
+  a.step = (uint32_t)h->tstep;
   cudaError_t e;
   switch (h->cfg.storage) {
     case LBM_FP32: e = dispatch_s<LBM_FP32>(a, h->S, h->has_walls, charged, h->st); break;
