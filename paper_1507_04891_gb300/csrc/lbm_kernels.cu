@@ -44,6 +44,10 @@ __host__ __device__ __forceinline__ constexpr int OPP(int p) {
 __host__ __device__ __forceinline__ constexpr float WT(int p) {
   return p == 0 ? (1.0f / 3.0f) : (p <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f));
 }
+// 1 / w_p, exact in FP32
+__host__ __device__ __forceinline__ constexpr float INV_WT(int p) {
+  return p == 0 ? 3.0f : (p <= 6 ? 18.0f : 36.0f);
+}
 constexpr float CS2 = 1.0f / 3.0f;
 
 // ---------------------------------------------------------------------------
@@ -72,11 +76,11 @@ struct Fmt<LBM_FP16_SHIFT> {
   static __device__ __forceinline__ float ld(const T* p, float wn) {
     return wn * (1.0f + __half2float(*p));
   }
-  static __device__ __forceinline__ void st(T* p, float v, float wn) {
-    *p = __float2half_rn(v / wn - 1.0f);
+  static __device__ __forceinline__ void st(T* p, float v, float inv_wn) {
+    *p = __float2half_rn(fmaf(v, inv_wn, -1.0f));
   }
-  static __device__ __forceinline__ void st_sr(T* p, float v, float wn, uint32_t rnd) {
-    const float hv = v / wn - 1.0f;
+  static __device__ __forceinline__ void st_sr(T* p, float v, float inv_wn, uint32_t rnd) {
+    const float hv = fmaf(v, inv_wn, -1.0f);
     // FP16 keeps 10 of the 23 FP32 mantissa bits: dither the 13 dropped bits
     const float d = __uint_as_float(__float_as_uint(hv) + (rnd >> 19));
     *p = __float2half_rz(d);
@@ -88,11 +92,11 @@ struct Fmt<LBM_BF16_SHIFT> {
   static __device__ __forceinline__ float ld(const T* p, float wn) {
     return wn * (1.0f + __bfloat162float(*p));
   }
-  static __device__ __forceinline__ void st(T* p, float v, float wn) {
-    *p = __float2bfloat16_rn(v / wn - 1.0f);
+  static __device__ __forceinline__ void st(T* p, float v, float inv_wn) {
+    *p = __float2bfloat16_rn(fmaf(v, inv_wn, -1.0f));
   }
-  static __device__ __forceinline__ void st_sr(T* p, float v, float wn, uint32_t rnd) {
-    const float hv = v / wn - 1.0f;
+  static __device__ __forceinline__ void st_sr(T* p, float v, float inv_wn, uint32_t rnd) {
+    const float hv = fmaf(v, inv_wn, -1.0f);
     // BF16 is the upper half of FP32: dither the 16 dropped bits, truncate
     const uint32_t b = __float_as_uint(hv) + (rnd >> 16);
     __nv_bfloat16_raw raw;
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs a) {
     const float Fu = Fx * ux + Fy * uy + Fz * uz;
     // p-independent part of omega*phi/(n w) + g/(n w)
     const float base = om * (1.0f - 1.5f * usq) - 3.0f * Fu;
-    const float nr = a.nref[s];
+    const float inr = 1.0f / a.nref[s];
     // moving populations first; the rest population then takes
     // f*_0 = n - sum_{p>0} f*_p, which holds exactly in real arithmetic
     // (phi_perp carries mass n, g_p none) and keeps FP32 rounding of the
@@ -343,9 +347,9 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs a) {
                         3.0f * fc + 9.0f * fc * uc;
       const float fo = (1.0f - om) * f[s][p] + wn * src;
       moved += fo;
-      Fmt<ST>::st_sr(fout + (int64_t)(s * Q + p) * N + i, fo, WT(p) * nr, lcg_next(rnd));
+      Fmt<ST>::st_sr(fout + (int64_t)(s * Q + p) * N + i, fo, INV_WT(p) * inr, lcg_next(rnd));
     }
-    Fmt<ST>::st_sr(fout + (int64_t)(s * Q) * N + i, n[s] - moved, WT(0) * nr, lcg_next(rnd));
+    Fmt<ST>::st_sr(fout + (int64_t)(s * Q) * N + i, n[s] - moved, INV_WT(0) * inr, lcg_next(rnd));
   }
 }
 
@@ -391,7 +395,7 @@ __global__ void k_init(int s, const double* __restrict__ n0,
     } else {
       dst = (int64_t)((int)i + upstream(o, p));
     }
-    Fmt<ST>::st(fout + (int64_t)(s * Q + q) * N + dst, feq, WT(q) * nref);
+    Fmt<ST>::st(fout + (int64_t)(s * Q + q) * N + dst, feq, INV_WT(q) / nref);
   }
 }
 
