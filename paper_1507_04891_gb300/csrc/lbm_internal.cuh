@@ -74,6 +74,11 @@ struct Poisson {
   int64_t nfluid = 0;
   int coarse_sweeps = 16;
   double conv = 0.15;    // measured residual reduction per V-cycle (last solve)
+  // one V-cycle plus the residual, captured as a CUDA graph per starting
+  // potential buffer (the cycle ping-pongs the two buffers)
+  cudaGraphExec_t cyc[2] = {nullptr, nullptr};
+  int cyc_kernels = 0;
+  bool cyc_failed = false;
   int nu1 = 2, nu2 = 2;
 };
 

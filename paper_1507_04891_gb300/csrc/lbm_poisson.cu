@@ -619,8 +619,19 @@ CL make_cl(const PoissonLevel& l) {
 
 }  // namespace
 
+namespace {
+void drop_graphs(Poisson& P) {
+  for (int k = 0; k < 2; ++k) {
+    if (P.cyc[k]) cudaGraphExecDestroy(P.cyc[k]);
+    P.cyc[k] = nullptr;
+  }
+  P.cyc_failed = false;
+}
+}  // namespace
+
 void poisson_free(lbm_t* h) {
   Poisson& P = h->ps;
+  drop_graphs(P);
   for (auto& l : P.lev) {
     cudaFree(l.e);
     cudaFree(l.rhs);
@@ -649,6 +660,7 @@ size_t sub_smem(const Poisson& P, int lc);
 // Builds the grid hierarchy.  solid_host: lattice mask or NULL.
 lbm_status poisson_setup(lbm_t* h, const uint8_t* solid) {
   Poisson& P = h->ps;
+  drop_graphs(P);
   const int nx = h->cfg.nx, ny = h->cfg.ny, nz = h->cfg.nz;
   const int64_t nxy = (int64_t)nx * ny;
   // Trim fully solid bottom and top planes (slit geometry): the Poisson box
@@ -988,6 +1000,56 @@ cudaError_t vcycle(lbm_t* h) {
 
 }  // namespace
 
+namespace {
+
+// One V-cycle followed by the residual of the corrected potential.  Replays
+// a CUDA graph captured on first use (one per starting potential buffer);
+// falls back to direct launches if capture is unavailable on the stream.
+cudaError_t cycle(lbm_t* h) {
+  Poisson& P = h->ps;
+  const int start = P.cur;
+  if (!P.cyc[start] && !P.cyc_failed) {
+    cudaStreamCaptureStatus cs;
+    cudaError_t e = cudaStreamIsCapturing(h->st, &cs);
+    if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone && h->st != nullptr &&
+        cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int64_t before = h->launches;
+      cudaError_t e1 = vcycle(h);
+      cudaError_t e2 = e1 == cudaSuccess ? residual_launch(h) : e1;
+      cudaGraph_t g = nullptr;
+      cudaError_t e3 = cudaStreamEndCapture(h->st, &g);
+      P.cur = start;                 // capture only recorded the work
+      const int nk = (int)(h->launches - before);
+      h->launches = before;
+      cudaGraphExec_t ex = nullptr;
+      if (e2 == cudaSuccess && e3 == cudaSuccess && g &&
+          cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+        P.cyc[start] = ex;
+        P.cyc_kernels = nk;
+      } else {
+        P.cyc_failed = true;
+      }
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    } else {
+      cudaGetLastError();
+      P.cyc_failed = true;
+    }
+  }
+  if (P.cyc[start]) {
+    cudaError_t e = cudaGraphLaunch(P.cyc[start], h->st);
+    if (e != cudaSuccess) return e;
+    P.cur ^= 1;
+    h->launches += P.cyc_kernels;
+    return cudaSuccess;
+  }
+  cudaError_t e = vcycle(h);
+  if (e != cudaSuccess) return e;
+  return residual_launch(h);
+}
+
+}  // namespace
+
 lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
                          double* rel_res) {
   Poisson& P = h->ps;
@@ -1009,10 +1071,7 @@ lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
     }
     while (!done && it < maxit) {
       const int nb = std::min(batch, maxit - it);
-      for (int k = 0; k < nb; ++k) {
-        LBM_CUDA_TRY(h, vcycle(h));
-        LBM_CUDA_TRY(h, residual_launch(h));
-      }
+      for (int k = 0; k < nb; ++k) LBM_CUDA_TRY(h, cycle(h));
       it += nb;
       batch = 1;
       s = residual_read(h, tol, &rel, &done);
