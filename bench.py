@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--schmidt", type=float, default=1.0)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
-    ap.add_argument("--poisson", default="mg", choices=["mg", "sor"])
+    ap.add_argument("--poisson", default="mg", choices=["mg", "sor", "fft"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 

@@ -50,7 +50,13 @@ typedef enum {
 } lbm_status;
 
 enum { LBM_FP32 = 0, LBM_FP16_SHIFT = 1, LBM_BF16_SHIFT = 2 };
-enum { LBM_POISSON_MG = 0, LBM_POISSON_SOR = 1 };
+/* Poisson solvers.  MG: geometric multigrid (any wall geometry).  SOR:
+ * red-black successive over-relaxation (any geometry; slow, a reference).
+ * FFT: 2-D FFT in x, y with tridiagonal solves along z, exact in one pass
+ * up to FP32 rounding; needs power-of-two nx, ny with nx*ny <= 16384 and
+ * every z-plane all fluid or all wall (periodic boxes, slits, stacks of
+ * slits); the source mean is removed per run of fluid planes.            */
+enum { LBM_POISSON_MG = 0, LBM_POISSON_SOR = 1, LBM_POISSON_FFT = 2 };
 
 typedef struct {
   int nx, ny, nz;        /* lattice extents, each >= 1                       */
@@ -60,7 +66,7 @@ typedef struct {
   double bjerrum;        /* l_B of Eq. (Poisson); 0 = neutral, no Poisson    */
   double e_ext[3];       /* applied field, acceleration per unit valence     */
   int storage;           /* LBM_FP32 | LBM_FP16_SHIFT | LBM_BF16_SHIFT       */
-  int poisson;           /* LBM_POISSON_MG | LBM_POISSON_SOR                 */
+  int poisson;           /* LBM_POISSON_MG | LBM_POISSON_SOR | LBM_POISSON_FFT */
   double poisson_tol;    /* ||s - A psi||_2 / ||s||_2 target, e.g. 1e-8      */
   int poisson_maxit;     /* iteration cap (V-cycles or SOR sweeps)           */
   int device;            /* CUDA device ordinal                              */

@@ -198,20 +198,33 @@ def poisson_matrix(fluid):
     return A, idx
 
 
+def fluid_components(fluid):
+    """Connected components of the fluid cells (face neighbours, periodic):
+    (number of components, label per fluid cell in the order of fluid.ravel())."""
+    from scipy.sparse.csgraph import connected_components
+    A, _ = poisson_matrix(fluid)
+    return connected_components(A, directed=False)
+
+
 def poisson_source(rho_e, p: Params, shape):
-    """s = 4 pi l_B (rho_e + w - mean over fluid), the right-hand side of
-    A psi = s.  The mean is removed so that the Neumann/periodic problem is
-    solvable (neutralising background)."""
+    """s = 4 pi l_B (rho_e + w - mean), the right-hand side of A psi = s.
+    The mean is taken over each connected fluid component (a neutralising
+    background per isolated fluid domain), which makes every component's
+    Neumann/periodic problem solvable."""
     fluid = fluid_mask(shape, p)
     tot = rho_e + wall_charge_per_cell(p, shape)
-    mean = tot[fluid].mean()
-    s = np.where(fluid, 4.0 * np.pi * p.bjerrum * (tot - mean), 0.0)
+    ncomp, lab = fluid_components(fluid)
+    vals = tot[fluid]
+    means = np.bincount(lab, weights=vals, minlength=ncomp) / np.bincount(lab, minlength=ncomp)
+    s = np.zeros(shape)
+    s[fluid] = 4.0 * np.pi * p.bjerrum * (vals - means[lab])
     return s
 
 
 class PoissonSolver:
-    """Solves A psi = s on the fluid cells with zero mean (the constant is
-    free for the periodic / Neumann problem).  Sparse LU of the bordered
+    """Solves A psi = s on the fluid cells with zero mean on every connected
+    fluid component (the constant of each is free for the periodic /
+    Neumann problem).  Sparse LU of the bordered
     system [[A, 1], [1^T, 0]] for small lattices, conjugate gradients with a
     1e-13 relative tolerance for large ones; either is far tighter than the
     1e-8 the GPU iterates to."""
@@ -221,21 +234,28 @@ class PoissonSolver:
         self.A, self.idx = poisson_matrix(fluid)
         nf = self.A.shape[0]
         self.nf = nf
+        self.ncomp, self.lab = fluid_components(fluid)
         self.direct = nf <= direct_limit
         if self.direct:
-            one = sp.csr_matrix(np.ones((nf, 1)))
-            B = sp.bmat([[self.A, one], [one.T, None]], format="csc")
+            # one zero-mean constraint per connected component
+            E = sp.csr_matrix((np.ones(nf), (np.arange(nf), self.lab)), shape=(nf, self.ncomp))
+            B = sp.bmat([[self.A, E], [E.T, None]], format="csc")
             self.lu = spla.splu(B)
+
+    def _zero_mean(self, x):
+        cnt = np.bincount(self.lab, minlength=self.ncomp)
+        means = np.bincount(self.lab, weights=x, minlength=self.ncomp) / cnt
+        return x - means[self.lab]
 
     def solve(self, s):
         b = s[self.fluid]
         if self.direct:
-            x = self.lu.solve(np.concatenate([b, [0.0]]))[:-1]
+            x = self.lu.solve(np.concatenate([b, np.zeros(self.ncomp)]))[:self.nf]
         else:
             x, info = spla.cg(self.A, b, rtol=1e-13, atol=0.0, maxiter=20000)
             if info != 0:
                 raise RuntimeError("oracle CG did not converge")
-            x -= x.mean()
+            x = self._zero_mean(x)
         psi = np.zeros(self.fluid.shape)
         psi[self.fluid] = x
         return psi
@@ -445,7 +465,7 @@ def omega_drag_for_schmidt(omega_visc, sc):
 __all__ = [
     "C", "Q", "W", "OPP", "CS2", "Params", "number_density", "species_velocity",
     "barycentric_velocity", "drag_acceleration", "drag_velocity", "wall_face_charge",
-    "wall_charge_per_cell", "poisson_matrix", "poisson_source", "PoissonSolver",
+    "wall_charge_per_cell", "poisson_matrix", "poisson_source", "fluid_components", "PoissonSolver",
     "potential_gradient", "electric_acceleration", "phi_perp", "forcing_term",
     "collide", "stream", "Oracle", "StepInfo",
     "diffusivity", "viscosity", "omega_drag_for_schmidt", "fluid_mask",

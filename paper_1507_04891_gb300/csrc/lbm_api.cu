@@ -136,7 +136,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     g_create_error = "unknown storage code";
     return LBM_EINVAL;
   }
-  if (c.poisson != LBM_POISSON_MG && c.poisson != LBM_POISSON_SOR) {
+  if (c.poisson != LBM_POISSON_MG && c.poisson != LBM_POISSON_SOR && c.poisson != LBM_POISSON_FFT) {
     g_create_error = "unknown Poisson solver code";
     return LBM_EINVAL;
   }
@@ -201,6 +201,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
       cudaMemset(h->ps.psi[1], 0, N * sizeof(int64_t));
       cudaMemset(h->ps.dsum, 0, 4 * sizeof(double));
       s = poisson_setup(h, nullptr);
+      if (s == LBM_OK && c.poisson == LBM_POISSON_FFT) s = spectral_setup(h, nullptr);
     }
   }
   if (s == LBM_OK && cudaDeviceSynchronize() != cudaSuccess) s = LBM_ECUDA;
@@ -226,6 +227,7 @@ void lbm_destroy(lbm_t* h) {
   cudaFree(h->dflag);
   if (h->hred) cudaFreeHost(h->hred);
   poisson_free(h);
+  spectral_free(h);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
@@ -309,6 +311,7 @@ lbm_status lbm_set_walls(lbm_t* h, const uint8_t* solid, const double* sigma) {
     h->ps.nfluid = nfluid;
     s = poisson_setup(h, solid);
     if (s != LBM_OK) return s;
+    if (h->cfg.poisson == LBM_POISSON_FFT && (s = spectral_setup(h, solid)) != LBM_OK) return s;
   }
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   LBM_CUDA_TRY(h, cudaDeviceSynchronize());

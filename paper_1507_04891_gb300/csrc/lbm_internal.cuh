@@ -84,6 +84,10 @@ struct Poisson {
 
 }  // namespace lbm_gb300
 
+namespace lbm_gb300 {
+struct SpectralPlan;
+}
+
 struct lbm {
   lbm_config cfg;
   int S = 0;
@@ -105,6 +109,7 @@ struct lbm {
   int64_t* wsrc = nullptr;  // 4 pi l_B w_i in fixed point (wall charge of each fluid cell)
   int64_t nfluid = 0;
   lbm_gb300::Poisson ps;
+  lbm_gb300::SpectralPlan* spec = nullptr;  // spectral Poisson plan (LBM_POISSON_FFT)
   bool psi_valid = false;
   double* dred = nullptr;   // diagnostics reduction buffer (device)
   double* hred = nullptr;   // pinned mirror
@@ -145,6 +150,12 @@ void poisson_free(lbm_t* h);
 // Solves A psi = src - mean starting from the current psi buffer.
 lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
                          double* rel_res);
+
+// ---- lbm_spectral.cu ----
+lbm_status spectral_setup(lbm_t* h, const uint8_t* solid_host);
+void spectral_free(lbm_t* h);
+lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters,
+                          double* rel_res);
 
 }  // namespace lbm_gb300
 

@@ -336,18 +336,25 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs a) {
     // f*_0 = n - sum_{p>0} f*_p, which holds exactly in real arithmetic
     // (phi_perp carries mass n, g_p none) and keeps FP32 rounding of the
     // weights from drifting the species mass.
+    // Directions come in opposite pairs (p, p+1), c_{p+1} = -c_p: a = u^a.c,
+    // F.c and u.c flip sign, so each pair shares the even part
+    // base + 4.5 om a^2 + 9 (F.c)(u.c) and takes +/- the odd part
+    // 3 (om a + F.c).
+    const float omm = 1.0f - om;
     float moved = 0.f;
 #pragma unroll
-    for (int p = 1; p < Q; ++p) {
+    for (int p = 1; p < Q; p += 2) {
       const float av = CX(p) * usx + CY(p) * usy + CZ(p) * usz;
       const float fc = CX(p) * Fx + CY(p) * Fy + CZ(p) * Fz;
       const float uc = CX(p) * ux + CY(p) * uy + CZ(p) * uz;
-      const float wn = WT(p) * n[s];
-      const float src = base + om * (3.0f * av + 4.5f * av * av) +
-                        3.0f * fc + 9.0f * fc * uc;
-      const float fo = (1.0f - om) * f[s][p] + wn * src;
-      moved += fo;
-      Fmt<ST>::st_sr(fout + (int64_t)(s * Q + p) * N + i, fo, INV_WT(p) * inr, lcg_next(rnd));
+      const float wn = WT(p) * n[s];  // same weight for p and p+1
+      const float even = wn * (base + 4.5f * om * av * av + 9.0f * fc * uc);
+      const float odd = wn * 3.0f * (om * av + fc);
+      const float fa = omm * f[s][p] + (even + odd);
+      const float fb = omm * f[s][p + 1] + (even - odd);
+      moved += fa + fb;
+      Fmt<ST>::st_sr(fout + (int64_t)(s * Q + p) * N + i, fa, INV_WT(p) * inr, lcg_next(rnd));
+      Fmt<ST>::st_sr(fout + (int64_t)(s * Q + p + 1) * N + i, fb, INV_WT(p) * inr, lcg_next(rnd));
     }
     Fmt<ST>::st_sr(fout + (int64_t)(s * Q) * N + i, n[s] - moved, INV_WT(0) * inr, lcg_next(rnd));
   }

@@ -1052,6 +1052,7 @@ cudaError_t cycle(lbm_t* h) {
 
 lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
                          double* rel_res) {
+  if (h->cfg.poisson == LBM_POISSON_FFT) return spectral_solve(h, tol, maxit, iters, rel_res);
   Poisson& P = h->ps;
   double rel = 0.0, rel0 = 0.0;
   bool done = false;

@@ -1,0 +1,586 @@
+// Spectral Poisson solver for lattices whose every z-plane is either all
+// fluid or all wall (periodic boxes, slits, stacks of slits).  It solves the
+// same finite-volume problem as the multigrid (Eq. Poisson with the
+// surface-charge condition):
+//   A psi = s - <s>_run,   (A psi)_i = sum_open faces (psi_i - psi_j),
+// where <s>_run is the mean of the source over each run of consecutive
+// fluid planes (each run is a separate connected fluid domain).
+//
+// The x and y directions are periodic and uniform, so a 2-D discrete
+// Fourier transform diagonalises them: for the mode (kx, ky) the operator
+// becomes lambda(kx, ky) + (1-D operator along z), and the z operator of a
+// run is tridiagonal (walls at both ends: one open face there) or cyclic
+// (a run that is the whole periodic z axis).  One application solves the
+// problem to FP32 accuracy; it is used for defect correction on the exact
+// fixed-point residual, so two applications usually reach 1e-8.
+//
+// Kernels per application: forward FFT of the residual per plane (shared
+// memory, radix 2), one tridiagonal solve per mode and run, inverse FFT per
+// plane fused with the update psi += round(e).
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+namespace lbm_gb300 {
+namespace {
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ unsigned brev(unsigned v, int bits) {
+  return __brev(v) >> (32 - bits);
+}
+
+// In-place radix-2 FFTs of `count` rows of length n = 2^lg stored with
+// element stride `es` and row stride `rs` in shared memory.  Input in
+// bit-reversed order.  tw[k] = exp(-2 pi i k / n) (k < n/2); sign -1 forward,
+// +1 inverse (conjugate twiddles).
+__device__ void fft_rows(float2* a, int n, int lg, int count, int es, int rs,
+                         const float2* tw, float sign) {
+  const int half = n >> 1;
+  for (int s = 1; s <= lg; ++s) {
+    const int m = 1 << s, mh = m >> 1;
+    const int tstep = n >> s;  // twiddle index step
+    for (int t = threadIdx.x; t < count * half; t += blockDim.x) {
+      const int row = t / half;
+      const int b = t - row * half;          // butterfly within the row
+      const int grp = b / mh, j = b - grp * mh;
+      const int i0 = grp * m + j, i1 = i0 + mh;
+      float2 w = tw[j * tstep];
+      w.y *= -sign;  // table holds exp(-i..); forward keeps it, inverse conjugates
+      float2* p0 = a + row * rs + i0 * es;
+      float2* p1 = a + row * rs + i1 * es;
+      const float2 u = *p0;
+      const float2 v = cmul(w, *p1);
+      *p0 = make_float2(u.x + v.x, u.y + v.y);
+      *p1 = make_float2(u.x - v.x, u.y - v.y);
+    }
+    __syncthreads();
+  }
+}
+
+struct SpecArgs {
+  int nx, ny, nz, lgx, lgy;
+  const float2* twx;
+  const float2* twy;
+};
+
+// Forward 2-D FFT of the FP32 residual of each fluid plane:
+// rhat[z][ky][kx] = sum_x,y r[z][y][x] exp(-2 pi i (kx x/nx + ky y/ny)).
+__global__ void __launch_bounds__(512) k_fft_fwd(const float* __restrict__ r,
+                                                 float2* __restrict__ rhat,
+                                                 const int* __restrict__ planes,
+                                                 SpecArgs a) {
+  extern __shared__ float2 buf[];
+  const int z = planes[blockIdx.x];
+  const int nxy = a.nx * a.ny;
+  const float* src = r + (int64_t)z * nxy;
+  // load with bit-reversed x and y (both passes then take natural output)
+  for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
+    const int y = k / a.nx, x = k - y * a.nx;
+    const int xr = a.lgx ? (int)brev(x, a.lgx) : 0, yr = a.lgy ? (int)brev(y, a.lgy) : 0;
+    buf[yr * a.nx + xr] = make_float2(src[k], 0.f);
+  }
+  __syncthreads();
+  fft_rows(buf, a.nx, a.lgx, a.ny, 1, a.nx, a.twx, -1.f);   // along x
+  fft_rows(buf, a.ny, a.lgy, a.nx, a.nx, 1, a.twy, -1.f);   // along y
+  float2* dst = rhat + (int64_t)z * nxy;
+  for (int k = threadIdx.x; k < nxy; k += blockDim.x) dst[k] = buf[k];
+}
+
+// Inverse 2-D FFT of the correction of each fluid plane, scaled by
+// 1/(nx ny), and the update psi_out = psi_in + round(e).
+__global__ void __launch_bounds__(512) k_fft_inv_apply(const float2* __restrict__ ehat,
+                                                       const int* __restrict__ planes,
+                                                       SpecArgs a,
+                                                       const int64_t* __restrict__ psi_in,
+                                                       int64_t* __restrict__ psi_out) {
+  extern __shared__ float2 buf[];
+  const int z = planes[blockIdx.x];
+  const int nxy = a.nx * a.ny;
+  const float2* src = ehat + (int64_t)z * nxy;
+  for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
+    const int y = k / a.nx, x = k - y * a.nx;
+    const int xr = a.lgx ? (int)brev(x, a.lgx) : 0, yr = a.lgy ? (int)brev(y, a.lgy) : 0;
+    buf[yr * a.nx + xr] = src[k];
+  }
+  __syncthreads();
+  fft_rows(buf, a.nx, a.lgx, a.ny, 1, a.nx, a.twx, 1.f);
+  fft_rows(buf, a.ny, a.lgy, a.nx, a.nx, 1, a.twy, 1.f);
+  const float scale = 1.0f / (float)nxy;
+  const int64_t base = (int64_t)z * nxy;
+  for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
+    const float e = buf[k].x * scale;
+    psi_out[base + k] = psi_in[base + k] + llrintf(e * PSI_SCALE_F);
+  }
+}
+
+// Tridiagonal solve along z for one Fourier mode (thread) of one run
+// (blockIdx.y): -x_{z-1} + (lambda + d_z) x_z - x_{z+1} = rhat_z, with
+// d_z = 2 inside, 1 at a wall end; a cyclic run closes the chain
+// (Sherman-Morrison).  The mode (0,0) is singular: its run mean is free, so
+// x at the first plane of the run is pinned to 0 and the remaining planes
+// are solved (the pinned plane's equation is redundant once the run sum of
+// the right-hand side is zero, which the run-mean removal guarantees).
+// Overwrites rhat with the solution; cp holds the elimination factors.
+struct Run {
+  int z0, len, cyclic;
+};
+
+__global__ void __launch_bounds__(256) k_zsolve(float2* __restrict__ x,
+                                                float* __restrict__ cp,
+                                                float2* __restrict__ w2,
+                                                const Run* __restrict__ runs,
+                                                SpecArgs a) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nxy = a.nx * a.ny;
+  if (m >= nxy) return;
+  const Run R = runs[blockIdx.y];
+  const int ky = m / a.nx, kx = m - ky * a.nx;
+  const float lam = (2.f - 2.f * cospif(2.f * kx / a.nx)) + (2.f - 2.f * cospif(2.f * ky / a.ny));
+  const int L = R.len;
+  auto at = [&](int k) -> int64_t {  // plane k of the run (wraps the lattice)
+    int z = R.z0 + k;
+    if (z >= a.nz) z -= a.nz;
+    return (int64_t)z * nxy + m;
+  };
+  const bool singular = (kx == 0 && ky == 0);
+  if (!R.cyclic) {
+    // diagonal: lambda + 2 inside, lambda + 1 at the ends (lambda alone if L == 1)
+    auto diag = [&](int k) -> float {
+      const int open = (k > 0) + (k < L - 1);
+      return lam + (float)open;
+    };
+    int k0 = 0;
+    if (singular) {
+      x[at(0)] = make_float2(0.f, 0.f);
+      k0 = 1;
+      if (L == 1) return;
+    }
+    // forward elimination
+    float c = 0.f;
+    float2 d = make_float2(0.f, 0.f);
+    for (int k = k0; k < L; ++k) {
+      const float den = diag(k) + (k > k0 ? c : 0.f);
+      const float inv = 1.0f / den;
+      const float2 rk = x[at(k)];
+      d = make_float2((rk.x + (k > k0 ? d.x : 0.f)) * inv, (rk.y + (k > k0 ? d.y : 0.f)) * inv);
+      c = -inv;
+      x[at(k)] = d;
+      cp[at(k)] = c;
+    }
+    // back substitution
+    float2 nxt = x[at(L - 1)];
+    for (int k = L - 2; k >= k0; --k) {
+      const float ck = cp[at(k)];
+      const float2 dk = x[at(k)];
+      nxt = make_float2(dk.x - ck * nxt.x, dk.y - ck * nxt.y);
+      x[at(k)] = nxt;
+    }
+    return;
+  }
+  // cyclic run of length L >= 3 (periodic z axis)
+  if (singular) {
+    // pin x_0 = 0; planes 1..L-1 form a Dirichlet chain (diagonal 2)
+    x[at(0)] = make_float2(0.f, 0.f);
+    float c = 0.f;
+    float2 d = make_float2(0.f, 0.f);
+    for (int k = 1; k < L; ++k) {
+      const float den = 2.f + (k > 1 ? c : 0.f);
+      const float inv = 1.0f / den;
+      const float2 rk = x[at(k)];
+      d = make_float2((rk.x + (k > 1 ? d.x : 0.f)) * inv, (rk.y + (k > 1 ? d.y : 0.f)) * inv);
+      c = -inv;
+      x[at(k)] = d;
+      cp[at(k)] = c;
+    }
+    float2 nxt = x[at(L - 1)];
+    for (int k = L - 2; k >= 1; --k) {
+      const float ck = cp[at(k)];
+      const float2 dk = x[at(k)];
+      nxt = make_float2(dk.x - ck * nxt.x, dk.y - ck * nxt.y);
+      x[at(k)] = nxt;
+    }
+    return;
+  }
+  // Sherman-Morrison: A = T + u v^T with corner entries -1.
+  // gamma = -b; T has b - gamma at the first and b - 1/gamma at the last plane.
+  const float b = lam + 2.f;
+  const float gam = -b;
+  auto tdiag = [&](int k) -> float {
+    if (k == 0) return b - gam;
+    if (k == L - 1) return b - 1.0f / gam;
+    return b;
+  };
+  // solve T y = r (complex, in x) and T q = u (real, in w2.x), u = (gam, 0.., 0, -1)
+  float c = 0.f;
+  float2 d = make_float2(0.f, 0.f);
+  float dq = 0.f;
+  for (int k = 0; k < L; ++k) {
+    const float den = tdiag(k) + (k > 0 ? c : 0.f);
+    const float inv = 1.0f / den;
+    const float2 rk = x[at(k)];
+    const float uk = (k == 0) ? gam : (k == L - 1 ? -1.f : 0.f);
+    d = make_float2((rk.x + (k > 0 ? d.x : 0.f)) * inv, (rk.y + (k > 0 ? d.y : 0.f)) * inv);
+    dq = (uk + (k > 0 ? dq : 0.f)) * inv;
+    c = -inv;
+    x[at(k)] = d;
+    w2[at(k)] = make_float2(dq, 0.f);
+    cp[at(k)] = c;
+  }
+  float2 ny_ = x[at(L - 1)];
+  float nq = w2[at(L - 1)].x;
+  for (int k = L - 2; k >= 0; --k) {
+    const float ck = cp[at(k)];
+    const float2 dk = x[at(k)];
+    ny_ = make_float2(dk.x - ck * ny_.x, dk.y - ck * ny_.y);
+    nq = w2[at(k)].x - ck * nq;
+    x[at(k)] = ny_;
+    w2[at(k)] = make_float2(nq, 0.f);
+  }
+  // v = (1, 0, .., 0, -1/gam):  x = y - q (v.y) / (1 + v.q)
+  const float2 y0 = x[at(0)], yl = x[at(L - 1)];
+  const float q0 = w2[at(0)].x, ql = w2[at(L - 1)].x;
+  const float den = 1.f + q0 - ql / gam;
+  const float2 f = make_float2((y0.x - yl.x / gam) / den, (y0.y - yl.y / gam) / den);
+  for (int k = 0; k < L; ++k) {
+    const float qk = w2[at(k)].x;
+    const float2 yk = x[at(k)];
+    x[at(k)] = make_float2(yk.x - qk * f.x, yk.y - qk * f.y);
+  }
+}
+
+// Per-plane sums of the fixed-point source (one CTA per plane, exact).
+__global__ void __launch_bounds__(256) k_plane_sums(const int64_t* __restrict__ src,
+                                                    long long* __restrict__ psum,
+                                                    int nxy) {
+  __shared__ long long red[8];
+  const int64_t base = (int64_t)blockIdx.x * nxy;
+  long long v = 0;
+  for (int k = threadIdx.x; k < nxy; k += blockDim.x) v += src[base + k];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    psum[blockIdx.x] = t;
+  }
+}
+
+// Mean of the source over each run, broadcast to its planes (wall planes: 0).
+__global__ void k_run_means(const long long* __restrict__ psum, const Run* __restrict__ runs,
+                            int nruns, long long* __restrict__ mean_z, int nz, int nxy) {
+  for (int z = threadIdx.x; z < nz; z += blockDim.x) mean_z[z] = 0;
+  __syncthreads();
+  for (int r = threadIdx.x; r < nruns; r += blockDim.x) {
+    const Run R = runs[r];
+    double tot = 0.0;
+    for (int k = 0; k < R.len; ++k) {
+      int z = R.z0 + k;
+      if (z >= nz) z -= nz;
+      tot += (double)psum[z];
+    }
+    const long long mean = llrint(tot / ((double)R.len * nxy));
+    for (int k = 0; k < R.len; ++k) {
+      int z = R.z0 + k;
+      if (z >= nz) z -= nz;
+      mean_z[z] = mean;
+    }
+  }
+}
+
+// Residual with per-plane means: r = s - mean_z - A psi (exact), norms into
+// dsum[1], dsum[2].  Wall planes contribute nothing.
+__global__ void __launch_bounds__(256) k_res_planes(
+    const int64_t* __restrict__ psi, const int64_t* __restrict__ src,
+    const long long* __restrict__ mean_z, const unsigned char* __restrict__ plane_fluid,
+    float* __restrict__ r, double* dsum, int nx, int ny, int nz) {
+  __shared__ float red_r[8], red_s[8];
+  const int nxy = nx * ny;
+  const int64_t N = (int64_t)nxy * nz;
+  float rr = 0.f, ss = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int z = (int)(i / nxy);
+    const int k = (int)(i - (int64_t)z * nxy);
+    if (!plane_fluid[z]) {
+      r[i] = 0.f;
+      continue;
+    }
+    const int y = k / nx, x = k - y * nx;
+    const int64_t pc = psi[i];
+    int64_t Ap = 0;
+    if (nx > 1) {
+      Ap += pc - psi[i + (x == nx - 1 ? -(nx - 1) : 1)];
+      Ap += pc - psi[i + (x == 0 ? nx - 1 : -1)];
+    }
+    if (ny > 1) {
+      Ap += pc - psi[i + (y == ny - 1 ? -(int64_t)(ny - 1) * nx : nx)];
+      Ap += pc - psi[i + (y == 0 ? (int64_t)(ny - 1) * nx : -nx)];
+    }
+    if (nz > 1) {
+      const int zp = (z == nz - 1) ? 0 : z + 1, zm = (z == 0) ? nz - 1 : z - 1;
+      if (plane_fluid[zp] && zp != z) Ap += pc - psi[(int64_t)zp * nxy + k];
+      if (plane_fluid[zm] && zm != z) Ap += pc - psi[(int64_t)zm * nxy + k];
+    }
+    const int64_t sfx = src[i] - mean_z[z];
+    const float rf = (float)(sfx - Ap);
+    r[i] = rf * PSI_INV_SCALE_F;
+    rr += rf * rf;
+    const float sf = (float)sfx;
+    ss += sf * sf;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    rr += __shfl_down_sync(0xffffffffu, rr, off);
+    ss += __shfl_down_sync(0xffffffffu, ss, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_r[threadIdx.x >> 5] = rr;
+    red_s[threadIdx.x >> 5] = ss;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0, ts = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tr += (double)red_r[w];
+      ts += (double)red_s[w];
+    }
+    atomicAdd(dsum + 1, tr);
+    atomicAdd(dsum + 2, ts);
+  }
+}
+
+int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return (1 << l) == n ? l : -1;
+}
+
+}  // namespace
+
+struct SpectralPlan {
+  int nx, ny, nz, lgx, lgy;
+  int nplanes = 0, nruns = 0;
+  int* planes = nullptr;           // indices of fluid planes
+  Run* runs = nullptr;
+  unsigned char* plane_fluid = nullptr;
+  float2* twx = nullptr;
+  float2* twy = nullptr;
+  float2* spec = nullptr;          // N complex
+  float* cp = nullptr;             // N
+  float2* w2 = nullptr;            // N complex (cyclic runs only)
+  float* r = nullptr;              // N
+  long long* psum = nullptr;       // nz
+  long long* mean_z = nullptr;     // nz
+  size_t smem = 0;
+};
+
+void spectral_free(lbm_t* h) {
+  SpectralPlan* s = h->spec;
+  if (!s) return;
+  cudaFree(s->planes);
+  cudaFree(s->runs);
+  cudaFree(s->plane_fluid);
+  cudaFree(s->twx);
+  cudaFree(s->twy);
+  cudaFree(s->spec);
+  cudaFree(s->cp);
+  cudaFree(s->w2);
+  cudaFree(s->r);
+  cudaFree(s->psum);
+  cudaFree(s->mean_z);
+  delete s;
+  h->spec = nullptr;
+}
+
+lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
+  spectral_free(h);
+  const int nx = h->cfg.nx, ny = h->cfg.ny, nz = h->cfg.nz;
+  const int lgx = ilog2(nx), lgy = ilog2(ny);
+  if (lgx < 0 || lgy < 0 || (int64_t)nx * ny > 16384) {
+    h->err = "spectral Poisson solver needs power-of-two nx, ny with nx*ny <= 16384";
+    return LBM_EINVAL;
+  }
+  const int64_t nxy = (int64_t)nx * ny;
+  std::vector<unsigned char> pf(nz, 1);
+  if (solid) {
+    for (int z = 0; z < nz; ++z) {
+      int64_t cnt = 0;
+      for (int64_t k = 0; k < nxy; ++k) cnt += solid[(int64_t)z * nxy + k] ? 1 : 0;
+      if (cnt != 0 && cnt != nxy) {
+        h->err = "spectral Poisson solver needs every z-plane all fluid or all wall";
+        return LBM_EINVAL;
+      }
+      pf[z] = cnt == 0;
+    }
+  }
+  std::vector<int> planes;
+  for (int z = 0; z < nz; ++z)
+    if (pf[z]) planes.push_back(z);
+  if (planes.empty()) {
+    h->err = "no fluid plane";
+    return LBM_EINVAL;
+  }
+  std::vector<Run> runs;
+  if ((int)planes.size() == nz) {
+    Run R;
+    R.z0 = 0;
+    R.len = nz;
+    R.cyclic = nz >= 3 ? 1 : 0;
+    runs.push_back(R);
+  } else {
+    // start the scan after a wall plane so that runs never straddle it
+    int zs = 0;
+    while (pf[zs]) ++zs;
+    for (int k = 1; k <= nz; ++k) {
+      const int z = (zs + k) % nz;
+      if (!pf[z]) continue;
+      const int prev = (z - 1 + nz) % nz;
+      if (!pf[prev]) {
+        Run R;
+        R.z0 = z;
+        R.len = 0;
+        R.cyclic = 0;
+        runs.push_back(R);
+      }
+      runs.back().len++;
+    }
+  }
+  SpectralPlan* s = new SpectralPlan();
+  h->spec = s;
+  s->nx = nx;
+  s->ny = ny;
+  s->nz = nz;
+  s->lgx = lgx;
+  s->lgy = lgy;
+  s->nplanes = (int)planes.size();
+  s->nruns = (int)runs.size();
+  const int64_t N = h->N;
+  auto al = [&](void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  };
+  bool ok = al((void**)&s->planes, planes.size() * sizeof(int)) &&
+            al((void**)&s->runs, runs.size() * sizeof(Run)) &&
+            al((void**)&s->plane_fluid, nz) && al((void**)&s->twx, std::max(1, nx / 2) * sizeof(float2)) &&
+            al((void**)&s->twy, std::max(1, ny / 2) * sizeof(float2)) &&
+            al((void**)&s->spec, N * sizeof(float2)) && al((void**)&s->cp, N * sizeof(float)) &&
+            al((void**)&s->r, N * sizeof(float)) && al((void**)&s->psum, nz * sizeof(long long)) &&
+            al((void**)&s->mean_z, nz * sizeof(long long));
+  if (ok && runs.size() == 1 && runs[0].cyclic) ok = al((void**)&s->w2, N * sizeof(float2));
+  if (!ok) {
+    spectral_free(h);
+    h->err = "spectral Poisson allocation failed";
+    return LBM_ENOMEM;
+  }
+  auto twiddles = [](int n) {
+    std::vector<float2> t(std::max(1, n / 2));
+    for (int k = 0; k < n / 2; ++k) {
+      const double ang = -2.0 * 3.14159265358979323846 * k / n;
+      t[k] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+    return t;
+  };
+  auto tx = twiddles(nx), ty = twiddles(ny);
+  LBM_CUDA_TRY(h, cudaMemcpy(s->planes, planes.data(), planes.size() * sizeof(int), cudaMemcpyHostToDevice));
+  LBM_CUDA_TRY(h, cudaMemcpy(s->runs, runs.data(), runs.size() * sizeof(Run), cudaMemcpyHostToDevice));
+  LBM_CUDA_TRY(h, cudaMemcpy(s->plane_fluid, pf.data(), nz, cudaMemcpyHostToDevice));
+  LBM_CUDA_TRY(h, cudaMemcpy(s->twx, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  LBM_CUDA_TRY(h, cudaMemcpy(s->twy, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  s->smem = (size_t)nxy * sizeof(float2);
+  if (s->smem > 48 * 1024) {
+    LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem));
+    LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_inv_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem));
+  }
+  return LBM_OK;
+}
+
+namespace {
+
+SpecArgs args_of(const SpectralPlan* s) {
+  SpecArgs a;
+  a.nx = s->nx;
+  a.ny = s->ny;
+  a.nz = s->nz;
+  a.lgx = s->lgx;
+  a.lgy = s->lgy;
+  a.twx = s->twx;
+  a.twy = s->twy;
+  return a;
+}
+
+cudaError_t spec_residual(lbm_t* h) {
+  SpectralPlan* s = h->spec;
+  Poisson& P = h->ps;
+  cudaError_t e = cudaMemsetAsync(P.dsum + 1, 0, 2 * sizeof(double), h->st);
+  if (e != cudaSuccess) return e;
+  const unsigned nb = (unsigned)std::min<int64_t>(nblk(h->N, 256), h->grid_cap);
+  k_res_planes<<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, s->mean_z, s->plane_fluid, s->r,
+                                      P.dsum, s->nx, s->ny, s->nz);
+  ++h->launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+}
+
+cudaError_t spec_apply(lbm_t* h) {
+  SpectralPlan* s = h->spec;
+  Poisson& P = h->ps;
+  const SpecArgs a = args_of(s);
+  const int threads = (int)std::min<int64_t>(512, std::max<int64_t>(32, (int64_t)s->nx * s->ny / 2));
+  k_fft_fwd<<<s->nplanes, threads, s->smem, h->st>>>(s->r, s->spec, s->planes, a);
+  dim3 g(nblk((int64_t)s->nx * s->ny, 256), s->nruns);
+  k_zsolve<<<g, 256, 0, h->st>>>(s->spec, s->cp, s->w2, s->runs, a);
+  k_fft_inv_apply<<<s->nplanes, threads, s->smem, h->st>>>(s->spec, s->planes, a, P.psi[P.cur],
+                                                          P.psi[P.cur ^ 1]);
+  h->launches += 3;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) P.cur ^= 1;
+  return e;
+}
+
+}  // namespace
+
+lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* rel_res) {
+  SpectralPlan* s = h->spec;
+  Poisson& P = h->ps;
+  k_plane_sums<<<s->nz, 256, 0, h->st>>>(P.src, s->psum, s->nx * s->ny);
+  k_run_means<<<1, 256, 0, h->st>>>(s->psum, s->runs, s->nruns, s->mean_z, s->nz, s->nx * s->ny);
+  h->launches += 2;
+  LBM_CUDA_TRY(h, cudaGetLastError());
+  LBM_CUDA_TRY(h, spec_residual(h));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  double rn = sqrt(P.hsum[1]), sn = sqrt(P.hsum[2]);
+  auto conv = [&]() { return rn <= tol * sn || rn <= 2.0 * sqrt((double)h->nfluid); };
+  int it = 0;
+  while (!conv() && it < maxit) {
+    LBM_CUDA_TRY(h, spec_apply(h));
+    LBM_CUDA_TRY(h, spec_residual(h));
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    rn = sqrt(P.hsum[1]);
+    sn = sqrt(P.hsum[2]);
+    if (!isfinite(rn) || !isfinite(sn)) {
+      h->err = "Poisson residual is not finite";
+      return LBM_EUNSTABLE;
+    }
+    ++it;
+  }
+  if (iters) *iters = it;
+  if (rel_res) *rel_res = sn > 0.0 ? rn / sn : 0.0;
+  if (!conv()) {
+    h->err = "Poisson solve did not reach the tolerance within the iteration cap";
+    return LBM_ENOCONV;
+  }
+  return LBM_OK;
+}
+
+}  // namespace lbm_gb300

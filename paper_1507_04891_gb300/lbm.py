@@ -20,7 +20,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOCONV, LBM_EUNSTABLE, LBM_ETIME
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
                 4: "LBM_ENOCONV", 5: "LBM_EUNSTABLE", 6: "LBM_ETIMEOUT"}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
-POISSON = {"mg": 0, "sor": 1}
+POISSON = {"mg": 0, "sor": 1, "fft": 2}
 
 # every symbol include/lbm.h declares
 EXPORTED = [

@@ -542,3 +542,39 @@ def test_slit_equilibrium_is_poisson_boltzmann(schmidt, steps):
         dev = np.log(n[a, 1:-1, 0, 0]) + z * psi
         assert np.ptp(dev) < 0.03 * np.ptp(psi)
     assert info.poisson_rel_residual < 1e-12
+
+
+def test_poisson_components_are_independent():
+    """Two slits stacked along z (separated by wall planes) are independent
+    domains: the solve on the stack equals the exact quadratic of each slit
+    (per-component neutralising background and zero mean)."""
+    lB = 0.7
+    W1, W2, s1, s2 = 5, 8, -0.011, -0.004
+    nz = W1 + W2 + 2
+    shape = (nz, 2, 3)
+    solid = np.zeros(shape, bool)
+    solid[0] = True
+    solid[W1 + 1] = True
+    sig = np.zeros(shape)
+    sig[0] = s1
+    sig[W1 + 1] = s2
+    # uniform charge in each slit; each slit sees its two walls
+    rho = np.zeros(shape)
+    rho[1:W1 + 1] = 0.002
+    rho[W1 + 2:] = -0.001
+    p = O.Params(1.0, 1.0, [1.0], [1.0], bjerrum=lB, solid=solid, sigma=sig)
+    so = O.PoissonSolver(~solid)
+    assert so.ncomp == 2
+    psi = so.solve(O.poisson_source(rho, p, shape))
+    for lo, W, sa, sb, r0 in [(1, W1, s1, s2, 0.002), (W1 + 2, W2, s2, s1, -0.001)]:
+        # net charge density with the component mean removed: each wall plane
+        # has fluid on both sides and hands half its charge to each
+        q = np.full(W, r0)
+        q[0] += 0.5 * sa
+        q[-1] += 0.5 * sb
+        q -= q.mean()
+        # exact 1-D finite-volume solve (Neumann chain), zero mean
+        A = np.diag(np.r_[1, np.full(W - 2, 2), 1].astype(float)) - np.eye(W, k=1) - np.eye(W, k=-1)
+        x = np.linalg.lstsq(A, 4 * math.pi * lB * q, rcond=None)[0]
+        x -= x.mean()
+        np.testing.assert_allclose(psi[lo:lo + W, 1, 2], x, atol=1e-12)
