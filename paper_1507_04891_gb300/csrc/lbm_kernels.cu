@@ -411,44 +411,48 @@ __global__ void k_init(int s, const double* __restrict__ n0,
 // rho_e = sum_alpha z^alpha n^alpha(r, t) from the pulled populations of the
 // charged species; block sums of s over fluid nodes go to dsum[0] (FP64).
 // ---------------------------------------------------------------------------
-template <bool WALLS, int ST>
+template <int S, bool WALLS, int ST>
 __global__ void __launch_bounds__(256) k_charge(
     const void* fin_v, const uint32_t* links, const int64_t* wsrc, int64_t* src,
-    long long* part, int nx, int ny, int nz, int64_t N, int S, float4 val,
-    float4 nref, float fourpi_lb) {
+    long long* part, int nx, int ny, int nz, int64_t N, float4 val, float4 nref,
+    float fourpi_lb) {
   using T = typename Fmt<ST>::T;
   const T* fin = static_cast<const T*>(fin_v);
   const float vz[4] = {val.x, val.y, val.z, val.w};
   const float nr[4] = {nref.x, nref.y, nref.z, nref.w};
   long long acc = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)N;
-       i += gridDim.x * blockDim.x) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < (uint32_t)N) {
     uint32_t lk = 0;
+    bool fluid = true;
     if (WALLS) {
       lk = links[i];
-      if (lk & LINK_SOLID) {
-        src[i] = 0;
-        continue;
-      }
+      fluid = !(lk & LINK_SOLID);
     }
-    int x, y, z;
-    site_xyz(i, nx, ny, x, y, z);
-    const Nbr o = neighbours(x, y, z, nx, ny, nz);
-    float rho = 0.f;
-    for (int s = 0; s < S; ++s) {
-      if (vz[s] == 0.f) continue;
-      float m0 = 0.f;
+    long long sv = 0;
+    if (fluid) {
+      int x, y, z;
+      site_xyz(i, nx, ny, x, y, z);
+      const Nbr o = neighbours(x, y, z, nx, ny, nz);
+      float rho = 0.f;
+      // all pulls of the charged species are independent: unrolled so that
+      // they are in flight together
 #pragma unroll
-      for (int p = 0; p < Q; ++p)
-        m0 += pull<ST, WALLS>(fin, N, s, p, i, upstream(o, p), lk, nr[s]);
-      rho += vz[s] * m0;
+      for (int s = 0; s < S; ++s) {
+        if (vz[s] == 0.f) continue;
+        float m0 = 0.f;
+#pragma unroll
+        for (int p = 0; p < Q; ++p)
+          m0 += pull<ST, WALLS>(fin, N, s, p, i, upstream(o, p), lk, nr[s]);
+        rho += vz[s] * m0;
+      }
+      // exact conversion: a float times a power of two, to a 64-bit integer;
+      // the wall charge is already in fixed point
+      sv = (long long)(fourpi_lb * rho * PSI_SCALE_F);
+      if (wsrc) sv += wsrc[i];
     }
-    // exact conversion: a float times a power of two, to a 64-bit integer;
-    // the wall charge is already in fixed point
-    long long sv = (long long)(fourpi_lb * rho * PSI_SCALE_F);
-    if (wsrc) sv += wsrc[i];
     src[i] = sv;
-    acc += sv;
+    acc = sv;
   }
   block_partial(acc, part);
 }
@@ -713,10 +717,18 @@ cudaError_t launch_charge(lbm_t* h) {
   // in flight); per-CTA partial sums instead of same-address atomics
   const int nb = (int)nblocks(h->N, 256);
   const float k = (float)(4.0 * 3.14159265358979323846 * h->cfg.bjerrum);
-  LBM_DISPATCH_WS(h, (k_charge<W_, ST_><<<nb, 256, 0, h->st>>>(
-                         h->f[h->cur], h->links, h->wsrc, h->ps.src,
-                         h->ps.part, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,
-                         h->S, as_f4(h->valence), as_f4(h->nref), k)));
+#define LBM_CHARGE_S(SS)                                                        \
+  LBM_DISPATCH_WS(h, (k_charge<SS, W_, ST_><<<nb, 256, 0, h->st>>>(              \
+                         h->f[h->cur], h->links, h->wsrc, h->ps.src, h->ps.part, \
+                         h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,                  \
+                         as_f4(h->valence), as_f4(h->nref), k)))
+  switch (h->S) {
+    case 1: LBM_CHARGE_S(1); break;
+    case 2: LBM_CHARGE_S(2); break;
+    case 3: LBM_CHARGE_S(3); break;
+    default: LBM_CHARGE_S(4); break;
+  }
+#undef LBM_CHARGE_S
   k_sum_partials<<<1, 1024, 0, h->st>>>(h->ps.part, nb, h->ps.dsum);
   h->launches += 2;
   return cudaGetLastError();

@@ -38,22 +38,33 @@ __device__ __forceinline__ unsigned brev(unsigned v, int bits) {
 }
 
 // In-place radix-2 FFTs of `count` rows of length n = 2^lg stored with
-// element stride `es` and row stride `rs` in shared memory.  Input in
-// bit-reversed order.  tw[k] = exp(-2 pi i k / n) (k < n/2); sign -1 forward,
-// +1 inverse (conjugate twiddles).
-__device__ void fft_rows(float2* a, int n, int lg, int count, int es, int rs,
+// element stride `es` and row stride `rs` in shared memory (count = 2^lgc).
+// Input in bit-reversed order.  tw[k] = exp(-2 pi i k / n) (k < n/2); sign
+// -1 forward, +1 inverse (conjugate twiddles).  Consecutive threads take
+// consecutive butterflies of one row when the elements are contiguous
+// (es == 1) and the same butterfly of consecutive rows otherwise, so that
+// shared-memory accesses never stride by a row.
+__device__ void fft_rows(float2* a, int lg, int lgc, int es, int rs,
                          const float2* tw, float sign) {
-  const int half = n >> 1;
+  if (lg == 0) return;
+  const int half = 1 << (lg - 1);
+  const int total = half << lgc;
   for (int s = 1; s <= lg; ++s) {
-    const int m = 1 << s, mh = m >> 1;
-    const int tstep = n >> s;  // twiddle index step
-    for (int t = threadIdx.x; t < count * half; t += blockDim.x) {
-      const int row = t / half;
-      const int b = t - row * half;          // butterfly within the row
-      const int grp = b / mh, j = b - grp * mh;
-      const int i0 = grp * m + j, i1 = i0 + mh;
-      float2 w = tw[j * tstep];
-      w.y *= -sign;  // table holds exp(-i..); forward keeps it, inverse conjugates
+    const int mh = 1 << (s - 1);
+    const int tshift = lg - s;  // twiddle index step n/m = 2^(lg - s)
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      int row, b;
+      if (es == 1) {
+        row = t >> (lg - 1);
+        b = t & (half - 1);
+      } else {
+        row = t & ((1 << lgc) - 1);
+        b = t >> lgc;
+      }
+      const int j = b & (mh - 1);
+      const int i0 = ((b >> (s - 1)) << s) + j, i1 = i0 + mh;
+      float2 w = tw[j << tshift];
+      w.y *= -sign;
       float2* p0 = a + row * rs + i0 * es;
       float2* p1 = a + row * rs + i1 * es;
       const float2 u = *p0;
@@ -83,13 +94,13 @@ __global__ void __launch_bounds__(512) k_fft_fwd(const float* __restrict__ r,
   const float* src = r + (int64_t)z * nxy;
   // load with bit-reversed x and y (both passes then take natural output)
   for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
-    const int y = k / a.nx, x = k - y * a.nx;
+    const int y = k >> a.lgx, x = k & (a.nx - 1);
     const int xr = a.lgx ? (int)brev(x, a.lgx) : 0, yr = a.lgy ? (int)brev(y, a.lgy) : 0;
     buf[yr * a.nx + xr] = make_float2(src[k], 0.f);
   }
   __syncthreads();
-  fft_rows(buf, a.nx, a.lgx, a.ny, 1, a.nx, a.twx, -1.f);   // along x
-  fft_rows(buf, a.ny, a.lgy, a.nx, a.nx, 1, a.twy, -1.f);   // along y
+  fft_rows(buf, a.lgx, a.lgy, 1, a.nx, a.twx, -1.f);   // along x (ny rows)
+  fft_rows(buf, a.lgy, a.lgx, a.nx, 1, a.twy, -1.f);   // along y (nx columns)
   float2* dst = rhat + (int64_t)z * nxy;
   for (int k = threadIdx.x; k < nxy; k += blockDim.x) dst[k] = buf[k];
 }
@@ -106,13 +117,13 @@ __global__ void __launch_bounds__(512) k_fft_inv_apply(const float2* __restrict_
   const int nxy = a.nx * a.ny;
   const float2* src = ehat + (int64_t)z * nxy;
   for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
-    const int y = k / a.nx, x = k - y * a.nx;
+    const int y = k >> a.lgx, x = k & (a.nx - 1);
     const int xr = a.lgx ? (int)brev(x, a.lgx) : 0, yr = a.lgy ? (int)brev(y, a.lgy) : 0;
     buf[yr * a.nx + xr] = src[k];
   }
   __syncthreads();
-  fft_rows(buf, a.nx, a.lgx, a.ny, 1, a.nx, a.twx, 1.f);
-  fft_rows(buf, a.ny, a.lgy, a.nx, a.nx, 1, a.twy, 1.f);
+  fft_rows(buf, a.lgx, a.lgy, 1, a.nx, a.twx, 1.f);
+  fft_rows(buf, a.lgy, a.lgx, a.nx, 1, a.twy, 1.f);
   const float scale = 1.0f / (float)nxy;
   const int64_t base = (int64_t)z * nxy;
   for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
@@ -121,138 +132,125 @@ __global__ void __launch_bounds__(512) k_fft_inv_apply(const float2* __restrict_
   }
 }
 
-// Tridiagonal solve along z for one Fourier mode (thread) of one run
-// (blockIdx.y): -x_{z-1} + (lambda + d_z) x_z - x_{z+1} = rhat_z, with
+// Tridiagonal solve along z for one Fourier mode of one run:
+//   -x_{z-1} + (lambda + d_z) x_z - x_{z+1} = rhat_z,
 // d_z = 2 inside, 1 at a wall end; a cyclic run closes the chain
 // (Sherman-Morrison).  The mode (0,0) is singular: its run mean is free, so
 // x at the first plane of the run is pinned to 0 and the remaining planes
 // are solved (the pinned plane's equation is redundant once the run sum of
 // the right-hand side is zero, which the run-mean removal guarantees).
-// Overwrites rhat with the solution; cp holds the elimination factors.
+// X, C, Qv: the pencil's values, elimination factors and the Sherman-
+// Morrison auxiliary vector, element k at index k * st (shared memory).
 struct Run {
   int z0, len, cyclic;
 };
 
-__global__ void __launch_bounds__(256) k_zsolve(float2* __restrict__ x,
-                                                float* __restrict__ cp,
-                                                float2* __restrict__ w2,
-                                                const Run* __restrict__ runs,
-                                                SpecArgs a) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nxy = a.nx * a.ny;
-  if (m >= nxy) return;
-  const Run R = runs[blockIdx.y];
-  const int ky = m / a.nx, kx = m - ky * a.nx;
-  const float lam = (2.f - 2.f * cospif(2.f * kx / a.nx)) + (2.f - 2.f * cospif(2.f * ky / a.ny));
-  const int L = R.len;
-  auto at = [&](int k) -> int64_t {  // plane k of the run (wraps the lattice)
-    int z = R.z0 + k;
-    if (z >= a.nz) z -= a.nz;
-    return (int64_t)z * nxy + m;
-  };
-  const bool singular = (kx == 0 && ky == 0);
-  if (!R.cyclic) {
-    // diagonal: lambda + 2 inside, lambda + 1 at the ends (lambda alone if L == 1)
-    auto diag = [&](int k) -> float {
-      const int open = (k > 0) + (k < L - 1);
-      return lam + (float)open;
-    };
-    int k0 = 0;
-    if (singular) {
-      x[at(0)] = make_float2(0.f, 0.f);
-      k0 = 1;
-      if (L == 1) return;
-    }
-    // forward elimination
-    float c = 0.f;
+__device__ void solve_pencil(float2* X, float* C, float* Qv, int st, int L, float lam,
+                             bool singular, bool cyclic) {
+  auto thomas = [&](int k0, int k1, auto diagf, bool with_q, auto qrhs) {
+    // forward elimination on planes k0..k1-1 (off-diagonals -1)
+    float c = 0.f, dq = 0.f;
     float2 d = make_float2(0.f, 0.f);
-    for (int k = k0; k < L; ++k) {
-      const float den = diag(k) + (k > k0 ? c : 0.f);
+    for (int k = k0; k < k1; ++k) {
+      const float den = diagf(k) + (k > k0 ? c : 0.f);
       const float inv = 1.0f / den;
-      const float2 rk = x[at(k)];
+      const float2 rk = X[k * st];
       d = make_float2((rk.x + (k > k0 ? d.x : 0.f)) * inv, (rk.y + (k > k0 ? d.y : 0.f)) * inv);
+      if (with_q) {
+        dq = (qrhs(k) + (k > k0 ? dq : 0.f)) * inv;
+        Qv[k * st] = dq;
+      }
       c = -inv;
-      x[at(k)] = d;
-      cp[at(k)] = c;
+      X[k * st] = d;
+      C[k * st] = c;
     }
-    // back substitution
-    float2 nxt = x[at(L - 1)];
-    for (int k = L - 2; k >= k0; --k) {
-      const float ck = cp[at(k)];
-      const float2 dk = x[at(k)];
-      nxt = make_float2(dk.x - ck * nxt.x, dk.y - ck * nxt.y);
-      x[at(k)] = nxt;
+    float2 nx_ = X[(k1 - 1) * st];
+    float nq = with_q ? Qv[(k1 - 1) * st] : 0.f;
+    for (int k = k1 - 2; k >= k0; --k) {
+      const float ck = C[k * st];
+      const float2 dk = X[k * st];
+      nx_ = make_float2(dk.x - ck * nx_.x, dk.y - ck * nx_.y);
+      X[k * st] = nx_;
+      if (with_q) {
+        nq = Qv[k * st] - ck * nq;
+        Qv[k * st] = nq;
+      }
+    }
+  };
+  auto noq = [](int) { return 0.f; };
+  if (!cyclic) {
+    auto diag = [&](int k) { return lam + (float)((k > 0) + (k < L - 1)); };
+    if (singular) {
+      X[0] = make_float2(0.f, 0.f);
+      if (L > 1) thomas(1, L, diag, false, noq);
+    } else {
+      thomas(0, L, diag, false, noq);
     }
     return;
   }
-  // cyclic run of length L >= 3 (periodic z axis)
   if (singular) {
     // pin x_0 = 0; planes 1..L-1 form a Dirichlet chain (diagonal 2)
-    x[at(0)] = make_float2(0.f, 0.f);
-    float c = 0.f;
-    float2 d = make_float2(0.f, 0.f);
-    for (int k = 1; k < L; ++k) {
-      const float den = 2.f + (k > 1 ? c : 0.f);
-      const float inv = 1.0f / den;
-      const float2 rk = x[at(k)];
-      d = make_float2((rk.x + (k > 1 ? d.x : 0.f)) * inv, (rk.y + (k > 1 ? d.y : 0.f)) * inv);
-      c = -inv;
-      x[at(k)] = d;
-      cp[at(k)] = c;
-    }
-    float2 nxt = x[at(L - 1)];
-    for (int k = L - 2; k >= 1; --k) {
-      const float ck = cp[at(k)];
-      const float2 dk = x[at(k)];
-      nxt = make_float2(dk.x - ck * nxt.x, dk.y - ck * nxt.y);
-      x[at(k)] = nxt;
-    }
+    X[0] = make_float2(0.f, 0.f);
+    thomas(1, L, [](int) { return 2.f; }, false, noq);
     return;
   }
-  // Sherman-Morrison: A = T + u v^T with corner entries -1.
-  // gamma = -b; T has b - gamma at the first and b - 1/gamma at the last plane.
+  // Sherman-Morrison: A = T + u v^T, corners -1, gamma = -b,
+  // T = A without corners, T_00 = b - gamma, T_LL = b - 1/gamma,
+  // u = (gamma, 0, .., 0, -1), v = (1, 0, .., 0, -1/gamma).
   const float b = lam + 2.f;
   const float gam = -b;
-  auto tdiag = [&](int k) -> float {
-    if (k == 0) return b - gam;
-    if (k == L - 1) return b - 1.0f / gam;
-    return b;
+  auto tdiag = [&](int k) {
+    return k == 0 ? b - gam : (k == L - 1 ? b - 1.0f / gam : b);
   };
-  // solve T y = r (complex, in x) and T q = u (real, in w2.x), u = (gam, 0.., 0, -1)
-  float c = 0.f;
-  float2 d = make_float2(0.f, 0.f);
-  float dq = 0.f;
-  for (int k = 0; k < L; ++k) {
-    const float den = tdiag(k) + (k > 0 ? c : 0.f);
-    const float inv = 1.0f / den;
-    const float2 rk = x[at(k)];
-    const float uk = (k == 0) ? gam : (k == L - 1 ? -1.f : 0.f);
-    d = make_float2((rk.x + (k > 0 ? d.x : 0.f)) * inv, (rk.y + (k > 0 ? d.y : 0.f)) * inv);
-    dq = (uk + (k > 0 ? dq : 0.f)) * inv;
-    c = -inv;
-    x[at(k)] = d;
-    w2[at(k)] = make_float2(dq, 0.f);
-    cp[at(k)] = c;
-  }
-  float2 ny_ = x[at(L - 1)];
-  float nq = w2[at(L - 1)].x;
-  for (int k = L - 2; k >= 0; --k) {
-    const float ck = cp[at(k)];
-    const float2 dk = x[at(k)];
-    ny_ = make_float2(dk.x - ck * ny_.x, dk.y - ck * ny_.y);
-    nq = w2[at(k)].x - ck * nq;
-    x[at(k)] = ny_;
-    w2[at(k)] = make_float2(nq, 0.f);
-  }
-  // v = (1, 0, .., 0, -1/gam):  x = y - q (v.y) / (1 + v.q)
-  const float2 y0 = x[at(0)], yl = x[at(L - 1)];
-  const float q0 = w2[at(0)].x, ql = w2[at(L - 1)].x;
+  auto urhs = [&](int k) { return k == 0 ? gam : (k == L - 1 ? -1.f : 0.f); };
+  thomas(0, L, tdiag, true, urhs);
+  const float2 y0 = X[0], yl = X[(L - 1) * st];
+  const float q0 = Qv[0], ql = Qv[(L - 1) * st];
   const float den = 1.f + q0 - ql / gam;
   const float2 f = make_float2((y0.x - yl.x / gam) / den, (y0.y - yl.y / gam) / den);
   for (int k = 0; k < L; ++k) {
-    const float qk = w2[at(k)].x;
-    const float2 yk = x[at(k)];
-    x[at(k)] = make_float2(yk.x - qk * f.x, yk.y - qk * f.y);
+    const float qk = Qv[k * st];
+    const float2 yk = X[k * st];
+    X[k * st] = make_float2(yk.x - qk * f.x, yk.y - qk * f.y);
+  }
+}
+
+constexpr int ZP = 32;  // pencils (Fourier modes) per CTA of the z solve
+
+// One CTA: ZP consecutive modes of one run.  The pencils are staged in
+// shared memory (coalesced: consecutive modes are contiguous in each
+// plane), solved one per thread, and written back in place.
+__global__ void __launch_bounds__(128) k_zsolve(float2* __restrict__ x,
+                                                const Run* __restrict__ runs,
+                                                SpecArgs a) {
+  extern __shared__ float zsm[];
+  const Run R = runs[blockIdx.y];
+  const int L = R.len;
+  const int nxy = a.nx * a.ny;
+  const int m0 = blockIdx.x * ZP;
+  float2* X = reinterpret_cast<float2*>(zsm);
+  float* C = zsm + 2 * ZP * L;
+  float* Qv = C + ZP * L;
+  for (int idx = threadIdx.x; idx < ZP * L; idx += blockDim.x) {
+    const int k = idx / ZP, j = idx - k * ZP;
+    int z = R.z0 + k;
+    if (z >= a.nz) z -= a.nz;
+    if (m0 + j < nxy) X[idx] = x[(int64_t)z * nxy + m0 + j];
+  }
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < ZP && m0 + j < nxy) {
+    const int m = m0 + j;
+    const int ky = m >> a.lgx, kx = m & (a.nx - 1);
+    const float lam = (2.f - 2.f * cospif(2.f * kx / a.nx)) + (2.f - 2.f * cospif(2.f * ky / a.ny));
+    solve_pencil(X + j, C + j, Qv + j, ZP, L, lam, kx == 0 && ky == 0, R.cyclic != 0);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < ZP * L; idx += blockDim.x) {
+    const int k = idx / ZP, jj = idx - k * ZP;
+    int z = R.z0 + k;
+    if (z >= a.nz) z -= a.nz;
+    if (m0 + jj < nxy) x[(int64_t)z * nxy + m0 + jj] = X[idx];
   }
 }
 
@@ -301,20 +299,21 @@ __global__ void k_run_means(const long long* __restrict__ psum, const Run* __res
 __global__ void __launch_bounds__(256) k_res_planes(
     const int64_t* __restrict__ psi, const int64_t* __restrict__ src,
     const long long* __restrict__ mean_z, const unsigned char* __restrict__ plane_fluid,
-    float* __restrict__ r, double* dsum, int nx, int ny, int nz) {
+    float* __restrict__ r, double* dsum, int nx, int ny, int nz, int lgx, int lgxy) {
   __shared__ float red_r[8], red_s[8];
   const int nxy = nx * ny;
   const int64_t N = (int64_t)nxy * nz;
   float rr = 0.f, ss = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int z = (int)(i / nxy);
-    const int k = (int)(i - (int64_t)z * nxy);
+    // nx, ny are powers of two: plane, row and column by shifts
+    const int z = (int)(i >> lgxy);
+    const int k = (int)(i & (nxy - 1));
     if (!plane_fluid[z]) {
       r[i] = 0.f;
       continue;
     }
-    const int y = k / nx, x = k - y * nx;
+    const int y = k >> lgx, x = k & (nx - 1);
     const int64_t pc = psi[i];
     int64_t Ap = 0;
     if (nx > 1) {
@@ -374,8 +373,7 @@ struct SpectralPlan {
   float2* twx = nullptr;
   float2* twy = nullptr;
   float2* spec = nullptr;          // N complex
-  float* cp = nullptr;             // N
-  float2* w2 = nullptr;            // N complex (cyclic runs only)
+  size_t zsmem = 0;                // shared memory of the z solve
   float* r = nullptr;              // N
   long long* psum = nullptr;       // nz
   long long* mean_z = nullptr;     // nz
@@ -391,8 +389,6 @@ void spectral_free(lbm_t* h) {
   cudaFree(s->twx);
   cudaFree(s->twy);
   cudaFree(s->spec);
-  cudaFree(s->cp);
-  cudaFree(s->w2);
   cudaFree(s->r);
   cudaFree(s->psum);
   cudaFree(s->mean_z);
@@ -474,10 +470,9 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
             al((void**)&s->runs, runs.size() * sizeof(Run)) &&
             al((void**)&s->plane_fluid, nz) && al((void**)&s->twx, std::max(1, nx / 2) * sizeof(float2)) &&
             al((void**)&s->twy, std::max(1, ny / 2) * sizeof(float2)) &&
-            al((void**)&s->spec, N * sizeof(float2)) && al((void**)&s->cp, N * sizeof(float)) &&
+            al((void**)&s->spec, N * sizeof(float2)) &&
             al((void**)&s->r, N * sizeof(float)) && al((void**)&s->psum, nz * sizeof(long long)) &&
             al((void**)&s->mean_z, nz * sizeof(long long));
-  if (ok && runs.size() == 1 && runs[0].cyclic) ok = al((void**)&s->w2, N * sizeof(float2));
   if (!ok) {
     spectral_free(h);
     h->err = "spectral Poisson allocation failed";
@@ -497,6 +492,17 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   LBM_CUDA_TRY(h, cudaMemcpy(s->plane_fluid, pf.data(), nz, cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->twx, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->twy, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  int lmax = 0;
+  for (const Run& R : runs) lmax = std::max(lmax, R.len);
+  s->zsmem = (size_t)ZP * lmax * (2 + 1 + 1) * sizeof(float);
+  int optin = 0;
+  LBM_CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
+  if ((int)s->zsmem > optin) {
+    h->err = "spectral Poisson solver: fluid run along z too long for shared memory";
+    return LBM_EINVAL;
+  }
+  if (s->zsmem > 48 * 1024)
+    LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->zsmem));
   s->smem = (size_t)nxy * sizeof(float2);
   if (s->smem > 48 * 1024) {
     LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem));
@@ -526,7 +532,7 @@ cudaError_t spec_residual(lbm_t* h) {
   if (e != cudaSuccess) return e;
   const unsigned nb = (unsigned)std::min<int64_t>(nblk(h->N, 256), h->grid_cap);
   k_res_planes<<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, s->mean_z, s->plane_fluid, s->r,
-                                      P.dsum, s->nx, s->ny, s->nz);
+                                      P.dsum, s->nx, s->ny, s->nz, s->lgx, s->lgx + s->lgy);
   ++h->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
@@ -538,8 +544,8 @@ cudaError_t spec_apply(lbm_t* h) {
   const SpecArgs a = args_of(s);
   const int threads = (int)std::min<int64_t>(512, std::max<int64_t>(32, (int64_t)s->nx * s->ny / 2));
   k_fft_fwd<<<s->nplanes, threads, s->smem, h->st>>>(s->r, s->spec, s->planes, a);
-  dim3 g(nblk((int64_t)s->nx * s->ny, 256), s->nruns);
-  k_zsolve<<<g, 256, 0, h->st>>>(s->spec, s->cp, s->w2, s->runs, a);
+  dim3 g(nblk((int64_t)s->nx * s->ny, ZP), s->nruns);
+  k_zsolve<<<g, 128, s->zsmem, h->st>>>(s->spec, s->runs, a);
   k_fft_inv_apply<<<s->nplanes, threads, s->smem, h->st>>>(s->spec, s->planes, a, P.psi[P.cur],
                                                           P.psi[P.cur ^ 1]);
   h->launches += 3;
