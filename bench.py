@@ -3,7 +3,8 @@
 Workload (default): charged ternary mixture (solvent, cation z=+1, anion
 z=-1), D3Q19, 128^3 periodic, ion number fractions 0.01 +/- U(1e-3) seeded,
 Bjerrum length 0.7, Poisson solved every step to a relative residual of
-1e-8, Sc = 1, FP32.  One step = charge density + Poisson solve + fused
+1e-8 (spectral solver; the multigrid solver is timed beside it), Sc = 1,
+FP32.  One step = charge density + Poisson solve + fused
 stream/collide of all species.  Metric: species-site MLUPS (S * N * steps /
 time / 1e6), with the stream/collide kernel's fraction of the measured HBM
 roofline and the Poisson iterations per step.
@@ -45,7 +46,8 @@ def parse():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--schmidt", type=float, default=1.0)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
-    ap.add_argument("--poisson", default="mg", choices=["mg", "sor", "fft"])
+    ap.add_argument("--poisson", default="fft", choices=["mg", "sor", "fft"])
+    ap.add_argument("--no-alt", action="store_true", help="skip the multigrid comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -67,10 +69,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_traffic():
+def kernel_traffic(storage="fp32"):
     """DRAM bytes per stream/collide launch from the committed ncu summary,
     valid only while the kernel source is unchanged (hash recorded there)."""
-    path = os.path.join(ROOT, "profiles", "stream_collide_ternary_128.md")
+    path = os.path.join(ROOT, "profiles", "stream_collide_ternary_128_%s.md" % storage)
     src = os.path.join(ROOT, "paper_1507_04891_gb300", "csrc", "lbm_kernels.cu")
     try:
         text = open(src, "rb").read()
@@ -215,18 +217,12 @@ def run_ours(args, rank, world, local):
     wl = WL.ternary_bulk(n=n, seed=1235 + rank, schmidt=args.schmidt)
     S, N = wl.nspecies, wl.sites
     od = lbm.omega_drag_for_schmidt(wl.omega_visc, args.schmidt)
+    warm = max(3, args.warmup)
 
-    def make():
+    def make(poisson):
         return lbm.Lattice(n, n, n, S, omega_visc=wl.omega_visc, omega_drag=od, bjerrum=wl.bjerrum,
-                           storage=args.storage, poisson=args.poisson, poisson_tol=1e-8,
+                           storage=args.storage, poisson=poisson, poisson_tol=1e-8,
                            poisson_maxit=500, device=local)
-
-    lat = make()
-    for s in range(S):
-        lat.set_species(s, 1.0, wl.valence[s], wl.n0[s])
-    stream = torch.cuda.ExternalStream(lat.stream, device=torch.device("cuda", local))
-    lat.step(max(3, args.warmup))
-    lat.synchronize()
 
     def barrier():
         if world > 1:
@@ -234,38 +230,62 @@ def run_ours(args, rank, world, local):
             dist.barrier()
         torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
-    barrier()
-    lat.set_timing(True)
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    lat.step(args.steps)
-    e1.record(stream)
-    lat.synchronize()
-    barrier()
-    clk = clocks.stop()
-    t_ms = e0.elapsed_time(e1)
-    tm = lat.get_timing()
-    lat.set_timing(False)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    def max_over_ranks(x):
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([x], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            return float(tt.item())
+        return x
+
+    def timed(poisson, sample_clocks):
+        """W warm-up steps, then K steps timed with CUDA events on the
+        library's stream; phase times from the library's own events."""
+        lat = make(poisson)
+        for s in range(S):
+            lat.set_species(s, 1.0, wl.valence[s], wl.n0[s])
+        stream = torch.cuda.ExternalStream(lat.stream, device=torch.device("cuda", local))
+        lat.step(warm)
+        lat.synchronize()
+        clocks = ClockSampler(local) if sample_clocks else None
+        barrier()
+        lat.set_timing(True)
+        if clocks:
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(args.steps)
+        e1.record(stream)
+        lat.synchronize()
+        barrier()
+        clk = clocks.stop() if clocks else None
+        t_ms = max_over_ranks(e0.elapsed_time(e1))
+        tm = lat.get_timing()
+        lat.set_timing(False)
+        diag = lat.diagnostics()
+        lat.destroy()
+        return t_ms, tm, diag, clk
+
+    t_ms, tm, diag, clk = timed(args.poisson, True)
     value = world * S * N * args.steps / (t_ms / 1e3) / 1e6
     collide_ms = tm["collide_ms"] / max(1, tm["collide_launches"])
     bpl = BYTES_PER_SPECIES_SITE[args.storage] * S * N
     peak, peak_kind = measured_peaks()
     achieved = bpl / (collide_ms / 1e3) / 1e9
-    traffic = kernel_traffic() if args.storage == "fp32" and n == 128 else None
-    diag = lat.diagnostics()
+    traffic = kernel_traffic(args.storage) if n == 128 else None
+
+    # the same workload with the multigrid solver, for comparison
+    alt = None
+    if args.poisson != "mg" and not args.no_alt:
+        ta, tma, _, _ = timed("mg", False)
+        alt = {"poisson": "mg", "value": world * S * N * args.steps / (ta / 1e3) / 1e6,
+               "ms_per_step": ta / args.steps, "poisson_iters_per_step": tma["poisson_iters"] / args.steps,
+               "poisson_ms_per_step": tma["poisson_ms"] / args.steps}
 
     # end to end through the C ABI with host buffers: initial state uploaded
     # from pinned host memory, every step's FP64 diagnostics read back.
-    lat.destroy()
-    lat2 = make()
+    lat2 = make(args.poisson)
     pinned = [torch.from_numpy(np.ascontiguousarray(wl.n0[s])).pin_memory().numpy() for s in range(S)]
     barrier()
     t0 = time.perf_counter()
@@ -276,7 +296,7 @@ def run_ours(args, rank, world, local):
         lat2.diagnostics()
     lat2.synchronize()
     barrier()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_value = world * S * N * args.steps / e2e_s / 1e6
     lat2.destroy()
 
@@ -290,14 +310,13 @@ def run_ours(args, rank, world, local):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": t_ms / args.steps,
+            "warmup": warm, "ms_per_step": t_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.storage == "fp32" else args.storage + "-storage/f32",
-            "data": "synthetic",
+            "dtype": "f32", "data": "synthetic",
             "config": {"workload": "ternary_bulk_%d^3" % n, "species": S, "sc": args.schmidt,
                        "omega_visc": wl.omega_visc, "omega_drag": od, "bjerrum": wl.bjerrum,
                        "poisson": args.poisson, "poisson_tol": 1e-8, "storage": args.storage,
-                       "l2": "inputs larger than L2 (2 x %.0f MB population lattices)"
+                       "l2": "not flushed: inputs larger than L2 (2 x %.0f MB population lattices)"
                              % (BYTES_PER_SPECIES_SITE[args.storage] / 2 * S * N / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
             "poisson_iters_per_step": iters / args.steps,
@@ -313,6 +332,7 @@ def run_ours(args, rank, world, local):
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * S * N / args.steps,
                     "d2h_bytes_per_step": 8 * (S + 7)},
+            "poisson_alternative": alt,
             "diagnostics": {"mass": list(map(float, diag["mass"])),
                             "poisson_residual_last": diag["poisson_residual"]},
             "cpu_baseline": cpu,

@@ -70,7 +70,14 @@ typedef struct {
   double poisson_tol;    /* ||s - A psi||_2 / ||s||_2 target, e.g. 1e-8      */
   int poisson_maxit;     /* iteration cap (V-cycles or SOR sweeps)           */
   int device;            /* CUDA device ordinal                              */
+  int flags;             /* LBM_FLAG_* bits                                  */
 } lbm_config;
+
+/* LBM_FLAG_STEP_GRAPH: every time step (charge density, spectral Poisson
+ * solve in a device-side loop, stream/collide) is one CUDA graph replay, with
+ * no host round trip between steps.  Needs LBM_POISSON_FFT and l_B > 0.
+ * Per-phase timings (lbm_get_timing) then cover whole steps only.         */
+#define LBM_FLAG_STEP_GRAPH 1
 
 /* Fills *cfg with defaults: omega_visc = 1, omega_drag = 1, l_B = 0,
  * FP32 storage, multigrid Poisson, tol 1e-8, maxit 200, device 0.        */
@@ -81,6 +88,28 @@ void lbm_config_default(lbm_config* cfg);
  * outside 1..4, omega outside (0, 2), storage/poisson codes unknown;
  * LBM_ENOMEM when device memory runs out.  *out is NULL on failure.      */
 lbm_status lbm_create(const lbm_config* cfg, lbm_t** out);
+
+/* Batched instances.  Creates one lattice that stacks `count` independent
+ * instances along z (each instance closes itself with its own wall planes,
+ * set by the caller through lbm_set_walls on the stacked arrays).  All
+ * cfgs share nx, ny, nspecies, omega_visc, bjerrum, e_ext, storage,
+ * poisson, tolerances, device and flags; each brings its own nz and
+ * omega_drag (the drag frequency becomes a per-plane field).  Instance i
+ * occupies planes [lbm_instance_z0(h, i), lbm_instance_z0(h, i) + cfgs[i].nz).
+ * LBM_EINVAL if the shared fields differ.                                 */
+lbm_status lbm_create_stack(int count, const lbm_config* cfgs, lbm_t** out);
+int lbm_instance_z0(const lbm_t* h, int i);
+
+/* Per-plane drag frequency: omega (nz doubles, each in (0, 2)) replaces
+ * the config's omega_drag on every node of plane z; NULL restores the
+ * config value.                                                           */
+lbm_status lbm_set_plane_omega_drag(lbm_t* h, const double* omega);
+
+/* Autotuner: times the stream/collide and charge kernels of the current
+ * state at several CTA sizes (64, 128, 256) and keeps the fastest; the state
+ * does not advance.  out (may be NULL) receives the chosen sizes and their
+ * times in ms: [collide_threads, collide_ms, charge_threads, charge_ms].  */
+lbm_status lbm_autotune(lbm_t* h, double* out);
 
 /* Releases every device buffer of h.  NULL is accepted.                  */
 void lbm_destroy(lbm_t* h);

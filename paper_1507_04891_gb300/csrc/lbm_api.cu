@@ -104,6 +104,7 @@ void lbm_config_default(lbm_config* c) {
   c->poisson_tol = 1e-8;
   c->poisson_maxit = 200;
   c->device = 0;
+  c->flags = 0;
 }
 
 lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
@@ -146,6 +147,10 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
   }
   if (c.bjerrum > 0.0 && (!(c.poisson_tol > 0.0) || c.poisson_maxit < 1)) {
     g_create_error = "poisson_tol must be > 0 and poisson_maxit >= 1";
+    return LBM_EINVAL;
+  }
+  if ((c.flags & LBM_FLAG_STEP_GRAPH) && (c.poisson != LBM_POISSON_FFT || !(c.bjerrum > 0.0))) {
+    g_create_error = "LBM_FLAG_STEP_GRAPH needs the spectral Poisson solver and bjerrum > 0";
     return LBM_EINVAL;
   }
   int ndev = 0;
@@ -193,7 +198,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.psi[1], N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.src, N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.dsum, 4);
-    if (s == LBM_OK) s = dev_alloc(h, &h->ps.part, (size_t)((N + 255) / 256));
+    if (s == LBM_OK) s = dev_alloc(h, &h->ps.part, (size_t)((N + 63) / 64));
     if (s == LBM_OK && cudaMallocHost(&h->ps.hsum, 4 * sizeof(double)) != cudaSuccess)
       s = LBM_ENOMEM;
     if (s == LBM_OK) {
@@ -226,8 +231,12 @@ void lbm_destroy(lbm_t* h) {
   cudaFree(h->dred);
   cudaFree(h->dflag);
   if (h->hred) cudaFreeHost(h->hred);
+  spectral_graph_free(h);
   poisson_free(h);
   spectral_free(h);
+  cudaFree(h->omega_drag_z);
+  cudaFree(h->gstatus);
+  if (h->hstatus) cudaFreeHost(h->hstatus);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
@@ -376,6 +385,12 @@ lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
   cudaSetDevice(h->dev);
   h->st = stream ? (cudaStream_t)stream : h->own;
   const bool charged = h->cfg.bjerrum > 0.0;
+  if (h->cfg.flags & LBM_FLAG_STEP_GRAPH) {
+    Phase pg(h, 1);
+    lbm_status s = spectral_graph_steps(h, nsteps);
+    LBM_CUDA_TRY(h, pg.stop());
+    return s;
+  }
   // bound the number of outstanding timing events
   if (h->timing && h->ev_used > 4096) LBM_CUDA_TRY(h, drain_timing(h));
   for (int k = 0; k < nsteps; ++k) {
@@ -543,6 +558,145 @@ lbm_status lbm_set_state(lbm_t* h, const float* state, int64_t step) {
                                   cudaMemcpyHostToDevice, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   h->tstep = step;
+  return LBM_OK;
+}
+
+lbm_status lbm_create_stack(int count, const lbm_config* cfgs, lbm_t** out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !cfgs) {
+    g_create_error = "count must be >= 1 and cfgs non-NULL";
+    return LBM_EINVAL;
+  }
+  lbm_config c = cfgs[0];
+  int64_t nz = 0;
+  for (int i = 0; i < count; ++i) {
+    const lbm_config& k = cfgs[i];
+    if (k.nx != c.nx || k.ny != c.ny || k.nspecies != c.nspecies || k.omega_visc != c.omega_visc ||
+        k.bjerrum != c.bjerrum || k.e_ext[0] != c.e_ext[0] || k.e_ext[1] != c.e_ext[1] ||
+        k.e_ext[2] != c.e_ext[2] || k.storage != c.storage || k.poisson != c.poisson ||
+        k.poisson_tol != c.poisson_tol || k.poisson_maxit != c.poisson_maxit ||
+        k.device != c.device || k.flags != c.flags) {
+      g_create_error = "stacked instances must share every field but nz and omega_drag";
+      return LBM_EINVAL;
+    }
+    if (k.nz < 1 || !(k.omega_drag > 0.0 && k.omega_drag < 2.0)) {
+      g_create_error = "instance nz must be >= 1 and omega_drag in (0, 2)";
+      return LBM_EINVAL;
+    }
+    nz += k.nz;
+  }
+  if (nz > (1 << 30)) {
+    g_create_error = "stack too tall";
+    return LBM_EINVAL;
+  }
+  c.nz = (int)nz;
+  lbm_t* h = nullptr;
+  lbm_status s = lbm_create(&c, &h);
+  if (s != LBM_OK) return s;
+  std::vector<double> om;
+  om.reserve(nz);
+  h->instance_z0.clear();
+  for (int i = 0; i < count; ++i) {
+    h->instance_z0.push_back((int)om.size());
+    for (int z = 0; z < cfgs[i].nz; ++z) om.push_back(cfgs[i].omega_drag);
+  }
+  s = lbm_set_plane_omega_drag(h, om.data());
+  if (s != LBM_OK) {
+    g_create_error = h->err;
+    lbm_destroy(h);
+    return s;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_instance_z0(const lbm_t* h, int i) {
+  if (!h) return -1;
+  if (h->instance_z0.empty()) return i == 0 ? 0 : -1;
+  if (i < 0 || i >= (int)h->instance_z0.size()) return -1;
+  return h->instance_z0[i];
+}
+
+lbm_status lbm_set_plane_omega_drag(lbm_t* h, const double* omega) {
+  if (!h) return LBM_EINVAL;
+  cudaSetDevice(h->dev);
+  if (!omega) {
+    cudaFree(h->omega_drag_z);
+    h->omega_drag_z = nullptr;
+    spectral_graph_free(h);
+    return LBM_OK;
+  }
+  const int nz = h->cfg.nz;
+  std::vector<float> w(nz);
+  for (int z = 0; z < nz; ++z) {
+    if (!(omega[z] > 0.0 && omega[z] < 2.0)) return fail(h, LBM_EINVAL, "omega_drag must lie in (0, 2)");
+    w[z] = (float)omega[z];
+  }
+  if (!h->omega_drag_z) {
+    lbm_status s = dev_alloc(h, &h->omega_drag_z, nz);
+    if (s != LBM_OK) return s;
+  }
+  LBM_CUDA_TRY(h, cudaMemcpy(h->omega_drag_z, w.data(), nz * sizeof(float), cudaMemcpyHostToDevice));
+  spectral_graph_free(h);
+  return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_t* h, double* out) {
+  if (!h) return LBM_EINVAL;
+  if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set first");
+  cudaSetDevice(h->dev);
+  h->st = h->own;
+  cudaEvent_t e0, e1;
+  LBM_CUDA_TRY(h, cudaEventCreate(&e0));
+  LBM_CUDA_TRY(h, cudaEventCreate(&e1));
+  const int sizes[3] = {64, 128, 256};
+  double best_c = 1e30, best_q = 1e30;
+  int tc = h->collide_threads, tq = h->charge_threads;
+  const int reps = 5;
+  for (int k = 0; k < 3; ++k) {
+    LBM_CUDA_TRY(h, launch_stream_collide_probe(h, sizes[k]));  // warm
+    LBM_CUDA_TRY(h, cudaEventRecord(e0, h->st));
+    for (int r = 0; r < reps; ++r) LBM_CUDA_TRY(h, launch_stream_collide_probe(h, sizes[k]));
+    LBM_CUDA_TRY(h, cudaEventRecord(e1, h->st));
+    LBM_CUDA_TRY(h, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    LBM_CUDA_TRY(h, cudaEventElapsedTime(&ms, e0, e1));
+    if (ms / reps < best_c) {
+      best_c = ms / reps;
+      tc = sizes[k];
+    }
+  }
+  if (h->cfg.bjerrum > 0.0) {
+    const int saved = h->charge_threads;
+    for (int k = 0; k < 3; ++k) {
+      h->charge_threads = sizes[k];
+      LBM_CUDA_TRY(h, launch_charge(h));
+      LBM_CUDA_TRY(h, cudaEventRecord(e0, h->st));
+      for (int r = 0; r < reps; ++r) LBM_CUDA_TRY(h, launch_charge(h));
+      LBM_CUDA_TRY(h, cudaEventRecord(e1, h->st));
+      LBM_CUDA_TRY(h, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      LBM_CUDA_TRY(h, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms / reps < best_q) {
+        best_q = ms / reps;
+        tq = sizes[k];
+      }
+    }
+    h->charge_threads = saved;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->collide_threads = tc;
+  h->charge_threads = tq;
+  spectral_graph_free(h);  // graphs baked the old sizes
+  h->psi_valid = false;
+  if (out) {
+    out[0] = tc;
+    out[1] = best_c;
+    out[2] = tq;
+    out[3] = best_q < 1e29 ? best_q : 0.0;
+  }
   return LBM_OK;
 }
 

@@ -43,11 +43,13 @@ struct StepArgs {
   int nx, ny, nz;
   int64_t N;
   float omega_visc, omega_drag;
+  const float* omega_drag_z;  // per z-plane drag frequency (stacked instances) or NULL
   float fourpi_lb;
   float eext[3];
   float valence[MAX_SPECIES];
   float nref[MAX_SPECIES];  // reference density of the 16-bit shifted storage
   uint32_t step;            // time step (seeds the stochastic rounding)
+  const uint32_t* step_dev; // device copy of the step (graph replays) or NULL
 };
 
 struct PoissonLevel {
@@ -125,7 +127,17 @@ struct lbm {
   double t_acc[3] = {0, 0, 0};
   int64_t t_cnt[3] = {0, 0, 0};
   int64_t launches = 0;
-  int grid_cap = 1216;   // CTAs of the grid-stride reduction kernels (8 per SM)  // kernels launched since timing was (re)set
+  int grid_cap = 1216;   // CTAs of the grid-stride reduction kernels (8 per SM)
+  float* omega_drag_z = nullptr;  // per-plane drag frequency (lbm_set_plane_omega_drag)
+  int collide_threads = 128;      // CTA size of the stream-collide kernel (autotuned)
+  // whole-step CUDA graphs (LBM_FLAG_STEP_GRAPH), one per population parity
+  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+  void* gstatus = nullptr;        // device status of graph steps
+  void* hstatus = nullptr;        // pinned mirror
+  int graph_kernels_fixed = 0;    // kernels per step outside the Poisson loop
+  int graph_kernels_iter = 0;     // kernels per Poisson iteration
+  std::vector<int> instance_z0;   // first plane of each stacked instance
+  int charge_threads = 256;       // CTA size of the charge kernel (autotuned)  // kernels launched since timing was (re)set
   std::string err;
 };
 
@@ -135,6 +147,9 @@ namespace lbm_gb300 {
 cudaError_t launch_init_species(lbm_t* h, int s, const double* n0_dev,
                                 const double* u0_dev);
 cudaError_t launch_stream_collide(lbm_t* h);
+// Stream-collide into the spare lattice with a given CTA size, without
+// advancing the state (autotuning).
+cudaError_t launch_stream_collide_probe(lbm_t* h, int threads);
 cudaError_t launch_charge(lbm_t* h);
 cudaError_t launch_gather(lbm_t* h, int s, double* n_dev, double* u_dev,
                           double* f_dev);
@@ -156,6 +171,10 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid_host);
 void spectral_free(lbm_t* h);
 lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters,
                           double* rel_res);
+// Whole-step graphs: build (if needed) and replay nsteps steps; reads the
+// device status once at the end.
+lbm_status spectral_graph_steps(lbm_t* h, int nsteps);
+void spectral_graph_free(lbm_t* h);
 
 }  // namespace lbm_gb300
 

@@ -246,7 +246,7 @@ __device__ __forceinline__ void block_sum_to(long long v, double* out) {
 //   5. store f* at r.
 // ---------------------------------------------------------------------------
 template <int S, bool WALLS, bool CHARGED, int ST>
-__global__ void __launch_bounds__(128) k_stream_collide(const StepArgs a) {
+__global__ void __launch_bounds__(256) k_stream_collide(const StepArgs a) {
   using T = typename Fmt<ST>::T;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (uint32_t)a.N) return;
@@ -315,9 +315,10 @@ __global__ void __launch_bounds__(128) k_stream_collide(const StepArgs a) {
   const float vby = (Jy + 0.5f * zn * Ey) * inv_ntot;
   const float vbz = (Jz + 0.5f * zn * Ez) * inv_ntot;
 
-  const float om = a.omega_visc, omd = a.omega_drag;
+  const float om = a.omega_visc;
+  const float omd = a.omega_drag_z ? a.omega_drag_z[z] : a.omega_drag;
   uint32_t rnd = 0;
-  if (ST != LBM_FP32) rnd = mix32(i * 0x9E3779B9u ^ mix32(a.step));
+  if (ST != LBM_FP32) rnd = mix32(i * 0x9E3779B9u ^ mix32(a.step_dev ? *a.step_dev : a.step));
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const float inv_n = 1.0f / n[s];
@@ -622,24 +623,24 @@ __global__ void __launch_bounds__(256) k_src_from_rho(
 inline unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 template <int S, bool W, bool C, int ST>
-cudaError_t launch_sc(const StepArgs& a, cudaStream_t st) {
-  k_stream_collide<S, W, C, ST><<<nblocks(a.N, 128), 128, 0, st>>>(a);
+cudaError_t launch_sc(const StepArgs& a, cudaStream_t st, int threads) {
+  k_stream_collide<S, W, C, ST><<<nblocks(a.N, threads), threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int S, int ST>
-cudaError_t dispatch_wc(const StepArgs& a, bool w, bool c, cudaStream_t st) {
-  if (w) return c ? launch_sc<S, true, true, ST>(a, st) : launch_sc<S, true, false, ST>(a, st);
-  return c ? launch_sc<S, false, true, ST>(a, st) : launch_sc<S, false, false, ST>(a, st);
+cudaError_t dispatch_wc(const StepArgs& a, bool w, bool c, cudaStream_t st, int t) {
+  if (w) return c ? launch_sc<S, true, true, ST>(a, st, t) : launch_sc<S, true, false, ST>(a, st, t);
+  return c ? launch_sc<S, false, true, ST>(a, st, t) : launch_sc<S, false, false, ST>(a, st, t);
 }
 
 template <int ST>
-cudaError_t dispatch_s(const StepArgs& a, int S, bool w, bool c, cudaStream_t st) {
+cudaError_t dispatch_s(const StepArgs& a, int S, bool w, bool c, cudaStream_t st, int t) {
   switch (S) {
-    case 1: return dispatch_wc<1, ST>(a, w, c, st);
-    case 2: return dispatch_wc<2, ST>(a, w, c, st);
-    case 3: return dispatch_wc<3, ST>(a, w, c, st);
-    case 4: return dispatch_wc<4, ST>(a, w, c, st);
+    case 1: return dispatch_wc<1, ST>(a, w, c, st, t);
+    case 2: return dispatch_wc<2, ST>(a, w, c, st, t);
+    case 3: return dispatch_wc<3, ST>(a, w, c, st, t);
+    case 4: return dispatch_wc<4, ST>(a, w, c, st, t);
   }
   return cudaErrorInvalidValue;
 }
@@ -648,7 +649,8 @@ float4 as_f4(const float* v) { return make_float4(v[0], v[1], v[2], v[3]); }
 
 }  // namespace
 
-cudaError_t launch_stream_collide(lbm_t* h) {
+namespace {
+cudaError_t collide_into_spare(lbm_t* h, int threads) {
   StepArgs a;
   a.fin = h->f[h->cur];
   a.fout = h->f[h->cur ^ 1];
@@ -662,6 +664,7 @@ cudaError_t launch_stream_collide(lbm_t* h) {
   a.N = h->N;
   a.omega_visc = (float)h->cfg.omega_visc;
   a.omega_drag = (float)h->cfg.omega_drag;
+  a.omega_drag_z = h->omega_drag_z;
   a.fourpi_lb = (float)(4.0 * 3.14159265358979323846 * h->cfg.bjerrum);
   for (int d = 0; d < 3; ++d) a.eext[d] = (float)h->cfg.e_ext[d];
   for (int s = 0; s < MAX_SPECIES; ++s) {
@@ -669,17 +672,29 @@ cudaError_t launch_stream_collide(lbm_t* h) {
     a.nref[s] = h->nref[s];
   }
   a.step = (uint32_t)h->tstep;
-  cudaError_t e;
+  a.step_dev = nullptr;
+  if (h->gstatus) a.step_dev = reinterpret_cast<const uint32_t*>(h->gstatus);
   switch (h->cfg.storage) {
-    case LBM_FP32: e = dispatch_s<LBM_FP32>(a, h->S, h->has_walls, charged, h->st); break;
-    case LBM_FP16_SHIFT: e = dispatch_s<LBM_FP16_SHIFT>(a, h->S, h->has_walls, charged, h->st); break;
-    case LBM_BF16_SHIFT: e = dispatch_s<LBM_BF16_SHIFT>(a, h->S, h->has_walls, charged, h->st); break;
-    default: return cudaErrorInvalidValue;
+    case LBM_FP32: return dispatch_s<LBM_FP32>(a, h->S, h->has_walls, charged, h->st, threads);
+    case LBM_FP16_SHIFT: return dispatch_s<LBM_FP16_SHIFT>(a, h->S, h->has_walls, charged, h->st, threads);
+    case LBM_BF16_SHIFT: return dispatch_s<LBM_BF16_SHIFT>(a, h->S, h->has_walls, charged, h->st, threads);
   }
+  return cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t launch_stream_collide(lbm_t* h) {
+  cudaError_t e = collide_into_spare(h, h->collide_threads);
   if (e == cudaSuccess) {
     h->cur ^= 1;
     ++h->launches;
   }
+  return e;
+}
+
+cudaError_t launch_stream_collide_probe(lbm_t* h, int threads) {
+  cudaError_t e = collide_into_spare(h, threads);
+  if (e == cudaSuccess) ++h->launches;
   return e;
 }
 
@@ -715,10 +730,11 @@ cudaError_t launch_init_species(lbm_t* h, int s, const double* n0,
 cudaError_t launch_charge(lbm_t* h) {
   // one node per thread (the pulled loads of a node are independent and all
   // in flight); per-CTA partial sums instead of same-address atomics
-  const int nb = (int)nblocks(h->N, 256);
+  const int ct = h->charge_threads;
+  const int nb = (int)nblocks(h->N, ct);
   const float k = (float)(4.0 * 3.14159265358979323846 * h->cfg.bjerrum);
 #define LBM_CHARGE_S(SS)                                                        \
-  LBM_DISPATCH_WS(h, (k_charge<SS, W_, ST_><<<nb, 256, 0, h->st>>>(              \
+  LBM_DISPATCH_WS(h, (k_charge<SS, W_, ST_><<<nb, ct, 0, h->st>>>(               \
                          h->f[h->cur], h->links, h->wsrc, h->ps.src, h->ps.part, \
                          h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,                  \
                          as_f4(h->valence), as_f4(h->nref), k)))

@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "lbm_internal.cuh"
@@ -106,12 +107,11 @@ __global__ void __launch_bounds__(512) k_fft_fwd(const float* __restrict__ r,
 }
 
 // Inverse 2-D FFT of the correction of each fluid plane, scaled by
-// 1/(nx ny), and the update psi_out = psi_in + round(e).
+// 1/(nx ny), and the in-place update psi += round(e).
 __global__ void __launch_bounds__(512) k_fft_inv_apply(const float2* __restrict__ ehat,
                                                        const int* __restrict__ planes,
                                                        SpecArgs a,
-                                                       const int64_t* __restrict__ psi_in,
-                                                       int64_t* __restrict__ psi_out) {
+                                                       int64_t* psi) {
   extern __shared__ float2 buf[];
   const int z = planes[blockIdx.x];
   const int nxy = a.nx * a.ny;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(512) k_fft_inv_apply(const float2* __restrict_
   const int64_t base = (int64_t)z * nxy;
   for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
     const float e = buf[k].x * scale;
-    psi_out[base + k] = psi_in[base + k] + llrintf(e * PSI_SCALE_F);
+    psi[base + k] += llrintf(e * PSI_SCALE_F);  // in place: one cell per thread
   }
 }
 
@@ -525,7 +525,7 @@ SpecArgs args_of(const SpectralPlan* s) {
   return a;
 }
 
-cudaError_t spec_residual(lbm_t* h) {
+cudaError_t spec_residual(lbm_t* h, bool to_host = true) {
   SpectralPlan* s = h->spec;
   Poisson& P = h->ps;
   cudaError_t e = cudaMemsetAsync(P.dsum + 1, 0, 2 * sizeof(double), h->st);
@@ -535,7 +535,17 @@ cudaError_t spec_residual(lbm_t* h) {
                                       P.dsum, s->nx, s->ny, s->nz, s->lgx, s->lgx + s->lgy);
   ++h->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (!to_host) return cudaSuccess;
   return cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+}
+
+cudaError_t spec_means(lbm_t* h) {
+  SpectralPlan* s = h->spec;
+  Poisson& P = h->ps;
+  k_plane_sums<<<s->nz, 256, 0, h->st>>>(P.src, s->psum, s->nx * s->ny);
+  k_run_means<<<1, 256, 0, h->st>>>(s->psum, s->runs, s->nruns, s->mean_z, s->nz, s->nx * s->ny);
+  h->launches += 2;
+  return cudaGetLastError();
 }
 
 cudaError_t spec_apply(lbm_t* h) {
@@ -546,12 +556,9 @@ cudaError_t spec_apply(lbm_t* h) {
   k_fft_fwd<<<s->nplanes, threads, s->smem, h->st>>>(s->r, s->spec, s->planes, a);
   dim3 g(nblk((int64_t)s->nx * s->ny, ZP), s->nruns);
   k_zsolve<<<g, 128, s->zsmem, h->st>>>(s->spec, s->runs, a);
-  k_fft_inv_apply<<<s->nplanes, threads, s->smem, h->st>>>(s->spec, s->planes, a, P.psi[P.cur],
-                                                          P.psi[P.cur ^ 1]);
+  k_fft_inv_apply<<<s->nplanes, threads, s->smem, h->st>>>(s->spec, s->planes, a, P.psi[P.cur]);
   h->launches += 3;
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) P.cur ^= 1;
-  return e;
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -559,10 +566,7 @@ cudaError_t spec_apply(lbm_t* h) {
 lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* rel_res) {
   SpectralPlan* s = h->spec;
   Poisson& P = h->ps;
-  k_plane_sums<<<s->nz, 256, 0, h->st>>>(P.src, s->psum, s->nx * s->ny);
-  k_run_means<<<1, 256, 0, h->st>>>(s->psum, s->runs, s->nruns, s->mean_z, s->nz, s->nx * s->ny);
-  h->launches += 2;
-  LBM_CUDA_TRY(h, cudaGetLastError());
+  LBM_CUDA_TRY(h, spec_means(h));
   LBM_CUDA_TRY(h, spec_residual(h));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   double rn = sqrt(P.hsum[1]), sn = sqrt(P.hsum[2]);
@@ -584,6 +588,203 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
   if (rel_res) *rel_res = sn > 0.0 ? rn / sn : 0.0;
   if (!conv()) {
     h->err = "Poisson solve did not reach the tolerance within the iteration cap";
+    return LBM_ENOCONV;
+  }
+  return LBM_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Whole-step CUDA graphs.  One graph per population parity holds a full time
+// step: charge density, run means, residual, a device-side while loop
+// (conditional graph node) of spectral applications + residual + test, and
+// the fused stream/collide.  Steps are replayed back to back with no host
+// round trip; the test kernel keeps the per-step status on the device.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct GraphStatus {
+  uint32_t step;       // time step (read by the stream/collide kernel)
+  int iters;           // Poisson iterations of the current step
+  long long total;     // iterations summed over replayed steps
+  int fails;           // steps whose solve stopped at the iteration cap
+  int pad;
+  double rel;          // final relative residual of the last step
+};
+
+// Convergence test of the last residual (one thread): sets the loop
+// condition of the enclosing conditional node.
+__global__ void k_graph_check(const double* __restrict__ dsum, GraphStatus* st, double tol,
+                              double floor2, int maxit, int first,
+                              cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double rn2 = dsum[1], sn2 = dsum[2];
+  const bool conv = rn2 <= tol * tol * sn2 || rn2 <= floor2;
+  if (first) {
+    st->iters = 0;
+    st->step += 1;
+  } else {
+    st->iters += 1;
+  }
+  const bool more = !conv && st->iters < maxit;
+  cudaGraphSetConditional(cond, more ? 1u : 0u);
+  st->rel = sn2 > 0.0 ? sqrt(rn2 / sn2) : 0.0;
+  if (!more) {
+    st->total += st->iters;
+    if (!conv) st->fails += 1;
+  }
+}
+
+}  // namespace
+
+void spectral_graph_free(lbm_t* h) {
+  for (int k = 0; k < 2; ++k) {
+    if (h->step_graph[k]) cudaGraphExecDestroy(h->step_graph[k]);
+    h->step_graph[k] = nullptr;
+  }
+}
+
+namespace {
+
+lbm_status build_step_graph(lbm_t* h, int parity) {
+  Poisson& P = h->ps;
+  const int saved_cur = h->cur;
+  h->cur = parity;
+  GraphStatus* gs = reinterpret_cast<GraphStatus*>(h->gstatus);
+  const double tol = h->cfg.poisson_tol;
+  const double floor2 = 4.0 * (double)h->nfluid;
+  const int maxit = h->cfg.poisson_maxit;
+  cudaGraph_t G = nullptr;
+  LBM_CUDA_TRY(h, cudaGraphCreate(&G, 0));
+  cudaGraphConditionalHandle cond;
+  LBM_CUDA_TRY(h, cudaGraphConditionalHandleCreate(&cond, G, 0, cudaGraphCondAssignDefault));
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  const int64_t l0 = h->launches;
+  // part A: source, means, first residual and test
+  LBM_CUDA_TRY(h, cudaStreamBeginCaptureToGraph(h->st, G, nullptr, nullptr, 0, mode));
+  cudaError_t e = cudaMemsetAsync(P.dsum, 0, 3 * sizeof(double), h->st);
+  if (e == cudaSuccess) e = launch_charge(h);
+  if (e == cudaSuccess) e = spec_means(h);
+  if (e == cudaSuccess) e = spec_residual(h, false);
+  if (e == cudaSuccess) {
+    k_graph_check<<<1, 32, 0, h->st>>>(P.dsum, gs, tol, floor2, maxit, 1, cond);
+    ++h->launches;
+    e = cudaGetLastError();
+  }
+  std::vector<cudaGraphNode_t> deps;
+  if (e == cudaSuccess) {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    e = cudaStreamGetCaptureInfo(h->st, &cs, nullptr, nullptr, &d, nullptr, &nd);
+    if (e == cudaSuccess) deps.assign(d, d + nd);
+  }
+  cudaGraph_t Gc = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(h->st, &Gc);
+  if (e == cudaSuccess) e = e2;
+  // the conditional while node and its body
+  cudaGraphNode_t cnode = nullptr;
+  cudaGraph_t body = nullptr;
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&cnode, G, deps.data(), nullptr, deps.size(), &cp);
+    if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+  }
+  const int64_t l1 = h->launches;
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, mode);
+    if (e == cudaSuccess) {
+      cudaError_t eb = spec_apply(h);
+      if (eb == cudaSuccess) eb = spec_residual(h, false);
+      if (eb == cudaSuccess) {
+        k_graph_check<<<1, 32, 0, h->st>>>(P.dsum, gs, tol, floor2, maxit, 0, cond);
+        ++h->launches;
+        eb = cudaGetLastError();
+      }
+      cudaGraph_t bb = nullptr;
+      e = cudaStreamEndCapture(h->st, &bb);
+      if (e == cudaSuccess) e = eb;
+    }
+  }
+  const int64_t l2 = h->launches;
+  // part B: fused stream/collide after the loop
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCaptureToGraph(h->st, G, &cnode, nullptr, 1, mode);
+    if (e == cudaSuccess) {
+      cudaError_t eb = launch_stream_collide(h);
+      cudaGraph_t gg = nullptr;
+      e = cudaStreamEndCapture(h->st, &gg);
+      if (e == cudaSuccess) e = eb;
+    }
+  }
+  const int64_t l3 = h->launches;
+  h->launches = l0;
+  h->cur = saved_cur;
+  cudaGraphExec_t ex = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, G, 0);
+  cudaGraphDestroy(G);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->err = std::string("step graph construction failed: ") + cudaGetErrorString(e);
+    return LBM_ECUDA;
+  }
+  h->step_graph[parity] = ex;
+  h->graph_kernels_fixed = (int)((l1 - l0) + (l3 - l2));
+  h->graph_kernels_iter = (int)(l2 - l1);
+  return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
+  if (!h->gstatus) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(GraphStatus)) != cudaSuccess) {
+      cudaGetLastError();
+      h->err = "graph status allocation failed";
+      return LBM_ENOMEM;
+    }
+    GraphStatus z = {};
+    z.step = (uint32_t)h->tstep;
+    cudaMemcpy(p, &z, sizeof z, cudaMemcpyHostToDevice);
+    h->gstatus = p;
+    if (cudaMallocHost(&h->hstatus, sizeof(GraphStatus)) != cudaSuccess) {
+      h->err = "pinned allocation failed";
+      return LBM_ENOMEM;
+    }
+  }
+  for (int k = 0; k < 2; ++k)
+    if (!h->step_graph[k]) {
+      lbm_status s = build_step_graph(h, k);
+      if (s != LBM_OK) return s;
+    }
+  GraphStatus* hs = reinterpret_cast<GraphStatus*>(h->hstatus);
+  // status before, to count this call's iterations and failures
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(hs, h->gstatus, sizeof(GraphStatus), cudaMemcpyDeviceToHost, h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  const long long total0 = hs->total;
+  const int fails0 = hs->fails;
+  for (int k = 0; k < nsteps; ++k) {
+    LBM_CUDA_TRY(h, cudaGraphLaunch(h->step_graph[h->cur], h->st));
+    h->cur ^= 1;
+    ++h->tstep;
+  }
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(hs, h->gstatus, sizeof(GraphStatus), cudaMemcpyDeviceToHost, h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  const long long iters = hs->total - total0;
+  h->launches += (int64_t)nsteps * h->graph_kernels_fixed + iters * h->graph_kernels_iter;
+  h->t_cnt[1] += iters;
+  h->t_cnt[0] += nsteps;
+  h->t_cnt[2] += nsteps;
+  h->last_iters = hs->iters;
+  h->last_res = hs->rel;
+  h->psi_valid = true;
+  if (hs->fails != fails0) {
+    h->err = "a Poisson solve inside the step graph stopped at the iteration cap";
     return LBM_ENOCONV;
   }
   return LBM_OK;

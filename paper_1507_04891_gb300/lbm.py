@@ -20,6 +20,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOCONV, LBM_EUNSTABLE, LBM_ETIME
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
                 4: "LBM_ENOCONV", 5: "LBM_EUNSTABLE", 6: "LBM_ETIMEOUT"}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+LBM_FLAG_STEP_GRAPH = 1
 POISSON = {"mg": 0, "sor": 1, "fft": 2}
 
 # every symbol include/lbm.h declares
@@ -27,7 +28,8 @@ EXPORTED = [
     "lbm_config_default", "lbm_create", "lbm_destroy", "lbm_set_walls", "lbm_set_species",
     "lbm_step", "lbm_synchronize", "lbm_get_moments", "lbm_get_populations",
     "lbm_get_potential", "lbm_solve_poisson", "lbm_diagnostics", "lbm_get_state",
-    "lbm_set_state", "lbm_set_timing", "lbm_get_timing", "lbm_num_nodes", "lbm_state_len", "lbm_stream", "lbm_last_error",
+    "lbm_set_state", "lbm_set_timing", "lbm_get_timing", "lbm_num_nodes",
+    "lbm_create_stack", "lbm_instance_z0", "lbm_set_plane_omega_drag", "lbm_autotune", "lbm_state_len", "lbm_stream", "lbm_last_error",
 ]
 
 
@@ -39,7 +41,7 @@ class LbmConfig(ctypes.Structure):
         ("bjerrum", ctypes.c_double), ("e_ext", ctypes.c_double * 3),
         ("storage", ctypes.c_int), ("poisson", ctypes.c_int),
         ("poisson_tol", ctypes.c_double), ("poisson_maxit", ctypes.c_int),
-        ("device", ctypes.c_int),
+        ("device", ctypes.c_int), ("flags", ctypes.c_int),
     ]
 
 
@@ -95,6 +97,14 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_set_timing.restype = I
     lib.lbm_get_timing.argtypes = [P, P]
     lib.lbm_get_timing.restype = I
+    lib.lbm_create_stack.argtypes = [I, ctypes.POINTER(LbmConfig), ctypes.POINTER(P)]
+    lib.lbm_create_stack.restype = I
+    lib.lbm_instance_z0.argtypes = [P, I]
+    lib.lbm_instance_z0.restype = I
+    lib.lbm_set_plane_omega_drag.argtypes = [P, P]
+    lib.lbm_set_plane_omega_drag.restype = I
+    lib.lbm_autotune.argtypes = [P, P]
+    lib.lbm_autotune.restype = I
     lib.lbm_num_nodes.argtypes = [P]
     lib.lbm_num_nodes.restype = ctypes.c_int64
     lib.lbm_state_len.argtypes = [P]
@@ -105,6 +115,23 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
+
+
+def make_config(nx, ny, nz, nspecies, omega_visc=1.0, omega_drag=1.0, bjerrum=0.0,
+                e_ext=(0.0, 0.0, 0.0), storage="fp32", poisson="mg", poisson_tol=1e-8,
+                poisson_maxit=200, device=0, step_graph=False):
+    lib = load_library()
+    cfg = LbmConfig()
+    lib.lbm_config_default(ctypes.byref(cfg))
+    cfg.nx, cfg.ny, cfg.nz, cfg.nspecies = int(nx), int(ny), int(nz), int(nspecies)
+    cfg.omega_visc, cfg.omega_drag, cfg.bjerrum = float(omega_visc), float(omega_drag), float(bjerrum)
+    for d in range(3):
+        cfg.e_ext[d] = float(e_ext[d])
+    cfg.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    cfg.poisson = POISSON[poisson] if isinstance(poisson, str) else int(poisson)
+    cfg.poisson_tol, cfg.poisson_maxit, cfg.device = float(poisson_tol), int(poisson_maxit), int(device)
+    cfg.flags = LBM_FLAG_STEP_GRAPH if step_graph else 0
+    return cfg
 
 
 def _ptr(a):
@@ -123,26 +150,52 @@ class Lattice:
 
     def __init__(self, nx, ny, nz, nspecies, omega_visc=1.0, omega_drag=1.0,
                  bjerrum=0.0, e_ext=(0.0, 0.0, 0.0), storage="fp32", poisson="mg",
-                 poisson_tol=1e-8, poisson_maxit=200, device=0):
+                 poisson_tol=1e-8, poisson_maxit=200, device=0, step_graph=False,
+                 _stack=None):
         self._lib = load_library()
-        cfg = LbmConfig()
-        self._lib.lbm_config_default(ctypes.byref(cfg))
-        cfg.nx, cfg.ny, cfg.nz, cfg.nspecies = int(nx), int(ny), int(nz), int(nspecies)
-        cfg.omega_visc, cfg.omega_drag, cfg.bjerrum = float(omega_visc), float(omega_drag), float(bjerrum)
-        for d in range(3):
-            cfg.e_ext[d] = float(e_ext[d])
-        cfg.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
-        cfg.poisson = POISSON[poisson] if isinstance(poisson, str) else int(poisson)
-        cfg.poisson_tol, cfg.poisson_maxit, cfg.device = float(poisson_tol), int(poisson_maxit), int(device)
+        cfg = make_config(nx, ny, nz, nspecies, omega_visc, omega_drag, bjerrum, e_ext, storage,
+                          poisson, poisson_tol, poisson_maxit, device, step_graph)
         self.cfg = cfg
-        self.shape = (int(nz), int(ny), int(nx))
         self.S = int(nspecies)
         h = ctypes.c_void_p()
-        st = self._lib.lbm_create(ctypes.byref(cfg), ctypes.byref(h))
+        if _stack is None:
+            st = self._lib.lbm_create(ctypes.byref(cfg), ctypes.byref(h))
+        else:
+            arr = (LbmConfig * len(_stack))(*_stack)
+            st = self._lib.lbm_create_stack(len(_stack), arr, ctypes.byref(h))
+            nz = sum(c.nz for c in _stack)
         if st != LBM_OK:
             raise LBMError(st, self._lib.lbm_last_error(None).decode())
+        self.shape = (int(nz), int(ny), int(nx))
         self.h = h
         self.N = int(self._lib.lbm_num_nodes(h))
+
+    @classmethod
+    def create_stack(cls, nx, ny, nzs, omega_drags, nspecies, **kw):
+        """lbm_create_stack: instances of extents nzs[i] and drag
+        frequencies omega_drags[i] stacked along z."""
+        cfgs = [make_config(nx, ny, nz_i, nspecies, kw.get("omega_visc", 1.0), od,
+                            kw.get("bjerrum", 0.0), kw.get("e_ext", (0.0, 0.0, 0.0)),
+                            kw.get("storage", "fp32"), kw.get("poisson", "fft"),
+                            kw.get("poisson_tol", 1e-8), kw.get("poisson_maxit", 200),
+                            kw.get("device", 0), kw.get("step_graph", False))
+                for nz_i, od in zip(nzs, omega_drags)]
+        return cls(nx, ny, sum(nzs), nspecies, _stack=cfgs)
+
+    def instance_z0(self, i):
+        return int(self._lib.lbm_instance_z0(self.h, int(i)))
+
+    def set_plane_omega_drag(self, omega):
+        om = None if omega is None else np.ascontiguousarray(omega, dtype=np.float64)
+        if om is not None and om.shape != (self.shape[0],):
+            raise ValueError("one omega per z-plane")
+        self._check(self._lib.lbm_set_plane_omega_drag(self.h, _ptr(om)))
+
+    def autotune(self):
+        out = np.zeros(4)
+        self._check(self._lib.lbm_autotune(self.h, _ptr(out)))
+        return {"collide_threads": int(out[0]), "collide_ms": out[1],
+                "charge_threads": int(out[2]), "charge_ms": out[3]}
 
     # -- helpers -----------------------------------------------------------
     def _check(self, st, allow=()):
@@ -272,3 +325,26 @@ def from_workload(wl, storage="fp32", poisson="mg", poisson_tol=1e-8, poisson_ma
         u0 = None if wl.u0 is None else wl.u0[s]
         lat.set_species(s, wl.mass[s], wl.valence[s], wl.n0[s], u0)
     return lat
+
+
+def stack_slits(instances, storage="fp16", step_graph=True, poisson_tol=1e-8, device=0):
+    """Batched independent slit channels (workloads.slit instances sharing
+    nx, ny, omega_visc, l_B and the applied field) stacked along z in one
+    lattice: each instance keeps its own walls, wall charge and drag
+    frequency.  Returns (lattice, list of first planes)."""
+    nx = instances[0].shape[2]
+    ny = instances[0].shape[1]
+    nzs = [w.shape[0] for w in instances]
+    ods = [omega_drag_for_schmidt(w.omega_visc, w.schmidt) for w in instances]
+    w0 = instances[0]
+    lat = Lattice.create_stack(nx, ny, nzs, ods, w0.nspecies, omega_visc=w0.omega_visc,
+                               bjerrum=w0.bjerrum, e_ext=w0.e_ext, storage=storage, poisson="fft",
+                               poisson_tol=poisson_tol, device=device, step_graph=step_graph)
+    solid = np.concatenate([w.solid for w in instances], axis=0)
+    sigma = np.concatenate([w.sigma for w in instances], axis=0)
+    lat.set_walls(solid, sigma)
+    for s in range(w0.nspecies):
+        n0 = np.concatenate([np.where(w.solid, 1.0, w.n0[s]) for w in instances], axis=0)
+        lat.set_species(s, w0.mass[s], w0.valence[s], n0)
+    z0 = [lat.instance_z0(i) for i in range(len(instances))]
+    return lat, z0
