@@ -111,6 +111,35 @@ lbm_status lbm_set_plane_omega_drag(lbm_t* h, const double* omega);
  * times in ms: [collide_threads, collide_ms, charge_threads, charge_ms].  */
 lbm_status lbm_autotune(lbm_t* h, double* out);
 
+/* Learned initial guess of the Poisson solve.  The paper has no
+ * counterpart: this is an addition of this library.  A small periodic 3-D
+ * convolutional network (two 3x3x3 layers, `hidden` channels, tanh) maps
+ * the normalised residual of the warm-start potential and the fluid mask
+ * to a correction of psi.  The solver applies it before iterating, keeps it
+ * only if the residual drops, and always iterates to the same tolerance.
+ *   lbm_nn_init     random initialisation (seeded), hidden in 1..16;
+ *                   requires l_B > 0 and host-driven steps
+ *   lbm_nn_collect  store the initial residual of each following solve in
+ *                   a ring of `capacity` fields (0 stops collecting)
+ *   lbm_nn_train    `epochs` passes of Adam (rate lr) over the collected
+ *                   fields on the GPU; losses[e] (may be NULL) receives the
+ *                   mean loss ||r - A dpsi||^2 / ||r||^2 of each epoch
+ *   lbm_nn_use      enable / disable the guess (FP16 inference)
+ *   lbm_nn_params   copy the FP32 parameters out (get) or in (set), either
+ *                   may be NULL; *nparams receives their count
+ *   lbm_nn_loss_grad  loss and parameter gradient (FP32) on a given
+ *                   normalised residual field x0 (N floats, host)
+ *   lbm_nn_stats    out[0] guesses tried, out[1] kept, out[2] mean residual
+ *                   ratio after/before of the kept ones, out[3] collected
+ *                   fields, out[4] parameter count                        */
+lbm_status lbm_nn_init(lbm_t* h, int hidden, uint64_t seed);
+lbm_status lbm_nn_collect(lbm_t* h, int capacity);
+lbm_status lbm_nn_train(lbm_t* h, int epochs, double lr, double* losses);
+lbm_status lbm_nn_use(lbm_t* h, int enable);
+lbm_status lbm_nn_params(lbm_t* h, float* get, const float* set, int* nparams);
+lbm_status lbm_nn_loss_grad(lbm_t* h, const float* x0, double* loss, float* grad);
+lbm_status lbm_nn_stats(lbm_t* h, double* out);
+
 /* Releases every device buffer of h.  NULL is accepted.                  */
 void lbm_destroy(lbm_t* h);
 

@@ -234,6 +234,7 @@ void lbm_destroy(lbm_t* h) {
   spectral_graph_free(h);
   poisson_free(h);
   spectral_free(h);
+  nn_free(h);
   cudaFree(h->omega_drag_z);
   cudaFree(h->gstatus);
   if (h->hstatus) cudaFreeHost(h->hstatus);
@@ -697,6 +698,55 @@ lbm_status lbm_autotune(lbm_t* h, double* out) {
     out[2] = tq;
     out[3] = best_q < 1e29 ? best_q : 0.0;
   }
+  return LBM_OK;
+}
+
+lbm_status lbm_nn_init(lbm_t* h, int hidden, uint64_t seed) {
+  if (!h) return LBM_EINVAL;
+  if (!(h->cfg.bjerrum > 0.0)) return fail(h, LBM_EINVAL, "requires bjerrum > 0");
+  if (h->cfg.flags & LBM_FLAG_STEP_GRAPH)
+    return fail(h, LBM_EINVAL, "the learned guess runs in host-driven steps only");
+  cudaSetDevice(h->dev);
+  h->st = h->own;
+  return nn_init(h, hidden, seed);
+}
+
+lbm_status lbm_nn_collect(lbm_t* h, int capacity) {
+  if (!h) return LBM_EINVAL;
+  cudaSetDevice(h->dev);
+  return nn_collect(h, capacity);
+}
+
+lbm_status lbm_nn_train(lbm_t* h, int epochs, double lr, double* losses) {
+  if (!h) return LBM_EINVAL;
+  if (epochs < 0 || !(lr > 0.0)) return fail(h, LBM_EINVAL, "epochs >= 0 and lr > 0 required");
+  cudaSetDevice(h->dev);
+  h->st = h->own;
+  return nn_train(h, epochs, lr, losses);
+}
+
+lbm_status lbm_nn_use(lbm_t* h, int enable) {
+  if (!h) return LBM_EINVAL;
+  return nn_set_use(h, enable);
+}
+
+lbm_status lbm_nn_params(lbm_t* h, float* get, const float* set, int* nparams) {
+  if (!h) return LBM_EINVAL;
+  cudaSetDevice(h->dev);
+  h->st = h->own;
+  return nn_params(h, get, set, nparams);
+}
+
+lbm_status lbm_nn_loss_grad(lbm_t* h, const float* x0, double* loss, float* grad) {
+  if (!h || !x0 || !loss) return LBM_EINVAL;
+  cudaSetDevice(h->dev);
+  h->st = h->own;
+  return nn_loss_grad_host(h, x0, loss, grad);
+}
+
+lbm_status lbm_nn_stats(lbm_t* h, double* out) {
+  if (!h || !out) return LBM_EINVAL;
+  nn_stats(h, out);
   return LBM_OK;
 }
 

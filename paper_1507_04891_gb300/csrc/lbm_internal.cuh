@@ -88,6 +88,7 @@ struct Poisson {
 
 namespace lbm_gb300 {
 struct SpectralPlan;
+struct NNet;
 }
 
 struct lbm {
@@ -112,6 +113,7 @@ struct lbm {
   int64_t nfluid = 0;
   lbm_gb300::Poisson ps;
   lbm_gb300::SpectralPlan* spec = nullptr;  // spectral Poisson plan (LBM_POISSON_FFT)
+  lbm_gb300::NNet* nn = nullptr;            // learned Poisson initial guess
   bool psi_valid = false;
   double* dred = nullptr;   // diagnostics reduction buffer (device)
   double* hred = nullptr;   // pinned mirror
@@ -175,6 +177,23 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters,
 // device status once at the end.
 lbm_status spectral_graph_steps(lbm_t* h, int nsteps);
 void spectral_graph_free(lbm_t* h);
+
+// ---- lbm_nn.cu ----
+lbm_status nn_init(lbm_t* h, int hidden, uint64_t seed);
+void nn_free(lbm_t* h);
+lbm_status nn_collect(lbm_t* h, int capacity);
+lbm_status nn_train(lbm_t* h, int epochs, double lr, double* losses);
+lbm_status nn_loss_grad_host(lbm_t* h, const float* x0, double* loss, float* grad);
+lbm_status nn_params(lbm_t* h, float* get, const float* set, int* np);
+// Solver hooks: given the initial FP32 residual (planes [zlo, zlo+nzb)),
+// stores it for training and/or applies the learned correction to psi.
+lbm_status nn_before_solve(lbm_t* h, const float* r, int zlo, int nzb, double rms,
+                           bool* applied, float** dpsi);
+lbm_status nn_revert(lbm_t* h, const float* dpsi);
+void nn_record(lbm_t* h, double ratio);
+bool nn_active(const lbm_t* h);
+void nn_stats(const lbm_t* h, double* out);
+lbm_status nn_set_use(lbm_t* h, int enable);
 
 }  // namespace lbm_gb300
 

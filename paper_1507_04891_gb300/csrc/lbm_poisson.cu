@@ -1059,6 +1059,32 @@ lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
   LBM_CUDA_TRY(h, residual_launch(h));
   lbm_status s = residual_read(h, tol, &rel, &done);
   if (s != LBM_OK) return s;
+  if (!done && nn_active(h)) {
+    // learned initial guess: apply, keep it only if the residual drops
+    const double rn = sqrt(P.hsum[1]) * PSI_INV_SCALE;
+    bool applied = false;
+    float* dpsi = nullptr;
+    s = nn_before_solve(h, P.lev[0].rhs, P.zlo, P.nzb, rn / sqrt((double)h->nfluid), &applied, &dpsi);
+    if (s != LBM_OK) return s;
+    if (applied) {
+      double rel_nn = 0.0;
+      bool done_nn = false;
+      LBM_CUDA_TRY(h, residual_launch(h));
+      s = residual_read(h, tol, &rel_nn, &done_nn);
+      if (s != LBM_OK) return s;
+      if (rel_nn < rel) {
+        nn_record(h, rel_nn / rel);
+        rel = rel_nn;
+        done = done_nn;
+      } else {
+        s = nn_revert(h, dpsi);
+        if (s != LBM_OK) return s;
+        LBM_CUDA_TRY(h, residual_launch(h));
+        s = residual_read(h, tol, &rel, &done);
+        if (s != LBM_OK) return s;
+      }
+    }
+  }
   rel0 = rel;
   int it = 0;
   if (h->cfg.poisson == LBM_POISSON_MG) {

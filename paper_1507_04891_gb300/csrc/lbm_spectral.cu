@@ -571,6 +571,28 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   double rn = sqrt(P.hsum[1]), sn = sqrt(P.hsum[2]);
   auto conv = [&]() { return rn <= tol * sn || rn <= 2.0 * sqrt((double)h->nfluid); };
+  if (!conv() && nn_active(h)) {
+    bool applied = false;
+    float* dpsi = nullptr;
+    lbm_status st = nn_before_solve(h, s->r, 0, s->nz, rn * PSI_INV_SCALE / sqrt((double)h->nfluid),
+                                    &applied, &dpsi);
+    if (st != LBM_OK) return st;
+    if (applied) {
+      const double rn_old = rn;
+      LBM_CUDA_TRY(h, spec_residual(h));
+      LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+      rn = sqrt(P.hsum[1]);
+      if (rn < rn_old) {
+        nn_record(h, rn / rn_old);
+      } else {
+        st = nn_revert(h, dpsi);
+        if (st != LBM_OK) return st;
+        LBM_CUDA_TRY(h, spec_residual(h));
+        LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+        rn = sqrt(P.hsum[1]);
+      }
+    }
+  }
   int it = 0;
   while (!conv() && it < maxit) {
     LBM_CUDA_TRY(h, spec_apply(h));

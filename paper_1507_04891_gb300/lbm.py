@@ -29,7 +29,9 @@ EXPORTED = [
     "lbm_step", "lbm_synchronize", "lbm_get_moments", "lbm_get_populations",
     "lbm_get_potential", "lbm_solve_poisson", "lbm_diagnostics", "lbm_get_state",
     "lbm_set_state", "lbm_set_timing", "lbm_get_timing", "lbm_num_nodes",
-    "lbm_create_stack", "lbm_instance_z0", "lbm_set_plane_omega_drag", "lbm_autotune", "lbm_state_len", "lbm_stream", "lbm_last_error",
+    "lbm_create_stack", "lbm_instance_z0", "lbm_set_plane_omega_drag", "lbm_autotune",
+    "lbm_nn_init", "lbm_nn_collect", "lbm_nn_train", "lbm_nn_use", "lbm_nn_params",
+    "lbm_nn_loss_grad", "lbm_nn_stats", "lbm_state_len", "lbm_stream", "lbm_last_error",
 ]
 
 
@@ -105,6 +107,20 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_set_plane_omega_drag.restype = I
     lib.lbm_autotune.argtypes = [P, P]
     lib.lbm_autotune.restype = I
+    lib.lbm_nn_init.argtypes = [P, I, ctypes.c_uint64]
+    lib.lbm_nn_init.restype = I
+    lib.lbm_nn_collect.argtypes = [P, I]
+    lib.lbm_nn_collect.restype = I
+    lib.lbm_nn_train.argtypes = [P, I, D, P]
+    lib.lbm_nn_train.restype = I
+    lib.lbm_nn_use.argtypes = [P, I]
+    lib.lbm_nn_use.restype = I
+    lib.lbm_nn_params.argtypes = [P, P, P, ctypes.POINTER(I)]
+    lib.lbm_nn_params.restype = I
+    lib.lbm_nn_loss_grad.argtypes = [P, P, ctypes.POINTER(D), P]
+    lib.lbm_nn_loss_grad.restype = I
+    lib.lbm_nn_stats.argtypes = [P, P]
+    lib.lbm_nn_stats.restype = I
     lib.lbm_num_nodes.argtypes = [P]
     lib.lbm_num_nodes.restype = ctypes.c_int64
     lib.lbm_state_len.argtypes = [P]
@@ -190,6 +206,46 @@ class Lattice:
         if om is not None and om.shape != (self.shape[0],):
             raise ValueError("one omega per z-plane")
         self._check(self._lib.lbm_set_plane_omega_drag(self.h, _ptr(om)))
+
+    # -- learned Poisson initial guess --------------------------------------
+    def nn_init(self, hidden=8, seed=1):
+        self._check(self._lib.lbm_nn_init(self.h, int(hidden), int(seed)))
+
+    def nn_collect(self, capacity):
+        self._check(self._lib.lbm_nn_collect(self.h, int(capacity)))
+
+    def nn_train(self, epochs, lr=1e-2):
+        losses = np.zeros(max(1, int(epochs)))
+        self._check(self._lib.lbm_nn_train(self.h, int(epochs), float(lr), _ptr(losses)))
+        return losses[:int(epochs)]
+
+    def nn_use(self, enable=True):
+        self._check(self._lib.lbm_nn_use(self.h, int(bool(enable))))
+
+    def nn_params(self, set_to=None):
+        n = ctypes.c_int(0)
+        self._check(self._lib.lbm_nn_params(self.h, None, None, ctypes.byref(n)))
+        out = np.empty(n.value, dtype=np.float32)
+        src = None if set_to is None else np.ascontiguousarray(set_to, dtype=np.float32)
+        self._check(self._lib.lbm_nn_params(self.h, _ptr(out), _ptr(src), ctypes.byref(n)))
+        return out
+
+    def nn_loss_grad(self, x0, grad=True):
+        x0 = np.ascontiguousarray(x0, dtype=np.float32)
+        if x0.shape != self.shape:
+            raise ValueError("x0 must have the lattice shape")
+        loss = ctypes.c_double(0.0)
+        n = ctypes.c_int(0)
+        self._check(self._lib.lbm_nn_params(self.h, None, None, ctypes.byref(n)))
+        g = np.zeros(n.value, dtype=np.float32) if grad else None
+        self._check(self._lib.lbm_nn_loss_grad(self.h, _ptr(x0), ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def nn_stats(self):
+        out = np.zeros(5)
+        self._check(self._lib.lbm_nn_stats(self.h, _ptr(out)))
+        return {"tried": int(out[0]), "kept": int(out[1]), "mean_ratio": out[2],
+                "collected": int(out[3]), "nparams": int(out[4])}
 
     def autotune(self):
         out = np.zeros(4)
