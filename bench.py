@@ -219,10 +219,10 @@ def run_ours(args, rank, world, local):
     od = lbm.omega_drag_for_schmidt(wl.omega_visc, args.schmidt)
     warm = max(3, args.warmup)
 
-    def make(poisson):
+    def make(poisson, graph=False):
         return lbm.Lattice(n, n, n, S, omega_visc=wl.omega_visc, omega_drag=od, bjerrum=wl.bjerrum,
                            storage=args.storage, poisson=poisson, poisson_tol=1e-8,
-                           poisson_maxit=500, device=local)
+                           poisson_maxit=500, device=local, step_graph=graph)
 
     def barrier():
         if world > 1:
@@ -238,10 +238,10 @@ def run_ours(args, rank, world, local):
             return float(tt.item())
         return x
 
-    def timed(poisson, sample_clocks):
+    def timed(poisson, sample_clocks, graph=False):
         """W warm-up steps, then K steps timed with CUDA events on the
         library's stream; phase times from the library's own events."""
-        lat = make(poisson)
+        lat = make(poisson, graph)
         for s in range(S):
             lat.set_species(s, 1.0, wl.valence[s], wl.n0[s])
         stream = torch.cuda.ExternalStream(lat.stream, device=torch.device("cuda", local))
@@ -282,6 +282,16 @@ def run_ours(args, rank, world, local):
         alt = {"poisson": "mg", "value": world * S * N * args.steps / (ta / 1e3) / 1e6,
                "ms_per_step": ta / args.steps, "poisson_iters_per_step": tma["poisson_iters"] / args.steps,
                "poisson_ms_per_step": tma["poisson_ms"] / args.steps}
+
+    # the same workload with every step one CUDA-graph replay (device-side
+    # Poisson loop, no host round trip between steps)
+    graph_run = None
+    if args.poisson == "fft" and not args.no_alt:
+        tg, tmg, dg, _ = timed("fft", False, graph=True)
+        graph_run = {"value": world * S * N * args.steps / (tg / 1e3) / 1e6,
+                     "ms_per_step": tg / args.steps,
+                     "poisson_iters_per_step": tmg["poisson_iters"] / args.steps,
+                     "poisson_residual_last": dg["poisson_residual"]}
 
     # end to end through the C ABI with host buffers: initial state uploaded
     # from pinned host memory, every step's FP64 diagnostics read back.
@@ -333,6 +343,7 @@ def run_ours(args, rank, world, local):
                     "h2d_bytes_per_step": 8 * S * N / args.steps,
                     "d2h_bytes_per_step": 8 * (S + 7)},
             "poisson_alternative": alt,
+            "step_graph": graph_run,
             "diagnostics": {"mass": list(map(float, diag["mass"])),
                             "poisson_residual_last": diag["poisson_residual"]},
             "cpu_baseline": cpu,

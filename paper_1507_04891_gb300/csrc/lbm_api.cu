@@ -197,14 +197,14 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     s = dev_alloc(h, &h->ps.psi[0], N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.psi[1], N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.src, N);
-    if (s == LBM_OK) s = dev_alloc(h, &h->ps.dsum, 4);
+    if (s == LBM_OK) s = dev_alloc(h, &h->ps.dsum, 1 + 2 * Poisson::NSLOT);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.part, (size_t)((N + 63) / 64));
-    if (s == LBM_OK && cudaMallocHost(&h->ps.hsum, 4 * sizeof(double)) != cudaSuccess)
+    if (s == LBM_OK && cudaMallocHost(&h->ps.hsum, (1 + 2 * Poisson::NSLOT) * sizeof(double)) != cudaSuccess)
       s = LBM_ENOMEM;
     if (s == LBM_OK) {
       cudaMemset(h->ps.psi[0], 0, N * sizeof(int64_t));
       cudaMemset(h->ps.psi[1], 0, N * sizeof(int64_t));
-      cudaMemset(h->ps.dsum, 0, 4 * sizeof(double));
+      cudaMemset(h->ps.dsum, 0, (1 + 2 * Poisson::NSLOT) * sizeof(double));
       s = poisson_setup(h, nullptr);
       if (s == LBM_OK && c.poisson == LBM_POISSON_FFT) s = spectral_setup(h, nullptr);
     }

@@ -64,13 +64,14 @@ struct PoissonLevel {
 };
 
 struct Poisson {
+  static constexpr int NSLOT = 8;  // residual norm slots (batched spectral applications)
   // box of the fine grid inside the lattice: x, y full, z in [zlo, zlo+nzb)
   int zlo = 0, nzb = 0, perz = 1;
   std::vector<PoissonLevel> lev;
   int64_t* psi[2] = {nullptr, nullptr};  // lattice-sized fixed-point buffers
   int cur = 0;
   int64_t* src = nullptr; // 4 pi l_B (rho_e + w) per lattice node (fixed point), no mean removed
-  double* dsum = nullptr; // [0] sum of src over fluid, [1] sum r^2, [2] sum s^2 (fixed-point units)
+  double* dsum = nullptr; // [0] sum of src over fluid, [1 + 2k] sum r^2, [2 + 2k] sum s^2 (fixed-point units), k < NSLOT
   double* hsum = nullptr; // pinned mirror of dsum
   long long* part = nullptr; // per-CTA partial sums of the charge kernel
   int64_t nfluid = 0;
