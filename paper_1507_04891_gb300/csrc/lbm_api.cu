@@ -319,6 +319,63 @@ lbm_status lbm_set_walls(lbm_t* h, const uint8_t* solid, const double* sigma) {
   h->nfluid = nfluid;
   if (h->cfg.bjerrum > 0.0) {
     h->ps.nfluid = nfluid;
+    // connected fluid components over face neighbours (periodic): each is a
+    // separate Poisson domain with its own neutralising mean (the spectral
+    // solver takes the mean per run of fluid planes instead)
+    std::vector<int> lab(h->cfg.poisson == LBM_POISSON_FFT ? 0 : N, -1);
+    std::vector<long long> sizes;
+    std::vector<int64_t> stack;
+    for (int64_t i0 = 0; i0 < (int64_t)lab.size(); ++i0) {
+      if (solid[i0] || lab[i0] >= 0) continue;
+      const int c = (int)sizes.size();
+      long long cnt = 0;
+      lab[i0] = c;
+      stack.push_back(i0);
+      while (!stack.empty()) {
+        const int64_t i = stack.back();
+        stack.pop_back();
+        ++cnt;
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
+        for (auto& d : fd) {
+          const int64_t j = idx(x + d[0], y + d[1], z + d[2]);
+          if (!solid[j] && lab[j] < 0) {
+            lab[j] = c;
+            stack.push_back(j);
+          }
+        }
+      }
+      sizes.push_back(cnt);
+    }
+    Poisson& P = h->ps;
+    cudaFree(P.label);
+    cudaFree(P.comp_sum);
+    cudaFree(P.comp_size);
+    cudaFree(P.comp_mean);
+    P.label = nullptr;
+    P.comp_sum = nullptr;
+    P.comp_size = nullptr;
+    P.comp_mean = nullptr;
+    P.ncomp = (int)sizes.size();
+    if (P.ncomp > 1) {
+      // relabel so that the largest component is 0
+      int big = 0;
+      for (int c = 1; c < P.ncomp; ++c)
+        if (sizes[c] > sizes[big]) big = c;
+      for (int64_t i = 0; i < N; ++i) {
+        if (lab[i] == big) lab[i] = 0;
+        else if (lab[i] == 0) lab[i] = big;
+      }
+      std::swap(sizes[0], sizes[big]);
+      if ((s = dev_alloc(h, &P.label, N)) != LBM_OK) return s;
+      if ((s = dev_alloc(h, &P.comp_sum, P.ncomp)) != LBM_OK) return s;
+      if ((s = dev_alloc(h, &P.comp_size, P.ncomp)) != LBM_OK) return s;
+      if ((s = dev_alloc(h, &P.comp_mean, P.ncomp)) != LBM_OK) return s;
+      for (int64_t i = 0; i < N; ++i)
+        if (lab[i] < 0) lab[i] = 0;  // wall nodes: unused
+      LBM_CUDA_TRY(h, cudaMemcpy(P.label, lab.data(), N * sizeof(int), cudaMemcpyHostToDevice));
+      LBM_CUDA_TRY(h, cudaMemcpy(P.comp_size, sizes.data(), P.ncomp * sizeof(long long),
+                                 cudaMemcpyHostToDevice));
+    }
     s = poisson_setup(h, solid);
     if (s != LBM_OK) return s;
     if (h->cfg.poisson == LBM_POISSON_FFT && (s = spectral_setup(h, solid)) != LBM_OK) return s;
@@ -399,6 +456,8 @@ lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
     if (charged) {
       Phase pc(h, 0);
       LBM_CUDA_TRY(h, cudaMemsetAsync(h->ps.dsum, 0, 3 * sizeof(double), h->st));
+      if (h->ps.comp_sum)
+        LBM_CUDA_TRY(h, cudaMemsetAsync(h->ps.comp_sum, 0, h->ps.ncomp * sizeof(long long), h->st));
       LBM_CUDA_TRY(h, launch_charge(h));
       LBM_CUDA_TRY(h, pc.stop());
       h->t_cnt[0] += 1;
@@ -500,6 +559,8 @@ lbm_status lbm_solve_poisson(lbm_t* h, const double* rho_e, double* psi,
   LBM_CUDA_TRY(h, cudaMemcpyAsync(drho, rho_e, N * sizeof(double), cudaMemcpyHostToDevice, h->st));
   LBM_CUDA_TRY(h, cudaMemcpyAsync(dpsi, psi, N * sizeof(double), cudaMemcpyHostToDevice, h->st));
   LBM_CUDA_TRY(h, cudaMemsetAsync(h->ps.dsum, 0, 3 * sizeof(double), h->st));
+  if (h->ps.comp_sum)
+    LBM_CUDA_TRY(h, cudaMemsetAsync(h->ps.comp_sum, 0, h->ps.ncomp * sizeof(long long), h->st));
   LBM_CUDA_TRY(h, launch_src_from_rho(h, drho));
   LBM_CUDA_TRY(h, launch_psi_from_double(h, dpsi, h->ps.psi[h->ps.cur]));
   int it = 0;

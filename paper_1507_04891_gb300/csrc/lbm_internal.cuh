@@ -74,6 +74,13 @@ struct Poisson {
   double* dsum = nullptr; // [0] sum of src over fluid, [1 + 2k] sum r^2, [2 + 2k] sum s^2 (fixed-point units), k < NSLOT
   double* hsum = nullptr; // pinned mirror of dsum
   long long* part = nullptr; // per-CTA partial sums of the charge kernel
+  // connected fluid components (face neighbours): label per lattice node
+  // (0 = largest component), allocated only when there is more than one
+  int ncomp = 1;
+  int* label = nullptr;
+  unsigned long long* comp_sum = nullptr;  // source sums of components >= 1
+  long long* comp_size = nullptr;           // cells per component
+  long long* comp_mean = nullptr;           // source mean per component (fixed point)
   int64_t nfluid = 0;
   int coarse_sweeps = 16;
   double conv = 0.15;    // measured residual reduction per V-cycle (last solve)

@@ -415,8 +415,8 @@ __global__ void k_init(int s, const double* __restrict__ n0,
 template <int S, bool WALLS, int ST>
 __global__ void __launch_bounds__(256) k_charge(
     const void* fin_v, const uint32_t* links, const int64_t* wsrc, int64_t* src,
-    long long* part, int nx, int ny, int nz, int64_t N, float4 val, float4 nref,
-    float fourpi_lb) {
+    long long* part, const int* label, unsigned long long* comp_sum, int nx, int ny,
+    int nz, int64_t N, float4 val, float4 nref, float fourpi_lb) {
   using T = typename Fmt<ST>::T;
   const T* fin = static_cast<const T*>(fin_v);
   const float vz[4] = {val.x, val.y, val.z, val.w};
@@ -453,7 +453,13 @@ __global__ void __launch_bounds__(256) k_charge(
       if (wsrc) sv += wsrc[i];
     }
     src[i] = sv;
-    acc = sv;
+    // the largest fluid component (label 0) is summed per CTA; the cells of
+    // other components (rare: pockets closed off by walls) add to their own
+    // sum (two's-complement wrap-around keeps the 64-bit sum exact)
+    if (label && fluid && label[i] != 0)
+      atomicAdd(comp_sum + label[i], (unsigned long long)sv);
+    else
+      acc = sv;
   }
   block_partial(acc, part);
 }
@@ -607,7 +613,8 @@ __global__ void k_psi_from_double(const double* in, int64_t* psi,
 
 __global__ void __launch_bounds__(256) k_src_from_rho(
     const double* rho, const uint32_t* links, const int64_t* wsrc, int64_t* src,
-    double* dsum, int64_t N, double fourpi_lb) {
+    double* dsum, const int* label, unsigned long long* comp_sum, int64_t N,
+    double fourpi_lb) {
   long long acc = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -615,9 +622,24 @@ __global__ void __launch_bounds__(256) k_src_from_rho(
     long long sv = 0;
     if (!solid) sv = llrint(fourpi_lb * rho[i] * PSI_SCALE) + (wsrc ? wsrc[i] : 0);
     src[i] = sv;
-    acc += sv;
+    if (label && !solid && label[i] != 0)
+      atomicAdd(comp_sum + label[i], (unsigned long long)sv);
+    else
+      acc += sv;
   }
   block_sum_to(acc, dsum);
+}
+
+// Mean of the source over each fluid component, in fixed point:
+// component 0 from the CTA sums in dsum[0], the others from comp_sum.
+__global__ void k_comp_means(const double* dsum, const unsigned long long* comp_sum,
+                             const long long* comp_size, int ncomp, long long* comp_mean) {
+  for (int k = threadIdx.x; k < ncomp; k += blockDim.x) {
+    if (k == 0)
+      comp_mean[0] = llrint(dsum[0] / (double)comp_size[0]);
+    else
+      comp_mean[k] = llrint((double)(long long)comp_sum[k] / (double)comp_size[k]);
+  }
 }
 
 inline unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -736,6 +758,7 @@ cudaError_t launch_charge(lbm_t* h) {
 #define LBM_CHARGE_S(SS)                                                        \
   LBM_DISPATCH_WS(h, (k_charge<SS, W_, ST_><<<nb, ct, 0, h->st>>>(               \
                          h->f[h->cur], h->links, h->wsrc, h->ps.src, h->ps.part, \
+                         h->ps.label, h->ps.comp_sum,                            \
                          h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,                  \
                          as_f4(h->valence), as_f4(h->nref), k)))
   switch (h->S) {
@@ -747,6 +770,11 @@ cudaError_t launch_charge(lbm_t* h) {
 #undef LBM_CHARGE_S
   k_sum_partials<<<1, 1024, 0, h->st>>>(h->ps.part, nb, h->ps.dsum);
   h->launches += 2;
+  if (h->ps.label) {
+    k_comp_means<<<1, 256, 0, h->st>>>(h->ps.dsum, h->ps.comp_sum, h->ps.comp_size,
+                                        h->ps.ncomp, h->ps.comp_mean);
+    ++h->launches;
+  }
   return cudaGetLastError();
 }
 
@@ -792,7 +820,13 @@ cudaError_t launch_psi_from_double(lbm_t* h, const double* in, int64_t* psi) {
 cudaError_t launch_src_from_rho(lbm_t* h, const double* rho_dev) {
   const double k = 4.0 * 3.14159265358979323846 * h->cfg.bjerrum;
   k_src_from_rho<<<(unsigned)std::min<int64_t>(nblocks(h->N, 256), h->grid_cap), 256, 0,
-                   h->st>>>(rho_dev, h->links, h->wsrc, h->ps.src, h->ps.dsum, h->N, k);
+                   h->st>>>(rho_dev, h->links, h->wsrc, h->ps.src, h->ps.dsum, h->ps.label,
+                            h->ps.comp_sum, h->N, k);
+  if (h->ps.label) {
+    k_comp_means<<<1, 256, 0, h->st>>>(h->ps.dsum, h->ps.comp_sum, h->ps.comp_size,
+                                        h->ps.ncomp, h->ps.comp_mean);
+    ++h->launches;
+  }
   ++h->launches;
   return cudaGetLastError();
 }

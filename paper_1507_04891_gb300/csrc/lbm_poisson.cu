@@ -77,7 +77,8 @@ template <bool WALLS>
 __global__ void __launch_bounds__(256) k_res0(
     const int64_t* __restrict__ psi, const int64_t* __restrict__ src,
     const uint32_t* __restrict__ links, float* __restrict__ r, double* dsum,
-    Box b, int64_t nbox, double inv_nfluid) {
+    Box b, int64_t nbox, double inv_nfluid, const int* __restrict__ label,
+    const long long* __restrict__ comp_mean) {
   __shared__ long long s_mean;
   __shared__ float red_r[8], red_s[8];
   if (threadIdx.x == 0) s_mean = llrint(dsum[0] * inv_nfluid);
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(256) k_res0(
       if (WALLS && !open_face(lk, f)) continue;
       Ap += pc - psi[i + d[f]];
     }
-    const int64_t sfx = src[i] - s_mean;
+    const int64_t sfx = src[i] - (label ? comp_mean[label[i]] : (int64_t)s_mean);
     const float rf = (float)(sfx - Ap);
     r[c] = rf * PSI_INV_SCALE_F;
     rr += rf * rf;
@@ -200,7 +201,8 @@ template <bool WALLS>
 __global__ void __launch_bounds__(256) k_sor0(
     int64_t* __restrict__ psi, const int64_t* __restrict__ src,
     const uint32_t* __restrict__ links, const double* dsum, Box b,
-    int64_t nbox, double inv_nfluid, int color, float omega) {
+    int64_t nbox, double inv_nfluid, int color, float omega, const int* __restrict__ label,
+    const long long* __restrict__ comp_mean) {
   __shared__ long long s_mean;
   if (threadIdx.x == 0) s_mean = llrint(dsum[0] * inv_nfluid);
   __syncthreads();
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(256) k_sor0(
     ++cnt;
   }
   if (cnt == 0) return;
-  const int64_t rfx = src[i] - s_mean - Ap;
+  const int64_t rfx = src[i] - (label ? comp_mean[label[i]] : (int64_t)s_mean) - Ap;
   psi[i] = pc + llrintf(omega * (float)rfx / (float)cnt);
 }
 
@@ -645,6 +647,15 @@ void poisson_free(lbm_t* h) {
   cudaFree(P.dsum);
   cudaFree(P.part);
   P.part = nullptr;
+  cudaFree(P.label);
+  cudaFree(P.comp_sum);
+  cudaFree(P.comp_size);
+  cudaFree(P.comp_mean);
+  P.label = nullptr;
+  P.comp_sum = nullptr;
+  P.comp_size = nullptr;
+  P.comp_mean = nullptr;
+  P.ncomp = 1;
   if (P.hsum) cudaFreeHost(P.hsum);
   P.psi[0] = P.psi[1] = nullptr;
   P.src = nullptr;
@@ -832,10 +843,10 @@ cudaError_t residual_launch(lbm_t* h) {
   const unsigned nb = (unsigned)std::min<int64_t>(nblocks(nbox, 256), h->grid_cap);
   if (h->has_walls)
     k_res0<true><<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, h->links, P.lev[0].rhs, P.dsum,
-                                        b, nbox, inv_nf);
+                                        b, nbox, inv_nf, P.label, P.comp_mean);
   else
     k_res0<false><<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, nullptr, P.lev[0].rhs, P.dsum,
-                                         b, nbox, inv_nf);
+                                         b, nbox, inv_nf, nullptr, nullptr);
   ++h->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
@@ -1126,10 +1137,12 @@ lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
         for (int color = 0; color < 2; ++color) {
           if (h->has_walls)
             k_sor0<true><<<nblocks(nbox, 256), 256, 0, h->st>>>(
-                P.psi[P.cur], P.src, h->links, P.dsum, b, nbox, inv_nf, color, omega);
+                P.psi[P.cur], P.src, h->links, P.dsum, b, nbox, inv_nf, color, omega, P.label,
+                P.comp_mean);
           else
             k_sor0<false><<<nblocks(nbox, 256), 256, 0, h->st>>>(
-                P.psi[P.cur], P.src, nullptr, P.dsum, b, nbox, inv_nf, color, omega);
+                P.psi[P.cur], P.src, nullptr, P.dsum, b, nbox, inv_nf, color, omega, nullptr,
+                nullptr);
           ++h->launches;
         }
       LBM_CUDA_TRY(h, cudaGetLastError());

@@ -277,3 +277,30 @@ def test_fft_charged_ternary_periodic_steps():
         assert d["poisson_residual"] <= 1e-8 and d["poisson_iters"] <= 3
         o.step()
     compare_fields(lat, o)
+
+
+@pytest.mark.parametrize("solver", ["mg", "sor"])
+def test_poisson_with_isolated_fluid_pockets(solver):
+    """Walls that close off single fluid cells: every connected fluid
+    component is its own Poisson domain with its own neutralising mean."""
+    shape = (12, 10, 16)
+    solid, sigma = WL.random_solid(shape, seed=42, fraction=0.1)
+    # wall in two single cells completely
+    for (z, y, x) in [(3, 4, 5), (8, 2, 11)]:
+        solid[z, y, x] = False
+        for dz, dy, dx in [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]:
+            solid[(z + dz) % 12, (y + dy) % 10, (x + dx) % 16] = True
+    sigma = np.where(solid, sigma, 0.0)
+    g = np.random.Generator(np.random.PCG64(43))
+    rho = g.uniform(-0.01, 0.01, size=shape)
+    lat = lbm.Lattice(16, 10, 12, 1, bjerrum=0.7, poisson=solver, poisson_maxit=20000)
+    lat.set_walls(solid, sigma)
+    psi, iters, res, st = lat.solve_poisson(rho, tol=1e-10)
+    assert st == lbm.LBM_OK and res <= 1e-10
+    p = O.Params(1.0, 1.0, [1.0], [1.0], bjerrum=0.7, solid=solid, sigma=sigma)
+    so = O.PoissonSolver(~solid)
+    assert so.ncomp >= 3
+    s = O.poisson_source(np.where(solid, 0.0, rho), p, shape)
+    assert so.residual(psi, s) <= 2e-10
+    d = so._zero_mean(psi[~solid]) - so.solve(s)[~solid]
+    assert np.abs(d).max() <= 1e-7 * np.abs(so.solve(s)).max()
