@@ -77,6 +77,26 @@ __device__ __forceinline__ int64_t wrap_idx(const Geo& G, int x, int y, int z) {
   return ((int64_t)z * G.ny + y) * G.nx + x;
 }
 
+// The 27 neighbours of a cell from six wrapped axis offsets (no modulo per
+// tap): offset of (dx, dy, dz) = ox[dx+1] + oy[dy+1] + oz[dz+1].
+struct Taps {
+  int ox[3], oy[3], oz[3];
+};
+__device__ __forceinline__ Taps taps_of(const Geo& G, int x, int y, int z) {
+  Taps t;
+  const int nxy = G.nx * G.ny;
+  t.ox[0] = x == 0 ? G.nx - 1 : -1;
+  t.ox[1] = 0;
+  t.ox[2] = x == G.nx - 1 ? -(G.nx - 1) : 1;
+  t.oy[0] = (y == 0 ? G.ny - 1 : -1) * G.nx;
+  t.oy[1] = 0;
+  t.oy[2] = (y == G.ny - 1 ? -(G.ny - 1) : 1) * G.nx;
+  t.oz[0] = (z == 0 ? G.nz - 1 : -1) * nxy;
+  t.oz[1] = 0;
+  t.oz[2] = (z == G.nz - 1 ? -(G.nz - 1) : 1) * nxy;
+  return t;
+}
+
 __device__ __forceinline__ bool fluid_at(const Geo& G, int64_t i) {
   return !G.links || !(G.links[i] & LINK_SOLID);
 }
@@ -172,11 +192,12 @@ __global__ void __launch_bounds__(256) k_nn_infer1(const float* __restrict__ x0,
   if (i >= G.N) return;
   int x, y, z;
   xyz(i, G, x, y, z);
+  const Taps T = taps_of(G, x, y, z);
   float acc[16];
   for (int c = 0; c < C; ++c) acc[c] = __half2float(ph[C * 2 * 27 + c]);
+#pragma unroll
   for (int o = 0; o < 27; ++o) {
-    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-    const int64_t j = wrap_idx(G, x + dx, y + dy, z + dz);
+    const int64_t j = i + T.ox[o % 3] + T.oy[(o / 3) % 3] + T.oz[o / 9];
     const __half a0 = __float2half(x0[j]);
     const __half a1 = __float2half(fluid_at(G, j) ? 1.f : 0.f);
     for (int c = 0; c < C; ++c)
@@ -195,11 +216,12 @@ __global__ void __launch_bounds__(256) k_nn_infer2(const __half* __restrict__ hi
   }
   int x, yy, z;
   xyz(i, G, x, yy, z);
+  const Taps T = taps_of(G, x, yy, z);
   const __half* W2 = ph + C * 2 * 27 + C;
   float acc = 0.f;
+#pragma unroll
   for (int o = 0; o < 27; ++o) {
-    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-    const int64_t j = wrap_idx(G, x + dx, yy + dy, z + dz);
+    const int64_t j = i + T.ox[o % 3] + T.oy[(o / 3) % 3] + T.oz[o / 9];
     for (int c = 0; c < C; ++c) acc += __half2float(__hmul(W2[c * 27 + o], hid[(int64_t)c * G.N + j]));
   }
   dpsi[i] = sigma * acc;
