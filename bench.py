@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--poisson", default="fft", choices=["mg", "sor", "fft"])
     ap.add_argument("--no-alt", action="store_true", help="skip the multigrid comparison run")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-slit and learned-guess measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -201,6 +203,116 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_batched(lbm, WL, steps=40, local=0):
+    """Batched slit sweep (64 channels, widths U{16..128}, 32x32, Sc
+    log-uniform 1..1000, wall charge U[-0.02,-0.002]) stacked in one lattice,
+    FP16 storage, every step one CUDA-graph replay; compared with the same
+    64 channels stepped one after another as separate FP32 lattices with
+    host-driven steps."""
+    import torch
+    insts = WL.batched_slits()
+    S = 3
+    sites = sum(int(np.prod(w.shape)) for w in insts)
+    lat, _ = lbm.stack_slits(insts, storage="fp16", step_graph=True, device=local)
+    tune = lat.autotune()
+    lat.step(3)
+    lat.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.ExternalStream(lat.stream)
+    t0.record(stream)
+    lat.step(steps)
+    t1.record(stream)
+    lat.synchronize()
+    tb = t0.elapsed_time(t1)
+    d = lat.diagnostics()
+    lat.destroy()
+    # plain: one FP32 lattice per channel, host-driven steps
+    total = 0.0
+    for w in insts:
+        one = lbm.Lattice(w.shape[2], w.shape[1], w.shape[0], 3, omega_visc=w.omega_visc,
+                          omega_drag=lbm.omega_drag_for_schmidt(w.omega_visc, w.schmidt),
+                          bjerrum=w.bjerrum, e_ext=w.e_ext, storage="fp32", poisson="fft",
+                          device=local)
+        one.set_walls(w.solid, w.sigma)
+        for s in range(3):
+            one.set_species(s, 1.0, w.valence[s], np.where(w.solid, 1.0, w.n0[s]))
+        one.step(2)
+        one.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.ExternalStream(one.stream)
+        e0.record(st)
+        one.step(steps)
+        e1.record(st)
+        one.synchronize()
+        total += e0.elapsed_time(e1)
+        one.destroy()
+    return {"workload": "64 slit channels 32x32xW, W~U{16..128} (seed 1237), %d nodes" % sites,
+            "storage": "fp16", "step_graph": True, "autotune": tune,
+            "value": S * sites * steps / (tb / 1e3) / 1e6, "unit": UNIT,
+            "ms_per_step": tb / steps, "poisson_residual_last": d["poisson_residual"],
+            "plain_fp32_sequential": {"value": S * sites * steps / (total / 1e3) / 1e6,
+                                      "ms_per_step": total / steps},
+            "speedup": total / tb}
+
+
+def run_learned(lbm, WL, n=64, steps=10, local=0):
+    """Learned Poisson initial guess vs plain warm start, multigrid to 1e-8,
+    on a charged ternary porous box (spheres radius 4..12, 20% solid,
+    surface charge +/-0.01): the network is trained on the initial residuals
+    of 16 solver steps, then both arms run the same held-out steps from the
+    same state."""
+    wl = WL.porous_spheres(n=n, seed=1238)
+    od = lbm.omega_drag_for_schmidt(1.0, 1.0)
+
+    def make():
+        lat = lbm.Lattice(n, n, n, 3, omega_drag=od, bjerrum=0.7, poisson="mg", poisson_maxit=200,
+                          device=local)
+        lat.set_walls(wl.solid, wl.sigma)
+        for s in range(3):
+            lat.set_species(s, 1.0, wl.valence[s], np.where(wl.solid, 1.0, wl.n0[s]))
+        return lat
+
+    base = make()
+    base.step(4)
+    base.nn_init(hidden=8, seed=3)
+    base.nn_collect(16)
+    base.step(16)
+    t = time.perf_counter()
+    losses = base.nn_train(epochs=40, lr=5e-3)
+    train_s = time.perf_counter() - t
+    params = base.nn_params()
+    state, step = base.get_state()
+    psi = base.get_potential()
+    base.destroy()
+    out = {}
+    for use in (False, True):
+        lat = make()
+        lat.set_state(state, step)
+        rho = lat.get_moments(1)[0] - lat.get_moments(2)[0]
+        lat.solve_poisson(rho, psi, tol=1e-12)
+        if use:
+            lat.nn_init(hidden=8, seed=3)
+            lat.nn_params(params)
+            lat.nn_use(True)
+        lat.set_timing(True)
+        lat.step(steps)
+        tm = lat.get_timing()
+        st = lat.nn_stats() if use else None
+        out["learned" if use else "plain"] = {
+            "poisson_iters_per_step": tm["poisson_iters"] / steps,
+            "poisson_ms_per_step": tm["poisson_ms"] / steps,
+            "residual_ratio_after_guess": st["mean_ratio"] if st else None,
+            "guesses_kept": ("%d/%d" % (st["kept"], st["tried"])) if st else None,
+            "final_residual": lat.diagnostics()["poisson_residual"]}
+        lat.destroy()
+    out["workload"] = "porous_%d^3 ternary, solid %.3f, multigrid" % (n, wl.meta["solid_fraction"])
+    out["training"] = {"fields": 16, "epochs": 40, "loss_first": float(losses[0]),
+                       "loss_last": float(losses[-1]), "seconds": train_s, "params": int(params.size)}
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -293,6 +405,11 @@ def run_ours(args, rank, world, local):
                      "poisson_iters_per_step": tmg["poisson_iters"] / args.steps,
                      "poisson_residual_last": dg["poisson_residual"]}
 
+    batched = learned = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        batched = run_batched(lbm, WL, local=local)
+        learned = run_learned(lbm, WL, local=local)
+
     # end to end through the C ABI with host buffers: initial state uploaded
     # from pinned host memory, every step's FP64 diagnostics read back.
     lat2 = make(args.poisson)
@@ -344,6 +461,8 @@ def run_ours(args, rank, world, local):
                     "d2h_bytes_per_step": 8 * (S + 7)},
             "poisson_alternative": alt,
             "step_graph": graph_run,
+            "batched": batched,
+            "learned_vs_plain": learned,
             "diagnostics": {"mass": list(map(float, diag["mass"])),
                             "poisson_residual_last": diag["poisson_residual"]},
             "cpu_baseline": cpu,
