@@ -55,10 +55,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1507_04891_gb300 import replicas
+    return replicas.env()
 
 
 def measured_peaks():
@@ -320,11 +318,11 @@ def run_ours(args, rank, world, local):
     from paper_1507_04891_gb300 import workloads as WL
     from paper_1507_04891_gb300.build import build_library
 
+    from paper_1507_04891_gb300 import replicas
+
     build_library()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    replicas.init(world, backend="nccl", device=torch.device("cuda", local))
     n = args.n
     wl = WL.ternary_bulk(n=n, seed=1235 + rank, schmidt=args.schmidt)
     S, N = wl.nspecies, wl.sites
@@ -337,18 +335,11 @@ def run_ours(args, rank, world, local):
                            poisson_maxit=500, device=local, step_graph=graph)
 
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        replicas.barrier(world)
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([x], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            return float(tt.item())
-        return x
+        return replicas.max_over_ranks(x, world, device="cuda")
 
     def timed(poisson, sample_clocks, graph=False):
         """W warm-up steps, then K steps timed with CUDA events on the
@@ -468,9 +459,7 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    replicas.finish(world)
     return 0
 
 

@@ -578,3 +578,33 @@ def test_poisson_components_are_independent():
         x = np.linalg.lstsq(A, 4 * math.pi * lB * q, rcond=None)[0]
         x -= x.mean()
         np.testing.assert_allclose(psi[lo:lo + W, 1, 2], x, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# P11: electro-osmotic flow in the charged slit follows Helmholtz-
+# Smoluchowski: the mixture momentum balance nu rho u'' = -rho_e E with
+# Poisson psi'' = -4 pi l_B rho_e and no slip gives
+# u_x(z) = E (psi(z) - psi_wall) / (4 pi l_B rho nu)  (Eq. globalmomentumcontc)
+# ---------------------------------------------------------------------------
+def test_slit_electroosmotic_profile_helmholtz_smoluchowski():
+    Wd, lB, sig, debye, E = 12, 0.7, -0.01, 4.0, 1e-5
+    wl = WL.slit(nx=1, ny=1, width=Wd, sigma=sig, debye=debye, bjerrum=lB, e_field=0.0,
+                 schmidt=1.0)
+    eq = _oracle_from(wl)
+    eq.run(1500)                         # ions at rest reach equilibrium first
+    p = O.Params(1.0, O.omega_drag_for_schmidt(1.0, 100.0), wl.mass, wl.valence, bjerrum=lB,
+                 e_ext=(E, 0.0, 0.0), solid=wl.solid, sigma=wl.sigma)
+    o = O.Oracle(p, wl.shape)
+    o.f = eq.f.copy()
+    info = o.run(2000)                   # flow develops in ~ W^2 / (pi^2 nu) steps
+    n, u = info.n[:, 1:-1, 0, 0], info.u[:, :, 1:-1, 0, 0]
+    psi = info.psi[1:-1, 0, 0]
+    rho = n.sum(0)
+    rho_e = (wl.valence[:, None] * n).sum(0)
+    # mid-step (force-shifted) barycentric velocity
+    ux = ((n * u[:, 0]).sum(0) + 0.5 * rho_e * E) / rho
+    psi_wall = psi[0] + 2 * math.pi * lB * sig   # half a cell out, Neumann slope
+    nu = O.viscosity(1.0)
+    pred = E * (psi - psi_wall) / (4 * math.pi * lB * rho * nu)
+    assert pred.max() > 1e-6
+    assert np.abs(ux - pred).max() <= 0.02 * np.abs(pred).max()
