@@ -417,6 +417,7 @@ struct SpectralPlan {
   int lgz = -1;                    // log2(nz) when the z axis is one periodic run
   float2* twz = nullptr;           // z twiddles (periodic power-of-two z)
   int last_iters = 2;              // applications of the previous solve
+  bool runs_fit = true;            // z solve fits in shared memory
   float* r = nullptr;              // N
   long long* psum = nullptr;       // nz
   long long* mean_z = nullptr;     // nz
@@ -536,7 +537,10 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   LBM_CUDA_TRY(h, cudaMemcpy(s->plane_fluid, pf.data(), nz, cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->twx, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->twy, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice));
-  if (runs.size() == 1 && runs[0].cyclic && ilog2(nz) > 0 && nz >= 4) {
+  int optin = 0;
+  LBM_CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
+  if (runs.size() == 1 && runs[0].cyclic && ilog2(nz) > 0 && nz >= 4 &&
+      (size_t)2 * ZP * nz * sizeof(float2) <= (size_t)optin) {
     s->lgz = ilog2(nz);
     auto tz = twiddles(nz);
     if (!al((void**)&s->twz, tz.size() * sizeof(float2))) {
@@ -552,13 +556,13 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   int lmax = 0;
   for (const Run& R : runs) lmax = std::max(lmax, R.len);
   s->zsmem = (size_t)ZP * lmax * (2 + 1 + 1) * sizeof(float);
-  int optin = 0;
-  LBM_CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
-  if ((int)s->zsmem > optin) {
+  s->runs_fit = s->lgz > 0 || (int)s->zsmem <= optin;
+  if (!s->runs_fit && solid) {
     h->err = "spectral Poisson solver: fluid run along z too long for shared memory";
     return LBM_EINVAL;
   }
-  if (s->zsmem > 48 * 1024)
+  // (without walls yet the plan is provisional: set_walls rebuilds it)
+  if (s->runs_fit && s->zsmem > 48 * 1024)
     LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->zsmem));
   s->smem = (size_t)nxy * sizeof(float2);
   if (s->smem > 48 * 1024) {
@@ -631,6 +635,10 @@ cudaError_t spec_apply(lbm_t* h) {
 lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* rel_res) {
   SpectralPlan* s = h->spec;
   Poisson& P = h->ps;
+  if (!s->runs_fit) {
+    h->err = "spectral Poisson solver: fluid run along z too long for shared memory";
+    return LBM_EINVAL;
+  }
   LBM_CUDA_TRY(h, spec_means(h));
   LBM_CUDA_TRY(h, spec_residual(h));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
@@ -854,6 +862,10 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
 }  // namespace
 
 lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
+  if (!h->spec->runs_fit) {
+    h->err = "spectral Poisson solver: fluid run along z too long for shared memory";
+    return LBM_EINVAL;
+  }
   if (!h->gstatus) {
     void* p = nullptr;
     if (cudaMalloc(&p, sizeof(GraphStatus)) != cudaSuccess) {
