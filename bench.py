@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--poisson", default="fft", choices=["mg", "sor", "fft"])
     ap.add_argument("--no-alt", action="store_true", help="skip the multigrid comparison run")
+    ap.add_argument("--only", choices=["batched", "learned"], default=None,
+                    help="run one extra measurement alone and print it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-slit and learned-guess measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -466,6 +468,15 @@ def run_ours(args, rank, world, local):
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.only:
+        from paper_1507_04891_gb300 import lbm
+        from paper_1507_04891_gb300 import workloads as WL
+        from paper_1507_04891_gb300.build import build_library
+        build_library()
+        res = (run_batched(lbm, WL, steps=max(1, args.steps)) if args.only == "batched"
+               else run_learned(lbm, WL))
+        print(json.dumps({"metric": METRIC, "only": args.only, **res}), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args, rank, world)
     return run_ours(args, rank, world, local)
