@@ -63,13 +63,31 @@ struct Fmt<LBM_FP32> {
   static __device__ __forceinline__ float ld(const T* p, float) { return *p; }
   static __device__ __forceinline__ void st(T* p, float v, float) { *p = v; }
   static __device__ __forceinline__ void st_sr(T* p, float v, float, uint32_t) { *p = v; }
+  static __device__ __forceinline__ void st_sr2(T* pa, float va, T* pb, float vb, float, uint32_t) {
+    *pa = va;
+    *pb = vb;
+  }
 };
+
+// Two values rounded stochastically into a packed 16-bit pair by the
+// hardware conversion with random bits (cvt.rs, sm_100 family); the first
+// operand lands in the upper half.
+__device__ __forceinline__ uint32_t cvt_rs_f16x2(float hi, float lo, uint32_t rbits) {
+  uint32_t d;
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+  return d;
+}
+__device__ __forceinline__ uint32_t cvt_rs_bf16x2(float hi, float lo, uint32_t rbits) {
+  uint32_t d;
+  asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+  return d;
+}
 // 16-bit formats: h = f / (w_p n_ref) - 1.  st() rounds to nearest; st_sr()
-// rounds stochastically: random bits are added below the kept mantissa of
-// the FP32 value and the result is truncated toward zero, so the stored
-// value is unbiased.  The per-step change of a slowly diffusing mode is a
-// fraction of one 16-bit ulp of h; round-to-nearest would return the same
-// value every step and freeze the mode.
+// and st_sr2() round stochastically (the hardware conversion draws on random
+// bits to round up with probability equal to the dropped fraction), so the
+// stored value is unbiased.  The per-step change of a slowly diffusing mode
+// is a fraction of one 16-bit ulp of h; round-to-nearest would return the
+// same value every step and freeze the mode.
 template <>
 struct Fmt<LBM_FP16_SHIFT> {
   using T = __half;
@@ -81,9 +99,14 @@ struct Fmt<LBM_FP16_SHIFT> {
   }
   static __device__ __forceinline__ void st_sr(T* p, float v, float inv_wn, uint32_t rnd) {
     const float hv = fmaf(v, inv_wn, -1.0f);
-    // FP16 keeps 10 of the 23 FP32 mantissa bits: dither the 13 dropped bits
-    const float d = __uint_as_float(__float_as_uint(hv) + (rnd >> 19));
-    *p = __float2half_rz(d);
+    const uint32_t d = cvt_rs_f16x2(hv, 0.0f, rnd);
+    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(d >> 16);
+  }
+  static __device__ __forceinline__ void st_sr2(T* pa, float va, T* pb, float vb, float inv_wn,
+                                                uint32_t rnd) {
+    const uint32_t d = cvt_rs_f16x2(fmaf(va, inv_wn, -1.0f), fmaf(vb, inv_wn, -1.0f), rnd);
+    *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(d >> 16);
+    *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(d & 0xFFFFu);
   }
 };
 template <>
@@ -97,11 +120,14 @@ struct Fmt<LBM_BF16_SHIFT> {
   }
   static __device__ __forceinline__ void st_sr(T* p, float v, float inv_wn, uint32_t rnd) {
     const float hv = fmaf(v, inv_wn, -1.0f);
-    // BF16 is the upper half of FP32: dither the 16 dropped bits, truncate
-    const uint32_t b = __float_as_uint(hv) + (rnd >> 16);
-    __nv_bfloat16_raw raw;
-    raw.x = (unsigned short)(b >> 16);
-    *p = __nv_bfloat16(raw);
+    const uint32_t d = cvt_rs_bf16x2(hv, 0.0f, rnd);
+    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(d >> 16);
+  }
+  static __device__ __forceinline__ void st_sr2(T* pa, float va, T* pb, float vb, float inv_wn,
+                                                uint32_t rnd) {
+    const uint32_t d = cvt_rs_bf16x2(fmaf(va, inv_wn, -1.0f), fmaf(vb, inv_wn, -1.0f), rnd);
+    *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(d >> 16);
+    *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(d & 0xFFFFu);
   }
 };
 
@@ -156,10 +182,14 @@ __device__ __forceinline__ float pull(const typename Fmt<ST>::T* __restrict__ f,
                                       int64_t N, int s, int p, uint32_t i,
                                       int d, uint32_t lk, float nref) {
   const float wn = WT(p) * nref;
-  if (WALLS && ((lk >> p) & 1u)) {
-    return Fmt<ST>::ld(f + (int64_t)(s * Q + OPP(p)) * N + i, wn);
+  // branch-free: the bounce-back source only changes the address, so the
+  // loads of all directions stay independent and are issued together
+  int64_t idx = (int64_t)(s * Q + p) * N + (int64_t)((int)i + d);
+  if (WALLS) {
+    const int64_t bb = (int64_t)(s * Q + OPP(p)) * N + i;
+    idx = ((lk >> p) & 1u) ? bb : idx;
   }
-  return Fmt<ST>::ld(f + (int64_t)(s * Q + p) * N + (int64_t)((int)i + d), wn);
+  return Fmt<ST>::ld(f + idx, wn);
 }
 
 __device__ __forceinline__ void site_xyz(uint32_t i, int nx, int ny, int& x,
@@ -354,8 +384,8 @@ __global__ void __launch_bounds__(256) k_stream_collide(const StepArgs a) {
       const float fa = omm * f[s][p] + (even + odd);
       const float fb = omm * f[s][p + 1] + (even - odd);
       moved += fa + fb;
-      Fmt<ST>::st_sr(fout + (int64_t)(s * Q + p) * N + i, fa, INV_WT(p) * inr, lcg_next(rnd));
-      Fmt<ST>::st_sr(fout + (int64_t)(s * Q + p + 1) * N + i, fb, INV_WT(p) * inr, lcg_next(rnd));
+      Fmt<ST>::st_sr2(fout + (int64_t)(s * Q + p) * N + i, fa, fout + (int64_t)(s * Q + p + 1) * N + i,
+                      fb, INV_WT(p) * inr, lcg_next(rnd));
     }
     Fmt<ST>::st_sr(fout + (int64_t)(s * Q) * N + i, n[s] - moved, INV_WT(0) * inr, lcg_next(rnd));
   }
