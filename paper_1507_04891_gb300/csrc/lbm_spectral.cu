@@ -14,9 +14,10 @@
 // problem to FP32 accuracy; it is used for defect correction on the exact
 // fixed-point residual, so two applications usually reach 1e-8.
 //
-// Kernels per application: forward FFT of the residual per plane (shared
-// memory, radix 2), one tridiagonal solve per mode and run, inverse FFT per
-// plane fused with the update psi += round(e).
+// Kernels per application: forward FFT of the residual, two real planes per
+// complex transform (shared memory, radix 2); along z an FFT (periodic
+// power-of-two z) or one tridiagonal solve per mode and run; inverse FFT
+// fused with the update psi += round(e).
 #include <math.h>
 
 #include <algorithm>
@@ -81,55 +82,78 @@ struct SpecArgs {
   int nx, ny, nz, lgx, lgy;
   const float2* twx;
   const float2* twy;
+  const float* lam_xy;  // eigenvalue of the x-y Laplacian per mode (nx*ny)
+  const float* lam_z;   // eigenvalue along a periodic z per kz (nz) or NULL
 };
 
-// Forward 2-D FFT of the FP32 residual of each fluid plane:
-// rhat[z][ky][kx] = sum_x,y r[z][y][x] exp(-2 pi i (kx x/nx + ky y/ny)).
-__global__ void __launch_bounds__(512) k_fft_fwd(const float* __restrict__ r,
-                                                 float2* __restrict__ rhat,
-                                                 const int* __restrict__ planes,
-                                                 SpecArgs a) {
+// Two real planes per CTA: the residual of plane a is the real part and
+// that of plane b the imaginary part of one complex 2-D FFT; the two
+// spectra follow from the Hermitian symmetry of real data,
+//   A(k) = (C(k) + conj C(-k)) / 2,   B(k) = (C(k) - conj C(-k)) / (2i).
+__global__ void __launch_bounds__(512) k_fft_fwd2(const float* __restrict__ r,
+                                                  float2* __restrict__ rhat,
+                                                  const int* __restrict__ planes, int nplanes,
+                                                  SpecArgs a) {
   extern __shared__ float2 buf[];
-  const int z = planes[blockIdx.x];
+  const int za = planes[2 * blockIdx.x];
+  const int zb = (2 * blockIdx.x + 1 < nplanes) ? planes[2 * blockIdx.x + 1] : -1;
   const int nxy = a.nx * a.ny;
-  const float* src = r + (int64_t)z * nxy;
-  // load with bit-reversed x and y (both passes then take natural output)
+  const float* ra = r + (int64_t)za * nxy;
+  const float* rb = zb >= 0 ? r + (int64_t)zb * nxy : nullptr;
   for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
     const int y = k >> a.lgx, x = k & (a.nx - 1);
     const int xr = a.lgx ? (int)brev(x, a.lgx) : 0, yr = a.lgy ? (int)brev(y, a.lgy) : 0;
-    buf[yr * a.nx + xr] = make_float2(src[k], 0.f);
+    buf[yr * a.nx + xr] = make_float2(ra[k], rb ? rb[k] : 0.f);
   }
   __syncthreads();
-  fft_rows(buf, a.lgx, a.lgy, 1, a.nx, a.twx, -1.f);   // along x (ny rows)
-  fft_rows(buf, a.lgy, a.lgx, a.nx, 1, a.twy, -1.f);   // along y (nx columns)
-  float2* dst = rhat + (int64_t)z * nxy;
-  for (int k = threadIdx.x; k < nxy; k += blockDim.x) dst[k] = buf[k];
+  fft_rows(buf, a.lgx, a.lgy, 1, a.nx, a.twx, -1.f);
+  fft_rows(buf, a.lgy, a.lgx, a.nx, 1, a.twy, -1.f);
+  float2* da = rhat + (int64_t)za * nxy;
+  float2* db = zb >= 0 ? rhat + (int64_t)zb * nxy : nullptr;
+  for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
+    const int ky = k >> a.lgx, kx = k & (a.nx - 1);
+    const int km = (((a.ny - ky) & (a.ny - 1)) << a.lgx) | ((a.nx - kx) & (a.nx - 1));
+    const float2 c = buf[k], cm = buf[km];
+    da[k] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
+    if (db) db[k] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
+  }
 }
 
-// Inverse 2-D FFT of the correction of each fluid plane, scaled by
-// 1/(nx ny), and the in-place update psi += round(e).
-__global__ void __launch_bounds__(512) k_fft_inv_apply(const float2* __restrict__ ehat,
-                                                       const int* __restrict__ planes,
-                                                       SpecArgs a,
-                                                       int64_t* psi) {
+// Inverse of two real planes at once: C = E_a + i E_b, inverse 2-D FFT, the
+// real part corrects plane a and the imaginary part plane b (in place,
+// psi += round(e)).
+__global__ void __launch_bounds__(512) k_fft_inv2_apply(const float2* __restrict__ ehat,
+                                                        const int* __restrict__ planes,
+                                                        int nplanes, SpecArgs a, int64_t* psi) {
   extern __shared__ float2 buf[];
-  const int z = planes[blockIdx.x];
+  const int za = planes[2 * blockIdx.x];
+  const int zb = (2 * blockIdx.x + 1 < nplanes) ? planes[2 * blockIdx.x + 1] : -1;
   const int nxy = a.nx * a.ny;
-  const float2* src = ehat + (int64_t)z * nxy;
+  const float2* ea = ehat + (int64_t)za * nxy;
+  const float2* eb = zb >= 0 ? ehat + (int64_t)zb * nxy : nullptr;
   for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
     const int y = k >> a.lgx, x = k & (a.nx - 1);
     const int xr = a.lgx ? (int)brev(x, a.lgx) : 0, yr = a.lgy ? (int)brev(y, a.lgy) : 0;
-    buf[yr * a.nx + xr] = src[k];
+    const float2 va = ea[k];
+    const float2 vb = eb ? eb[k] : make_float2(0.f, 0.f);
+    buf[yr * a.nx + xr] = make_float2(va.x - vb.y, va.y + vb.x);
   }
   __syncthreads();
   fft_rows(buf, a.lgx, a.lgy, 1, a.nx, a.twx, 1.f);
   fft_rows(buf, a.lgy, a.lgx, a.nx, 1, a.twy, 1.f);
   const float scale = 1.0f / (float)nxy;
-  const int64_t base = (int64_t)z * nxy;
   for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
-    const float e = buf[k].x * scale;
-    psi[base + k] += llrintf(e * PSI_SCALE_F);  // in place: one cell per thread
+    const float2 c = buf[k];
+    psi[(int64_t)za * nxy + k] += llrintf(c.x * scale * PSI_SCALE_F);
+    if (zb >= 0) psi[(int64_t)zb * nxy + k] += llrintf(c.y * scale * PSI_SCALE_F);
   }
+}
+
+// Mean of the source over the whole fluid (one run, periodic z), from the
+// charge kernel's total in dsum[0].
+__global__ void k_global_mean(const double* dsum, double inv_nfluid, long long* mean_z, int nz) {
+  const long long m = llrint(dsum[0] * inv_nfluid);
+  for (int z = threadIdx.x; z < nz; z += blockDim.x) mean_z[z] = m;
 }
 
 // Tridiagonal solve along z for one Fourier mode of one run:
@@ -241,9 +265,7 @@ __global__ void __launch_bounds__(128) k_zsolve(float2* __restrict__ x,
   const int j = threadIdx.x;
   if (j < ZP && m0 + j < nxy) {
     const int m = m0 + j;
-    const int ky = m >> a.lgx, kx = m & (a.nx - 1);
-    const float lam = (2.f - 2.f * cospif(2.f * kx / a.nx)) + (2.f - 2.f * cospif(2.f * ky / a.ny));
-    solve_pencil(X + j, C + j, Qv + j, ZP, L, lam, kx == 0 && ky == 0, R.cyclic != 0);
+    solve_pencil(X + j, C + j, Qv + j, ZP, L, a.lam_xy[m], m == 0, R.cyclic != 0);
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < ZP * L; idx += blockDim.x) {
@@ -279,10 +301,8 @@ __global__ void __launch_bounds__(256) k_zfft(float2* __restrict__ x, const floa
   for (int idx = threadIdx.x; idx < ZP * L; idx += blockDim.x) {
     const int kz = idx >> lgp, j = idx & (ZP - 1);
     const int m = m0 + j;
-    const int ky = m >> a.lgx, kx = m & (a.nx - 1);
-    const float lam = (2.f - 2.f * cospif(2.f * kx / a.nx)) + (2.f - 2.f * cospif(2.f * ky / a.ny)) +
-                      (2.f - 2.f * cospif(2.f * kz / L));
-    const float sc = (kx == 0 && ky == 0 && kz == 0) ? 0.f : invL / lam;
+    const float lam = (m < nxy ? a.lam_xy[m] : 1.f) + a.lam_z[kz];
+    const float sc = (m == 0 && kz == 0) ? 0.f : invL / lam;
     const float2 v = A[idx];
     B[(int)brev(kz, lgz) * ZP + j] = make_float2(v.x * sc, v.y * sc);
   }
@@ -416,6 +436,8 @@ struct SpectralPlan {
   size_t zsmem = 0;                // shared memory of the z solve
   int lgz = -1;                    // log2(nz) when the z axis is one periodic run
   float2* twz = nullptr;           // z twiddles (periodic power-of-two z)
+  float* lam_xy = nullptr;         // x-y Laplacian eigenvalues per mode
+  float* lam_z = nullptr;          // z Laplacian eigenvalues (periodic power-of-two z)
   int last_iters = 2;              // applications of the previous solve
   bool runs_fit = true;            // z solve fits in shared memory
   float* r = nullptr;              // N
@@ -433,6 +455,8 @@ void spectral_free(lbm_t* h) {
   cudaFree(s->twx);
   cudaFree(s->twy);
   cudaFree(s->twz);
+  cudaFree(s->lam_xy);
+  cudaFree(s->lam_z);
   cudaFree(s->spec);
   cudaFree(s->r);
   cudaFree(s->psum);
@@ -537,6 +561,26 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   LBM_CUDA_TRY(h, cudaMemcpy(s->plane_fluid, pf.data(), nz, cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->twx, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->twy, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  {
+    // eigenvalues of the periodic x-y Laplacian, 2 - 2 cos(2 pi k / n) per
+    // axis, computed once in double precision
+    std::vector<float> lxy(nxy);
+    for (int ky = 0; ky < ny; ++ky)
+      for (int kx = 0; kx < nx; ++kx)
+        lxy[(int64_t)ky * nx + kx] =
+            (float)((2.0 - 2.0 * cos(2.0 * 3.14159265358979323846 * kx / nx)) +
+                    (2.0 - 2.0 * cos(2.0 * 3.14159265358979323846 * ky / ny)));
+    std::vector<float> lz(nz);
+    for (int kz = 0; kz < nz; ++kz)
+      lz[kz] = (float)(2.0 - 2.0 * cos(2.0 * 3.14159265358979323846 * kz / nz));
+    if (!al((void**)&s->lam_xy, nxy * sizeof(float)) || !al((void**)&s->lam_z, nz * sizeof(float))) {
+      spectral_free(h);
+      h->err = "spectral Poisson allocation failed";
+      return LBM_ENOMEM;
+    }
+    LBM_CUDA_TRY(h, cudaMemcpy(s->lam_xy, lxy.data(), nxy * sizeof(float), cudaMemcpyHostToDevice));
+    LBM_CUDA_TRY(h, cudaMemcpy(s->lam_z, lz.data(), nz * sizeof(float), cudaMemcpyHostToDevice));
+  }
   int optin = 0;
   LBM_CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
   if (runs.size() == 1 && runs[0].cyclic && ilog2(nz) > 0 && nz >= 4 &&
@@ -566,8 +610,8 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
     LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->zsmem));
   s->smem = (size_t)nxy * sizeof(float2);
   if (s->smem > 48 * 1024) {
-    LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem));
-    LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_inv_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem));
+    LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_fwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem));
+    LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_inv2_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem));
   }
   return LBM_OK;
 }
@@ -583,6 +627,8 @@ SpecArgs args_of(const SpectralPlan* s) {
   a.lgy = s->lgy;
   a.twx = s->twx;
   a.twy = s->twy;
+  a.lam_xy = s->lam_xy;
+  a.lam_z = s->lam_z;
   return a;
 }
 
@@ -606,6 +652,13 @@ cudaError_t spec_residual(lbm_t* h, bool to_host = true, int slot = 0) {
 cudaError_t spec_means(lbm_t* h) {
   SpectralPlan* s = h->spec;
   Poisson& P = h->ps;
+  if (s->nruns == 1 && (int)s->nplanes == s->nz) {
+    // one periodic run: the mean over all fluid, already summed by the
+    // source kernel
+    k_global_mean<<<1, 256, 0, h->st>>>(P.dsum, 1.0 / (double)h->nfluid, s->mean_z, s->nz);
+    ++h->launches;
+    return cudaGetLastError();
+  }
   k_plane_sums<<<s->nz, 256, 0, h->st>>>(P.src, s->psum, s->nx * s->ny);
   k_run_means<<<1, 256, 0, h->st>>>(s->psum, s->runs, s->nruns, s->mean_z, s->nz, s->nx * s->ny);
   h->launches += 2;
@@ -617,7 +670,8 @@ cudaError_t spec_apply(lbm_t* h) {
   Poisson& P = h->ps;
   const SpecArgs a = args_of(s);
   const int threads = (int)std::min<int64_t>(512, std::max<int64_t>(32, (int64_t)s->nx * s->ny / 2));
-  k_fft_fwd<<<s->nplanes, threads, s->smem, h->st>>>(s->r, s->spec, s->planes, a);
+  const int npairs = (s->nplanes + 1) / 2;
+  k_fft_fwd2<<<npairs, threads, s->smem, h->st>>>(s->r, s->spec, s->planes, s->nplanes, a);
   if (s->lgz > 0) {
     k_zfft<<<nblk((int64_t)s->nx * s->ny, ZP), 256, (size_t)2 * ZP * s->nz * sizeof(float2), h->st>>>(
         s->spec, s->twz, s->lgz, a);
@@ -625,7 +679,8 @@ cudaError_t spec_apply(lbm_t* h) {
     dim3 g(nblk((int64_t)s->nx * s->ny, ZP), s->nruns);
     k_zsolve<<<g, 128, s->zsmem, h->st>>>(s->spec, s->runs, a);
   }
-  k_fft_inv_apply<<<s->nplanes, threads, s->smem, h->st>>>(s->spec, s->planes, a, P.psi[P.cur]);
+  k_fft_inv2_apply<<<npairs, threads, s->smem, h->st>>>(s->spec, s->planes, s->nplanes, a,
+                                                       P.psi[P.cur]);
   h->launches += 3;
   return cudaGetLastError();
 }
