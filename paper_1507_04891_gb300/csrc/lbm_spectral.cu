@@ -86,66 +86,103 @@ struct SpecArgs {
   const float* lam_z;   // eigenvalue along a periodic z per kz (nz) or NULL
 };
 
-// Two real planes per CTA: the residual of plane a is the real part and
-// that of plane b the imaginary part of one complex 2-D FFT; the two
-// spectra follow from the Hermitian symmetry of real data,
-//   A(k) = (C(k) + conj C(-k)) / 2,   B(k) = (C(k) - conj C(-k)) / (2i).
-__global__ void __launch_bounds__(512) k_fft_fwd2(const float* __restrict__ r,
-                                                  float2* __restrict__ rhat,
-                                                  const int* __restrict__ planes, int nplanes,
-                                                  SpecArgs a) {
-  extern __shared__ float2 buf[];
-  const int za = planes[2 * blockIdx.x];
-  const int zb = (2 * blockIdx.x + 1 < nplanes) ? planes[2 * blockIdx.x + 1] : -1;
-  const int nxy = a.nx * a.ny;
-  const float* ra = r + (int64_t)za * nxy;
-  const float* rb = zb >= 0 ? r + (int64_t)zb * nxy : nullptr;
-  for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
-    const int y = k >> a.lgx, x = k & (a.nx - 1);
-    const int xr = a.lgx ? (int)brev(x, a.lgx) : 0, yr = a.lgy ? (int)brev(y, a.lgy) : 0;
-    buf[yr * a.nx + xr] = make_float2(ra[k], rb ? rb[k] : 0.f);
+// The 2-D transform runs as separate passes with many small CTAs: rows
+// along x (two real rows packed in one complex FFT), then columns along y.
+//
+// Forward x pass: rows y0 = 2q and y1 = 2q + 1 of a fluid plane form
+// C = r_y0 + i r_y1; after the FFT, R_y0(k) = (C(k) + conj C(-k)) / 2 and
+// R_y1(k) = (C(k) - conj C(-k)) / (2i) by the symmetry of real data.  One CTA
+// handles RXP row pairs.
+constexpr int RXP = 8;
+__global__ void __launch_bounds__(256) k_fft_x_fwd(const float* __restrict__ r,
+                                                   float2* __restrict__ spec,
+                                                   const int* __restrict__ planes, int npairs_row,
+                                                   int64_t total_pairs, SpecArgs a) {
+  extern __shared__ float2 rb[];
+  const int nx = a.nx, lgx = a.lgx;
+  const int64_t p0 = (int64_t)blockIdx.x * RXP;
+  const int cnt = (int)min((int64_t)RXP, total_pairs - p0);
+  for (int idx = threadIdx.x; idx < cnt * nx; idx += blockDim.x) {
+    const int q = idx >> lgx, x = idx & (nx - 1);
+    const int64_t pp = p0 + q;
+    const int z = planes[pp / npairs_row];
+    const int y0 = 2 * (int)(pp % npairs_row), y1 = y0 + 1;
+    const float* row = r + ((int64_t)z * a.ny) * nx;
+    const float v0 = row[(int64_t)y0 * nx + x];
+    const float v1 = (y1 < a.ny) ? row[(int64_t)y1 * nx + x] : 0.f;
+    rb[q * nx + (lgx ? (int)brev(x, lgx) : 0)] = make_float2(v0, v1);
   }
   __syncthreads();
-  fft_rows(buf, a.lgx, a.lgy, 1, a.nx, a.twx, -1.f);
-  fft_rows(buf, a.lgy, a.lgx, a.nx, 1, a.twy, -1.f);
-  float2* da = rhat + (int64_t)za * nxy;
-  float2* db = zb >= 0 ? rhat + (int64_t)zb * nxy : nullptr;
-  for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
-    const int ky = k >> a.lgx, kx = k & (a.nx - 1);
-    const int km = (((a.ny - ky) & (a.ny - 1)) << a.lgx) | ((a.nx - kx) & (a.nx - 1));
-    const float2 c = buf[k], cm = buf[km];
-    da[k] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
-    if (db) db[k] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
+  fft_rows(rb, lgx, 3, 1, nx, a.twx, -1.f);  // RXP = 8 = 2^3 rows
+  for (int idx = threadIdx.x; idx < cnt * nx; idx += blockDim.x) {
+    const int q = idx >> lgx, k = idx & (nx - 1);
+    const int64_t pp = p0 + q;
+    const int z = planes[pp / npairs_row];
+    const int y0 = 2 * (int)(pp % npairs_row), y1 = y0 + 1;
+    const float2 c = rb[q * nx + k], cm = rb[q * nx + ((nx - k) & (nx - 1))];
+    float2* out = spec + ((int64_t)z * a.ny) * nx;
+    out[(int64_t)y0 * nx + k] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
+    if (y1 < a.ny) out[(int64_t)y1 * nx + k] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
   }
 }
 
-// Inverse of two real planes at once: C = E_a + i E_b, inverse 2-D FFT, the
-// real part corrects plane a and the imaginary part plane b (in place,
-// psi += round(e)).
-__global__ void __launch_bounds__(512) k_fft_inv2_apply(const float2* __restrict__ ehat,
-                                                        const int* __restrict__ planes,
-                                                        int nplanes, SpecArgs a, int64_t* psi) {
-  extern __shared__ float2 buf[];
-  const int za = planes[2 * blockIdx.x];
-  const int zb = (2 * blockIdx.x + 1 < nplanes) ? planes[2 * blockIdx.x + 1] : -1;
-  const int nxy = a.nx * a.ny;
-  const float2* ea = ehat + (int64_t)za * nxy;
-  const float2* eb = zb >= 0 ? ehat + (int64_t)zb * nxy : nullptr;
-  for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
-    const int y = k >> a.lgx, x = k & (a.nx - 1);
-    const int xr = a.lgx ? (int)brev(x, a.lgx) : 0, yr = a.lgy ? (int)brev(y, a.lgy) : 0;
-    const float2 va = ea[k];
-    const float2 vb = eb ? eb[k] : make_float2(0.f, 0.f);
-    buf[yr * a.nx + xr] = make_float2(va.x - vb.y, va.y + vb.x);
+// y pass (in place): one CTA takes CYC consecutive kx columns of one plane,
+// staged in shared memory as [y][column] (coalesced), FFT along y.
+constexpr int CYC = 16;
+__global__ void __launch_bounds__(256) k_fft_y(float2* __restrict__ spec,
+                                               const int* __restrict__ planes, int cols_per_plane,
+                                               SpecArgs a, float sign) {
+  extern __shared__ float2 cb[];
+  const int ny = a.ny, lgy = a.lgy, nx = a.nx;
+  const int z = planes[blockIdx.x / cols_per_plane];
+  const int k0 = (blockIdx.x % cols_per_plane) * CYC;
+  const int w = min(CYC, nx - k0);
+  float2* base = spec + (int64_t)z * ny * nx + k0;
+  for (int idx = threadIdx.x; idx < ny * CYC; idx += blockDim.x) {
+    const int y = idx / CYC, j = idx - y * CYC;
+    if (j < w) cb[(lgy ? (int)brev(y, lgy) : 0) * CYC + j] = base[(int64_t)y * nx + j];
   }
   __syncthreads();
-  fft_rows(buf, a.lgx, a.lgy, 1, a.nx, a.twx, 1.f);
-  fft_rows(buf, a.lgy, a.lgx, a.nx, 1, a.twy, 1.f);
-  const float scale = 1.0f / (float)nxy;
-  for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
-    const float2 c = buf[k];
-    psi[(int64_t)za * nxy + k] += llrintf(c.x * scale * PSI_SCALE_F);
-    if (zb >= 0) psi[(int64_t)zb * nxy + k] += llrintf(c.y * scale * PSI_SCALE_F);
+  fft_rows(cb, lgy, 4, CYC, 1, a.twy, sign);  // CYC = 16 = 2^4 columns
+  for (int idx = threadIdx.x; idx < ny * CYC; idx += blockDim.x) {
+    const int y = idx / CYC, j = idx - y * CYC;
+    if (j < w) base[(int64_t)y * nx + j] = cb[y * CYC + j];
+  }
+}
+
+// Inverse x pass fused with the update: rows y0, y1 of the corrections
+// (Hermitian spectra) form C = E_y0 + i E_y1; the inverse FFT gives e_y0 in
+// the real and e_y1 in the imaginary part; psi += round(e / (nx ny)).
+__global__ void __launch_bounds__(256) k_fft_x_inv_apply(const float2* __restrict__ spec,
+                                                         const int* __restrict__ planes,
+                                                         int npairs_row, int64_t total_pairs,
+                                                         SpecArgs a, int64_t* psi) {
+  extern __shared__ float2 rb[];
+  const int nx = a.nx, lgx = a.lgx;
+  const int64_t p0 = (int64_t)blockIdx.x * RXP;
+  const int cnt = (int)min((int64_t)RXP, total_pairs - p0);
+  for (int idx = threadIdx.x; idx < cnt * nx; idx += blockDim.x) {
+    const int q = idx >> lgx, k = idx & (nx - 1);
+    const int64_t pp = p0 + q;
+    const int z = planes[pp / npairs_row];
+    const int y0 = 2 * (int)(pp % npairs_row), y1 = y0 + 1;
+    const float2* row = spec + ((int64_t)z * a.ny) * nx;
+    const float2 e0 = row[(int64_t)y0 * nx + k];
+    const float2 e1 = (y1 < a.ny) ? row[(int64_t)y1 * nx + k] : make_float2(0.f, 0.f);
+    rb[q * nx + (lgx ? (int)brev(k, lgx) : 0)] = make_float2(e0.x - e1.y, e0.y + e1.x);
+  }
+  __syncthreads();
+  fft_rows(rb, lgx, 3, 1, nx, a.twx, 1.f);
+  const float scale = PSI_SCALE_F / (float)(nx * a.ny);
+  for (int idx = threadIdx.x; idx < cnt * nx; idx += blockDim.x) {
+    const int q = idx >> lgx, x = idx & (nx - 1);
+    const int64_t pp = p0 + q;
+    const int z = planes[pp / npairs_row];
+    const int y0 = 2 * (int)(pp % npairs_row), y1 = y0 + 1;
+    const float2 c = rb[q * nx + x];
+    int64_t* row = psi + ((int64_t)z * a.ny) * nx;
+    row[(int64_t)y0 * nx + x] += llrintf(c.x * scale);
+    if (y1 < a.ny) row[(int64_t)y1 * nx + x] += llrintf(c.y * scale);
   }
 }
 
@@ -469,8 +506,8 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   spectral_free(h);
   const int nx = h->cfg.nx, ny = h->cfg.ny, nz = h->cfg.nz;
   const int lgx = ilog2(nx), lgy = ilog2(ny);
-  if (lgx < 0 || lgy < 0 || (int64_t)nx * ny > 16384) {
-    h->err = "spectral Poisson solver needs power-of-two nx, ny with nx*ny <= 16384";
+  if (lgx < 0 || lgy < 0) {
+    h->err = "spectral Poisson solver needs power-of-two nx, ny";
     return LBM_EINVAL;
   }
   const int64_t nxy = (int64_t)nx * ny;
@@ -609,9 +646,18 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   if (s->runs_fit && s->zsmem > 48 * 1024)
     LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->zsmem));
   s->smem = (size_t)nxy * sizeof(float2);
-  if (s->smem > 48 * 1024) {
-    LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_fwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem));
-    LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_inv2_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem));
+  {
+    const int xs = (int)(RXP * nx * sizeof(float2)), ys = (int)(CYC * ny * sizeof(float2));
+    if (xs > optin || ys > optin) {
+      h->err = "spectral Poisson solver: lattice rows too long for shared memory";
+      return LBM_EINVAL;
+    }
+    if (xs > 48 * 1024) {
+      LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_x_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, xs));
+      LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_x_inv_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, xs));
+    }
+    if (ys > 48 * 1024)
+      LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_y, cudaFuncAttributeMaxDynamicSharedMemorySize, ys));
   }
   return LBM_OK;
 }
@@ -669,9 +715,14 @@ cudaError_t spec_apply(lbm_t* h) {
   SpectralPlan* s = h->spec;
   Poisson& P = h->ps;
   const SpecArgs a = args_of(s);
-  const int threads = (int)std::min<int64_t>(512, std::max<int64_t>(32, (int64_t)s->nx * s->ny / 2));
-  const int npairs = (s->nplanes + 1) / 2;
-  k_fft_fwd2<<<npairs, threads, s->smem, h->st>>>(s->r, s->spec, s->planes, s->nplanes, a);
+  const int npairs_row = (s->ny + 1) / 2;
+  const int64_t total_pairs = (int64_t)s->nplanes * npairs_row;
+  const unsigned gx = (unsigned)((total_pairs + RXP - 1) / RXP);
+  const size_t xs = (size_t)RXP * s->nx * sizeof(float2);
+  const int cols = (s->nx + CYC - 1) / CYC;
+  const size_t ys = (size_t)CYC * s->ny * sizeof(float2);
+  k_fft_x_fwd<<<gx, 256, xs, h->st>>>(s->r, s->spec, s->planes, npairs_row, total_pairs, a);
+  k_fft_y<<<s->nplanes * cols, 256, ys, h->st>>>(s->spec, s->planes, cols, a, -1.f);
   if (s->lgz > 0) {
     k_zfft<<<nblk((int64_t)s->nx * s->ny, ZP), 256, (size_t)2 * ZP * s->nz * sizeof(float2), h->st>>>(
         s->spec, s->twz, s->lgz, a);
@@ -679,9 +730,10 @@ cudaError_t spec_apply(lbm_t* h) {
     dim3 g(nblk((int64_t)s->nx * s->ny, ZP), s->nruns);
     k_zsolve<<<g, 128, s->zsmem, h->st>>>(s->spec, s->runs, a);
   }
-  k_fft_inv2_apply<<<npairs, threads, s->smem, h->st>>>(s->spec, s->planes, s->nplanes, a,
-                                                       P.psi[P.cur]);
-  h->launches += 3;
+  k_fft_y<<<s->nplanes * cols, 256, ys, h->st>>>(s->spec, s->planes, cols, a, 1.f);
+  k_fft_x_inv_apply<<<gx, 256, xs, h->st>>>(s->spec, s->planes, npairs_row, total_pairs, a,
+                                             P.psi[P.cur]);
+  h->launches += 5;
   return cudaGetLastError();
 }
 
