@@ -93,15 +93,16 @@ struct SpecArgs {
 // C = r_y0 + i r_y1; after the FFT, R_y0(k) = (C(k) + conj C(-k)) / 2 and
 // R_y1(k) = (C(k) - conj C(-k)) / (2i) by the symmetry of real data.  One CTA
 // handles RXP row pairs.
-constexpr int RXP = 8;
 __global__ void __launch_bounds__(256) k_fft_x_fwd(const float* __restrict__ r,
                                                    float2* __restrict__ spec,
                                                    const int* __restrict__ planes, int npairs_row,
-                                                   int64_t total_pairs, SpecArgs a) {
+                                                   int64_t total_pairs, SpecArgs a, int lgr) {
   extern __shared__ float2 rb[];
   const int nx = a.nx, lgx = a.lgx;
-  const int64_t p0 = (int64_t)blockIdx.x * RXP;
-  const int cnt = (int)min((int64_t)RXP, total_pairs - p0);
+  const int rxp = 1 << lgr;  // row pairs per CTA
+  const int64_t p0 = (int64_t)blockIdx.x * rxp;
+  const int cnt = (int)min((int64_t)rxp, total_pairs - p0);
+#pragma unroll 4
   for (int idx = threadIdx.x; idx < cnt * nx; idx += blockDim.x) {
     const int q = idx >> lgx, x = idx & (nx - 1);
     const int64_t pp = p0 + q;
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(256) k_fft_x_fwd(const float* __restrict__ r,
     rb[q * nx + (lgx ? (int)brev(x, lgx) : 0)] = make_float2(v0, v1);
   }
   __syncthreads();
-  fft_rows(rb, lgx, 3, 1, nx, a.twx, -1.f);  // RXP = 8 = 2^3 rows
+  fft_rows(rb, lgx, lgr, 1, nx, a.twx, -1.f);
   for (int idx = threadIdx.x; idx < cnt * nx; idx += blockDim.x) {
     const int q = idx >> lgx, k = idx & (nx - 1);
     const int64_t pp = p0 + q;
@@ -128,24 +129,25 @@ __global__ void __launch_bounds__(256) k_fft_x_fwd(const float* __restrict__ r,
 
 // y pass (in place): one CTA takes CYC consecutive kx columns of one plane,
 // staged in shared memory as [y][column] (coalesced), FFT along y.
-constexpr int CYC = 16;
 __global__ void __launch_bounds__(256) k_fft_y(float2* __restrict__ spec,
                                                const int* __restrict__ planes, int cols_per_plane,
-                                               SpecArgs a, float sign) {
+                                               SpecArgs a, float sign, int lgc) {
   extern __shared__ float2 cb[];
   const int ny = a.ny, lgy = a.lgy, nx = a.nx;
+  const int CYC = 1 << lgc;  // columns per CTA
   const int z = planes[blockIdx.x / cols_per_plane];
   const int k0 = (blockIdx.x % cols_per_plane) * CYC;
   const int w = min(CYC, nx - k0);
   float2* base = spec + (int64_t)z * ny * nx + k0;
+#pragma unroll 4
   for (int idx = threadIdx.x; idx < ny * CYC; idx += blockDim.x) {
-    const int y = idx / CYC, j = idx - y * CYC;
+    const int y = idx >> lgc, j = idx & (CYC - 1);
     if (j < w) cb[(lgy ? (int)brev(y, lgy) : 0) * CYC + j] = base[(int64_t)y * nx + j];
   }
   __syncthreads();
-  fft_rows(cb, lgy, 4, CYC, 1, a.twy, sign);  // CYC = 16 = 2^4 columns
+  fft_rows(cb, lgy, lgc, CYC, 1, a.twy, sign);
   for (int idx = threadIdx.x; idx < ny * CYC; idx += blockDim.x) {
-    const int y = idx / CYC, j = idx - y * CYC;
+    const int y = idx >> lgc, j = idx & (CYC - 1);
     if (j < w) base[(int64_t)y * nx + j] = cb[y * CYC + j];
   }
 }
@@ -156,11 +158,12 @@ __global__ void __launch_bounds__(256) k_fft_y(float2* __restrict__ spec,
 __global__ void __launch_bounds__(256) k_fft_x_inv_apply(const float2* __restrict__ spec,
                                                          const int* __restrict__ planes,
                                                          int npairs_row, int64_t total_pairs,
-                                                         SpecArgs a, int64_t* psi) {
+                                                         SpecArgs a, int64_t* psi, int lgr) {
   extern __shared__ float2 rb[];
   const int nx = a.nx, lgx = a.lgx;
-  const int64_t p0 = (int64_t)blockIdx.x * RXP;
-  const int cnt = (int)min((int64_t)RXP, total_pairs - p0);
+  const int rxp = 1 << lgr;
+  const int64_t p0 = (int64_t)blockIdx.x * rxp;
+  const int cnt = (int)min((int64_t)rxp, total_pairs - p0);
   for (int idx = threadIdx.x; idx < cnt * nx; idx += blockDim.x) {
     const int q = idx >> lgx, k = idx & (nx - 1);
     const int64_t pp = p0 + q;
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(256) k_fft_x_inv_apply(const float2* __restric
     rb[q * nx + (lgx ? (int)brev(k, lgx) : 0)] = make_float2(e0.x - e1.y, e0.y + e1.x);
   }
   __syncthreads();
-  fft_rows(rb, lgx, 3, 1, nx, a.twx, 1.f);
+  fft_rows(rb, lgx, lgr, 1, nx, a.twx, 1.f);
   const float scale = PSI_SCALE_F / (float)(nx * a.ny);
   for (int idx = threadIdx.x; idx < cnt * nx; idx += blockDim.x) {
     const int q = idx >> lgx, x = idx & (nx - 1);
@@ -324,30 +327,47 @@ __global__ void __launch_bounds__(256) k_zfft(float2* __restrict__ x, const floa
   const int L = 1 << lgz;
   const int nxy = a.nx * a.ny;
   const int m0 = blockIdx.x * ZP;
-  float2* A = zb;
-  float2* B = zb + ZP * L;
   const int lgp = 5;  // log2(ZP)
-  for (int idx = threadIdx.x; idx < ZP * L; idx += blockDim.x) {
+  // stage: plane k of pencil j at zb[brev(k) * ZP + j] (coalesced loads)
+#pragma unroll 8
+  for (int idx = threadIdx.x; idx < ZP * L; idx += 256) {
     const int k = idx >> lgp, j = idx & (ZP - 1);
-    A[(int)brev(k, lgz) * ZP + j] =
+    zb[(int)brev(k, lgz) * ZP + j] =
         (m0 + j < nxy) ? x[(int64_t)k * nxy + m0 + j] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  fft_rows(A, lgz, lgp, ZP, 1, twz, -1.f);
+  fft_rows(zb, lgz, lgp, ZP, 1, twz, -1.f);
+  // divide by the eigenvalue and put the spectrum back in bit-reversed
+  // order for the inverse transform (through registers, one buffer)
   const float invL = 1.0f / (float)L;
-  for (int idx = threadIdx.x; idx < ZP * L; idx += blockDim.x) {
-    const int kz = idx >> lgp, j = idx & (ZP - 1);
-    const int m = m0 + j;
-    const float lam = (m < nxy ? a.lam_xy[m] : 1.f) + a.lam_z[kz];
-    const float sc = (m == 0 && kz == 0) ? 0.f : invL / lam;
-    const float2 v = A[idx];
-    B[(int)brev(kz, lgz) * ZP + j] = make_float2(v.x * sc, v.y * sc);
+  constexpr int PER = 32;  // elements per thread for L <= 256 (ZP * L / 256)
+  float2 v[PER];
+  int dst[PER];
+  int cnt = 0;
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int idx = threadIdx.x + t * 256;
+    if (idx < ZP * L) {
+      const int kz = idx >> lgp, j = idx & (ZP - 1);
+      const int m = m0 + j;
+      const float lam = (m < nxy ? a.lam_xy[m] : 1.f) + a.lam_z[kz];
+      const float sc = (m == 0 && kz == 0) ? 0.f : invL / lam;
+      const float2 c = zb[idx];
+      v[t] = make_float2(c.x * sc, c.y * sc);
+      dst[t] = (int)brev(kz, lgz) * ZP + j;
+      cnt = t + 1;
+    }
   }
   __syncthreads();
-  fft_rows(B, lgz, lgp, ZP, 1, twz, 1.f);
-  for (int idx = threadIdx.x; idx < ZP * L; idx += blockDim.x) {
+#pragma unroll
+  for (int t = 0; t < PER; ++t)
+    if (t < cnt) zb[dst[t]] = v[t];
+  __syncthreads();
+  fft_rows(zb, lgz, lgp, ZP, 1, twz, 1.f);
+#pragma unroll 8
+  for (int idx = threadIdx.x; idx < ZP * L; idx += 256) {
     const int k = idx >> lgp, j = idx & (ZP - 1);
-    if (m0 + j < nxy) x[(int64_t)k * nxy + m0 + j] = B[idx];
+    if (m0 + j < nxy) x[(int64_t)k * nxy + m0 + j] = zb[idx];
   }
 }
 
@@ -620,8 +640,8 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   }
   int optin = 0;
   LBM_CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
-  if (runs.size() == 1 && runs[0].cyclic && ilog2(nz) > 0 && nz >= 4 &&
-      (size_t)2 * ZP * nz * sizeof(float2) <= (size_t)optin) {
+  if (runs.size() == 1 && runs[0].cyclic && ilog2(nz) > 0 && nz >= 4 && nz <= 256 &&
+      (size_t)ZP * nz * sizeof(float2) <= (size_t)optin) {
     s->lgz = ilog2(nz);
     auto tz = twiddles(nz);
     if (!al((void**)&s->twz, tz.size() * sizeof(float2))) {
@@ -630,7 +650,7 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
       return LBM_ENOMEM;
     }
     LBM_CUDA_TRY(h, cudaMemcpy(s->twz, tz.data(), tz.size() * sizeof(float2), cudaMemcpyHostToDevice));
-    const size_t zf = (size_t)2 * ZP * nz * sizeof(float2);
+    const size_t zf = (size_t)ZP * nz * sizeof(float2);
     if (zf > 48 * 1024)
       LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_zfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zf));
   }
@@ -647,7 +667,8 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
     LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->zsmem));
   s->smem = (size_t)nxy * sizeof(float2);
   {
-    const int xs = (int)(RXP * nx * sizeof(float2)), ys = (int)(CYC * ny * sizeof(float2));
+    const int lgr = std::max(0, 10 - lgx), lgc = std::max(0, 10 - lgy);
+    const int xs = (int)(((size_t)nx << lgr) * sizeof(float2)), ys = (int)(((size_t)ny << lgc) * sizeof(float2));
     if (xs > optin || ys > optin) {
       h->err = "spectral Poisson solver: lattice rows too long for shared memory";
       return LBM_EINVAL;
@@ -717,22 +738,24 @@ cudaError_t spec_apply(lbm_t* h) {
   const SpecArgs a = args_of(s);
   const int npairs_row = (s->ny + 1) / 2;
   const int64_t total_pairs = (int64_t)s->nplanes * npairs_row;
-  const unsigned gx = (unsigned)((total_pairs + RXP - 1) / RXP);
-  const size_t xs = (size_t)RXP * s->nx * sizeof(float2);
-  const int cols = (s->nx + CYC - 1) / CYC;
-  const size_t ys = (size_t)CYC * s->ny * sizeof(float2);
-  k_fft_x_fwd<<<gx, 256, xs, h->st>>>(s->r, s->spec, s->planes, npairs_row, total_pairs, a);
-  k_fft_y<<<s->nplanes * cols, 256, ys, h->st>>>(s->spec, s->planes, cols, a, -1.f);
+  // about 1024 complex values per CTA in each pass
+  const int lgr = std::max(0, 10 - s->lgx), lgc = std::max(0, 10 - s->lgy);
+  const unsigned gx = (unsigned)((total_pairs + (1 << lgr) - 1) >> lgr);
+  const size_t xs = ((size_t)s->nx << lgr) * sizeof(float2);
+  const int cols = (s->nx + (1 << lgc) - 1) >> lgc;
+  const size_t ys = ((size_t)s->ny << lgc) * sizeof(float2);
+  k_fft_x_fwd<<<gx, 256, xs, h->st>>>(s->r, s->spec, s->planes, npairs_row, total_pairs, a, lgr);
+  k_fft_y<<<s->nplanes * cols, 256, ys, h->st>>>(s->spec, s->planes, cols, a, -1.f, lgc);
   if (s->lgz > 0) {
-    k_zfft<<<nblk((int64_t)s->nx * s->ny, ZP), 256, (size_t)2 * ZP * s->nz * sizeof(float2), h->st>>>(
+    k_zfft<<<nblk((int64_t)s->nx * s->ny, ZP), 256, (size_t)ZP * s->nz * sizeof(float2), h->st>>>(
         s->spec, s->twz, s->lgz, a);
   } else {
     dim3 g(nblk((int64_t)s->nx * s->ny, ZP), s->nruns);
     k_zsolve<<<g, 128, s->zsmem, h->st>>>(s->spec, s->runs, a);
   }
-  k_fft_y<<<s->nplanes * cols, 256, ys, h->st>>>(s->spec, s->planes, cols, a, 1.f);
+  k_fft_y<<<s->nplanes * cols, 256, ys, h->st>>>(s->spec, s->planes, cols, a, 1.f, lgc);
   k_fft_x_inv_apply<<<gx, 256, xs, h->st>>>(s->spec, s->planes, npairs_row, total_pairs, a,
-                                             P.psi[P.cur]);
+                                             P.psi[P.cur], lgr);
   h->launches += 5;
   return cudaGetLastError();
 }
