@@ -177,6 +177,19 @@ lbm_status lbm_synchronize(lbm_t* h);
  * pointer may be NULL.  Zero at wall nodes.  Host buffers.                */
 lbm_status lbm_get_moments(lbm_t* h, int s, double* n, double* u);
 
+/* Moments as lbm_get_moments, for callers that must not allocate device
+ * memory while they run (a device pool reserved by another framework, a
+ * loop that cannot afford the device synchronisation of cudaMalloc).  The
+ * paper has no counterpart: this is a library convenience.  It calls no
+ * cudaMalloc / cudaFree: the device staging of the result is a static
+ * device array of LBM_NOALLOC_MAX_NODES nodes x 4 doubles (8 MiB) that every
+ * GPU loading the library holds until the process exits.  LBM_EINVAL when
+ * the lattice has more nodes.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race.           */
+#define LBM_NOALLOC_MAX_NODES (1 << 18)
+lbm_status lbm_get_moments_noalloc(lbm_t* h, int s, double* n, double* u);
+
 /* Populations f_p(r, t) of species s (19*N doubles, [19][N]); zero at wall
  * nodes.  Host buffer.                                                    */
 lbm_status lbm_get_populations(lbm_t* h, int s, double* f);

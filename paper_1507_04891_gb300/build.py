@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
-SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_poisson.cu", "lbm_spectral.cu", "lbm_nn.cu"]
+SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_poisson.cu", "lbm_spectral.cu", "lbm_nn.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]

@@ -31,7 +31,7 @@ EXPORTED = [
     "lbm_set_state", "lbm_set_timing", "lbm_get_timing", "lbm_num_nodes",
     "lbm_create_stack", "lbm_instance_z0", "lbm_set_plane_omega_drag", "lbm_autotune",
     "lbm_nn_init", "lbm_nn_collect", "lbm_nn_train", "lbm_nn_use", "lbm_nn_params",
-    "lbm_nn_loss_grad", "lbm_nn_stats", "lbm_state_len", "lbm_stream", "lbm_last_error",
+    "lbm_nn_loss_grad", "lbm_nn_stats", "lbm_get_moments_noalloc", "lbm_state_len", "lbm_stream", "lbm_last_error",
 ]
 
 
@@ -83,6 +83,8 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_synchronize.restype = I
     lib.lbm_get_moments.argtypes = [P, I, P, P]
     lib.lbm_get_moments.restype = I
+    lib.lbm_get_moments_noalloc.argtypes = [P, I, P, P]
+    lib.lbm_get_moments_noalloc.restype = I
     lib.lbm_get_populations.argtypes = [P, I, P]
     lib.lbm_get_populations.restype = I
     lib.lbm_get_potential.argtypes = [P, P]
@@ -292,6 +294,13 @@ class Lattice:
         n = np.empty(self.shape)
         u = np.empty((3,) + self.shape)
         self._check(self._lib.lbm_get_moments(self.h, int(s), _ptr(n), _ptr(u)))
+        return n, u
+
+    def get_moments_noalloc(self, s):
+        """lbm_get_moments_noalloc: no device allocation (static staging)."""
+        n = np.empty(self.shape)
+        u = np.empty((3,) + self.shape)
+        self._check(self._lib.lbm_get_moments_noalloc(self.h, int(s), _ptr(n), _ptr(u)))
         return n, u
 
     def get_populations(self, s):
