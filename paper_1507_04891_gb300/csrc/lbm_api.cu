@@ -497,6 +497,7 @@ lbm_status lbm_get_moments(lbm_t* h, int s, double* n, double* u) {
   if (!(h->species_set >> s & 1u)) return fail(h, LBM_EINVAL, "species not set");
   if (!n && !u) return LBM_OK;
   cudaSetDevice(h->dev);
+  h->st = h->own;  // calls without a stream argument use the library's stream
   const int64_t N = h->N;
   Scratch sc;
   if (cudaMalloc(&sc.p, 4 * N * sizeof(double)) != cudaSuccess)
@@ -514,6 +515,7 @@ lbm_status lbm_get_populations(lbm_t* h, int s, double* f) {
   if (!h) return LBM_EINVAL;
   if (s < 0 || s >= h->S || !f) return fail(h, LBM_EINVAL, "bad species index or NULL buffer");
   cudaSetDevice(h->dev);
+  h->st = h->own;  // calls without a stream argument use the library's stream
   const int64_t N = h->N;
   Scratch sc;
   if (cudaMalloc(&sc.p, (size_t)Q * N * sizeof(double)) != cudaSuccess)
@@ -528,6 +530,7 @@ lbm_status lbm_get_potential(lbm_t* h, double* psi) {
   if (!h || !psi) return LBM_EINVAL;
   if (!(h->cfg.bjerrum > 0.0)) return fail(h, LBM_EINVAL, "neutral lattice has no potential");
   cudaSetDevice(h->dev);
+  h->st = h->own;  // calls without a stream argument use the library's stream
   const int64_t N = h->N;
   Scratch sc;
   if (cudaMalloc(&sc.p, N * sizeof(double)) != cudaSuccess)
@@ -579,6 +582,7 @@ lbm_status lbm_diagnostics(lbm_t* h, double* out) {
   if (!h || !out) return LBM_EINVAL;
   if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set first");
   cudaSetDevice(h->dev);
+  h->st = h->own;  // calls without a stream argument use the library's stream
   LBM_CUDA_TRY(h, cudaMemsetAsync(h->dred, 0, (MAX_SPECIES + 8) * sizeof(double), h->st));
   LBM_CUDA_TRY(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->st));
   LBM_CUDA_TRY(h, launch_diagnostics(h));
@@ -603,6 +607,7 @@ lbm_status lbm_get_state(lbm_t* h, float* state, int64_t* step) {
   if (h->cfg.storage != LBM_FP32)
     return fail(h, LBM_EINVAL, "raw state access needs FP32 storage");
   cudaSetDevice(h->dev);
+  h->st = h->own;  // calls without a stream argument use the library's stream
   LBM_CUDA_TRY(h, cudaMemcpyAsync(state, h->f[h->cur], (size_t)h->S * Q * h->N * sizeof(float),
                                   cudaMemcpyDeviceToHost, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
@@ -616,6 +621,7 @@ lbm_status lbm_set_state(lbm_t* h, const float* state, int64_t step) {
     return fail(h, LBM_EINVAL, "raw state access needs FP32 storage");
   if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set first");
   cudaSetDevice(h->dev);
+  h->st = h->own;  // calls without a stream argument use the library's stream
   LBM_CUDA_TRY(h, cudaMemcpyAsync(h->f[h->cur], state, (size_t)h->S * Q * h->N * sizeof(float),
                                   cudaMemcpyHostToDevice, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
