@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--poisson", default="fft", choices=["mg", "sor", "fft"])
     ap.add_argument("--no-alt", action="store_true", help="skip the multigrid comparison run")
-    ap.add_argument("--only", choices=["batched", "learned"], default=None,
+    ap.add_argument("--only", choices=["batched", "learned", "slit"], default=None,
                     help="run one extra measurement alone and print it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-slit and learned-guess measurements")
@@ -313,6 +313,57 @@ def run_learned(lbm, WL, n=64, steps=10, local=0):
     return out
 
 
+def run_slit(lbm, WL, steps=2000, local=0):
+    """Charged slit 64x64x(64 + 2 walls), wall charge -0.01 per node, Debye
+    length 8, field 1e-4 along x: FP32, FP16 and BF16 storage at Sc 1 ... 1000
+    (graph steps, spectral Poisson): throughput, the 16-bit fields against
+    FP32, and the electro-osmotic mass flow rate I_m = sum_z rho u_x."""
+    import torch
+    out = []
+    for sc in (1.0, 10.0, 100.0, 1000.0):
+        wl = WL.slit(nx=64, ny=64, width=64, sigma=-0.01, debye=8.0, e_field=1e-4, schmidt=sc)
+        od = lbm.omega_drag_for_schmidt(1.0, sc)
+        fields = {}
+        row = {"sc": sc, "omega_drag": od}
+        for storage in ("fp32", "fp16", "bf16"):
+            lat = lbm.Lattice(64, 64, 66, 3, omega_drag=od, bjerrum=wl.bjerrum, e_ext=wl.e_ext,
+                              storage=storage, poisson="fft", step_graph=True, device=local)
+            lat.set_walls(wl.solid, wl.sigma)
+            for s in range(3):
+                lat.set_species(s, 1.0, wl.valence[s], np.where(wl.solid, 1.0, wl.n0[s]))
+            lat.step(3)
+            lat.synchronize()
+            st = torch.cuda.ExternalStream(lat.stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            lat.step(steps)
+            e1.record(st)
+            lat.synchronize()
+            ms = e0.elapsed_time(e1)
+            mom = [lat.get_moments(s) for s in range(3)]
+            n = np.stack([m[0] for m in mom])
+            j = np.stack([m[0][None] * m[1] for m in mom])
+            fields[storage] = (n, j)
+            jx = j[:, 0].sum(0)  # mixture momentum density along x
+            im = float(jx[1:-1].mean(axis=(1, 2)).sum())
+            row[storage] = {"value": 3 * wl.sites * steps / (ms / 1e3) / 1e6,
+                            "ms_per_step": ms / steps, "mass_flow_rate": im,
+                            "poisson_residual_last": lat.diagnostics()["poisson_residual"]}
+            lat.destroy()
+        fl = ~wl.solid
+        n32, j32 = fields["fp32"]
+        for storage in ("fp16", "bf16"):
+            n16, j16 = fields[storage]
+            row[storage]["max_rel_density_error_vs_fp32"] = float(
+                (np.abs(n16 - n32)[:, fl] / n32[:, fl]).max())
+            row[storage]["max_momentum_error_vs_fp32"] = float(
+                (np.abs(j16 - j32)[:, :, fl] / (n32[:, None, fl] / math.sqrt(3.0))).max())
+        out.append(row)
+    return {"workload": "slit 64x64x66, sigma -0.01, Debye 8, E 1e-4, %d steps" % steps,
+            "runs": out}
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -473,8 +524,12 @@ def main():
         from paper_1507_04891_gb300 import workloads as WL
         from paper_1507_04891_gb300.build import build_library
         build_library()
-        res = (run_batched(lbm, WL, steps=max(1, args.steps)) if args.only == "batched"
-               else run_learned(lbm, WL))
+        if args.only == "batched":
+            res = run_batched(lbm, WL, steps=max(1, args.steps))
+        elif args.only == "slit":
+            res = run_slit(lbm, WL, steps=max(1, args.steps))
+        else:
+            res = run_learned(lbm, WL)
         print(json.dumps({"metric": METRIC, "only": args.only, **res}), flush=True)
         return 0
     if args.impl == "reference":

@@ -55,9 +55,7 @@ def test_full_size_invariants_over_50_steps():
     # species mass (FP64 sums of FP32 state) and total momentum
     assert np.all(np.abs(d1["mass"] / d0["mass"] - 1) <= 1e-6)
     assert np.all(np.abs(d1["momentum"]) <= 1e-6 * d0["mass"].sum() * CS)
-    # the potential of the last step solves the finite-volume problem of
-    # its own charge to 1e-8 under the oracle's FP64 operator: rebuild that
-    # charge from the state before the last step
+    # every solve of the run reached the tolerance
     assert d1["poisson_residual"] <= 1e-8 and not d1["unstable"]
 
 
