@@ -52,10 +52,11 @@ typedef enum {
 enum { LBM_FP32 = 0, LBM_FP16_SHIFT = 1, LBM_BF16_SHIFT = 2 };
 /* Poisson solvers.  MG: geometric multigrid (any wall geometry).  SOR:
  * red-black successive over-relaxation (any geometry; slow, a reference).
- * FFT: 2-D FFT in x, y with tridiagonal solves along z, exact in one pass
- * up to FP32 rounding; needs power-of-two nx, ny with nx*ny <= 16384 and
- * every z-plane all fluid or all wall (periodic boxes, slits, stacks of
- * slits); the source mean is removed per run of fluid planes.            */
+ * FFT: 2-D FFT in x, y with an FFT (periodic power-of-two nz, 8..256) or
+ * tridiagonal solves along z, exact in one pass up to FP32 rounding; needs
+ * power-of-two nx, ny in [8, 256] with nx*ny <= 16384 and every z-plane
+ * all fluid or all wall (periodic boxes, slits, stacks of slits); the
+ * source mean is removed per run of fluid planes.                        */
 enum { LBM_POISSON_MG = 0, LBM_POISSON_SOR = 1, LBM_POISSON_FFT = 2 };
 
 typedef struct {

@@ -14,10 +14,17 @@
 // problem to FP32 accuracy; it is used for defect correction on the exact
 // fixed-point residual, so two applications usually reach 1e-8.
 //
-// Kernels per application: forward FFT of the residual, two real planes per
-// complex transform (shared memory, radix 2); along z an FFT (periodic
-// power-of-two z) or one tridiagonal solve per mode and run; inverse FFT
-// fused with the update psi += round(e).
+// One application is three kernels:
+//   k_plane_fwd  one CTA per fluid plane (or several small planes): the
+//                exact residual of the plane, its real-to-complex 2-D FFT
+//                (two real rows per complex transform along x, then the
+//                nx/2 + 1 columns along y), the half spectrum to memory;
+//   k_zfft / k_zsolve  along z for every mode: FFT, division by the
+//                eigenvalue, inverse FFT (one periodic power-of-two run),
+//                else one tridiagonal solve per mode and run;
+//   k_plane_inv  inverse 2-D FFT of each plane fused with psi += round(e).
+// The FFTs keep eight values per thread in registers (Stockham stages of
+// radix 8, then 4 or 2) and exchange through shared memory between stages.
 #include <math.h>
 
 #include <algorithm>
@@ -34,158 +41,430 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-
-__device__ __forceinline__ unsigned brev(unsigned v, int bits) {
-  return __brev(v) >> (32 - bits);
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// a * (sign i)
+__device__ __forceinline__ float2 cmul_si(float2 a, float sign) {
+  return make_float2(-sign * a.y, sign * a.x);
 }
 
-// In-place radix-2 FFTs of `count` rows of length n = 2^lg stored with
-// element stride `es` and row stride `rs` in shared memory (count = 2^lgc).
-// Input in bit-reversed order.  tw[k] = exp(-2 pi i k / n) (k < n/2); sign
-// -1 forward, +1 inverse (conjugate twiddles).  Consecutive threads take
-// consecutive butterflies of one row when the elements are contiguous
-// (es == 1) and the same butterfly of consecutive rows otherwise, so that
-// shared-memory accesses never stride by a row.
-__device__ void fft_rows(float2* a, int lg, int lgc, int es, int rs,
-                         const float2* tw, float sign) {
-  if (lg == 0) return;
-  const int half = 1 << (lg - 1);
-  const int total = half << lgc;
-  for (int s = 1; s <= lg; ++s) {
-    const int mh = 1 << (s - 1);
-    const int tshift = lg - s;  // twiddle index step n/m = 2^(lg - s)
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      int row, b;
-      if (es == 1) {
-        row = t >> (lg - 1);
-        b = t & (half - 1);
-      } else {
-        row = t & ((1 << lgc) - 1);
-        b = t >> lgc;
-      }
-      const int j = b & (mh - 1);
-      const int i0 = ((b >> (s - 1)) << s) + j, i1 = i0 + mh;
-      float2 w = tw[j << tshift];
-      w.y *= -sign;
-      float2* p0 = a + row * rs + i0 * es;
-      float2* p1 = a + row * rs + i1 * es;
-      const float2 u = *p0;
-      const float2 v = cmul(w, *p1);
-      *p0 = make_float2(u.x + v.x, u.y + v.y);
-      *p1 = make_float2(u.x - v.x, u.y - v.y);
-    }
+// Small DFTs in place, X_q = sum_r a_r exp(sign 2 pi i r q / R).
+__device__ __forceinline__ void dft2(float2& a0, float2& a1) {
+  const float2 t = a0;
+  a0 = cadd(t, a1);
+  a1 = csub(t, a1);
+}
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3, float sign) {
+  const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+  const float2 t2 = cadd(a1, a3), t3 = cmul_si(csub(a1, a3), sign);
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+// radix 8 as two radix-4 transforms of the even and odd inputs joined by
+// the twiddles exp(sign 2 pi i q / 8), q = 0..3
+__device__ __forceinline__ void dft8(float2 (&v)[8], float sign) {
+  dft4(v[0], v[2], v[4], v[6], sign);
+  dft4(v[1], v[3], v[5], v[7], sign);
+  const float c = 0.70710678118654752f;
+  const float2 o0 = v[1];
+  const float2 o1 = cmul(v[3], make_float2(c, sign * c));
+  const float2 o2 = cmul_si(v[5], sign);
+  const float2 o3 = cmul(v[7], make_float2(-c, sign * c));
+  const float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1);
+  v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2);
+  v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3);
+  v[7] = csub(e3, o3);
+}
+
+// Shared-memory line of one transform.  PadLine: contiguous, one spare slot
+// after every eight elements (the first Stockham stage writes with stride 8,
+// which would hit two banks only).  StrideLine: element d at d * es, used
+// when the lanes of a warp belong to different transforms (consecutive
+// lanes, consecutive lines).
+struct PadLine {
+  float2* p;
+  __device__ __forceinline__ float2& operator[](int d) const { return p[d + (d >> 3)]; }
+};
+struct StrideLine {
+  float2* p;
+  int es;
+  __device__ __forceinline__ float2& operator[](int d) const { return p[d * es]; }
+};
+__host__ __device__ constexpr int padded_len(int L) { return L + (L >> 3); }
+
+template <bool CTA>
+__device__ __forceinline__ void line_sync() {
+  if (CTA)
     __syncthreads();
+  else
+    __syncwarp();
+}
+
+// FFT of length L = 2^lg (8 <= L <= 256) held by T = L / 8 threads, thread t
+// holding elements t + u T (u = 0..7) before and after.  Stockham autosort
+// stages (the formulation of Stockham's self-sorting FFT used for GPUs by
+// Govindaraju et al., SC 2008): the stage of radix R after earlier radices
+// of product Ns takes butterfly j's inputs x[j + r L/R], multiplies input r
+// by w^(r (j mod Ns) L / (Ns R)) with w = exp(sign 2 pi i / L), transforms
+// them, and writes output q to (j div Ns) Ns R + (j mod Ns) + q Ns.  With
+// eight values per thread a radix-R stage is 8/R butterflies j = t + s T per
+// thread; the last stage's outputs fall on j + q L/R = t + (s + q 8/R) T,
+// the starting distribution, so they stay in registers.  tw[m] =
+// exp(-2 pi i m / L), m < L (the inverse conjugates it).  CTA: the T
+// threads are in different warps (barrier), else in one warp.
+template <bool CTA, class Line>
+__device__ __forceinline__ void fft_regs(float2 (&v)[8], int t, int lg, Line line,
+                                         const float2* __restrict__ tw, float sign) {
+  const int T = 1 << (lg - 3);
+  int lns = 0;  // log2 Ns
+  int rem = lg;
+  while (true) {
+    const int lr = rem >= 3 ? 3 : rem;
+    rem -= lr;
+    const int Ns = 1 << lns;
+    const int tws = lg - lns - lr;  // log2(L / (Ns R))
+    if (lr == 3) {
+      if (lns > 0) {
+        const int k = t & (Ns - 1);
+#pragma unroll
+        for (int r = 1; r < 8; ++r) {
+          float2 w = __ldg(tw + ((r * k) << tws));
+          w.y *= -sign;
+          v[r] = cmul(v[r], w);
+        }
+      }
+      dft8(v, sign);
+    } else if (lr == 2) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (lns > 0) {
+          const int k = (t + s * T) & (Ns - 1);
+#pragma unroll
+          for (int r = 1; r < 4; ++r) {
+            float2 w = __ldg(tw + ((r * k) << tws));
+            w.y *= -sign;
+            v[s + 2 * r] = cmul(v[s + 2 * r], w);
+          }
+        }
+        dft4(v[s], v[s + 2], v[s + 4], v[s + 6], sign);
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        if (lns > 0) {
+          const int k = (t + s * T) & (Ns - 1);
+          float2 w = __ldg(tw + (k << tws));
+          w.y *= -sign;
+          v[s + 4] = cmul(v[s + 4], w);
+        }
+        dft2(v[s], v[s + 4]);
+      }
+    }
+    if (rem == 0) break;
+    // slot u = s + G q holds output q of butterfly j = t + s T (G = 8 / R)
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int s = u & ((8 >> lr) - 1), q = u >> (3 - lr);
+      const int j = t + s * T;
+      line[((j >> lns) << (lns + lr)) + (j & (Ns - 1)) + (q << lns)] = v[u];
+    }
+    line_sync<CTA>();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = line[t + u * T];
+    line_sync<CTA>();
+    lns += lr;
   }
 }
 
 struct SpecArgs {
-  int nx, ny, nz, lgx, lgy;
-  const float2* twx;
+  int nx, ny, nz, lgx, lgy, lgz;
+  int H;       // nx / 2: the half spectrum keeps kx = 0..H
+  int mxy;     // modes per plane, (H + 1) ny, mode m = ky (H + 1) + kx
+  int lgtp;    // log2 of the threads per plane in the plane kernels (nx ny / 16)
+  const float2* twx;  // exp(-2 pi i m / n), m < n, per axis
   const float2* twy;
-  const float* lam_xy;  // eigenvalue of the x-y Laplacian per mode (nx*ny)
-  const float* lam_z;   // eigenvalue along a periodic z per kz (nz) or NULL
+  const float2* twz;
+  const float* lamx;  // 2 - 2 cos(2 pi k / n): H + 1, ny and nz values
+  const float* lamy;
+  const float* lamz;
 };
 
-// The 2-D transform runs as separate passes with many small CTAs: rows
-// along x (two real rows packed in one complex FFT), then columns along y.
-//
-// Forward x pass: rows y0 = 2q and y1 = 2q + 1 of a fluid plane form
-// C = r_y0 + i r_y1; after the FFT, R_y0(k) = (C(k) + conj C(-k)) / 2 and
-// R_y1(k) = (C(k) - conj C(-k)) / (2i) by the symmetry of real data.  One CTA
-// handles RXP row pairs.
-__global__ void __launch_bounds__(256) k_fft_x_fwd(const float* __restrict__ r,
-                                                   float2* __restrict__ spec,
-                                                   const int* __restrict__ planes, int npairs_row,
-                                                   int64_t total_pairs, SpecArgs a, int lgr) {
-  extern __shared__ float2 rb[];
-  const int nx = a.nx, lgx = a.lgx;
-  const int rxp = 1 << lgr;  // row pairs per CTA
-  const int64_t p0 = (int64_t)blockIdx.x * rxp;
-  const int cnt = (int)min((int64_t)rxp, total_pairs - p0);
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < cnt * nx; idx += blockDim.x) {
-    const int q = idx >> lgx, x = idx & (nx - 1);
-    const int64_t pp = p0 + q;
-    const int z = planes[pp / npairs_row];
-    const int y0 = 2 * (int)(pp % npairs_row), y1 = y0 + 1;
-    const float* row = r + ((int64_t)z * a.ny) * nx;
-    const float v0 = row[(int64_t)y0 * nx + x];
-    const float v1 = (y1 < a.ny) ? row[(int64_t)y1 * nx + x] : 0.f;
-    rb[q * nx + (lgx ? (int)brev(x, lgx) : 0)] = make_float2(v0, v1);
+// Shared memory of one plane in the plane kernels: the half spectrum
+// (mxy values, row stride H + 1, odd) and the padded lines of the row or
+// column transforms (nx ny / 2 elements with padding).
+__host__ __device__ constexpr int plane_smem_words(int nx, int ny) {
+  return (nx / 2 + 1) * ny + (nx * ny / 16) * 9;
+}
+
+// Forward plane kernel.  Thread w of a plane's TP = nx ny / 16 threads is,
+// along x, thread t = w mod (nx/8) of row pair q = w div (nx/8) (rows 2q and
+// 2q + 1 packed as C = r_2q + i r_2q+1), and along y thread w mod (ny/8) of
+// column c = w div (ny/8) (c = 0 carries the real columns kx = 0 and kx = H
+// packed the same way).  The residual r = s - <s> - A psi is computed
+// exactly in int64 as the x transform loads it; its squared norms (and the
+// source's) go to dsum[0], dsum[1] of the slot given.
+__global__ void __launch_bounds__(1024, 1) k_plane_fwd(
+    const int64_t* __restrict__ psi, const int64_t* __restrict__ src,
+    const long long* __restrict__ mean_z, const unsigned char* __restrict__ plane_fluid,
+    const int* __restrict__ planes, int nplanes, float2* __restrict__ spec, double* norms,
+    SpecArgs a) {
+  extern __shared__ __align__(16) float2 sm[];
+  __shared__ float red_r[32], red_s[32];
+  const int nx = a.nx, ny = a.ny, H = a.H, lgx = a.lgx, lgy = a.lgy;
+  const int tp = 1 << a.lgtp;
+  const int slot = threadIdx.x >> a.lgtp, w = threadIdx.x & (tp - 1);
+  const int pi = blockIdx.x * (blockDim.x >> a.lgtp) + slot;
+  const bool valid = pi < nplanes;
+  const int z = valid ? planes[pi] : 0;
+  float2* S = sm + (size_t)slot * plane_smem_words(nx, ny);
+  float2* scr = S + a.mxy;
+  const int rs = H + 1;  // row stride of S
+  float2 v[8];
+  float rr = 0.f, ss = 0.f;
+
+  // ---- x: residual rows 2q, 2q + 1 -> complex FFT -> half spectra
+  {
+    const int Tx = nx >> 3;
+    const int q = w >> (lgx - 3), t = w & (Tx - 1);
+    const PadLine line{scr + q * padded_len(nx)};
+    const int y0 = 2 * q;
+    if (valid) {
+      const int nz = a.nz;
+      const int64_t nxy = (int64_t)nx * ny;
+      const int zp = (z == nz - 1) ? 0 : z + 1, zm = (z == 0) ? nz - 1 : z - 1;
+      const bool up = nz > 1 && zp != z && plane_fluid[zp];
+      const bool dn = nz > 1 && zm != z && plane_fluid[zm];
+      const int64_t dup = (int64_t)(zp - z) * nxy, ddn = (int64_t)(zm - z) * nxy;
+      const long long mz = mean_z[z];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int x = t + u * Tx;
+        float rv[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int y = y0 + h;
+          const int64_t i = ((int64_t)z * ny + y) * nx + x;
+          const int64_t pc = psi[i];
+          int64_t Ap = 4 * pc;
+          Ap -= psi[i + (x == nx - 1 ? -(nx - 1) : 1)];
+          Ap -= psi[i + (x == 0 ? nx - 1 : -1)];
+          Ap -= psi[i + (y == ny - 1 ? -(int64_t)(ny - 1) * nx : nx)];
+          Ap -= psi[i + (y == 0 ? (int64_t)(ny - 1) * nx : -nx)];
+          if (up) Ap += pc - psi[i + dup];
+          if (dn) Ap += pc - psi[i + ddn];
+          const int64_t sfx = src[i] - mz;
+          const float rf = (float)(sfx - Ap);
+          rr += rf * rf;
+          const float sf = (float)sfx;
+          ss += sf * sf;
+          rv[h] = rf * PSI_INV_SCALE_F;
+        }
+        v[u] = make_float2(rv[0], rv[1]);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = make_float2(0.f, 0.f);
+    }
+    fft_regs<false>(v, t, lgx, line, a.twx, -1.f);
+    // R_2q(k) = (C(k) + conj C(-k)) / 2, R_2q+1(k) = (C(k) - conj C(-k)) / 2i
+#pragma unroll
+    for (int u = 0; u < 8; ++u) line[t + u * Tx] = v[u];
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+      const int k = t + u * Tx;  // k <= H: u < 4, or u == 4 and t == 0
+      if (u < 4 || t == 0) {
+        const float2 c = v[u], cm = line[(nx - k) & (nx - 1)];
+        S[y0 * rs + k] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
+        S[(y0 + 1) * rs + k] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
+      }
+    }
   }
   __syncthreads();
-  fft_rows(rb, lgx, lgr, 1, nx, a.twx, -1.f);
-  for (int idx = threadIdx.x; idx < cnt * nx; idx += blockDim.x) {
-    const int q = idx >> lgx, k = idx & (nx - 1);
-    const int64_t pp = p0 + q;
-    const int z = planes[pp / npairs_row];
-    const int y0 = 2 * (int)(pp % npairs_row), y1 = y0 + 1;
-    const float2 c = rb[q * nx + k], cm = rb[q * nx + ((nx - k) & (nx - 1))];
-    float2* out = spec + ((int64_t)z * a.ny) * nx;
-    out[(int64_t)y0 * nx + k] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
-    if (y1 < a.ny) out[(int64_t)y1 * nx + k] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
+
+  // ---- y: columns kx = 1..H-1, and kx = 0, H packed as one complex column
+  {
+    const int Ty = ny >> 3;
+    const int c = w >> (lgy - 3), t = w & (Ty - 1);
+    const PadLine line{scr + c * padded_len(ny)};
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int y = t + u * Ty;
+      v[u] = c == 0 ? make_float2(S[y * rs].x, S[y * rs + H].x) : S[y * rs + c];
+    }
+    fft_regs<false>(v, t, lgy, line, a.twy, -1.f);
+    // unpack the two real columns: F0 = (Z + conj Z(-k)) / 2, FH = (Z - conj Z(-k)) / 2i
+#pragma unroll
+    for (int u = 0; u < 8; ++u) line[t + u * Ty] = v[u];
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int ky = t + u * Ty;
+      if (c == 0) {
+        const float2 zk = v[u], zm = line[(ny - ky) & (ny - 1)];
+        S[ky * rs] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        S[ky * rs + H] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      } else {
+        S[ky * rs + c] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    float4* dst = reinterpret_cast<float4*>(spec + (int64_t)z * a.mxy);
+    const float4* s4 = reinterpret_cast<const float4*>(S);
+    // mxy is even (ny >= 8) and the plane offset is a multiple of 2 values
+    for (int i = w; i < (a.mxy >> 1); i += tp) dst[i] = s4[i];
+  }
+
+  // norms: warp, then CTA, one atomic pair per CTA
+  for (int off = 16; off > 0; off >>= 1) {
+    rr += __shfl_down_sync(0xffffffffu, rr, off);
+    ss += __shfl_down_sync(0xffffffffu, ss, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_r[threadIdx.x >> 5] = rr;
+    red_s[threadIdx.x >> 5] = ss;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0, ts = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      tr += (double)red_r[i];
+      ts += (double)red_s[i];
+    }
+    atomicAdd(norms, tr);
+    atomicAdd(norms + 1, ts);
   }
 }
 
-// y pass (in place): one CTA takes CYC consecutive kx columns of one plane,
-// staged in shared memory as [y][column] (coalesced), FFT along y.
-__global__ void __launch_bounds__(256) k_fft_y(float2* __restrict__ spec,
-                                               const int* __restrict__ planes, int cols_per_plane,
-                                               SpecArgs a, float sign, int lgc) {
-  extern __shared__ float2 cb[];
-  const int ny = a.ny, lgy = a.lgy, nx = a.nx;
-  const int CYC = 1 << lgc;  // columns per CTA
-  const int z = planes[blockIdx.x / cols_per_plane];
-  const int k0 = (blockIdx.x % cols_per_plane) * CYC;
-  const int w = min(CYC, nx - k0);
-  float2* base = spec + (int64_t)z * ny * nx + k0;
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < ny * CYC; idx += blockDim.x) {
-    const int y = idx >> lgc, j = idx & (CYC - 1);
-    if (j < w) cb[(lgy ? (int)brev(y, lgy) : 0) * CYC + j] = base[(int64_t)y * nx + j];
+// Inverse plane kernel: y inverse (column 0 carries kx = 0 and H packed as
+// F0 + i FH, whose inverse is f0 + i fH with both real), then rows 2q, 2q+1
+// as C(k) = E_2q(k) + i E_2q+1(k) over the full k range (E(k) = conj E(nx-k)
+// above H), inverse along x, psi += round(e / (nx ny)) in fixed point.
+__global__ void __launch_bounds__(1024, 1) k_plane_inv(const float2* __restrict__ spec,
+                                                      const int* __restrict__ planes,
+                                                      int nplanes, int64_t* __restrict__ psi,
+                                                      SpecArgs a) {
+  extern __shared__ __align__(16) float2 sm[];
+  const int nx = a.nx, ny = a.ny, H = a.H, lgx = a.lgx, lgy = a.lgy;
+  const int tp = 1 << a.lgtp;
+  const int slot = threadIdx.x >> a.lgtp, w = threadIdx.x & (tp - 1);
+  const int pi = blockIdx.x * (blockDim.x >> a.lgtp) + slot;
+  const bool valid = pi < nplanes;
+  const int z = valid ? planes[pi] : 0;
+  float2* S = sm + (size_t)slot * plane_smem_words(nx, ny);
+  float2* scr = S + a.mxy;
+  const int rs = H + 1;
+  float2 v[8];
+  {
+    float4* s4 = reinterpret_cast<float4*>(S);
+    const float4* src4 = reinterpret_cast<const float4*>(spec + (int64_t)z * a.mxy);
+    for (int i = w; i < (a.mxy >> 1); i += tp) s4[i] = valid ? src4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
-  fft_rows(cb, lgy, lgc, CYC, 1, a.twy, sign);
-  for (int idx = threadIdx.x; idx < ny * CYC; idx += blockDim.x) {
-    const int y = idx >> lgc, j = idx & (CYC - 1);
-    if (j < w) base[(int64_t)y * nx + j] = cb[y * CYC + j];
+  {
+    const int Ty = ny >> 3;
+    const int c = w >> (lgy - 3), t = w & (Ty - 1);
+    const PadLine line{scr + c * padded_len(ny)};
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int y = t + u * Ty;
+      if (c == 0) {
+        const float2 f0 = S[y * rs], fh = S[y * rs + H];
+        v[u] = make_float2(f0.x - fh.y, f0.y + fh.x);
+      } else {
+        v[u] = S[y * rs + c];
+      }
+    }
+    fft_regs<false>(v, t, lgy, line, a.twy, 1.f);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int y = t + u * Ty;
+      if (c == 0) {
+        S[y * rs] = make_float2(v[u].x, 0.f);
+        S[y * rs + H] = make_float2(v[u].y, 0.f);
+      } else {
+        S[y * rs + c] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  {
+    const int Tx = nx >> 3;
+    const int q = w >> (lgx - 3), t = w & (Tx - 1);
+    const PadLine line{scr + q * padded_len(nx)};
+    const int y0 = 2 * q;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int k = t + u * Tx;
+      float2 e0, e1;
+      if (k <= H) {
+        e0 = S[y0 * rs + k];
+        e1 = S[(y0 + 1) * rs + k];
+      } else {
+        e0 = S[y0 * rs + nx - k];
+        e1 = S[(y0 + 1) * rs + nx - k];
+        e0.y = -e0.y;
+        e1.y = -e1.y;
+      }
+      v[u] = make_float2(e0.x - e1.y, e0.y + e1.x);
+    }
+    fft_regs<false>(v, t, lgx, line, a.twx, 1.f);
+    if (valid) {
+      const float scale = PSI_SCALE_F / (float)(nx * ny);
+      int64_t* row0 = psi + ((int64_t)z * ny + y0) * nx;
+      int64_t* row1 = row0 + nx;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int x = t + u * Tx;
+        row0[x] += llrintf(v[u].x * scale);
+        row1[x] += llrintf(v[u].y * scale);
+      }
+    }
   }
 }
 
-// Inverse x pass fused with the update: rows y0, y1 of the corrections
-// (Hermitian spectra) form C = E_y0 + i E_y1; the inverse FFT gives e_y0 in
-// the real and e_y1 in the imaginary part; psi += round(e / (nx ny)).
-__global__ void __launch_bounds__(256) k_fft_x_inv_apply(const float2* __restrict__ spec,
-                                                         const int* __restrict__ planes,
-                                                         int npairs_row, int64_t total_pairs,
-                                                         SpecArgs a, int64_t* psi, int lgr) {
-  extern __shared__ float2 rb[];
-  const int nx = a.nx, lgx = a.lgx;
-  const int rxp = 1 << lgr;
-  const int64_t p0 = (int64_t)blockIdx.x * rxp;
-  const int cnt = (int)min((int64_t)rxp, total_pairs - p0);
-  for (int idx = threadIdx.x; idx < cnt * nx; idx += blockDim.x) {
-    const int q = idx >> lgx, k = idx & (nx - 1);
-    const int64_t pp = p0 + q;
-    const int z = planes[pp / npairs_row];
-    const int y0 = 2 * (int)(pp % npairs_row), y1 = y0 + 1;
-    const float2* row = spec + ((int64_t)z * a.ny) * nx;
-    const float2 e0 = row[(int64_t)y0 * nx + k];
-    const float2 e1 = (y1 < a.ny) ? row[(int64_t)y1 * nx + k] : make_float2(0.f, 0.f);
-    rb[q * nx + (lgx ? (int)brev(k, lgx) : 0)] = make_float2(e0.x - e1.y, e0.y + e1.x);
+// Periodic z axis of power-of-two length (8..256): the z operator is
+// circulant, so an FFT along z diagonalises it too (eigenvalue
+// 2 - 2 cos(2 pi kz / nz)).  One CTA: 32 consecutive modes, thread
+// (t, p) = threadIdx.x = 32 t + p, so every warp reads 32 consecutive modes
+// of one plane; the pencil of mode p exchanges through column p of a
+// [z][33] shared array.  Forward FFT, division by lambda (the free mean,
+// mode (0,0,0), set to 0), inverse FFT, all in registers between exchanges.
+__global__ void __launch_bounds__(1024, 1) k_zfft(float2* __restrict__ spec, SpecArgs a) {
+  extern __shared__ __align__(16) float2 zb[];
+  const int lgz = a.lgz, T = 1 << (lgz - 3);
+  const int p = threadIdx.x & 31, t = threadIdx.x >> 5;
+  const int m = blockIdx.x * 32 + p;
+  const bool ok = m < a.mxy;
+  const int64_t mxy = a.mxy;
+  float2 v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    v[u] = ok ? spec[(int64_t)(t + u * T) * mxy + m] : make_float2(0.f, 0.f);
+  const StrideLine line{zb + p, 33};
+  fft_regs<true>(v, t, lgz, line, a.twz, -1.f);
+  const int ky = ok ? m / (a.H + 1) : 0, kx = ok ? m - ky * (a.H + 1) : 0;
+  const float lxy = a.lamx[kx] + a.lamy[ky];
+  const float invL = 1.0f / (float)(1 << lgz);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int kz = t + u * T;
+    const float sc = (m == 0 && kz == 0) ? 0.f : invL / (lxy + a.lamz[kz]);
+    v[u] = make_float2(v[u].x * sc, v[u].y * sc);
   }
-  __syncthreads();
-  fft_rows(rb, lgx, lgr, 1, nx, a.twx, 1.f);
-  const float scale = PSI_SCALE_F / (float)(nx * a.ny);
-  for (int idx = threadIdx.x; idx < cnt * nx; idx += blockDim.x) {
-    const int q = idx >> lgx, x = idx & (nx - 1);
-    const int64_t pp = p0 + q;
-    const int z = planes[pp / npairs_row];
-    const int y0 = 2 * (int)(pp % npairs_row), y1 = y0 + 1;
-    const float2 c = rb[q * nx + x];
-    int64_t* row = psi + ((int64_t)z * a.ny) * nx;
-    row[(int64_t)y0 * nx + x] += llrintf(c.x * scale);
-    if (y1 < a.ny) row[(int64_t)y1 * nx + x] += llrintf(c.y * scale);
+  fft_regs<true>(v, t, lgz, line, a.twz, 1.f);
+  if (ok) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) spec[(int64_t)(t + u * T) * mxy + m] = v[u];
   }
 }
 
@@ -290,7 +569,7 @@ __global__ void __launch_bounds__(128) k_zsolve(float2* __restrict__ x,
   extern __shared__ float zsm[];
   const Run R = runs[blockIdx.y];
   const int L = R.len;
-  const int nxy = a.nx * a.ny;
+  const int nxy = a.mxy;  // modes per plane of the half spectrum
   const int m0 = blockIdx.x * ZP;
   float2* X = reinterpret_cast<float2*>(zsm);
   float* C = zsm + 2 * ZP * L;
@@ -305,7 +584,8 @@ __global__ void __launch_bounds__(128) k_zsolve(float2* __restrict__ x,
   const int j = threadIdx.x;
   if (j < ZP && m0 + j < nxy) {
     const int m = m0 + j;
-    solve_pencil(X + j, C + j, Qv + j, ZP, L, a.lam_xy[m], m == 0, R.cyclic != 0);
+    const int ky = m / (a.H + 1), kx = m - ky * (a.H + 1);
+    solve_pencil(X + j, C + j, Qv + j, ZP, L, a.lamx[kx] + a.lamy[ky], m == 0, R.cyclic != 0);
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < ZP * L; idx += blockDim.x) {
@@ -313,61 +593,6 @@ __global__ void __launch_bounds__(128) k_zsolve(float2* __restrict__ x,
     int z = R.z0 + k;
     if (z >= a.nz) z -= a.nz;
     if (m0 + jj < nxy) x[(int64_t)z * nxy + m0 + jj] = X[idx];
-  }
-}
-
-// Periodic z axis of power-of-two length: the z operator is circulant, so an
-// FFT along z diagonalises it too (eigenvalue 2 - 2 cos(2 pi kz / nz)).
-// One CTA: ZP consecutive modes; forward FFT of each pencil in shared
-// memory, division by lambda_xy + lambda_z (the (0,0,0) mode, the free mean,
-// set to 0), inverse FFT, store.
-__global__ void __launch_bounds__(256) k_zfft(float2* __restrict__ x, const float2* __restrict__ twz,
-                                              int lgz, SpecArgs a) {
-  extern __shared__ float2 zb[];
-  const int L = 1 << lgz;
-  const int nxy = a.nx * a.ny;
-  const int m0 = blockIdx.x * ZP;
-  const int lgp = 5;  // log2(ZP)
-  // stage: plane k of pencil j at zb[brev(k) * ZP + j] (coalesced loads)
-#pragma unroll 8
-  for (int idx = threadIdx.x; idx < ZP * L; idx += 256) {
-    const int k = idx >> lgp, j = idx & (ZP - 1);
-    zb[(int)brev(k, lgz) * ZP + j] =
-        (m0 + j < nxy) ? x[(int64_t)k * nxy + m0 + j] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  fft_rows(zb, lgz, lgp, ZP, 1, twz, -1.f);
-  // divide by the eigenvalue and put the spectrum back in bit-reversed
-  // order for the inverse transform (through registers, one buffer)
-  const float invL = 1.0f / (float)L;
-  constexpr int PER = 32;  // elements per thread for L <= 256 (ZP * L / 256)
-  float2 v[PER];
-  int dst[PER];
-  int cnt = 0;
-#pragma unroll
-  for (int t = 0; t < PER; ++t) {
-    const int idx = threadIdx.x + t * 256;
-    if (idx < ZP * L) {
-      const int kz = idx >> lgp, j = idx & (ZP - 1);
-      const int m = m0 + j;
-      const float lam = (m < nxy ? a.lam_xy[m] : 1.f) + a.lam_z[kz];
-      const float sc = (m == 0 && kz == 0) ? 0.f : invL / lam;
-      const float2 c = zb[idx];
-      v[t] = make_float2(c.x * sc, c.y * sc);
-      dst[t] = (int)brev(kz, lgz) * ZP + j;
-      cnt = t + 1;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int t = 0; t < PER; ++t)
-    if (t < cnt) zb[dst[t]] = v[t];
-  __syncthreads();
-  fft_rows(zb, lgz, lgp, ZP, 1, twz, 1.f);
-#pragma unroll 8
-  for (int idx = threadIdx.x; idx < ZP * L; idx += 256) {
-    const int k = idx >> lgp, j = idx & (ZP - 1);
-    if (m0 + j < nxy) x[(int64_t)k * nxy + m0 + j] = zb[idx];
   }
 }
 
@@ -412,7 +637,8 @@ __global__ void k_run_means(const long long* __restrict__ psum, const Run* __res
 }
 
 // Residual with per-plane means: r = s - mean_z - A psi (exact), norms into
-// dsum[1], dsum[2].  Wall planes contribute nothing.
+// dsum[1], dsum[2]; r (scaled to real units) is stored only when r != NULL.
+// Wall planes contribute nothing.
 __global__ void __launch_bounds__(256) k_res_planes(
     const int64_t* __restrict__ psi, const int64_t* __restrict__ src,
     const long long* __restrict__ mean_z, const unsigned char* __restrict__ plane_fluid,
@@ -427,7 +653,7 @@ __global__ void __launch_bounds__(256) k_res_planes(
     const int z = (int)(i >> lgxy);
     const int k = (int)(i & (nxy - 1));
     if (!plane_fluid[z]) {
-      r[i] = 0.f;
+      if (r) r[i] = 0.f;
       continue;
     }
     const int y = k >> lgx, x = k & (nx - 1);
@@ -448,7 +674,7 @@ __global__ void __launch_bounds__(256) k_res_planes(
     }
     const int64_t sfx = src[i] - mean_z[z];
     const float rf = (float)(sfx - Ap);
-    r[i] = rf * PSI_INV_SCALE_F;
+    if (r) r[i] = rf * PSI_INV_SCALE_F;
     rr += rf * rf;
     const float sf = (float)sfx;
     ss += sf * sf;
@@ -487,20 +713,20 @@ struct SpectralPlan {
   int* planes = nullptr;           // indices of fluid planes
   Run* runs = nullptr;
   unsigned char* plane_fluid = nullptr;
-  float2* twx = nullptr;
-  float2* twy = nullptr;
-  float2* spec = nullptr;          // N complex
+  float2* tw = nullptr;            // twiddles: nx, then ny, then nz values
+  float* lam = nullptr;            // eigenvalues: H + 1, then ny, then nz values
+  float2* spec = nullptr;          // half spectrum, nz * mxy values
+  int mxy = 0;
+  int lgtp = 0;                    // log2 of the threads per plane
+  int ppc = 1;                     // planes per CTA of the plane kernels
+  size_t plane_smem = 0;           // shared memory of a plane-kernel CTA
   size_t zsmem = 0;                // shared memory of the z solve
   int lgz = -1;                    // log2(nz) when the z axis is one periodic run
-  float2* twz = nullptr;           // z twiddles (periodic power-of-two z)
-  float* lam_xy = nullptr;         // x-y Laplacian eigenvalues per mode
-  float* lam_z = nullptr;          // z Laplacian eigenvalues (periodic power-of-two z)
   int last_iters = 2;              // applications of the previous solve
   bool runs_fit = true;            // z solve fits in shared memory
-  float* r = nullptr;              // N
+  float* r = nullptr;              // N (residual for the learned guess)
   long long* psum = nullptr;       // nz
   long long* mean_z = nullptr;     // nz
-  size_t smem = 0;
 };
 
 void spectral_free(lbm_t* h) {
@@ -509,11 +735,8 @@ void spectral_free(lbm_t* h) {
   cudaFree(s->planes);
   cudaFree(s->runs);
   cudaFree(s->plane_fluid);
-  cudaFree(s->twx);
-  cudaFree(s->twy);
-  cudaFree(s->twz);
-  cudaFree(s->lam_xy);
-  cudaFree(s->lam_z);
+  cudaFree(s->tw);
+  cudaFree(s->lam);
   cudaFree(s->spec);
   cudaFree(s->r);
   cudaFree(s->psum);
@@ -526,8 +749,8 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   spectral_free(h);
   const int nx = h->cfg.nx, ny = h->cfg.ny, nz = h->cfg.nz;
   const int lgx = ilog2(nx), lgy = ilog2(ny);
-  if (lgx < 0 || lgy < 0) {
-    h->err = "spectral Poisson solver needs power-of-two nx, ny";
+  if (lgx < 3 || lgy < 3 || lgx > 8 || lgy > 8 || nx * ny > 16384) {
+    h->err = "spectral Poisson solver needs power-of-two nx, ny in [8, 256] with nx*ny <= 16384";
     return LBM_EINVAL;
   }
   const int64_t nxy = (int64_t)nx * ny;
@@ -584,6 +807,9 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   s->lgy = lgy;
   s->nplanes = (int)planes.size();
   s->nruns = (int)runs.size();
+  s->mxy = (nx / 2 + 1) * ny;
+  s->lgtp = lgx + lgy - 4;
+  s->ppc = std::max(1, 256 >> s->lgtp);
   const int64_t N = h->N;
   auto al = [&](void** p, size_t bytes) {
     if (cudaMalloc(p, bytes) != cudaSuccess) {
@@ -592,11 +818,11 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
     }
     return true;
   };
+  const size_t ntw = (size_t)nx + ny + nz, nlam = (size_t)nx / 2 + 1 + ny + nz;
   bool ok = al((void**)&s->planes, planes.size() * sizeof(int)) &&
-            al((void**)&s->runs, runs.size() * sizeof(Run)) &&
-            al((void**)&s->plane_fluid, nz) && al((void**)&s->twx, std::max(1, nx / 2) * sizeof(float2)) &&
-            al((void**)&s->twy, std::max(1, ny / 2) * sizeof(float2)) &&
-            al((void**)&s->spec, N * sizeof(float2)) &&
+            al((void**)&s->runs, runs.size() * sizeof(Run)) && al((void**)&s->plane_fluid, nz) &&
+            al((void**)&s->tw, ntw * sizeof(float2)) && al((void**)&s->lam, nlam * sizeof(float)) &&
+            al((void**)&s->spec, (size_t)nz * s->mxy * sizeof(float2)) &&
             al((void**)&s->r, N * sizeof(float)) && al((void**)&s->psum, nz * sizeof(long long)) &&
             al((void**)&s->mean_z, nz * sizeof(long long));
   if (!ok) {
@@ -604,53 +830,33 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
     h->err = "spectral Poisson allocation failed";
     return LBM_ENOMEM;
   }
-  auto twiddles = [](int n) {
-    std::vector<float2> t(std::max(1, n / 2));
-    for (int k = 0; k < n / 2; ++k) {
-      const double ang = -2.0 * 3.14159265358979323846 * k / n;
-      t[k] = make_float2((float)cos(ang), (float)sin(ang));
-    }
-    return t;
+  // twiddles exp(-2 pi i m / n), m < n, and eigenvalues 2 - 2 cos(2 pi k / n)
+  // of the periodic second difference, in double precision, rounded once;
+  // the eigenvalue of k and n - k is the same number
+  const double twopi = 2.0 * 3.14159265358979323846;
+  std::vector<float2> tw;
+  std::vector<float> lam;
+  for (int n : {nx, ny, nz})
+    for (int m = 0; m < n; ++m)
+      tw.push_back(make_float2((float)cos(-twopi * m / n), (float)sin(-twopi * m / n)));
+  auto eig = [&](int k, int n) {
+    const int kk = std::min(k, n - k);
+    return (float)(2.0 - 2.0 * cos(twopi * kk / n));
   };
-  auto tx = twiddles(nx), ty = twiddles(ny);
+  for (int k = 0; k <= nx / 2; ++k) lam.push_back(eig(k, nx));
+  for (int k = 0; k < ny; ++k) lam.push_back(eig(k, ny));
+  for (int k = 0; k < nz; ++k) lam.push_back(eig(k, nz));
   LBM_CUDA_TRY(h, cudaMemcpy(s->planes, planes.data(), planes.size() * sizeof(int), cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->runs, runs.data(), runs.size() * sizeof(Run), cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->plane_fluid, pf.data(), nz, cudaMemcpyHostToDevice));
-  LBM_CUDA_TRY(h, cudaMemcpy(s->twx, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice));
-  LBM_CUDA_TRY(h, cudaMemcpy(s->twy, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice));
-  {
-    // eigenvalues of the periodic x-y Laplacian, 2 - 2 cos(2 pi k / n) per
-    // axis, computed once in double precision
-    std::vector<float> lxy(nxy);
-    for (int ky = 0; ky < ny; ++ky)
-      for (int kx = 0; kx < nx; ++kx)
-        lxy[(int64_t)ky * nx + kx] =
-            (float)((2.0 - 2.0 * cos(2.0 * 3.14159265358979323846 * kx / nx)) +
-                    (2.0 - 2.0 * cos(2.0 * 3.14159265358979323846 * ky / ny)));
-    std::vector<float> lz(nz);
-    for (int kz = 0; kz < nz; ++kz)
-      lz[kz] = (float)(2.0 - 2.0 * cos(2.0 * 3.14159265358979323846 * kz / nz));
-    if (!al((void**)&s->lam_xy, nxy * sizeof(float)) || !al((void**)&s->lam_z, nz * sizeof(float))) {
-      spectral_free(h);
-      h->err = "spectral Poisson allocation failed";
-      return LBM_ENOMEM;
-    }
-    LBM_CUDA_TRY(h, cudaMemcpy(s->lam_xy, lxy.data(), nxy * sizeof(float), cudaMemcpyHostToDevice));
-    LBM_CUDA_TRY(h, cudaMemcpy(s->lam_z, lz.data(), nz * sizeof(float), cudaMemcpyHostToDevice));
-  }
+  LBM_CUDA_TRY(h, cudaMemcpy(s->tw, tw.data(), ntw * sizeof(float2), cudaMemcpyHostToDevice));
+  LBM_CUDA_TRY(h, cudaMemcpy(s->lam, lam.data(), nlam * sizeof(float), cudaMemcpyHostToDevice));
   int optin = 0;
   LBM_CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
-  if (runs.size() == 1 && runs[0].cyclic && ilog2(nz) > 0 && nz >= 4 && nz <= 256 &&
-      (size_t)ZP * nz * sizeof(float2) <= (size_t)optin) {
-    s->lgz = ilog2(nz);
-    auto tz = twiddles(nz);
-    if (!al((void**)&s->twz, tz.size() * sizeof(float2))) {
-      spectral_free(h);
-      h->err = "spectral Poisson allocation failed";
-      return LBM_ENOMEM;
-    }
-    LBM_CUDA_TRY(h, cudaMemcpy(s->twz, tz.data(), tz.size() * sizeof(float2), cudaMemcpyHostToDevice));
-    const size_t zf = (size_t)ZP * nz * sizeof(float2);
+  const int lgz = ilog2(nz);
+  if (runs.size() == 1 && runs[0].cyclic && lgz >= 3 && lgz <= 8) {
+    s->lgz = lgz;
+    const size_t zf = (size_t)nz * 33 * sizeof(float2);
     if (zf > 48 * 1024)
       LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_zfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zf));
   }
@@ -663,22 +869,16 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
     return LBM_EINVAL;
   }
   // (without walls yet the plan is provisional: set_walls rebuilds it)
-  if (s->runs_fit && s->zsmem > 48 * 1024)
+  if (s->runs_fit && s->lgz < 0 && s->zsmem > 48 * 1024)
     LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->zsmem));
-  s->smem = (size_t)nxy * sizeof(float2);
-  {
-    const int lgr = std::max(0, 10 - lgx), lgc = std::max(0, 10 - lgy);
-    const int xs = (int)(((size_t)nx << lgr) * sizeof(float2)), ys = (int)(((size_t)ny << lgc) * sizeof(float2));
-    if (xs > optin || ys > optin) {
-      h->err = "spectral Poisson solver: lattice rows too long for shared memory";
-      return LBM_EINVAL;
-    }
-    if (xs > 48 * 1024) {
-      LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_x_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, xs));
-      LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_x_inv_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, xs));
-    }
-    if (ys > 48 * 1024)
-      LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_y, cudaFuncAttributeMaxDynamicSharedMemorySize, ys));
+  s->plane_smem = (size_t)s->ppc * plane_smem_words(nx, ny) * sizeof(float2);
+  if ((int)s->plane_smem > optin - 256) {
+    h->err = "spectral Poisson solver: x-y plane too large for shared memory";
+    return LBM_EINVAL;
+  }
+  if (s->plane_smem > 48 * 1024) {
+    LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_plane_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->plane_smem));
+    LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_plane_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->plane_smem));
   }
   return LBM_OK;
 }
@@ -692,28 +892,37 @@ SpecArgs args_of(const SpectralPlan* s) {
   a.nz = s->nz;
   a.lgx = s->lgx;
   a.lgy = s->lgy;
-  a.twx = s->twx;
-  a.twy = s->twy;
-  a.lam_xy = s->lam_xy;
-  a.lam_z = s->lam_z;
+  a.lgz = s->lgz;
+  a.H = s->nx / 2;
+  a.mxy = s->mxy;
+  a.lgtp = s->lgtp;
+  a.twx = s->tw;
+  a.twy = s->tw + s->nx;
+  a.twz = s->tw + s->nx + s->ny;
+  a.lamx = s->lam;
+  a.lamy = s->lam + s->nx / 2 + 1;
+  a.lamz = a.lamy + s->ny;
   return a;
 }
 
-// Residual of the current potential; its norms go to dsum[1 + 2 slot] and
-// dsum[2 + 2 slot] (slot 0 is the one the host reads by default).
-cudaError_t spec_residual(lbm_t* h, bool to_host = true, int slot = 0) {
+// Norm slot i: dsum[1 + 2 i] (residual^2), dsum[2 + 2 i] (source^2), in
+// fixed-point units squared.
+double* norm_slot(lbm_t* h, int slot) { return h->ps.dsum + 1 + 2 * slot; }
+
+// Residual of the current potential (exact, k_res_planes) with its norms in
+// the slot; stores r (for the learned guess) when with_r.
+cudaError_t spec_residual(lbm_t* h, int slot, bool with_r) {
   SpectralPlan* s = h->spec;
   Poisson& P = h->ps;
-  double* out = P.dsum + 2 * slot;
-  cudaError_t e = cudaMemsetAsync(out + 1, 0, 2 * sizeof(double), h->st);
+  double* out = norm_slot(h, slot);
+  cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), h->st);
   if (e != cudaSuccess) return e;
   const unsigned nb = (unsigned)std::min<int64_t>(nblk(h->N, 256), h->grid_cap);
-  k_res_planes<<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, s->mean_z, s->plane_fluid, s->r,
-                                      out, s->nx, s->ny, s->nz, s->lgx, s->lgx + s->lgy);
+  k_res_planes<<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, s->mean_z, s->plane_fluid,
+                                      with_r ? s->r : nullptr, out - 1, s->nx, s->ny, s->nz,
+                                      s->lgx, s->lgx + s->lgy);
   ++h->launches;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (!to_host) return cudaSuccess;
-  return cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+  return cudaGetLastError();
 }
 
 cudaError_t spec_means(lbm_t* h) {
@@ -732,32 +941,44 @@ cudaError_t spec_means(lbm_t* h) {
   return cudaGetLastError();
 }
 
-cudaError_t spec_apply(lbm_t* h) {
+// First kernel of an application: the residual of the current potential
+// (norms into the slot) and its 2-D half spectrum.
+cudaError_t spec_fwd(lbm_t* h, int slot) {
   SpectralPlan* s = h->spec;
   Poisson& P = h->ps;
   const SpecArgs a = args_of(s);
-  const int npairs_row = (s->ny + 1) / 2;
-  const int64_t total_pairs = (int64_t)s->nplanes * npairs_row;
-  // about 1024 complex values per CTA in each pass
-  const int lgr = std::max(0, 10 - s->lgx), lgc = std::max(0, 10 - s->lgy);
-  const unsigned gx = (unsigned)((total_pairs + (1 << lgr) - 1) >> lgr);
-  const size_t xs = ((size_t)s->nx << lgr) * sizeof(float2);
-  const int cols = (s->nx + (1 << lgc) - 1) >> lgc;
-  const size_t ys = ((size_t)s->ny << lgc) * sizeof(float2);
-  k_fft_x_fwd<<<gx, 256, xs, h->st>>>(s->r, s->spec, s->planes, npairs_row, total_pairs, a, lgr);
-  k_fft_y<<<s->nplanes * cols, 256, ys, h->st>>>(s->spec, s->planes, cols, a, -1.f, lgc);
+  double* out = norm_slot(h, slot);
+  cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), h->st);
+  if (e != cudaSuccess) return e;
+  const unsigned gp = (unsigned)((s->nplanes + s->ppc - 1) / s->ppc);
+  k_plane_fwd<<<gp, s->ppc << s->lgtp, s->plane_smem, h->st>>>(
+      P.psi[P.cur], P.src, s->mean_z, s->plane_fluid, s->planes, s->nplanes, s->spec, out, a);
+  ++h->launches;
+  return cudaGetLastError();
+}
+
+// Rest of an application: the z solve and the inverse transform with the
+// update of psi.
+cudaError_t spec_zinv(lbm_t* h) {
+  SpectralPlan* s = h->spec;
+  Poisson& P = h->ps;
+  const SpecArgs a = args_of(s);
   if (s->lgz > 0) {
-    k_zfft<<<nblk((int64_t)s->nx * s->ny, ZP), 256, (size_t)ZP * s->nz * sizeof(float2), h->st>>>(
-        s->spec, s->twz, s->lgz, a);
+    k_zfft<<<nblk(s->mxy, 32), 4 * s->nz, (size_t)s->nz * 33 * sizeof(float2), h->st>>>(s->spec, a);
   } else {
-    dim3 g(nblk((int64_t)s->nx * s->ny, ZP), s->nruns);
+    dim3 g(nblk(s->mxy, ZP), s->nruns);
     k_zsolve<<<g, 128, s->zsmem, h->st>>>(s->spec, s->runs, a);
   }
-  k_fft_y<<<s->nplanes * cols, 256, ys, h->st>>>(s->spec, s->planes, cols, a, 1.f, lgc);
-  k_fft_x_inv_apply<<<gx, 256, xs, h->st>>>(s->spec, s->planes, npairs_row, total_pairs, a,
-                                             P.psi[P.cur], lgr);
-  h->launches += 5;
+  const unsigned gp = (unsigned)((s->nplanes + s->ppc - 1) / s->ppc);
+  k_plane_inv<<<gp, s->ppc << s->lgtp, s->plane_smem, h->st>>>(s->spec, s->planes, s->nplanes,
+                                                                P.psi[P.cur], a);
+  h->launches += 2;
   return cudaGetLastError();
+}
+
+cudaError_t spec_apply(lbm_t* h, int slot) {
+  cudaError_t e = spec_fwd(h, slot);
+  return e == cudaSuccess ? spec_zinv(h) : e;
 }
 
 }  // namespace
@@ -769,65 +990,81 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
     h->err = "spectral Poisson solver: fluid run along z too long for shared memory";
     return LBM_EINVAL;
   }
+  const double floor = 2.0 * sqrt((double)h->nfluid);
+  auto conv_of = [&](double rn, double sn) { return rn <= tol * sn || rn <= floor; };
   LBM_CUDA_TRY(h, spec_means(h));
-  LBM_CUDA_TRY(h, spec_residual(h));
-  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
-  double rn = sqrt(P.hsum[1]), sn = sqrt(P.hsum[2]);
-  auto conv = [&]() { return rn <= tol * sn || rn <= 2.0 * sqrt((double)h->nfluid); };
-  if (!conv() && nn_active(h)) {
-    bool applied = false;
-    float* dpsi = nullptr;
-    lbm_status st = nn_before_solve(h, s->r, 0, s->nz, rn * PSI_INV_SCALE / sqrt((double)h->nfluid),
-                                    &applied, &dpsi);
-    if (st != LBM_OK) return st;
-    if (applied) {
-      const double rn_old = rn;
-      LBM_CUDA_TRY(h, spec_residual(h));
-      LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
-      rn = sqrt(P.hsum[1]);
-      if (rn < rn_old) {
-        nn_record(h, rn / rn_old);
-      } else {
-        st = nn_revert(h, dpsi);
-        if (st != LBM_OK) return st;
-        LBM_CUDA_TRY(h, spec_residual(h));
+  double rn = 0.0, sn = 0.0;
+  int it = 0;
+  bool known = false;  // rn, sn hold the norms of the current potential
+  if (nn_active(h)) {
+    LBM_CUDA_TRY(h, spec_residual(h, 0, true));
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    rn = sqrt(P.hsum[1]);
+    sn = sqrt(P.hsum[2]);
+    known = true;
+    if (!conv_of(rn, sn)) {
+      bool applied = false;
+      float* dpsi = nullptr;
+      lbm_status st = nn_before_solve(h, s->r, 0, s->nz, rn * PSI_INV_SCALE / sqrt((double)h->nfluid),
+                                      &applied, &dpsi);
+      if (st != LBM_OK) return st;
+      if (applied) {
+        const double rn_old = rn;
+        LBM_CUDA_TRY(h, spec_residual(h, 0, false));
+        LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
         LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
         rn = sqrt(P.hsum[1]);
+        if (rn < rn_old) {
+          nn_record(h, rn / rn_old);
+        } else {
+          st = nn_revert(h, dpsi);
+          if (st != LBM_OK) return st;
+          LBM_CUDA_TRY(h, spec_residual(h, 0, false));
+          LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+          LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+          rn = sqrt(P.hsum[1]);
+        }
       }
     }
-  }
-  int it = 0;
-  if (!nn_active(h) && !conv()) {
-    // Queue the number of applications the previous solve needed, each
-    // followed by its residual in its own slot, and read all norms with one
-    // host synchronisation.
+  } else if (maxit > 0) {
+    // Queue the number of applications the previous solve needed without
+    // looking at the first residual (each application computes the norms
+    // of the residual it transforms), the final residual's norms, and read
+    // all norms with one host synchronisation.  An application beyond the
+    // one that reached the tolerance only refines psi further.
     const int k = std::max(1, std::min(std::min(s->last_iters, maxit), Poisson::NSLOT - 1));
-    for (int i = 1; i <= k; ++i) {
-      LBM_CUDA_TRY(h, spec_apply(h));
-      LBM_CUDA_TRY(h, spec_residual(h, false, i));
-    }
+    for (int i = 0; i < k; ++i) LBM_CUDA_TRY(h, spec_apply(h, i));
+    LBM_CUDA_TRY(h, spec_residual(h, k, false));
     LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, (3 + 2 * k) * sizeof(double),
                                     cudaMemcpyDeviceToHost, h->st));
     LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
     int need = k;
-    for (int i = 1; i <= k; ++i) {
-      const double ri = sqrt(P.hsum[1 + 2 * i]), si = sqrt(P.hsum[2 + 2 * i]);
-      if (ri <= tol * si || ri <= 2.0 * sqrt((double)h->nfluid)) {
+    for (int i = 0; i <= k; ++i)
+      if (conv_of(sqrt(P.hsum[1 + 2 * i]), sqrt(P.hsum[2 + 2 * i]))) {
         need = i;
         break;
       }
-    }
     rn = sqrt(P.hsum[1 + 2 * k]);
     sn = sqrt(P.hsum[2 + 2 * k]);
+    known = true;
     it = k;
-    s->last_iters = need;
+    s->last_iters = std::max(1, need);
   }
-  while (!conv() && it < maxit) {
-    LBM_CUDA_TRY(h, spec_apply(h));
-    LBM_CUDA_TRY(h, spec_residual(h));
+  if (!known) {
+    LBM_CUDA_TRY(h, spec_residual(h, 0, false));
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
     rn = sqrt(P.hsum[1]);
     sn = sqrt(P.hsum[2]);
+  }
+  while (!conv_of(rn, sn) && it < maxit) {
+    LBM_CUDA_TRY(h, spec_apply(h, 0));
+    LBM_CUDA_TRY(h, spec_residual(h, 1, false));
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    rn = sqrt(P.hsum[3]);
+    sn = sqrt(P.hsum[4]);
     if (!isfinite(rn) || !isfinite(sn)) {
       h->err = "Poisson residual is not finite";
       return LBM_EUNSTABLE;
@@ -835,9 +1072,13 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
     ++it;
     s->last_iters = it;
   }
+  if (!isfinite(rn) || !isfinite(sn)) {
+    h->err = "Poisson residual is not finite";
+    return LBM_EUNSTABLE;
+  }
   if (iters) *iters = it;
   if (rel_res) *rel_res = sn > 0.0 ? rn / sn : 0.0;
-  if (!conv()) {
+  if (!conv_of(rn, sn)) {
     h->err = "Poisson solve did not reach the tolerance within the iteration cap";
     return LBM_ENOCONV;
   }
@@ -847,10 +1088,12 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
 
 // ---------------------------------------------------------------------------
 // Whole-step CUDA graphs.  One graph per population parity holds a full time
-// step: charge density, run means, residual, a device-side while loop
-// (conditional graph node) of spectral applications + residual + test, and
-// the fused stream/collide.  Steps are replayed back to back with no host
-// round trip; the test kernel keeps the per-step status on the device.
+// step: charge density, run means, the forward kernel of the first
+// application (first residual) and its test, a device-side while loop
+// (conditional graph node) of [z solve, inverse + update, next forward
+// kernel (residual of the update), test], and the fused stream/collide.
+// Steps are replayed back to back with no host round trip; the test kernel
+// keeps the per-step status on the device.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -916,7 +1159,8 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
   cudaError_t e = cudaMemsetAsync(P.dsum, 0, 3 * sizeof(double), h->st);
   if (e == cudaSuccess) e = launch_charge(h);
   if (e == cudaSuccess) e = spec_means(h);
-  if (e == cudaSuccess) e = spec_residual(h, false);
+  // the first application's forward kernel: residual norms and spectrum
+  if (e == cudaSuccess) e = spec_fwd(h, 0);
   if (e == cudaSuccess) {
     k_graph_check<<<1, 32, 0, h->st>>>(P.dsum, gs, tol, floor2, maxit, 1, cond);
     ++h->launches;
@@ -949,8 +1193,10 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
   if (e == cudaSuccess) {
     e = cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, mode);
     if (e == cudaSuccess) {
-      cudaError_t eb = spec_apply(h);
-      if (eb == cudaSuccess) eb = spec_residual(h, false);
+      // finish the application, then the next one's forward kernel: the
+      // residual tested below is that of the updated potential
+      cudaError_t eb = spec_zinv(h);
+      if (eb == cudaSuccess) eb = spec_fwd(h, 0);
       if (eb == cudaSuccess) {
         k_graph_check<<<1, 32, 0, h->st>>>(P.dsum, gs, tol, floor2, maxit, 0, cond);
         ++h->launches;
