@@ -40,7 +40,7 @@ BYTES_PER_SPECIES_SITE = {"fp32": 152, "fp16": 76, "bf16": 76}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128)
@@ -94,51 +94,87 @@ def kernel_traffic(storage="fp32"):
 
 
 class ClockSampler:
+    """nvidia-smi samples (every 50 ms, timestamped) of the SM clock and the
+    throttle reasons; stop() keeps the samples taken inside the window given
+    by begin() / end() (host wall clock), or the one nearest to it when the
+    window is shorter than the sampling interval."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
     def __init__(self, index=0):
         self.proc = None
         self.index = index
         self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index),
-                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
-                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait for the first sample so that the window is covered from its start
+        deadline = time.time() + 5.0
+        while time.time() < deadline and self.proc.poll() is None:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                pass
+            time.sleep(0.02)
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _epoch(ts):
+        from datetime import datetime
+        return datetime.strptime(ts.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.06)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 6:
+            if len(parts) < 7:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx = float(parts[1])
+                t = self._epoch(parts[0])
+                sm, mx = float(parts[1]), float(parts[2])
             except ValueError:
                 continue
-            for n, v in zip(names, parts[2:6]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
+            rows.append((t, sm, mx, [n for n, v in zip(self.NAMES, parts[3:7]) if v.lower() == "active"]))
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = rows
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows if self.t0 <= r[0] <= self.t1]
+            if not inside:
+                mid = 0.5 * (self.t0 + self.t1)
+                inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+        reasons = sorted({n for r in inside for n in r[3]})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": inside[-1][2],
+                "reasons": reasons, "samples": len(inside),
+                "window_s": None if self.t0 is None or self.t1 is None else round(self.t1 - self.t0, 3)}
 
 
 def cpu_oracle_sample(n_sample=32, budget_s=12.0, schmidt=1.0):
@@ -410,10 +446,14 @@ def run_ours(args, rank, world, local):
             clocks.start()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        if clocks:
+            clocks.begin()
         e0.record(stream)
         lat.step(args.steps)
         e1.record(stream)
         lat.synchronize()
+        if clocks:
+            clocks.end()
         barrier()
         clk = clocks.stop() if clocks else None
         t_ms = max_over_ranks(e0.elapsed_time(e1))

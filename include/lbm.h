@@ -68,7 +68,8 @@ typedef struct {
   double e_ext[3];       /* applied field, acceleration per unit valence     */
   int storage;           /* LBM_FP32 | LBM_FP16_SHIFT | LBM_BF16_SHIFT       */
   int poisson;           /* LBM_POISSON_MG | LBM_POISSON_SOR | LBM_POISSON_FFT */
-  double poisson_tol;    /* ||s - A psi||_2 / ||s||_2 target, e.g. 1e-8      */
+  double poisson_tol;    /* ||s - A psi||_2 / ||s||_2 target, e.g. 1e-8, or
+                            rms residual <= 4 * 2^-52 (psi's resolution)  */
   int poisson_maxit;     /* iteration cap (V-cycles or SOR sweeps)           */
   int device;            /* CUDA device ordinal                              */
   int flags;             /* LBM_FLAG_* bits                                  */

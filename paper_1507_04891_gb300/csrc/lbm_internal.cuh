@@ -28,6 +28,48 @@ constexpr double PSI_INV_SCALE = 1.0 / 4503599627370496.0;
 constexpr float PSI_SCALE_F = 4503599627370496.0f;
 constexpr float PSI_INV_SCALE_F = 1.0f / 4503599627370496.0f;
 constexpr double PSI_MAX = 2048.0;                      // 2^11
+// Absolute convergence floor of the Poisson solvers, as an rms residual in
+// fixed-point units: rounding psi to the 2^-52 grid alone leaves a residual
+// of rms sqrt((36 + 6) / 12) = 1.9 units under the 7-point operator, so a
+// source of vanishing norm is solved once the residual is within twice that.
+constexpr double RES_FLOOR_RMS = 4.0;
+
+#ifdef __CUDACC__
+// Conversions between 64-bit integers and FP32 on the 32-bit integer and FP32
+// pipes: the instructions for 64-bit conversions issue on the FP64 pipe,
+// which is narrow on this GPU (ncu shows the residual kernels bound by it).
+//
+// i64_to_f32: |v| = hi 2^32 + lo; hi, lo >> 16 and lo & 0xffff (each below
+// 2^23) become floats exactly by placing them in the mantissa of 2^23 and
+// subtracting 2^23; two FMAs join them (two roundings: within about one ulp
+// of the correctly rounded value).  |v| >= 2^55 takes the plain conversion.
+__device__ __forceinline__ float i64_to_f32(int64_t v) {
+  const bool neg = v < 0;
+  const uint64_t a = neg ? 0ull - (uint64_t)v : (uint64_t)v;
+  const uint32_t hi = (uint32_t)(a >> 32), lo = (uint32_t)a;
+  if (hi >= (1u << 23)) return (float)v;
+  const float fh = __uint_as_float(0x4B000000u | hi) - 8388608.0f;
+  const float fm = __uint_as_float(0x4B000000u | (lo >> 16)) - 8388608.0f;
+  const float fl = __uint_as_float(0x4B000000u | (lo & 0xFFFFu)) - 8388608.0f;
+  const float f = fmaf(fh, 4294967296.0f, fmaf(fm, 65536.0f, fl));
+  return neg ? -f : f;
+}
+
+// f32_to_i64_rn: nearest integer (ties to even), |f| < 2^63.  |f| < 2^22:
+// adding 1.5 * 2^23 rounds f to an integer in the low mantissa bits.  Else
+// |f| rounded to an integer (exactly, by adding and subtracting 2^23 below
+// 2^23) is mantissa * 2^e, shifted into place.
+__device__ __forceinline__ int64_t f32_to_i64_rn(float f) {
+  const float a = fabsf(f);
+  if (a < 4194304.0f) return (int64_t)(__float_as_int(f + 12582912.0f) - 0x4B400000);
+  const float r = a < 8388608.0f ? (a + 8388608.0f) - 8388608.0f : a;
+  const uint32_t b = __float_as_uint(r);
+  const int e = (int)(b >> 23) - 150;
+  const uint64_t mant = (uint64_t)((b & 0x7FFFFFu) | 0x800000u);
+  const int64_t m = (int64_t)(e >= 0 ? mant << e : mant >> 1);
+  return f < 0.f ? -m : m;
+}
+#endif
 
 // Per-node link word (only allocated when walls exist):
 //   bit 0      node is a wall node

@@ -372,7 +372,7 @@ __global__ void k_to_half(const float* p, __half* ph, int n) {
 __global__ void k_nn_apply(int64_t* psi, const float* __restrict__ dpsi, int64_t n, int sign) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int64_t d = llrintf(dpsi[i] * PSI_SCALE_F);
+  const int64_t d = f32_to_i64_rn(dpsi[i] * PSI_SCALE_F);
   psi[i] += sign > 0 ? d : -d;
 }
 

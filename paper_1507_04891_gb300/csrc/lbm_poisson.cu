@@ -67,7 +67,7 @@ __device__ __forceinline__ void box_xyz(uint32_t c, const Box& b, int& x,
 }
 
 __device__ __forceinline__ int64_t fx_of(float e) {
-  return llrintf(e * PSI_SCALE_F);
+  return f32_to_i64_rn(e * PSI_SCALE_F);
 }
 
 // Residual on the fine box, r = s - <s> - A psi, exact in 64-bit integers.
@@ -107,10 +107,10 @@ __global__ void __launch_bounds__(256) k_res0(
       Ap += pc - psi[i + d[f]];
     }
     const int64_t sfx = src[i] - (label ? comp_mean[label[i]] : (int64_t)s_mean);
-    const float rf = (float)(sfx - Ap);
+    const float rf = i64_to_f32(sfx - Ap);
     r[c] = rf * PSI_INV_SCALE_F;
     rr += rf * rf;
-    const float sf = (float)sfx;
+    const float sf = i64_to_f32(sfx);
     ss += sf * sf;
   }
 #pragma unroll
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256) k_sor0(
   }
   if (cnt == 0) return;
   const int64_t rfx = src[i] - (label ? comp_mean[label[i]] : (int64_t)s_mean) - Ap;
-  psi[i] = pc + llrintf(omega * (float)rfx / (float)cnt);
+  psi[i] = pc + f32_to_i64_rn(omega * i64_to_f32(rfx) / (float)cnt);
 }
 
 struct CL {  // coarse level view
@@ -865,7 +865,7 @@ lbm_status residual_read(lbm_t* h, double tol, double* rel, bool* done) {
     h->err = "Poisson residual is not finite";
     return LBM_EUNSTABLE;
   }
-  *done = rn <= tol * sn || rn <= 2.0 * sqrt((double)h->nfluid);
+  *done = rn <= tol * sn || rn <= RES_FLOOR_RMS * sqrt((double)h->nfluid);
   return LBM_OK;
 }
 

@@ -196,6 +196,73 @@ struct SpecArgs {
   const float* lamz;
 };
 
+// Geometry of one fluid plane for the residual: the offsets of the planes
+// above and below and whether those are fluid (open faces).
+struct PlaneNbr {
+  int64_t dup, ddn;
+  bool up, dn;
+  long long mean;
+};
+
+__device__ __forceinline__ PlaneNbr plane_nbr(const unsigned char* __restrict__ plane_fluid,
+                                              const long long* __restrict__ mean_z, int z,
+                                              int nx, int ny, int nz) {
+  PlaneNbr g;
+  const int64_t nxy = (int64_t)nx * ny;
+  const int zp = (z == nz - 1) ? 0 : z + 1, zm = (z == 0) ? nz - 1 : z - 1;
+  g.up = nz > 1 && zp != z && plane_fluid[zp];
+  g.dn = nz > 1 && zm != z && plane_fluid[zm];
+  g.dup = (int64_t)(zp - z) * nxy;
+  g.ddn = (int64_t)(zm - z) * nxy;
+  g.mean = mean_z[z];
+  return g;
+}
+
+template <int G>
+__device__ __forceinline__ void loadg(const int64_t* __restrict__ p, int64_t (&v)[G]) {
+#pragma unroll
+  for (int k = 0; k < G / 2; ++k) {
+    const longlong2 a = __ldg(reinterpret_cast<const longlong2*>(p) + k);
+    v[2 * k] = a.x;
+    v[2 * k + 1] = a.y;
+  }
+}
+
+// Exact residual r = s - <s> - A psi at the G (2 or 4) consecutive nodes
+// x0..x0+G-1 (x0 a multiple of G) of row y of a fluid plane, i0 the index of
+// (x0, y): 16-byte loads of the row, the rows y +- 1 and the planes z +- 1,
+// two scalar loads for the x neighbours at the ends.  r in fixed-point
+// units (FP32); rr, ss accumulate |r|^2 and |s - <s>|^2.
+template <int G>
+__device__ __forceinline__ void residual_g(const int64_t* __restrict__ psi,
+                                           const int64_t* __restrict__ src, int64_t i0, int x0,
+                                           int y, int nx, int ny, const PlaneNbr& g,
+                                           float (&r)[G], float& rr, float& ss) {
+  int64_t c[G], yp[G], ym[G], zp[G], zm[G], sv[G];
+  loadg<G>(psi + i0, c);
+  const int64_t row = i0 - x0;
+  const int64_t xl = __ldg(psi + row + ((x0 - 1) & (nx - 1)));
+  const int64_t xr = __ldg(psi + row + ((x0 + G) & (nx - 1)));
+  loadg<G>(psi + (y == ny - 1 ? i0 - (int64_t)(ny - 1) * nx : i0 + nx), yp);
+  loadg<G>(psi + (y == 0 ? i0 + (int64_t)(ny - 1) * nx : i0 - nx), ym);
+  if (g.up) loadg<G>(psi + i0 + g.dup, zp);
+  if (g.dn) loadg<G>(psi + i0 + g.ddn, zm);
+  loadg<G>(src + i0, sv);
+#pragma unroll
+  for (int j = 0; j < G; ++j) {
+    const int64_t left = j == 0 ? xl : c[j - 1], right = j == G - 1 ? xr : c[j + 1];
+    int64_t Ap = 4 * c[j] - left - right - yp[j] - ym[j];
+    if (g.up) Ap += c[j] - zp[j];
+    if (g.dn) Ap += c[j] - zm[j];
+    const int64_t sfx = sv[j] - g.mean;
+    const float rf = i64_to_f32(sfx - Ap);
+    const float sf = i64_to_f32(sfx);
+    rr += rf * rf;
+    ss += sf * sf;
+    r[j] = rf;
+  }
+}
+
 // Shared memory of one plane in the plane kernels: the half spectrum
 // (mxy values, row stride H + 1, odd) and the padded lines of the row or
 // column transforms (nx ny / 2 elements with padding).
@@ -229,48 +296,37 @@ __global__ void __launch_bounds__(1024, 1) k_plane_fwd(
   float2 v[8];
   float rr = 0.f, ss = 0.f;
 
-  // ---- x: residual rows 2q, 2q + 1 -> complex FFT -> half spectra
+  // ---- residual of the plane, two consecutive x per thread and step,
+  // into the line of its row pair (row 2q at float offset 0, row 2q + 1 at
+  // nx); a transform later overwrites only its own line, after reading it
+  if (valid) {
+    const PlaneNbr g = plane_nbr(plane_fluid, mean_z, z, nx, ny, a.nz);
+    const int ngroups = (nx * ny) >> 1, gpr = nx >> 1;
+    for (int gi = w; gi < ngroups; gi += tp) {
+      const int y = gi / gpr, x0 = (gi - y * gpr) << 1;
+      float r2[2];
+      residual_g<2>(psi, src, ((int64_t)z * ny + y) * nx + x0, x0, y, nx, ny, g, r2, rr, ss);
+      float* rb = reinterpret_cast<float*>(scr + (y >> 1) * padded_len(nx)) + (y & 1) * nx + x0;
+      rb[0] = r2[0] * PSI_INV_SCALE_F;
+      rb[1] = r2[1] * PSI_INV_SCALE_F;
+    }
+  }
+  __syncthreads();
+
+  // ---- x: rows 2q, 2q + 1 -> one complex FFT -> half spectra
   {
     const int Tx = nx >> 3;
     const int q = w >> (lgx - 3), t = w & (Tx - 1);
     const PadLine line{scr + q * padded_len(nx)};
     const int y0 = 2 * q;
-    if (valid) {
-      const int nz = a.nz;
-      const int64_t nxy = (int64_t)nx * ny;
-      const int zp = (z == nz - 1) ? 0 : z + 1, zm = (z == 0) ? nz - 1 : z - 1;
-      const bool up = nz > 1 && zp != z && plane_fluid[zp];
-      const bool dn = nz > 1 && zm != z && plane_fluid[zm];
-      const int64_t dup = (int64_t)(zp - z) * nxy, ddn = (int64_t)(zm - z) * nxy;
-      const long long mz = mean_z[z];
+    {
+      const float* rb = reinterpret_cast<const float*>(scr + q * padded_len(nx));
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int x = t + u * Tx;
-        float rv[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int y = y0 + h;
-          const int64_t i = ((int64_t)z * ny + y) * nx + x;
-          const int64_t pc = psi[i];
-          int64_t Ap = 4 * pc;
-          Ap -= psi[i + (x == nx - 1 ? -(nx - 1) : 1)];
-          Ap -= psi[i + (x == 0 ? nx - 1 : -1)];
-          Ap -= psi[i + (y == ny - 1 ? -(int64_t)(ny - 1) * nx : nx)];
-          Ap -= psi[i + (y == 0 ? (int64_t)(ny - 1) * nx : -nx)];
-          if (up) Ap += pc - psi[i + dup];
-          if (dn) Ap += pc - psi[i + ddn];
-          const int64_t sfx = src[i] - mz;
-          const float rf = (float)(sfx - Ap);
-          rr += rf * rf;
-          const float sf = (float)sfx;
-          ss += sf * sf;
-          rv[h] = rf * PSI_INV_SCALE_F;
-        }
-        v[u] = make_float2(rv[0], rv[1]);
+        v[u] = valid ? make_float2(rb[x], rb[nx + x]) : make_float2(0.f, 0.f);
       }
-    } else {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = make_float2(0.f, 0.f);
+      __syncwarp();
     }
     fft_regs<false>(v, t, lgx, line, a.twx, -1.f);
     // R_2q(k) = (C(k) + conj C(-k)) / 2, R_2q+1(k) = (C(k) - conj C(-k)) / 2i
@@ -425,8 +481,8 @@ __global__ void __launch_bounds__(1024, 1) k_plane_inv(const float2* __restrict_
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int x = t + u * Tx;
-        row0[x] += llrintf(v[u].x * scale);
-        row1[x] += llrintf(v[u].y * scale);
+        row0[x] += f32_to_i64_rn(v[u].x * scale);
+        row1[x] += f32_to_i64_rn(v[u].y * scale);
       }
     }
   }
@@ -638,46 +694,33 @@ __global__ void k_run_means(const long long* __restrict__ psum, const Run* __res
 
 // Residual with per-plane means: r = s - mean_z - A psi (exact), norms into
 // dsum[1], dsum[2]; r (scaled to real units) is stored only when r != NULL.
-// Wall planes contribute nothing.
-__global__ void __launch_bounds__(256) k_res_planes(
+// Four consecutive x per thread and step (residual_g).  Wall planes
+// contribute nothing.
+__global__ void __launch_bounds__(256, 2) k_res_planes(
     const int64_t* __restrict__ psi, const int64_t* __restrict__ src,
     const long long* __restrict__ mean_z, const unsigned char* __restrict__ plane_fluid,
     float* __restrict__ r, double* dsum, int nx, int ny, int nz, int lgx, int lgxy) {
   __shared__ float red_r[8], red_s[8];
-  const int nxy = nx * ny;
-  const int64_t N = (int64_t)nxy * nz;
+  const int64_t ngroups = ((int64_t)nx * ny * nz) >> 2;
+  const int lgg = lgxy - 2, lgr = lgx - 2;  // groups per plane, per row
   float rr = 0.f, ss = 0.f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    // nx, ny are powers of two: plane, row and column by shifts
-    const int z = (int)(i >> lgxy);
-    const int k = (int)(i & (nxy - 1));
+  for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < ngroups;
+       gi += (int64_t)gridDim.x * blockDim.x) {
+    const int z = (int)(gi >> lgg);
+    const int k = (int)(gi & ((1 << lgg) - 1));
+    const int y = k >> lgr, x0 = (k & ((1 << lgr) - 1)) << 2;
+    const int64_t i0 = ((int64_t)z * ny + y) * nx + x0;
     if (!plane_fluid[z]) {
-      if (r) r[i] = 0.f;
+      if (r) *reinterpret_cast<float4*>(r + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
       continue;
     }
-    const int y = k >> lgx, x = k & (nx - 1);
-    const int64_t pc = psi[i];
-    int64_t Ap = 0;
-    if (nx > 1) {
-      Ap += pc - psi[i + (x == nx - 1 ? -(nx - 1) : 1)];
-      Ap += pc - psi[i + (x == 0 ? nx - 1 : -1)];
-    }
-    if (ny > 1) {
-      Ap += pc - psi[i + (y == ny - 1 ? -(int64_t)(ny - 1) * nx : nx)];
-      Ap += pc - psi[i + (y == 0 ? (int64_t)(ny - 1) * nx : -nx)];
-    }
-    if (nz > 1) {
-      const int zp = (z == nz - 1) ? 0 : z + 1, zm = (z == 0) ? nz - 1 : z - 1;
-      if (plane_fluid[zp] && zp != z) Ap += pc - psi[(int64_t)zp * nxy + k];
-      if (plane_fluid[zm] && zm != z) Ap += pc - psi[(int64_t)zm * nxy + k];
-    }
-    const int64_t sfx = src[i] - mean_z[z];
-    const float rf = (float)(sfx - Ap);
-    if (r) r[i] = rf * PSI_INV_SCALE_F;
-    rr += rf * rf;
-    const float sf = (float)sfx;
-    ss += sf * sf;
+    const PlaneNbr g = plane_nbr(plane_fluid, mean_z, z, nx, ny, nz);
+    float r4[4];
+    residual_g<4>(psi, src, i0, x0, y, nx, ny, g, r4, rr, ss);
+    if (r)
+      *reinterpret_cast<float4*>(r + i0) =
+          make_float4(r4[0] * PSI_INV_SCALE_F, r4[1] * PSI_INV_SCALE_F, r4[2] * PSI_INV_SCALE_F,
+                      r4[3] * PSI_INV_SCALE_F);
   }
   for (int off = 16; off > 0; off >>= 1) {
     rr += __shfl_down_sync(0xffffffffu, rr, off);
@@ -917,7 +960,7 @@ cudaError_t spec_residual(lbm_t* h, int slot, bool with_r) {
   double* out = norm_slot(h, slot);
   cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), h->st);
   if (e != cudaSuccess) return e;
-  const unsigned nb = (unsigned)std::min<int64_t>(nblk(h->N, 256), h->grid_cap);
+  const unsigned nb = (unsigned)std::min<int64_t>(nblk(h->N / 4, 256), h->grid_cap);
   k_res_planes<<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, s->mean_z, s->plane_fluid,
                                       with_r ? s->r : nullptr, out - 1, s->nx, s->ny, s->nz,
                                       s->lgx, s->lgx + s->lgy);
@@ -990,7 +1033,7 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
     h->err = "spectral Poisson solver: fluid run along z too long for shared memory";
     return LBM_EINVAL;
   }
-  const double floor = 2.0 * sqrt((double)h->nfluid);
+  const double floor = RES_FLOOR_RMS * sqrt((double)h->nfluid);
   auto conv_of = [&](double rn, double sn) { return rn <= tol * sn || rn <= floor; };
   LBM_CUDA_TRY(h, spec_means(h));
   double rn = 0.0, sn = 0.0;
@@ -1146,7 +1189,7 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
   h->cur = parity;
   GraphStatus* gs = reinterpret_cast<GraphStatus*>(h->gstatus);
   const double tol = h->cfg.poisson_tol;
-  const double floor2 = 4.0 * (double)h->nfluid;
+  const double floor2 = RES_FLOOR_RMS * RES_FLOOR_RMS * (double)h->nfluid;
   const int maxit = h->cfg.poisson_maxit;
   cudaGraph_t G = nullptr;
   LBM_CUDA_TRY(h, cudaGraphCreate(&G, 0));
