@@ -494,21 +494,31 @@ __global__ void __launch_bounds__(256) k_charge(
   block_partial(acc, part);
 }
 
-// Sums the per-CTA partials of k_charge into *out (FP64; each partial is
-// exact in FP64).
+// Sums the per-CTA partials of k_charge into *out exactly in 128-bit
+// integers (FP64 arithmetic is slow on this GPU), converted to FP64 once.
 __global__ void __launch_bounds__(1024) k_sum_partials(const long long* part, int n,
                                                        double* out) {
-  __shared__ double red[32];
-  double v = 0.0;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) v += (double)part[k];
+  __shared__ long long red_hi[32];
+  __shared__ unsigned long long red_lo[32];
+  __int128 v = 0;
+#pragma unroll 8
+  for (int k = threadIdx.x; k < n; k += blockDim.x) v += (__int128)part[k];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  for (int off = 16; off > 0; off >>= 1) {
+    const long long hi = __shfl_down_sync(0xffffffffu, (long long)(v >> 64), off);
+    const unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)v, off);
+    v += ((__int128)hi << 64) | (__int128)lo;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_hi[threadIdx.x >> 5] = (long long)(v >> 64);
+    red_lo[threadIdx.x >> 5] = (unsigned long long)v;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-    *out = tot;
+    __int128 tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      tot += ((__int128)red_hi[w] << 64) | (__int128)red_lo[w];
+    *out = (double)tot;
   }
 }
 

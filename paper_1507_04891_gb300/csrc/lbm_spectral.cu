@@ -183,6 +183,40 @@ __device__ __forceinline__ void fft_regs(float2 (&v)[8], int t, int lg, Line lin
   }
 }
 
+// Squared norms are accumulated by CTA b into partial NACC slot b mod NACC:
+// one FP32 atomic per CTA and quantity (FP64 atomics are slow on this GPU),
+// spread over addresses so that thousands of CTAs do not queue on one, and
+// scaled by 2^-40 so that sums of squares of fixed-point values stay far
+// inside the FP32 range.  A norm slot holds NACC partials of |r|^2 followed
+// by NACC of |s - <s>|^2; the reader sums them in FP64 and scales back.  The
+// norms only decide convergence, so FP32 partials (relative error ~1e-6)
+// are ample.
+constexpr int NACC = 64;
+constexpr float NORM_SCALE = 1.0f / 1099511627776.0f;  // 2^-40
+
+__device__ __forceinline__ void add_norms(float* acc, float rr, float ss, float* red_r,
+                                          float* red_s) {
+  for (int off = 16; off > 0; off >>= 1) {
+    rr += __shfl_down_sync(0xffffffffu, rr, off);
+    ss += __shfl_down_sync(0xffffffffu, ss, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_r[threadIdx.x >> 5] = rr * NORM_SCALE;
+    red_s[threadIdx.x >> 5] = ss * NORM_SCALE;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float tr = 0.f, ts = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      tr += red_r[i];
+      ts += red_s[i];
+    }
+    const int k = blockIdx.x & (NACC - 1);
+    atomicAdd(acc + k, tr);
+    atomicAdd(acc + NACC + k, ts);
+  }
+}
+
 struct SpecArgs {
   int nx, ny, nz, lgx, lgy, lgz;
   int H;       // nx / 2: the half spectrum keeps kx = 0..H
@@ -196,28 +230,6 @@ struct SpecArgs {
   const float* lamz;
 };
 
-// Geometry of one fluid plane for the residual: the offsets of the planes
-// above and below and whether those are fluid (open faces).
-struct PlaneNbr {
-  int64_t dup, ddn;
-  bool up, dn;
-  long long mean;
-};
-
-__device__ __forceinline__ PlaneNbr plane_nbr(const unsigned char* __restrict__ plane_fluid,
-                                              const long long* __restrict__ mean_z, int z,
-                                              int nx, int ny, int nz) {
-  PlaneNbr g;
-  const int64_t nxy = (int64_t)nx * ny;
-  const int zp = (z == nz - 1) ? 0 : z + 1, zm = (z == 0) ? nz - 1 : z - 1;
-  g.up = nz > 1 && zp != z && plane_fluid[zp];
-  g.dn = nz > 1 && zm != z && plane_fluid[zm];
-  g.dup = (int64_t)(zp - z) * nxy;
-  g.ddn = (int64_t)(zm - z) * nxy;
-  g.mean = mean_z[z];
-  return g;
-}
-
 template <int G>
 __device__ __forceinline__ void loadg(const int64_t* __restrict__ p, int64_t (&v)[G]) {
 #pragma unroll
@@ -229,32 +241,41 @@ __device__ __forceinline__ void loadg(const int64_t* __restrict__ p, int64_t (&v
 }
 
 // Exact residual r = s - <s> - A psi at the G (2 or 4) consecutive nodes
-// x0..x0+G-1 (x0 a multiple of G) of row y of a fluid plane, i0 the index of
-// (x0, y): 16-byte loads of the row, the rows y +- 1 and the planes z +- 1,
-// two scalar loads for the x neighbours at the ends.  r in fixed-point
-// units (FP32); rr, ss accumulate |r|^2 and |s - <s>|^2.
+// x0..x0+G-1 (x0 a multiple of G) of row y of plane z, i0 the index of
+// (x0, y, z): 16-byte loads of the row, the rows y +- 1 and the planes
+// z +- 1, two scalar loads for the x neighbours at the ends.  Every load,
+// the flags of the planes z +- 1 (open faces) and the plane's source mean
+// included, is issued before any is used: one memory round trip.  r in
+// fixed-point units (FP32); returns |r|^2 and |s - <s>|^2 through rr, ss.
 template <int G>
 __device__ __forceinline__ void residual_g(const int64_t* __restrict__ psi,
-                                           const int64_t* __restrict__ src, int64_t i0, int x0,
-                                           int y, int nx, int ny, const PlaneNbr& g,
+                                           const int64_t* __restrict__ src,
+                                           const unsigned char* __restrict__ plane_fluid,
+                                           const long long* __restrict__ mean_z, int64_t i0,
+                                           int x0, int y, int z, int nx, int ny, int nz,
                                            float (&r)[G], float& rr, float& ss) {
-  int64_t c[G], yp[G], ym[G], zp[G], zm[G], sv[G];
+  const int64_t nxy = (int64_t)nx * ny;
+  const int zp = (z == nz - 1) ? 0 : z + 1, zm = (z == 0) ? nz - 1 : z - 1;
+  int64_t c[G], yp[G], ym[G], up[G], dn[G], sv[G];
   loadg<G>(psi + i0, c);
   const int64_t row = i0 - x0;
   const int64_t xl = __ldg(psi + row + ((x0 - 1) & (nx - 1)));
   const int64_t xr = __ldg(psi + row + ((x0 + G) & (nx - 1)));
   loadg<G>(psi + (y == ny - 1 ? i0 - (int64_t)(ny - 1) * nx : i0 + nx), yp);
   loadg<G>(psi + (y == 0 ? i0 + (int64_t)(ny - 1) * nx : i0 - nx), ym);
-  if (g.up) loadg<G>(psi + i0 + g.dup, zp);
-  if (g.dn) loadg<G>(psi + i0 + g.ddn, zm);
+  loadg<G>(psi + i0 + (int64_t)(zp - z) * nxy, up);
+  loadg<G>(psi + i0 + (int64_t)(zm - z) * nxy, dn);
   loadg<G>(src + i0, sv);
+  const bool fup = nz > 1 && zp != z && __ldg(plane_fluid + zp);
+  const bool fdn = nz > 1 && zm != z && __ldg(plane_fluid + zm);
+  const long long mean = __ldg(mean_z + z);
 #pragma unroll
   for (int j = 0; j < G; ++j) {
     const int64_t left = j == 0 ? xl : c[j - 1], right = j == G - 1 ? xr : c[j + 1];
     int64_t Ap = 4 * c[j] - left - right - yp[j] - ym[j];
-    if (g.up) Ap += c[j] - zp[j];
-    if (g.dn) Ap += c[j] - zm[j];
-    const int64_t sfx = sv[j] - g.mean;
+    if (fup) Ap += c[j] - up[j];
+    if (fdn) Ap += c[j] - dn[j];
+    const int64_t sfx = sv[j] - mean;
     const float rf = i64_to_f32(sfx - Ap);
     const float sf = i64_to_f32(sfx);
     rr += rf * rf;
@@ -275,12 +296,13 @@ __host__ __device__ constexpr int plane_smem_words(int nx, int ny) {
 // 2q + 1 packed as C = r_2q + i r_2q+1), and along y thread w mod (ny/8) of
 // column c = w div (ny/8) (c = 0 carries the real columns kx = 0 and kx = H
 // packed the same way).  The residual r = s - <s> - A psi is computed
-// exactly in int64 as the x transform loads it; its squared norms (and the
-// source's) go to dsum[0], dsum[1] of the slot given.
+// exactly in int64 (two nodes per thread and step); its squared norms (and
+// the source's) are added to the norm slot given.  planes: the fluid planes' indices, or
+// NULL when every plane is fluid (plane index = CTA slot index).
 __global__ void __launch_bounds__(1024, 1) k_plane_fwd(
     const int64_t* __restrict__ psi, const int64_t* __restrict__ src,
     const long long* __restrict__ mean_z, const unsigned char* __restrict__ plane_fluid,
-    const int* __restrict__ planes, int nplanes, float2* __restrict__ spec, double* norms,
+    const int* __restrict__ planes, int nplanes, float2* __restrict__ spec, float* norms,
     SpecArgs a) {
   extern __shared__ __align__(16) float2 sm[];
   __shared__ float red_r[32], red_s[32];
@@ -289,7 +311,7 @@ __global__ void __launch_bounds__(1024, 1) k_plane_fwd(
   const int slot = threadIdx.x >> a.lgtp, w = threadIdx.x & (tp - 1);
   const int pi = blockIdx.x * (blockDim.x >> a.lgtp) + slot;
   const bool valid = pi < nplanes;
-  const int z = valid ? planes[pi] : 0;
+  const int z = !valid ? 0 : (planes ? planes[pi] : pi);
   float2* S = sm + (size_t)slot * plane_smem_words(nx, ny);
   float2* scr = S + a.mxy;
   const int rs = H + 1;  // row stride of S
@@ -300,12 +322,15 @@ __global__ void __launch_bounds__(1024, 1) k_plane_fwd(
   // into the line of its row pair (row 2q at float offset 0, row 2q + 1 at
   // nx); a transform later overwrites only its own line, after reading it
   if (valid) {
-    const PlaneNbr g = plane_nbr(plane_fluid, mean_z, z, nx, ny, a.nz);
-    const int ngroups = (nx * ny) >> 1, gpr = nx >> 1;
-    for (int gi = w; gi < ngroups; gi += tp) {
+    const int gpr = nx >> 1;
+    // nx ny / 2 pairs over nx ny / 16 threads: eight per thread
+#pragma unroll 2
+    for (int j = 0; j < 8; ++j) {
+      const int gi = w + j * tp;
       const int y = gi / gpr, x0 = (gi - y * gpr) << 1;
       float r2[2];
-      residual_g<2>(psi, src, ((int64_t)z * ny + y) * nx + x0, x0, y, nx, ny, g, r2, rr, ss);
+      residual_g<2>(psi, src, plane_fluid, mean_z, ((int64_t)z * ny + y) * nx + x0, x0, y, z, nx,
+                    ny, a.nz, r2, rr, ss);
       float* rb = reinterpret_cast<float*>(scr + (y >> 1) * padded_len(nx)) + (y & 1) * nx + x0;
       rb[0] = r2[0] * PSI_INV_SCALE_F;
       rb[1] = r2[1] * PSI_INV_SCALE_F;
@@ -376,29 +401,15 @@ __global__ void __launch_bounds__(1024, 1) k_plane_fwd(
   if (valid) {
     float4* dst = reinterpret_cast<float4*>(spec + (int64_t)z * a.mxy);
     const float4* s4 = reinterpret_cast<const float4*>(S);
-    // mxy is even (ny >= 8) and the plane offset is a multiple of 2 values
-    for (int i = w; i < (a.mxy >> 1); i += tp) dst[i] = s4[i];
+    // mxy / 2 = 4 tp + ny / 2 pairs of values (mxy even, plane offset even)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int i = w + k * tp;
+      if (k < 4 || i < (a.mxy >> 1)) dst[i] = s4[i];
+    }
   }
 
-  // norms: warp, then CTA, one atomic pair per CTA
-  for (int off = 16; off > 0; off >>= 1) {
-    rr += __shfl_down_sync(0xffffffffu, rr, off);
-    ss += __shfl_down_sync(0xffffffffu, ss, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red_r[threadIdx.x >> 5] = rr;
-    red_s[threadIdx.x >> 5] = ss;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tr = 0.0, ts = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      tr += (double)red_r[i];
-      ts += (double)red_s[i];
-    }
-    atomicAdd(norms, tr);
-    atomicAdd(norms + 1, ts);
-  }
+  add_norms(norms, rr, ss, red_r, red_s);
 }
 
 // Inverse plane kernel: y inverse (column 0 carries kx = 0 and H packed as
@@ -415,7 +426,7 @@ __global__ void __launch_bounds__(1024, 1) k_plane_inv(const float2* __restrict_
   const int slot = threadIdx.x >> a.lgtp, w = threadIdx.x & (tp - 1);
   const int pi = blockIdx.x * (blockDim.x >> a.lgtp) + slot;
   const bool valid = pi < nplanes;
-  const int z = valid ? planes[pi] : 0;
+  const int z = !valid ? 0 : (planes ? planes[pi] : pi);
   float2* S = sm + (size_t)slot * plane_smem_words(nx, ny);
   float2* scr = S + a.mxy;
   const int rs = H + 1;
@@ -423,7 +434,17 @@ __global__ void __launch_bounds__(1024, 1) k_plane_inv(const float2* __restrict_
   {
     float4* s4 = reinterpret_cast<float4*>(S);
     const float4* src4 = reinterpret_cast<const float4*>(spec + (int64_t)z * a.mxy);
-    for (int i = w; i < (a.mxy >> 1); i += tp) s4[i] = valid ? src4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 t4[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int i = w + k * tp;
+      t4[k] = valid && (k < 4 || i < (a.mxy >> 1)) ? src4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int i = w + k * tp;
+      if (k < 4 || i < (a.mxy >> 1)) s4[i] = t4[k];
+    }
   }
   __syncthreads();
   {
@@ -692,54 +713,37 @@ __global__ void k_run_means(const long long* __restrict__ psum, const Run* __res
   }
 }
 
-// Residual with per-plane means: r = s - mean_z - A psi (exact), norms into
-// dsum[1], dsum[2]; r (scaled to real units) is stored only when r != NULL.
-// Four consecutive x per thread and step (residual_g).  Wall planes
-// contribute nothing.
-__global__ void __launch_bounds__(256, 2) k_res_planes(
+// Residual with per-plane means: r = s - mean_z - A psi (exact), its
+// squared norms (and the source's) added to the norm slot acc; r (scaled to
+// real units) is stored only when r != NULL.  One thread per two consecutive
+// x (residual_g), no loop: every load of a thread is in flight at once.
+// Wall planes contribute nothing.
+__global__ void __launch_bounds__(256, 4) k_res_planes(
     const int64_t* __restrict__ psi, const int64_t* __restrict__ src,
     const long long* __restrict__ mean_z, const unsigned char* __restrict__ plane_fluid,
-    float* __restrict__ r, double* dsum, int nx, int ny, int nz, int lgx, int lgxy) {
+    float* __restrict__ r, float* acc, int nx, int ny, int nz, int lgx, int lgxy) {
   __shared__ float red_r[8], red_s[8];
-  const int64_t ngroups = ((int64_t)nx * ny * nz) >> 2;
-  const int lgg = lgxy - 2, lgr = lgx - 2;  // groups per plane, per row
+  const int64_t npairs = ((int64_t)nx * ny * nz) >> 1;
+  const int lgg = lgxy - 1, lgr = lgx - 1;  // pairs per plane, per row
   float rr = 0.f, ss = 0.f;
-  for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < ngroups;
-       gi += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gi < npairs) {
     const int z = (int)(gi >> lgg);
     const int k = (int)(gi & ((1 << lgg) - 1));
-    const int y = k >> lgr, x0 = (k & ((1 << lgr) - 1)) << 2;
+    const int y = k >> lgr, x0 = (k & ((1 << lgr) - 1)) << 1;
     const int64_t i0 = ((int64_t)z * ny + y) * nx + x0;
-    if (!plane_fluid[z]) {
-      if (r) *reinterpret_cast<float4*>(r + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
-      continue;
+    const bool fluid = __ldg(plane_fluid + z);
+    float r2[2], a = 0.f, b = 0.f;
+    residual_g<2>(psi, src, plane_fluid, mean_z, i0, x0, y, z, nx, ny, nz, r2, a, b);
+    if (fluid) {
+      rr = a;
+      ss = b;
+    } else {
+      r2[0] = r2[1] = 0.f;
     }
-    const PlaneNbr g = plane_nbr(plane_fluid, mean_z, z, nx, ny, nz);
-    float r4[4];
-    residual_g<4>(psi, src, i0, x0, y, nx, ny, g, r4, rr, ss);
-    if (r)
-      *reinterpret_cast<float4*>(r + i0) =
-          make_float4(r4[0] * PSI_INV_SCALE_F, r4[1] * PSI_INV_SCALE_F, r4[2] * PSI_INV_SCALE_F,
-                      r4[3] * PSI_INV_SCALE_F);
+    if (r) *reinterpret_cast<float2*>(r + i0) = make_float2(r2[0] * PSI_INV_SCALE_F, r2[1] * PSI_INV_SCALE_F);
   }
-  for (int off = 16; off > 0; off >>= 1) {
-    rr += __shfl_down_sync(0xffffffffu, rr, off);
-    ss += __shfl_down_sync(0xffffffffu, ss, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red_r[threadIdx.x >> 5] = rr;
-    red_s[threadIdx.x >> 5] = ss;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tr = 0.0, ts = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      tr += (double)red_r[w];
-      ts += (double)red_s[w];
-    }
-    atomicAdd(dsum + 1, tr);
-    atomicAdd(dsum + 2, ts);
-  }
+  add_norms(acc, rr, ss, red_r, red_s);
 }
 
 int ilog2(int n) {
@@ -770,6 +774,8 @@ struct SpectralPlan {
   float* r = nullptr;              // N (residual for the learned guess)
   long long* psum = nullptr;       // nz
   long long* mean_z = nullptr;     // nz
+  float* nacc = nullptr;           // norm slots, Poisson::NSLOT x 2 NACC
+  float* hacc = nullptr;           // pinned mirror
 };
 
 void spectral_free(lbm_t* h) {
@@ -784,6 +790,8 @@ void spectral_free(lbm_t* h) {
   cudaFree(s->r);
   cudaFree(s->psum);
   cudaFree(s->mean_z);
+  cudaFree(s->nacc);
+  if (s->hacc) cudaFreeHost(s->hacc);
   delete s;
   h->spec = nullptr;
 }
@@ -867,7 +875,13 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
             al((void**)&s->tw, ntw * sizeof(float2)) && al((void**)&s->lam, nlam * sizeof(float)) &&
             al((void**)&s->spec, (size_t)nz * s->mxy * sizeof(float2)) &&
             al((void**)&s->r, N * sizeof(float)) && al((void**)&s->psum, nz * sizeof(long long)) &&
-            al((void**)&s->mean_z, nz * sizeof(long long));
+            al((void**)&s->mean_z, nz * sizeof(long long)) &&
+            al((void**)&s->nacc, (size_t)Poisson::NSLOT * 2 * NACC * sizeof(float));
+  if (ok && cudaMallocHost((void**)&s->hacc, (size_t)Poisson::NSLOT * 2 * NACC * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    s->hacc = nullptr;
+    ok = false;
+  }
   if (!ok) {
     spectral_free(h);
     h->err = "spectral Poisson allocation failed";
@@ -948,22 +962,43 @@ SpecArgs args_of(const SpectralPlan* s) {
   return a;
 }
 
-// Norm slot i: dsum[1 + 2 i] (residual^2), dsum[2 + 2 i] (source^2), in
-// fixed-point units squared.
-double* norm_slot(lbm_t* h, int slot) { return h->ps.dsum + 1 + 2 * slot; }
+// Norm slot i: 2 NACC partial sums (residual^2, then source^2, in
+// fixed-point units squared).
+float* norm_slot(lbm_t* h, int slot) { return h->spec->nacc + (size_t)slot * 2 * NACC; }
+
+cudaError_t clear_slot(lbm_t* h, int slot) {
+  return cudaMemsetAsync(norm_slot(h, slot), 0, 2 * NACC * sizeof(float), h->st);
+}
+
+// Copies norm slots 0..n-1 to the host and waits.
+cudaError_t read_slots(lbm_t* h, int n) {
+  cudaError_t e = cudaMemcpyAsync(h->spec->hacc, h->spec->nacc, (size_t)n * 2 * NACC * sizeof(float),
+                                  cudaMemcpyDeviceToHost, h->st);
+  return e == cudaSuccess ? cudaStreamSynchronize(h->st) : e;
+}
+
+// Norms |r|_2, |s - <s>|_2 of a slot read by read_slots.
+void slot_norms(const lbm_t* h, int slot, double* rn, double* sn) {
+  const float* p = h->spec->hacc + (size_t)slot * 2 * NACC;
+  double a = 0.0, b = 0.0;
+  for (int k = 0; k < NACC; ++k) {
+    a += (double)p[k];
+    b += (double)p[NACC + k];
+  }
+  *rn = sqrt(a * 1099511627776.0);
+  *sn = sqrt(b * 1099511627776.0);
+}
 
 // Residual of the current potential (exact, k_res_planes) with its norms in
 // the slot; stores r (for the learned guess) when with_r.
 cudaError_t spec_residual(lbm_t* h, int slot, bool with_r) {
   SpectralPlan* s = h->spec;
   Poisson& P = h->ps;
-  double* out = norm_slot(h, slot);
-  cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), h->st);
+  cudaError_t e = clear_slot(h, slot);
   if (e != cudaSuccess) return e;
-  const unsigned nb = (unsigned)std::min<int64_t>(nblk(h->N / 4, 256), h->grid_cap);
-  k_res_planes<<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, s->mean_z, s->plane_fluid,
-                                      with_r ? s->r : nullptr, out - 1, s->nx, s->ny, s->nz,
-                                      s->lgx, s->lgx + s->lgy);
+  k_res_planes<<<nblk(h->N / 2, 256), 256, 0, h->st>>>(P.psi[P.cur], P.src, s->mean_z, s->plane_fluid,
+                                                     with_r ? s->r : nullptr, norm_slot(h, slot),
+                                                     s->nx, s->ny, s->nz, s->lgx, s->lgx + s->lgy);
   ++h->launches;
   return cudaGetLastError();
 }
@@ -990,12 +1025,13 @@ cudaError_t spec_fwd(lbm_t* h, int slot) {
   SpectralPlan* s = h->spec;
   Poisson& P = h->ps;
   const SpecArgs a = args_of(s);
-  double* out = norm_slot(h, slot);
-  cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), h->st);
+  float* out = norm_slot(h, slot);
+  cudaError_t e = clear_slot(h, slot);
   if (e != cudaSuccess) return e;
   const unsigned gp = (unsigned)((s->nplanes + s->ppc - 1) / s->ppc);
   k_plane_fwd<<<gp, s->ppc << s->lgtp, s->plane_smem, h->st>>>(
-      P.psi[P.cur], P.src, s->mean_z, s->plane_fluid, s->planes, s->nplanes, s->spec, out, a);
+      P.psi[P.cur], P.src, s->mean_z, s->plane_fluid, s->nplanes == s->nz ? nullptr : s->planes,
+      s->nplanes, s->spec, out, a);
   ++h->launches;
   return cudaGetLastError();
 }
@@ -1013,8 +1049,8 @@ cudaError_t spec_zinv(lbm_t* h) {
     k_zsolve<<<g, 128, s->zsmem, h->st>>>(s->spec, s->runs, a);
   }
   const unsigned gp = (unsigned)((s->nplanes + s->ppc - 1) / s->ppc);
-  k_plane_inv<<<gp, s->ppc << s->lgtp, s->plane_smem, h->st>>>(s->spec, s->planes, s->nplanes,
-                                                                P.psi[P.cur], a);
+  k_plane_inv<<<gp, s->ppc << s->lgtp, s->plane_smem, h->st>>>(
+      s->spec, s->nplanes == s->nz ? nullptr : s->planes, s->nplanes, P.psi[P.cur], a);
   h->launches += 2;
   return cudaGetLastError();
 }
@@ -1028,7 +1064,6 @@ cudaError_t spec_apply(lbm_t* h, int slot) {
 
 lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* rel_res) {
   SpectralPlan* s = h->spec;
-  Poisson& P = h->ps;
   if (!s->runs_fit) {
     h->err = "spectral Poisson solver: fluid run along z too long for shared memory";
     return LBM_EINVAL;
@@ -1041,10 +1076,8 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
   bool known = false;  // rn, sn hold the norms of the current potential
   if (nn_active(h)) {
     LBM_CUDA_TRY(h, spec_residual(h, 0, true));
-    LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
-    rn = sqrt(P.hsum[1]);
-    sn = sqrt(P.hsum[2]);
+    LBM_CUDA_TRY(h, read_slots(h, 1));
+    slot_norms(h, 0, &rn, &sn);
     known = true;
     if (!conv_of(rn, sn)) {
       bool applied = false;
@@ -1055,18 +1088,16 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
       if (applied) {
         const double rn_old = rn;
         LBM_CUDA_TRY(h, spec_residual(h, 0, false));
-        LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-        LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
-        rn = sqrt(P.hsum[1]);
+        LBM_CUDA_TRY(h, read_slots(h, 1));
+        slot_norms(h, 0, &rn, &sn);
         if (rn < rn_old) {
           nn_record(h, rn / rn_old);
         } else {
           st = nn_revert(h, dpsi);
           if (st != LBM_OK) return st;
           LBM_CUDA_TRY(h, spec_residual(h, 0, false));
-          LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-          LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
-          rn = sqrt(P.hsum[1]);
+          LBM_CUDA_TRY(h, read_slots(h, 1));
+          slot_norms(h, 0, &rn, &sn);
         }
       }
     }
@@ -1079,35 +1110,30 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
     const int k = std::max(1, std::min(std::min(s->last_iters, maxit), Poisson::NSLOT - 1));
     for (int i = 0; i < k; ++i) LBM_CUDA_TRY(h, spec_apply(h, i));
     LBM_CUDA_TRY(h, spec_residual(h, k, false));
-    LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, (3 + 2 * k) * sizeof(double),
-                                    cudaMemcpyDeviceToHost, h->st));
-    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    LBM_CUDA_TRY(h, read_slots(h, k + 1));
     int need = k;
-    for (int i = 0; i <= k; ++i)
-      if (conv_of(sqrt(P.hsum[1 + 2 * i]), sqrt(P.hsum[2 + 2 * i]))) {
+    for (int i = 0; i <= k; ++i) {
+      slot_norms(h, i, &rn, &sn);
+      if (conv_of(rn, sn)) {
         need = i;
         break;
       }
-    rn = sqrt(P.hsum[1 + 2 * k]);
-    sn = sqrt(P.hsum[2 + 2 * k]);
+    }
+    slot_norms(h, k, &rn, &sn);
     known = true;
     it = k;
     s->last_iters = std::max(1, need);
   }
   if (!known) {
     LBM_CUDA_TRY(h, spec_residual(h, 0, false));
-    LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
-    rn = sqrt(P.hsum[1]);
-    sn = sqrt(P.hsum[2]);
+    LBM_CUDA_TRY(h, read_slots(h, 1));
+    slot_norms(h, 0, &rn, &sn);
   }
   while (!conv_of(rn, sn) && it < maxit) {
     LBM_CUDA_TRY(h, spec_apply(h, 0));
     LBM_CUDA_TRY(h, spec_residual(h, 1, false));
-    LBM_CUDA_TRY(h, cudaMemcpyAsync(P.hsum, P.dsum, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
-    rn = sqrt(P.hsum[3]);
-    sn = sqrt(P.hsum[4]);
+    LBM_CUDA_TRY(h, read_slots(h, 2));
+    slot_norms(h, 1, &rn, &sn);
     if (!isfinite(rn) || !isfinite(sn)) {
       h->err = "Poisson residual is not finite";
       return LBM_EUNSTABLE;
@@ -1151,11 +1177,17 @@ struct GraphStatus {
 
 // Convergence test of the last residual (one thread): sets the loop
 // condition of the enclosing conditional node.
-__global__ void k_graph_check(const double* __restrict__ dsum, GraphStatus* st, double tol,
+__global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, double tol,
                               double floor2, int maxit, int first,
                               cudaGraphConditionalHandle cond) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double rn2 = dsum[1], sn2 = dsum[2];
+  double rn2 = 0.0, sn2 = 0.0;
+  for (int k = 0; k < NACC; ++k) {
+    rn2 += (double)acc[k];
+    sn2 += (double)acc[NACC + k];
+  }
+  rn2 *= 1099511627776.0;
+  sn2 *= 1099511627776.0;
   const bool conv = rn2 <= tol * tol * sn2 || rn2 <= floor2;
   if (first) {
     st->iters = 0;
@@ -1205,7 +1237,7 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
   // the first application's forward kernel: residual norms and spectrum
   if (e == cudaSuccess) e = spec_fwd(h, 0);
   if (e == cudaSuccess) {
-    k_graph_check<<<1, 32, 0, h->st>>>(P.dsum, gs, tol, floor2, maxit, 1, cond);
+    k_graph_check<<<1, 32, 0, h->st>>>(norm_slot(h, 0), gs, tol, floor2, maxit, 1, cond);
     ++h->launches;
     e = cudaGetLastError();
   }
@@ -1241,7 +1273,7 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
       cudaError_t eb = spec_zinv(h);
       if (eb == cudaSuccess) eb = spec_fwd(h, 0);
       if (eb == cudaSuccess) {
-        k_graph_check<<<1, 32, 0, h->st>>>(P.dsum, gs, tol, floor2, maxit, 0, cond);
+        k_graph_check<<<1, 32, 0, h->st>>>(norm_slot(h, 0), gs, tol, floor2, maxit, 0, cond);
         ++h->launches;
         eb = cudaGetLastError();
       }
