@@ -107,7 +107,7 @@ __device__ __forceinline__ void line_sync() {
     __syncwarp();
 }
 
-// FFT of length L = 2^lg (8 <= L <= 256) held by T = L / 8 threads, thread t
+// FFT of length L = 2^LG (8 <= L <= 256) held by T = L / 8 threads, thread t
 // holding elements t + u T (u = 0..7) before and after.  Stockham autosort
 // stages (the formulation of Stockham's self-sorting FFT used for GPUs by
 // Govindaraju et al., SC 2008): the stage of radix R after earlier radices
@@ -118,18 +118,20 @@ __device__ __forceinline__ void line_sync() {
 // thread; the last stage's outputs fall on j + q L/R = t + (s + q 8/R) T,
 // the starting distribution, so they stay in registers.  tw[m] =
 // exp(-2 pi i m / L), m < L (the inverse conjugates it).  CTA: the T
-// threads are in different warps (barrier), else in one warp.
-template <bool CTA, class Line>
-__device__ __forceinline__ void fft_regs(float2 (&v)[8], int t, int lg, Line line,
+// threads are in different warps (barrier), else in one warp.  LG is a
+// template parameter so that every stage's radix, shifts and offsets are
+// constants.
+template <int LG, bool CTA, class Line>
+__device__ __forceinline__ void fft_regs(float2 (&v)[8], int t, Line line,
                                          const float2* __restrict__ tw, float sign) {
-  const int T = 1 << (lg - 3);
-  int lns = 0;  // log2 Ns
-  int rem = lg;
-  while (true) {
-    const int lr = rem >= 3 ? 3 : rem;
-    rem -= lr;
+  constexpr int T = 1 << (LG - 3);
+  constexpr int NST = (LG + 2) / 3;
+#pragma unroll
+  for (int st = 0; st < NST; ++st) {
+    const int lns = 3 * st;                              // log2 Ns
+    const int lr = LG - lns >= 3 ? 3 : LG - lns;         // log2 R
     const int Ns = 1 << lns;
-    const int tws = lg - lns - lr;  // log2(L / (Ns R))
+    const int tws = LG - lns - lr;                       // log2(L / (Ns R))
     if (lr == 3) {
       if (lns > 0) {
         const int k = t & (Ns - 1);
@@ -167,7 +169,7 @@ __device__ __forceinline__ void fft_regs(float2 (&v)[8], int t, int lg, Line lin
         dft2(v[s], v[s + 4]);
       }
     }
-    if (rem == 0) break;
+    if (st == NST - 1) break;
     // slot u = s + G q holds output q of butterfly j = t + s T (G = 8 / R)
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -179,9 +181,19 @@ __device__ __forceinline__ void fft_regs(float2 (&v)[8], int t, int lg, Line lin
 #pragma unroll
     for (int u = 0; u < 8; ++u) v[u] = line[t + u * T];
     line_sync<CTA>();
-    lns += lr;
   }
 }
+
+// Calls F<LG>(args...) for the runtime lg in [3, 8].
+#define LBM_LG_DISPATCH(lg, F, ...) \
+  switch (lg) {                     \
+    case 3: F<3>(__VA_ARGS__); break; \
+    case 4: F<4>(__VA_ARGS__); break; \
+    case 5: F<5>(__VA_ARGS__); break; \
+    case 6: F<6>(__VA_ARGS__); break; \
+    case 7: F<7>(__VA_ARGS__); break; \
+    default: F<8>(__VA_ARGS__); break; \
+  }
 
 // Squared norms are accumulated by CTA b into partial NACC slot b mod NACC:
 // one FP32 atomic per CTA and quantity (FP64 atomics are slow on this GPU),
@@ -240,22 +252,38 @@ __device__ __forceinline__ void loadg(const int64_t* __restrict__ p, int64_t (&v
   }
 }
 
+// Plane data for the residual: offsets of the planes z +- 1, whether their
+// faces are open (fluid planes), and the plane's source mean.
+struct PlaneNbr {
+  int64_t dup, ddn;
+  bool up, dn;
+  long long mean;
+};
+
+__device__ __forceinline__ PlaneNbr plane_nbr(const unsigned char* __restrict__ plane_fluid,
+                                              const long long* __restrict__ mean_z, int z,
+                                              int nxy, int nz) {
+  PlaneNbr g;
+  const int zp = (z == nz - 1) ? 0 : z + 1, zm = (z == 0) ? nz - 1 : z - 1;
+  g.dup = (int64_t)(zp - z) * nxy;
+  g.ddn = (int64_t)(zm - z) * nxy;
+  g.up = nz > 1 && zp != z && __ldg(plane_fluid + zp);
+  g.dn = nz > 1 && zm != z && __ldg(plane_fluid + zm);
+  g.mean = __ldg(mean_z + z);
+  return g;
+}
+
 // Exact residual r = s - <s> - A psi at the G (2 or 4) consecutive nodes
-// x0..x0+G-1 (x0 a multiple of G) of row y of plane z, i0 the index of
-// (x0, y, z): 16-byte loads of the row, the rows y +- 1 and the planes
-// z +- 1, two scalar loads for the x neighbours at the ends.  Every load,
-// the flags of the planes z +- 1 (open faces) and the plane's source mean
-// included, is issued before any is used: one memory round trip.  r in
-// fixed-point units (FP32); returns |r|^2 and |s - <s>|^2 through rr, ss.
+// x0..x0+G-1 (x0 a multiple of G) of row y of a plane, i0 the index of
+// (x0, y): 16-byte loads of the row, the rows y +- 1 and the planes z +- 1
+// (loaded whether or not their faces are open, so that no load waits on
+// the plane data), two scalar loads for the x neighbours at the ends.  r in
+// fixed-point units (FP32); rr, ss accumulate |r|^2 and |s - <s>|^2.
 template <int G>
 __device__ __forceinline__ void residual_g(const int64_t* __restrict__ psi,
-                                           const int64_t* __restrict__ src,
-                                           const unsigned char* __restrict__ plane_fluid,
-                                           const long long* __restrict__ mean_z, int64_t i0,
-                                           int x0, int y, int z, int nx, int ny, int nz,
+                                           const int64_t* __restrict__ src, int64_t i0, int x0,
+                                           int y, int nx, int ny, const PlaneNbr& g,
                                            float (&r)[G], float& rr, float& ss) {
-  const int64_t nxy = (int64_t)nx * ny;
-  const int zp = (z == nz - 1) ? 0 : z + 1, zm = (z == 0) ? nz - 1 : z - 1;
   int64_t c[G], yp[G], ym[G], up[G], dn[G], sv[G];
   loadg<G>(psi + i0, c);
   const int64_t row = i0 - x0;
@@ -263,19 +291,16 @@ __device__ __forceinline__ void residual_g(const int64_t* __restrict__ psi,
   const int64_t xr = __ldg(psi + row + ((x0 + G) & (nx - 1)));
   loadg<G>(psi + (y == ny - 1 ? i0 - (int64_t)(ny - 1) * nx : i0 + nx), yp);
   loadg<G>(psi + (y == 0 ? i0 + (int64_t)(ny - 1) * nx : i0 - nx), ym);
-  loadg<G>(psi + i0 + (int64_t)(zp - z) * nxy, up);
-  loadg<G>(psi + i0 + (int64_t)(zm - z) * nxy, dn);
+  loadg<G>(psi + i0 + g.dup, up);
+  loadg<G>(psi + i0 + g.ddn, dn);
   loadg<G>(src + i0, sv);
-  const bool fup = nz > 1 && zp != z && __ldg(plane_fluid + zp);
-  const bool fdn = nz > 1 && zm != z && __ldg(plane_fluid + zm);
-  const long long mean = __ldg(mean_z + z);
 #pragma unroll
   for (int j = 0; j < G; ++j) {
     const int64_t left = j == 0 ? xl : c[j - 1], right = j == G - 1 ? xr : c[j + 1];
     int64_t Ap = 4 * c[j] - left - right - yp[j] - ym[j];
-    if (fup) Ap += c[j] - up[j];
-    if (fdn) Ap += c[j] - dn[j];
-    const int64_t sfx = sv[j] - mean;
+    if (g.up) Ap += c[j] - up[j];
+    if (g.dn) Ap += c[j] - dn[j];
+    const int64_t sfx = sv[j] - g.mean;
     const float rf = i64_to_f32(sfx - Ap);
     const float sf = i64_to_f32(sfx);
     rr += rf * rf;
@@ -291,14 +316,161 @@ __host__ __device__ constexpr int plane_smem_words(int nx, int ny) {
   return (nx / 2 + 1) * ny + (nx * ny / 16) * 9;
 }
 
+// Phases of the plane kernels, templated on the transform's log2 length.
+// S: the plane's half spectrum (row stride rs = nx/2 + 1); scr: the padded
+// lines (one per row pair along x, one per packed column along y).
+
+// x forward: rows 2q, 2q + 1 (residual rows staged in the pair's own line,
+// row 2q at float offset 0, row 2q + 1 at nx) -> one complex FFT -> half
+// spectra R_2q(k) = (C(k) + conj C(-k)) / 2, R_2q+1(k) = (C(k) - conj C(-k)) / 2i.
+template <int LGX>
+__device__ __forceinline__ void xphase_fwd(float2* S, float2* scr, int w, bool valid,
+                                           const float2* __restrict__ twx) {
+  constexpr int NX = 1 << LGX, TX = NX >> 3, H = NX >> 1, RS = H + 1;
+  const int q = w >> (LGX - 3), t = w & (TX - 1);
+  const PadLine line{scr + q * padded_len(NX)};
+  const int y0 = 2 * q;
+  float2 v[8];
+  {
+    const float* rb = reinterpret_cast<const float*>(scr + q * padded_len(NX));
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int x = t + u * TX;
+      v[u] = valid ? make_float2(rb[x], rb[NX + x]) : make_float2(0.f, 0.f);
+    }
+    __syncwarp();
+  }
+  fft_regs<LGX, false>(v, t, line, twx, -1.f);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) line[t + u * TX] = v[u];
+  __syncwarp();
+#pragma unroll
+  for (int u = 0; u < 5; ++u) {
+    const int k = t + u * TX;  // k <= H: u < 4, or u == 4 and t == 0
+    if (u < 4 || t == 0) {
+      const float2 c = v[u], cm = line[(NX - k) & (NX - 1)];
+      S[y0 * RS + k] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
+      S[(y0 + 1) * RS + k] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
+    }
+  }
+}
+
+// y forward: columns kx = 1..H-1, and kx = 0, H packed as one complex column
+// (both real), unpacked after the FFT: F0 = (Z + conj Z(-k)) / 2,
+// FH = (Z - conj Z(-k)) / 2i.
+template <int LGY>
+__device__ __forceinline__ void yphase_fwd(float2* S, float2* scr, int w, int H,
+                                           const float2* __restrict__ twy) {
+  constexpr int NY = 1 << LGY, TY = NY >> 3;
+  const int rs = H + 1;
+  const int c = w >> (LGY - 3), t = w & (TY - 1);
+  const PadLine line{scr + c * padded_len(NY)};
+  float2 v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int y = t + u * TY;
+    v[u] = c == 0 ? make_float2(S[y * rs].x, S[y * rs + H].x) : S[y * rs + c];
+  }
+  fft_regs<LGY, false>(v, t, line, twy, -1.f);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) line[t + u * TY] = v[u];
+  __syncwarp();
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int ky = t + u * TY;
+    if (c == 0) {
+      const float2 zk = v[u], zm = line[(NY - ky) & (NY - 1)];
+      S[ky * rs] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      S[ky * rs + H] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    } else {
+      S[ky * rs + c] = v[u];
+    }
+  }
+}
+
+// y inverse: column 0 carries kx = 0 and H packed as F0 + i FH, whose
+// inverse is f0 + i fH with both real.
+template <int LGY>
+__device__ __forceinline__ void yphase_inv(float2* S, float2* scr, int w, int H,
+                                           const float2* __restrict__ twy) {
+  constexpr int NY = 1 << LGY, TY = NY >> 3;
+  const int rs = H + 1;
+  const int c = w >> (LGY - 3), t = w & (TY - 1);
+  const PadLine line{scr + c * padded_len(NY)};
+  float2 v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int y = t + u * TY;
+    if (c == 0) {
+      const float2 f0 = S[y * rs], fh = S[y * rs + H];
+      v[u] = make_float2(f0.x - fh.y, f0.y + fh.x);
+    } else {
+      v[u] = S[y * rs + c];
+    }
+  }
+  fft_regs<LGY, false>(v, t, line, twy, 1.f);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int y = t + u * TY;
+    if (c == 0) {
+      S[y * rs] = make_float2(v[u].x, 0.f);
+      S[y * rs + H] = make_float2(v[u].y, 0.f);
+    } else {
+      S[y * rs + c] = v[u];
+    }
+  }
+}
+
+// x inverse: rows 2q, 2q+1 as C(k) = E_2q(k) + i E_2q+1(k) over the full k
+// range (E(k) = conj E(nx - k) above H); the inverse gives e_2q + i e_2q+1;
+// psi += round(e / (nx ny)) in fixed point (rows of the plane at psi_z).
+template <int LGX>
+__device__ __forceinline__ void xphase_inv(const float2* S, float2* scr, int w, int ny,
+                                           bool valid, int64_t* __restrict__ psi_z,
+                                           const float2* __restrict__ twx) {
+  constexpr int NX = 1 << LGX, TX = NX >> 3, H = NX >> 1, RS = H + 1;
+  const int q = w >> (LGX - 3), t = w & (TX - 1);
+  const PadLine line{scr + q * padded_len(NX)};
+  const int y0 = 2 * q;
+  float2 v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int k = t + u * TX;
+    float2 e0, e1;
+    if (k <= H) {
+      e0 = S[y0 * RS + k];
+      e1 = S[(y0 + 1) * RS + k];
+    } else {
+      e0 = S[y0 * RS + NX - k];
+      e1 = S[(y0 + 1) * RS + NX - k];
+      e0.y = -e0.y;
+      e1.y = -e1.y;
+    }
+    v[u] = make_float2(e0.x - e1.y, e0.y + e1.x);
+  }
+  fft_regs<LGX, false>(v, t, line, twx, 1.f);
+  if (valid) {
+    const float scale = PSI_SCALE_F / (float)(NX * ny);
+    int64_t* row0 = psi_z + (int64_t)y0 * NX;
+    int64_t* row1 = row0 + NX;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int x = t + u * TX;
+      row0[x] += f32_to_i64_rn(v[u].x * scale);
+      row1[x] += f32_to_i64_rn(v[u].y * scale);
+    }
+  }
+}
+
 // Forward plane kernel.  Thread w of a plane's TP = nx ny / 16 threads is,
 // along x, thread t = w mod (nx/8) of row pair q = w div (nx/8) (rows 2q and
 // 2q + 1 packed as C = r_2q + i r_2q+1), and along y thread w mod (ny/8) of
 // column c = w div (ny/8) (c = 0 carries the real columns kx = 0 and kx = H
 // packed the same way).  The residual r = s - <s> - A psi is computed
 // exactly in int64 (two nodes per thread and step); its squared norms (and
-// the source's) are added to the norm slot given.  planes: the fluid planes' indices, or
-// NULL when every plane is fluid (plane index = CTA slot index).
+// the source's) are added to the norm slot given.  planes: the fluid
+// planes' indices, or NULL when every plane is fluid (plane index = CTA slot
+// index).
 __global__ void __launch_bounds__(1024, 1) k_plane_fwd(
     const int64_t* __restrict__ psi, const int64_t* __restrict__ src,
     const long long* __restrict__ mean_z, const unsigned char* __restrict__ plane_fluid,
@@ -306,7 +478,7 @@ __global__ void __launch_bounds__(1024, 1) k_plane_fwd(
     SpecArgs a) {
   extern __shared__ __align__(16) float2 sm[];
   __shared__ float red_r[32], red_s[32];
-  const int nx = a.nx, ny = a.ny, H = a.H, lgx = a.lgx, lgy = a.lgy;
+  const int nx = a.nx, ny = a.ny;
   const int tp = 1 << a.lgtp;
   const int slot = threadIdx.x >> a.lgtp, w = threadIdx.x & (tp - 1);
   const int pi = blockIdx.x * (blockDim.x >> a.lgtp) + slot;
@@ -314,89 +486,32 @@ __global__ void __launch_bounds__(1024, 1) k_plane_fwd(
   const int z = !valid ? 0 : (planes ? planes[pi] : pi);
   float2* S = sm + (size_t)slot * plane_smem_words(nx, ny);
   float2* scr = S + a.mxy;
-  const int rs = H + 1;  // row stride of S
-  float2 v[8];
   float rr = 0.f, ss = 0.f;
 
-  // ---- residual of the plane, two consecutive x per thread and step,
-  // into the line of its row pair (row 2q at float offset 0, row 2q + 1 at
-  // nx); a transform later overwrites only its own line, after reading it
+  // residual of the plane, two consecutive x per thread and step, into the
+  // line of its row pair; a transform later overwrites only its own line,
+  // after reading it
   if (valid) {
-    const int gpr = nx >> 1;
+    const PlaneNbr g = plane_nbr(plane_fluid, mean_z, z, nx * ny, a.nz);
+    const int64_t* psi_z = psi + (int64_t)z * nx * ny;
+    const int64_t* src_z = src + (int64_t)z * nx * ny;
+    const int lgp = a.lgx - 1;  // pairs per row
     // nx ny / 2 pairs over nx ny / 16 threads: eight per thread
 #pragma unroll 2
     for (int j = 0; j < 8; ++j) {
       const int gi = w + j * tp;
-      const int y = gi / gpr, x0 = (gi - y * gpr) << 1;
+      const int y = gi >> lgp, x0 = (gi & ((1 << lgp) - 1)) << 1;
       float r2[2];
-      residual_g<2>(psi, src, plane_fluid, mean_z, ((int64_t)z * ny + y) * nx + x0, x0, y, z, nx,
-                    ny, a.nz, r2, rr, ss);
+      residual_g<2>(psi_z, src_z, y * nx + x0, x0, y, nx, ny, g, r2, rr, ss);
       float* rb = reinterpret_cast<float*>(scr + (y >> 1) * padded_len(nx)) + (y & 1) * nx + x0;
       rb[0] = r2[0] * PSI_INV_SCALE_F;
       rb[1] = r2[1] * PSI_INV_SCALE_F;
     }
   }
   __syncthreads();
-
-  // ---- x: rows 2q, 2q + 1 -> one complex FFT -> half spectra
-  {
-    const int Tx = nx >> 3;
-    const int q = w >> (lgx - 3), t = w & (Tx - 1);
-    const PadLine line{scr + q * padded_len(nx)};
-    const int y0 = 2 * q;
-    {
-      const float* rb = reinterpret_cast<const float*>(scr + q * padded_len(nx));
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int x = t + u * Tx;
-        v[u] = valid ? make_float2(rb[x], rb[nx + x]) : make_float2(0.f, 0.f);
-      }
-      __syncwarp();
-    }
-    fft_regs<false>(v, t, lgx, line, a.twx, -1.f);
-    // R_2q(k) = (C(k) + conj C(-k)) / 2, R_2q+1(k) = (C(k) - conj C(-k)) / 2i
-#pragma unroll
-    for (int u = 0; u < 8; ++u) line[t + u * Tx] = v[u];
-    __syncwarp();
-#pragma unroll
-    for (int u = 0; u < 5; ++u) {
-      const int k = t + u * Tx;  // k <= H: u < 4, or u == 4 and t == 0
-      if (u < 4 || t == 0) {
-        const float2 c = v[u], cm = line[(nx - k) & (nx - 1)];
-        S[y0 * rs + k] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
-        S[(y0 + 1) * rs + k] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
-      }
-    }
-  }
+  LBM_LG_DISPATCH(a.lgx, xphase_fwd, S, scr, w, valid, a.twx)
   __syncthreads();
-
-  // ---- y: columns kx = 1..H-1, and kx = 0, H packed as one complex column
-  {
-    const int Ty = ny >> 3;
-    const int c = w >> (lgy - 3), t = w & (Ty - 1);
-    const PadLine line{scr + c * padded_len(ny)};
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int y = t + u * Ty;
-      v[u] = c == 0 ? make_float2(S[y * rs].x, S[y * rs + H].x) : S[y * rs + c];
-    }
-    fft_regs<false>(v, t, lgy, line, a.twy, -1.f);
-    // unpack the two real columns: F0 = (Z + conj Z(-k)) / 2, FH = (Z - conj Z(-k)) / 2i
-#pragma unroll
-    for (int u = 0; u < 8; ++u) line[t + u * Ty] = v[u];
-    __syncwarp();
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int ky = t + u * Ty;
-      if (c == 0) {
-        const float2 zk = v[u], zm = line[(ny - ky) & (ny - 1)];
-        S[ky * rs] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-        S[ky * rs + H] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-      } else {
-        S[ky * rs + c] = v[u];
-      }
-    }
-  }
+  LBM_LG_DISPATCH(a.lgy, yphase_fwd, S, scr, w, a.H, a.twy)
   __syncthreads();
   if (valid) {
     float4* dst = reinterpret_cast<float4*>(spec + (int64_t)z * a.mxy);
@@ -408,20 +523,17 @@ __global__ void __launch_bounds__(1024, 1) k_plane_fwd(
       if (k < 4 || i < (a.mxy >> 1)) dst[i] = s4[i];
     }
   }
-
   add_norms(norms, rr, ss, red_r, red_s);
 }
 
-// Inverse plane kernel: y inverse (column 0 carries kx = 0 and H packed as
-// F0 + i FH, whose inverse is f0 + i fH with both real), then rows 2q, 2q+1
-// as C(k) = E_2q(k) + i E_2q+1(k) over the full k range (E(k) = conj E(nx-k)
-// above H), inverse along x, psi += round(e / (nx ny)) in fixed point.
+// Inverse plane kernel: load the plane's half spectrum, y inverse, x inverse
+// with the update of psi.
 __global__ void __launch_bounds__(1024, 1) k_plane_inv(const float2* __restrict__ spec,
                                                       const int* __restrict__ planes,
                                                       int nplanes, int64_t* __restrict__ psi,
                                                       SpecArgs a) {
   extern __shared__ __align__(16) float2 sm[];
-  const int nx = a.nx, ny = a.ny, H = a.H, lgx = a.lgx, lgy = a.lgy;
+  const int nx = a.nx, ny = a.ny;
   const int tp = 1 << a.lgtp;
   const int slot = threadIdx.x >> a.lgtp, w = threadIdx.x & (tp - 1);
   const int pi = blockIdx.x * (blockDim.x >> a.lgtp) + slot;
@@ -429,8 +541,6 @@ __global__ void __launch_bounds__(1024, 1) k_plane_inv(const float2* __restrict_
   const int z = !valid ? 0 : (planes ? planes[pi] : pi);
   float2* S = sm + (size_t)slot * plane_smem_words(nx, ny);
   float2* scr = S + a.mxy;
-  const int rs = H + 1;
-  float2 v[8];
   {
     float4* s4 = reinterpret_cast<float4*>(S);
     const float4* src4 = reinterpret_cast<const float4*>(spec + (int64_t)z * a.mxy);
@@ -447,66 +557,9 @@ __global__ void __launch_bounds__(1024, 1) k_plane_inv(const float2* __restrict_
     }
   }
   __syncthreads();
-  {
-    const int Ty = ny >> 3;
-    const int c = w >> (lgy - 3), t = w & (Ty - 1);
-    const PadLine line{scr + c * padded_len(ny)};
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int y = t + u * Ty;
-      if (c == 0) {
-        const float2 f0 = S[y * rs], fh = S[y * rs + H];
-        v[u] = make_float2(f0.x - fh.y, f0.y + fh.x);
-      } else {
-        v[u] = S[y * rs + c];
-      }
-    }
-    fft_regs<false>(v, t, lgy, line, a.twy, 1.f);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int y = t + u * Ty;
-      if (c == 0) {
-        S[y * rs] = make_float2(v[u].x, 0.f);
-        S[y * rs + H] = make_float2(v[u].y, 0.f);
-      } else {
-        S[y * rs + c] = v[u];
-      }
-    }
-  }
+  LBM_LG_DISPATCH(a.lgy, yphase_inv, S, scr, w, a.H, a.twy)
   __syncthreads();
-  {
-    const int Tx = nx >> 3;
-    const int q = w >> (lgx - 3), t = w & (Tx - 1);
-    const PadLine line{scr + q * padded_len(nx)};
-    const int y0 = 2 * q;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int k = t + u * Tx;
-      float2 e0, e1;
-      if (k <= H) {
-        e0 = S[y0 * rs + k];
-        e1 = S[(y0 + 1) * rs + k];
-      } else {
-        e0 = S[y0 * rs + nx - k];
-        e1 = S[(y0 + 1) * rs + nx - k];
-        e0.y = -e0.y;
-        e1.y = -e1.y;
-      }
-      v[u] = make_float2(e0.x - e1.y, e0.y + e1.x);
-    }
-    fft_regs<false>(v, t, lgx, line, a.twx, 1.f);
-    if (valid) {
-      const float scale = PSI_SCALE_F / (float)(nx * ny);
-      int64_t* row0 = psi + ((int64_t)z * ny + y0) * nx;
-      int64_t* row1 = row0 + nx;
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int x = t + u * Tx;
-        row0[x] += f32_to_i64_rn(v[u].x * scale);
-        row1[x] += f32_to_i64_rn(v[u].y * scale);
-      }
-    }
-  }
+  LBM_LG_DISPATCH(a.lgx, xphase_inv, S, scr, w, ny, valid, psi + (int64_t)z * nx * ny, a.twx)
 }
 
 // Periodic z axis of power-of-two length (8..256): the z operator is
@@ -516,9 +569,10 @@ __global__ void __launch_bounds__(1024, 1) k_plane_inv(const float2* __restrict_
 // of one plane; the pencil of mode p exchanges through column p of a
 // [z][33] shared array.  Forward FFT, division by lambda (the free mean,
 // mode (0,0,0), set to 0), inverse FFT, all in registers between exchanges.
-__global__ void __launch_bounds__(1024, 1) k_zfft(float2* __restrict__ spec, SpecArgs a) {
+template <int LGZ>
+__global__ void __launch_bounds__(4 << LGZ) k_zfft(float2* __restrict__ spec, SpecArgs a) {
   extern __shared__ __align__(16) float2 zb[];
-  const int lgz = a.lgz, T = 1 << (lgz - 3);
+  constexpr int L = 1 << LGZ, T = L >> 3;
   const int p = threadIdx.x & 31, t = threadIdx.x >> 5;
   const int m = blockIdx.x * 32 + p;
   const bool ok = m < a.mxy;
@@ -528,17 +582,17 @@ __global__ void __launch_bounds__(1024, 1) k_zfft(float2* __restrict__ spec, Spe
   for (int u = 0; u < 8; ++u)
     v[u] = ok ? spec[(int64_t)(t + u * T) * mxy + m] : make_float2(0.f, 0.f);
   const StrideLine line{zb + p, 33};
-  fft_regs<true>(v, t, lgz, line, a.twz, -1.f);
+  fft_regs<LGZ, true>(v, t, line, a.twz, -1.f);
   const int ky = ok ? m / (a.H + 1) : 0, kx = ok ? m - ky * (a.H + 1) : 0;
   const float lxy = a.lamx[kx] + a.lamy[ky];
-  const float invL = 1.0f / (float)(1 << lgz);
+  constexpr float invL = 1.0f / (float)L;
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int kz = t + u * T;
     const float sc = (m == 0 && kz == 0) ? 0.f : invL / (lxy + a.lamz[kz]);
     v[u] = make_float2(v[u].x * sc, v[u].y * sc);
   }
-  fft_regs<true>(v, t, lgz, line, a.twz, 1.f);
+  fft_regs<LGZ, true>(v, t, line, a.twz, 1.f);
   if (ok) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) spec[(int64_t)(t + u * T) * mxy + m] = v[u];
@@ -733,8 +787,9 @@ __global__ void __launch_bounds__(256, 4) k_res_planes(
     const int y = k >> lgr, x0 = (k & ((1 << lgr) - 1)) << 1;
     const int64_t i0 = ((int64_t)z * ny + y) * nx + x0;
     const bool fluid = __ldg(plane_fluid + z);
+    const PlaneNbr g = plane_nbr(plane_fluid, mean_z, z, nx * ny, nz);
     float r2[2], a = 0.f, b = 0.f;
-    residual_g<2>(psi, src, plane_fluid, mean_z, i0, x0, y, z, nx, ny, nz, r2, a, b);
+    residual_g<2>(psi, src, i0, x0, y, nx, ny, g, r2, a, b);
     if (fluid) {
       rr = a;
       ss = b;
@@ -770,6 +825,7 @@ struct SpectralPlan {
   size_t zsmem = 0;                // shared memory of the z solve
   int lgz = -1;                    // log2(nz) when the z axis is one periodic run
   int last_iters = 2;              // applications of the previous solve
+  int graph_k = 0;                 // applications baked into the step graphs
   bool runs_fit = true;            // z solve fits in shared memory
   float* r = nullptr;              // N (residual for the learned guess)
   long long* psum = nullptr;       // nz
@@ -915,7 +971,18 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
     s->lgz = lgz;
     const size_t zf = (size_t)nz * 33 * sizeof(float2);
     if (zf > 48 * 1024)
-      LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_zfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zf));
+    {
+      cudaError_t e = cudaSuccess;
+      switch (lgz) {
+        case 3: e = cudaFuncSetAttribute(k_zfft<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zf); break;
+        case 4: e = cudaFuncSetAttribute(k_zfft<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zf); break;
+        case 5: e = cudaFuncSetAttribute(k_zfft<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zf); break;
+        case 6: e = cudaFuncSetAttribute(k_zfft<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zf); break;
+        case 7: e = cudaFuncSetAttribute(k_zfft<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zf); break;
+        default: e = cudaFuncSetAttribute(k_zfft<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zf); break;
+      }
+      LBM_CUDA_TRY(h, e);
+    }
   }
   int lmax = 0;
   for (const Run& R : runs) lmax = std::max(lmax, R.len);
@@ -1043,7 +1110,16 @@ cudaError_t spec_zinv(lbm_t* h) {
   Poisson& P = h->ps;
   const SpecArgs a = args_of(s);
   if (s->lgz > 0) {
-    k_zfft<<<nblk(s->mxy, 32), 4 * s->nz, (size_t)s->nz * 33 * sizeof(float2), h->st>>>(s->spec, a);
+    const unsigned g = nblk(s->mxy, 32);
+    const size_t zs = (size_t)s->nz * 33 * sizeof(float2);
+    switch (s->lgz) {
+      case 3: k_zfft<3><<<g, 4 * s->nz, zs, h->st>>>(s->spec, a); break;
+      case 4: k_zfft<4><<<g, 4 * s->nz, zs, h->st>>>(s->spec, a); break;
+      case 5: k_zfft<5><<<g, 4 * s->nz, zs, h->st>>>(s->spec, a); break;
+      case 6: k_zfft<6><<<g, 4 * s->nz, zs, h->st>>>(s->spec, a); break;
+      case 7: k_zfft<7><<<g, 4 * s->nz, zs, h->st>>>(s->spec, a); break;
+      default: k_zfft<8><<<g, 4 * s->nz, zs, h->st>>>(s->spec, a); break;
+    }
   } else {
     dim3 g(nblk(s->mxy, ZP), s->nruns);
     k_zsolve<<<g, 128, s->zsmem, h->st>>>(s->spec, s->runs, a);
@@ -1157,10 +1233,11 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
 
 // ---------------------------------------------------------------------------
 // Whole-step CUDA graphs.  One graph per population parity holds a full time
-// step: charge density, run means, the forward kernel of the first
-// application (first residual) and its test, a device-side while loop
-// (conditional graph node) of [z solve, inverse + update, next forward
-// kernel (residual of the update), test], and the fused stream/collide.
+// step: charge density, run means, the number of spectral applications the
+// host path predicts (k), the final residual and its test, a device-side
+// while loop (conditional graph node) of [application, residual, test] for
+// a step that needs more, and the fused stream/collide.  The graphs are
+// rebuilt when the applications a step needs change.
 // Steps are replayed back to back with no host round trip; the test kernel
 // keeps the per-step status on the device.
 // ---------------------------------------------------------------------------
@@ -1168,39 +1245,56 @@ namespace {
 
 struct GraphStatus {
   uint32_t step;       // time step (read by the stream/collide kernel)
-  int iters;           // Poisson iterations of the current step
-  long long total;     // iterations summed over replayed steps
+  int iters;           // Poisson applications of the current step
+  long long total;     // applications summed over replayed steps
   int fails;           // steps whose solve stopped at the iteration cap
-  int pad;
+  int need_max;        // most applications a step needed since the host reset it
   double rel;          // final relative residual of the last step
 };
 
-// Convergence test of the last residual (one thread): sets the loop
-// condition of the enclosing conditional node.
+// Convergence test (one warp).  first: after the k applications queued
+// unconditionally (norm slots 0..k hold the residual before each and after
+// the last); records how many a step needed.  Otherwise after one more
+// application (slot k).  Sets the condition of the enclosing while node.
 __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, double tol,
-                              double floor2, int maxit, int first,
+                              double floor2, int maxit, int k, int first,
                               cudaGraphConditionalHandle cond) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0) return;
+  const int lane = threadIdx.x;
+  // lane i < k + 1 tests slot i
+  bool conv_i = false;
   double rn2 = 0.0, sn2 = 0.0;
-  for (int k = 0; k < NACC; ++k) {
-    rn2 += (double)acc[k];
-    sn2 += (double)acc[NACC + k];
+  if (lane <= k) {
+    const float* a = acc + (size_t)lane * 2 * NACC;
+    for (int j = 0; j < NACC; ++j) {
+      rn2 += (double)a[j];
+      sn2 += (double)a[NACC + j];
+    }
+    rn2 *= 1099511627776.0;
+    sn2 *= 1099511627776.0;
+    conv_i = rn2 <= tol * tol * sn2 || rn2 <= floor2;
   }
-  rn2 *= 1099511627776.0;
-  sn2 *= 1099511627776.0;
-  const bool conv = rn2 <= tol * tol * sn2 || rn2 <= floor2;
+  const unsigned convmask = __ballot_sync(0xffffffffu, conv_i);
+  const double rnk = __shfl_sync(0xffffffffu, rn2, k), snk = __shfl_sync(0xffffffffu, sn2, k);
+  if (lane != 0) return;
+  const bool conv = (convmask >> k) & 1u;
   if (first) {
-    st->iters = 0;
+    st->iters = k;
     st->step += 1;
   } else {
     st->iters += 1;
   }
   const bool more = !conv && st->iters < maxit;
   cudaGraphSetConditional(cond, more ? 1u : 0u);
-  st->rel = sn2 > 0.0 ? sqrt(rn2 / sn2) : 0.0;
+  st->rel = snk > 0.0 ? sqrt(rnk / snk) : 0.0;
+  if (first && convmask) {
+    const int need = max(1, __ffs(convmask) - 1);
+    st->need_max = max(st->need_max, need);
+  }
   if (!more) {
     st->total += st->iters;
     if (!conv) st->fails += 1;
+    if (!(first && convmask)) st->need_max = max(st->need_max, st->iters);
   }
 }
 
@@ -1229,15 +1323,18 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
   LBM_CUDA_TRY(h, cudaGraphConditionalHandleCreate(&cond, G, 0, cudaGraphCondAssignDefault));
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
   const int64_t l0 = h->launches;
-  // part A: source, means, first residual and test
+  // part A: source, means, the predicted number k of applications (each
+  // records the norms of the residual it transforms), the final residual
+  // and the test
+  const int k = h->spec->graph_k;
   LBM_CUDA_TRY(h, cudaStreamBeginCaptureToGraph(h->st, G, nullptr, nullptr, 0, mode));
   cudaError_t e = cudaMemsetAsync(P.dsum, 0, 3 * sizeof(double), h->st);
   if (e == cudaSuccess) e = launch_charge(h);
   if (e == cudaSuccess) e = spec_means(h);
-  // the first application's forward kernel: residual norms and spectrum
-  if (e == cudaSuccess) e = spec_fwd(h, 0);
+  for (int i = 0; i < k && e == cudaSuccess; ++i) e = spec_apply(h, i);
+  if (e == cudaSuccess) e = spec_residual(h, k, false);
   if (e == cudaSuccess) {
-    k_graph_check<<<1, 32, 0, h->st>>>(norm_slot(h, 0), gs, tol, floor2, maxit, 1, cond);
+    k_graph_check<<<1, 32, 0, h->st>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 1, cond);
     ++h->launches;
     e = cudaGetLastError();
   }
@@ -1268,12 +1365,11 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
   if (e == cudaSuccess) {
     e = cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, mode);
     if (e == cudaSuccess) {
-      // finish the application, then the next one's forward kernel: the
-      // residual tested below is that of the updated potential
-      cudaError_t eb = spec_zinv(h);
-      if (eb == cudaSuccess) eb = spec_fwd(h, 0);
+      // one more application and its residual
+      cudaError_t eb = spec_apply(h, 0);
+      if (eb == cudaSuccess) eb = spec_residual(h, k, false);
       if (eb == cudaSuccess) {
-        k_graph_check<<<1, 32, 0, h->st>>>(norm_slot(h, 0), gs, tol, floor2, maxit, 0, cond);
+        k_graph_check<<<1, 32, 0, h->st>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 0, cond);
         ++h->launches;
         eb = cudaGetLastError();
       }
@@ -1333,13 +1429,21 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
       return LBM_ENOMEM;
     }
   }
+  SpectralPlan* sp = h->spec;
+  const int want = std::max(1, std::min(std::min(sp->last_iters, h->cfg.poisson_maxit), Poisson::NSLOT - 1));
+  if (sp->graph_k != want) {
+    spectral_graph_free(h);
+    sp->graph_k = want;
+  }
   for (int k = 0; k < 2; ++k)
     if (!h->step_graph[k]) {
       lbm_status s = build_step_graph(h, k);
       if (s != LBM_OK) return s;
     }
   GraphStatus* hs = reinterpret_cast<GraphStatus*>(h->hstatus);
-  // status before, to count this call's iterations and failures
+  // status before, to count this call's iterations and failures; the need
+  // of this call's steps starts from 0
+  LBM_CUDA_TRY(h, cudaMemsetAsync(&reinterpret_cast<GraphStatus*>(h->gstatus)->need_max, 0, sizeof(int), h->st));
   LBM_CUDA_TRY(h, cudaMemcpyAsync(hs, h->gstatus, sizeof(GraphStatus), cudaMemcpyDeviceToHost, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   const long long total0 = hs->total;
@@ -1352,12 +1456,16 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
   LBM_CUDA_TRY(h, cudaMemcpyAsync(hs, h->gstatus, sizeof(GraphStatus), cudaMemcpyDeviceToHost, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   const long long iters = hs->total - total0;
-  h->launches += (int64_t)nsteps * h->graph_kernels_fixed + iters * h->graph_kernels_iter;
+  // the body of the while node ran once per application beyond the k baked
+  // into every step
+  h->launches += (int64_t)nsteps * h->graph_kernels_fixed +
+                 (iters - (long long)nsteps * sp->graph_k) * h->graph_kernels_iter;
   h->t_cnt[1] += iters;
   h->t_cnt[0] += nsteps;
   h->t_cnt[2] += nsteps;
   h->last_iters = hs->iters;
   h->last_res = hs->rel;
+  if (hs->need_max > 0) sp->last_iters = hs->need_max;
   h->psi_valid = true;
   if (hs->fails != fails0) {
     h->err = "a Poisson solve inside the step graph stopped at the iteration cap";
