@@ -5,9 +5,12 @@ z=-1), D3Q19, 128^3 periodic, ion number fractions 0.01 +/- U(1e-3) seeded,
 Bjerrum length 0.7, Poisson solved every step to a relative residual of
 1e-8 (spectral solver; the multigrid solver is timed beside it), Sc = 1,
 FP32.  One step = charge density + Poisson solve + fused
-stream/collide of all species.  Metric: species-site MLUPS (S * N * steps /
-time / 1e6), with the stream/collide kernel's fraction of the measured HBM
-roofline and the Poisson iterations per step.
+stream/collide of all species, each step one CUDA-graph replay (the
+library's LBM_FLAG_STEP_GRAPH; --host-steps drives the steps from the host
+instead).  Metric: species-site MLUPS (S * N * steps / time / 1e6), with
+the stream/collide kernel's fraction of the measured HBM roofline and the
+Poisson iterations per step.  A host-stepped run of the same workload
+gives the per-phase CUDA-event times (phase_ms_per_step, host_steps).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -53,6 +56,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-slit and learned-guess measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-steps", action="store_true",
+                    help="headline with host-driven steps instead of CUDA-graph steps")
     return ap.parse_args()
 
 
@@ -463,8 +468,18 @@ def run_ours(args, rank, world, local):
         lat.destroy()
         return t_ms, tm, diag, clk
 
-    t_ms, tm, diag, clk = timed(args.poisson, True)
+    # headline: every step one CUDA-graph replay (spectral solver); the
+    # host-stepped run beside it gives the per-phase CUDA-event times
+    graph_head = args.poisson == "fft" and not args.host_steps
+    t_ms, tm_head, diag, clk = timed(args.poisson, True, graph=graph_head)
     value = world * S * N * args.steps / (t_ms / 1e3) / 1e6
+    if graph_head:
+        t_host, tm, _, _ = timed(args.poisson, False, graph=False)
+        host_run = {"value": world * S * N * args.steps / (t_host / 1e3) / 1e6,
+                    "ms_per_step": t_host / args.steps,
+                    "poisson_iters_per_step": tm["poisson_iters"] / args.steps}
+    else:
+        tm, host_run = tm_head, None
     collide_ms = tm["collide_ms"] / max(1, tm["collide_launches"])
     bpl = BYTES_PER_SPECIES_SITE[args.storage] * S * N
     peak, peak_kind = measured_peaks()
@@ -479,16 +494,6 @@ def run_ours(args, rank, world, local):
                "ms_per_step": ta / args.steps, "poisson_iters_per_step": tma["poisson_iters"] / args.steps,
                "poisson_ms_per_step": tma["poisson_ms"] / args.steps}
 
-    # the same workload with every step one CUDA-graph replay (device-side
-    # Poisson loop, no host round trip between steps)
-    graph_run = None
-    if args.poisson == "fft" and not args.no_alt:
-        tg, tmg, dg, _ = timed("fft", False, graph=True)
-        graph_run = {"value": world * S * N * args.steps / (tg / 1e3) / 1e6,
-                     "ms_per_step": tg / args.steps,
-                     "poisson_iters_per_step": tmg["poisson_iters"] / args.steps,
-                     "poisson_residual_last": dg["poisson_residual"]}
-
     batched = learned = None
     if rank == 0 and world == 1 and not args.no_extras:
         batched = run_batched(lbm, WL, local=local)
@@ -496,7 +501,7 @@ def run_ours(args, rank, world, local):
 
     # end to end through the C ABI with host buffers: initial state uploaded
     # from pinned host memory, every step's FP64 diagnostics read back.
-    lat2 = make(args.poisson)
+    lat2 = make(args.poisson, graph_head)
     pinned = [torch.from_numpy(np.ascontiguousarray(wl.n0[s])).pin_memory().numpy() for s in range(S)]
     barrier()
     t0 = time.perf_counter()
@@ -511,7 +516,7 @@ def run_ours(args, rank, world, local):
     e2e_value = world * S * N * args.steps / e2e_s / 1e6
     lat2.destroy()
 
-    iters = tm["poisson_iters"]
+    iters = tm_head["poisson_iters"]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -529,6 +534,7 @@ def run_ours(args, rank, world, local):
                        "poisson": args.poisson, "poisson_tol": 1e-8, "storage": args.storage,
                        "l2": "not flushed: inputs larger than L2 (2 x %.0f MB population lattices)"
                              % (BYTES_PER_SPECIES_SITE[args.storage] / 2 * S * N / 1e6),
+                       "steps": "cuda_graph" if graph_head else "host",
                        "parallelism": "replicas" if world > 1 else "single"},
             "poisson_iters_per_step": iters / args.steps,
             "phase_ms_per_step": {"charge": tm["charge_ms"] / args.steps,
@@ -539,12 +545,12 @@ def run_ours(args, rank, world, local):
                          "peak_source": peak_kind,
                          "algorithmic_bytes_per_launch": bpl, "traffic": traffic},
             "clocks": clk,
-            "gpu_launches": tm["kernel_launches"],
+            "gpu_launches": tm_head["kernel_launches"],
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * S * N / args.steps,
                     "d2h_bytes_per_step": 8 * (S + 7)},
             "poisson_alternative": alt,
-            "step_graph": graph_run,
+            "host_steps": host_run,
             "batched": batched,
             "learned_vs_plain": learned,
             "diagnostics": {"mass": list(map(float, diag["mass"])),
