@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(1024, 1) k_plane_inv(const float2* __restrict_
 // [z][33] shared array.  Forward FFT, division by lambda (the free mean,
 // mode (0,0,0), set to 0), inverse FFT, all in registers between exchanges.
 template <int LGZ>
-__global__ void __launch_bounds__(4 << LGZ) k_zfft(float2* __restrict__ spec, SpecArgs a) {
+__global__ void __launch_bounds__(4 << LGZ, LGZ <= 7 ? 2 : 1) k_zfft(float2* __restrict__ spec, SpecArgs a) {
   extern __shared__ __align__(16) float2 zb[];
   constexpr int L = 1 << LGZ, T = L >> 3;
   const int p = threadIdx.x & 31, t = threadIdx.x >> 5;
