@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--poisson", default="fft", choices=["mg", "sor", "fft"])
     ap.add_argument("--no-alt", action="store_true", help="skip the multigrid comparison run")
-    ap.add_argument("--only", choices=["batched", "learned", "slit"], default=None,
+    ap.add_argument("--only", choices=["batched", "learned", "slit", "conductivity"], default=None,
                     help="run one extra measurement alone and print it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-slit and learned-guess measurements")
@@ -354,6 +354,51 @@ def run_learned(lbm, WL, n=64, steps=10, local=0):
     return out
 
 
+def run_conductivity(lbm, WL, n=64, local=0):
+    """Bulk conductivity (Sec. 4, current against D; Eq. Drude): a uniform
+    neutral ternary electrolyte (ion fractions 0.01) in a field 1e-3 along
+    x, n^3 periodic, graph steps, spectral Poisson, FP32, at Sc 1 ... 1000.
+    Each run lasts until the species velocities have relaxed (they relax by
+    |1 - omega_drag| per step); the measured current J = sum z n u over the
+    box is compared with the Drude-Lorentz value (D / c_s^2) sum z^2 n E,
+    D = c_s^2 (1/omega_drag - 1/2)."""
+    import torch
+    cs2, e, fraction = 1.0 / 3.0, 1e-3, 0.01
+    out = []
+    for sc in (1.0, 3.0, 10.0, 30.0, 100.0, 300.0, 1000.0):
+        wl = WL.bulk_conductivity(n=n, e_field=e, schmidt=sc, fraction=fraction)
+        od = lbm.omega_drag_for_schmidt(wl.omega_visc, sc)
+        q = abs(1.0 - od)
+        steps = 200 if q < 1e-3 else 200 + int(math.log(1e-9) / math.log(q))
+        lat = lbm.Lattice(n, n, n, 3, omega_visc=wl.omega_visc, omega_drag=od, bjerrum=wl.bjerrum,
+                          e_ext=wl.e_ext, poisson="fft", step_graph=True, device=local)
+        for s in range(3):
+            lat.set_species(s, 1.0, wl.valence[s], wl.n0[s])
+        lat.step(3)
+        lat.synchronize()
+        st = torch.cuda.ExternalStream(lat.stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        lat.step(steps)
+        e1.record(st)
+        lat.synchronize()
+        ms = e0.elapsed_time(e1)
+        J = 0.0
+        for s in range(3):
+            ns, us = lat.get_moments(s)
+            J += float(wl.valence[s] * (ns * us[0]).mean())
+        D = cs2 * (1.0 / od - 0.5)
+        jd = D / cs2 * 2 * fraction * e
+        out.append({"sc": sc, "omega_drag": od, "D": D, "steps": steps, "current": J,
+                    "drude": jd, "current_over_drude": J / jd,
+                    "value": 3 * wl.sites * steps / (ms / 1e3) / 1e6,
+                    "poisson_residual_last": lat.diagnostics()["poisson_residual"]})
+        lat.destroy()
+    return {"workload": "bulk conductivity %d^3, ion fractions 0.01, E 1e-3 along x" % n,
+            "runs": out}
+
+
 def run_slit(lbm, WL, steps=2000, local=0):
     """Charged slit 64x64x(64 + 2 walls), wall charge -0.01 per node, Debye
     length 8, field 1e-4 along x: FP32, FP16 and BF16 storage at Sc 1 ... 1000
@@ -574,6 +619,8 @@ def main():
             res = run_batched(lbm, WL, steps=max(1, args.steps))
         elif args.only == "slit":
             res = run_slit(lbm, WL, steps=max(1, args.steps))
+        elif args.only == "conductivity":
+            res = run_conductivity(lbm, WL, n=args.n if args.n != 128 else 64)
         else:
             res = run_learned(lbm, WL)
         print(json.dumps({"metric": METRIC, "only": args.only, **res}), flush=True)

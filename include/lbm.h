@@ -49,6 +49,11 @@ typedef enum {
   LBM_ETIMEOUT = 6   /* a bounded device wait gave up                   */
 } lbm_status;
 
+/* Population storage.  Every format stores the deviation of a population
+ * from the reference equilibrium at rest, h = f / (w_p n_ref) - 1, with
+ * n_ref the species' mean initial density (set by lbm_set_species), in
+ * FP32, FP16 or BF16; the step computes in FP32 on deviations.  16-bit
+ * stores round stochastically.                                            */
 enum { LBM_FP32 = 0, LBM_FP16_SHIFT = 1, LBM_BF16_SHIFT = 2 };
 /* Poisson solvers.  MG: geometric multigrid (any wall geometry).  SOR:
  * red-black successive over-relaxation (any geometry; slow, a reference).
@@ -223,10 +228,12 @@ lbm_status lbm_solve_poisson(lbm_t* h, const double* rho_e, double* psi,
 #define LBM_DIAG_LEN(S) ((S) + 7)
 lbm_status lbm_diagnostics(lbm_t* h, double* out);
 
-/* Raw state for checkpointing: the stored populations of all species as
- * FP32 values, S*19*N floats, in the library's internal order (post-
- * collision populations of the last step, before streaming), plus the step
- * counter.  lbm_set_state restores exactly what lbm_get_state returned.   */
+/* Raw state for checkpointing (FP32 storage): the stored values of all
+ * species, S*19*N floats in the library's internal order and form (post-
+ * collision populations of the last step, before streaming, as
+ * h = f / (w_p n_ref) - 1), plus the step counter.  lbm_set_state restores
+ * exactly what lbm_get_state returned, into a lattice whose species were
+ * set with the same initial densities (hence the same n_ref).            */
 lbm_status lbm_get_state(lbm_t* h, float* state, int64_t* step);
 lbm_status lbm_set_state(lbm_t* h, const float* state, int64_t step);
 

@@ -591,10 +591,16 @@ lbm_status lbm_diagnostics(lbm_t* h, double* out) {
   int bad = 0;
   LBM_CUDA_TRY(h, cudaMemcpyAsync(&bad, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  // the kernel sums deviations from n_ref; the reference parts are exact
   const int S = h->S;
-  for (int s = 0; s < S; ++s) out[s] = h->hred[s];
+  const double nf = (double)h->nfluid;
+  double zref = 0.0;
+  for (int s = 0; s < S; ++s) {
+    out[s] = nf * (double)h->nref[s] + h->hred[s];
+    zref += (double)h->valence[s] * (double)h->nref[s];
+  }
   for (int d = 0; d < 3; ++d) out[S + d] = h->mass0 * h->hred[MAX_SPECIES + d];
-  out[S + 3] = h->hred[MAX_SPECIES + 3];
+  out[S + 3] = nf * zref + h->hred[MAX_SPECIES + 3];
   out[S + 4] = (double)h->last_iters;
   out[S + 5] = h->last_res;
   out[S + 6] = (double)h->tstep;

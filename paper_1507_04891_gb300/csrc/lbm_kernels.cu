@@ -57,15 +57,26 @@ constexpr float CS2 = 1.0f / 3.0f;
 // ---------------------------------------------------------------------------
 template <int ST>
 struct Fmt;
+// Every format stores the population's deviation from the reference
+// equilibrium at rest, h = f / (w_p n_ref) - 1 (n_ref: the species' mean
+// initial density).  The arithmetic of the step works on deviations
+// d = f - w_p n_ref = w_p n_ref h, so FP32 rounding is relative to the
+// deviation, not to f: a drift far below one ulp of f (the ion current of a
+// high-Schmidt-number run) is still resolved.  ld returns f, ldd returns d;
+// the stores take d.
 template <>
 struct Fmt<LBM_FP32> {
   using T = float;
-  static __device__ __forceinline__ float ld(const T* p, float) { return *p; }
-  static __device__ __forceinline__ void st(T* p, float v, float) { *p = v; }
-  static __device__ __forceinline__ void st_sr(T* p, float v, float, uint32_t) { *p = v; }
-  static __device__ __forceinline__ void st_sr2(T* pa, float va, T* pb, float vb, float, uint32_t) {
-    *pa = va;
-    *pb = vb;
+  static __device__ __forceinline__ float ld(const T* p, float wn) { return wn * (1.0f + *p); }
+  static __device__ __forceinline__ float ldd(const T* p, float wn) { return wn * *p; }
+  static __device__ __forceinline__ void st(T* p, float d, float inv_wn) { *p = d * inv_wn; }
+  static __device__ __forceinline__ void st_sr(T* p, float d, float inv_wn, uint32_t) {
+    *p = d * inv_wn;
+  }
+  static __device__ __forceinline__ void st_sr2(T* pa, float da, T* pb, float db, float inv_wn,
+                                                uint32_t) {
+    *pa = da * inv_wn;
+    *pb = db * inv_wn;
   }
 };
 
@@ -82,31 +93,31 @@ __device__ __forceinline__ uint32_t cvt_rs_bf16x2(float hi, float lo, uint32_t r
   asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
   return d;
 }
-// 16-bit formats: h = f / (w_p n_ref) - 1.  st() rounds to nearest; st_sr()
-// and st_sr2() round stochastically (the hardware conversion draws on random
-// bits to round up with probability equal to the dropped fraction), so the
-// stored value is unbiased.  The per-step change of a slowly diffusing mode
-// is a fraction of one 16-bit ulp of h; round-to-nearest would return the
-// same value every step and freeze the mode.
+// 16-bit formats: the same h.  st() rounds to nearest; st_sr() and st_sr2()
+// round stochastically (the hardware conversion draws on random bits to
+// round up with probability equal to the dropped fraction), so the stored
+// value is unbiased.  The per-step change of a slowly diffusing mode is a
+// fraction of one 16-bit ulp of h; round-to-nearest would return the same
+// value every step and freeze the mode.
 template <>
 struct Fmt<LBM_FP16_SHIFT> {
   using T = __half;
   static __device__ __forceinline__ float ld(const T* p, float wn) {
     return wn * (1.0f + __half2float(*p));
   }
-  static __device__ __forceinline__ void st(T* p, float v, float inv_wn) {
-    *p = __float2half_rn(fmaf(v, inv_wn, -1.0f));
+  static __device__ __forceinline__ float ldd(const T* p, float wn) { return wn * __half2float(*p); }
+  static __device__ __forceinline__ void st(T* p, float d, float inv_wn) {
+    *p = __float2half_rn(d * inv_wn);
   }
-  static __device__ __forceinline__ void st_sr(T* p, float v, float inv_wn, uint32_t rnd) {
-    const float hv = fmaf(v, inv_wn, -1.0f);
-    const uint32_t d = cvt_rs_f16x2(hv, 0.0f, rnd);
-    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(d >> 16);
+  static __device__ __forceinline__ void st_sr(T* p, float d, float inv_wn, uint32_t rnd) {
+    const uint32_t v = cvt_rs_f16x2(d * inv_wn, 0.0f, rnd);
+    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(v >> 16);
   }
-  static __device__ __forceinline__ void st_sr2(T* pa, float va, T* pb, float vb, float inv_wn,
+  static __device__ __forceinline__ void st_sr2(T* pa, float da, T* pb, float db, float inv_wn,
                                                 uint32_t rnd) {
-    const uint32_t d = cvt_rs_f16x2(fmaf(va, inv_wn, -1.0f), fmaf(vb, inv_wn, -1.0f), rnd);
-    *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(d >> 16);
-    *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(d & 0xFFFFu);
+    const uint32_t v = cvt_rs_f16x2(da * inv_wn, db * inv_wn, rnd);
+    *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(v >> 16);
+    *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(v & 0xFFFFu);
   }
 };
 template <>
@@ -115,19 +126,21 @@ struct Fmt<LBM_BF16_SHIFT> {
   static __device__ __forceinline__ float ld(const T* p, float wn) {
     return wn * (1.0f + __bfloat162float(*p));
   }
-  static __device__ __forceinline__ void st(T* p, float v, float inv_wn) {
-    *p = __float2bfloat16_rn(fmaf(v, inv_wn, -1.0f));
+  static __device__ __forceinline__ float ldd(const T* p, float wn) {
+    return wn * __bfloat162float(*p);
   }
-  static __device__ __forceinline__ void st_sr(T* p, float v, float inv_wn, uint32_t rnd) {
-    const float hv = fmaf(v, inv_wn, -1.0f);
-    const uint32_t d = cvt_rs_bf16x2(hv, 0.0f, rnd);
-    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(d >> 16);
+  static __device__ __forceinline__ void st(T* p, float d, float inv_wn) {
+    *p = __float2bfloat16_rn(d * inv_wn);
   }
-  static __device__ __forceinline__ void st_sr2(T* pa, float va, T* pb, float vb, float inv_wn,
+  static __device__ __forceinline__ void st_sr(T* p, float d, float inv_wn, uint32_t rnd) {
+    const uint32_t v = cvt_rs_bf16x2(d * inv_wn, 0.0f, rnd);
+    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(v >> 16);
+  }
+  static __device__ __forceinline__ void st_sr2(T* pa, float da, T* pb, float db, float inv_wn,
                                                 uint32_t rnd) {
-    const uint32_t d = cvt_rs_bf16x2(fmaf(va, inv_wn, -1.0f), fmaf(vb, inv_wn, -1.0f), rnd);
-    *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(d >> 16);
-    *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(d & 0xFFFFu);
+    const uint32_t v = cvt_rs_bf16x2(da * inv_wn, db * inv_wn, rnd);
+    *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(v >> 16);
+    *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(v & 0xFFFFu);
   }
 };
 
@@ -175,8 +188,9 @@ __device__ __forceinline__ int upstream(const Nbr& o, int p) {
   return d;
 }
 
-// Pulls f_p(r, t) of species s: the post-collision value of r - c_p, or the
-// reversed population of r itself when r - c_p is a wall node.
+// Pulls the deviation d_p = f_p(r, t) - w_p n_ref of species s: the
+// post-collision value of r - c_p, or the reversed population of r itself
+// when r - c_p is a wall node (w_p is the same for p and its opposite).
 template <int ST, bool WALLS>
 __device__ __forceinline__ float pull(const typename Fmt<ST>::T* __restrict__ f,
                                       int64_t N, int s, int p, uint32_t i,
@@ -189,7 +203,7 @@ __device__ __forceinline__ float pull(const typename Fmt<ST>::T* __restrict__ f,
     const int64_t bb = (int64_t)(s * Q + OPP(p)) * N + i;
     idx = ((lk >> p) & 1u) ? bb : idx;
   }
-  return Fmt<ST>::ld(f + idx, wn);
+  return Fmt<ST>::ldd(f + idx, wn);
 }
 
 __device__ __forceinline__ void site_xyz(uint32_t i, int nx, int ny, int& x,
@@ -264,7 +278,8 @@ __device__ __forceinline__ void block_sum_to(long long v, double* out) {
 
 // ---------------------------------------------------------------------------
 // Fused stream + collide, one thread per node, all S species in registers.
-//   1. pull the 19*S populations f_p^alpha(r, t)            (Eq. latboeq, lhs)
+//   1. pull the 19*S populations f_p^alpha(r, t), as deviations from
+//      w_p n_ref                                            (Eq. latboeq, lhs)
 //   2. n^alpha, bare u^alpha = sum c f / n, barycentric u   (Sec. 3 definitions)
 //   3. F^alpha = F_el + F_drag: electric z(-c_s^2 grad psi + E) and the drag
 //      -omega_drag sum_beta (n_beta/n)(u^a - u^b) on velocities shifted by
@@ -292,6 +307,7 @@ __global__ void __launch_bounds__(256) k_stream_collide(const StepArgs a) {
   T* __restrict__ fout = static_cast<T*>(a.fout);
   const int64_t N = a.N;
 
+  // deviations d_p = f_p - w_p n_ref of every species
   float f[S][Q];
 #pragma unroll
   for (int p = 0; p < Q; ++p) {
@@ -302,7 +318,8 @@ __global__ void __launch_bounds__(256) k_stream_collide(const StepArgs a) {
     }
   }
 
-  float n[S], jx[S], jy[S], jz[S];
+  // n = n_ref + dn (sum w_p = 1), j = sum c_p d_p (sum w_p c_p = 0)
+  float dn[S], n[S], jx[S], jy[S], jz[S];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     float m0 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
@@ -313,7 +330,8 @@ __global__ void __launch_bounds__(256) k_stream_collide(const StepArgs a) {
       if (CY(p)) my += CY(p) * f[s][p];
       if (CZ(p)) mz += CZ(p) * f[s][p];
     }
-    n[s] = m0;
+    dn[s] = m0;
+    n[s] = a.nref[s] + m0;
     jx[s] = mx;
     jy[s] = my;
     jz[s] = mz;
@@ -360,17 +378,24 @@ __global__ void __launch_bounds__(256) k_stream_collide(const StepArgs a) {
     const float Fz = ez - omd * (usz + 0.5f * ez - vbz);
     const float usq = usx * usx + usy * usy + usz * usz;
     const float Fu = Fx * ux + Fy * uy + Fz * uz;
-    // p-independent part of omega*phi/(n w) + g/(n w)
-    const float base = om * (1.0f - 1.5f * usq) - 3.0f * Fu;
+    // In deviations, d*_p = (1 - omega) d_p + [omega phi_p + g_p - omega w_p n_ref]
+    // with, per weight w_p,
+    //   omega phi_p + g_p - omega w_p n_ref
+    //     = w_p [omega dn + n (-1.5 omega |u^a|^2 - 3 F.u
+    //                          + 4.5 omega a^2 + 9 (F.c)(u.c))]      (even in c)
+    //     + w_p n 3 (omega a + F.c)                                 (odd in c)
+    // a = u^a.c (phi_perp in its reduced form, the Appendix expression;
+    // g_p of Eq. ourforc).  Every term is of the size of the deviations.
+    const float base = n[s] * (-1.5f * om * usq - 3.0f * Fu);
+    const float odn = om * dn[s];
     const float inr = 1.0f / a.nref[s];
     // moving populations first; the rest population then takes
-    // f*_0 = n - sum_{p>0} f*_p, which holds exactly in real arithmetic
+    // d*_0 = dn - sum_{p>0} d*_p, which holds exactly in real arithmetic
     // (phi_perp carries mass n, g_p none) and keeps FP32 rounding of the
     // weights from drifting the species mass.
     // Directions come in opposite pairs (p, p+1), c_{p+1} = -c_p: a = u^a.c,
-    // F.c and u.c flip sign, so each pair shares the even part
-    // base + 4.5 om a^2 + 9 (F.c)(u.c) and takes +/- the odd part
-    // 3 (om a + F.c).
+    // F.c and u.c flip sign, so each pair shares the even part and takes
+    // +/- the odd part.
     const float omm = 1.0f - om;
     float moved = 0.f;
 #pragma unroll
@@ -378,16 +403,16 @@ __global__ void __launch_bounds__(256) k_stream_collide(const StepArgs a) {
       const float av = CX(p) * usx + CY(p) * usy + CZ(p) * usz;
       const float fc = CX(p) * Fx + CY(p) * Fy + CZ(p) * Fz;
       const float uc = CX(p) * ux + CY(p) * uy + CZ(p) * uz;
-      const float wn = WT(p) * n[s];  // same weight for p and p+1
-      const float even = wn * (base + 4.5f * om * av * av + 9.0f * fc * uc);
-      const float odd = wn * 3.0f * (om * av + fc);
-      const float fa = omm * f[s][p] + (even + odd);
-      const float fb = omm * f[s][p + 1] + (even - odd);
-      moved += fa + fb;
-      Fmt<ST>::st_sr2(fout + (int64_t)(s * Q + p) * N + i, fa, fout + (int64_t)(s * Q + p + 1) * N + i,
-                      fb, INV_WT(p) * inr, lcg_next(rnd));
+      const float w = WT(p);  // same weight for p and p+1
+      const float even = w * (odn + base + n[s] * (4.5f * om * av * av + 9.0f * fc * uc));
+      const float odd = w * n[s] * 3.0f * (om * av + fc);
+      const float da = omm * f[s][p] + (even + odd);
+      const float db = omm * f[s][p + 1] + (even - odd);
+      moved += da + db;
+      Fmt<ST>::st_sr2(fout + (int64_t)(s * Q + p) * N + i, da, fout + (int64_t)(s * Q + p + 1) * N + i,
+                      db, INV_WT(p) * inr, lcg_next(rnd));
     }
-    Fmt<ST>::st_sr(fout + (int64_t)(s * Q) * N + i, n[s] - moved, INV_WT(0) * inr, lcg_next(rnd));
+    Fmt<ST>::st_sr(fout + (int64_t)(s * Q) * N + i, dn[s] - moved, INV_WT(0) * inr, lcg_next(rnd));
   }
 }
 
@@ -414,6 +439,7 @@ __global__ void k_init(int s, const double* __restrict__ n0,
   const Nbr o = neighbours(x, y, z, nx, ny, nz);
   T* fout = static_cast<T*>(fout_v);
   const float n = (float)n0[i];
+  const float dn = (float)(n0[i] - (double)nref);  // deviation from n_ref, exact in FP64
   float vx = 0.f, vy = 0.f, vz = 0.f;
   if (u0) {
     vx = (float)u0[i];
@@ -424,7 +450,8 @@ __global__ void k_init(int s, const double* __restrict__ n0,
 #pragma unroll
   for (int p = 0; p < Q; ++p) {
     const float av = CX(p) * vx + CY(p) * vy + CZ(p) * vz;
-    const float feq = WT(p) * n * (1.0f + 3.0f * av + 4.5f * av * av - 1.5f * usq);
+    // phi_p - w_p n_ref = w_p [dn + n (3 a + 4.5 a^2 - 1.5 |u|^2)]
+    const float deq = WT(p) * (dn + n * (3.0f * av + 4.5f * av * av - 1.5f * usq));
     int64_t dst;
     int q = p;
     if (WALLS && ((lk >> p) & 1u)) {
@@ -433,20 +460,20 @@ __global__ void k_init(int s, const double* __restrict__ n0,
     } else {
       dst = (int64_t)((int)i + upstream(o, p));
     }
-    Fmt<ST>::st(fout + (int64_t)(s * Q + q) * N + dst, feq, INV_WT(q) / nref);
+    Fmt<ST>::st(fout + (int64_t)(s * Q + q) * N + dst, deq, INV_WT(q) / nref);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Charge density for the Poisson source: s_r = 4 pi l_B (rho_e + w_r) with
 // rho_e = sum_alpha z^alpha n^alpha(r, t) from the pulled populations of the
-// charged species; block sums of s over fluid nodes go to dsum[0] (FP64).
+// charged species; per-CTA sums of s over fluid nodes (exact, int64).
 // ---------------------------------------------------------------------------
 template <int S, bool WALLS, int ST>
 __global__ void __launch_bounds__(256) k_charge(
     const void* fin_v, const uint32_t* links, const int64_t* wsrc, int64_t* src,
     long long* part, const int* label, unsigned long long* comp_sum, int nx, int ny,
-    int nz, int64_t N, float4 val, float4 nref, float fourpi_lb) {
+    int nz, int64_t N, float4 val, float4 nref, float fourpi_lb, long long src_ref) {
   using T = typename Fmt<ST>::T;
   const T* fin = static_cast<const T*>(fin_v);
   const float vz[4] = {val.x, val.y, val.z, val.w};
@@ -465,7 +492,10 @@ __global__ void __launch_bounds__(256) k_charge(
       int x, y, z;
       site_xyz(i, nx, ny, x, y, z);
       const Nbr o = neighbours(x, y, z, nx, ny, nz);
-      float rho = 0.f;
+      // rho_e = sum z n_ref + sum z dn: the first part is the same at every
+      // node (src_ref, fixed point, from the host); the deviations carry
+      // the local charge at full FP32 precision
+      float drho = 0.f;
       // all pulls of the charged species are independent: unrolled so that
       // they are in flight together
 #pragma unroll
@@ -475,11 +505,11 @@ __global__ void __launch_bounds__(256) k_charge(
 #pragma unroll
         for (int p = 0; p < Q; ++p)
           m0 += pull<ST, WALLS>(fin, N, s, p, i, upstream(o, p), lk, nr[s]);
-        rho += vz[s] * m0;
+        drho += vz[s] * m0;
       }
       // exact conversion: a float times a power of two, to a 64-bit integer;
       // the wall charge is already in fixed point
-      sv = (long long)(fourpi_lb * rho * PSI_SCALE_F);
+      sv = src_ref + (long long)(fourpi_lb * drho * PSI_SCALE_F);
       if (wsrc) sv += wsrc[i];
     }
     src[i] = sv;
@@ -522,7 +552,8 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const long long* part, in
   }
 }
 
-// Gathers f(t) of species s and its moments n, u = sum c f / n (doubles).
+// Gathers f(t) of species s and its moments n, u = sum c f / n (doubles,
+// from the deviations: n = n_ref + sum d, j = sum c d).
 template <bool WALLS, int ST>
 __global__ void k_gather(const void* fin_v, const uint32_t* links, int s,
                          int nx, int ny, int nz, int64_t N, float nref,
@@ -543,11 +574,11 @@ __global__ void k_gather(const void* fin_v, const uint32_t* links, int s,
   site_xyz(i, nx, ny, x, y, z);
   const Nbr o = neighbours(x, y, z, nx, ny, nz);
   const T* fin = static_cast<const T*>(fin_v);
-  double m0 = 0, mx = 0, my = 0, mz = 0;
+  double m0 = nref, mx = 0, my = 0, mz = 0;
 #pragma unroll
   for (int p = 0; p < Q; ++p) {
     const float v = pull<ST, WALLS>(fin, N, s, p, i, upstream(o, p), lk, nref);
-    if (f_out) f_out[(int64_t)p * N + i] = (double)v;
+    if (f_out) f_out[(int64_t)p * N + i] = (double)WT(p) * nref + (double)v;
     m0 += v;
     mx += CX(p) * (double)v;
     my += CY(p) * (double)v;
@@ -561,8 +592,14 @@ __global__ void k_gather(const void* fin_v, const uint32_t* links, int s,
   }
 }
 
-// FP64 diagnostics: per-species particle number, total momentum, net charge;
-// flags non-finite or non-positive densities.  out layout as lbm_diagnostics.
+// Diagnostics: per species the sum over fluid nodes of dn = n - n_ref, the
+// total momentum and the net charge of the deviations (the host adds the
+// reference parts n_ref x fluid nodes, exactly); flags non-finite or
+// non-positive densities.  Deviations are summed per thread and per warp in
+// FP32 (they are small next to the reference part, so their rounding is far
+// below the FP64 resolution of the total), then per CTA in FP64 with one
+// FP64 atomic per CTA and quantity.  out layout: [0, MAX_SPECIES) dn per
+// species, then momentum x, y, z, then charge.
 template <bool WALLS, int ST>
 __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
                                               const uint32_t* links, int nx,
@@ -570,8 +607,10 @@ __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
                                               float4 val, float4 nref,
                                               double* out, int* bad) {
   using T = typename Fmt<ST>::T;
-  double acc[MAX_SPECIES + 4];
-  for (int k = 0; k < MAX_SPECIES + 4; ++k) acc[k] = 0.0;
+  float acc[MAX_SPECIES + 4];
+  for (int k = 0; k < MAX_SPECIES + 4; ++k) acc[k] = 0.f;
+  const float vz[4] = {val.x, val.y, val.z, val.w};
+  const float nr[4] = {nref.x, nref.y, nref.z, nref.w};
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)N;
        i += gridDim.x * blockDim.x) {
     uint32_t lk = 0;
@@ -585,8 +624,6 @@ __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
       site_xyz(i, nx, ny, x, y, z);
       const Nbr o = neighbours(x, y, z, nx, ny, nz);
       const T* fin = static_cast<const T*>(fin_v);
-      const float vz[4] = {val.x, val.y, val.z, val.w};
-      const float nr[4] = {nref.x, nref.y, nref.z, nref.w};
       for (int s = 0; s < S; ++s) {
         float m0 = 0, mx = 0, my = 0, mz = 0;
 #pragma unroll
@@ -597,23 +634,23 @@ __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
           my += CY(p) * v;
           mz += CZ(p) * v;
         }
-        if (!(m0 > 0.f) || !isfinite(m0) || !isfinite(mx) || !isfinite(my) ||
+        if (!(nr[s] + m0 > 0.f) || !isfinite(m0) || !isfinite(mx) || !isfinite(my) ||
             !isfinite(mz))
           atomicOr(bad, 1);
         acc[s] += m0;
         acc[MAX_SPECIES + 0] += mx;
         acc[MAX_SPECIES + 1] += my;
         acc[MAX_SPECIES + 2] += mz;
-        acc[MAX_SPECIES + 3] += (double)vz[s] * m0;
+        acc[MAX_SPECIES + 3] += vz[s] * m0;
       }
     }
   }
   __shared__ double red[8][MAX_SPECIES + 4];
   for (int k = 0; k < MAX_SPECIES + 4; ++k) {
-    double v = acc[k];
+    float v = acc[k];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = (double)v;
   }
   __syncthreads();
   if (threadIdx.x < MAX_SPECIES + 4) {
@@ -795,12 +832,17 @@ cudaError_t launch_charge(lbm_t* h) {
   const int ct = h->charge_threads;
   const int nb = (int)nblocks(h->N, ct);
   const float k = (float)(4.0 * 3.14159265358979323846 * h->cfg.bjerrum);
+  // reference part of the source, 4 pi l_B sum_alpha z^alpha n_ref^alpha,
+  // in fixed point (FP64 on the host, the same at every fluid node)
+  double zref = 0.0;
+  for (int s = 0; s < h->S; ++s) zref += (double)h->valence[s] * (double)h->nref[s];
+  const long long src_ref = llrint(4.0 * 3.14159265358979323846 * h->cfg.bjerrum * zref * PSI_SCALE);
 #define LBM_CHARGE_S(SS)                                                        \
   LBM_DISPATCH_WS(h, (k_charge<SS, W_, ST_><<<nb, ct, 0, h->st>>>(               \
                          h->f[h->cur], h->links, h->wsrc, h->ps.src, h->ps.part, \
                          h->ps.label, h->ps.comp_sum,                            \
                          h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,                  \
-                         as_f4(h->valence), as_f4(h->nref), k)))
+                         as_f4(h->valence), as_f4(h->nref), k, src_ref)))
   switch (h->S) {
     case 1: LBM_CHARGE_S(1); break;
     case 2: LBM_CHARGE_S(2); break;

@@ -826,6 +826,9 @@ struct SpectralPlan {
   int lgz = -1;                    // log2(nz) when the z axis is one periodic run
   int last_iters = 2;              // applications of the previous solve
   int graph_k = 0;                 // applications baked into the step graphs
+  int graph_pred = 0;              // applications the last graph steps suggest (0: none yet)
+  int need_acc[4] = {0, 0, 0, 0};  // steps needing 1, 2, 3, >= 4 applications, not yet decided on
+  bool status_read = false;        // the host copy of the graph status is current
   bool runs_fit = true;            // z solve fits in shared memory
   float* r = nullptr;              // N (residual for the learned guess)
   long long* psum = nullptr;       // nz
@@ -1237,7 +1240,8 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
 // host path predicts (k), the final residual and its test, a device-side
 // while loop (conditional graph node) of [application, residual, test] for
 // a step that needs more, and the fused stream/collide.  The graphs are
-// rebuilt when the applications a step needs change.
+// rebuilt when the applications steps need change (k from the distribution
+// of the previous call's steps).
 // Steps are replayed back to back with no host round trip; the test kernel
 // keeps the per-step status on the device.
 // ---------------------------------------------------------------------------
@@ -1248,8 +1252,9 @@ struct GraphStatus {
   int iters;           // Poisson applications of the current step
   long long total;     // applications summed over replayed steps
   int fails;           // steps whose solve stopped at the iteration cap
-  int need_max;        // most applications a step needed since the host reset it
+  int pad;
   double rel;          // final relative residual of the last step
+  int need[4];         // steps that needed 1, 2, 3, >= 4 applications since the host reset it
 };
 
 // Convergence test (one warp).  first: after the k applications queued
@@ -1287,14 +1292,11 @@ __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, do
   const bool more = !conv && st->iters < maxit;
   cudaGraphSetConditional(cond, more ? 1u : 0u);
   st->rel = snk > 0.0 ? sqrt(rnk / snk) : 0.0;
-  if (first && convmask) {
-    const int need = max(1, __ffs(convmask) - 1);
-    st->need_max = max(st->need_max, need);
-  }
+  if (first && convmask) st->need[min(max(1, __ffs(convmask) - 1), 4) - 1] += 1;
   if (!more) {
     st->total += st->iters;
     if (!conv) st->fails += 1;
-    if (!(first && convmask)) st->need_max = max(st->need_max, st->iters);
+    if (!(first && convmask)) st->need[min(st->iters, 4) - 1] += 1;
   }
 }
 
@@ -1430,42 +1432,74 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     }
   }
   SpectralPlan* sp = h->spec;
-  const int want = std::max(1, std::min(std::min(sp->last_iters, h->cfg.poisson_maxit), Poisson::NSLOT - 1));
-  if (sp->graph_k != want) {
-    spectral_graph_free(h);
-    sp->graph_k = want;
-  }
-  for (int k = 0; k < 2; ++k)
-    if (!h->step_graph[k]) {
-      lbm_status s = build_step_graph(h, k);
-      if (s != LBM_OK) return s;
-    }
   GraphStatus* hs = reinterpret_cast<GraphStatus*>(h->hstatus);
-  // status before, to count this call's iterations and failures; the need
-  // of this call's steps starts from 0
-  LBM_CUDA_TRY(h, cudaMemsetAsync(&reinterpret_cast<GraphStatus*>(h->gstatus)->need_max, 0, sizeof(int), h->st));
-  LBM_CUDA_TRY(h, cudaMemcpyAsync(hs, h->gstatus, sizeof(GraphStatus), cudaMemcpyDeviceToHost, h->st));
-  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  GraphStatus* ds = reinterpret_cast<GraphStatus*>(h->gstatus);
+  // status before, to count this call's applications and failures (the
+  // host copy from the end of the previous call is current: only these
+  // graphs write the status)
+  if (!sp->status_read) {
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(hs, ds, sizeof(GraphStatus), cudaMemcpyDeviceToHost, h->st));
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    sp->status_read = true;
+  }
   const long long total0 = hs->total;
   const int fails0 = hs->fails;
-  for (int k = 0; k < nsteps; ++k) {
-    LBM_CUDA_TRY(h, cudaGraphLaunch(h->step_graph[h->cur], h->st));
-    h->cur ^= 1;
-    ++h->tstep;
+  // Steps are replayed in chunks; the distribution of the applications the
+  // steps needed (accumulated over at least 64 steps) sets the number k
+  // baked into the graphs (rebuilt only when k changes).  A step needing more than k runs the
+  // while loop, one application and one residual per extra application; an
+  // application costs about four residuals, so k stays below the need of a
+  // step unless more than 3/4 of the steps need more.
+  constexpr int CHUNK = 128;
+  int done = 0;
+  while (done < nsteps) {
+    const int pred = sp->graph_pred > 0 ? sp->graph_pred : sp->last_iters;
+    const int want = std::max(1, std::min(std::min(pred, h->cfg.poisson_maxit), Poisson::NSLOT - 1));
+    if (sp->graph_k != want) {
+      spectral_graph_free(h);
+      sp->graph_k = want;
+    }
+    for (int k = 0; k < 2; ++k)
+      if (!h->step_graph[k]) {
+        lbm_status s = build_step_graph(h, k);
+        if (s != LBM_OK) return s;
+      }
+    const int n = std::min(CHUNK, nsteps - done);
+    const long long tot_before = hs->total;
+    LBM_CUDA_TRY(h, cudaMemsetAsync(ds->need, 0, 4 * sizeof(int), h->st));
+    for (int k = 0; k < n; ++k) {
+      LBM_CUDA_TRY(h, cudaGraphLaunch(h->step_graph[h->cur], h->st));
+      h->cur ^= 1;
+      ++h->tstep;
+    }
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(hs, ds, sizeof(GraphStatus), cudaMemcpyDeviceToHost, h->st));
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    // the body of the while node ran once per application beyond the k
+    // baked into every step
+    h->launches += (int64_t)n * h->graph_kernels_fixed +
+                   (hs->total - tot_before - (long long)n * sp->graph_k) * h->graph_kernels_iter;
+    // decide once at least 64 steps have been seen (across chunks and calls)
+    for (int j = 0; j < 4; ++j) sp->need_acc[j] += hs->need[j];
+    const int tot = sp->need_acc[0] + sp->need_acc[1] + sp->need_acc[2] + sp->need_acc[3];
+    if (tot >= 64 || (sp->graph_pred == 0 && tot > 0)) {
+      int k = 1, above = tot - sp->need_acc[0];
+      while (k < 4 && 4 * above > 3 * tot) {
+        above -= sp->need_acc[k];
+        ++k;
+      }
+      sp->graph_pred = k;
+      if (tot >= 64)
+        for (int j = 0; j < 4; ++j) sp->need_acc[j] = 0;
+    }
+    done += n;
+    if (hs->fails != fails0) break;
   }
-  LBM_CUDA_TRY(h, cudaMemcpyAsync(hs, h->gstatus, sizeof(GraphStatus), cudaMemcpyDeviceToHost, h->st));
-  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   const long long iters = hs->total - total0;
-  // the body of the while node ran once per application beyond the k baked
-  // into every step
-  h->launches += (int64_t)nsteps * h->graph_kernels_fixed +
-                 (iters - (long long)nsteps * sp->graph_k) * h->graph_kernels_iter;
   h->t_cnt[1] += iters;
-  h->t_cnt[0] += nsteps;
-  h->t_cnt[2] += nsteps;
+  h->t_cnt[0] += done;
+  h->t_cnt[2] += done;
   h->last_iters = hs->iters;
   h->last_res = hs->rel;
-  if (hs->need_max > 0) sp->last_iters = hs->need_max;
   h->psi_valid = true;
   if (hs->fails != fails0) {
     h->err = "a Poisson solve inside the step graph stopped at the iteration cap";

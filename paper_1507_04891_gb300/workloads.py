@@ -87,6 +87,20 @@ def ternary_bulk(n=128, seed=1235, schmidt=1.0, omega_visc=1.0, bjerrum=0.7,
                     bjerrum=bjerrum, steps=steps, meta={"seed": seed})
 
 
+def bulk_conductivity(n=64, fraction=0.01, e_field=1e-3, schmidt=1.0, omega_visc=1.0,
+                      bjerrum=0.7, shape=None):
+    """Uniform neutral ternary electrolyte (solvent z=0, cation z=+1, anion
+    z=-1, ion number fractions `fraction`, solvent fills total density 1)
+    in a uniform field along x: the bulk conductivity experiment (Sec. 4,
+    current against D, Eq. Drude).  No random numbers."""
+    shape = (n, n, n) if shape is None else tuple(shape)
+    ones = np.ones(shape)
+    n0 = np.stack([(1.0 - 2 * fraction) * ones, fraction * ones, fraction * ones])
+    return Workload("bulk_conductivity_%dx%dx%d" % shape[::-1], shape, n0, np.ones(3),
+                    np.array([0.0, 1.0, -1.0]), omega_visc, schmidt, bjerrum=bjerrum,
+                    e_ext=(e_field, 0.0, 0.0), meta={"fraction": fraction})
+
+
 def slit(nx=64, ny=64, width=64, sigma=-0.01, debye=8.0, bjerrum=0.7,
          e_field=1e-4, schmidt=1.0, omega_visc=1.0, steps=20000):
     """Charged slit channel: solid planes z = 0 and z = width + 1, each wall

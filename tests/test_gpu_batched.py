@@ -75,8 +75,12 @@ def test_stacked_slits_equal_independent_instances():
             nb, ub = lat.get_moments(s)
             nb, ub = nb[z0[i]:z0[i] + nz], ub[:, z0[i]:z0[i] + nz]
             fl = ~wl.solid
-            assert (np.abs(nb - n1)[fl] / n1[fl]).max() <= 1e-6
-            assert (np.abs(nb * ub - n1 * u1)[:, fl] / (n1[fl] * CS)).max() <= 1e-6
+            # the stack stores deviations from one reference density per
+            # species (the mean over all channels), a single channel from its
+            # own: the same arithmetic rounds differently, so the two agree to
+            # FP32 accuracy (the 1e-5 parity bar), not to the last bit
+            assert (np.abs(nb - n1)[fl] / n1[fl]).max() <= 1e-5
+            assert (np.abs(nb * ub - n1 * u1)[:, fl] / (n1[fl] * CS)).max() <= 1e-5
 
 
 def test_stacked_slit_against_oracle():
