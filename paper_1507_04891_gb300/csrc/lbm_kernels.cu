@@ -469,13 +469,16 @@ __global__ void k_init(int s, const double* __restrict__ n0,
 // rho_e = sum_alpha z^alpha n^alpha(r, t) from the pulled populations of the
 // charged species; per-CTA sums of s over fluid nodes (exact, int64).
 // ---------------------------------------------------------------------------
-template <int S, bool WALLS, int ST>
+// NC charged species, species indices cs, valences val, reference densities
+// nref (the neutral species are not read).
+template <int NC, bool WALLS, int ST>
 __global__ void __launch_bounds__(256) k_charge(
     const void* fin_v, const uint32_t* links, const int64_t* wsrc, int64_t* src,
     long long* part, const int* label, unsigned long long* comp_sum, int nx, int ny,
-    int nz, int64_t N, float4 val, float4 nref, float fourpi_lb, long long src_ref) {
+    int nz, int64_t N, int4 cs, float4 val, float4 nref, float fourpi_lb, long long src_ref) {
   using T = typename Fmt<ST>::T;
   const T* fin = static_cast<const T*>(fin_v);
+  const int sp[4] = {cs.x, cs.y, cs.z, cs.w};
   const float vz[4] = {val.x, val.y, val.z, val.w};
   const float nr[4] = {nref.x, nref.y, nref.z, nref.w};
   long long acc = 0;
@@ -495,17 +498,22 @@ __global__ void __launch_bounds__(256) k_charge(
       // rho_e = sum z n_ref + sum z dn: the first part is the same at every
       // node (src_ref, fixed point, from the host); the deviations carry
       // the local charge at full FP32 precision
-      float drho = 0.f;
-      // all pulls of the charged species are independent: unrolled so that
-      // they are in flight together
+      // all pulls of the charged species are independent and in one basic
+      // block, so that they are in flight together
+      float v[NC > 0 ? NC : 1][Q];
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        if (vz[s] == 0.f) continue;
+      for (int p = 0; p < Q; ++p) {
+        const int d = upstream(o, p);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[c][p] = pull<ST, WALLS>(fin, N, sp[c], p, i, d, lk, nr[c]);
+      }
+      float drho = 0.f;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
         float m0 = 0.f;
 #pragma unroll
-        for (int p = 0; p < Q; ++p)
-          m0 += pull<ST, WALLS>(fin, N, s, p, i, upstream(o, p), lk, nr[s]);
-        drho += vz[s] * m0;
+        for (int p = 0; p < Q; ++p) m0 += v[c][p];
+        drho += vz[c] * m0;
       }
       // exact conversion: a float times a power of two, to a 64-bit integer;
       // the wall charge is already in fixed point
@@ -600,10 +608,10 @@ __global__ void k_gather(const void* fin_v, const uint32_t* links, int s,
 // below the FP64 resolution of the total), then per CTA in FP64 with one
 // FP64 atomic per CTA and quantity.  out layout: [0, MAX_SPECIES) dn per
 // species, then momentum x, y, z, then charge.
-template <bool WALLS, int ST>
+template <int S, bool WALLS, int ST>
 __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
                                               const uint32_t* links, int nx,
-                                              int ny, int nz, int64_t N, int S,
+                                              int ny, int nz, int64_t N,
                                               float4 val, float4 nref,
                                               double* out, int* bad) {
   using T = typename Fmt<ST>::T;
@@ -624,6 +632,9 @@ __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
       site_xyz(i, nx, ny, x, y, z);
       const Nbr o = neighbours(x, y, z, nx, ny, nz);
       const T* fin = static_cast<const T*>(fin_v);
+      // S is a template parameter: acc stays in registers and the loads of
+      // all species are issued together
+#pragma unroll
       for (int s = 0; s < S; ++s) {
         float m0 = 0, mx = 0, my = 0, mz = 0;
 #pragma unroll
@@ -837,13 +848,28 @@ cudaError_t launch_charge(lbm_t* h) {
   double zref = 0.0;
   for (int s = 0; s < h->S; ++s) zref += (double)h->valence[s] * (double)h->nref[s];
   const long long src_ref = llrint(4.0 * 3.14159265358979323846 * h->cfg.bjerrum * zref * PSI_SCALE);
-#define LBM_CHARGE_S(SS)                                                        \
-  LBM_DISPATCH_WS(h, (k_charge<SS, W_, ST_><<<nb, ct, 0, h->st>>>(               \
+  // the charged species, packed
+  int csi[4] = {0, 0, 0, 0};
+  float cval[4] = {0.f, 0.f, 0.f, 0.f}, cref[4] = {1.f, 1.f, 1.f, 1.f};
+  int nc = 0;
+  for (int s = 0; s < h->S; ++s)
+    if (h->valence[s] != 0.f) {
+      csi[nc] = s;
+      cval[nc] = h->valence[s];
+      cref[nc] = h->nref[s];
+      ++nc;
+    }
+  const int4 cs4 = make_int4(csi[0], csi[1], csi[2], csi[3]);
+  const float4 cv4 = make_float4(cval[0], cval[1], cval[2], cval[3]);
+  const float4 cr4 = make_float4(cref[0], cref[1], cref[2], cref[3]);
+#define LBM_CHARGE_S(NC)                                                        \
+  LBM_DISPATCH_WS(h, (k_charge<NC, W_, ST_><<<nb, ct, 0, h->st>>>(               \
                          h->f[h->cur], h->links, h->wsrc, h->ps.src, h->ps.part, \
                          h->ps.label, h->ps.comp_sum,                            \
                          h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,                  \
-                         as_f4(h->valence), as_f4(h->nref), k, src_ref)))
-  switch (h->S) {
+                         cs4, cv4, cr4, k, src_ref)))
+  switch (nc) {
+    case 0: LBM_CHARGE_S(0); break;
     case 1: LBM_CHARGE_S(1); break;
     case 2: LBM_CHARGE_S(2); break;
     case 3: LBM_CHARGE_S(3); break;
@@ -872,10 +898,18 @@ cudaError_t launch_gather(lbm_t* h, int s, double* n_dev, double* u_dev,
 
 cudaError_t launch_diagnostics(lbm_t* h) {
   const int nb = (int)std::min<int64_t>(nblocks(h->N, 256), h->grid_cap);
-  LBM_DISPATCH_WS(h, (k_diag<W_, ST_><<<nb, 256, 0, h->st>>>(
-                         h->f[h->cur], h->links, h->cfg.nx, h->cfg.ny,
-                         h->cfg.nz, h->N, h->S, as_f4(h->valence),
-                         as_f4(h->nref), h->dred, h->dflag)));
+#define LBM_DIAG_S(SS)                                                         \
+  LBM_DISPATCH_WS(h, (k_diag<SS, W_, ST_><<<nb, 256, 0, h->st>>>(               \
+                         h->f[h->cur], h->links, h->cfg.nx, h->cfg.ny,         \
+                         h->cfg.nz, h->N, as_f4(h->valence),                   \
+                         as_f4(h->nref), h->dred, h->dflag)))
+  switch (h->S) {
+    case 1: LBM_DIAG_S(1); break;
+    case 2: LBM_DIAG_S(2); break;
+    case 3: LBM_DIAG_S(3); break;
+    default: LBM_DIAG_S(4); break;
+  }
+#undef LBM_DIAG_S
   ++h->launches;
   return cudaGetLastError();
 }
