@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--poisson", default="fft", choices=["mg", "sor", "fft"])
     ap.add_argument("--no-alt", action="store_true", help="skip the multigrid comparison run")
-    ap.add_argument("--only", choices=["batched", "learned", "slit", "conductivity"], default=None,
+    ap.add_argument("--only", choices=["batched", "learned", "slit", "conductivity", "slit_transport"], default=None,
                     help="run one extra measurement alone and print it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-slit and learned-guess measurements")
@@ -402,6 +402,68 @@ def run_conductivity(lbm, WL, n=64, local=0):
             "runs": out}
 
 
+def slit_theory(e, sigma, debye, width, nu):
+    """Helmholtz-Smoluchowski mass flow and Debye-Hueckel convective current
+    of a slit of `width` fluid planes (h = width / 2), wall charge `sigma`
+    per wall node, k = 1 / debye (unit density, derived from the model:
+    u_x = E (psi - psi_w) / (4 pi l_B nu), psi = psi_w cosh(k z) / cosh(k h),
+    psi_w = 4 pi l_B sigma / (k tanh(k h)))."""
+    k, h = 1.0 / debye, 0.5 * width
+    kh = k * h
+    im = (e * sigma / nu) * (2.0 / k ** 2) * (1.0 - kh / math.tanh(kh))
+    ieo = -(e * sigma ** 2 / (nu * k * math.tanh(kh) ** 2)) * (
+        (kh + 0.5 * math.sinh(2 * kh)) / math.cosh(kh) ** 2 - 2.0 * math.tanh(kh))
+    return im, ieo
+
+
+def run_slit_transport(lbm, WL, local=0, relax=20000):
+    """Slit transport sweep (Sec. 4, Figs. of I_m, I, I_eo against
+    lambda_D / L_z and omega_drag): 32 x 8 x (50 + 2 walls), wall charge
+    -1e-4 per wall node (the paper's Sigma Lx Ly = -0.04 on a 40 x 10 wall),
+    field 1e-4 along x, lambda_D / L_z = 0.4, 0.2, 0.1, Sc = 1, 10, 100, 1000.
+    The double layer is formed at Sc = 1 (ion diffusion over lambda_D^2 / D
+    is 10^3 times slower at Sc = 1000); each Sc then sets the drag frequency
+    of every plane and runs `relax` steps (flow: L^2 / (pi^2 nu) ~ 1500 steps
+    per e-fold; drift: |1 - omega_drag| per step) before the currents are
+    read.  The steady state does not depend on the path."""
+    import torch
+    from paper_1507_04891_gb300 import transport
+    W, sigma, e = 50, -1e-4, 1e-4
+    nu = (1.0 / 3.0) * (1.0 / 1.0 - 0.5)
+    out = []
+    for ratio in (0.4, 0.2, 0.1):
+        debye = ratio * W
+        wl = WL.slit(nx=32, ny=8, width=W, sigma=sigma, debye=debye, e_field=e, schmidt=1.0)
+        lat = lbm.Lattice(32, 8, W + 2, 3, omega_drag=lbm.omega_drag_for_schmidt(1.0, 1.0),
+                          bjerrum=wl.bjerrum, e_ext=wl.e_ext, poisson="fft", step_graph=True,
+                          device=local)
+        lat.set_walls(wl.solid, wl.sigma)
+        for s in range(3):
+            lat.set_species(s, 1.0, wl.valence[s], np.where(wl.solid, 1.0, wl.n0[s]))
+        im_th, ieo_th = slit_theory(e, sigma, debye, W, nu)
+        for sc in (1.0, 10.0, 100.0, 1000.0):
+            od = lbm.omega_drag_for_schmidt(1.0, sc)
+            lat.set_plane_omega_drag(np.full(W + 2, od))
+            st = torch.cuda.ExternalStream(lat.stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            lat.step(relax)
+            e1.record(st)
+            lat.synchronize()
+            ms = e0.elapsed_time(e1)
+            c = transport.slit_currents(lat, wl.valence, e, od, wl.solid)
+            c.update({"lambda_D_over_Lz": ratio, "sc": sc, "omega_drag": od,
+                      "I_m_theory_HS": im_th, "I_m_over_theory": c["I_m"] / im_th,
+                      "I_eo_theory_DH": ieo_th, "I_eo_over_theory": c["I_eo"] / ieo_th,
+                      "value": 3 * wl.sites * relax / (ms / 1e3) / 1e6,
+                      "poisson_residual_last": lat.diagnostics()["poisson_residual"]})
+            out.append(c)
+        lat.destroy()
+    return {"workload": "slit 32x8x(50+2), sigma -1e-4 per wall node, E 1e-4, %d steps per Sc "
+                        "after the Sc = 1 run" % relax, "runs": out}
+
+
 def run_slit(lbm, WL, steps=2000, local=0):
     """Charged slit 64x64x(64 + 2 walls), wall charge -0.01 per node, Debye
     length 8, field 1e-4 along x: FP32, FP16 and BF16 storage at Sc 1 ... 1000
@@ -622,6 +684,8 @@ def main():
             res = run_batched(lbm, WL, steps=max(1, args.steps))
         elif args.only == "slit":
             res = run_slit(lbm, WL, steps=max(1, args.steps))
+        elif args.only == "slit_transport":
+            res = run_slit_transport(lbm, WL)
         elif args.only == "conductivity":
             res = run_conductivity(lbm, WL, n=args.n if args.n != 128 else 64)
         else:
