@@ -533,8 +533,9 @@ def run_ours(args, rank, world, local):
     od = lbm.omega_drag_for_schmidt(wl.omega_visc, args.schmidt)
     warm = max(3, args.warmup)
 
-    def make(poisson, graph=False):
-        return lbm.Lattice(n, n, n, S, omega_visc=wl.omega_visc, omega_drag=od, bjerrum=wl.bjerrum,
+    def make(poisson, graph=False, omega_drag=None):
+        return lbm.Lattice(n, n, n, S, omega_visc=wl.omega_visc,
+                           omega_drag=od if omega_drag is None else omega_drag, bjerrum=wl.bjerrum,
                            storage=args.storage, poisson=poisson, poisson_tol=1e-8,
                            poisson_maxit=500, device=local, step_graph=graph)
 
@@ -545,10 +546,10 @@ def run_ours(args, rank, world, local):
     def max_over_ranks(x):
         return replicas.max_over_ranks(x, world, device="cuda")
 
-    def timed(poisson, sample_clocks, graph=False):
+    def timed(poisson, sample_clocks, graph=False, omega_drag=None):
         """W warm-up steps, then K steps timed with CUDA events on the
         library's stream; phase times from the library's own events."""
-        lat = make(poisson, graph)
+        lat = make(poisson, graph, omega_drag)
         for s in range(S):
             lat.set_species(s, 1.0, wl.valence[s], wl.n0[s])
         stream = torch.cuda.ExternalStream(lat.stream, device=torch.device("cuda", local))
@@ -603,6 +604,16 @@ def run_ours(args, rank, world, local):
         alt = {"poisson": "mg", "value": world * S * N * args.steps / (ta / 1e3) / 1e6,
                "ms_per_step": ta / args.steps, "poisson_iters_per_step": tma["poisson_iters"] / args.steps,
                "poisson_ms_per_step": tma["poisson_ms"] / args.steps}
+
+    # the survey's second Schmidt number of the same configuration
+    sc100 = None
+    if args.schmidt == 1.0 and not args.no_alt:
+        od100 = lbm.omega_drag_for_schmidt(wl.omega_visc, 100.0)
+        t100, tm100, _, _ = timed(args.poisson, False, graph=graph_head, omega_drag=od100)
+        sc100 = {"sc": 100.0, "omega_drag": od100,
+                 "value": world * S * N * args.steps / (t100 / 1e3) / 1e6,
+                 "ms_per_step": t100 / args.steps,
+                 "poisson_iters_per_step": tm100["poisson_iters"] / args.steps}
 
     batched = learned = None
     if rank == 0 and world == 1 and not args.no_extras:
@@ -660,6 +671,7 @@ def run_ours(args, rank, world, local):
                     "h2d_bytes_per_step": 8 * S * N / args.steps,
                     "d2h_bytes_per_step": 8 * (S + 7)},
             "poisson_alternative": alt,
+            "sc100": sc100,
             "host_steps": host_run,
             "batched": batched,
             "learned_vs_plain": learned,
