@@ -189,9 +189,9 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
       cudaMemset(h->f[k], 0, pops);
     }
   }
-  if (s == LBM_OK) s = dev_alloc(h, &h->dred, MAX_SPECIES + 8);
+  if (s == LBM_OK) s = dev_alloc(h, &h->dred, (MAX_SPECIES + 4) * DIAG_SPREAD);
   if (s == LBM_OK) s = dev_alloc(h, &h->dflag, 1);
-  if (s == LBM_OK && cudaMallocHost(&h->hred, (MAX_SPECIES + 8) * sizeof(double)) != cudaSuccess)
+  if (s == LBM_OK && cudaMallocHost(&h->hred, (MAX_SPECIES + 4) * DIAG_SPREAD * sizeof(double)) != cudaSuccess)
     s = LBM_ENOMEM;
   if (s == LBM_OK && c.bjerrum > 0.0) {
     s = dev_alloc(h, &h->ps.psi[0], N);
@@ -583,15 +583,21 @@ lbm_status lbm_diagnostics(lbm_t* h, double* out) {
   if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set first");
   cudaSetDevice(h->dev);
   h->st = h->own;  // calls without a stream argument use the library's stream
-  LBM_CUDA_TRY(h, cudaMemsetAsync(h->dred, 0, (MAX_SPECIES + 8) * sizeof(double), h->st));
+  LBM_CUDA_TRY(h, cudaMemsetAsync(h->dred, 0, (MAX_SPECIES + 4) * DIAG_SPREAD * sizeof(double), h->st));
   LBM_CUDA_TRY(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->st));
   LBM_CUDA_TRY(h, launch_diagnostics(h));
-  LBM_CUDA_TRY(h, cudaMemcpyAsync(h->hred, h->dred, (MAX_SPECIES + 4) * sizeof(double),
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(h->hred, h->dred, (MAX_SPECIES + 4) * DIAG_SPREAD * sizeof(double),
                                   cudaMemcpyDeviceToHost, h->st));
   int bad = 0;
   LBM_CUDA_TRY(h, cudaMemcpyAsync(&bad, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
-  // the kernel sums deviations from n_ref; the reference parts are exact
+  // the kernel sums deviations from n_ref into DIAG_SPREAD partials per
+  // quantity; the reference parts are exact
+  for (int k = 0; k < MAX_SPECIES + 4; ++k) {
+    double t = 0.0;
+    for (int j = 0; j < DIAG_SPREAD; ++j) t += h->hred[k * DIAG_SPREAD + j];
+    h->hred[k] = t;
+  }
   const int S = h->S;
   const double nf = (double)h->nfluid;
   double zref = 0.0;

@@ -14,6 +14,8 @@ namespace lbm_gb300 {
 
 constexpr int Q = 19;
 constexpr int MAX_SPECIES = 4;
+// partial slots per diagnostics quantity (k_diag)
+constexpr int DIAG_SPREAD = 64;
 
 // Potential psi is held on the device as a signed 64-bit fixed-point number
 // with 52 fractional bits: psi = k * 2^-52 (|psi| < 2^11 = 2048, far beyond
@@ -165,7 +167,7 @@ struct lbm {
   lbm_gb300::SpectralPlan* spec = nullptr;  // spectral Poisson plan (LBM_POISSON_FFT)
   lbm_gb300::NNet* nn = nullptr;            // learned Poisson initial guess
   bool psi_valid = false;
-  double* dred = nullptr;   // diagnostics reduction buffer (device)
+  double* dred = nullptr;   // diagnostics partials, (MAX_SPECIES + 4) x DIAG_SPREAD (device)
   double* hred = nullptr;   // pinned mirror
   int* dflag = nullptr;
   int last_iters = 0;

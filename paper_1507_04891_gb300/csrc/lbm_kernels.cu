@@ -603,11 +603,14 @@ __global__ void k_gather(const void* fin_v, const uint32_t* links, int s,
 // Diagnostics: per species the sum over fluid nodes of dn = n - n_ref, the
 // total momentum and the net charge of the deviations (the host adds the
 // reference parts n_ref x fluid nodes, exactly); flags non-finite or
-// non-positive densities.  Deviations are summed per thread and per warp in
-// FP32 (they are small next to the reference part, so their rounding is far
-// below the FP64 resolution of the total), then per CTA in FP64 with one
-// FP64 atomic per CTA and quantity.  out layout: [0, MAX_SPECIES) dn per
-// species, then momentum x, y, z, then charge.
+// non-positive densities.  One node per thread, all species' loads in
+// flight; deviations summed per warp in FP32 (they are small next to the
+// reference part, so their rounding is far below the FP64 resolution of the
+// total), per CTA in FP64, and added to one of DIAG_SPREAD partial slots per
+// quantity (slot b mod DIAG_SPREAD for CTA b: FP64 atomics of thousands of
+// CTAs on one address queue).  out layout: quantity k in
+// [k * DIAG_SPREAD, (k + 1) * DIAG_SPREAD), k < MAX_SPECIES: dn per species,
+// then momentum x, y, z, then charge.
 template <int S, bool WALLS, int ST>
 __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
                                               const uint32_t* links, int nx,
@@ -615,12 +618,14 @@ __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
                                               float4 val, float4 nref,
                                               double* out, int* bad) {
   using T = typename Fmt<ST>::T;
-  float acc[MAX_SPECIES + 4];
-  for (int k = 0; k < MAX_SPECIES + 4; ++k) acc[k] = 0.f;
+  constexpr int NQ = MAX_SPECIES + 4;
+  float acc[NQ];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) acc[k] = 0.f;
   const float vz[4] = {val.x, val.y, val.z, val.w};
   const float nr[4] = {nref.x, nref.y, nref.z, nref.w};
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)N;
-       i += gridDim.x * blockDim.x) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < (uint32_t)N) {
     uint32_t lk = 0;
     bool fluid = true;
     if (WALLS) {
@@ -632,18 +637,22 @@ __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
       site_xyz(i, nx, ny, x, y, z);
       const Nbr o = neighbours(x, y, z, nx, ny, nz);
       const T* fin = static_cast<const T*>(fin_v);
-      // S is a template parameter: acc stays in registers and the loads of
-      // all species are issued together
+      float v[S][Q];
+#pragma unroll
+      for (int p = 0; p < Q; ++p) {
+        const int d = upstream(o, p);
+#pragma unroll
+        for (int s = 0; s < S; ++s) v[s][p] = pull<ST, WALLS>(fin, N, s, p, i, d, lk, nr[s]);
+      }
 #pragma unroll
       for (int s = 0; s < S; ++s) {
         float m0 = 0, mx = 0, my = 0, mz = 0;
 #pragma unroll
         for (int p = 0; p < Q; ++p) {
-          const float v = pull<ST, WALLS>(fin, N, s, p, i, upstream(o, p), lk, nr[s]);
-          m0 += v;
-          mx += CX(p) * v;
-          my += CY(p) * v;
-          mz += CZ(p) * v;
+          m0 += v[s][p];
+          mx += CX(p) * v[s][p];
+          my += CY(p) * v[s][p];
+          mz += CZ(p) * v[s][p];
         }
         if (!(nr[s] + m0 > 0.f) || !isfinite(m0) || !isfinite(mx) || !isfinite(my) ||
             !isfinite(mz))
@@ -656,18 +665,19 @@ __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
       }
     }
   }
-  __shared__ double red[8][MAX_SPECIES + 4];
-  for (int k = 0; k < MAX_SPECIES + 4; ++k) {
+  __shared__ double red[8][NQ];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
     float v = acc[k];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = (double)v;
   }
   __syncthreads();
-  if (threadIdx.x < MAX_SPECIES + 4) {
+  if (threadIdx.x < NQ) {
     double tot = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w][threadIdx.x];
-    atomicAdd(out + threadIdx.x, tot);
+    atomicAdd(out + threadIdx.x * DIAG_SPREAD + (blockIdx.x & (DIAG_SPREAD - 1)), tot);
   }
 }
 
@@ -897,7 +907,7 @@ cudaError_t launch_gather(lbm_t* h, int s, double* n_dev, double* u_dev,
 }
 
 cudaError_t launch_diagnostics(lbm_t* h) {
-  const int nb = (int)std::min<int64_t>(nblocks(h->N, 256), h->grid_cap);
+  const int nb = (int)nblocks(h->N, 256);
 #define LBM_DIAG_S(SS)                                                         \
   LBM_DISPATCH_WS(h, (k_diag<SS, W_, ST_><<<nb, 256, 0, h->st>>>(               \
                          h->f[h->cur], h->links, h->cfg.nx, h->cfg.ny,         \
