@@ -168,6 +168,13 @@ struct lbm {
   lbm_gb300::NNet* nn = nullptr;            // learned Poisson initial guess
   bool psi_valid = false;
   double* dred = nullptr;   // diagnostics partials, (MAX_SPECIES + 4) x DIAG_SPREAD (device)
+  // set by the spectral plan when the fluid is one periodic run: the charge
+  // kernel's partial sum writes the source mean of every plane there, and
+  // sets charge_means_ready for the next solve (which consumes it)
+  long long* charge_mean_z = nullptr;
+  bool charge_means_ready = false;
+  // step counter advanced by the charge path while graph steps are captured
+  uint32_t* charge_step = nullptr;
   double* hred = nullptr;   // pinned mirror
   int* dflag = nullptr;
   int last_iters = 0;
@@ -190,6 +197,7 @@ struct lbm {
   void* hstatus = nullptr;        // pinned mirror
   int graph_kernels_fixed = 0;    // kernels per step outside the Poisson loop
   int graph_kernels_iter = 0;     // kernels per Poisson iteration
+  int graph_kernels_redo = 0;     // kernels of the stream/collide run again after the loop
   std::vector<int> instance_z0;   // first plane of each stacked instance
   int charge_threads = 256;       // CTA size of the charge kernel (autotuned)  // kernels launched since timing was (re)set
   std::string err;

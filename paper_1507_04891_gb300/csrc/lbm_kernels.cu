@@ -534,10 +534,16 @@ __global__ void __launch_bounds__(256) k_charge(
 
 // Sums the per-CTA partials of k_charge into *out exactly in 128-bit
 // integers (FP64 arithmetic is slow on this GPU), converted to FP64 once.
+// When mean_z is given (one periodic run of fluid planes), the source mean
+// over the fluid, rounded to the fixed-point grid, is written to its nz
+// planes; when step is given, the step counter of the graph steps is
+// advanced (both save a launch per step).
 __global__ void __launch_bounds__(1024) k_sum_partials(const long long* part, int n,
-                                                       double* out) {
+                                                       double* out, long long* mean_z, int nz,
+                                                       double inv_nfluid, uint32_t* step) {
   __shared__ long long red_hi[32];
   __shared__ unsigned long long red_lo[32];
+  __shared__ long long s_mean;
   __int128 v = 0;
 #pragma unroll 8
   for (int k = threadIdx.x; k < n; k += blockDim.x) v += (__int128)part[k];
@@ -556,7 +562,14 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const long long* part, in
     __int128 tot = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
       tot += ((__int128)red_hi[w] << 64) | (__int128)red_lo[w];
-    *out = (double)tot;
+    const double t = (double)tot;
+    *out = t;
+    s_mean = llrint(t * inv_nfluid);
+    if (step) *step += 1u;
+  }
+  if (mean_z) {
+    __syncthreads();
+    for (int z = threadIdx.x; z < nz; z += blockDim.x) mean_z[z] = s_mean;
   }
 }
 
@@ -886,7 +899,12 @@ cudaError_t launch_charge(lbm_t* h) {
     default: LBM_CHARGE_S(4); break;
   }
 #undef LBM_CHARGE_S
-  k_sum_partials<<<1, 1024, 0, h->st>>>(h->ps.part, nb, h->ps.dsum);
+  // the spectral solver's source mean for one periodic run is written here;
+  // the solve then skips its own mean kernel once (charge_means_ready)
+  long long* mz = h->charge_mean_z;
+  k_sum_partials<<<1, 1024, 0, h->st>>>(h->ps.part, nb, h->ps.dsum, mz, h->cfg.nz,
+                                        1.0 / (double)h->nfluid, h->charge_step);
+  h->charge_means_ready = mz != nullptr;
   h->launches += 2;
   if (h->ps.label) {
     k_comp_means<<<1, 256, 0, h->st>>>(h->ps.dsum, h->ps.comp_sum, h->ps.comp_size,

@@ -849,6 +849,8 @@ void spectral_free(lbm_t* h) {
   cudaFree(s->r);
   cudaFree(s->psum);
   cudaFree(s->mean_z);
+  h->charge_mean_z = nullptr;
+  h->charge_means_ready = false;
   cudaFree(s->nacc);
   if (s->hacc) cudaFreeHost(s->hacc);
   delete s;
@@ -998,6 +1000,8 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   // (without walls yet the plan is provisional: set_walls rebuilds it)
   if (s->runs_fit && s->lgz < 0 && s->zsmem > 48 * 1024)
     LBM_CUDA_TRY(h, cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->zsmem));
+  h->charge_mean_z = (s->nruns == 1 && s->nplanes == nz) ? s->mean_z : nullptr;
+  h->charge_means_ready = false;
   s->plane_smem = (size_t)s->ppc * plane_smem_words(nx, ny) * sizeof(float2);
   if ((int)s->plane_smem > optin - 256) {
     h->err = "spectral Poisson solver: x-y plane too large for shared memory";
@@ -1077,8 +1081,12 @@ cudaError_t spec_means(lbm_t* h) {
   SpectralPlan* s = h->spec;
   Poisson& P = h->ps;
   if (s->nruns == 1 && (int)s->nplanes == s->nz) {
-    // one periodic run: the mean over all fluid, already summed by the
-    // source kernel
+    // one periodic run: the mean over all fluid, written by the charge
+    // path's partial sum, or here from its total
+    if (h->charge_means_ready) {
+      h->charge_means_ready = false;
+      return cudaSuccess;
+    }
     k_global_mean<<<1, 256, 0, h->st>>>(P.dsum, 1.0 / (double)h->nfluid, s->mean_z, s->nz);
     ++h->launches;
     return cudaGetLastError();
@@ -1236,10 +1244,12 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
 
 // ---------------------------------------------------------------------------
 // Whole-step CUDA graphs.  One graph per population parity holds a full time
-// step: charge density, run means, the number of spectral applications the
-// host path predicts (k), the final residual and its test, a device-side
-// while loop (conditional graph node) of [application, residual, test] for
-// a step that needs more, and the fused stream/collide.  The graphs are
+// step: charge density, run means, k spectral applications, then side by
+// side the fused stream/collide on that potential and the final residual
+// with its test; a device-side while loop (conditional graph node) of
+// [application, residual, test] for a step that needs more, and an if node
+// that runs the stream/collide again on the refined potential (it writes
+// the spare lattice, so running it twice is harmless).  The graphs are
 // rebuilt when the applications steps need change (k from the distribution
 // of the previous call's steps).
 // Steps are replayed back to back with no host round trip; the test kernel
@@ -1259,11 +1269,12 @@ struct GraphStatus {
 
 // Convergence test (one warp).  first: after the k applications queued
 // unconditionally (norm slots 0..k hold the residual before each and after
-// the last); records how many a step needed.  Otherwise after one more
-// application (slot k).  Sets the condition of the enclosing while node.
+// the last); records how many a step needed and sets `redo` when the loop
+// will run.  Otherwise after one more application (slot k).  Sets the
+// condition of the while node.
 __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, double tol,
                               double floor2, int maxit, int k, int first,
-                              cudaGraphConditionalHandle cond) {
+                              cudaGraphConditionalHandle cond, cudaGraphConditionalHandle redo) {
   if (blockIdx.x != 0) return;
   const int lane = threadIdx.x;
   // lane i < k + 1 tests slot i
@@ -1283,14 +1294,15 @@ __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, do
   const double rnk = __shfl_sync(0xffffffffu, rn2, k), snk = __shfl_sync(0xffffffffu, sn2, k);
   if (lane != 0) return;
   const bool conv = (convmask >> k) & 1u;
-  if (first) {
+  if (first)
     st->iters = k;
-    st->step += 1;
-  } else {
+  else
     st->iters += 1;
-  }
   const bool more = !conv && st->iters < maxit;
   cudaGraphSetConditional(cond, more ? 1u : 0u);
+  // the stream/collide ran beside this test on the potential after k
+  // applications: it runs again after the loop when the loop runs
+  if (first) cudaGraphSetConditional(redo, more ? 1u : 0u);
   st->rel = snk > 0.0 ? sqrt(rnk / snk) : 0.0;
   if (first && convmask) st->need[min(max(1, __ffs(convmask) - 1), 4) - 1] += 1;
   if (!more) {
@@ -1312,7 +1324,6 @@ void spectral_graph_free(lbm_t* h) {
 namespace {
 
 lbm_status build_step_graph(lbm_t* h, int parity) {
-  Poisson& P = h->ps;
   const int saved_cur = h->cur;
   h->cur = parity;
   GraphStatus* gs = reinterpret_cast<GraphStatus*>(h->gstatus);
@@ -1321,90 +1332,128 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
   const int maxit = h->cfg.poisson_maxit;
   cudaGraph_t G = nullptr;
   LBM_CUDA_TRY(h, cudaGraphCreate(&G, 0));
-  cudaGraphConditionalHandle cond;
+  cudaGraphConditionalHandle cond, redo;
   LBM_CUDA_TRY(h, cudaGraphConditionalHandleCreate(&cond, G, 0, cudaGraphCondAssignDefault));
+  LBM_CUDA_TRY(h, cudaGraphConditionalHandleCreate(&redo, G, 0, cudaGraphCondAssignDefault));
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  cudaStream_t main = h->st, side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
   const int64_t l0 = h->launches;
-  // part A: source, means, the predicted number k of applications (each
-  // records the norms of the residual it transforms), the final residual
-  // and the test
+  int64_t lc = 0;  // launches of the stream/collide
+  // part A: source (advancing the step counter), means, the predicted
+  // number k of applications (each records the norms of the residual it
+  // transforms); then, side by side, the stream/collide on that potential
+  // and the final residual with the test
   const int k = h->spec->graph_k;
-  LBM_CUDA_TRY(h, cudaStreamBeginCaptureToGraph(h->st, G, nullptr, nullptr, 0, mode));
-  cudaError_t e = cudaMemsetAsync(P.dsum, 0, 3 * sizeof(double), h->st);
-  if (e == cudaSuccess) e = launch_charge(h);
-  if (e == cudaSuccess) e = spec_means(h);
-  for (int i = 0; i < k && e == cudaSuccess; ++i) e = spec_apply(h, i);
-  if (e == cudaSuccess) e = spec_residual(h, k, false);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(main, G, nullptr, nullptr, 0, mode);
   if (e == cudaSuccess) {
-    k_graph_check<<<1, 32, 0, h->st>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 1, cond);
-    ++h->launches;
-    e = cudaGetLastError();
-  }
-  std::vector<cudaGraphNode_t> deps;
-  if (e == cudaSuccess) {
-    cudaStreamCaptureStatus cs;
-    const cudaGraphNode_t* d = nullptr;
-    size_t nd = 0;
-    e = cudaStreamGetCaptureInfo(h->st, &cs, nullptr, nullptr, &d, nullptr, &nd);
-    if (e == cudaSuccess) deps.assign(d, d + nd);
-  }
-  cudaGraph_t Gc = nullptr;
-  cudaError_t e2 = cudaStreamEndCapture(h->st, &Gc);
-  if (e == cudaSuccess) e = e2;
-  // the conditional while node and its body
-  cudaGraphNode_t cnode = nullptr;
-  cudaGraph_t body = nullptr;
-  if (e == cudaSuccess) {
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    e = cudaGraphAddNode(&cnode, G, deps.data(), nullptr, deps.size(), &cp);
-    if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
-  }
-  const int64_t l1 = h->launches;
-  if (e == cudaSuccess) {
-    e = cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, mode);
+    h->charge_step = &gs->step;
+    cudaError_t ec = launch_charge(h);
+    h->charge_step = nullptr;
+    if (ec == cudaSuccess) ec = spec_means(h);
+    for (int i = 0; i < k && ec == cudaSuccess; ++i) ec = spec_apply(h, i);
+    if (ec == cudaSuccess) ec = cudaEventRecord(fork, main);
+    if (ec == cudaSuccess) ec = cudaStreamWaitEvent(side, fork, 0);
+    if (ec == cudaSuccess) {
+      const int64_t a = h->launches;
+      h->st = side;
+      ec = launch_stream_collide(h);
+      h->st = main;
+      lc = h->launches - a;
+    }
+    if (ec == cudaSuccess) ec = cudaEventRecord(join, side);
+    if (ec == cudaSuccess) ec = spec_residual(h, k, false);
+    if (ec == cudaSuccess) {
+      k_graph_check<<<1, 32, 0, main>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 1, cond, redo);
+      ++h->launches;
+      ec = cudaGetLastError();
+    }
+    if (ec == cudaSuccess) ec = cudaStreamWaitEvent(main, join, 0);
+    std::vector<cudaGraphNode_t> deps;
+    if (ec == cudaSuccess) {
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t* d = nullptr;
+      size_t nd = 0;
+      ec = cudaStreamGetCaptureInfo(main, &cs, nullptr, nullptr, &d, nullptr, &nd);
+      if (ec == cudaSuccess) deps.assign(d, d + nd);
+    }
+    cudaGraph_t Gc = nullptr;
+    e = cudaStreamEndCapture(main, &Gc);
+    if (e == cudaSuccess) e = ec;
+    // the conditional while node: one more application, its residual, the test
+    cudaGraphNode_t cnode = nullptr;
+    cudaGraph_t body = nullptr;
     if (e == cudaSuccess) {
-      // one more application and its residual
-      cudaError_t eb = spec_apply(h, 0);
-      if (eb == cudaSuccess) eb = spec_residual(h, k, false);
-      if (eb == cudaSuccess) {
-        k_graph_check<<<1, 32, 0, h->st>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 0, cond);
-        ++h->launches;
-        eb = cudaGetLastError();
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&cnode, G, deps.data(), nullptr, deps.size(), &cp);
+      if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    const int64_t l1 = h->launches;
+    if (e == cudaSuccess) {
+      e = cudaStreamBeginCaptureToGraph(main, body, nullptr, nullptr, 0, mode);
+      if (e == cudaSuccess) {
+        cudaError_t eb = spec_apply(h, 0);
+        if (eb == cudaSuccess) eb = spec_residual(h, k, false);
+        if (eb == cudaSuccess) {
+          k_graph_check<<<1, 32, 0, main>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 0, cond,
+                                            redo);
+          ++h->launches;
+          eb = cudaGetLastError();
+        }
+        cudaGraph_t bb = nullptr;
+        e = cudaStreamEndCapture(main, &bb);
+        if (e == cudaSuccess) e = eb;
       }
-      cudaGraph_t bb = nullptr;
-      e = cudaStreamEndCapture(h->st, &bb);
-      if (e == cudaSuccess) e = eb;
     }
-  }
-  const int64_t l2 = h->launches;
-  // part B: fused stream/collide after the loop
-  if (e == cudaSuccess) {
-    e = cudaStreamBeginCaptureToGraph(h->st, G, &cnode, nullptr, 1, mode);
+    const int64_t l2 = h->launches;
+    // the conditional if node: the stream/collide again, on the potential
+    // the loop refined
+    cudaGraphNode_t inode = nullptr;
+    cudaGraph_t ibody = nullptr;
     if (e == cudaSuccess) {
-      cudaError_t eb = launch_stream_collide(h);
-      cudaGraph_t gg = nullptr;
-      e = cudaStreamEndCapture(h->st, &gg);
-      if (e == cudaSuccess) e = eb;
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = redo;
+      cp.conditional.type = cudaGraphCondTypeIf;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&inode, G, &cnode, nullptr, 1, &cp);
+      if (e == cudaSuccess) ibody = cp.conditional.phGraph_out[0];
     }
+    if (e == cudaSuccess) {
+      e = cudaStreamBeginCaptureToGraph(main, ibody, nullptr, nullptr, 0, mode);
+      if (e == cudaSuccess) {
+        cudaError_t eb = launch_stream_collide(h);
+        cudaGraph_t gg = nullptr;
+        e = cudaStreamEndCapture(main, &gg);
+        if (e == cudaSuccess) e = eb;
+      }
+    }
+    h->graph_kernels_fixed = (int)(l1 - l0);
+    h->graph_kernels_iter = (int)(l2 - l1);
+    h->graph_kernels_redo = (int)lc;
   }
-  const int64_t l3 = h->launches;
   h->launches = l0;
   h->cur = saved_cur;
+  h->st = main;
   cudaGraphExec_t ex = nullptr;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, G, 0);
   cudaGraphDestroy(G);
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
+  if (side) cudaStreamDestroy(side);
   if (e != cudaSuccess) {
     cudaGetLastError();
     h->err = std::string("step graph construction failed: ") + cudaGetErrorString(e);
     return LBM_ECUDA;
   }
   h->step_graph[parity] = ex;
-  h->graph_kernels_fixed = (int)((l1 - l0) + (l3 - l2));
-  h->graph_kernels_iter = (int)(l2 - l1);
   return LBM_OK;
 }
 
@@ -1476,8 +1525,12 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
     // the body of the while node ran once per application beyond the k
     // baked into every step
+    // steps that needed more than k ran the while loop and the stream/collide again
+    int redo_steps = 0;
+    for (int j = sp->graph_k; j < 4; ++j) redo_steps += hs->need[j];
     h->launches += (int64_t)n * h->graph_kernels_fixed +
-                   (hs->total - tot_before - (long long)n * sp->graph_k) * h->graph_kernels_iter;
+                   (hs->total - tot_before - (long long)n * sp->graph_k) * h->graph_kernels_iter +
+                   (int64_t)redo_steps * h->graph_kernels_redo;
     // decide once at least 64 steps have been seen (across chunks and calls)
     for (int j = 0; j < 4; ++j) sp->need_acc[j] += hs->need[j];
     const int tot = sp->need_acc[0] + sp->need_acc[1] + sp->need_acc[2] + sp->need_acc[3];
