@@ -142,3 +142,31 @@ def test_stack_rejects_mismatched_instances():
             lbm.make_config(16, 8, 8, 3, bjerrum=0.5, poisson="fft")]
     with pytest.raises(lbm.LBMError):
         lbm.Lattice(16, 8, 16, 3, _stack=cfgs)
+
+
+def test_step_graph_with_steps_needing_more_applications_than_baked():
+    """The step graph bakes k applications and runs the stream/collide beside
+    the final test; a step that needs more runs the while loop and the
+    stream/collide again.  A standalone solve capped at one application
+    primes the prediction to k = 1 while the steps need two: the graph path
+    must still equal the host-driven one."""
+    wl = WL.ternary_bulk(shape=(12, 16, 32), seed=36, spread=3e-3)
+    od = lbm.omega_drag_for_schmidt(1.0, 3.0)
+    rho0 = (wl.valence[:, None, None, None] * wl.n0).sum(0)
+    lats = []
+    for graph in (False, True):
+        lat = lbm.Lattice(32, 16, 12, 3, omega_drag=od, bjerrum=0.7, poisson="fft",
+                          step_graph=graph)
+        for s in range(3):
+            lat.set_species(s, 1.0, wl.valence[s], wl.n0[s])
+        lat.solve_poisson(rho0, tol=1e-8, maxit=1)    # one application: k = 1 next
+        lats.append(lat)
+    lats[0].step(20)
+    assert lats[1].step(20) == lbm.LBM_OK
+    d = lats[1].diagnostics()
+    assert d["steps"] == 20 and d["poisson_residual"] <= 1e-8 and d["poisson_iters"] >= 2
+    for s in range(3):
+        a, ua = lats[0].get_moments(s)
+        b, ub = lats[1].get_moments(s)
+        assert np.abs(a - b).max() <= 1e-7 * np.abs(a).max()
+        assert np.abs(a * ua - b * ub).max() <= 1e-9
