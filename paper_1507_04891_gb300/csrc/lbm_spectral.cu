@@ -12,7 +12,7 @@
 // run is tridiagonal (walls at both ends: one open face there) or cyclic
 // (a run that is the whole periodic z axis).  One application solves the
 // problem to FP32 accuracy; it is used for defect correction on the exact
-// fixed-point residual, so two applications usually reach 1e-8.
+// fixed-point residual: one or two applications reach 1e-8.
 //
 // One application is three kernels:
 //   k_plane_fwd  one CTA per fluid plane (or several small planes): the
