@@ -101,6 +101,81 @@ def kernel_traffic(storage="fp32"):
         return None
 
 
+class NvmlClockSampler:
+    """SM clock and throttle reasons read through NVML (the driver's
+    libnvidia-ml, via ctypes; read-only queries) every 2 ms from a thread
+    while the timed steps run, so that even a 30 ms timed window holds
+    samples.  Bits of the reasons mask from the public nvml.h: SW power cap
+    0x4, HW slowdown 0x8, SW thermal 0x20, HW thermal 0x40."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, index=0):
+        import ctypes
+        import threading
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint(0)
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, ctypes.c_int(1), ctypes.byref(mx))
+        self.max_mhz = float(mx.value)
+        self.rows = []
+        self.t0 = self.t1 = None
+        self.stop_flag = threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        ct = self.ct
+        clk, bits = ct.c_uint(0), ct.c_ulonglong(0)
+        while not self.stop_flag.is_set():
+            t = time.time()
+            ok = self.lib.nvmlDeviceGetClockInfo(self.h, ct.c_int(1), ct.byref(clk)) == 0
+            ok = ok and self.reasons_fn(self.h, ct.byref(bits)) == 0
+            if ok:
+                self.rows.append((t, float(clk.value), int(bits.value)))
+            time.sleep(0.002)
+
+    def start(self):
+        self.thread.start()
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    def stop(self):
+        self.stop_flag.set()
+        self.thread.join(timeout=5)
+        try:
+            self.lib.nvmlShutdown()
+        except Exception:
+            pass
+        inside = [r for r in self.rows if self.t0 is not None and self.t1 is not None
+                  and self.t0 <= r[0] <= self.t1]
+        if not inside:
+            return None
+        reasons = sorted({n for r in inside for b, n in self.REASONS.items() if r[2] & b})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(inside), "source": "nvml",
+                "window_s": round(self.t1 - self.t0, 3)}
+
+
+def clock_sampler(index=0):
+    """NVML sampler when the driver library loads, else nvidia-smi."""
+    try:
+        return NvmlClockSampler(index)
+    except Exception:
+        return ClockSampler(index)
+
+
 class ClockSampler:
     """nvidia-smi samples (every 50 ms, timestamped) of the SM clock and the
     throttle reasons; stop() keeps the samples taken inside the window given
@@ -181,7 +256,7 @@ class ClockSampler:
                 inside = [min(rows, key=lambda r: abs(r[0] - mid))]
         reasons = sorted({n for r in inside for n in r[3]})
         return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": inside[-1][2],
-                "reasons": reasons, "samples": len(inside),
+                "reasons": reasons, "samples": len(inside), "source": "nvidia-smi",
                 "window_s": None if self.t0 is None or self.t1 is None else round(self.t1 - self.t0, 3)}
 
 
@@ -555,7 +630,7 @@ def run_ours(args, rank, world, local):
         stream = torch.cuda.ExternalStream(lat.stream, device=torch.device("cuda", local))
         lat.step(warm)
         lat.synchronize()
-        clocks = ClockSampler(local) if sample_clocks else None
+        clocks = clock_sampler(local) if sample_clocks else None
         barrier()
         lat.set_timing(True)
         if clocks:
