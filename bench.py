@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -190,7 +191,7 @@ class ClockSampler:
     def __init__(self, index=0):
         self.proc = None
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        self.path = os.path.join(tempfile.gettempdir(), "lbm_bench_clocks_%d.csv" % os.getpid())
         self.t0 = self.t1 = None
 
     def start(self):
