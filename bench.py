@@ -44,7 +44,7 @@ BYTES_PER_SPECIES_SITE = {"fp32": 152, "fp16": 76, "bf16": 76}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    # the survey's C2 protocol: 100 timed steps after 10 warm-up steps (the
+    # the benchmark's protocol: 100 timed steps after 10 warm-up steps (the
     # bulk charge relaxes over the run; later steps need fewer Poisson
     # applications, so longer runs would flatter the rate)
     ap.add_argument("--steps", type=int, default=100)
@@ -681,7 +681,7 @@ def run_ours(args, rank, world, local):
                "ms_per_step": ta / args.steps, "poisson_iters_per_step": tma["poisson_iters"] / args.steps,
                "poisson_ms_per_step": tma["poisson_ms"] / args.steps}
 
-    # the survey's second Schmidt number of the same configuration
+    # the benchmark's second Schmidt number, Sc = 100, same configuration
     sc100 = None
     if args.schmidt == 1.0 and not args.no_alt:
         od100 = lbm.omega_drag_for_schmidt(wl.omega_visc, 100.0)
