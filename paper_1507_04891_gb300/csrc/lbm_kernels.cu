@@ -69,7 +69,13 @@ struct Fmt<LBM_FP32> {
   using T = float;
   static __device__ __forceinline__ float ld(const T* p, float wn) { return wn * (1.0f + *p); }
   static __device__ __forceinline__ float ldd(const T* p, float wn) { return wn * *p; }
+  static __device__ __forceinline__ float ldh(const T* p) { return *p; }
   static __device__ __forceinline__ void st(T* p, float d, float inv_wn) { *p = d * inv_wn; }
+  static __device__ __forceinline__ void sth_sr(T* p, float h, uint32_t) { *p = h; }
+  static __device__ __forceinline__ void sth_sr2(T* pa, float ha, T* pb, float hb, uint32_t) {
+    *pa = ha;
+    *pb = hb;
+  }
   static __device__ __forceinline__ void st_sr(T* p, float d, float inv_wn, uint32_t) {
     *p = d * inv_wn;
   }
@@ -106,6 +112,16 @@ struct Fmt<LBM_FP16_SHIFT> {
     return wn * (1.0f + __half2float(*p));
   }
   static __device__ __forceinline__ float ldd(const T* p, float wn) { return wn * __half2float(*p); }
+  static __device__ __forceinline__ float ldh(const T* p) { return __half2float(*p); }
+  static __device__ __forceinline__ void sth_sr(T* p, float h, uint32_t rnd) {
+    const uint32_t v = cvt_rs_f16x2(h, 0.0f, rnd);
+    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(v >> 16);
+  }
+  static __device__ __forceinline__ void sth_sr2(T* pa, float ha, T* pb, float hb, uint32_t rnd) {
+    const uint32_t v = cvt_rs_f16x2(ha, hb, rnd);
+    *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(v >> 16);
+    *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(v & 0xFFFFu);
+  }
   static __device__ __forceinline__ void st(T* p, float d, float inv_wn) {
     *p = __float2half_rn(d * inv_wn);
   }
@@ -128,6 +144,16 @@ struct Fmt<LBM_BF16_SHIFT> {
   }
   static __device__ __forceinline__ float ldd(const T* p, float wn) {
     return wn * __bfloat162float(*p);
+  }
+  static __device__ __forceinline__ float ldh(const T* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void sth_sr(T* p, float h, uint32_t rnd) {
+    const uint32_t v = cvt_rs_bf16x2(h, 0.0f, rnd);
+    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(v >> 16);
+  }
+  static __device__ __forceinline__ void sth_sr2(T* pa, float ha, T* pb, float hb, uint32_t rnd) {
+    const uint32_t v = cvt_rs_bf16x2(ha, hb, rnd);
+    *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(v >> 16);
+    *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(v & 0xFFFFu);
   }
   static __device__ __forceinline__ void st(T* p, float d, float inv_wn) {
     *p = __float2bfloat16_rn(d * inv_wn);
@@ -204,6 +230,19 @@ __device__ __forceinline__ float pull(const typename Fmt<ST>::T* __restrict__ f,
     idx = ((lk >> p) & 1u) ? bb : idx;
   }
   return Fmt<ST>::ldd(f + idx, wn);
+}
+
+// Pulls the stored h_p = d_p / (w_p n_ref) (same addressing as pull).
+template <int ST, bool WALLS>
+__device__ __forceinline__ float pull_h(const typename Fmt<ST>::T* __restrict__ f,
+                                        int64_t N, int s, int p, uint32_t i, int d,
+                                        uint32_t lk) {
+  int64_t idx = (int64_t)(s * Q + p) * N + (int64_t)((int)i + d);
+  if (WALLS) {
+    const int64_t bb = (int64_t)(s * Q + OPP(p)) * N + i;
+    idx = ((lk >> p) & 1u) ? bb : idx;
+  }
+  return Fmt<ST>::ldh(f + idx);
 }
 
 __device__ __forceinline__ void site_xyz(uint32_t i, int nx, int ny, int& x,
@@ -307,34 +346,37 @@ __global__ void __launch_bounds__(256) k_stream_collide(const StepArgs a) {
   T* __restrict__ fout = static_cast<T*>(a.fout);
   const int64_t N = a.N;
 
-  // deviations d_p = f_p - w_p n_ref of every species
+  // stored h_p = (f_p - w_p n_ref) / (w_p n_ref) of every species
   float f[S][Q];
 #pragma unroll
   for (int p = 0; p < Q; ++p) {
     const int d = upstream(o, p);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      f[s][p] = pull<ST, WALLS>(fin, N, s, p, i, d, lk, a.nref[s]);
+      f[s][p] = pull_h<ST, WALLS>(fin, N, s, p, i, d, lk);
     }
   }
 
-  // n = n_ref + dn (sum w_p = 1), j = sum c_p d_p (sum w_p c_p = 0)
-  float dn[S], n[S], jx[S], jy[S], jz[S];
+  // n = n_ref (1 + sum w h), j = n_ref sum c w h  (sum w = 1, sum w c = 0)
+  float mh[S], dn[S], n[S], jx[S], jy[S], jz[S];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     float m0 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
 #pragma unroll
     for (int p = 0; p < Q; ++p) {
-      m0 += f[s][p];
-      if (CX(p)) mx += CX(p) * f[s][p];
-      if (CY(p)) my += CY(p) * f[s][p];
-      if (CZ(p)) mz += CZ(p) * f[s][p];
+      const float wh = WT(p) * f[s][p];
+      m0 += wh;
+      if (CX(p)) mx += CX(p) * wh;
+      if (CY(p)) my += CY(p) * wh;
+      if (CZ(p)) mz += CZ(p) * wh;
     }
-    dn[s] = m0;
-    n[s] = a.nref[s] + m0;
-    jx[s] = mx;
-    jy[s] = my;
-    jz[s] = mz;
+    const float r = a.nref[s];
+    mh[s] = m0;
+    dn[s] = r * m0;
+    n[s] = r + dn[s];
+    jx[s] = r * mx;
+    jy[s] = r * my;
+    jz[s] = r * mz;
   }
 
   float ntot = 0.f, Jx = 0.f, Jy = 0.f, Jz = 0.f;
@@ -385,14 +427,18 @@ __global__ void __launch_bounds__(256) k_stream_collide(const StepArgs a) {
     //                          + 4.5 omega a^2 + 9 (F.c)(u.c))]      (even in c)
     //     + w_p n 3 (omega a + F.c)                                 (odd in c)
     // a = u^a.c (phi_perp in its reduced form, the Appendix expression;
-    // g_p of Eq. ourforc).  Every term is of the size of the deviations.
+    // g_p of Eq. ourforc).  Divided by w_p n_ref this updates the stored
+    // h = d / (w_p n_ref) directly: h*_p = (1 - omega) h_p + (even' +/- odd') / n_ref,
+    // with the bracket values even', odd' free of w_p.  Every term is of
+    // the size of the deviations.
     const float base = n[s] * (-1.5f * om * usq - 3.0f * Fu);
     const float odn = om * dn[s];
     const float inr = 1.0f / a.nref[s];
     // moving populations first; the rest population then takes
-    // d*_0 = dn - sum_{p>0} d*_p, which holds exactly in real arithmetic
-    // (phi_perp carries mass n, g_p none) and keeps FP32 rounding of the
-    // weights from drifting the species mass.
+    // d*_0 = dn - sum_{p>0} d*_p, i.e. h*_0 = (sum w h - sum_{p>0} w h*_p) / w_0,
+    // which holds exactly in real arithmetic (phi_perp carries mass n,
+    // g_p none) and keeps FP32 rounding of the weights from drifting the
+    // species mass.
     // Directions come in opposite pairs (p, p+1), c_{p+1} = -c_p: a = u^a.c,
     // F.c and u.c flip sign, so each pair shares the even part and takes
     // +/- the odd part.
@@ -403,16 +449,15 @@ __global__ void __launch_bounds__(256) k_stream_collide(const StepArgs a) {
       const float av = CX(p) * usx + CY(p) * usy + CZ(p) * usz;
       const float fc = CX(p) * Fx + CY(p) * Fy + CZ(p) * Fz;
       const float uc = CX(p) * ux + CY(p) * uy + CZ(p) * uz;
-      const float w = WT(p);  // same weight for p and p+1
-      const float even = w * (odn + base + n[s] * (4.5f * om * av * av + 9.0f * fc * uc));
-      const float odd = w * n[s] * 3.0f * (om * av + fc);
-      const float da = omm * f[s][p] + (even + odd);
-      const float db = omm * f[s][p + 1] + (even - odd);
-      moved += da + db;
-      Fmt<ST>::st_sr2(fout + (int64_t)(s * Q + p) * N + i, da, fout + (int64_t)(s * Q + p + 1) * N + i,
-                      db, INV_WT(p) * inr, lcg_next(rnd));
+      const float even = inr * (odn + base + n[s] * (4.5f * om * av * av + 9.0f * fc * uc));
+      const float odd = inr * n[s] * 3.0f * (om * av + fc);
+      const float ha = omm * f[s][p] + (even + odd);
+      const float hb = omm * f[s][p + 1] + (even - odd);
+      moved += WT(p) * (ha + hb);  // same weight for p and p+1
+      Fmt<ST>::sth_sr2(fout + (int64_t)(s * Q + p) * N + i, ha,
+                       fout + (int64_t)(s * Q + p + 1) * N + i, hb, lcg_next(rnd));
     }
-    Fmt<ST>::st_sr(fout + (int64_t)(s * Q) * N + i, dn[s] - moved, INV_WT(0) * inr, lcg_next(rnd));
+    Fmt<ST>::sth_sr(fout + (int64_t)(s * Q) * N + i, (mh[s] - moved) * INV_WT(0), lcg_next(rnd));
   }
 }
 
