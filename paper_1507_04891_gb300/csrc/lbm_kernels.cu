@@ -330,7 +330,7 @@ __device__ __forceinline__ void block_sum_to(long long v, double* out) {
 //   5. store f* at r.
 // ---------------------------------------------------------------------------
 template <int S, bool WALLS, bool CHARGED, int ST>
-__global__ void __launch_bounds__(256) k_stream_collide(const StepArgs a) {
+__global__ void __launch_bounds__(256, WALLS ? 2 : 1) k_stream_collide(const StepArgs a) {
   using T = typename Fmt<ST>::T;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (uint32_t)a.N) return;
