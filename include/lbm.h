@@ -81,9 +81,12 @@ typedef struct {
 } lbm_config;
 
 /* LBM_FLAG_STEP_GRAPH: every time step (charge density, spectral Poisson
- * solve in a device-side loop, stream/collide) is one CUDA graph replay, with
- * no host round trip between steps.  Needs LBM_POISSON_FFT and l_B > 0.
- * Per-phase timings (lbm_get_timing) then cover whole steps only.         */
+ * solve with a device-side loop for extra applications, stream/collide) is
+ * one CUDA graph replay; the host reads a small status after every 128
+ * steps (and at the end of each lbm_step call) to report failures and to
+ * adapt the number of applications baked into the graphs.  Needs
+ * LBM_POISSON_FFT and l_B > 0.  Per-phase timings (lbm_get_timing) then
+ * cover whole steps only.                                                 */
 #define LBM_FLAG_STEP_GRAPH 1
 
 /* Fills *cfg with defaults: omega_visc = 1, omega_drag = 1, l_B = 0,
