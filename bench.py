@@ -11,6 +11,8 @@ instead).  Metric: species-site MLUPS (S * N * steps / time / 1e6), with
 the stream/collide kernel's fraction of the measured HBM roofline and the
 Poisson iterations per step.  A host-stepped run of the same workload
 gives the per-phase CUDA-event times (phase_ms_per_step, host_steps).
+Each spectral solve starts from the extrapolation of the three previous
+potentials (--no-extrapolation: from the previous one).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -62,6 +64,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--host-steps", action="store_true",
                     help="headline with host-driven steps instead of CUDA-graph steps")
+    ap.add_argument("--no-extrapolation", action="store_true",
+                    help="spectral solves start from the previous potential, not its "
+                         "extrapolation in time")
     return ap.parse_args()
 
 
@@ -613,7 +618,8 @@ def run_ours(args, rank, world, local):
         return lbm.Lattice(n, n, n, S, omega_visc=wl.omega_visc,
                            omega_drag=od if omega_drag is None else omega_drag, bjerrum=wl.bjerrum,
                            storage=args.storage, poisson=poisson, poisson_tol=1e-8,
-                           poisson_maxit=500, device=local, step_graph=graph)
+                           poisson_maxit=500, device=local, step_graph=graph,
+                           extrapolate=not args.no_extrapolation)
 
     def barrier():
         replicas.barrier(world)
@@ -729,6 +735,8 @@ def run_ours(args, rank, world, local):
             "config": {"workload": "ternary_bulk_%d^3" % n, "species": S, "sc": args.schmidt,
                        "omega_visc": wl.omega_visc, "omega_drag": od, "bjerrum": wl.bjerrum,
                        "poisson": args.poisson, "poisson_tol": 1e-8, "storage": args.storage,
+                       "poisson_start": ("previous psi" if args.no_extrapolation or args.poisson != "fft"
+                                         else "3 psi(t-1) - 3 psi(t-2) + psi(t-3)"),
                        "l2": "not flushed: inputs larger than L2 (2 x %.0f MB population lattices)"
                              % (BYTES_PER_SPECIES_SITE[args.storage] / 2 * S * N / 1e6),
                        "steps": "cuda_graph" if graph_head else "host",

@@ -82,12 +82,22 @@ typedef struct {
 
 /* LBM_FLAG_STEP_GRAPH: every time step (charge density, spectral Poisson
  * solve with a device-side loop for extra applications, stream/collide) is
- * one CUDA graph replay; the host reads a small status after every 128
+ * one CUDA graph replay; the host reads a small status after every 32
  * steps (and at the end of each lbm_step call) to report failures and to
  * adapt the number of applications baked into the graphs.  Needs
  * LBM_POISSON_FFT and l_B > 0.  Per-phase timings (lbm_get_timing) then
  * cover whole steps only.                                                 */
 #define LBM_FLAG_STEP_GRAPH 1
+
+/* LBM_FLAG_NO_EXTRAPOLATION: with the spectral solver, each step's solve
+ * starts from the previous step's potential.  Without the flag it starts
+ * from the extrapolation in time through the three previous potentials,
+ * 3 psi(t-1) - 3 psi(t-2) + psi(t-3) (fewer terms for the first steps after
+ * lbm_create, lbm_set_species, lbm_set_state or lbm_solve_poisson, which
+ * restart the history); the solve still iterates to poisson_tol.  Not
+ * applied while the learned guess is collecting or in use.  The paper
+ * has no counterpart: a property of this library's solver.              */
+#define LBM_FLAG_NO_EXTRAPOLATION 2
 
 /* Fills *cfg with defaults: omega_visc = 1, omega_drag = 1, l_B = 0,
  * FP32 storage, multigrid Poisson, tol 1e-8, maxit 200, device 0.        */

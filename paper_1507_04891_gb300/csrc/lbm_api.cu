@@ -433,7 +433,7 @@ lbm_status lbm_set_species(lbm_t* h, int s, double mass, double valence,
   h->species_set |= 1u << s;
   h->tstep = 0;
   h->psi_valid = false;
-  return LBM_OK;
+  return spectral_history_reset(h);
 }
 
 lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
@@ -464,6 +464,10 @@ lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
       int it = 0;
       double rel = 0.0;
       Phase pp(h, 1);
+      if (h->spec) {
+        lbm_status se = spectral_step_start(h);
+        if (se != LBM_OK) return se;
+      }
       s = poisson_solve(h, h->cfg.poisson_tol, h->cfg.poisson_maxit, &it, &rel);
       LBM_CUDA_TRY(h, pp.stop());
       h->t_cnt[1] += it;
@@ -572,6 +576,8 @@ lbm_status lbm_solve_poisson(lbm_t* h, const double* rho_e, double* psi,
   if (iters) *iters = it;
   if (rel_res) *rel_res = rel;
   if (s != LBM_OK && s != LBM_ENOCONV) return s;
+  const lbm_status sr = spectral_history_reset(h);
+  if (sr != LBM_OK) return sr;
   LBM_CUDA_TRY(h, launch_psi_to_double(h, h->ps.psi[h->ps.cur], dpsi));
   LBM_CUDA_TRY(h, cudaMemcpyAsync(psi, dpsi, N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
@@ -638,7 +644,7 @@ lbm_status lbm_set_state(lbm_t* h, const float* state, int64_t step) {
                                   cudaMemcpyHostToDevice, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   h->tstep = step;
-  return LBM_OK;
+  return spectral_history_reset(h);
 }
 
 lbm_status lbm_create_stack(int count, const lbm_config* cfgs, lbm_t** out) {

@@ -237,6 +237,11 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters,
 // device status once at the end.
 lbm_status spectral_graph_steps(lbm_t* h, int nsteps);
 void spectral_graph_free(lbm_t* h);
+// Host-driven steps: psi <- its extrapolation from the previous steps
+// before the step's solve (LBM_FLAG_NO_EXTRAPOLATION off, no learned guess).
+lbm_status spectral_step_start(lbm_t* h);
+// Restarts the potential history (psi was set from outside the steps).
+lbm_status spectral_history_reset(lbm_t* h);
 
 // ---- lbm_nn.cu ----
 lbm_status nn_init(lbm_t* h, int hidden, uint64_t seed);

@@ -801,6 +801,35 @@ __global__ void __launch_bounds__(256, 4) k_res_planes(
   add_norms(acc, rr, ss, red_r, red_s);
 }
 
+// Start of a step's solve: psi(t-1) is replaced by its extrapolation in
+// time, 3 psi(t-1) - 3 psi(t-2) + psi(t-3) (the parabola through the three
+// previous potentials), or 2 psi(t-1) - psi(t-2) and psi(t-1) while the
+// history fills (`order` valid entries, read from *order_dev when given);
+// the history moves one step.  Exact in int64; a guess outside 2^61 fixed-
+// point units keeps psi(t-1).  Any start is valid: the solve iterates to the
+// same tolerance from it.  Two nodes per thread (N is even: nx >= 8).
+__device__ __forceinline__ int64_t extrapolate1(int64_t a, int64_t b, int64_t c, int order) {
+  if (order <= 0) return a;
+  const __int128 g = order == 1 ? (__int128)2 * a - b : (__int128)3 * ((__int128)a - b) + c;
+  const __int128 lim = (__int128)1 << 61;
+  return (g > lim || g < -lim) ? a : (int64_t)g;
+}
+
+__global__ void __launch_bounds__(256) k_extrapolate(int64_t* __restrict__ psi, int64_t* __restrict__ h1,
+                                                     int64_t* __restrict__ h2, int64_t npairs,
+                                                     const int* __restrict__ order_dev, int order) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npairs) return;
+  const int ord = order_dev ? min(*order_dev, 2) : order;
+  longlong2* P = reinterpret_cast<longlong2*>(psi);
+  longlong2* H1 = reinterpret_cast<longlong2*>(h1);
+  longlong2* H2 = reinterpret_cast<longlong2*>(h2);
+  const longlong2 a = P[i], b = H1[i], c = H2[i];
+  P[i] = make_longlong2(extrapolate1(a.x, b.x, c.x, ord), extrapolate1(a.y, b.y, c.y, ord));
+  H1[i] = a;
+  H2[i] = b;
+}
+
 int ilog2(int n) {
   int l = 0;
   while ((1 << l) < n) ++l;
@@ -831,6 +860,8 @@ struct SpectralPlan {
   bool status_read = false;        // the host copy of the graph status is current
   bool runs_fit = true;            // z solve fits in shared memory
   float* r = nullptr;              // N (residual for the learned guess)
+  int64_t* hist = nullptr;         // 2 N: psi one and two steps older than psi
+  int hist_n = 0;                  // valid entries of hist (host-driven steps)
   long long* psum = nullptr;       // nz
   long long* mean_z = nullptr;     // nz
   float* nacc = nullptr;           // norm slots, Poisson::NSLOT x 2 NACC
@@ -847,6 +878,7 @@ void spectral_free(lbm_t* h) {
   cudaFree(s->lam);
   cudaFree(s->spec);
   cudaFree(s->r);
+  cudaFree(s->hist);
   cudaFree(s->psum);
   cudaFree(s->mean_z);
   h->charge_mean_z = nullptr;
@@ -936,6 +968,7 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
             al((void**)&s->tw, ntw * sizeof(float2)) && al((void**)&s->lam, nlam * sizeof(float)) &&
             al((void**)&s->spec, (size_t)nz * s->mxy * sizeof(float2)) &&
             al((void**)&s->r, N * sizeof(float)) && al((void**)&s->psum, nz * sizeof(long long)) &&
+            al((void**)&s->hist, 2 * N * sizeof(int64_t)) &&
             al((void**)&s->mean_z, nz * sizeof(long long)) &&
             al((void**)&s->nacc, (size_t)Poisson::NSLOT * 2 * NACC * sizeof(float));
   if (ok && cudaMallocHost((void**)&s->hacc, (size_t)Poisson::NSLOT * 2 * NACC * sizeof(float)) != cudaSuccess) {
@@ -964,6 +997,7 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   for (int k = 0; k <= nx / 2; ++k) lam.push_back(eig(k, nx));
   for (int k = 0; k < ny; ++k) lam.push_back(eig(k, ny));
   for (int k = 0; k < nz; ++k) lam.push_back(eig(k, nz));
+  LBM_CUDA_TRY(h, cudaMemset(s->hist, 0, 2 * N * sizeof(int64_t)));
   LBM_CUDA_TRY(h, cudaMemcpy(s->planes, planes.data(), planes.size() * sizeof(int), cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->runs, runs.data(), runs.size() * sizeof(Run), cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->plane_fluid, pf.data(), nz, cudaMemcpyHostToDevice));
@@ -1147,7 +1181,34 @@ cudaError_t spec_apply(lbm_t* h, int slot) {
   return e == cudaSuccess ? spec_zinv(h) : e;
 }
 
+// psi <- its extrapolation from the previous steps (k_extrapolate); the
+// number of valid history entries comes from *order_dev (graph steps) or
+// from the host count, which advances here.
+cudaError_t spec_extrapolate(lbm_t* h, const int* order_dev) {
+  SpectralPlan* s = h->spec;
+  Poisson& P = h->ps;
+  const int64_t np = h->N / 2;
+  k_extrapolate<<<nblk(np, 256), 256, 0, h->st>>>(P.psi[P.cur], s->hist, s->hist + h->N, np, order_dev,
+                                                  s->hist_n);
+  ++h->launches;
+  if (!order_dev) s->hist_n = std::min(s->hist_n + 1, 2);
+  return cudaGetLastError();
+}
+
+bool extrapolation_on(const lbm_t* h) {
+  return !(h->cfg.flags & LBM_FLAG_NO_EXTRAPOLATION) && !nn_active(h);
+}
+
 }  // namespace
+
+lbm_status spectral_step_start(lbm_t* h) {
+  if (!extrapolation_on(h)) {
+    h->spec->hist_n = 0;
+    return LBM_OK;
+  }
+  LBM_CUDA_TRY(h, spec_extrapolate(h, nullptr));
+  return LBM_OK;
+}
 
 lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* rel_res) {
   SpectralPlan* s = h->spec;
@@ -1262,7 +1323,7 @@ struct GraphStatus {
   int iters;           // Poisson applications of the current step
   long long total;     // applications summed over replayed steps
   int fails;           // steps whose solve stopped at the iteration cap
-  int pad;
+  int hist;            // valid entries of the potential history (0..2)
   double rel;          // final relative residual of the last step
   int need[4];         // steps that needed 1, 2, 3, >= 4 applications since the host reset it
 };
@@ -1294,10 +1355,12 @@ __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, do
   const double rnk = __shfl_sync(0xffffffffu, rn2, k), snk = __shfl_sync(0xffffffffu, sn2, k);
   if (lane != 0) return;
   const bool conv = (convmask >> k) & 1u;
-  if (first)
+  if (first) {
     st->iters = k;
-  else
+    st->hist = min(st->hist + 1, 2);  // this step's potential joins the history
+  } else {
     st->iters += 1;
+  }
   const bool more = !conv && st->iters < maxit;
   cudaGraphSetConditional(cond, more ? 1u : 0u);
   // the stream/collide ran beside this test on the potential after k
@@ -1319,6 +1382,19 @@ void spectral_graph_free(lbm_t* h) {
     if (h->step_graph[k]) cudaGraphExecDestroy(h->step_graph[k]);
     h->step_graph[k] = nullptr;
   }
+}
+
+lbm_status spectral_history_reset(lbm_t* h) {
+  if (!h->spec) return LBM_OK;
+  h->spec->hist_n = 0;
+  if (h->gstatus) {
+    // no graph step is in flight: every lbm_step call with graph steps ends
+    // with a synchronisation
+    const int zero = 0;
+    LBM_CUDA_TRY(h, cudaMemcpy(&reinterpret_cast<GraphStatus*>(h->gstatus)->hist, &zero, sizeof zero,
+                               cudaMemcpyHostToDevice));
+  }
+  return LBM_OK;
 }
 
 namespace {
@@ -1343,15 +1419,17 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
   const int64_t l0 = h->launches;
   int64_t lc = 0;  // launches of the stream/collide
-  // part A: source (advancing the step counter), means, the predicted
-  // number k of applications (each records the norms of the residual it
+  // part A: the extrapolated starting potential, source (advancing the
+  // step counter), means, the predicted number k of applications (each records the norms of the residual it
   // transforms); then, side by side, the stream/collide on that potential
   // and the final residual with the test
   const int k = h->spec->graph_k;
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(main, G, nullptr, nullptr, 0, mode);
   if (e == cudaSuccess) {
+    cudaError_t ec = cudaSuccess;
+    if (!(h->cfg.flags & LBM_FLAG_NO_EXTRAPOLATION)) ec = spec_extrapolate(h, &gs->hist);
     h->charge_step = &gs->step;
-    cudaError_t ec = launch_charge(h);
+    if (ec == cudaSuccess) ec = launch_charge(h);
     h->charge_step = nullptr;
     if (ec == cudaSuccess) ec = spec_means(h);
     for (int i = 0; i < k && ec == cudaSuccess; ++i) ec = spec_apply(h, i);
@@ -1494,12 +1572,12 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
   const long long total0 = hs->total;
   const int fails0 = hs->fails;
   // Steps are replayed in chunks; the distribution of the applications the
-  // steps needed (accumulated over at least 64 steps) sets the number k
+  // steps needed (accumulated over at least CHUNK steps) sets the number k
   // baked into the graphs (rebuilt only when k changes).  A step needing more than k runs the
   // while loop, one application and one residual per extra application; an
   // application costs about four residuals, so k stays below the need of a
   // step unless more than 3/4 of the steps need more.
-  constexpr int CHUNK = 128;
+  constexpr int CHUNK = 32;
   int done = 0;
   while (done < nsteps) {
     const int pred = sp->graph_pred > 0 ? sp->graph_pred : sp->last_iters;
@@ -1531,17 +1609,17 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     h->launches += (int64_t)n * h->graph_kernels_fixed +
                    (hs->total - tot_before - (long long)n * sp->graph_k) * h->graph_kernels_iter +
                    (int64_t)redo_steps * h->graph_kernels_redo;
-    // decide once at least 64 steps have been seen (across chunks and calls)
+    // decide once at least CHUNK steps have been seen (across chunks and calls)
     for (int j = 0; j < 4; ++j) sp->need_acc[j] += hs->need[j];
     const int tot = sp->need_acc[0] + sp->need_acc[1] + sp->need_acc[2] + sp->need_acc[3];
-    if (tot >= 64 || (sp->graph_pred == 0 && tot > 0)) {
+    if (tot >= CHUNK || (sp->graph_pred == 0 && tot > 0)) {
       int k = 1, above = tot - sp->need_acc[0];
       while (k < 4 && 4 * above > 3 * tot) {
         above -= sp->need_acc[k];
         ++k;
       }
       sp->graph_pred = k;
-      if (tot >= 64)
+      if (tot >= CHUNK)
         for (int j = 0; j < 4; ++j) sp->need_acc[j] = 0;
     }
     done += n;

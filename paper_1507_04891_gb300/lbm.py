@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
                 4: "LBM_ENOCONV", 5: "LBM_EUNSTABLE", 6: "LBM_ETIMEOUT"}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 LBM_FLAG_STEP_GRAPH = 1
+LBM_FLAG_NO_EXTRAPOLATION = 2
 POISSON = {"mg": 0, "sor": 1, "fft": 2}
 
 # every symbol include/lbm.h declares
@@ -137,7 +138,7 @@ def load_library(path: str = LIB_PATH):
 
 def make_config(nx, ny, nz, nspecies, omega_visc=1.0, omega_drag=1.0, bjerrum=0.0,
                 e_ext=(0.0, 0.0, 0.0), storage="fp32", poisson="mg", poisson_tol=1e-8,
-                poisson_maxit=200, device=0, step_graph=False):
+                poisson_maxit=200, device=0, step_graph=False, extrapolate=True):
     lib = load_library()
     cfg = LbmConfig()
     lib.lbm_config_default(ctypes.byref(cfg))
@@ -148,7 +149,8 @@ def make_config(nx, ny, nz, nspecies, omega_visc=1.0, omega_drag=1.0, bjerrum=0.
     cfg.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     cfg.poisson = POISSON[poisson] if isinstance(poisson, str) else int(poisson)
     cfg.poisson_tol, cfg.poisson_maxit, cfg.device = float(poisson_tol), int(poisson_maxit), int(device)
-    cfg.flags = LBM_FLAG_STEP_GRAPH if step_graph else 0
+    cfg.flags = (LBM_FLAG_STEP_GRAPH if step_graph else 0) | \
+                (0 if extrapolate else LBM_FLAG_NO_EXTRAPOLATION)
     return cfg
 
 
@@ -169,10 +171,10 @@ class Lattice:
     def __init__(self, nx, ny, nz, nspecies, omega_visc=1.0, omega_drag=1.0,
                  bjerrum=0.0, e_ext=(0.0, 0.0, 0.0), storage="fp32", poisson="mg",
                  poisson_tol=1e-8, poisson_maxit=200, device=0, step_graph=False,
-                 _stack=None):
+                 extrapolate=True, _stack=None):
         self._lib = load_library()
         cfg = make_config(nx, ny, nz, nspecies, omega_visc, omega_drag, bjerrum, e_ext, storage,
-                          poisson, poisson_tol, poisson_maxit, device, step_graph)
+                          poisson, poisson_tol, poisson_maxit, device, step_graph, extrapolate)
         self.cfg = cfg
         self.S = int(nspecies)
         h = ctypes.c_void_p()
@@ -196,7 +198,8 @@ class Lattice:
                             kw.get("bjerrum", 0.0), kw.get("e_ext", (0.0, 0.0, 0.0)),
                             kw.get("storage", "fp32"), kw.get("poisson", "fft"),
                             kw.get("poisson_tol", 1e-8), kw.get("poisson_maxit", 200),
-                            kw.get("device", 0), kw.get("step_graph", False))
+                            kw.get("device", 0), kw.get("step_graph", False),
+                            kw.get("extrapolate", True))
                 for nz_i, od in zip(nzs, omega_drags)]
         return cls(nx, ny, sum(nzs), nspecies, _stack=cfgs)
 

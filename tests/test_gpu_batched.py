@@ -149,14 +149,15 @@ def test_step_graph_with_steps_needing_more_applications_than_baked():
     the final test; a step that needs more runs the while loop and the
     stream/collide again.  A standalone solve capped at one application
     primes the prediction to k = 1 while the steps need two: the graph path
-    must still equal the host-driven one."""
+    must still equal the host-driven one.  The solves start from the previous
+    potential (no extrapolation), so every step needs two."""
     wl = WL.ternary_bulk(shape=(12, 16, 32), seed=36, spread=3e-3)
     od = lbm.omega_drag_for_schmidt(1.0, 3.0)
     rho0 = (wl.valence[:, None, None, None] * wl.n0).sum(0)
     lats = []
     for graph in (False, True):
         lat = lbm.Lattice(32, 16, 12, 3, omega_drag=od, bjerrum=0.7, poisson="fft",
-                          step_graph=graph)
+                          step_graph=graph, extrapolate=False)
         for s in range(3):
             lat.set_species(s, 1.0, wl.valence[s], wl.n0[s])
         lat.solve_poisson(rho0, tol=1e-8, maxit=1)    # one application: k = 1 next
