@@ -82,7 +82,7 @@ typedef struct {
 
 /* LBM_FLAG_STEP_GRAPH: every time step (charge density, spectral Poisson
  * solve with a device-side loop for extra applications, stream/collide) is
- * one CUDA graph replay; the host reads a small status after every 32
+ * one CUDA graph replay; the host reads a small status after every 16
  * steps (and at the end of each lbm_step call) to report failures and to
  * adapt the number of applications baked into the graphs.  Needs
  * LBM_POISSON_FFT and l_B > 0.  Per-phase timings (lbm_get_timing) then

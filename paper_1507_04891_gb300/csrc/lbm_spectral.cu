@@ -1573,11 +1573,15 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
   const int fails0 = hs->fails;
   // Steps are replayed in chunks; the distribution of the applications the
   // steps needed (accumulated over at least CHUNK steps) sets the number k
-  // baked into the graphs (rebuilt only when k changes).  A step needing more than k runs the
-  // while loop, one application and one residual per extra application; an
-  // application costs about four residuals, so k stays below the need of a
-  // step unless more than 3/4 of the steps need more.
-  constexpr int CHUNK = 32;
+  // baked into the graphs (rebuilt only when k changes): the k of least
+  // expected cost per step.  A step costs its k applications; one that
+  // needs m > k also runs the while loop, m - k applications and residuals,
+  // and the stream/collide again.  In units of a residual an application
+  // costs about 4 and the stream/collide about 3.3 per FP32 species (3 per
+  // 16-bit one), all three streaming the lattice at similar rates.
+  constexpr int CHUNK = 16;
+  const double costA = 4.0, costR = 1.0;
+  const double costC = (h->cfg.storage == LBM_FP32 ? 3.3 : 3.0) * h->S;
   int done = 0;
   while (done < nsteps) {
     const int pred = sp->graph_pred > 0 ? sp->graph_pred : sp->last_iters;
@@ -1609,18 +1613,23 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     h->launches += (int64_t)n * h->graph_kernels_fixed +
                    (hs->total - tot_before - (long long)n * sp->graph_k) * h->graph_kernels_iter +
                    (int64_t)redo_steps * h->graph_kernels_redo;
-    // decide once at least CHUNK steps have been seen (across chunks and calls)
+    // decide from the steps since the last decision once there are at least
+    // CHUNK of them (across chunks and calls), or at the first chance
     for (int j = 0; j < 4; ++j) sp->need_acc[j] += hs->need[j];
     const int tot = sp->need_acc[0] + sp->need_acc[1] + sp->need_acc[2] + sp->need_acc[3];
     if (tot >= CHUNK || (sp->graph_pred == 0 && tot > 0)) {
-      int k = 1, above = tot - sp->need_acc[0];
-      while (k < 4 && 4 * above > 3 * tot) {
-        above -= sp->need_acc[k];
-        ++k;
+      int best = 1;
+      double best_cost = 0.0;
+      for (int k = 1; k <= 4; ++k) {
+        double c = costA * k * tot;
+        for (int j = k; j < 4; ++j) c += sp->need_acc[j] * ((j + 1 - k) * (costA + costR) + costC);
+        if (k == 1 || c < best_cost) {
+          best = k;
+          best_cost = c;
+        }
       }
-      sp->graph_pred = k;
-      if (tot >= CHUNK)
-        for (int j = 0; j < 4; ++j) sp->need_acc[j] = 0;
+      sp->graph_pred = best;
+      for (int j = 0; j < 4; ++j) sp->need_acc[j] = 0;
     }
     done += n;
     if (hs->fails != fails0) break;
