@@ -328,7 +328,7 @@ def run_reference(args, rank, world):
     return 0
 
 
-def run_batched(lbm, WL, steps=40, local=0):
+def run_batched(lbm, WL, steps=40, local=0, extrapolate=True):
     """Batched slit sweep (64 channels, widths U{16..128}, 32x32, Sc
     log-uniform 1..1000, wall charge U[-0.02,-0.002]) stacked in one lattice,
     FP16 storage, every step one CUDA-graph replay; compared with the same
@@ -338,18 +338,22 @@ def run_batched(lbm, WL, steps=40, local=0):
     insts = WL.batched_slits()
     S = 3
     sites = sum(int(np.prod(w.shape)) for w in insts)
-    lat, _ = lbm.stack_slits(insts, storage="fp16", step_graph=True, device=local)
+    lat, _ = lbm.stack_slits(insts, storage="fp16", step_graph=True, device=local,
+                             extrapolate=extrapolate)
     tune = lat.autotune()
     lat.step(3)
     lat.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.ExternalStream(lat.stream)
+    lat.set_timing(True)
     t0.record(stream)
     lat.step(steps)
     t1.record(stream)
     lat.synchronize()
     tb = t0.elapsed_time(t1)
+    iters = lat.get_timing()["poisson_iters"]
+    lat.set_timing(False)
     d = lat.diagnostics()
     lat.destroy()
     # plain: one FP32 lattice per channel, host-driven steps
@@ -377,6 +381,7 @@ def run_batched(lbm, WL, steps=40, local=0):
             "storage": "fp16", "step_graph": True, "autotune": tune,
             "value": S * sites * steps / (tb / 1e3) / 1e6, "unit": UNIT,
             "ms_per_step": tb / steps, "poisson_residual_last": d["poisson_residual"],
+            "poisson_iters_per_step": iters / steps, "extrapolated_start": extrapolate,
             "plain_fp32_sequential": {"value": S * sites * steps / (total / 1e3) / 1e6,
                                       "ms_per_step": total / steps},
             "speedup": total / tb}
@@ -699,7 +704,7 @@ def run_ours(args, rank, world, local):
 
     batched = learned = None
     if rank == 0 and world == 1 and not args.no_extras:
-        batched = run_batched(lbm, WL, local=local)
+        batched = run_batched(lbm, WL, local=local, extrapolate=not args.no_extrapolation)
         learned = run_learned(lbm, WL, local=local)
 
     # end to end through the C ABI with host buffers: initial state uploaded
@@ -777,7 +782,7 @@ def main():
         from paper_1507_04891_gb300.build import build_library
         build_library()
         if args.only == "batched":
-            res = run_batched(lbm, WL, steps=max(1, args.steps))
+            res = run_batched(lbm, WL, steps=max(1, args.steps), extrapolate=not args.no_extrapolation)
         elif args.only == "slit":
             res = run_slit(lbm, WL, steps=max(1, args.steps))
         elif args.only == "slit_transport":

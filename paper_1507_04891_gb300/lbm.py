@@ -395,7 +395,8 @@ def from_workload(wl, storage="fp32", poisson="mg", poisson_tol=1e-8, poisson_ma
     return lat
 
 
-def stack_slits(instances, storage="fp16", step_graph=True, poisson_tol=1e-8, device=0):
+def stack_slits(instances, storage="fp16", step_graph=True, poisson_tol=1e-8, device=0,
+                extrapolate=True):
     """Batched independent slit channels (workloads.slit instances sharing
     nx, ny, omega_visc, l_B and the applied field) stacked along z in one
     lattice: each instance keeps its own walls, wall charge and drag
@@ -407,7 +408,8 @@ def stack_slits(instances, storage="fp16", step_graph=True, poisson_tol=1e-8, de
     w0 = instances[0]
     lat = Lattice.create_stack(nx, ny, nzs, ods, w0.nspecies, omega_visc=w0.omega_visc,
                                bjerrum=w0.bjerrum, e_ext=w0.e_ext, storage=storage, poisson="fft",
-                               poisson_tol=poisson_tol, device=device, step_graph=step_graph)
+                               poisson_tol=poisson_tol, device=device, step_graph=step_graph,
+                               extrapolate=extrapolate)
     solid = np.concatenate([w.solid for w in instances], axis=0)
     sigma = np.concatenate([w.sigma for w in instances], axis=0)
     lat.set_walls(solid, sigma)
