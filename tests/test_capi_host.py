@@ -96,3 +96,30 @@ def test_config_layout_matches_c_compiler(tmp_path):
     assert int(out["size"]) == ctypes.sizeof(lbm.LbmConfig)
     for f in fields:
         assert int(out[f]) == getattr(lbm.LbmConfig, f).offset, f
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """Status codes, storage and solver codes and flag bits of the binding
+    are the values the C compiler sees in include/lbm.h."""
+    names = {"LBM_OK": lbm.LBM_OK, "LBM_EINVAL": lbm.LBM_EINVAL, "LBM_ENOMEM": lbm.LBM_ENOMEM,
+             "LBM_ECUDA": lbm.LBM_ECUDA, "LBM_ENOCONV": lbm.LBM_ENOCONV,
+             "LBM_EUNSTABLE": lbm.LBM_EUNSTABLE, "LBM_ETIMEOUT": lbm.LBM_ETIMEOUT,
+             "LBM_FP32": lbm.STORAGE["fp32"], "LBM_FP16_SHIFT": lbm.STORAGE["fp16"],
+             "LBM_BF16_SHIFT": lbm.STORAGE["bf16"], "LBM_POISSON_MG": lbm.POISSON["mg"],
+             "LBM_POISSON_SOR": lbm.POISSON["sor"], "LBM_POISSON_FFT": lbm.POISSON["fft"],
+             "LBM_FLAG_STEP_GRAPH": lbm.LBM_FLAG_STEP_GRAPH,
+             "LBM_FLAG_NO_EXTRAPOLATION": lbm.LBM_FLAG_NO_EXTRAPOLATION}
+    src = tmp_path / "consts.c"
+    body = "".join('printf("%s %%d\\n", (int)(%s));' % (n, n) for n in names)
+    src.write_text('#include <stdio.h>\n#include "lbm.h"\nint main(void){' + body + 'return 0;}\n')
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for n, v in names.items():
+        assert int(out[n]) == v, n
+    # flag bits are distinct powers of two
+    flags = [lbm.LBM_FLAG_STEP_GRAPH, lbm.LBM_FLAG_NO_EXTRAPOLATION]
+    assert all(f & (f - 1) == 0 for f in flags) and len(set(flags)) == len(flags)
+    cfg = lbm.make_config(8, 8, 8, 1, step_graph=True, extrapolate=False)
+    assert cfg.flags == lbm.LBM_FLAG_STEP_GRAPH | lbm.LBM_FLAG_NO_EXTRAPOLATION
