@@ -72,12 +72,13 @@ def test_graph_and_host_steps_agree_with_extrapolation():
     assert_same_moments(host, graph)
 
 
-def test_history_restarts_with_the_state():
+@pytest.mark.parametrize("graph", [False, True])
+def test_history_restarts_with_the_state(graph):
     """set_state puts back populations of an earlier step: the steps after it
     start from psi(t-1) again, then build up the history, and the run
     repeats the first one up to the round-off of the solves."""
     wl = WL.ternary_bulk(shape=SHAPE, seed=91, spread=3e-3)
-    lat = make(wl)
+    lat = make(wl, graph)
     lat.step(6)
     state, step = lat.get_state()
     lat.step(10)
@@ -90,3 +91,23 @@ def test_history_restarts_with_the_state():
         nb, ub = lat.get_moments(s)
         assert np.abs(a[s][0] - nb).max() <= 1e-7 * np.abs(nb).max()
         assert np.abs(a[s][0] * a[s][1] - nb * ub).max() <= 1e-9
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_history_restarts_after_a_standalone_solve(graph):
+    """solve_poisson replaces psi (and the source) from outside the steps:
+    the steps after it restart the history and reach the tolerance, on the
+    same trajectory as a lattice that never called it."""
+    wl = WL.ternary_bulk(shape=SHAPE, seed=93, spread=3e-3)
+    a, b = make(wl, graph), make(wl, graph)
+    a.step(8)
+    b.step(8)
+    rho = np.zeros(SHAPE)
+    psi, iters, res, st = b.solve_poisson(rho + 1e-3 * np.cos(2 * np.pi * np.arange(SHAPE[2]) / SHAPE[2]),
+                                          tol=1e-8)
+    assert st == lbm.LBM_OK and res <= 1e-8
+    a.step(12)
+    assert b.step(12) == lbm.LBM_OK
+    d = b.diagnostics()
+    assert d["steps"] == 20 and d["poisson_residual"] <= 1e-8 and not d["unstable"]
+    assert_same_moments(a, b)
