@@ -42,7 +42,9 @@ class Params:
 
     omega_visc : BGK frequency of the non-hydrodynamic modes, Eq. (dufty1).
     omega_drag : drag frequency, Sec. 2 ("omega_drag ... used to tune the
-                 diffusion coefficient").
+                 diffusion coefficient"); or a symmetric (S, S) matrix of
+                 pair frequencies omega^{alpha beta} for the general
+                 gamma^{alpha beta} of Sec. 2 (see pair_drag_frequencies).
     mass       : (S,) particle masses m^alpha (all equal on one lattice).
     valence    : (S,) z^alpha.
     bjerrum    : l_B of Eq. (Poisson); 0 switches the electrostatics off.
@@ -54,7 +56,8 @@ class Params:
     def __init__(self, omega_visc, omega_drag, mass, valence, bjerrum=0.0,
                  e_ext=(0.0, 0.0, 0.0), solid=None, sigma=None):
         self.omega_visc = float(omega_visc)
-        self.omega_drag = float(omega_drag)
+        od = np.asarray(omega_drag, dtype=np.float64)
+        self.omega_drag = float(od) if od.ndim == 0 else od.copy()
         self.mass = np.asarray(mass, dtype=np.float64)
         self.valence = np.asarray(valence, dtype=np.float64)
         self.bjerrum = float(bjerrum)
@@ -104,19 +107,43 @@ def barycentric_velocity(n, u, mass):
 # Forces (accelerations per particle), Sec. 2 drag force and Eq. (Poisson)
 # ---------------------------------------------------------------------------
 def drag_acceleration(n, u, omega_drag):
-    """F^{alpha,drag}/m = -omega_drag sum_beta (n_beta/n) (u^alpha - u^beta).
+    """F^{alpha,drag}/m = -sum_beta omega^{alpha beta} (n_beta/n) (u^alpha - u^beta).
 
-    Written as the literal double sum over the species pair (alpha, beta),
-    with n = sum_beta n_beta.
+    omega_drag is the paper's single drag frequency (Sec. 2, the equal-mass,
+    equal-diameter form gamma^{alpha beta} = omega_drag n_beta / n), or a
+    symmetric (S, S) matrix of pair frequencies (the general gamma^{alpha
+    beta} of Sec. 2 for equal masses, gamma^{alpha beta} = omega^{alpha
+    beta} n_beta / n).  Written as the literal double sum over the species
+    pair (alpha, beta), with n = sum_beta n_beta.
     """
     S = n.shape[0]
+    W = np.asarray(omega_drag, dtype=np.float64)
+    if W.ndim == 0:
+        W = np.full((S, S), float(W))
     ntot = n.sum(axis=0)
     safe = np.where(ntot != 0.0, ntot, 1.0)
     F = np.zeros_like(u)
     for a in range(S):
         for b in range(S):
-            F[a] += -omega_drag * (n[b] / safe)[None] * (u[a] - u[b])
+            F[a] += -W[a, b] * (n[b] / safe)[None] * (u[a] - u[b])
     return F
+
+
+def pair_drag_frequencies(diameters, n_total, g_contact=None, kT_over_m=None):
+    """omega^{alpha beta} of the general drag coefficient of Sec. 2 for
+    species of equal mass m and diameters sigma_alpha:
+    gamma^{alpha beta} = (8/3) sigma_ab^2 n_beta sqrt(k_B T / (pi m)) g_ab
+    with sigma_ab = (sigma_a + sigma_b)/2 and g_ab the pair correlation at
+    contact (the paper's expression with m_alpha = m_beta), written as
+    omega^{alpha beta} n_beta / n, so
+    omega^{alpha beta} = (8/3) sigma_ab^2 n sqrt(k_B T / (pi m)) g_ab.
+    k_B T / m defaults to v_T^2 of the lattice; g_ab to 1."""
+    d = np.asarray(diameters, dtype=np.float64)
+    S = d.size
+    g = np.ones((S, S)) if g_contact is None else np.asarray(g_contact, dtype=np.float64)
+    kt = CS2 if kT_over_m is None else float(kT_over_m)
+    sab = 0.5 * (d[:, None] + d[None, :])
+    return (8.0 / 3.0) * sab ** 2 * float(n_total) * np.sqrt(kt / np.pi) * g
 
 
 def drag_velocity(ua, Fel):
@@ -464,7 +491,8 @@ def omega_drag_for_schmidt(omega_visc, sc):
 
 __all__ = [
     "C", "Q", "W", "OPP", "CS2", "Params", "number_density", "species_velocity",
-    "barycentric_velocity", "drag_acceleration", "drag_velocity", "wall_face_charge",
+    "barycentric_velocity", "drag_acceleration", "pair_drag_frequencies", "drag_velocity",
+    "wall_face_charge",
     "wall_charge_per_cell", "poisson_matrix", "poisson_source", "fluid_components", "PoissonSolver",
     "potential_gradient", "electric_acceleration", "phi_perp", "forcing_term",
     "collide", "stream", "Oracle", "StepInfo",
