@@ -391,14 +391,16 @@ def run_learned(lbm, WL, n=64, steps=10, local=0):
     """Learned Poisson initial guess vs plain warm start, multigrid to 1e-8,
     on a charged ternary porous box (spheres radius 4..12, 20% solid,
     surface charge +/-0.01): the network is trained on the initial residuals
-    of 16 solver steps, then both arms run the same held-out steps from the
-    same state."""
+    of 16 solver steps, then three arms run the same held-out steps from the
+    same state: plain (each solve from the previous potential), learned
+    (the network's correction of that start), extrapolated (each solve from
+    the parabola through the three previous potentials, no network)."""
     wl = WL.porous_spheres(n=n, seed=1238)
     od = lbm.omega_drag_for_schmidt(1.0, 1.0)
 
-    def make():
+    def make(extrapolate=False):
         lat = lbm.Lattice(n, n, n, 3, omega_drag=od, bjerrum=0.7, poisson="mg", poisson_maxit=200,
-                          device=local)
+                          device=local, extrapolate=extrapolate)
         lat.set_walls(wl.solid, wl.sigma)
         for s in range(3):
             lat.set_species(s, 1.0, wl.valence[s], np.where(wl.solid, 1.0, wl.n0[s]))
@@ -417,20 +419,22 @@ def run_learned(lbm, WL, n=64, steps=10, local=0):
     psi = base.get_potential()
     base.destroy()
     out = {}
-    for use in (False, True):
-        lat = make()
+    # plain and learned start each solve from the previous potential; the
+    # third arm starts from its extrapolation in time (no network)
+    for use in (False, True, "extrapolated"):
+        lat = make(extrapolate=use == "extrapolated")
         lat.set_state(state, step)
         rho = lat.get_moments(1)[0] - lat.get_moments(2)[0]
         lat.solve_poisson(rho, psi, tol=1e-12)
-        if use:
+        if use is True:
             lat.nn_init(hidden=8, seed=3)
             lat.nn_params(params)
             lat.nn_use(True)
         lat.set_timing(True)
         lat.step(steps)
         tm = lat.get_timing()
-        st = lat.nn_stats() if use else None
-        out["learned" if use else "plain"] = {
+        st = lat.nn_stats() if use is True else None
+        out[{False: "plain", True: "learned"}.get(use, "extrapolated")] = {
             "poisson_iters_per_step": tm["poisson_iters"] / steps,
             "poisson_ms_per_step": tm["poisson_ms"] / steps,
             "residual_ratio_after_guess": st["mean_ratio"] if st else None,

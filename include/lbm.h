@@ -89,7 +89,7 @@ typedef struct {
  * cover whole steps only.                                                 */
 #define LBM_FLAG_STEP_GRAPH 1
 
-/* LBM_FLAG_NO_EXTRAPOLATION: with the spectral solver, each step's solve
+/* LBM_FLAG_NO_EXTRAPOLATION: each step's Poisson solve (every solver)
  * starts from the previous step's potential.  Without the flag it starts
  * from the extrapolation in time through the three previous potentials,
  * 3 psi(t-1) - 3 psi(t-2) + psi(t-3) (fewer terms for the first steps after

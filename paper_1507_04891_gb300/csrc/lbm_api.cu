@@ -197,6 +197,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     s = dev_alloc(h, &h->ps.psi[0], N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.psi[1], N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.src, N);
+    if (s == LBM_OK && c.poisson != LBM_POISSON_FFT) s = dev_alloc(h, &h->ps.hist, 2 * (size_t)N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.dsum, 1 + 2 * Poisson::NSLOT);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.part, (size_t)((N + 63) / 64));
     if (s == LBM_OK && cudaMallocHost(&h->ps.hsum, (1 + 2 * Poisson::NSLOT) * sizeof(double)) != cudaSuccess)
@@ -204,6 +205,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     if (s == LBM_OK) {
       cudaMemset(h->ps.psi[0], 0, N * sizeof(int64_t));
       cudaMemset(h->ps.psi[1], 0, N * sizeof(int64_t));
+      if (h->ps.hist) cudaMemset(h->ps.hist, 0, 2 * N * sizeof(int64_t));
       cudaMemset(h->ps.dsum, 0, (1 + 2 * Poisson::NSLOT) * sizeof(double));
       s = poisson_setup(h, nullptr);
       if (s == LBM_OK && c.poisson == LBM_POISSON_FFT) s = spectral_setup(h, nullptr);
@@ -433,7 +435,7 @@ lbm_status lbm_set_species(lbm_t* h, int s, double mass, double valence,
   h->species_set |= 1u << s;
   h->tstep = 0;
   h->psi_valid = false;
-  return spectral_history_reset(h);
+  return potential_history_reset(h);
 }
 
 lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
@@ -464,10 +466,8 @@ lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
       int it = 0;
       double rel = 0.0;
       Phase pp(h, 1);
-      if (h->spec) {
-        lbm_status se = spectral_step_start(h);
-        if (se != LBM_OK) return se;
-      }
+      lbm_status se = h->spec ? spectral_step_start(h) : poisson_step_start(h);
+      if (se != LBM_OK) return se;
       s = poisson_solve(h, h->cfg.poisson_tol, h->cfg.poisson_maxit, &it, &rel);
       LBM_CUDA_TRY(h, pp.stop());
       h->t_cnt[1] += it;
@@ -576,7 +576,7 @@ lbm_status lbm_solve_poisson(lbm_t* h, const double* rho_e, double* psi,
   if (iters) *iters = it;
   if (rel_res) *rel_res = rel;
   if (s != LBM_OK && s != LBM_ENOCONV) return s;
-  const lbm_status sr = spectral_history_reset(h);
+  const lbm_status sr = potential_history_reset(h);
   if (sr != LBM_OK) return sr;
   LBM_CUDA_TRY(h, launch_psi_to_double(h, h->ps.psi[h->ps.cur], dpsi));
   LBM_CUDA_TRY(h, cudaMemcpyAsync(psi, dpsi, N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
@@ -644,7 +644,7 @@ lbm_status lbm_set_state(lbm_t* h, const float* state, int64_t step) {
                                   cudaMemcpyHostToDevice, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   h->tstep = step;
-  return spectral_history_reset(h);
+  return potential_history_reset(h);
 }
 
 lbm_status lbm_create_stack(int count, const lbm_config* cfgs, lbm_t** out) {

@@ -36,6 +36,18 @@ constexpr double PSI_MAX = 2048.0;                      // 2^11
 // source of vanishing norm is solved once the residual is within twice that.
 constexpr double RES_FLOOR_RMS = 4.0;
 
+// Extrapolation in time of a fixed-point potential from its last three
+// values a = psi(t-1), b = psi(t-2), c = psi(t-3): the parabola through them,
+// 3a - 3b + c, or 2a - b and a while the history holds one or no older
+// value (`order`).  Exact in 128-bit integers; a value outside 2^61 units
+// keeps a.
+__device__ __forceinline__ int64_t extrapolate1(int64_t a, int64_t b, int64_t c, int order) {
+  if (order <= 0) return a;
+  const __int128 g = order == 1 ? (__int128)2 * a - b : (__int128)3 * ((__int128)a - b) + c;
+  const __int128 lim = (__int128)1 << 61;
+  return (g > lim || g < -lim) ? a : (int64_t)g;
+}
+
 #ifdef __CUDACC__
 // Conversions between 64-bit integers and FP32 on the 32-bit integer and FP32
 // pipes: the instructions for 64-bit conversions issue on the FP64 pipe,
@@ -113,6 +125,8 @@ struct Poisson {
   int zlo = 0, nzb = 0, perz = 1;
   std::vector<PoissonLevel> lev;
   int64_t* psi[2] = {nullptr, nullptr};  // lattice-sized fixed-point buffers
+  int64_t* hist = nullptr;  // multigrid / SOR: 2 N, psi one and two steps older than psi
+  int hist_n = 0;           // valid entries of hist
   int cur = 0;
   int64_t* src = nullptr; // 4 pi l_B (rho_e + w) per lattice node (fixed point), no mean removed
   double* dsum = nullptr; // [0] sum of src over fluid, [1 + 2k] sum r^2, [2 + 2k] sum s^2 (fixed-point units), k < NSLOT
@@ -227,6 +241,9 @@ void poisson_free(lbm_t* h);
 // Solves A psi = src - mean starting from the current psi buffer.
 lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
                          double* rel_res);
+// Multigrid / SOR host-driven steps: psi <- its extrapolation from the
+// previous steps before the step's solve (as spectral_step_start).
+lbm_status poisson_step_start(lbm_t* h);
 
 // ---- lbm_spectral.cu ----
 lbm_status spectral_setup(lbm_t* h, const uint8_t* solid_host);
@@ -240,8 +257,9 @@ void spectral_graph_free(lbm_t* h);
 // Host-driven steps: psi <- its extrapolation from the previous steps
 // before the step's solve (LBM_FLAG_NO_EXTRAPOLATION off, no learned guess).
 lbm_status spectral_step_start(lbm_t* h);
-// Restarts the potential history (psi was set from outside the steps).
-lbm_status spectral_history_reset(lbm_t* h);
+// Restarts the potential history of every solver (psi was set from outside
+// the steps).
+lbm_status potential_history_reset(lbm_t* h);
 
 // ---- lbm_nn.cu ----
 lbm_status nn_init(lbm_t* h, int hidden, uint64_t seed);

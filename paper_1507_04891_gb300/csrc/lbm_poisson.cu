@@ -622,6 +622,20 @@ CL make_cl(const PoissonLevel& l) {
 }  // namespace
 
 namespace {
+// psi <- extrapolate1(psi(t-1), psi(t-2), psi(t-3)) and the history moved
+// one step; one node per thread (any N).
+__global__ void __launch_bounds__(256) k_extrapolate_nodes(int64_t* __restrict__ psi,
+                                                           int64_t* __restrict__ h1,
+                                                           int64_t* __restrict__ h2, int64_t n,
+                                                           int order) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t a = psi[i], b = h1[i], c = h2[i];
+  psi[i] = extrapolate1(a, b, c, order);
+  h1[i] = a;
+  h2[i] = b;
+}
+
 void drop_graphs(Poisson& P) {
   for (int k = 0; k < 2; ++k) {
     if (P.cyc[k]) cudaGraphExecDestroy(P.cyc[k]);
@@ -630,6 +644,20 @@ void drop_graphs(Poisson& P) {
   P.cyc_failed = false;
 }
 }  // namespace
+
+lbm_status poisson_step_start(lbm_t* h) {
+  Poisson& P = h->ps;
+  if (!P.hist || (h->cfg.flags & LBM_FLAG_NO_EXTRAPOLATION) || nn_active(h)) {
+    P.hist_n = 0;
+    return LBM_OK;
+  }
+  k_extrapolate_nodes<<<nblocks(h->N, 256), 256, 0, h->st>>>(P.psi[P.cur], P.hist, P.hist + h->N, h->N,
+                                                            P.hist_n);
+  ++h->launches;
+  LBM_CUDA_TRY(h, cudaGetLastError());
+  P.hist_n = std::min(P.hist_n + 1, 2);
+  return LBM_OK;
+}
 
 void poisson_free(lbm_t* h) {
   Poisson& P = h->ps;
@@ -643,6 +671,9 @@ void poisson_free(lbm_t* h) {
   P.lev.clear();
   cudaFree(P.psi[0]);
   cudaFree(P.psi[1]);
+  cudaFree(P.hist);
+  P.hist = nullptr;
+  P.hist_n = 0;
   cudaFree(P.src);
   cudaFree(P.dsum);
   cudaFree(P.part);

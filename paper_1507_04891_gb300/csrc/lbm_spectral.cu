@@ -802,19 +802,11 @@ __global__ void __launch_bounds__(256, 4) k_res_planes(
 }
 
 // Start of a step's solve: psi(t-1) is replaced by its extrapolation in
-// time, 3 psi(t-1) - 3 psi(t-2) + psi(t-3) (the parabola through the three
-// previous potentials), or 2 psi(t-1) - psi(t-2) and psi(t-1) while the
-// history fills (`order` valid entries, read from *order_dev when given);
-// the history moves one step.  Exact in int64; a guess outside 2^61 fixed-
-// point units keeps psi(t-1).  Any start is valid: the solve iterates to the
-// same tolerance from it.  Two nodes per thread (N is even: nx >= 8).
-__device__ __forceinline__ int64_t extrapolate1(int64_t a, int64_t b, int64_t c, int order) {
-  if (order <= 0) return a;
-  const __int128 g = order == 1 ? (__int128)2 * a - b : (__int128)3 * ((__int128)a - b) + c;
-  const __int128 lim = (__int128)1 << 61;
-  return (g > lim || g < -lim) ? a : (int64_t)g;
-}
-
+// time (extrapolate1: the parabola through the three previous potentials,
+// fewer terms while the history fills; `order` valid entries, read from
+// *order_dev when given); the history moves one step.  Any start is valid:
+// the solve iterates to the same tolerance from it.  Two nodes per thread
+// (N is even: nx >= 8).
 __global__ void __launch_bounds__(256) k_extrapolate(int64_t* __restrict__ psi, int64_t* __restrict__ h1,
                                                      int64_t* __restrict__ h2, int64_t npairs,
                                                      const int* __restrict__ order_dev, int order) {
@@ -1384,7 +1376,8 @@ void spectral_graph_free(lbm_t* h) {
   }
 }
 
-lbm_status spectral_history_reset(lbm_t* h) {
+lbm_status potential_history_reset(lbm_t* h) {
+  h->ps.hist_n = 0;
   if (!h->spec) return LBM_OK;
   h->spec->hist_n = 0;
   if (h->gstatus) {

@@ -20,10 +20,10 @@ def _built():
     build_library()
 
 
-def make(wl, graph=False, extrapolate=True):
+def make(wl, graph=False, extrapolate=True, poisson="fft"):
     od = lbm.omega_drag_for_schmidt(wl.omega_visc, 1.0)
     lat = lbm.Lattice(SHAPE[2], SHAPE[1], SHAPE[0], 3, omega_drag=od, bjerrum=wl.bjerrum,
-                      poisson="fft", poisson_tol=1e-8, step_graph=graph, extrapolate=extrapolate)
+                      poisson=poisson, poisson_tol=1e-8, step_graph=graph, extrapolate=extrapolate)
     for s in range(3):
         lat.set_species(s, 1.0, wl.valence[s], wl.n0[s])
     return lat
@@ -45,10 +45,10 @@ def assert_same_moments(a, b, rel=1e-7):
         assert np.abs(na * ua - nb * ub).max() <= 1e-9, s
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_extrapolated_start_same_trajectory_fewer_applications(graph):
+@pytest.mark.parametrize("poisson,graph", [("fft", False), ("fft", True), ("mg", False)])
+def test_extrapolated_start_same_trajectory_fewer_applications(poisson, graph):
     wl = WL.ternary_bulk(shape=SHAPE, seed=1235)
-    plain, ext = make(wl, graph, False), make(wl, graph, True)
+    plain, ext = make(wl, graph, False, poisson), make(wl, graph, True, poisson)
     plain.step(16)
     ext.step(16)
     n_plain = applications(plain, 64)
@@ -59,9 +59,10 @@ def test_extrapolated_start_same_trajectory_fewer_applications(graph):
     assert_same_moments(plain, ext)
     # one FP32 transform leaves ~1e-7 of a smooth residual: the plain warm
     # start takes two applications a step; the extrapolated start is close
-    # enough for one in most steps
+    # enough for one in most steps.  Multigrid: a V-cycle cuts the residual
+    # about tenfold, and the extrapolated start begins orders of magnitude lower
     assert n_plain >= 64
-    assert n_ext <= 0.8 * n_plain, (n_ext, n_plain)
+    assert n_ext <= (0.8 if poisson == "fft" else 0.85) * n_plain, (n_ext, n_plain)
 
 
 def test_graph_and_host_steps_agree_with_extrapolation():
