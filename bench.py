@@ -369,14 +369,14 @@ def cpu_baseline(schmidt=1.0):
     """One core (one single-threaded instance), and every core beside it;
     the in-process sample if spawned processes are not available."""
     try:
-        one = cpu_oracle_instances(1, steps=60, schmidt=schmidt)
+        one = cpu_oracle_instances(1, steps=250, schmidt=schmidt)   # ~10 s on a GB300 host core
     except Exception as ex:
         one = cpu_oracle_sample(schmidt=schmidt)
         one["spawn_failed"] = repr(ex)
         return one
     one.pop("ms_per_step", None)
     try:
-        allc = cpu_oracle_instances(len(os.sched_getaffinity(0)), steps=40, schmidt=schmidt)
+        allc = cpu_oracle_instances(len(os.sched_getaffinity(0)), steps=100, schmidt=schmidt)
         allc.pop("kind", None)
         one["all_cores"] = allc
     except Exception as ex:  # reported, never required
