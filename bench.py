@@ -11,13 +11,14 @@ instead).  Metric: species-site MLUPS (S * N * steps / time / 1e6), with
 the stream/collide kernel's fraction of the measured HBM roofline and the
 Poisson iterations per step.  A host-stepped run of the same workload
 gives the per-phase CUDA-event times (phase_ms_per_step, host_steps).
-Each spectral solve starts from the extrapolation of the three previous
+Each Poisson solve starts from the extrapolation of the three previous
 potentials (--no-extrapolation: from the previous one).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (the only other implementation:
-the paper ships no code) on a bounded sample of the same workload.
+the paper ships no code) on bounded samples of the same workload, one
+single-threaded instance per host core.
 """
 
 from __future__ import annotations
