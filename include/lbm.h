@@ -137,6 +137,8 @@ lbm_status lbm_autotune(lbm_t* h, double* out);
  * the normalised residual of the warm-start potential and the fluid mask
  * to a correction of psi.  The solver applies it before iterating, keeps it
  * only if the residual drops, and always iterates to the same tolerance.
+ * While the network collects or is used, each solve starts from the
+ * previous step's potential (no extrapolation in time).
  *   lbm_nn_init     random initialisation (seeded), hidden in 1..16;
  *                   requires l_B > 0 and host-driven steps
  *   lbm_nn_collect  store the initial residual of each following solve in
@@ -246,7 +248,9 @@ lbm_status lbm_diagnostics(lbm_t* h, double* out);
  * collision populations of the last step, before streaming, as
  * h = f / (w_p n_ref) - 1), plus the step counter.  lbm_set_state restores
  * exactly what lbm_get_state returned, into a lattice whose species were
- * set with the same initial densities (hence the same n_ref).            */
+ * set with the same initial densities (hence the same n_ref).  The
+ * potential is not part of the state: the next solve starts from the
+ * lattice's current psi, and its history restarts.                       */
 lbm_status lbm_get_state(lbm_t* h, float* state, int64_t* step);
 lbm_status lbm_set_state(lbm_t* h, const float* state, int64_t step);
 
