@@ -166,7 +166,13 @@ def omega_drag_for_schmidt(omega_visc: float, schmidt: float) -> float:
 
 
 class Lattice:
-    """One lattice handle (lbm_t).  Methods carry the names of the C calls."""
+    """One lattice handle (lbm_t).  Methods carry the names of the C calls.
+
+    Constructor arguments are the fields of lbm_config: storage "fp32",
+    "fp16" or "bf16"; poisson "mg", "sor" or "fft"; step_graph sets
+    LBM_FLAG_STEP_GRAPH (spectral solver only); extrapolate=False sets
+    LBM_FLAG_NO_EXTRAPOLATION (each solve starts from the previous potential
+    instead of its extrapolation in time)."""
 
     def __init__(self, nx, ny, nz, nspecies, omega_visc=1.0, omega_drag=1.0,
                  bjerrum=0.0, e_ext=(0.0, 0.0, 0.0), storage="fp32", poisson="mg",
