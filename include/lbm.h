@@ -187,6 +187,10 @@ lbm_status lbm_set_species(lbm_t* h, int s, double mass, double valence,
  * collision of all species.  stream: a cudaStream_t, or NULL for the
  * library's own stream; the call returns after the work is queued except
  * that the Poisson convergence test reads one value back per iteration.
+ * Work on a caller's stream starts after the work queued on the library's
+ * stream, and every later call that runs on the library's stream (all
+ * calls without a stream argument) waits for it: no lbm_synchronize is
+ * needed between lbm_step(h, n, s) and lbm_get_moments(h, ...).
  * LBM_ENOCONV if a Poisson solve reached poisson_maxit (the state has then
  * advanced with the unconverged potential).                               */
 lbm_status lbm_step(lbm_t* h, int nsteps, void* stream);
@@ -208,7 +212,10 @@ lbm_status lbm_get_moments(lbm_t* h, int s, double* n, double* u);
  * GPU loading the library holds until the process exits.  LBM_EINVAL when
  * the lattice has more nodes.  The first call on a device looks up the
  * array's device address; make that first call before any stream capture.
- * All calls share the array: calls that overlap on the GPU race.           */
+ * Like every call without a stream argument it runs after the last
+ * lbm_step, also one queued on a caller's stream.  All calls share the
+ * array: calls that overlap on the GPU (two handles or host threads on one
+ * device) race on it.                                                      */
 #define LBM_NOALLOC_MAX_NODES (1 << 18)
 lbm_status lbm_get_moments_noalloc(lbm_t* h, int s, double* n, double* u);
 

@@ -89,6 +89,17 @@ struct Phase {
 
 }  // namespace
 
+namespace lbm_gb300 {
+
+cudaError_t own_stream(lbm_t* h) {
+  h->st = h->own;
+  if (!h->foreign_pending) return cudaSuccess;
+  h->foreign_pending = false;
+  return cudaStreamWaitEvent(h->own, h->order_ev, 0);
+}
+
+}  // namespace lbm_gb300
+
 extern "C" {
 
 void lbm_config_default(lbm_config* c) {
@@ -169,7 +180,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
   h->esize = (c.storage == LBM_FP32) ? 4 : 2;
   lbm_status s = LBM_OK;
   if (cudaSetDevice(h->dev) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming) != cudaSuccess) {
     g_create_error = "CUDA context or stream creation failed";
     lbm_destroy(h);
     return LBM_ECUDA;
@@ -241,6 +253,7 @@ void lbm_destroy(lbm_t* h) {
   cudaFree(h->gstatus);
   if (h->hstatus) cudaFreeHost(h->hstatus);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
+  if (h->order_ev) cudaEventDestroy(h->order_ev);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
 }
@@ -250,7 +263,7 @@ lbm_status lbm_set_walls(lbm_t* h, const uint8_t* solid, const double* sigma) {
   if (!solid) return fail(h, LBM_EINVAL, "solid mask is NULL");
   if (h->species_set) return fail(h, LBM_EINVAL, "walls must be set before any species");
   cudaSetDevice(h->dev);
-  h->st = h->own;
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   const int nx = h->cfg.nx, ny = h->cfg.ny, nz = h->cfg.nz;
   const int64_t N = h->N;
   int64_t nfluid = 0;
@@ -398,7 +411,7 @@ lbm_status lbm_set_species(lbm_t* h, int s, double mass, double valence,
     return fail(h, LBM_EINVAL,
                 "all species must have the same mass (one thermal speed on the lattice)");
   cudaSetDevice(h->dev);
-  h->st = h->own;
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   const int64_t N = h->N;
   // host checks and the reference density of the 16-bit shifted storage
   std::vector<uint8_t> solid;
@@ -443,7 +456,21 @@ lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
   if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
   if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set before stepping");
   cudaSetDevice(h->dev);
-  h->st = stream ? (cudaStream_t)stream : h->own;
+  LBM_CUDA_TRY(h, own_stream(h));
+  if (stream && (cudaStream_t)stream != h->own) {
+    // the caller's stream starts after everything queued on the own stream,
+    // and the next call on the own stream waits for this call's work
+    LBM_CUDA_TRY(h, cudaEventRecord(h->order_ev, h->own));
+    LBM_CUDA_TRY(h, cudaStreamWaitEvent((cudaStream_t)stream, h->order_ev, 0));
+    h->st = (cudaStream_t)stream;
+  }
+  struct Ordered {
+    lbm_t* h;
+    ~Ordered() {
+      if (h->st != h->own && cudaEventRecord(h->order_ev, h->st) == cudaSuccess)
+        h->foreign_pending = true;
+    }
+  } ordered{h};
   const bool charged = h->cfg.bjerrum > 0.0;
   if (h->cfg.flags & LBM_FLAG_STEP_GRAPH) {
     Phase pg(h, 1);
@@ -501,7 +528,7 @@ lbm_status lbm_get_moments(lbm_t* h, int s, double* n, double* u) {
   if (!(h->species_set >> s & 1u)) return fail(h, LBM_EINVAL, "species not set");
   if (!n && !u) return LBM_OK;
   cudaSetDevice(h->dev);
-  h->st = h->own;  // calls without a stream argument use the library's stream
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   const int64_t N = h->N;
   Scratch sc;
   if (cudaMalloc(&sc.p, 4 * N * sizeof(double)) != cudaSuccess)
@@ -519,7 +546,7 @@ lbm_status lbm_get_populations(lbm_t* h, int s, double* f) {
   if (!h) return LBM_EINVAL;
   if (s < 0 || s >= h->S || !f) return fail(h, LBM_EINVAL, "bad species index or NULL buffer");
   cudaSetDevice(h->dev);
-  h->st = h->own;  // calls without a stream argument use the library's stream
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   const int64_t N = h->N;
   Scratch sc;
   if (cudaMalloc(&sc.p, (size_t)Q * N * sizeof(double)) != cudaSuccess)
@@ -534,7 +561,7 @@ lbm_status lbm_get_potential(lbm_t* h, double* psi) {
   if (!h || !psi) return LBM_EINVAL;
   if (!(h->cfg.bjerrum > 0.0)) return fail(h, LBM_EINVAL, "neutral lattice has no potential");
   cudaSetDevice(h->dev);
-  h->st = h->own;  // calls without a stream argument use the library's stream
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   const int64_t N = h->N;
   Scratch sc;
   if (cudaMalloc(&sc.p, N * sizeof(double)) != cudaSuccess)
@@ -553,7 +580,7 @@ lbm_status lbm_solve_poisson(lbm_t* h, const double* rho_e, double* psi,
   if (!(tol > 0.0)) return fail(h, LBM_EINVAL, "tol must be > 0");
   if (maxit <= 0) maxit = h->cfg.poisson_maxit;
   cudaSetDevice(h->dev);
-  h->st = h->own;
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   const int64_t N = h->N;
   for (int64_t i = 0; i < N; ++i)
     if (!isfinite(rho_e[i]) || !isfinite(psi[i]) || fabs(psi[i]) >= PSI_MAX)
@@ -588,7 +615,7 @@ lbm_status lbm_diagnostics(lbm_t* h, double* out) {
   if (!h || !out) return LBM_EINVAL;
   if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set first");
   cudaSetDevice(h->dev);
-  h->st = h->own;  // calls without a stream argument use the library's stream
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   LBM_CUDA_TRY(h, cudaMemsetAsync(h->dred, 0, (MAX_SPECIES + 4) * DIAG_SPREAD * sizeof(double), h->st));
   LBM_CUDA_TRY(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->st));
   LBM_CUDA_TRY(h, launch_diagnostics(h));
@@ -625,7 +652,7 @@ lbm_status lbm_get_state(lbm_t* h, float* state, int64_t* step) {
   if (h->cfg.storage != LBM_FP32)
     return fail(h, LBM_EINVAL, "raw state access needs FP32 storage");
   cudaSetDevice(h->dev);
-  h->st = h->own;  // calls without a stream argument use the library's stream
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   LBM_CUDA_TRY(h, cudaMemcpyAsync(state, h->f[h->cur], (size_t)h->S * Q * h->N * sizeof(float),
                                   cudaMemcpyDeviceToHost, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
@@ -639,7 +666,7 @@ lbm_status lbm_set_state(lbm_t* h, const float* state, int64_t step) {
     return fail(h, LBM_EINVAL, "raw state access needs FP32 storage");
   if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set first");
   cudaSetDevice(h->dev);
-  h->st = h->own;  // calls without a stream argument use the library's stream
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   LBM_CUDA_TRY(h, cudaMemcpyAsync(h->f[h->cur], state, (size_t)h->S * Q * h->N * sizeof(float),
                                   cudaMemcpyHostToDevice, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
@@ -732,7 +759,7 @@ lbm_status lbm_autotune(lbm_t* h, double* out) {
   if (!h) return LBM_EINVAL;
   if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set first");
   cudaSetDevice(h->dev);
-  h->st = h->own;
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   cudaEvent_t e0, e1;
   LBM_CUDA_TRY(h, cudaEventCreate(&e0));
   LBM_CUDA_TRY(h, cudaEventCreate(&e1));
@@ -792,7 +819,7 @@ lbm_status lbm_nn_init(lbm_t* h, int hidden, uint64_t seed) {
   if (h->cfg.flags & LBM_FLAG_STEP_GRAPH)
     return fail(h, LBM_EINVAL, "the learned guess runs in host-driven steps only");
   cudaSetDevice(h->dev);
-  h->st = h->own;
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   return nn_init(h, hidden, seed);
 }
 
@@ -806,7 +833,7 @@ lbm_status lbm_nn_train(lbm_t* h, int epochs, double lr, double* losses) {
   if (!h) return LBM_EINVAL;
   if (epochs < 0 || !(lr > 0.0)) return fail(h, LBM_EINVAL, "epochs >= 0 and lr > 0 required");
   cudaSetDevice(h->dev);
-  h->st = h->own;
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   return nn_train(h, epochs, lr, losses);
 }
 
@@ -818,14 +845,14 @@ lbm_status lbm_nn_use(lbm_t* h, int enable) {
 lbm_status lbm_nn_params(lbm_t* h, float* get, const float* set, int* nparams) {
   if (!h) return LBM_EINVAL;
   cudaSetDevice(h->dev);
-  h->st = h->own;
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   return nn_params(h, get, set, nparams);
 }
 
 lbm_status lbm_nn_loss_grad(lbm_t* h, const float* x0, double* loss, float* grad) {
   if (!h || !x0 || !loss) return LBM_EINVAL;
   cudaSetDevice(h->dev);
-  h->st = h->own;
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   return nn_loss_grad_host(h, x0, loss, grad);
 }
 

@@ -164,6 +164,11 @@ struct lbm {
   int dev = 0;
   cudaStream_t own = nullptr;
   cudaStream_t st = nullptr;  // stream of the call in progress
+  // ordering between a caller's stream and the library's own stream: the
+  // last lbm_step on a caller's stream records this event there, and the
+  // next call on the own stream waits for it (foreign_pending)
+  cudaEvent_t order_ev = nullptr;
+  bool foreign_pending = false;
   size_t esize = 4;
   void* f[2] = {nullptr, nullptr};
   int cur = 0;
@@ -218,6 +223,11 @@ struct lbm {
 };
 
 namespace lbm_gb300 {
+
+// ---- lbm_api.cu ----
+// Makes the library's own stream the stream of the call in progress, after
+// the work that the last lbm_step queued on a caller's stream.
+cudaError_t own_stream(lbm_t* h);
 
 // ---- lbm_kernels.cu ----
 cudaError_t launch_init_species(lbm_t* h, int s, const double* n0_dev,

@@ -13,6 +13,8 @@
 // streams, two threads, two handles on one device) race on it.
 #include <string.h>
 
+#include <atomic>
+
 #include "lbm_internal.cuh"
 
 using namespace lbm_gb300;
@@ -24,8 +26,11 @@ static __device__ __align__(256) double g_moment_stage[4 * LBM_NOALLOC_MAX_NODES
 
 constexpr int kMaxDevices = 64;
 // device address of g_moment_stage per device (host code cannot use the
-// symbol itself: on the host it is only a stand-in, not a device address)
-double* g_stage_ptr[kMaxDevices] = {nullptr};
+// symbol itself: on the host it is only a stand-in, not a device address).
+// Host threads that make their first call at the same time may both look
+// the address up; they find the same value, and the atomic makes the
+// concurrent stores well defined.
+std::atomic<double*> g_stage_ptr[kMaxDevices] = {};
 
 }  // namespace
 
@@ -51,15 +56,16 @@ extern "C" lbm_status lbm_get_moments_noalloc(lbm_t* h, int s, double* n, double
   LBM_CUDA_TRY(h, cudaSetDevice(h->dev));
   // first call on this device: look up the device address of the array
   // (with this device current)
-  if (!g_stage_ptr[h->dev]) {
-    double* p = nullptr;
-    LBM_CUDA_TRY(h, cudaGetSymbolAddress((void**)&p, g_moment_stage));
-    g_stage_ptr[h->dev] = p;
+  double* dn = g_stage_ptr[h->dev].load(std::memory_order_acquire);
+  if (!dn) {
+    LBM_CUDA_TRY(h, cudaGetSymbolAddress((void**)&dn, g_moment_stage));
+    g_stage_ptr[h->dev].store(dn, std::memory_order_release);
   }
   const int64_t N = h->N;
-  double* dn = g_stage_ptr[h->dev];
   double* du = dn + N;
-  h->st = h->own;
+  // the gather runs on the library's stream after the last lbm_step, also
+  // when that step ran on a caller's stream
+  LBM_CUDA_TRY(h, own_stream(h));
   LBM_CUDA_TRY(h, launch_gather(h, s, dn, du, nullptr));
   if (n) LBM_CUDA_TRY(h, cudaMemcpyAsync(n, dn, N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   if (u) LBM_CUDA_TRY(h, cudaMemcpyAsync(u, du, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, h->st));

@@ -42,3 +42,24 @@ def test_noalloc_rejects_lattices_beyond_the_limit():
         lat.get_moments_noalloc(0)
     assert e.value.status == lbm.LBM_EINVAL
     assert "LBM_NOALLOC_MAX_NODES" in str(e.value)
+
+
+def test_noalloc_waits_for_steps_queued_on_a_caller_stream():
+    """Steps queued on a caller's stream (a torch side stream), then the
+    moments with no synchronisation in between: the call must see the state
+    after those steps, as lbm_get_moments does after lbm_synchronize.  A
+    neutral lattice, so that lbm_step queues its 50 launches without any
+    host read-back."""
+    torch = pytest.importorskip("torch")
+    wl = WL.binary_random((32, 64, 64), seed=98, schmidt=3.0)
+    lat = lbm.Lattice(64, 64, 32, 2, omega_drag=1.4)
+    for s in range(2):
+        lat.set_species(s, 1.0, 0.0, wl.n0[s], wl.u0[s])
+    side = torch.cuda.Stream()
+    lat.step(50, stream=side.cuda_stream)
+    n, u = lat.get_moments_noalloc(1)
+    lat.synchronize()
+    n_ref, u_ref = lat.get_moments(1)
+    assert np.array_equal(n, n_ref)
+    assert np.array_equal(u, u_ref)
+    assert lat.diagnostics()["steps"] == 50
