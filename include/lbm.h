@@ -46,7 +46,9 @@ typedef enum {
   LBM_ECUDA = 3,     /* CUDA runtime error (message has the CUDA text)  */
   LBM_ENOCONV = 4,   /* Poisson solve hit its iteration limit           */
   LBM_EUNSTABLE = 5, /* non-finite or non-positive density detected     */
-  LBM_ETIMEOUT = 6   /* a bounded device wait gave up                   */
+  LBM_ETIMEOUT = 6   /* reserved for a bounded device wait that gives up;
+                        no call of this version returns it (no kernel of
+                        the library waits on another CTA or device)     */
 } lbm_status;
 
 /* Population storage.  Every format stores the deviation of a population
@@ -91,12 +93,16 @@ typedef struct {
 
 /* LBM_FLAG_NO_EXTRAPOLATION: each step's Poisson solve (every solver)
  * starts from the previous step's potential.  Without the flag it starts
- * from the extrapolation in time through the three previous potentials,
- * 3 psi(t-1) - 3 psi(t-2) + psi(t-3) (fewer terms for the first steps after
- * lbm_create, lbm_set_species, lbm_set_state or lbm_solve_poisson, which
- * restart the history); the solve still iterates to poisson_tol.  Not
- * applied while the learned guess is collecting or in use.  The paper
- * has no counterpart: a property of this library's solver.              */
+ * from the extrapolation in time of the previous potentials,
+ * 2 psi(t-1) - 2 psi(t-3) + psi(t-4), exact for potentials quadratic in
+ * time and for a component that alternates sign every step (the ion flux
+ * at high Schmidt number); the first steps after lbm_create,
+ * lbm_set_species, lbm_set_state or lbm_solve_poisson (which restart the
+ * history) use psi(t-1), the line 2 psi(t-1) - psi(t-2) and the parabola
+ * 3 psi(t-1) - 3 psi(t-2) + psi(t-3) while the history fills.  The solve
+ * still iterates to poisson_tol.  Not applied while the learned guess is
+ * collecting or in use.  The paper has no counterpart: a property of this
+ * library's solver.                                                       */
 #define LBM_FLAG_NO_EXTRAPOLATION 2
 
 /* Fills *cfg with defaults: omega_visc = 1, omega_drag = 1, l_B = 0,
@@ -182,6 +188,17 @@ lbm_status lbm_set_walls(lbm_t* h, const uint8_t* solid, const double* sigma);
 lbm_status lbm_set_species(lbm_t* h, int s, double mass, double valence,
                            const double* n0, const double* u0);
 
+/* As lbm_set_species, with n0 (N doubles) and u0 (3N doubles, [3][N], or
+ * NULL) in device memory of the handle's device: caller-owned (for example
+ * torch tensors' data pointers), read by work queued on `stream` (a
+ * cudaStream_t, or NULL for the library's stream) during the call, never
+ * retained or freed.  The checks of lbm_set_species (n0 finite and > 0,
+ * u0 finite at every fluid node) run on the device; the call returns after
+ * they were read back and the initialisation was queued.  LBM_EINVAL as
+ * for lbm_set_species.                                                    */
+lbm_status lbm_set_species_dev(lbm_t* h, int s, double mass, double valence,
+                               const double* n0_dev, const double* u0_dev, void* stream);
+
 /* Advances nsteps >= 0 time steps of Eq. (latboeq).  Each step: charge
  * density and Poisson solve (if l_B > 0), fused stream + moments + forces +
  * collision of all species.  stream: a cudaStream_t, or NULL for the
@@ -202,6 +219,28 @@ lbm_status lbm_synchronize(lbm_t* h);
  * bare species velocity u = sum_p c_p f_p / n (3N doubles, [3][N]); either
  * pointer may be NULL.  Zero at wall nodes.  Host buffers.                */
 lbm_status lbm_get_moments(lbm_t* h, int s, double* n, double* u);
+
+/* As lbm_get_moments, into device memory of the handle's device: n_dev
+ * (N doubles) and u_dev (3N doubles, [3][N]), either may be NULL,
+ * caller-owned and never retained.  The gather is queued on `stream` (a
+ * cudaStream_t, or NULL for the library's stream) after the last step and
+ * the call returns without waiting for it; the caller orders its reads of
+ * the buffers on that stream.                                              */
+lbm_status lbm_get_moments_dev(lbm_t* h, int s, double* n_dev, double* u_dev, void* stream);
+
+/* Plane sums of the current state, for the slit currents of Sec. 4 (mass
+ * flow, electric and convective currents along the walls): for every
+ * z-plane and species, over the plane's fluid nodes,
+ *   out[(z*S + s)*4 + 0]      sum of n^s
+ *   out[(z*S + s)*4 + 1..3]   sum of n^s (u^s + F^s / 2), x, y, z
+ * with u^s the bare species velocity and F^s the force per unit mass of
+ * Sec. 2 that the collision applies (applied and induced electric field,
+ * drag on the force-shifted velocities): u^s + F^s / 2 is the velocity of
+ * the second-order forcing of Eq. ourforc.  The induced field is the one of
+ * the last Poisson solve (the potential the last step's collision used;
+ * the same as the current one in a steady state).  out: nz*S*4 doubles,
+ * host.                                                                     */
+lbm_status lbm_plane_fluxes(lbm_t* h, double* out);
 
 /* Moments as lbm_get_moments, for callers that must not allocate device
  * memory while they run (a device pool reserved by another framework, a
@@ -238,15 +277,20 @@ lbm_status lbm_solve_poisson(lbm_t* h, const double* rho_e, double* psi,
                              double tol, int maxit, int* iters,
                              double* rel_res);
 
-/* FP64 global diagnostics of the current state f(t), written to out:
+/* FP64 global diagnostics of the current state f(t).  After a step they
+ * come from sums that the stream/collide kernel formed over what it stored
+ * (per CTA, combined in FP64 in a fixed order: no pass over the lattice);
+ * otherwise (after lbm_set_species or lbm_set_state) from a pass over the
+ * populations.  Written to out:
  *   out[0 .. S-1]   total number of particles of each species
  *   out[S .. S+2]   total momentum sum_alpha sum_r m n^alpha u^alpha
  *   out[S+3]        net fluid charge sum_r sum_alpha z^alpha n^alpha
  *   out[S+4]        Poisson iterations of the last step
  *   out[S+5]        final relative Poisson residual of the last step
  *   out[S+6]        number of time steps taken
- * out must hold LBM_DIAG_LEN(S) doubles.  LBM_EUNSTABLE if a density is
- * non-finite or non-positive (the values are still written).             */
+ * out must hold LBM_DIAG_LEN(S) doubles.  LBM_EUNSTABLE if a sum is not
+ * finite or a density is non-finite or non-positive (after a step: a
+ * density entering the last step; the values are still written).        */
 #define LBM_DIAG_LEN(S) ((S) + 7)
 lbm_status lbm_diagnostics(lbm_t* h, double* out);
 
@@ -260,6 +304,14 @@ lbm_status lbm_diagnostics(lbm_t* h, double* out);
  * lattice's current psi, and its history restarts.                       */
 lbm_status lbm_get_state(lbm_t* h, float* state, int64_t* step);
 lbm_status lbm_set_state(lbm_t* h, const float* state, int64_t step);
+
+/* The drag frequency of a Schmidt number Sc = nu / D, with the lattice
+ * viscosity nu = c_s^2 (1/omega_visc - 1/2) and mutual diffusivity
+ * D = c_s^2 (1/omega_drag - 1/2) of Sec. 4:
+ *   omega_drag = 1 / (1/2 + (1/omega_visc - 1/2) / Sc).
+ * Returns 0 when omega_visc is outside (0, 2) or Sc is not finite and
+ * positive.                                                                */
+double lbm_omega_drag_for_schmidt(double omega_visc, double schmidt);
 
 /* Number of lattice nodes N = nx*ny*nz, and the element count of the raw
  * state (S*19*N).                                                          */

@@ -100,6 +100,56 @@ cudaError_t own_stream(lbm_t* h) {
 
 }  // namespace lbm_gb300
 
+namespace {
+
+// The stream of a call with a stream argument (NULL: the library's own
+// stream).  A caller's stream first waits for the work queued on the own
+// stream; when the call ends, an event recorded on the caller's stream
+// makes the next call on the own stream wait for this call's work.
+struct CallStream {
+  lbm_t* h;
+  cudaError_t err = cudaSuccess;
+  CallStream(lbm_t* hh, void* stream) : h(hh) {
+    err = own_stream(h);
+    if (err == cudaSuccess && stream && (cudaStream_t)stream != h->own) {
+      err = cudaEventRecord(h->order_ev, h->own);
+      if (err == cudaSuccess) err = cudaStreamWaitEvent((cudaStream_t)stream, h->order_ev, 0);
+      if (err == cudaSuccess) h->st = (cudaStream_t)stream;
+    }
+  }
+  ~CallStream() {
+    if (h->st != h->own && cudaEventRecord(h->order_ev, h->st) == cudaSuccess)
+      h->foreign_pending = true;
+  }
+};
+
+// Argument checks shared by lbm_set_species and lbm_set_species_dev.
+lbm_status species_args(lbm_t* h, int s, double mass, double valence, const void* n0) {
+  if (!h) return LBM_EINVAL;
+  if (s < 0 || s >= h->S) return fail(h, LBM_EINVAL, "species index out of range");
+  if (!n0) return fail(h, LBM_EINVAL, "n0 is NULL");
+  if (!(mass > 0.0) || !isfinite(mass) || !isfinite(valence))
+    return fail(h, LBM_EINVAL, "mass must be > 0 and valence finite");
+  if (h->species_set && fabs(mass - h->mass0) > 1e-12 * h->mass0)
+    return fail(h, LBM_EINVAL,
+                "all species must have the same mass (one thermal speed on the lattice)");
+  return LBM_OK;
+}
+
+// Bookkeeping after species s was initialised: the state restarts at step 0.
+lbm_status species_done(lbm_t* h, int s, double mass, double valence) {
+  h->mass[s] = (float)mass;
+  h->valence[s] = (float)valence;
+  if (!h->species_set) h->mass0 = mass;
+  h->species_set |= 1u << s;
+  h->tstep = 0;
+  h->psi_valid = false;
+  h->diag_valid = false;
+  return potential_history_reset(h);
+}
+
+}  // namespace
+
 extern "C" {
 
 void lbm_config_default(lbm_config* c) {
@@ -202,6 +252,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     }
   }
   if (s == LBM_OK) s = dev_alloc(h, &h->dred, (MAX_SPECIES + 4) * DIAG_SPREAD);
+  // diagnostics partials for the smallest CTA size the stream/collide uses (64)
+  if (s == LBM_OK) s = dev_alloc(h, &h->dpart, (size_t)((N + 63) / 64) * DIAG_NQ);
   if (s == LBM_OK) s = dev_alloc(h, &h->dflag, 1);
   if (s == LBM_OK && cudaMallocHost(&h->hred, (MAX_SPECIES + 4) * DIAG_SPREAD * sizeof(double)) != cudaSuccess)
     s = LBM_ENOMEM;
@@ -209,7 +261,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     s = dev_alloc(h, &h->ps.psi[0], N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.psi[1], N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.src, N);
-    if (s == LBM_OK && c.poisson != LBM_POISSON_FFT) s = dev_alloc(h, &h->ps.hist, 2 * (size_t)N);
+    if (s == LBM_OK && c.poisson != LBM_POISSON_FFT) s = dev_alloc(h, &h->ps.hist, HIST_SLOTS * (size_t)N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.dsum, 1 + 2 * Poisson::NSLOT);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.part, (size_t)((N + 63) / 64));
     if (s == LBM_OK && cudaMallocHost(&h->ps.hsum, (1 + 2 * Poisson::NSLOT) * sizeof(double)) != cudaSuccess)
@@ -217,7 +269,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     if (s == LBM_OK) {
       cudaMemset(h->ps.psi[0], 0, N * sizeof(int64_t));
       cudaMemset(h->ps.psi[1], 0, N * sizeof(int64_t));
-      if (h->ps.hist) cudaMemset(h->ps.hist, 0, 2 * N * sizeof(int64_t));
+      if (h->ps.hist) cudaMemset(h->ps.hist, 0, HIST_SLOTS * N * sizeof(int64_t));
       cudaMemset(h->ps.dsum, 0, (1 + 2 * Poisson::NSLOT) * sizeof(double));
       s = poisson_setup(h, nullptr);
       if (s == LBM_OK && c.poisson == LBM_POISSON_FFT) s = spectral_setup(h, nullptr);
@@ -243,6 +295,7 @@ void lbm_destroy(lbm_t* h) {
   cudaFree(h->wallq);
   cudaFree(h->wsrc);
   cudaFree(h->dred);
+  cudaFree(h->dpart);
   cudaFree(h->dflag);
   if (h->hred) cudaFreeHost(h->hred);
   spectral_graph_free(h);
@@ -402,14 +455,8 @@ lbm_status lbm_set_walls(lbm_t* h, const uint8_t* solid, const double* sigma) {
 
 lbm_status lbm_set_species(lbm_t* h, int s, double mass, double valence,
                            const double* n0, const double* u0) {
-  if (!h) return LBM_EINVAL;
-  if (s < 0 || s >= h->S) return fail(h, LBM_EINVAL, "species index out of range");
-  if (!n0) return fail(h, LBM_EINVAL, "n0 is NULL");
-  if (!(mass > 0.0) || !isfinite(mass) || !isfinite(valence))
-    return fail(h, LBM_EINVAL, "mass must be > 0 and valence finite");
-  if (h->species_set && fabs(mass - h->mass0) > 1e-12 * h->mass0)
-    return fail(h, LBM_EINVAL,
-                "all species must have the same mass (one thermal speed on the lattice)");
+  lbm_status sa = species_args(h, s, mass, valence, n0);
+  if (sa != LBM_OK) return sa;
   cudaSetDevice(h->dev);
   LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
   const int64_t N = h->N;
@@ -442,13 +489,52 @@ lbm_status lbm_set_species(lbm_t* h, int s, double mass, double valence,
   if (u0) LBM_CUDA_TRY(h, cudaMemcpy(du, u0, 3 * N * sizeof(double), cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, launch_init_species(h, s, dn, du));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
-  h->mass[s] = (float)mass;
-  h->valence[s] = (float)valence;
-  if (!h->species_set) h->mass0 = mass;
-  h->species_set |= 1u << s;
-  h->tstep = 0;
-  h->psi_valid = false;
-  return potential_history_reset(h);
+  return species_done(h, s, mass, valence);
+}
+
+lbm_status lbm_set_species_dev(lbm_t* h, int s, double mass, double valence,
+                               const double* n0_dev, const double* u0_dev, void* stream) {
+  lbm_status st = species_args(h, s, mass, valence, n0_dev);
+  if (st != LBM_OK) return st;
+  cudaSetDevice(h->dev);
+  CallStream cs(h, stream);
+  LBM_CUDA_TRY(h, cs.err);
+  // fluid-node sum of n0 (the reference density) and a count of invalid
+  // entries, per CTA, summed on the host in a fixed order
+  int nb = 0;
+  LBM_CUDA_TRY(h, launch_species_check(h, n0_dev, u0_dev, h->dred, &nb));
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(h->hred, h->dred, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost,
+                                  h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  double tot = 0.0, bad = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    tot += h->hred[2 * b];
+    bad += h->hred[2 * b + 1];
+  }
+  if (bad != 0.0)
+    return fail(h, LBM_EINVAL, "n0 must be finite and > 0 at every fluid node, u0 finite");
+  h->nref[s] = (float)(tot / (double)h->nfluid);
+  LBM_CUDA_TRY(h, launch_init_species(h, s, n0_dev, u0_dev));
+  return species_done(h, s, mass, valence);
+}
+
+lbm_status lbm_get_moments_dev(lbm_t* h, int s, double* n_dev, double* u_dev, void* stream) {
+  if (!h) return LBM_EINVAL;
+  if (s < 0 || s >= h->S) return fail(h, LBM_EINVAL, "species index out of range");
+  if (!(h->species_set >> s & 1u)) return fail(h, LBM_EINVAL, "species not set");
+  if (!n_dev && !u_dev) return LBM_OK;
+  cudaSetDevice(h->dev);
+  CallStream cs(h, stream);
+  LBM_CUDA_TRY(h, cs.err);
+  LBM_CUDA_TRY(h, launch_gather(h, s, n_dev, u_dev, nullptr));
+  return LBM_OK;
+}
+
+double lbm_omega_drag_for_schmidt(double omega_visc, double schmidt) {
+  // Sc = nu / D with nu = c_s^2 (1/omega_visc - 1/2) and
+  // D = c_s^2 (1/omega_drag - 1/2) (Sec. 4)
+  if (!(omega_visc > 0.0 && omega_visc < 2.0) || !(schmidt > 0.0) || !isfinite(schmidt)) return 0.0;
+  return 1.0 / (0.5 + (1.0 / omega_visc - 0.5) / schmidt);
 }
 
 lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
@@ -456,21 +542,8 @@ lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
   if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
   if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set before stepping");
   cudaSetDevice(h->dev);
-  LBM_CUDA_TRY(h, own_stream(h));
-  if (stream && (cudaStream_t)stream != h->own) {
-    // the caller's stream starts after everything queued on the own stream,
-    // and the next call on the own stream waits for this call's work
-    LBM_CUDA_TRY(h, cudaEventRecord(h->order_ev, h->own));
-    LBM_CUDA_TRY(h, cudaStreamWaitEvent((cudaStream_t)stream, h->order_ev, 0));
-    h->st = (cudaStream_t)stream;
-  }
-  struct Ordered {
-    lbm_t* h;
-    ~Ordered() {
-      if (h->st != h->own && cudaEventRecord(h->order_ev, h->st) == cudaSuccess)
-        h->foreign_pending = true;
-    }
-  } ordered{h};
+  CallStream cs(h, stream);
+  LBM_CUDA_TRY(h, cs.err);
   const bool charged = h->cfg.bjerrum > 0.0;
   if (h->cfg.flags & LBM_FLAG_STEP_GRAPH) {
     Phase pg(h, 1);
@@ -538,6 +611,21 @@ lbm_status lbm_get_moments(lbm_t* h, int s, double* n, double* u) {
   LBM_CUDA_TRY(h, launch_gather(h, s, dn, du, nullptr));
   if (n) LBM_CUDA_TRY(h, cudaMemcpyAsync(n, dn, N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   if (u) LBM_CUDA_TRY(h, cudaMemcpyAsync(u, du, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return LBM_OK;
+}
+
+lbm_status lbm_plane_fluxes(lbm_t* h, double* out) {
+  if (!h || !out) return LBM_EINVAL;
+  if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set first");
+  cudaSetDevice(h->dev);
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
+  const size_t len = (size_t)h->cfg.nz * h->S * 4;
+  Scratch sc;
+  if (cudaMalloc(&sc.p, len * sizeof(double)) != cudaSuccess)
+    return fail(h, LBM_ENOMEM, "scratch allocation failed");
+  LBM_CUDA_TRY(h, launch_plane_fluxes(h, (double*)sc.p));
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(out, sc.p, len * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   return LBM_OK;
 }
@@ -616,33 +704,50 @@ lbm_status lbm_diagnostics(lbm_t* h, double* out) {
   if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set first");
   cudaSetDevice(h->dev);
   LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
-  LBM_CUDA_TRY(h, cudaMemsetAsync(h->dred, 0, (MAX_SPECIES + 4) * DIAG_SPREAD * sizeof(double), h->st));
-  LBM_CUDA_TRY(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->st));
-  LBM_CUDA_TRY(h, launch_diagnostics(h));
-  LBM_CUDA_TRY(h, cudaMemcpyAsync(h->hred, h->dred, (MAX_SPECIES + 4) * DIAG_SPREAD * sizeof(double),
-                                  cudaMemcpyDeviceToHost, h->st));
-  int bad = 0;
-  LBM_CUDA_TRY(h, cudaMemcpyAsync(&bad, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
-  // the kernel sums deviations from n_ref into DIAG_SPREAD partials per
-  // quantity; the reference parts are exact
-  for (int k = 0; k < MAX_SPECIES + 4; ++k) {
-    double t = 0.0;
-    for (int j = 0; j < DIAG_SPREAD; ++j) t += h->hred[k * DIAG_SPREAD + j];
-    h->hred[k] = t;
+  // deviation sums: species masses, momentum x, y, z, charge
+  double sums[MAX_SPECIES + 4];
+  bool bad = false;
+  if (h->diag_valid) {
+    // the last stream/collide launch summed the state it wrote, per CTA
+    LBM_CUDA_TRY(h, launch_diag_reduce(h, h->dred));
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(h->hred, h->dred, DIAG_NQ * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->st));
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    for (int k = 0; k < MAX_SPECIES + 4; ++k) sums[k] = h->hred[k];
+    bad = h->hred[MAX_SPECIES + 4] != 0.0;
+  } else {
+    // a full pass over the populations of the current state
+    LBM_CUDA_TRY(h, cudaMemsetAsync(h->dred, 0, (MAX_SPECIES + 4) * DIAG_SPREAD * sizeof(double), h->st));
+    LBM_CUDA_TRY(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->st));
+    LBM_CUDA_TRY(h, launch_diagnostics(h));
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(h->hred, h->dred, (MAX_SPECIES + 4) * DIAG_SPREAD * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->st));
+    int flag = 0;
+    LBM_CUDA_TRY(h, cudaMemcpyAsync(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    // the kernel sums deviations from n_ref into DIAG_SPREAD partials per
+    // quantity
+    for (int k = 0; k < MAX_SPECIES + 4; ++k) {
+      double t = 0.0;
+      for (int j = 0; j < DIAG_SPREAD; ++j) t += h->hred[k * DIAG_SPREAD + j];
+      sums[k] = t;
+    }
+    bad = flag != 0;
   }
+  // the reference parts n_ref x fluid nodes are exact
   const int S = h->S;
   const double nf = (double)h->nfluid;
   double zref = 0.0;
   for (int s = 0; s < S; ++s) {
-    out[s] = nf * (double)h->nref[s] + h->hred[s];
+    out[s] = nf * (double)h->nref[s] + sums[s];
     zref += (double)h->valence[s] * (double)h->nref[s];
   }
-  for (int d = 0; d < 3; ++d) out[S + d] = h->mass0 * h->hred[MAX_SPECIES + d];
-  out[S + 3] = nf * zref + h->hred[MAX_SPECIES + 3];
+  for (int d = 0; d < 3; ++d) out[S + d] = h->mass0 * sums[MAX_SPECIES + d];
+  out[S + 3] = nf * zref + sums[MAX_SPECIES + 3];
   out[S + 4] = (double)h->last_iters;
   out[S + 5] = h->last_res;
   out[S + 6] = (double)h->tstep;
+  for (int k = 0; k < S + 4; ++k) bad = bad || !isfinite(out[k]);
   if (bad) return fail(h, LBM_EUNSTABLE, "non-finite or non-positive density detected");
   return LBM_OK;
 }
@@ -671,6 +776,7 @@ lbm_status lbm_set_state(lbm_t* h, const float* state, int64_t step) {
                                   cudaMemcpyHostToDevice, h->st));
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   h->tstep = step;
+  h->diag_valid = false;
   return potential_history_reset(h);
 }
 

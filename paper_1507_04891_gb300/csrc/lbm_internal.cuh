@@ -16,6 +16,10 @@ constexpr int Q = 19;
 constexpr int MAX_SPECIES = 4;
 // partial slots per diagnostics quantity (k_diag)
 constexpr int DIAG_SPREAD = 64;
+// quantities of the per-CTA diagnostics partials of the stream/collide
+// kernel: MAX_SPECIES mass deviations, momentum x, y, z, charge, count of
+// non-finite or non-positive densities
+constexpr int DIAG_NQ = MAX_SPECIES + 5;
 
 // Potential psi is held on the device as a signed 64-bit fixed-point number
 // with 52 fractional bits: psi = k * 2^-52 (|psi| < 2^11 = 2048, far beyond
@@ -36,17 +40,32 @@ constexpr double PSI_MAX = 2048.0;                      // 2^11
 // source of vanishing norm is solved once the residual is within twice that.
 constexpr double RES_FLOOR_RMS = 4.0;
 
-// Extrapolation in time of a fixed-point potential from its last three
-// values a = psi(t-1), b = psi(t-2), c = psi(t-3): the parabola through them,
-// 3a - 3b + c, or 2a - b and a while the history holds one or no older
-// value (`order`).  Exact in 128-bit integers; a value outside 2^61 units
-// keeps a.
-__device__ __forceinline__ int64_t extrapolate1(int64_t a, int64_t b, int64_t c, int order) {
+// Extrapolation in time of a fixed-point potential from its last values
+// a = psi(t-1), b = psi(t-2), c = psi(t-3), d = psi(t-4), `order` of the
+// older ones being valid:
+//   order 0   a
+//   order 1   2a - b             (line)
+//   order 2   3a - 3b + c        (parabola)
+//   order 3   2a - 2c + d        (exact for quadratics and for the
+//                                 alternation (-1)^t, which the parabola
+//                                 amplifies sevenfold; it needs no b)
+// Exact in 128-bit integers; a value outside 2^61 units keeps a.
+__device__ __forceinline__ int64_t extrapolate1(int64_t a, int64_t b, int64_t c, int64_t d,
+                                                int order) {
   if (order <= 0) return a;
-  const __int128 g = order == 1 ? (__int128)2 * a - b : (__int128)3 * ((__int128)a - b) + c;
+  const __int128 A = a;
+  const __int128 g = order == 1   ? 2 * A - b
+                     : order == 2 ? 3 * (A - b) + c
+                                  : 2 * (A - c) + d;
   const __int128 lim = (__int128)1 << 61;
   return (g > lim || g < -lim) ? a : (int64_t)g;
 }
+// The history of the extrapolation: HIST_SLOTS lattice-sized buffers used as
+// a ring.  With ring position r, psi(t-2) is in slot (r + 2) % 3, psi(t-3)
+// in (r + 1) % 3 and psi(t-4) in r % 3; the start of a solve overwrites
+// slot r % 3 with psi(t-1), and r advances by one.
+constexpr int HIST_SLOTS = 3;
+constexpr int HIST_ORDER = 3;  // valid entries of a full history
 
 #ifdef __CUDACC__
 // Conversions between 64-bit integers and FP32 on the 32-bit integer and FP32
@@ -106,6 +125,7 @@ struct StepArgs {
   float nref[MAX_SPECIES];  // reference density of the 16-bit shifted storage
   uint32_t step;            // time step (seeds the stochastic rounding)
   const uint32_t* step_dev; // device copy of the step (graph replays) or NULL
+  double* diag;             // per-CTA diagnostics partials (DIAG_NQ per CTA) or NULL
 };
 
 struct PoissonLevel {
@@ -125,8 +145,9 @@ struct Poisson {
   int zlo = 0, nzb = 0, perz = 1;
   std::vector<PoissonLevel> lev;
   int64_t* psi[2] = {nullptr, nullptr};  // lattice-sized fixed-point buffers
-  int64_t* hist = nullptr;  // multigrid / SOR: 2 N, psi one and two steps older than psi
-  int hist_n = 0;           // valid entries of hist
+  int64_t* hist = nullptr;  // multigrid / SOR: HIST_SLOTS x N, the ring of older potentials
+  int hist_n = 0;           // valid entries of hist (0..HIST_ORDER)
+  int hist_ring = 0;        // ring position
   int cur = 0;
   int64_t* src = nullptr; // 4 pi l_B (rho_e + w) per lattice node (fixed point), no mean removed
   double* dsum = nullptr; // [0] sum of src over fluid, [1 + 2k] sum r^2, [2 + 2k] sum s^2 (fixed-point units), k < NSLOT
@@ -187,6 +208,11 @@ struct lbm {
   lbm_gb300::NNet* nn = nullptr;            // learned Poisson initial guess
   bool psi_valid = false;
   double* dred = nullptr;   // diagnostics partials, (MAX_SPECIES + 4) x DIAG_SPREAD (device)
+  // per-CTA diagnostics partials written by every stream/collide launch
+  // (DIAG_NQ doubles per CTA); diag_valid: they describe the current state
+  double* dpart = nullptr;
+  int64_t dpart_ctas = 0;   // CTAs of the last stream/collide launch
+  bool diag_valid = false;
   // set by the spectral plan when the fluid is one periodic run: the charge
   // kernel's partial sum writes the source mean of every plane there, and
   // sets charge_means_ready for the next solve (which consumes it)
@@ -240,6 +266,17 @@ cudaError_t launch_charge(lbm_t* h);
 cudaError_t launch_gather(lbm_t* h, int s, double* n_dev, double* u_dev,
                           double* f_dev);
 cudaError_t launch_diagnostics(lbm_t* h);
+// Plane sums of n and of the mid-step flux per species (lbm_plane_fluxes):
+// nz * S * 4 doubles, device.
+cudaError_t launch_plane_fluxes(lbm_t* h, double* out_dev);
+// Checks an initial species field in device memory (lbm_set_species_dev):
+// per-CTA fluid sums of n0 and counts of invalid entries, 2 doubles per CTA
+// in out (at most 256 CTAs, *nblk of them).
+cudaError_t launch_species_check(lbm_t* h, const double* n0_dev, const double* u0_dev, double* out,
+                                 int* nblk);
+// Sums the stream/collide kernel's per-CTA diagnostics partials into out
+// (DIAG_NQ doubles, device).
+cudaError_t launch_diag_reduce(lbm_t* h, double* out);
 cudaError_t launch_links(lbm_t* h, const uint8_t* solid_dev);
 cudaError_t launch_psi_to_double(lbm_t* h, const int64_t* psi, double* out);
 cudaError_t launch_psi_from_double(lbm_t* h, const double* in, int64_t* psi);

@@ -71,18 +71,15 @@ struct Fmt<LBM_FP32> {
   static __device__ __forceinline__ float ldd(const T* p, float wn) { return wn * *p; }
   static __device__ __forceinline__ float ldh(const T* p) { return *p; }
   static __device__ __forceinline__ void st(T* p, float d, float inv_wn) { *p = d * inv_wn; }
-  static __device__ __forceinline__ void sth_sr(T* p, float h, uint32_t) { *p = h; }
-  static __device__ __forceinline__ void sth_sr2(T* pa, float ha, T* pb, float hb, uint32_t) {
+  // stores h (and a second value hb at pb); returns the stored values
+  static __device__ __forceinline__ float sth_sr(T* p, float h, uint32_t) {
+    *p = h;
+    return h;
+  }
+  static __device__ __forceinline__ float2 sth_sr2(T* pa, float ha, T* pb, float hb, uint32_t) {
     *pa = ha;
     *pb = hb;
-  }
-  static __device__ __forceinline__ void st_sr(T* p, float d, float inv_wn, uint32_t) {
-    *p = d * inv_wn;
-  }
-  static __device__ __forceinline__ void st_sr2(T* pa, float da, T* pb, float db, float inv_wn,
-                                                uint32_t) {
-    *pa = da * inv_wn;
-    *pb = db * inv_wn;
+    return make_float2(ha, hb);
   }
 };
 
@@ -99,7 +96,7 @@ __device__ __forceinline__ uint32_t cvt_rs_bf16x2(float hi, float lo, uint32_t r
   asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
   return d;
 }
-// 16-bit formats: the same h.  st() rounds to nearest; st_sr() and st_sr2()
+// 16-bit formats: the same h.  st() rounds to nearest; sth_sr() and sth_sr2()
 // round stochastically (the hardware conversion draws on random bits to
 // round up with probability equal to the dropped fraction), so the stored
 // value is unbiased.  The per-step change of a slowly diffusing mode is a
@@ -113,27 +110,21 @@ struct Fmt<LBM_FP16_SHIFT> {
   }
   static __device__ __forceinline__ float ldd(const T* p, float wn) { return wn * __half2float(*p); }
   static __device__ __forceinline__ float ldh(const T* p) { return __half2float(*p); }
-  static __device__ __forceinline__ void sth_sr(T* p, float h, uint32_t rnd) {
-    const uint32_t v = cvt_rs_f16x2(h, 0.0f, rnd);
-    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(v >> 16);
-  }
-  static __device__ __forceinline__ void sth_sr2(T* pa, float ha, T* pb, float hb, uint32_t rnd) {
-    const uint32_t v = cvt_rs_f16x2(ha, hb, rnd);
-    *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(v >> 16);
-    *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(v & 0xFFFFu);
-  }
   static __device__ __forceinline__ void st(T* p, float d, float inv_wn) {
     *p = __float2half_rn(d * inv_wn);
   }
-  static __device__ __forceinline__ void st_sr(T* p, float d, float inv_wn, uint32_t rnd) {
-    const uint32_t v = cvt_rs_f16x2(d * inv_wn, 0.0f, rnd);
+  // stochastic rounding; returns the stored values
+  static __device__ __forceinline__ float sth_sr(T* p, float h, uint32_t rnd) {
+    const uint32_t v = cvt_rs_f16x2(h, 0.0f, rnd);
     *reinterpret_cast<unsigned short*>(p) = (unsigned short)(v >> 16);
+    return __high2float(*reinterpret_cast<const __half2*>(&v));
   }
-  static __device__ __forceinline__ void st_sr2(T* pa, float da, T* pb, float db, float inv_wn,
-                                                uint32_t rnd) {
-    const uint32_t v = cvt_rs_f16x2(da * inv_wn, db * inv_wn, rnd);
+  static __device__ __forceinline__ float2 sth_sr2(T* pa, float ha, T* pb, float hb, uint32_t rnd) {
+    const uint32_t v = cvt_rs_f16x2(ha, hb, rnd);
     *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(v >> 16);
     *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(v & 0xFFFFu);
+    const float2 r = __half22float2(*reinterpret_cast<const __half2*>(&v));
+    return make_float2(r.y, r.x);  // ha sits in the upper half
   }
 };
 template <>
@@ -146,27 +137,21 @@ struct Fmt<LBM_BF16_SHIFT> {
     return wn * __bfloat162float(*p);
   }
   static __device__ __forceinline__ float ldh(const T* p) { return __bfloat162float(*p); }
-  static __device__ __forceinline__ void sth_sr(T* p, float h, uint32_t rnd) {
-    const uint32_t v = cvt_rs_bf16x2(h, 0.0f, rnd);
-    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(v >> 16);
-  }
-  static __device__ __forceinline__ void sth_sr2(T* pa, float ha, T* pb, float hb, uint32_t rnd) {
-    const uint32_t v = cvt_rs_bf16x2(ha, hb, rnd);
-    *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(v >> 16);
-    *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(v & 0xFFFFu);
-  }
   static __device__ __forceinline__ void st(T* p, float d, float inv_wn) {
     *p = __float2bfloat16_rn(d * inv_wn);
   }
-  static __device__ __forceinline__ void st_sr(T* p, float d, float inv_wn, uint32_t rnd) {
-    const uint32_t v = cvt_rs_bf16x2(d * inv_wn, 0.0f, rnd);
+  // stochastic rounding; returns the stored values (a bfloat16 is the upper
+  // half of the float it rounds)
+  static __device__ __forceinline__ float sth_sr(T* p, float h, uint32_t rnd) {
+    const uint32_t v = cvt_rs_bf16x2(h, 0.0f, rnd);
     *reinterpret_cast<unsigned short*>(p) = (unsigned short)(v >> 16);
+    return __uint_as_float(v & 0xFFFF0000u);
   }
-  static __device__ __forceinline__ void st_sr2(T* pa, float da, T* pb, float db, float inv_wn,
-                                                uint32_t rnd) {
-    const uint32_t v = cvt_rs_bf16x2(da * inv_wn, db * inv_wn, rnd);
+  static __device__ __forceinline__ float2 sth_sr2(T* pa, float ha, T* pb, float hb, uint32_t rnd) {
+    const uint32_t v = cvt_rs_bf16x2(ha, hb, rnd);
     *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(v >> 16);
     *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(v & 0xFFFFu);
+    return make_float2(__uint_as_float(v & 0xFFFF0000u), __uint_as_float(v << 16));
   }
 };
 
@@ -315,6 +300,20 @@ __device__ __forceinline__ void block_sum_to(long long v, double* out) {
   }
 }
 
+// Force per unit mass on species a (Sec. 2): the electric acceleration
+// z_a E (E: applied field minus c_s^2 grad psi) and the drag
+// -omega_drag sum_b (n_b / n)(v_a - v_b) on the velocities shifted by half
+// the electric acceleration, v = u + z E / 2, written with the number-
+// weighted mean vb of the v_b (equal masses).
+__device__ __forceinline__ void species_force(float usx, float usy, float usz, float zs, float Ex,
+                                              float Ey, float Ez, float vbx, float vby, float vbz,
+                                              float omd, float& Fx, float& Fy, float& Fz) {
+  const float ex = zs * Ex, ey = zs * Ey, ez = zs * Ez;
+  Fx = ex - omd * (usx + 0.5f * ex - vbx);
+  Fy = ey - omd * (usy + 0.5f * ey - vby);
+  Fz = ez - omd * (usz + 0.5f * ez - vbz);
+}
+
 // ---------------------------------------------------------------------------
 // Fused stream + collide, one thread per node, all S species in registers.
 //   1. pull the 19*S populations f_p^alpha(r, t), as deviations from
@@ -328,136 +327,199 @@ __device__ __forceinline__ void block_sum_to(long long v, double* out) {
 //      a = u^a . c (algebraically equal to the Appendix expression);
 //      g_p = n w [3 F.c + 9 (F.c)(u.c) - 3 F.u]             (Eq. ourforc)
 //   5. store f* at r.
+//   6. FP64 diagnostics of the state after the step (Sec. 3: species
+//      continuity, total momentum): every stored value is pulled by exactly
+//      one fluid node at the next step (by r + c_p, or by r itself in the
+//      opposite direction when r + c_p is a wall node), so the sums of the
+//      stored values give the next state's species masses, and the stored
+//      values signed by the direction they are pulled in give its momentum.
+//      Per CTA: the deviation sums (FP32 within a warp, FP64 across warps)
+//      and a count of nodes whose density entering the step was not finite
+//      and positive, written to a[blockIdx.x * DIAG_NQ + k].
 // ---------------------------------------------------------------------------
 template <int S, bool WALLS, bool CHARGED, int ST>
 __global__ void __launch_bounds__(256, WALLS ? 2 : 1) k_stream_collide(const StepArgs a) {
   using T = typename Fmt<ST>::T;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (uint32_t)a.N) return;
+  // deviation sums of the state after the step: masses, momentum, charge
+  float qm[S], qjx = 0.f, qjy = 0.f, qjz = 0.f, qbad = 0.f;
+#pragma unroll
+  for (int s = 0; s < S; ++s) qm[s] = 0.f;
   uint32_t lk = 0;
-  if (WALLS) {
+  bool active = i < (uint32_t)a.N;
+  if (WALLS && active) {
     lk = a.links[i];
-    if (lk & LINK_SOLID) return;
+    active = !(lk & LINK_SOLID);
   }
-  int x, y, z;
-  site_xyz(i, a.nx, a.ny, x, y, z);
-  const Nbr o = neighbours(x, y, z, a.nx, a.ny, a.nz);
-  const T* __restrict__ fin = static_cast<const T*>(a.fin);
-  T* __restrict__ fout = static_cast<T*>(a.fout);
-  const int64_t N = a.N;
+  if (active) {
+    int x, y, z;
+    site_xyz(i, a.nx, a.ny, x, y, z);
+    const Nbr o = neighbours(x, y, z, a.nx, a.ny, a.nz);
+    const T* __restrict__ fin = static_cast<const T*>(a.fin);
+    T* __restrict__ fout = static_cast<T*>(a.fout);
+    const int64_t N = a.N;
 
-  // stored h_p = (f_p - w_p n_ref) / (w_p n_ref) of every species
-  float f[S][Q];
-#pragma unroll
-  for (int p = 0; p < Q; ++p) {
-    const int d = upstream(o, p);
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      f[s][p] = pull_h<ST, WALLS>(fin, N, s, p, i, d, lk);
-    }
-  }
-
-  // n = n_ref (1 + sum w h), j = n_ref sum c w h  (sum w = 1, sum w c = 0)
-  float mh[S], dn[S], n[S], jx[S], jy[S], jz[S];
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    float m0 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+    // stored h_p = (f_p - w_p n_ref) / (w_p n_ref) of every species
+    float f[S][Q];
 #pragma unroll
     for (int p = 0; p < Q; ++p) {
-      const float wh = WT(p) * f[s][p];
-      m0 += wh;
-      if (CX(p)) mx += CX(p) * wh;
-      if (CY(p)) my += CY(p) * wh;
-      if (CZ(p)) mz += CZ(p) * wh;
+      const int d = upstream(o, p);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        f[s][p] = pull_h<ST, WALLS>(fin, N, s, p, i, d, lk);
+      }
     }
-    const float r = a.nref[s];
-    mh[s] = m0;
-    dn[s] = r * m0;
-    n[s] = r + dn[s];
-    jx[s] = r * mx;
-    jy[s] = r * my;
-    jz[s] = r * mz;
+
+    // n = n_ref (1 + sum w h), j = n_ref sum c w h  (sum w = 1, sum w c = 0)
+    float mh[S], dn[S], n[S], jx[S], jy[S], jz[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      float m0 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+      for (int p = 0; p < Q; ++p) {
+        const float wh = WT(p) * f[s][p];
+        m0 += wh;
+        if (CX(p)) mx += CX(p) * wh;
+        if (CY(p)) my += CY(p) * wh;
+        if (CZ(p)) mz += CZ(p) * wh;
+      }
+      const float r = a.nref[s];
+      mh[s] = m0;
+      dn[s] = r * m0;
+      n[s] = r + dn[s];
+      jx[s] = r * mx;
+      jy[s] = r * my;
+      jz[s] = r * mz;
+      if (!(n[s] > 0.f) || !isfinite(n[s])) qbad = 1.f;
+    }
+
+    float ntot = 0.f, Jx = 0.f, Jy = 0.f, Jz = 0.f;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      ntot += n[s];
+      Jx += jx[s];
+      Jy += jy[s];
+      Jz += jz[s];
+    }
+    const float inv_ntot = 1.0f / ntot;
+    // barycentric velocity (equal masses: mass-weighted = number-weighted)
+    const float ux = Jx * inv_ntot, uy = Jy * inv_ntot, uz = Jz * inv_ntot;
+
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (CHARGED) psi_gradient<WALLS>(a, i, o, lk, gx, gy, gz);
+    const float Ex = -CS2 * gx + a.eext[0];
+    const float Ey = -CS2 * gy + a.eext[1];
+    const float Ez = -CS2 * gz + a.eext[2];
+
+    // number-weighted mean of the drag velocities u^a + F_el^a / 2
+    float zn = 0.f;
+#pragma unroll
+    for (int s = 0; s < S; ++s) zn += a.valence[s] * n[s];
+    const float vbx = (Jx + 0.5f * zn * Ex) * inv_ntot;
+    const float vby = (Jy + 0.5f * zn * Ey) * inv_ntot;
+    const float vbz = (Jz + 0.5f * zn * Ez) * inv_ntot;
+
+    const float om = a.omega_visc;
+    const float omd = a.omega_drag_z ? a.omega_drag_z[z] : a.omega_drag;
+    uint32_t rnd = 0;
+    if (ST != LBM_FP32) rnd = mix32(i * 0x9E3779B9u ^ mix32(a.step_dev ? *a.step_dev : a.step));
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const float inv_n = 1.0f / n[s];
+      const float usx = jx[s] * inv_n, usy = jy[s] * inv_n, usz = jz[s] * inv_n;
+      float Fx, Fy, Fz;
+      species_force(usx, usy, usz, a.valence[s], Ex, Ey, Ez, vbx, vby, vbz, omd, Fx, Fy, Fz);
+      const float usq = usx * usx + usy * usy + usz * usz;
+      const float Fu = Fx * ux + Fy * uy + Fz * uz;
+      // In deviations, d*_p = (1 - omega) d_p + [omega phi_p + g_p - omega w_p n_ref]
+      // with, per weight w_p,
+      //   omega phi_p + g_p - omega w_p n_ref
+      //     = w_p [omega dn + n (-1.5 omega |u^a|^2 - 3 F.u
+      //                          + 4.5 omega a^2 + 9 (F.c)(u.c))]      (even in c)
+      //     + w_p n 3 (omega a + F.c)                                 (odd in c)
+      // a = u^a.c (phi_perp in its reduced form, the Appendix expression;
+      // g_p of Eq. ourforc).  Divided by w_p n_ref this updates the stored
+      // h = d / (w_p n_ref) directly: h*_p = (1 - omega) h_p + (even' +/- odd') / n_ref,
+      // with the bracket values even', odd' free of w_p.  Every term is of
+      // the size of the deviations.
+      const float base = n[s] * (-1.5f * om * usq - 3.0f * Fu);
+      const float odn = om * dn[s];
+      const float inr = 1.0f / a.nref[s];
+      // moving populations first; the rest population then takes
+      // d*_0 = dn - sum_{p>0} d*_p over the stored (rounded) moving values,
+      // i.e. h*_0 = (sum w h - sum_{p>0} w h*_p) / w_0, which holds exactly
+      // in real arithmetic (phi_perp carries mass n, g_p none) and keeps the
+      // rounding of the weights and of 16-bit stores from drifting the
+      // species mass.
+      // Directions come in opposite pairs (p, p+1), c_{p+1} = -c_p: a = u^a.c,
+      // F.c and u.c flip sign, so each pair shares the even part and takes
+      // +/- the odd part.
+      const float omm = 1.0f - om;
+      float moved = 0.f, mjx = 0.f, mjy = 0.f, mjz = 0.f;
+#pragma unroll
+      for (int p = 1; p < Q; p += 2) {
+        const float av = CX(p) * usx + CY(p) * usy + CZ(p) * usz;
+        const float fc = CX(p) * Fx + CY(p) * Fy + CZ(p) * Fz;
+        const float uc = CX(p) * ux + CY(p) * uy + CZ(p) * uz;
+        const float even = inr * (odn + base + n[s] * (4.5f * om * av * av + 9.0f * fc * uc));
+        const float odd = inr * n[s] * 3.0f * (om * av + fc);
+        const float2 hs = Fmt<ST>::sth_sr2(fout + (int64_t)(s * Q + p) * N + i,
+                                           omm * f[s][p] + (even + odd),
+                                           fout + (int64_t)(s * Q + p + 1) * N + i,
+                                           omm * f[s][p + 1] + (even - odd), lcg_next(rnd));
+        moved += WT(p) * (hs.x + hs.y);  // same weight for p and p+1
+        // momentum carried by the pair at the next step: h*_p moves along
+        // c_p unless r + c_p is a wall node (bit p+1), then it is pulled
+        // back along -c_p; h*_{p+1} likewise with bit p
+        float mj = hs.x - hs.y;
+        if (WALLS) mj = (((lk >> (p + 1)) & 1u) ? -hs.x : hs.x) - (((lk >> p) & 1u) ? -hs.y : hs.y);
+        if (CX(p)) mjx += CX(p) * WT(p) * mj;
+        if (CY(p)) mjy += CY(p) * WT(p) * mj;
+        if (CZ(p)) mjz += CZ(p) * WT(p) * mj;
+      }
+      const float h0 = Fmt<ST>::sth_sr(fout + (int64_t)(s * Q) * N + i, (mh[s] - moved) * INV_WT(0),
+                                       lcg_next(rnd));
+      const float r = a.nref[s];
+      qm[s] = r * (WT(0) * h0 + moved);
+      qjx += r * mjx;
+      qjy += r * mjy;
+      qjz += r * mjz;
+    }
   }
 
-  float ntot = 0.f, Jx = 0.f, Jy = 0.f, Jz = 0.f;
+  // per-CTA partial sums of the diagnostics (inactive threads add zeros)
+  if (a.diag) {
+    float q[DIAG_NQ];
 #pragma unroll
-  for (int s = 0; s < S; ++s) {
-    ntot += n[s];
-    Jx += jx[s];
-    Jy += jy[s];
-    Jz += jz[s];
-  }
-  const float inv_ntot = 1.0f / ntot;
-  // barycentric velocity (equal masses: mass-weighted = number-weighted)
-  const float ux = Jx * inv_ntot, uy = Jy * inv_ntot, uz = Jz * inv_ntot;
-
-  float gx = 0.f, gy = 0.f, gz = 0.f;
-  if (CHARGED) psi_gradient<WALLS>(a, i, o, lk, gx, gy, gz);
-  const float Ex = -CS2 * gx + a.eext[0];
-  const float Ey = -CS2 * gy + a.eext[1];
-  const float Ez = -CS2 * gz + a.eext[2];
-
-  // number-weighted mean of the drag velocities u^a + F_el^a / 2
-  float zn = 0.f;
+    for (int k = 0; k < DIAG_NQ; ++k) q[k] = 0.f;
+    float qc = 0.f;
 #pragma unroll
-  for (int s = 0; s < S; ++s) zn += a.valence[s] * n[s];
-  const float vbx = (Jx + 0.5f * zn * Ex) * inv_ntot;
-  const float vby = (Jy + 0.5f * zn * Ey) * inv_ntot;
-  const float vbz = (Jz + 0.5f * zn * Ez) * inv_ntot;
-
-  const float om = a.omega_visc;
-  const float omd = a.omega_drag_z ? a.omega_drag_z[z] : a.omega_drag;
-  uint32_t rnd = 0;
-  if (ST != LBM_FP32) rnd = mix32(i * 0x9E3779B9u ^ mix32(a.step_dev ? *a.step_dev : a.step));
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const float inv_n = 1.0f / n[s];
-    const float usx = jx[s] * inv_n, usy = jy[s] * inv_n, usz = jz[s] * inv_n;
-    const float zs = a.valence[s];
-    const float ex = zs * Ex, ey = zs * Ey, ez = zs * Ez;
-    const float Fx = ex - omd * (usx + 0.5f * ex - vbx);
-    const float Fy = ey - omd * (usy + 0.5f * ey - vby);
-    const float Fz = ez - omd * (usz + 0.5f * ez - vbz);
-    const float usq = usx * usx + usy * usy + usz * usz;
-    const float Fu = Fx * ux + Fy * uy + Fz * uz;
-    // In deviations, d*_p = (1 - omega) d_p + [omega phi_p + g_p - omega w_p n_ref]
-    // with, per weight w_p,
-    //   omega phi_p + g_p - omega w_p n_ref
-    //     = w_p [omega dn + n (-1.5 omega |u^a|^2 - 3 F.u
-    //                          + 4.5 omega a^2 + 9 (F.c)(u.c))]      (even in c)
-    //     + w_p n 3 (omega a + F.c)                                 (odd in c)
-    // a = u^a.c (phi_perp in its reduced form, the Appendix expression;
-    // g_p of Eq. ourforc).  Divided by w_p n_ref this updates the stored
-    // h = d / (w_p n_ref) directly: h*_p = (1 - omega) h_p + (even' +/- odd') / n_ref,
-    // with the bracket values even', odd' free of w_p.  Every term is of
-    // the size of the deviations.
-    const float base = n[s] * (-1.5f * om * usq - 3.0f * Fu);
-    const float odn = om * dn[s];
-    const float inr = 1.0f / a.nref[s];
-    // moving populations first; the rest population then takes
-    // d*_0 = dn - sum_{p>0} d*_p, i.e. h*_0 = (sum w h - sum_{p>0} w h*_p) / w_0,
-    // which holds exactly in real arithmetic (phi_perp carries mass n,
-    // g_p none) and keeps FP32 rounding of the weights from drifting the
-    // species mass.
-    // Directions come in opposite pairs (p, p+1), c_{p+1} = -c_p: a = u^a.c,
-    // F.c and u.c flip sign, so each pair shares the even part and takes
-    // +/- the odd part.
-    const float omm = 1.0f - om;
-    float moved = 0.f;
-#pragma unroll
-    for (int p = 1; p < Q; p += 2) {
-      const float av = CX(p) * usx + CY(p) * usy + CZ(p) * usz;
-      const float fc = CX(p) * Fx + CY(p) * Fy + CZ(p) * Fz;
-      const float uc = CX(p) * ux + CY(p) * uy + CZ(p) * uz;
-      const float even = inr * (odn + base + n[s] * (4.5f * om * av * av + 9.0f * fc * uc));
-      const float odd = inr * n[s] * 3.0f * (om * av + fc);
-      const float ha = omm * f[s][p] + (even + odd);
-      const float hb = omm * f[s][p + 1] + (even - odd);
-      moved += WT(p) * (ha + hb);  // same weight for p and p+1
-      Fmt<ST>::sth_sr2(fout + (int64_t)(s * Q + p) * N + i, ha,
-                       fout + (int64_t)(s * Q + p + 1) * N + i, hb, lcg_next(rnd));
+    for (int s = 0; s < S; ++s) {
+      q[s] = qm[s];
+      qc += a.valence[s] * qm[s];
     }
-    Fmt<ST>::sth_sr(fout + (int64_t)(s * Q) * N + i, (mh[s] - moved) * INV_WT(0), lcg_next(rnd));
+    q[MAX_SPECIES + 0] = qjx;
+    q[MAX_SPECIES + 1] = qjy;
+    q[MAX_SPECIES + 2] = qjz;
+    q[MAX_SPECIES + 3] = qc;
+    q[MAX_SPECIES + 4] = qbad;
+    __shared__ float red[8][DIAG_NQ];
+#pragma unroll
+    for (int k = 0; k < DIAG_NQ; ++k) {
+      float v = q[k];
+      if (k >= S && k < MAX_SPECIES) continue;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < DIAG_NQ) {
+      const int k = threadIdx.x;
+      double tot = 0.0;
+      if (k < S || k >= MAX_SPECIES)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += (double)red[w][k];
+      a.diag[(int64_t)blockIdx.x * DIAG_NQ + k] = tot;
+    }
   }
 }
 
@@ -739,6 +801,153 @@ __global__ void __launch_bounds__(256) k_diag(const void* fin_v,
   }
 }
 
+// Plane sums of the current state f(t): one CTA per z-plane; for each
+// species the sum over the plane's fluid nodes of n^a and of the mid-step
+// flux n^a (u^a + F^a / 2) (the velocity of the second-order forcing,
+// Eq. ourforc), F^a the force of the stream/collide kernel (species_force)
+// on f(t) with the potential in a.psi.  out[(z S + s) 4 + k], k = 0: n,
+// 1..3: flux x, y, z.  Node values in FP32 (as in the step), sums in FP64.
+template <int S, bool WALLS, bool CHARGED, int ST>
+__global__ void __launch_bounds__(256) k_plane_fluxes(const StepArgs a, double* __restrict__ out) {
+  using T = typename Fmt<ST>::T;
+  const int z = blockIdx.x;
+  const int nxy = a.nx * a.ny;
+  double acc[S][4];
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[s][k] = 0.0;
+  const T* __restrict__ fin = static_cast<const T*>(a.fin);
+  for (int k = threadIdx.x; k < nxy; k += blockDim.x) {
+    const uint32_t i = (uint32_t)z * (uint32_t)nxy + (uint32_t)k;
+    uint32_t lk = 0;
+    if (WALLS) {
+      lk = a.links[i];
+      if (lk & LINK_SOLID) continue;
+    }
+    int x, y, zz;
+    site_xyz(i, a.nx, a.ny, x, y, zz);
+    const Nbr o = neighbours(x, y, zz, a.nx, a.ny, a.nz);
+    float n[S], jx[S], jy[S], jz[S];
+    float ntot = 0.f, Jx = 0.f, Jy = 0.f, Jz = 0.f, zn = 0.f;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      float m0 = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+      for (int p = 0; p < Q; ++p) {
+        const float wh = WT(p) * pull_h<ST, WALLS>(fin, a.N, s, p, i, upstream(o, p), lk);
+        m0 += wh;
+        if (CX(p)) mx += CX(p) * wh;
+        if (CY(p)) my += CY(p) * wh;
+        if (CZ(p)) mz += CZ(p) * wh;
+      }
+      const float r = a.nref[s];
+      n[s] = r + r * m0;
+      jx[s] = r * mx;
+      jy[s] = r * my;
+      jz[s] = r * mz;
+      ntot += n[s];
+      Jx += jx[s];
+      Jy += jy[s];
+      Jz += jz[s];
+      zn += a.valence[s] * n[s];
+    }
+    const float inv_ntot = 1.0f / ntot;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (CHARGED) psi_gradient<WALLS>(a, i, o, lk, gx, gy, gz);
+    const float Ex = -CS2 * gx + a.eext[0];
+    const float Ey = -CS2 * gy + a.eext[1];
+    const float Ez = -CS2 * gz + a.eext[2];
+    const float vbx = (Jx + 0.5f * zn * Ex) * inv_ntot;
+    const float vby = (Jy + 0.5f * zn * Ey) * inv_ntot;
+    const float vbz = (Jz + 0.5f * zn * Ez) * inv_ntot;
+    const float omd = a.omega_drag_z ? a.omega_drag_z[zz] : a.omega_drag;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const float inv_n = 1.0f / n[s];
+      float Fx, Fy, Fz;
+      species_force(jx[s] * inv_n, jy[s] * inv_n, jz[s] * inv_n, a.valence[s], Ex, Ey, Ez, vbx, vby,
+                    vbz, omd, Fx, Fy, Fz);
+      acc[s][0] += (double)n[s];
+      acc[s][1] += (double)(jx[s] + 0.5f * n[s] * Fx);
+      acc[s][2] += (double)(jy[s] + 0.5f * n[s] * Fy);
+      acc[s][3] += (double)(jz[s] + 0.5f * n[s] * Fz);
+    }
+  }
+  __shared__ double red[8][S * 4];
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double v = acc[s][k];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][s * 4 + k] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < S * 4) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+    out[(int64_t)z * S * 4 + threadIdx.x] = t;
+  }
+}
+
+// Checks an initial density (and velocity) field in device memory: per CTA
+// (grid-stride) the sum of n0 over fluid nodes and the number of fluid nodes
+// where n0 is not finite and positive or u0 not finite, written to
+// out[2 b], out[2 b + 1].
+__global__ void __launch_bounds__(256) k_species_check(const double* __restrict__ n0,
+                                                       const double* __restrict__ u0,
+                                                       const uint32_t* __restrict__ links,
+                                                       int64_t N, double* __restrict__ out) {
+  double sum = 0.0, bad = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (links && (links[i] & LINK_SOLID)) continue;
+    const double v = n0[i];
+    bool ok = v > 0.0 && isfinite(v);
+    if (u0) ok = ok && isfinite(u0[i]) && isfinite(u0[N + i]) && isfinite(u0[2 * N + i]);
+    if (ok) sum += v;
+    else bad += 1.0;
+  }
+  __shared__ double red[2][8];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sum += __shfl_down_sync(0xffffffffu, sum, off);
+    bad += __shfl_down_sync(0xffffffffu, bad, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sum;
+    red[1][threadIdx.x >> 5] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+    out[2 * blockIdx.x + threadIdx.x] = t;
+  }
+}
+
+// Sums the per-CTA diagnostics partials of the stream/collide kernel: one
+// CTA per quantity, FP64, in a fixed order (the result does not depend on
+// scheduling).
+__global__ void __launch_bounds__(256) k_diag_reduce(const double* __restrict__ part,
+                                                     int64_t nctas, double* __restrict__ out) {
+  const int k = blockIdx.x;
+  double v = 0.0;
+  for (int64_t c = threadIdx.x; c < nctas; c += blockDim.x) v += part[c * DIAG_NQ + k];
+  __shared__ double red[8];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[k] = t;
+  }
+}
+
 // Link words from the wall mask: bit 0 = wall node, bit p = r - c_p is wall.
 __global__ void k_links(const uint8_t* solid, uint32_t* links, int nx, int ny,
                         int nz, int64_t N) {
@@ -828,7 +1037,7 @@ float4 as_f4(const float* v) { return make_float4(v[0], v[1], v[2], v[3]); }
 }  // namespace
 
 namespace {
-cudaError_t collide_into_spare(lbm_t* h, int threads) {
+StepArgs step_args(lbm_t* h) {
   StepArgs a;
   a.fin = h->f[h->cur];
   a.fout = h->f[h->cur ^ 1];
@@ -852,6 +1061,14 @@ cudaError_t collide_into_spare(lbm_t* h, int threads) {
   a.step = (uint32_t)h->tstep;
   a.step_dev = nullptr;
   if (h->gstatus) a.step_dev = reinterpret_cast<const uint32_t*>(h->gstatus);
+  a.diag = h->dpart;
+  return a;
+}
+
+cudaError_t collide_into_spare(lbm_t* h, int threads) {
+  const StepArgs a = step_args(h);
+  const bool charged = h->cfg.bjerrum > 0.0;
+  h->dpart_ctas = (int64_t)nblocks(h->N, threads);
   switch (h->cfg.storage) {
     case LBM_FP32: return dispatch_s<LBM_FP32>(a, h->S, h->has_walls, charged, h->st, threads);
     case LBM_FP16_SHIFT: return dispatch_s<LBM_FP16_SHIFT>(a, h->S, h->has_walls, charged, h->st, threads);
@@ -866,6 +1083,7 @@ cudaError_t launch_stream_collide(lbm_t* h) {
   if (e == cudaSuccess) {
     h->cur ^= 1;
     ++h->launches;
+    h->diag_valid = true;
   }
   return e;
 }
@@ -873,7 +1091,23 @@ cudaError_t launch_stream_collide(lbm_t* h) {
 cudaError_t launch_stream_collide_probe(lbm_t* h, int threads) {
   cudaError_t e = collide_into_spare(h, threads);
   if (e == cudaSuccess) ++h->launches;
+  h->diag_valid = false;  // the partials describe the spare lattice
   return e;
+}
+
+cudaError_t launch_species_check(lbm_t* h, const double* n0_dev, const double* u0_dev, double* out,
+                                 int* nblk) {
+  const int nb = (int)std::min<int64_t>(nblocks(h->N, 256), 256);
+  k_species_check<<<nb, 256, 0, h->st>>>(n0_dev, u0_dev, h->links, h->N, out);
+  ++h->launches;
+  *nblk = nb;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_reduce(lbm_t* h, double* out) {
+  k_diag_reduce<<<DIAG_NQ, 256, 0, h->st>>>(h->dpart, h->dpart_ctas, out);
+  ++h->launches;
+  return cudaGetLastError();
 }
 
 #define LBM_DISPATCH_WS(h, KERNEL_CALL)                                        \
@@ -894,6 +1128,24 @@ cudaError_t launch_stream_collide_probe(lbm_t* h, int threads) {
         break;                                                                 \
     }                                                                          \
   } while (0)
+
+cudaError_t launch_plane_fluxes(lbm_t* h, double* out_dev) {
+  const StepArgs a = step_args(h);
+  const bool c = h->cfg.bjerrum > 0.0;
+  const unsigned nb = (unsigned)h->cfg.nz;
+#define LBM_PF(SS)                                                                   \
+  LBM_DISPATCH_WS(h, (c ? k_plane_fluxes<SS, W_, true, ST_><<<nb, 256, 0, h->st>>>(a, out_dev)  \
+                        : k_plane_fluxes<SS, W_, false, ST_><<<nb, 256, 0, h->st>>>(a, out_dev)))
+  switch (h->S) {
+    case 1: LBM_PF(1); break;
+    case 2: LBM_PF(2); break;
+    case 3: LBM_PF(3); break;
+    default: LBM_PF(4); break;
+  }
+#undef LBM_PF
+  ++h->launches;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_init_species(lbm_t* h, int s, const double* n0,
                                 const double* u0) {

@@ -622,18 +622,23 @@ CL make_cl(const PoissonLevel& l) {
 }  // namespace
 
 namespace {
-// psi <- extrapolate1(psi(t-1), psi(t-2), psi(t-3)) and the history moved
-// one step; one node per thread (any N).
+// psi <- extrapolate1 of psi(t-1) and the older potentials of the history
+// ring (only those the order uses are read), psi(t-1) into the ring's
+// oldest slot; one node per thread (any N).
 __global__ void __launch_bounds__(256) k_extrapolate_nodes(int64_t* __restrict__ psi,
-                                                           int64_t* __restrict__ h1,
-                                                           int64_t* __restrict__ h2, int64_t n,
-                                                           int order) {
+                                                           int64_t* __restrict__ hist, int64_t n,
+                                                           int ring, int order) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int64_t a = psi[i], b = h1[i], c = h2[i];
-  psi[i] = extrapolate1(a, b, c, order);
-  h1[i] = a;
-  h2[i] = b;
+  int64_t* s2 = hist + (int64_t)((ring + 2) % HIST_SLOTS) * n;  // psi(t-2)
+  int64_t* s3 = hist + (int64_t)((ring + 1) % HIST_SLOTS) * n;  // psi(t-3)
+  int64_t* s4 = hist + (int64_t)(ring % HIST_SLOTS) * n;        // psi(t-4)
+  const int64_t a = psi[i];
+  const int64_t b = (order == 1 || order == 2) ? s2[i] : 0;
+  const int64_t c = order >= 2 ? s3[i] : 0;
+  const int64_t d = order >= 3 ? s4[i] : 0;
+  psi[i] = extrapolate1(a, b, c, d, order);
+  s4[i] = a;
 }
 
 void drop_graphs(Poisson& P) {
@@ -651,11 +656,12 @@ lbm_status poisson_step_start(lbm_t* h) {
     P.hist_n = 0;
     return LBM_OK;
   }
-  k_extrapolate_nodes<<<nblocks(h->N, 256), 256, 0, h->st>>>(P.psi[P.cur], P.hist, P.hist + h->N, h->N,
-                                                            P.hist_n);
+  k_extrapolate_nodes<<<nblocks(h->N, 256), 256, 0, h->st>>>(P.psi[P.cur], P.hist, h->N,
+                                                            P.hist_ring, P.hist_n);
   ++h->launches;
   LBM_CUDA_TRY(h, cudaGetLastError());
-  P.hist_n = std::min(P.hist_n + 1, 2);
+  P.hist_n = std::min(P.hist_n + 1, HIST_ORDER);
+  P.hist_ring = (P.hist_ring + 1) % HIST_SLOTS;
   return LBM_OK;
 }
 

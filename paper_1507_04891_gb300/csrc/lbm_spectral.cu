@@ -802,24 +802,32 @@ __global__ void __launch_bounds__(256, 4) k_res_planes(
 }
 
 // Start of a step's solve: psi(t-1) is replaced by its extrapolation in
-// time (extrapolate1: the parabola through the three previous potentials,
-// fewer terms while the history fills; `order` valid entries, read from
-// *order_dev when given); the history moves one step.  Any start is valid:
-// the solve iterates to the same tolerance from it.  Two nodes per thread
-// (N is even: nx >= 8).
-__global__ void __launch_bounds__(256) k_extrapolate(int64_t* __restrict__ psi, int64_t* __restrict__ h1,
-                                                     int64_t* __restrict__ h2, int64_t npairs,
-                                                     const int* __restrict__ order_dev, int order) {
+// time (extrapolate1 over the history ring; `order` valid entries and the
+// ring position read from the graph status when given); psi(t-1) joins the
+// ring in its oldest slot.  Only the history entries the order uses are
+// read: with a full history, psi, psi(t-3) and psi(t-4) in, psi and the
+// ring slot out.  Any start is valid: the solve iterates to the same
+// tolerance from it.  Two nodes per thread (N is even: nx >= 8).
+__global__ void __launch_bounds__(256) k_extrapolate(int64_t* __restrict__ psi, int64_t* __restrict__ hist,
+                                                     int64_t N, int64_t npairs,
+                                                     const int* __restrict__ order_dev,
+                                                     const int* __restrict__ ring_dev, int order,
+                                                     int ring) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= npairs) return;
-  const int ord = order_dev ? min(*order_dev, 2) : order;
+  const int ord = order_dev ? min(*order_dev, HIST_ORDER) : order;
+  const int rg = ring_dev ? *ring_dev : ring;
   longlong2* P = reinterpret_cast<longlong2*>(psi);
-  longlong2* H1 = reinterpret_cast<longlong2*>(h1);
-  longlong2* H2 = reinterpret_cast<longlong2*>(h2);
-  const longlong2 a = P[i], b = H1[i], c = H2[i];
-  P[i] = make_longlong2(extrapolate1(a.x, b.x, c.x, ord), extrapolate1(a.y, b.y, c.y, ord));
-  H1[i] = a;
-  H2[i] = b;
+  const longlong2* S2 = reinterpret_cast<const longlong2*>(hist + (int64_t)((rg + 2) % HIST_SLOTS) * N);
+  const longlong2* S3 = reinterpret_cast<const longlong2*>(hist + (int64_t)((rg + 1) % HIST_SLOTS) * N);
+  longlong2* S4 = reinterpret_cast<longlong2*>(hist + (int64_t)(rg % HIST_SLOTS) * N);
+  const longlong2 z = make_longlong2(0, 0);
+  const longlong2 a = P[i];
+  const longlong2 b = (ord == 1 || ord == 2) ? S2[i] : z;
+  const longlong2 c = ord >= 2 ? S3[i] : z;
+  const longlong2 d = ord >= 3 ? S4[i] : z;
+  P[i] = make_longlong2(extrapolate1(a.x, b.x, c.x, d.x, ord), extrapolate1(a.y, b.y, c.y, d.y, ord));
+  S4[i] = a;
 }
 
 int ilog2(int n) {
@@ -852,8 +860,9 @@ struct SpectralPlan {
   bool status_read = false;        // the host copy of the graph status is current
   bool runs_fit = true;            // z solve fits in shared memory
   float* r = nullptr;              // N (residual for the learned guess)
-  int64_t* hist = nullptr;         // 2 N: psi one and two steps older than psi
+  int64_t* hist = nullptr;         // HIST_SLOTS x N: the ring of older potentials
   int hist_n = 0;                  // valid entries of hist (host-driven steps)
+  int hist_ring = 0;               // ring position (host-driven steps)
   long long* psum = nullptr;       // nz
   long long* mean_z = nullptr;     // nz
   float* nacc = nullptr;           // norm slots, Poisson::NSLOT x 2 NACC
@@ -960,7 +969,7 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
             al((void**)&s->tw, ntw * sizeof(float2)) && al((void**)&s->lam, nlam * sizeof(float)) &&
             al((void**)&s->spec, (size_t)nz * s->mxy * sizeof(float2)) &&
             al((void**)&s->r, N * sizeof(float)) && al((void**)&s->psum, nz * sizeof(long long)) &&
-            al((void**)&s->hist, 2 * N * sizeof(int64_t)) &&
+            al((void**)&s->hist, HIST_SLOTS * N * sizeof(int64_t)) &&
             al((void**)&s->mean_z, nz * sizeof(long long)) &&
             al((void**)&s->nacc, (size_t)Poisson::NSLOT * 2 * NACC * sizeof(float));
   if (ok && cudaMallocHost((void**)&s->hacc, (size_t)Poisson::NSLOT * 2 * NACC * sizeof(float)) != cudaSuccess) {
@@ -989,7 +998,7 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   for (int k = 0; k <= nx / 2; ++k) lam.push_back(eig(k, nx));
   for (int k = 0; k < ny; ++k) lam.push_back(eig(k, ny));
   for (int k = 0; k < nz; ++k) lam.push_back(eig(k, nz));
-  LBM_CUDA_TRY(h, cudaMemset(s->hist, 0, 2 * N * sizeof(int64_t)));
+  LBM_CUDA_TRY(h, cudaMemset(s->hist, 0, HIST_SLOTS * N * sizeof(int64_t)));
   LBM_CUDA_TRY(h, cudaMemcpy(s->planes, planes.data(), planes.size() * sizeof(int), cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->runs, runs.data(), runs.size() * sizeof(Run), cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->plane_fluid, pf.data(), nz, cudaMemcpyHostToDevice));
@@ -1174,16 +1183,20 @@ cudaError_t spec_apply(lbm_t* h, int slot) {
 }
 
 // psi <- its extrapolation from the previous steps (k_extrapolate); the
-// number of valid history entries comes from *order_dev (graph steps) or
-// from the host count, which advances here.
-cudaError_t spec_extrapolate(lbm_t* h, const int* order_dev) {
+// number of valid history entries and the ring position come from the
+// graph status (graph steps: the test kernel advances them) or from the
+// host counts, which advance here.
+cudaError_t spec_extrapolate(lbm_t* h, const int* order_dev, const int* ring_dev) {
   SpectralPlan* s = h->spec;
   Poisson& P = h->ps;
   const int64_t np = h->N / 2;
-  k_extrapolate<<<nblk(np, 256), 256, 0, h->st>>>(P.psi[P.cur], s->hist, s->hist + h->N, np, order_dev,
-                                                  s->hist_n);
+  k_extrapolate<<<nblk(np, 256), 256, 0, h->st>>>(P.psi[P.cur], s->hist, h->N, np, order_dev, ring_dev,
+                                                  s->hist_n, s->hist_ring);
   ++h->launches;
-  if (!order_dev) s->hist_n = std::min(s->hist_n + 1, 2);
+  if (!order_dev) {
+    s->hist_n = std::min(s->hist_n + 1, HIST_ORDER);
+    s->hist_ring = (s->hist_ring + 1) % HIST_SLOTS;
+  }
   return cudaGetLastError();
 }
 
@@ -1198,7 +1211,7 @@ lbm_status spectral_step_start(lbm_t* h) {
     h->spec->hist_n = 0;
     return LBM_OK;
   }
-  LBM_CUDA_TRY(h, spec_extrapolate(h, nullptr));
+  LBM_CUDA_TRY(h, spec_extrapolate(h, nullptr, nullptr));
   return LBM_OK;
 }
 
@@ -1315,9 +1328,12 @@ struct GraphStatus {
   int iters;           // Poisson applications of the current step
   long long total;     // applications summed over replayed steps
   int fails;           // steps whose solve stopped at the iteration cap
-  int hist;            // valid entries of the potential history (0..2)
+  int hist;            // valid entries of the potential history (0..HIST_ORDER)
+  int ring;            // position of the history ring
   double rel;          // final relative residual of the last step
   int need[4];         // steps that needed 1, 2, 3, >= 4 applications since the host reset it
+  int needf[4];        // the same, counting only steps whose start had the full history
+  int full;            // the current step's start had the full history
 };
 
 // Convergence test (one warp).  first: after the k applications queued
@@ -1326,7 +1342,7 @@ struct GraphStatus {
 // will run.  Otherwise after one more application (slot k).  Sets the
 // condition of the while node.
 __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, double tol,
-                              double floor2, int maxit, int k, int first,
+                              double floor2, int maxit, int k, int first, int extrap,
                               cudaGraphConditionalHandle cond, cudaGraphConditionalHandle redo) {
   if (blockIdx.x != 0) return;
   const int lane = threadIdx.x;
@@ -1347,9 +1363,14 @@ __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, do
   const double rnk = __shfl_sync(0xffffffffu, rn2, k), snk = __shfl_sync(0xffffffffu, sn2, k);
   if (lane != 0) return;
   const bool conv = (convmask >> k) & 1u;
+  // the step counts towards the choice of k when its start was the one of
+  // the steady state: the full history (a start with fewer terms right
+  // after a restart is a transient), or any start without extrapolation
   if (first) {
+    st->full = !extrap || st->hist >= HIST_ORDER;
     st->iters = k;
-    st->hist = min(st->hist + 1, 2);  // this step's potential joins the history
+    st->hist = min(st->hist + 1, HIST_ORDER);  // this step's potential joins the history
+    st->ring = (st->ring + 1) % HIST_SLOTS;
   } else {
     st->iters += 1;
   }
@@ -1359,11 +1380,22 @@ __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, do
   // applications: it runs again after the loop when the loop runs
   if (first) cudaGraphSetConditional(redo, more ? 1u : 0u);
   st->rel = snk > 0.0 ? sqrt(rnk / snk) : 0.0;
-  if (first && convmask) st->need[min(max(1, __ffs(convmask) - 1), 4) - 1] += 1;
+  // applications this step needed, recorded once per step: at the first
+  // test when slot k converged (the earliest converged slot), else when the
+  // loop ends
+  int needed = 0;
+  if (first && conv)
+    needed = max(1, __ffs(convmask) - 1);
+  else if (!more)
+    needed = st->iters;
+  if (needed) {
+    const int j = min(needed, 4) - 1;
+    st->need[j] += 1;
+    if (st->full) st->needf[j] += 1;
+  }
   if (!more) {
     st->total += st->iters;
     if (!conv) st->fails += 1;
-    if (!(first && convmask)) st->need[min(st->iters, 4) - 1] += 1;
   }
 }
 
@@ -1399,6 +1431,7 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
   const double tol = h->cfg.poisson_tol;
   const double floor2 = RES_FLOOR_RMS * RES_FLOOR_RMS * (double)h->nfluid;
   const int maxit = h->cfg.poisson_maxit;
+  const int extrap = (h->cfg.flags & LBM_FLAG_NO_EXTRAPOLATION) ? 0 : 1;
   cudaGraph_t G = nullptr;
   LBM_CUDA_TRY(h, cudaGraphCreate(&G, 0));
   cudaGraphConditionalHandle cond, redo;
@@ -1420,7 +1453,7 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(main, G, nullptr, nullptr, 0, mode);
   if (e == cudaSuccess) {
     cudaError_t ec = cudaSuccess;
-    if (!(h->cfg.flags & LBM_FLAG_NO_EXTRAPOLATION)) ec = spec_extrapolate(h, &gs->hist);
+    if (extrap) ec = spec_extrapolate(h, &gs->hist, &gs->ring);
     h->charge_step = &gs->step;
     if (ec == cudaSuccess) ec = launch_charge(h);
     h->charge_step = nullptr;
@@ -1438,7 +1471,8 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
     if (ec == cudaSuccess) ec = cudaEventRecord(join, side);
     if (ec == cudaSuccess) ec = spec_residual(h, k, false);
     if (ec == cudaSuccess) {
-      k_graph_check<<<1, 32, 0, main>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 1, cond, redo);
+      k_graph_check<<<1, 32, 0, main>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 1, extrap, cond,
+                                        redo);
       ++h->launches;
       ec = cudaGetLastError();
     }
@@ -1473,8 +1507,8 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
         cudaError_t eb = spec_apply(h, 0);
         if (eb == cudaSuccess) eb = spec_residual(h, k, false);
         if (eb == cudaSuccess) {
-          k_graph_check<<<1, 32, 0, main>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 0, cond,
-                                            redo);
+          k_graph_check<<<1, 32, 0, main>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 0, extrap,
+                                            cond, redo);
           ++h->launches;
           eb = cudaGetLastError();
         }
@@ -1590,7 +1624,7 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
       }
     const int n = std::min(CHUNK, nsteps - done);
     const long long tot_before = hs->total;
-    LBM_CUDA_TRY(h, cudaMemsetAsync(ds->need, 0, 4 * sizeof(int), h->st));
+    LBM_CUDA_TRY(h, cudaMemsetAsync(ds->need, 0, 8 * sizeof(int), h->st));  // need, needf
     for (int k = 0; k < n; ++k) {
       LBM_CUDA_TRY(h, cudaGraphLaunch(h->step_graph[h->cur], h->st));
       h->cur ^= 1;
@@ -1606,9 +1640,10 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     h->launches += (int64_t)n * h->graph_kernels_fixed +
                    (hs->total - tot_before - (long long)n * sp->graph_k) * h->graph_kernels_iter +
                    (int64_t)redo_steps * h->graph_kernels_redo;
-    // decide from the steps since the last decision once there are at least
-    // CHUNK of them (across chunks and calls), or at the first chance
-    for (int j = 0; j < 4; ++j) sp->need_acc[j] += hs->need[j];
+    // decide from the steady-state steps (full history at their start)
+    // since the last decision once there are at least CHUNK of them (across
+    // chunks and calls), or at the first chance
+    for (int j = 0; j < 4; ++j) sp->need_acc[j] += hs->needf[j];
     const int tot = sp->need_acc[0] + sp->need_acc[1] + sp->need_acc[2] + sp->need_acc[3];
     if (tot >= CHUNK || (sp->graph_pred == 0 && tot > 0)) {
       int best = 1;
@@ -1626,6 +1661,20 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     }
     done += n;
     if (hs->fails != fails0) break;
+  }
+  // a new choice of k is built now, so that the next call starts replaying
+  // at once
+  if (sp->graph_pred > 0) {
+    const int want = std::max(1, std::min(std::min(sp->graph_pred, h->cfg.poisson_maxit),
+                                          Poisson::NSLOT - 1));
+    if (sp->graph_k != want) {
+      spectral_graph_free(h);
+      sp->graph_k = want;
+      for (int k = 0; k < 2; ++k) {
+        lbm_status s = build_step_graph(h, k);
+        if (s != LBM_OK) return s;
+      }
+    }
   }
   const long long iters = hs->total - total0;
   h->t_cnt[1] += iters;

@@ -33,6 +33,7 @@ EXPORTED = [
     "lbm_create_stack", "lbm_instance_z0", "lbm_set_plane_omega_drag", "lbm_autotune",
     "lbm_nn_init", "lbm_nn_collect", "lbm_nn_train", "lbm_nn_use", "lbm_nn_params",
     "lbm_nn_loss_grad", "lbm_nn_stats", "lbm_get_moments_noalloc", "lbm_state_len", "lbm_stream", "lbm_last_error",
+    "lbm_set_species_dev", "lbm_get_moments_dev", "lbm_plane_fluxes", "lbm_omega_drag_for_schmidt",
 ]
 
 
@@ -132,6 +133,14 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_stream.restype = P
     lib.lbm_last_error.argtypes = [P]
     lib.lbm_last_error.restype = ctypes.c_char_p
+    lib.lbm_set_species_dev.argtypes = [P, I, D, D, P, P, V]
+    lib.lbm_set_species_dev.restype = I
+    lib.lbm_get_moments_dev.argtypes = [P, I, P, P, V]
+    lib.lbm_get_moments_dev.restype = I
+    lib.lbm_plane_fluxes.argtypes = [P, P]
+    lib.lbm_plane_fluxes.restype = I
+    lib.lbm_omega_drag_for_schmidt.argtypes = [D, D]
+    lib.lbm_omega_drag_for_schmidt.restype = D
     _lib = lib
     return lib
 
@@ -159,10 +168,12 @@ def _ptr(a):
 
 
 def omega_drag_for_schmidt(omega_visc: float, schmidt: float) -> float:
-    """omega_drag with Sc = nu/D, nu = cs^2 (1/omega_visc - 1/2) and
-    D = cs^2 (1/omega_drag - 1/2) (Sec. 4 of the paper)."""
-    nu_over_cs2 = 1.0 / omega_visc - 0.5
-    return 1.0 / (0.5 + nu_over_cs2 / schmidt)
+    """lbm_omega_drag_for_schmidt: omega_drag with Sc = nu/D (Sec. 4 of the
+    paper); raises for omega_visc outside (0, 2) or Sc <= 0."""
+    od = float(load_library().lbm_omega_drag_for_schmidt(float(omega_visc), float(schmidt)))
+    if od == 0.0:
+        raise ValueError("omega_visc must lie in (0, 2) and the Schmidt number be positive")
+    return od
 
 
 class Lattice:
@@ -304,6 +315,29 @@ class Lattice:
         u = np.empty((3,) + self.shape)
         self._check(self._lib.lbm_get_moments(self.h, int(s), _ptr(n), _ptr(u)))
         return n, u
+
+    def set_species_dev(self, s, mass, valence, n0_ptr, u0_ptr=None, stream=None):
+        """lbm_set_species_dev: n0_ptr / u0_ptr are device addresses (for
+        example torch tensors' data_ptr()) of N and 3N doubles."""
+        self._check(self._lib.lbm_set_species_dev(
+            self.h, int(s), float(mass), float(valence), ctypes.c_void_p(int(n0_ptr)),
+            ctypes.c_void_p(int(u0_ptr)) if u0_ptr else None,
+            ctypes.c_void_p(int(stream)) if stream else None))
+
+    def get_moments_dev(self, s, n_ptr, u_ptr=None, stream=None):
+        """lbm_get_moments_dev: queues the moments of species s into device
+        memory at n_ptr (N doubles) and u_ptr (3N doubles) on `stream`."""
+        self._check(self._lib.lbm_get_moments_dev(
+            self.h, int(s), ctypes.c_void_p(int(n_ptr)) if n_ptr else None,
+            ctypes.c_void_p(int(u_ptr)) if u_ptr else None,
+            ctypes.c_void_p(int(stream)) if stream else None))
+
+    def plane_fluxes(self):
+        """lbm_plane_fluxes: array (nz, S, 4) of plane sums of n and of the
+        mid-step flux n (u + F/2) (x, y, z)."""
+        out = np.empty((self.shape[0], self.S, 4))
+        self._check(self._lib.lbm_plane_fluxes(self.h, _ptr(out)))
+        return out
 
     def get_moments_noalloc(self, s):
         """lbm_get_moments_noalloc: no device allocation (static staging)."""

