@@ -93,16 +93,16 @@ typedef struct {
 
 /* LBM_FLAG_NO_EXTRAPOLATION: each step's Poisson solve (every solver)
  * starts from the previous step's potential.  Without the flag it starts
- * from the extrapolation in time of the previous potentials,
- * 2 psi(t-1) - 2 psi(t-3) + psi(t-4), exact for potentials quadratic in
- * time and for a component that alternates sign every step (the ion flux
- * at high Schmidt number); the first steps after lbm_create,
- * lbm_set_species, lbm_set_state or lbm_solve_poisson (which restart the
- * history) use psi(t-1), the line 2 psi(t-1) - psi(t-2) and the parabola
- * 3 psi(t-1) - 3 psi(t-2) + psi(t-3) while the history fills.  The solve
- * still iterates to poisson_tol.  Not applied while the learned guess is
- * collecting or in use.  The paper has no counterpart: a property of this
- * library's solver.                                                       */
+ * from the previous potential advanced along the recent history of the
+ * solves: with the differences D_j = s(t-j) - s(t-j-1) of the last five
+ * Poisson sources and P_j of the potentials, the coefficients c that fit
+ * the new difference s(t) - s(t-1) best in least squares by sum c_j D_j
+ * give psi(t-1) + sum c_j P_j (the projection of the new right-hand side on
+ * the recent ones; fewer terms while the history fills after lbm_create,
+ * lbm_set_species, lbm_set_state or lbm_solve_poisson, which restart it).
+ * The solve still iterates to poisson_tol.  Not applied while the learned
+ * guess is collecting or in use.  The paper has no counterpart: a property
+ * of this library's solver.                                               */
 #define LBM_FLAG_NO_EXTRAPOLATION 2
 
 /* Fills *cfg with defaults: omega_visc = 1, omega_drag = 1, l_B = 0,
@@ -130,6 +130,21 @@ int lbm_instance_z0(const lbm_t* h, int i);
  * the config's omega_drag on every node of plane z; NULL restores the
  * config value.                                                           */
 lbm_status lbm_set_plane_omega_drag(lbm_t* h, const double* omega);
+
+/* Drag between every pair of species (Sec. 2: the drag coefficient
+ * gamma^{ab} of species of equal mass and diameters sigma_a, written as
+ * omega^{ab} n_b / n): F_drag^a = -sum_b omega^{ab} (n_b / n)(v_a - v_b),
+ * v the species velocities shifted by half the electric acceleration, as
+ * for the single omega_drag (which is the case of equal omega^{ab}).  omega:
+ * S*S doubles, row-major, symmetric (momentum is conserved), off-diagonal
+ * entries in (0, 2), the diagonal is not used; NULL restores the config's
+ * omega_drag.  For two species the drag depends on omega^{01} only, which
+ * replaces omega_drag.  The relaxation rates of the species velocities are
+ * then within (0, 2 max omega^{ab} (1 - x_a)) (Gershgorin), so entries below 1
+ * are stable at any composition.  LBM_EINVAL for an entry out of range, an
+ * asymmetric matrix, or per-plane drag frequencies (lbm_create_stack,
+ * lbm_set_plane_omega_drag) on the same lattice.                           */
+lbm_status lbm_set_drag_matrix(lbm_t* h, const double* omega);
 
 /* Autotuner: times the stream/collide and charge kernels of the current
  * state at several CTA sizes (64, 128, 256) and keeps the fastest; the state
@@ -192,10 +207,12 @@ lbm_status lbm_set_species(lbm_t* h, int s, double mass, double valence,
  * NULL) in device memory of the handle's device: caller-owned (for example
  * torch tensors' data pointers), read by work queued on `stream` (a
  * cudaStream_t, or NULL for the library's stream) during the call, never
- * retained or freed.  The checks of lbm_set_species (n0 finite and > 0,
- * u0 finite at every fluid node) run on the device; the call returns after
- * they were read back and the initialisation was queued.  LBM_EINVAL as
- * for lbm_set_species.                                                    */
+ * retained or freed.  Pass the stream on which the fields were written:
+ * the library's own stream is a non-blocking stream and does not wait for
+ * work on the legacy default stream.  The checks of lbm_set_species (n0
+ * finite and > 0, u0 finite at every fluid node) run on the device; the
+ * call returns after they were read back and the initialisation was
+ * queued.  LBM_EINVAL as for lbm_set_species.                             */
 lbm_status lbm_set_species_dev(lbm_t* h, int s, double mass, double valence,
                                const double* n0_dev, const double* u0_dev, void* stream);
 

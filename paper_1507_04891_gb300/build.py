@@ -18,7 +18,18 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
-SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_poisson.cu", "lbm_spectral.cu", "lbm_nn.cu", "lbm_noalloc.cu"]
+# (source, object name, extra nvcc flags): the stream/collide unit is compiled
+# once per population storage format (LBM_FP32 = 0, LBM_FP16_SHIFT = 1,
+# LBM_BF16_SHIFT = 2) so that its many kernel instances build in parallel
+UNITS = [("lbm_api.cu", "lbm_api", []), ("lbm_kernels.cu", "lbm_kernels", []),
+         ("lbm_collide.cu", "lbm_collide_fp32", ["-DLBM_COLLIDE_STORAGE=0"]),
+         ("lbm_collide.cu", "lbm_collide_fp16", ["-DLBM_COLLIDE_STORAGE=1"]),
+         ("lbm_collide.cu", "lbm_collide_bf16", ["-DLBM_COLLIDE_STORAGE=2"]),
+         ("lbm_poisson.cu", "lbm_poisson", []), ("lbm_spectral.cu", "lbm_spectral", []),
+         ("lbm_start.cu", "lbm_start", []), ("lbm_nn.cu", "lbm_nn", []),
+         ("lbm_noalloc.cu", "lbm_noalloc", [])]
+SOURCES = sorted({u[0] for u in UNITS})
+HEADERS = ["lbm_internal.cuh", "lbm_lattice.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]
@@ -35,9 +46,10 @@ def _nvcc():
     return exe
 
 
-def _compile(nvcc, src, verbose):
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+def _compile(nvcc, unit, verbose):
+    src, name, extra = unit
+    obj = os.path.join(BUILD, name + ".o")
+    cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -49,16 +61,16 @@ def _compile(nvcc, src, verbose):
 def build_library(verbose: bool = False, force: bool = False) -> str:
     """Compiles and links the library; returns its path."""
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "lbm_internal.cuh"), os.path.join(ROOT, "include", "lbm.h"),
-                   os.path.abspath(__file__)]
+    deps = srcs + [os.path.join(CSRC, h) for h in HEADERS] + \
+        [os.path.join(ROOT, "include", "lbm.h"), os.path.abspath(__file__)]
     if not force and os.path.exists(LIB):
         lib_t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= lib_t for d in deps):
             return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(lambda s: _compile(nvcc, s, verbose), SOURCES))
+    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+        results = list(ex.map(lambda u: _compile(nvcc, u, verbose), UNITS))
     if verbose:
         for _, log in results:
             sys.stderr.write(log)

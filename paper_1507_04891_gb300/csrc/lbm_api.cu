@@ -223,14 +223,19 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
   lbm_t* h = new (std::nothrow) lbm_t();
   if (!h) return LBM_ENOMEM;
   h->cfg = c;
+  h->omega_drag_cfg = c.omega_drag;
   h->S = c.nspecies;
   h->N = N;
   h->dev = c.device;
   h->nfluid = N;
   h->esize = (c.storage == LBM_FP32) ? 4 : 2;
   lbm_status s = LBM_OK;
+  // the library's stream at the greatest priority: kernels of lower-priority
+  // side work (the fit of the Poisson start) yield SMs to it
+  int prio_lo = 0, prio_hi = 0;
   if (cudaSetDevice(h->dev) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&h->own, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming) != cudaSuccess) {
     g_create_error = "CUDA context or stream creation failed";
     lbm_destroy(h);
@@ -261,7 +266,6 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     s = dev_alloc(h, &h->ps.psi[0], N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.psi[1], N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.src, N);
-    if (s == LBM_OK && c.poisson != LBM_POISSON_FFT) s = dev_alloc(h, &h->ps.hist, HIST_SLOTS * (size_t)N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.dsum, 1 + 2 * Poisson::NSLOT);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.part, (size_t)((N + 63) / 64));
     if (s == LBM_OK && cudaMallocHost(&h->ps.hsum, (1 + 2 * Poisson::NSLOT) * sizeof(double)) != cudaSuccess)
@@ -269,9 +273,9 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     if (s == LBM_OK) {
       cudaMemset(h->ps.psi[0], 0, N * sizeof(int64_t));
       cudaMemset(h->ps.psi[1], 0, N * sizeof(int64_t));
-      if (h->ps.hist) cudaMemset(h->ps.hist, 0, HIST_SLOTS * N * sizeof(int64_t));
       cudaMemset(h->ps.dsum, 0, (1 + 2 * Poisson::NSLOT) * sizeof(double));
       s = poisson_setup(h, nullptr);
+      if (s == LBM_OK) s = start_setup(h);
       if (s == LBM_OK && c.poisson == LBM_POISSON_FFT) s = spectral_setup(h, nullptr);
     }
   }
@@ -301,6 +305,7 @@ void lbm_destroy(lbm_t* h) {
   spectral_graph_free(h);
   poisson_free(h);
   spectral_free(h);
+  start_free(h);
   nn_free(h);
   cudaFree(h->omega_drag_z);
   cudaFree(h->gstatus);
@@ -566,8 +571,10 @@ lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
       int it = 0;
       double rel = 0.0;
       Phase pp(h, 1);
-      lbm_status se = h->spec ? spectral_step_start(h) : poisson_step_start(h);
-      if (se != LBM_OK) return se;
+      // spectral: the start from the previous fit, this step's fit beside
+      // the solve (joined before the next step); multigrid / SOR: the fit
+      // first
+      LBM_CUDA_TRY(h, start_step(h, h->spec != nullptr));
       s = poisson_solve(h, h->cfg.poisson_tol, h->cfg.poisson_maxit, &it, &rel);
       LBM_CUDA_TRY(h, pp.stop());
       h->t_cnt[1] += it;
@@ -577,8 +584,10 @@ lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
       h->psi_valid = true;
     }
     Phase ps(h, 2);
-    LBM_CUDA_TRY(h, launch_stream_collide(h));
+    // the last step of the call also sums the state it stores (diagnostics)
+    LBM_CUDA_TRY(h, launch_stream_collide(h, k == nsteps - 1));
     LBM_CUDA_TRY(h, ps.stop());
+    LBM_CUDA_TRY(h, start_join(h));
     h->t_cnt[2] += 1;
     ++h->tstep;
     if (s == LBM_ENOCONV) return s;
@@ -846,6 +855,8 @@ lbm_status lbm_set_plane_omega_drag(lbm_t* h, const double* omega) {
     spectral_graph_free(h);
     return LBM_OK;
   }
+  if (h->pair_on)
+    return fail(h, LBM_EINVAL, "a drag matrix and per-plane drag frequencies exclude each other");
   const int nz = h->cfg.nz;
   std::vector<float> w(nz);
   for (int z = 0; z < nz; ++z) {
@@ -858,6 +869,39 @@ lbm_status lbm_set_plane_omega_drag(lbm_t* h, const double* omega) {
   }
   LBM_CUDA_TRY(h, cudaMemcpy(h->omega_drag_z, w.data(), nz * sizeof(float), cudaMemcpyHostToDevice));
   spectral_graph_free(h);
+  return LBM_OK;
+}
+
+lbm_status lbm_set_drag_matrix(lbm_t* h, const double* omega) {
+  if (!h) return LBM_EINVAL;
+  const int S = h->S;
+  if (!omega) {
+    if (h->pair_on || h->cfg.omega_drag != h->omega_drag_cfg) spectral_graph_free(h);
+    h->pair_on = false;
+    h->cfg.omega_drag = h->omega_drag_cfg;
+    return LBM_OK;
+  }
+  if (h->omega_drag_z)
+    return fail(h, LBM_EINVAL, "a drag matrix and per-plane drag frequencies exclude each other");
+  for (int i = 0; i < S; ++i)
+    for (int j = 0; j < S; ++j) {
+      if (i == j) continue;
+      const double w = omega[i * S + j];
+      if (!(w > 0.0 && w < 2.0)) return fail(h, LBM_EINVAL, "pair drag frequencies must lie in (0, 2)");
+      if (fabs(w - omega[j * S + i]) > 1e-12 * w)
+        return fail(h, LBM_EINVAL, "the drag matrix must be symmetric");
+    }
+  spectral_graph_free(h);
+  if (S == 2) {
+    // a binary depends on its cross frequency only: the scalar form
+    h->pair_on = false;
+    h->cfg.omega_drag = omega[1];
+  } else if (S >= 3) {
+    h->pair_on = true;
+    for (int i = 0; i < MAX_SPECIES; ++i)
+      for (int j = 0; j < MAX_SPECIES; ++j)
+        h->pair[i][j] = (i < S && j < S && i != j) ? (float)omega[i * S + j] : 0.0f;
+  }
   return LBM_OK;
 }
 

@@ -40,32 +40,12 @@ constexpr double PSI_MAX = 2048.0;                      // 2^11
 // source of vanishing norm is solved once the residual is within twice that.
 constexpr double RES_FLOOR_RMS = 4.0;
 
-// Extrapolation in time of a fixed-point potential from its last values
-// a = psi(t-1), b = psi(t-2), c = psi(t-3), d = psi(t-4), `order` of the
-// older ones being valid:
-//   order 0   a
-//   order 1   2a - b             (line)
-//   order 2   3a - 3b + c        (parabola)
-//   order 3   2a - 2c + d        (exact for quadratics and for the
-//                                 alternation (-1)^t, which the parabola
-//                                 amplifies sevenfold; it needs no b)
-// Exact in 128-bit integers; a value outside 2^61 units keeps a.
-__device__ __forceinline__ int64_t extrapolate1(int64_t a, int64_t b, int64_t c, int64_t d,
-                                                int order) {
-  if (order <= 0) return a;
-  const __int128 A = a;
-  const __int128 g = order == 1   ? 2 * A - b
-                     : order == 2 ? 3 * (A - b) + c
-                                  : 2 * (A - c) + d;
-  const __int128 lim = (__int128)1 << 61;
-  return (g > lim || g < -lim) ? a : (int64_t)g;
-}
-// The history of the extrapolation: HIST_SLOTS lattice-sized buffers used as
-// a ring.  With ring position r, psi(t-2) is in slot (r + 2) % 3, psi(t-3)
-// in (r + 1) % 3 and psi(t-4) in r % 3; the start of a solve overwrites
-// slot r % 3 with psi(t-1), and r advances by one.
-constexpr int HIST_SLOTS = 3;
-constexpr int HIST_ORDER = 3;  // valid entries of a full history
+// Differences of the source and potential history kept for the start of
+// each step's Poisson solve (lbm_start.cu).
+constexpr int START_K = 5;
+// starts fitted on at least this many differences count as steady-state
+// steps for the graph steps' choice of the number of applications
+constexpr int START_FULL_TERMS = START_K;
 
 #ifdef __CUDACC__
 // Conversions between 64-bit integers and FP32 on the 32-bit integer and FP32
@@ -126,6 +106,10 @@ struct StepArgs {
   uint32_t step;            // time step (seeds the stochastic rounding)
   const uint32_t* step_dev; // device copy of the step (graph replays) or NULL
   double* diag;             // per-CTA diagnostics partials (DIAG_NQ per CTA) or NULL
+  // matrix of pair drag frequencies omega^{ab} (Sec. 2, general gamma^{ab}
+  // for equal masses; zero diagonal), used instead of omega_drag when pair_on
+  int pair_on;
+  float pair[MAX_SPECIES][MAX_SPECIES];
 };
 
 struct PoissonLevel {
@@ -145,9 +129,6 @@ struct Poisson {
   int zlo = 0, nzb = 0, perz = 1;
   std::vector<PoissonLevel> lev;
   int64_t* psi[2] = {nullptr, nullptr};  // lattice-sized fixed-point buffers
-  int64_t* hist = nullptr;  // multigrid / SOR: HIST_SLOTS x N, the ring of older potentials
-  int hist_n = 0;           // valid entries of hist (0..HIST_ORDER)
-  int hist_ring = 0;        // ring position
   int cur = 0;
   int64_t* src = nullptr; // 4 pi l_B (rho_e + w) per lattice node (fixed point), no mean removed
   double* dsum = nullptr; // [0] sum of src over fluid, [1 + 2k] sum r^2, [2 + 2k] sum s^2 (fixed-point units), k < NSLOT
@@ -169,6 +150,22 @@ struct Poisson {
   int cyc_kernels = 0;
   bool cyc_failed = false;
   int nu1 = 2, nu2 = 2;
+};
+
+// History of the start of the Poisson solves (lbm_start.cu), device memory.
+struct StartHistory {
+  int64_t* s_prev = nullptr;    // source of the previous step (fixed point)
+  int64_t* psi_prev = nullptr;  // potential of the step before the previous one
+  float* ring_d = nullptr;      // START_K x N: differences of consecutive sources
+  float* ring_p = nullptr;      // START_K x N: differences of consecutive potentials
+  float* part = nullptr;        // per-CTA inner products, START_K + 1 per CTA
+  double* gram = nullptr;       // START_K x START_K Gram matrix of the stored differences
+  float* coef = nullptr;        // START_K coefficients of the current step
+  int* state = nullptr;         // valid steps, ring position, terms of coef, terms used
+  int ctas = 0;
+  cudaStream_t side = nullptr;  // the fit runs here, beside the solve (lowest priority)
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool pending = false;         // a fit was queued on side and not yet joined
 };
 
 }  // namespace lbm_gb300
@@ -204,6 +201,7 @@ struct lbm {
   int64_t* wsrc = nullptr;  // 4 pi l_B w_i in fixed point (wall charge of each fluid cell)
   int64_t nfluid = 0;
   lbm_gb300::Poisson ps;
+  lbm_gb300::StartHistory start;  // start of each step's Poisson solve
   lbm_gb300::SpectralPlan* spec = nullptr;  // spectral Poisson plan (LBM_POISSON_FFT)
   lbm_gb300::NNet* nn = nullptr;            // learned Poisson initial guess
   bool psi_valid = false;
@@ -235,9 +233,15 @@ struct lbm {
   int64_t launches = 0;
   int grid_cap = 1216;   // CTAs of the grid-stride reduction kernels (8 per SM)
   float* omega_drag_z = nullptr;  // per-plane drag frequency (lbm_set_plane_omega_drag)
+  // matrix of pair drag frequencies (lbm_set_drag_matrix; three or more
+  // species), and the config's omega_drag before a binary matrix replaced it
+  bool pair_on = false;
+  float pair[lbm_gb300::MAX_SPECIES][lbm_gb300::MAX_SPECIES] = {};
+  double omega_drag_cfg = 0.0;
   int collide_threads = 128;      // CTA size of the stream-collide kernel (autotuned)
   // whole-step CUDA graphs (LBM_FLAG_STEP_GRAPH), one per population parity
-  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+  // [parity] and stream/collide variant [diag]
+  cudaGraphExec_t step_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   void* gstatus = nullptr;        // device status of graph steps
   void* hstatus = nullptr;        // pinned mirror
   int graph_kernels_fixed = 0;    // kernels per step outside the Poisson loop
@@ -255,10 +259,28 @@ namespace lbm_gb300 {
 // the work that the last lbm_step queued on a caller's stream.
 cudaError_t own_stream(lbm_t* h);
 
+// ---- lbm_collide.cu (one object per storage format) ----
+// Launches the fused stream/collide of storage format ST from a to a.fout:
+// S species, walls w, charged c, `threads` per CTA, diagnostics variant d.
+// (a.pair_on selects the pair-frequency drag; three or more species).
+template <int ST>
+cudaError_t collide_dispatch(const StepArgs& a, int S, bool w, bool c, cudaStream_t st,
+                             int threads, bool d);
+template <>
+cudaError_t collide_dispatch<LBM_FP32>(const StepArgs&, int, bool, bool, cudaStream_t, int, bool);
+template <>
+cudaError_t collide_dispatch<LBM_FP16_SHIFT>(const StepArgs&, int, bool, bool, cudaStream_t, int,
+                                             bool);
+template <>
+cudaError_t collide_dispatch<LBM_BF16_SHIFT>(const StepArgs&, int, bool, bool, cudaStream_t, int,
+                                             bool);
+
 // ---- lbm_kernels.cu ----
 cudaError_t launch_init_species(lbm_t* h, int s, const double* n0_dev,
                                 const double* u0_dev);
-cudaError_t launch_stream_collide(lbm_t* h);
+// diag: the variant that also writes the FP64 diagnostics partials of the
+// state it stores (the last step of an lbm_step call)
+cudaError_t launch_stream_collide(lbm_t* h, bool diag);
 // Stream-collide into the spare lattice with a given CTA size, without
 // advancing the state (autotuning).
 cudaError_t launch_stream_collide_probe(lbm_t* h, int threads);
@@ -288,9 +310,6 @@ void poisson_free(lbm_t* h);
 // Solves A psi = src - mean starting from the current psi buffer.
 lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
                          double* rel_res);
-// Multigrid / SOR host-driven steps: psi <- its extrapolation from the
-// previous steps before the step's solve (as spectral_step_start).
-lbm_status poisson_step_start(lbm_t* h);
 
 // ---- lbm_spectral.cu ----
 lbm_status spectral_setup(lbm_t* h, const uint8_t* solid_host);
@@ -301,12 +320,31 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters,
 // device status once at the end.
 lbm_status spectral_graph_steps(lbm_t* h, int nsteps);
 void spectral_graph_free(lbm_t* h);
-// Host-driven steps: psi <- its extrapolation from the previous steps
-// before the step's solve (LBM_FLAG_NO_EXTRAPOLATION off, no learned guess).
-lbm_status spectral_step_start(lbm_t* h);
 // Restarts the potential history of every solver (psi was set from outside
 // the steps).
 lbm_status potential_history_reset(lbm_t* h);
+
+// ---- lbm_start.cu ----
+lbm_status start_setup(lbm_t* h);
+void start_free(lbm_t* h);
+// The start is used (LBM_FLAG_NO_EXTRAPOLATION off, no learned guess).
+bool start_enabled(const lbm_t* h);
+// After the step's charge density: psi <- the start from the history.
+// lagged: with the coefficients of the previous step's fit, this step's
+// fit then queued on the side stream (start_join orders h->st after it);
+// otherwise this step's fit first, on h->st.  The history restarts when
+// the start is disabled.
+cudaError_t start_step(lbm_t* h, bool lagged);
+cudaError_t start_join(lbm_t* h);
+// The two halves for graph capture: the start on h->st, the fit on st;
+// `last` marks the step's last pass (it advances the history ring).
+cudaError_t start_apply(lbm_t* h, bool last);
+cudaError_t start_fit(lbm_t* h, cudaStream_t st, bool last);
+// The history restarts (psi or the state was set from outside the steps).
+cudaError_t start_reset(lbm_t* h);
+// Device address of the number of terms the current step's start used
+// (START_K: the full history).
+const int* start_terms_dev(const lbm_t* h);
 
 // ---- lbm_nn.cu ----
 lbm_status nn_init(lbm_t* h, int hidden, uint64_t seed);

@@ -622,25 +622,6 @@ CL make_cl(const PoissonLevel& l) {
 }  // namespace
 
 namespace {
-// psi <- extrapolate1 of psi(t-1) and the older potentials of the history
-// ring (only those the order uses are read), psi(t-1) into the ring's
-// oldest slot; one node per thread (any N).
-__global__ void __launch_bounds__(256) k_extrapolate_nodes(int64_t* __restrict__ psi,
-                                                           int64_t* __restrict__ hist, int64_t n,
-                                                           int ring, int order) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int64_t* s2 = hist + (int64_t)((ring + 2) % HIST_SLOTS) * n;  // psi(t-2)
-  int64_t* s3 = hist + (int64_t)((ring + 1) % HIST_SLOTS) * n;  // psi(t-3)
-  int64_t* s4 = hist + (int64_t)(ring % HIST_SLOTS) * n;        // psi(t-4)
-  const int64_t a = psi[i];
-  const int64_t b = (order == 1 || order == 2) ? s2[i] : 0;
-  const int64_t c = order >= 2 ? s3[i] : 0;
-  const int64_t d = order >= 3 ? s4[i] : 0;
-  psi[i] = extrapolate1(a, b, c, d, order);
-  s4[i] = a;
-}
-
 void drop_graphs(Poisson& P) {
   for (int k = 0; k < 2; ++k) {
     if (P.cyc[k]) cudaGraphExecDestroy(P.cyc[k]);
@@ -649,21 +630,6 @@ void drop_graphs(Poisson& P) {
   P.cyc_failed = false;
 }
 }  // namespace
-
-lbm_status poisson_step_start(lbm_t* h) {
-  Poisson& P = h->ps;
-  if (!P.hist || (h->cfg.flags & LBM_FLAG_NO_EXTRAPOLATION) || nn_active(h)) {
-    P.hist_n = 0;
-    return LBM_OK;
-  }
-  k_extrapolate_nodes<<<nblocks(h->N, 256), 256, 0, h->st>>>(P.psi[P.cur], P.hist, h->N,
-                                                            P.hist_ring, P.hist_n);
-  ++h->launches;
-  LBM_CUDA_TRY(h, cudaGetLastError());
-  P.hist_n = std::min(P.hist_n + 1, HIST_ORDER);
-  P.hist_ring = (P.hist_ring + 1) % HIST_SLOTS;
-  return LBM_OK;
-}
 
 void poisson_free(lbm_t* h) {
   Poisson& P = h->ps;
@@ -677,9 +643,6 @@ void poisson_free(lbm_t* h) {
   P.lev.clear();
   cudaFree(P.psi[0]);
   cudaFree(P.psi[1]);
-  cudaFree(P.hist);
-  P.hist = nullptr;
-  P.hist_n = 0;
   cudaFree(P.src);
   cudaFree(P.dsum);
   cudaFree(P.part);

@@ -801,35 +801,6 @@ __global__ void __launch_bounds__(256, 4) k_res_planes(
   add_norms(acc, rr, ss, red_r, red_s);
 }
 
-// Start of a step's solve: psi(t-1) is replaced by its extrapolation in
-// time (extrapolate1 over the history ring; `order` valid entries and the
-// ring position read from the graph status when given); psi(t-1) joins the
-// ring in its oldest slot.  Only the history entries the order uses are
-// read: with a full history, psi, psi(t-3) and psi(t-4) in, psi and the
-// ring slot out.  Any start is valid: the solve iterates to the same
-// tolerance from it.  Two nodes per thread (N is even: nx >= 8).
-__global__ void __launch_bounds__(256) k_extrapolate(int64_t* __restrict__ psi, int64_t* __restrict__ hist,
-                                                     int64_t N, int64_t npairs,
-                                                     const int* __restrict__ order_dev,
-                                                     const int* __restrict__ ring_dev, int order,
-                                                     int ring) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= npairs) return;
-  const int ord = order_dev ? min(*order_dev, HIST_ORDER) : order;
-  const int rg = ring_dev ? *ring_dev : ring;
-  longlong2* P = reinterpret_cast<longlong2*>(psi);
-  const longlong2* S2 = reinterpret_cast<const longlong2*>(hist + (int64_t)((rg + 2) % HIST_SLOTS) * N);
-  const longlong2* S3 = reinterpret_cast<const longlong2*>(hist + (int64_t)((rg + 1) % HIST_SLOTS) * N);
-  longlong2* S4 = reinterpret_cast<longlong2*>(hist + (int64_t)(rg % HIST_SLOTS) * N);
-  const longlong2 z = make_longlong2(0, 0);
-  const longlong2 a = P[i];
-  const longlong2 b = (ord == 1 || ord == 2) ? S2[i] : z;
-  const longlong2 c = ord >= 2 ? S3[i] : z;
-  const longlong2 d = ord >= 3 ? S4[i] : z;
-  P[i] = make_longlong2(extrapolate1(a.x, b.x, c.x, d.x, ord), extrapolate1(a.y, b.y, c.y, d.y, ord));
-  S4[i] = a;
-}
-
 int ilog2(int n) {
   int l = 0;
   while ((1 << l) < n) ++l;
@@ -860,9 +831,6 @@ struct SpectralPlan {
   bool status_read = false;        // the host copy of the graph status is current
   bool runs_fit = true;            // z solve fits in shared memory
   float* r = nullptr;              // N (residual for the learned guess)
-  int64_t* hist = nullptr;         // HIST_SLOTS x N: the ring of older potentials
-  int hist_n = 0;                  // valid entries of hist (host-driven steps)
-  int hist_ring = 0;               // ring position (host-driven steps)
   long long* psum = nullptr;       // nz
   long long* mean_z = nullptr;     // nz
   float* nacc = nullptr;           // norm slots, Poisson::NSLOT x 2 NACC
@@ -879,7 +847,6 @@ void spectral_free(lbm_t* h) {
   cudaFree(s->lam);
   cudaFree(s->spec);
   cudaFree(s->r);
-  cudaFree(s->hist);
   cudaFree(s->psum);
   cudaFree(s->mean_z);
   h->charge_mean_z = nullptr;
@@ -969,7 +936,6 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
             al((void**)&s->tw, ntw * sizeof(float2)) && al((void**)&s->lam, nlam * sizeof(float)) &&
             al((void**)&s->spec, (size_t)nz * s->mxy * sizeof(float2)) &&
             al((void**)&s->r, N * sizeof(float)) && al((void**)&s->psum, nz * sizeof(long long)) &&
-            al((void**)&s->hist, HIST_SLOTS * N * sizeof(int64_t)) &&
             al((void**)&s->mean_z, nz * sizeof(long long)) &&
             al((void**)&s->nacc, (size_t)Poisson::NSLOT * 2 * NACC * sizeof(float));
   if (ok && cudaMallocHost((void**)&s->hacc, (size_t)Poisson::NSLOT * 2 * NACC * sizeof(float)) != cudaSuccess) {
@@ -998,7 +964,6 @@ lbm_status spectral_setup(lbm_t* h, const uint8_t* solid) {
   for (int k = 0; k <= nx / 2; ++k) lam.push_back(eig(k, nx));
   for (int k = 0; k < ny; ++k) lam.push_back(eig(k, ny));
   for (int k = 0; k < nz; ++k) lam.push_back(eig(k, nz));
-  LBM_CUDA_TRY(h, cudaMemset(s->hist, 0, HIST_SLOTS * N * sizeof(int64_t)));
   LBM_CUDA_TRY(h, cudaMemcpy(s->planes, planes.data(), planes.size() * sizeof(int), cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->runs, runs.data(), runs.size() * sizeof(Run), cudaMemcpyHostToDevice));
   LBM_CUDA_TRY(h, cudaMemcpy(s->plane_fluid, pf.data(), nz, cudaMemcpyHostToDevice));
@@ -1182,38 +1147,7 @@ cudaError_t spec_apply(lbm_t* h, int slot) {
   return e == cudaSuccess ? spec_zinv(h) : e;
 }
 
-// psi <- its extrapolation from the previous steps (k_extrapolate); the
-// number of valid history entries and the ring position come from the
-// graph status (graph steps: the test kernel advances them) or from the
-// host counts, which advance here.
-cudaError_t spec_extrapolate(lbm_t* h, const int* order_dev, const int* ring_dev) {
-  SpectralPlan* s = h->spec;
-  Poisson& P = h->ps;
-  const int64_t np = h->N / 2;
-  k_extrapolate<<<nblk(np, 256), 256, 0, h->st>>>(P.psi[P.cur], s->hist, h->N, np, order_dev, ring_dev,
-                                                  s->hist_n, s->hist_ring);
-  ++h->launches;
-  if (!order_dev) {
-    s->hist_n = std::min(s->hist_n + 1, HIST_ORDER);
-    s->hist_ring = (s->hist_ring + 1) % HIST_SLOTS;
-  }
-  return cudaGetLastError();
-}
-
-bool extrapolation_on(const lbm_t* h) {
-  return !(h->cfg.flags & LBM_FLAG_NO_EXTRAPOLATION) && !nn_active(h);
-}
-
 }  // namespace
-
-lbm_status spectral_step_start(lbm_t* h) {
-  if (!extrapolation_on(h)) {
-    h->spec->hist_n = 0;
-    return LBM_OK;
-  }
-  LBM_CUDA_TRY(h, spec_extrapolate(h, nullptr, nullptr));
-  return LBM_OK;
-}
 
 lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* rel_res) {
   SpectralPlan* s = h->spec;
@@ -1328,8 +1262,6 @@ struct GraphStatus {
   int iters;           // Poisson applications of the current step
   long long total;     // applications summed over replayed steps
   int fails;           // steps whose solve stopped at the iteration cap
-  int hist;            // valid entries of the potential history (0..HIST_ORDER)
-  int ring;            // position of the history ring
   double rel;          // final relative residual of the last step
   int need[4];         // steps that needed 1, 2, 3, >= 4 applications since the host reset it
   int needf[4];        // the same, counting only steps whose start had the full history
@@ -1342,7 +1274,8 @@ struct GraphStatus {
 // will run.  Otherwise after one more application (slot k).  Sets the
 // condition of the while node.
 __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, double tol,
-                              double floor2, int maxit, int k, int first, int extrap,
+                              double floor2, int maxit, int k, int first,
+                              const int* __restrict__ start_terms,
                               cudaGraphConditionalHandle cond, cudaGraphConditionalHandle redo) {
   if (blockIdx.x != 0) return;
   const int lane = threadIdx.x;
@@ -1363,14 +1296,13 @@ __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, do
   const double rnk = __shfl_sync(0xffffffffu, rn2, k), snk = __shfl_sync(0xffffffffu, sn2, k);
   if (lane != 0) return;
   const bool conv = (convmask >> k) & 1u;
-  // the step counts towards the choice of k when its start was the one of
-  // the steady state: the full history (a start with fewer terms right
-  // after a restart is a transient), or any start without extrapolation
+  // the step counts towards the choice of k when its start was near the
+  // one of the steady state: fitted on at least START_FULL_TERMS stored
+  // differences (the first starts after a restart have fewer), or any step
+  // when the history start is off
   if (first) {
-    st->full = !extrap || st->hist >= HIST_ORDER;
+    st->full = !start_terms || *start_terms >= START_FULL_TERMS;
     st->iters = k;
-    st->hist = min(st->hist + 1, HIST_ORDER);  // this step's potential joins the history
-    st->ring = (st->ring + 1) % HIST_SLOTS;
   } else {
     st->iters += 1;
   }
@@ -1402,61 +1334,75 @@ __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, do
 }  // namespace
 
 void spectral_graph_free(lbm_t* h) {
-  for (int k = 0; k < 2; ++k) {
-    if (h->step_graph[k]) cudaGraphExecDestroy(h->step_graph[k]);
-    h->step_graph[k] = nullptr;
-  }
+  for (int k = 0; k < 2; ++k)
+    for (int d = 0; d < 2; ++d) {
+      if (h->step_graph[k][d]) cudaGraphExecDestroy(h->step_graph[k][d]);
+      h->step_graph[k][d] = nullptr;
+    }
 }
 
 lbm_status potential_history_reset(lbm_t* h) {
-  h->ps.hist_n = 0;
-  if (!h->spec) return LBM_OK;
-  h->spec->hist_n = 0;
-  if (h->gstatus) {
-    // no graph step is in flight: every lbm_step call with graph steps ends
-    // with a synchronisation
-    const int zero = 0;
-    LBM_CUDA_TRY(h, cudaMemcpy(&reinterpret_cast<GraphStatus*>(h->gstatus)->hist, &zero, sizeof zero,
-                               cudaMemcpyHostToDevice));
-  }
+  LBM_CUDA_TRY(h, start_join(h));  // a fit still queued writes the history
+  LBM_CUDA_TRY(h, start_reset(h));
   return LBM_OK;
 }
 
 namespace {
 
-lbm_status build_step_graph(lbm_t* h, int parity) {
+lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
   const int saved_cur = h->cur;
+  const bool saved_diag = h->diag_valid;  // capture runs nothing
   h->cur = parity;
   GraphStatus* gs = reinterpret_cast<GraphStatus*>(h->gstatus);
   const double tol = h->cfg.poisson_tol;
   const double floor2 = RES_FLOOR_RMS * RES_FLOOR_RMS * (double)h->nfluid;
   const int maxit = h->cfg.poisson_maxit;
-  const int extrap = (h->cfg.flags & LBM_FLAG_NO_EXTRAPOLATION) ? 0 : 1;
+  // steps count towards the choice of k once their start used the full
+  // history (any step when the start is off)
+  const int* terms = start_enabled(h) ? start_terms_dev(h) : nullptr;
   cudaGraph_t G = nullptr;
   LBM_CUDA_TRY(h, cudaGraphCreate(&G, 0));
   cudaGraphConditionalHandle cond, redo;
   LBM_CUDA_TRY(h, cudaGraphConditionalHandleCreate(&cond, G, 0, cudaGraphCondAssignDefault));
   LBM_CUDA_TRY(h, cudaGraphConditionalHandleCreate(&redo, G, 0, cudaGraphCondAssignDefault));
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
-  cudaStream_t main = h->st, side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t main = h->st, side = nullptr, side2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, join2 = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+  // the fit of the Poisson start for the next step runs at the lowest
+  // priority, beside the latency-bound transforms (node priorities are
+  // kept at instantiation)
+  if (e == cudaSuccess) {
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side2, cudaStreamNonBlocking, lo);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork2, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join2, cudaEventDisableTiming);
   const int64_t l0 = h->launches;
   int64_t lc = 0;  // launches of the stream/collide
-  // part A: the extrapolated starting potential, source (advancing the
-  // step counter), means, the predicted number k of applications (each records the norms of the residual it
+  // part A: the source (advancing the step counter), the start of the
+  // solve from the history (lbm_start.cu), the means, the predicted number
+  // k of applications (each records the norms of the residual it
   // transforms); then, side by side, the stream/collide on that potential
   // and the final residual with the test
   const int k = h->spec->graph_k;
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(main, G, nullptr, nullptr, 0, mode);
   if (e == cudaSuccess) {
     cudaError_t ec = cudaSuccess;
-    if (extrap) ec = spec_extrapolate(h, &gs->hist, &gs->ring);
     h->charge_step = &gs->step;
-    if (ec == cudaSuccess) ec = launch_charge(h);
+    ec = launch_charge(h);
     h->charge_step = nullptr;
+    // the start from the history, then the fit for the next step on the
+    // second side stream, beside the applications
+    if (ec == cudaSuccess) ec = start_apply(h, false);
+    const bool fit = start_enabled(h);
+    if (ec == cudaSuccess && fit) ec = cudaEventRecord(fork2, main);
+    if (ec == cudaSuccess && fit) ec = cudaStreamWaitEvent(side2, fork2, 0);
+    if (ec == cudaSuccess && fit) ec = start_fit(h, side2, true);
+    if (ec == cudaSuccess && fit) ec = cudaEventRecord(join2, side2);
     if (ec == cudaSuccess) ec = spec_means(h);
     for (int i = 0; i < k && ec == cudaSuccess; ++i) ec = spec_apply(h, i);
     if (ec == cudaSuccess) ec = cudaEventRecord(fork, main);
@@ -1464,19 +1410,20 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
     if (ec == cudaSuccess) {
       const int64_t a = h->launches;
       h->st = side;
-      ec = launch_stream_collide(h);
+      ec = launch_stream_collide(h, diag);
       h->st = main;
       lc = h->launches - a;
     }
     if (ec == cudaSuccess) ec = cudaEventRecord(join, side);
     if (ec == cudaSuccess) ec = spec_residual(h, k, false);
     if (ec == cudaSuccess) {
-      k_graph_check<<<1, 32, 0, main>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 1, extrap, cond,
+      k_graph_check<<<1, 32, 0, main>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 1, terms, cond,
                                         redo);
       ++h->launches;
       ec = cudaGetLastError();
     }
     if (ec == cudaSuccess) ec = cudaStreamWaitEvent(main, join, 0);
+    if (ec == cudaSuccess && fit) ec = cudaStreamWaitEvent(main, join2, 0);
     std::vector<cudaGraphNode_t> deps;
     if (ec == cudaSuccess) {
       cudaStreamCaptureStatus cs;
@@ -1507,7 +1454,7 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
         cudaError_t eb = spec_apply(h, 0);
         if (eb == cudaSuccess) eb = spec_residual(h, k, false);
         if (eb == cudaSuccess) {
-          k_graph_check<<<1, 32, 0, main>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 0, extrap,
+          k_graph_check<<<1, 32, 0, main>>>(norm_slot(h, 0), gs, tol, floor2, maxit, k, 0, terms,
                                             cond, redo);
           ++h->launches;
           eb = cudaGetLastError();
@@ -1534,7 +1481,7 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
     if (e == cudaSuccess) {
       e = cudaStreamBeginCaptureToGraph(main, ibody, nullptr, nullptr, 0, mode);
       if (e == cudaSuccess) {
-        cudaError_t eb = launch_stream_collide(h);
+        cudaError_t eb = launch_stream_collide(h, diag);
         cudaGraph_t gg = nullptr;
         e = cudaStreamEndCapture(main, &gg);
         if (e == cudaSuccess) e = eb;
@@ -1546,19 +1493,35 @@ lbm_status build_step_graph(lbm_t* h, int parity) {
   }
   h->launches = l0;
   h->cur = saved_cur;
+  h->diag_valid = saved_diag;
   h->st = main;
   cudaGraphExec_t ex = nullptr;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, G, 0);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, G, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(G);
   if (fork) cudaEventDestroy(fork);
   if (join) cudaEventDestroy(join);
+  if (fork2) cudaEventDestroy(fork2);
+  if (join2) cudaEventDestroy(join2);
   if (side) cudaStreamDestroy(side);
+  if (side2) cudaStreamDestroy(side2);
   if (e != cudaSuccess) {
     cudaGetLastError();
     h->err = std::string("step graph construction failed: ") + cudaGetErrorString(e);
     return LBM_ECUDA;
   }
-  h->step_graph[parity] = ex;
+  h->step_graph[parity][diag ? 1 : 0] = ex;
+  return LBM_OK;
+}
+
+// Builds the missing step graphs (both parities, both stream/collide
+// variants).
+lbm_status build_step_graphs(lbm_t* h) {
+  for (int k = 0; k < 2; ++k)
+    for (int d = 0; d < 2; ++d)
+      if (!h->step_graph[k][d]) {
+        lbm_status s = build_step_graph(h, k, d == 1);
+        if (s != LBM_OK) return s;
+      }
   return LBM_OK;
 }
 
@@ -1598,10 +1561,11 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
   }
   const long long total0 = hs->total;
   const int fails0 = hs->fails;
-  // Steps are replayed in chunks; the distribution of the applications the
-  // steps needed (accumulated over at least CHUNK steps) sets the number k
-  // baked into the graphs (rebuilt only when k changes): the k of least
-  // expected cost per step.  A step costs its k applications; one that
+  // Steps are replayed in chunks.  With the start from the solve history k
+  // is one.  Otherwise the distribution of the applications the steps
+  // needed (accumulated over at least CHUNK steps) sets the number k baked
+  // into the graphs (rebuilt only when k changes): the k of least expected
+  // cost per step.  A step costs its k applications; one that
   // needs m > k also runs the while loop, m - k applications and residuals,
   // and the stream/collide again.  In units of a residual an application
   // costs about 4 and the stream/collide about 3.3 per FP32 species (3 per
@@ -1611,24 +1575,30 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
   const double costC = (h->cfg.storage == LBM_FP32 ? 3.3 : 3.0) * h->S;
   int done = 0;
   while (done < nsteps) {
-    const int pred = sp->graph_pred > 0 ? sp->graph_pred : sp->last_iters;
+    // with the start from the history the steady state needs one
+    // application (the device-side loop adds what a step needs beyond
+    // it); otherwise the choice from the steps seen so far
+    const int pred = start_enabled(h) ? 1 : (sp->graph_pred > 0 ? sp->graph_pred : sp->last_iters);
     const int want = std::max(1, std::min(std::min(pred, h->cfg.poisson_maxit), Poisson::NSLOT - 1));
     if (sp->graph_k != want) {
       spectral_graph_free(h);
       sp->graph_k = want;
     }
-    for (int k = 0; k < 2; ++k)
-      if (!h->step_graph[k]) {
-        lbm_status s = build_step_graph(h, k);
-        if (s != LBM_OK) return s;
-      }
+    {
+      lbm_status s = build_step_graphs(h);
+      if (s != LBM_OK) return s;
+    }
     const int n = std::min(CHUNK, nsteps - done);
     const long long tot_before = hs->total;
     LBM_CUDA_TRY(h, cudaMemsetAsync(ds->need, 0, 8 * sizeof(int), h->st));  // need, needf
+    // the call's last step replays the variant that sums the state it
+    // stores (diagnostics)
     for (int k = 0; k < n; ++k) {
-      LBM_CUDA_TRY(h, cudaGraphLaunch(h->step_graph[h->cur], h->st));
+      const int d = (done + k == nsteps - 1) ? 1 : 0;
+      LBM_CUDA_TRY(h, cudaGraphLaunch(h->step_graph[h->cur][d], h->st));
       h->cur ^= 1;
       ++h->tstep;
+      h->diag_valid = d == 1;
     }
     LBM_CUDA_TRY(h, cudaMemcpyAsync(hs, ds, sizeof(GraphStatus), cudaMemcpyDeviceToHost, h->st));
     LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
@@ -1664,16 +1634,14 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
   }
   // a new choice of k is built now, so that the next call starts replaying
   // at once
-  if (sp->graph_pred > 0) {
+  if (sp->graph_pred > 0 && !start_enabled(h)) {
     const int want = std::max(1, std::min(std::min(sp->graph_pred, h->cfg.poisson_maxit),
                                           Poisson::NSLOT - 1));
     if (sp->graph_k != want) {
       spectral_graph_free(h);
       sp->graph_k = want;
-      for (int k = 0; k < 2; ++k) {
-        lbm_status s = build_step_graph(h, k);
-        if (s != LBM_OK) return s;
-      }
+      lbm_status s = build_step_graphs(h);
+      if (s != LBM_OK) return s;
     }
   }
   const long long iters = hs->total - total0;

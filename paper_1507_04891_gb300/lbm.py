@@ -34,6 +34,7 @@ EXPORTED = [
     "lbm_nn_init", "lbm_nn_collect", "lbm_nn_train", "lbm_nn_use", "lbm_nn_params",
     "lbm_nn_loss_grad", "lbm_nn_stats", "lbm_get_moments_noalloc", "lbm_state_len", "lbm_stream", "lbm_last_error",
     "lbm_set_species_dev", "lbm_get_moments_dev", "lbm_plane_fluxes", "lbm_omega_drag_for_schmidt",
+    "lbm_set_drag_matrix",
 ]
 
 
@@ -141,6 +142,8 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_plane_fluxes.restype = I
     lib.lbm_omega_drag_for_schmidt.argtypes = [D, D]
     lib.lbm_omega_drag_for_schmidt.restype = D
+    lib.lbm_set_drag_matrix.argtypes = [P, P]
+    lib.lbm_set_drag_matrix.restype = I
     _lib = lib
     return lib
 
@@ -222,6 +225,14 @@ class Lattice:
 
     def instance_z0(self, i):
         return int(self._lib.lbm_instance_z0(self.h, int(i)))
+
+    def set_drag_matrix(self, omega):
+        """lbm_set_drag_matrix: symmetric (S, S) matrix of pair drag
+        frequencies, or None for the config's single omega_drag."""
+        w = None if omega is None else np.ascontiguousarray(omega, dtype=np.float64)
+        if w is not None and w.shape != (self.S, self.S):
+            raise ValueError("the drag matrix must be (S, S)")
+        self._check(self._lib.lbm_set_drag_matrix(self.h, _ptr(w)))
 
     def set_plane_omega_drag(self, omega):
         om = None if omega is None else np.ascontiguousarray(omega, dtype=np.float64)

@@ -144,18 +144,28 @@ def porous_spheres(n=256, seed=1238, solid_fraction=0.20, rmin=4, rmax=12,
     shape = (n, n, n)
     solid = np.zeros(shape, dtype=bool)
     sign = np.zeros(shape)
-    zz, yy, xx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
-    while solid.mean() < solid_fraction:
+    nsolid, target = 0, solid_fraction * n ** 3
+    while nsolid < target:
         c = rng.integers(0, n, size=3)
         r = int(rng.integers(rmin, rmax + 1))
         s = 1.0 if rng.random() < 0.5 else -1.0
-        dz = (zz - c[0] + n // 2) % n - n // 2
-        dy = (yy - c[1] + n // 2) % n - n // 2
-        dx = (xx - c[2] + n // 2) % n - n // 2
-        inside = dx * dx + dy * dy + dz * dz <= r * r
-        new = inside & ~solid
-        sign[new] = s
-        solid |= inside
+        # the nodes within distance r of c (periodic, nearest image), taken
+        # from the bounding box of the sphere only (the whole axis when the
+        # box would wrap onto itself)
+        def offsets(ci):
+            if 2 * r + 1 <= n:
+                return np.arange(-r, r + 1)
+            return (np.arange(n) - ci + n // 2) % n - n // 2
+        oz, oy, ox = offsets(c[0]), offsets(c[1]), offsets(c[2])
+        iz, iy, ix = (c[0] + oz) % n, (c[1] + oy) % n, (c[2] + ox) % n
+        inside = (oz[:, None, None] ** 2 + oy[None, :, None] ** 2 + ox[None, None, :] ** 2) <= r * r
+        box = np.ix_(iz, iy, ix)
+        new = inside & ~solid[box]
+        sub = sign[box]
+        sub[new] = s
+        sign[box] = sub
+        solid[box] |= inside
+        nsolid += int(new.sum())
     fluid = ~solid
     surface = np.zeros(shape, dtype=bool)
     for ax in range(3):

@@ -1,8 +1,9 @@
-"""The extrapolated start of the Poisson solves (2 psi(t-1) - 2 psi(t-3) +
-psi(t-4) once the history is full): the same trajectory as the plain warm
-start within round-off of the 1e-8 solves, fewer applications per step, the
-same on host-driven and graph steps, and a history that restarts when the
-state is replaced."""
+"""The start of the Poisson solves from the history of the solves (the
+previous potential advanced by the least-squares fit of the new source
+difference over the last five): the same trajectory as the plain warm start
+within round-off of the 1e-8 solves, fewer applications per step, the same on
+host-driven and graph steps, and a history that restarts when the state is
+replaced."""
 
 import numpy as np
 import pytest

@@ -56,7 +56,7 @@ def test_slit_currents_against_theory_at_two_drag_frequencies():
         od = lbm.omega_drag_for_schmidt(1.0, sc)
         lat.set_plane_omega_drag(np.full(W + 2, od))
         lat.step(20000)
-        c = transport.slit_currents(lat, wl.valence, e, od, wl.solid)
+        c = transport.slit_currents(lat, wl.valence, wl.solid)
         assert lat.diagnostics()["poisson_residual"] <= 1e-8
         assert abs(c["I_m"] / im_th - 1) <= 0.01, (sc, c["I_m"], im_th)
         assert abs(c["I_eo"] / ieo_th - 1) <= 0.02, (sc, c["I_eo"], ieo_th)

@@ -1,10 +1,11 @@
 """Host analysis of slit currents (paper_1507_04891_gb300/transport.py) on
-synthetic moments with a known answer, and the bulk-conductivity input.
+prescribed plane sums, and the bulk-conductivity input.
 
-A stand-in lattice returns prescribed densities and bare velocities; the
-currents must follow from the mid-step velocities u + F/2 with
-F = z E - omega_drag (u + z E / 2 - v): computed here independently per
-node, in a loop, and compared with the vectorised analysis."""
+A stand-in lattice returns prescribed plane sums of n and of the mid-step
+flux (what lbm_plane_fluxes returns); the currents must be the sums over the
+fluid planes of the plane averages, computed here independently in a loop.
+The mid-step flux itself is computed on the GPU and checked against the
+oracle in tests/test_gpu_plane_fluxes.py."""
 
 import numpy as np
 
@@ -13,63 +14,52 @@ from paper_1507_04891_gb300 import workloads as WL
 
 
 class FakeLattice:
-    def __init__(self, n, u):
-        self.n, self.u = n, u
+    def __init__(self, sums):
+        self.sums = sums
 
-    def get_moments(self, s):
-        return self.n[s].copy(), self.u[s].copy()
+    def plane_fluxes(self):
+        return self.sums.copy()
 
 
 def test_slit_currents_match_a_direct_loop():
     rng = np.random.default_rng(3)
     S, shape = 3, (6, 2, 3)
-    solid = np.zeros(shape, bool)
-    solid[0] = solid[-1] = True
-    n = rng.uniform(0.001, 0.02, size=(S,) + shape)
-    n[0] = 1.0 - n[1] - n[2]
-    u = rng.normal(0, 1e-4, size=(S, 3) + shape)
-    n[:, solid] = 0.0
-    u[:, :, solid] = 0.0
-    valence, E, om = np.array([0.0, 1.0, -1.0]), 2e-4, 1.7
-    c = transport.slit_currents(FakeLattice(n, u), valence, E, om, solid)
-    # direct per-node computation
-    Im = I = Ieo = 0.0
     nz, ny, nx = shape
-    prof_n = np.zeros((S, nz))
-    prof_j = np.zeros((S, nz))
-    for zz in range(1, nz - 1):
-        for yy in range(ny):
-            for xx in range(nx):
-                nn = n[:, zz, yy, xx]
-                ux = u[:, 0, zz, yy, xx]
-                v = sum(nn[b] * (ux[b] + 0.5 * valence[b] * E) for b in range(S)) / nn.sum()
-                for a in range(S):
-                    F = valence[a] * E - om * (ux[a] + 0.5 * valence[a] * E - v)
-                    prof_n[a, zz] += nn[a] / (nx * ny)
-                    prof_j[a, zz] += nn[a] * (ux[a] + 0.5 * F) / (nx * ny)
-    for zz in range(1, nz - 1):
-        rho = prof_n[:, zz].sum()
-        uxb = prof_j[:, zz].sum() / rho
-        Im += prof_j[:, zz].sum()
-        I += sum(valence[a] * prof_j[a, zz] for a in range(S))
-        Ieo += sum(valence[a] * prof_n[a, zz] for a in range(S)) * uxb
-    np.testing.assert_allclose([c["I_m"], c["I"], c["I_eo"]], [Im, I, Ieo], rtol=1e-12, atol=1e-20)
-
-
-def test_half_force_shift_of_a_uniform_drift():
-    """A neutral pair drifting at the Einstein velocity in its bare moments:
-    the drag on force-shifted velocities leaves the mid-step current equal to
-    the bare one plus half the field's push, which cancels for +/- ions."""
-    shape = (4, 1, 1)
     solid = np.zeros(shape, bool)
     solid[0] = solid[-1] = True
-    n = np.zeros((3,) + shape)
-    n[:, 1:-1] = np.array([0.98, 0.01, 0.01])[:, None, None, None]
-    u = np.zeros((3, 3) + shape)
-    u[1, 0, 1:-1], u[2, 0, 1:-1] = 3e-5, -3e-5
-    c = transport.slit_currents(FakeLattice(n, u), np.array([0.0, 1.0, -1.0]), 1e-4, 1.5, solid)
-    assert abs(c["I_m"]) < 1e-18
-    assert c["I"] > 0 and abs(c["I_eo"]) < 1e-18
+    sums = np.zeros((nz, S, 4))
+    for z in range(1, nz - 1):
+        n = rng.uniform(0.001, 0.02, size=S)
+        n[0] = 1.0 - n[1] - n[2]
+        sums[z, :, 0] = n * nx * ny
+        sums[z, :, 1:] = rng.normal(0, 1e-4, size=(S, 3)) * nx * ny
+    valence = np.array([0.0, 1.0, -1.0])
+    c = transport.slit_currents(FakeLattice(sums), valence, solid)
+    Im = I = Ieo = 0.0
+    for z in range(1, nz - 1):
+        n = sums[z, :, 0] / (nx * ny)
+        j = sums[z, :, 1] / (nx * ny)
+        ux = j.sum() / n.sum()
+        Im += j.sum()
+        I += sum(valence[a] * j[a] for a in range(S))
+        Ieo += sum(valence[a] * n[a] for a in range(S)) * ux
+    np.testing.assert_allclose([c["I_m"], c["I"], c["I_eo"]], [Im, I, Ieo], rtol=1e-12, atol=1e-20)
+    u0 = sums[1:-1, 0, 1] / sums[1:-1, 0, 0]
+    uxb = sums[1:-1, :, 1].sum(1) / sums[1:-1, :, 0].sum(1)
+    assert abs(c["solvent_vs_barycentric"] - np.abs(u0 - uxb).max() / np.abs(uxb).max()) < 1e-12
+
+
+def test_only_whole_fluid_planes_count():
+    """A plane with any wall node is not part of the channel."""
+    S, shape = 2, (4, 2, 2)
+    solid = np.zeros(shape, bool)
+    solid[0] = True
+    solid[2, 0, 0] = True
+    sums = np.zeros((4, S, 4))
+    sums[:, :, 0] = 4.0
+    sums[:, 0, 1] = [0.0, 1.0, 100.0, 2.0]
+    c = transport.slit_currents(FakeLattice(sums), np.array([0.0, 0.0]), solid)
+    assert c["I_m"] == (1.0 + 2.0) / 4
 
 
 def test_bulk_conductivity_input_is_neutral_and_uniform():

@@ -93,3 +93,25 @@ def test_porous_spheres_recipe_small_box():
     assert np.all(wl.n0[:, solid] == 0)
     np.testing.assert_allclose(wl.n0[:, fluid].sum(0), 1.0, rtol=0, atol=1e-15)
     assert np.ptp(wl.n0[1][fluid]) == 0 and np.ptp(wl.n0[2][fluid]) == 0
+
+
+def test_porous_spheres_bounding_boxes_equal_the_whole_grid_recipe():
+    """The generator places each sphere through its bounding box; the same
+    draws applied to the whole grid (distance of every node to the centre,
+    nearest periodic image) give the same solid mask and charges."""
+    n, seed = 40, 77
+    wl = WL.porous_spheres(n=n, seed=seed, rmin=3, rmax=9)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    solid = np.zeros((n, n, n), bool)
+    sign = np.zeros((n, n, n))
+    zz, yy, xx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    while solid.mean() < 0.20:
+        c = rng.integers(0, n, size=3)
+        r = int(rng.integers(3, 9 + 1))
+        s = 1.0 if rng.random() < 0.5 else -1.0
+        d2 = sum(((g - ci + n // 2) % n - n // 2) ** 2 for g, ci in zip((zz, yy, xx), c))
+        inside = d2 <= r * r
+        sign[inside & ~solid] = s
+        solid |= inside
+    assert np.array_equal(wl.solid, solid)
+    assert np.array_equal(np.sign(wl.sigma), np.where(wl.sigma != 0, sign, 0.0))
