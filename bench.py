@@ -488,18 +488,21 @@ def run_batched(lbm, WL, steps=40, local=0, extrapolate=True):
             "speedup_fp16_vs_fp32_stacked": arms["stacked_fp32"]["ms_per_step"] / head["ms_per_step"]}
 
 
-def run_learned(lbm, WL, n=64, steps=10, local=0):
-    """Learned Poisson initial guess vs plain warm start, multigrid to 1e-8,
-    on a charged ternary porous box (spheres radius 4..12, 20% solid,
-    surface charge +/-0.01): the network is trained on the initial residuals
-    of 16 solver steps, then three arms run the same held-out steps from the
-    same state: plain (each solve from the previous potential), learned
-    (the network's correction of that start), extrapolated (each solve from
-    the parabola through the three previous potentials, no network)."""
+def run_learned(lbm, WL, n=64, steps=20, warm=20, local=0, train=None):
+    """Learned Poisson initial guess on the charged ternary porous box
+    (spheres of radius 4..12 up to 20% solid, surface charge +/-0.01),
+    multigrid to 1e-8 every step.  The network (two 3x3x3 layers) is trained
+    on the GPU on the residuals the solver's own starts leave (16 steps of a
+    training run), then three arms step the same trajectory from the same
+    initial state: each solve from the previous potential (plain), from the
+    history start (history), and from the history start corrected by the
+    network (learned).  Returns V-cycles and Poisson time per step and the
+    start residuals of each arm, and the trained parameters."""
+    import torch
     wl = WL.porous_spheres(n=n, seed=1238)
     od = lbm.omega_drag_for_schmidt(1.0, 1.0)
 
-    def make(extrapolate=False):
+    def make(extrapolate=True):
         lat = lbm.Lattice(n, n, n, 3, omega_drag=od, bjerrum=0.7, poisson="mg", poisson_maxit=200,
                           device=local, extrapolate=extrapolate)
         lat.set_walls(wl.solid, wl.sigma)
@@ -507,53 +510,64 @@ def run_learned(lbm, WL, n=64, steps=10, local=0):
             lat.set_species(s, 1.0, wl.valence[s], np.where(wl.solid, 1.0, wl.n0[s]))
         return lat
 
-    base = make()
-    base.step(4)
-    base.nn_init(hidden=8, seed=3)
-    base.nn_collect(16)
-    base.step(16)
-    t = time.perf_counter()
-    losses = base.nn_train(epochs=40, lr=5e-3)
-    train_s = time.perf_counter() - t
-    params = base.nn_params()
-    state, step = base.get_state()
-    psi = base.get_potential()
-    base.destroy()
-    out = {}
-    # plain and learned start each solve from the previous potential; the
-    # third arm starts from its extrapolation in time (no network)
-    for use in (False, True, "extrapolated"):
-        lat = make(extrapolate=use == "extrapolated")
-        lat.set_state(state, step)
-        rho = lat.get_moments(1)[0] - lat.get_moments(2)[0]
-        lat.solve_poisson(rho, psi, tol=1e-12)
-        if use is True:
+    out = {"workload": "porous_%d^3 ternary, solid %.3f, multigrid, Sc 1" % (n, wl.meta["solid_fraction"]),
+           "steps": steps, "warmup": warm}
+    if train is None:
+        base = make()
+        base.step(4)
+        base.nn_init(hidden=8, seed=3)
+        base.nn_collect(16)
+        base.step(16)
+        t = time.perf_counter()
+        losses = base.nn_train(epochs=40, lr=5e-3)
+        train_s = time.perf_counter() - t
+        params = base.nn_params()
+        base.destroy()
+        out["training"] = {"fields": 16, "epochs": 40, "loss_first": float(losses[0]),
+                           "loss_last": float(losses[-1]), "seconds": train_s,
+                           "params": int(params.size), "lattice": "%d^3" % n}
+    else:
+        params = train
+    for arm in ("plain", "history", "learned"):
+        lat = make(extrapolate=arm != "plain")
+        if arm == "learned":
             lat.nn_init(hidden=8, seed=3)
             lat.nn_params(params)
             lat.nn_use(True)
+        lat.step(warm)
+        lat.synchronize()
+        stream = torch.cuda.ExternalStream(lat.stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         lat.set_timing(True)
+        e0.record(stream)
         lat.step(steps)
+        e1.record(stream)
+        lat.synchronize()
+        t_ms = e0.elapsed_time(e1)
         tm = lat.get_timing()
-        st = lat.nn_stats() if use is True else None
-        out[{False: "plain", True: "learned"}.get(use, "extrapolated")] = {
-            "poisson_iters_per_step": tm["poisson_iters"] / steps,
-            "poisson_ms_per_step": tm["poisson_ms"] / steps,
-            "residual_ratio_after_guess": st["mean_ratio"] if st else None,
-            "guesses_kept": ("%d/%d" % (st["kept"], st["tried"])) if st else None,
-            "final_residual": lat.diagnostics()["poisson_residual"]}
+        ps = lat.poisson_stats()
+        st = lat.nn_stats() if arm == "learned" else None
+        out[arm] = {"vcycles_per_step": tm["poisson_iters"] / steps,
+                    "poisson_ms_per_step": tm["poisson_ms"] / steps,
+                    "ms_per_step": t_ms / steps,
+                    "value": 3 * wl.sites * steps / (t_ms / 1e3) / 1e6,
+                    "start_residual_geomean": ps["start_residual_geomean"],
+                    "residual_ratio_after_guess": st["mean_ratio"] if st else None,
+                    "guesses_kept": ("%d/%d" % (st["kept"], st["tried"])) if st else None,
+                    "final_residual": lat.diagnostics()["poisson_residual"]}
         lat.destroy()
-    out["workload"] = "porous_%d^3 ternary, solid %.3f, multigrid" % (n, wl.meta["solid_fraction"])
-    out["training"] = {"fields": 16, "epochs": 40, "loss_first": float(losses[0]),
-                       "loss_last": float(losses[-1]), "seconds": train_s, "params": int(params.size)}
+    out["params"] = params
     return out
 
 
-def run_porous(lbm, WL, steps=20, warm=5, local=0, n=256):
+def run_porous(lbm, WL, steps=20, warm=5, local=0, n=256, params=None):
     """The charged ternary porous box at full size (256^3, seeded spheres of
     radius 4..12 up to 20% solid, surface charge +/-0.01 per surface node),
     Sc = 1, the multigrid Poisson solve every step to 1e-8: whole-step rate,
     V-cycles per step and the phase times, for each solve's start from the
-    previous potential (plain) and from its extrapolation in time."""
+    previous potential (plain), from the history start (history) and, given
+    trained parameters, from the history start corrected by the network."""
     import torch
     t0 = time.perf_counter()
     wl = WL.porous_spheres(n=n, seed=1238)
@@ -561,14 +575,21 @@ def run_porous(lbm, WL, steps=20, warm=5, local=0, n=256):
     od = lbm.omega_drag_for_schmidt(1.0, 1.0)
     out = {"workload": "porous_%d^3 ternary, solid %.3f, multigrid, Sc 1" % (n, wl.meta["solid_fraction"]),
            "steps": steps, "warmup": warm, "input_seconds": gen_s}
-    for arm in ("plain", "extrapolated"):
+    arms = ("plain", "history") + (("learned",) if params is not None else ())
+    for arm in arms:
         t0 = time.perf_counter()
         lat = lbm.Lattice(n, n, n, 3, omega_drag=od, bjerrum=wl.bjerrum, poisson="mg",
                           poisson_tol=1e-8, poisson_maxit=200, device=local,
-                          extrapolate=arm == "extrapolated")
+                          extrapolate=arm != "plain")
         lat.set_walls(wl.solid, wl.sigma)
         for s in range(3):
             lat.set_species(s, 1.0, wl.valence[s], np.where(wl.solid, 1.0, wl.n0[s]))
+        if arm == "learned":
+            # the network trained on the 64^3 box (a convolution: it applies
+            # at any size)
+            lat.nn_init(hidden=8, seed=3)
+            lat.nn_params(params)
+            lat.nn_use(True)
         setup_s = time.perf_counter() - t0
         lat.step(warm)
         lat.synchronize()
@@ -582,9 +603,11 @@ def run_porous(lbm, WL, steps=20, warm=5, local=0, n=256):
         lat.synchronize()
         t_ms = e0.elapsed_time(e1)
         tm = lat.get_timing()
+        ps = lat.poisson_stats()
         lat.set_timing(False)
         d = lat.diagnostics()
         out[arm] = {"value": 3 * wl.sites * steps / (t_ms / 1e3) / 1e6, "unit": UNIT,
+                    "start_residual_geomean": ps["start_residual_geomean"],
                     "ms_per_step": t_ms / steps,
                     "vcycles_per_step": tm["poisson_iters"] / steps,
                     "poisson_ms_per_step": tm["poisson_ms"] / steps,
@@ -894,7 +917,7 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_extras:
         batched = run_batched(lbm, WL, local=local, extrapolate=not args.no_extrapolation)
         learned = run_learned(lbm, WL, local=local)
-        porous = run_porous(lbm, WL, steps=K, warm=warm, local=local)
+        porous = run_porous(lbm, WL, steps=K, warm=warm, local=local, params=learned.pop("params"))
 
     # end to end through the C ABI: the initial densities copied from pinned
     # host memory to device buffers and handed over with lbm_set_species_dev,
@@ -1008,6 +1031,7 @@ def main():
             res = run_conductivity(lbm, WL, n=args.n if args.n != 128 else 64)
         else:
             res = run_learned(lbm, WL)
+            res["porous_256"] = run_porous(lbm, WL, params=res.pop("params"))
         print(json.dumps({"metric": METRIC, "only": args.only, **res}), flush=True)
         return 0
     if args.impl == "reference":

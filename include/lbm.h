@@ -100,9 +100,9 @@ typedef struct {
  * give psi(t-1) + sum c_j P_j (the projection of the new right-hand side on
  * the recent ones; fewer terms while the history fills after lbm_create,
  * lbm_set_species, lbm_set_state or lbm_solve_poisson, which restart it).
- * The solve still iterates to poisson_tol.  Not applied while the learned
- * guess is collecting or in use.  The paper has no counterpart: a property
- * of this library's solver.                                               */
+ * The solve still iterates to poisson_tol.  The learned guess, when in
+ * use, corrects this start.  The paper has no counterpart: a property of
+ * this library's solver.                                                  */
 #define LBM_FLAG_NO_EXTRAPOLATION 2
 
 /* Fills *cfg with defaults: omega_visc = 1, omega_drag = 1, l_B = 0,
@@ -155,11 +155,11 @@ lbm_status lbm_autotune(lbm_t* h, double* out);
 /* Learned initial guess of the Poisson solve.  The paper has no
  * counterpart: this is an addition of this library.  A small periodic 3-D
  * convolutional network (two 3x3x3 layers, `hidden` channels, tanh) maps
- * the normalised residual of the warm-start potential and the fluid mask
- * to a correction of psi.  The solver applies it before iterating, keeps it
- * only if the residual drops, and always iterates to the same tolerance.
- * While the network collects or is used, each solve starts from the
- * previous step's potential (no extrapolation in time).
+ * the normalised residual of the solve's start (the history start of
+ * LBM_FLAG_NO_EXTRAPOLATION's note, or the previous potential with that
+ * flag) and the fluid mask to a correction of psi.  The solver applies it
+ * before iterating, keeps it only if the residual drops, and always
+ * iterates to the same tolerance.
  *   lbm_nn_init     random initialisation (seeded), hidden in 1..16;
  *                   requires l_B > 0 and host-driven steps
  *   lbm_nn_collect  store the initial residual of each following solve in
@@ -172,6 +172,10 @@ lbm_status lbm_autotune(lbm_t* h, double* out);
  *                   may be NULL; *nparams receives their count
  *   lbm_nn_loss_grad  loss and parameter gradient (FP32) on a given
  *                   normalised residual field x0 (N floats, host)
+ *   lbm_nn_infer    the inference pass the solver uses (FP16 weights and
+ *                   activations) on a given normalised residual x0: the
+ *                   correction y in units of the residual's rms (N floats,
+ *                   host; zero at wall nodes)
  *   lbm_nn_stats    out[0] guesses tried, out[1] kept, out[2] mean residual
  *                   ratio after/before of the kept ones, out[3] collected
  *                   fields, out[4] parameter count                        */
@@ -181,6 +185,7 @@ lbm_status lbm_nn_train(lbm_t* h, int epochs, double lr, double* losses);
 lbm_status lbm_nn_use(lbm_t* h, int enable);
 lbm_status lbm_nn_params(lbm_t* h, float* get, const float* set, int* nparams);
 lbm_status lbm_nn_loss_grad(lbm_t* h, const float* x0, double* loss, float* grad);
+lbm_status lbm_nn_infer(lbm_t* h, const float* x0, float* y);
 lbm_status lbm_nn_stats(lbm_t* h, double* out);
 
 /* Releases every device buffer of h.  NULL is accepted.                  */
@@ -334,6 +339,17 @@ double lbm_omega_drag_for_schmidt(double omega_visc, double schmidt);
  * state (S*19*N).                                                          */
 int64_t lbm_num_nodes(const lbm_t* h);
 int64_t lbm_state_len(const lbm_t* h);
+
+/* Start residuals of the Poisson solves (how good each solve's initial
+ * potential was), written to out (5 doubles):
+ *   out[0] iterations of the last solve (V-cycles, sweeps or applications)
+ *   out[1] relative residual ||s - A psi|| / ||s|| at the start of the last
+ *          solve (graph steps: the geometric mean over the last call's steps)
+ *   out[2] relative residual at its end
+ *   out[3] solves counted since lbm_set_timing
+ *   out[4] mean of log10 of their start residuals
+ * The paper has no counterpart: a measurement of this library's solver.   */
+lbm_status lbm_poisson_stats(lbm_t* h, double* out);
 
 /* Phase timing.  lbm_set_timing(h, 1) makes every following lbm_step record
  * CUDA events around its phases on the stream it runs on; lbm_get_timing

@@ -91,6 +91,13 @@ struct Phase {
 
 namespace lbm_gb300 {
 
+void note_start_residual(lbm_t* h, double rel) {
+  if (!(rel >= 0.0) || !isfinite(rel)) return;
+  h->last_start = rel;
+  h->start_log_sum += log10(std::max(rel, 1e-300));
+  h->start_count += 1;
+}
+
 cudaError_t own_stream(lbm_t* h) {
   h->st = h->own;
   if (!h->foreign_pending) return cudaSuccess;
@@ -1006,9 +1013,26 @@ lbm_status lbm_nn_loss_grad(lbm_t* h, const float* x0, double* loss, float* grad
   return nn_loss_grad_host(h, x0, loss, grad);
 }
 
+lbm_status lbm_nn_infer(lbm_t* h, const float* x0, float* y) {
+  if (!h || !x0 || !y) return LBM_EINVAL;
+  cudaSetDevice(h->dev);
+  LBM_CUDA_TRY(h, own_stream(h));  // calls without a stream argument use the library's stream
+  return nn_infer_host(h, x0, y);
+}
+
 lbm_status lbm_nn_stats(lbm_t* h, double* out) {
   if (!h || !out) return LBM_EINVAL;
   nn_stats(h, out);
+  return LBM_OK;
+}
+
+lbm_status lbm_poisson_stats(lbm_t* h, double* out) {
+  if (!h || !out) return LBM_EINVAL;
+  out[0] = (double)h->last_iters;
+  out[1] = h->last_start;
+  out[2] = h->last_res;
+  out[3] = (double)h->start_count;
+  out[4] = h->start_count ? h->start_log_sum / (double)h->start_count : 0.0;
   return LBM_OK;
 }
 
@@ -1018,6 +1042,8 @@ lbm_status lbm_set_timing(lbm_t* h, int enable) {
   LBM_CUDA_TRY(h, drain_timing(h));
   h->timing = enable != 0;
   h->launches = 0;
+  h->start_log_sum = 0.0;
+  h->start_count = 0;
   for (int k = 0; k < 3; ++k) {
     h->t_acc[k] = 0.0;
     h->t_cnt[k] = 0;

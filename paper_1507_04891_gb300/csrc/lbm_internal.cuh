@@ -222,6 +222,11 @@ struct lbm {
   int* dflag = nullptr;
   int last_iters = 0;
   double last_res = 0.0;
+  // start residuals of the Poisson solves (lbm_poisson_stats): the last
+  // one, and the sum of log10 and the count since lbm_set_timing
+  double last_start = 0.0;
+  double start_log_sum = 0.0;
+  int64_t start_count = 0;
   int64_t tstep = 0;
   // phase timing (lbm_set_timing)
   bool timing = false;
@@ -275,6 +280,9 @@ template <>
 cudaError_t collide_dispatch<LBM_BF16_SHIFT>(const StepArgs&, int, bool, bool, cudaStream_t, int,
                                              bool);
 
+// Records the relative residual at the start of a Poisson solve.
+void note_start_residual(lbm_t* h, double rel);
+
 // ---- lbm_kernels.cu ----
 cudaError_t launch_init_species(lbm_t* h, int s, const double* n0_dev,
                                 const double* u0_dev);
@@ -327,7 +335,7 @@ lbm_status potential_history_reset(lbm_t* h);
 // ---- lbm_start.cu ----
 lbm_status start_setup(lbm_t* h);
 void start_free(lbm_t* h);
-// The start is used (LBM_FLAG_NO_EXTRAPOLATION off, no learned guess).
+// The start is used (LBM_FLAG_NO_EXTRAPOLATION off).
 bool start_enabled(const lbm_t* h);
 // After the step's charge density: psi <- the start from the history.
 // lagged: with the coefficients of the previous step's fit, this step's
@@ -352,6 +360,7 @@ void nn_free(lbm_t* h);
 lbm_status nn_collect(lbm_t* h, int capacity);
 lbm_status nn_train(lbm_t* h, int epochs, double lr, double* losses);
 lbm_status nn_loss_grad_host(lbm_t* h, const float* x0, double* loss, float* grad);
+lbm_status nn_infer_host(lbm_t* h, const float* x0, float* y);
 lbm_status nn_params(lbm_t* h, float* get, const float* set, int* np);
 // Solver hooks: given the initial FP32 residual (planes [zlo, zlo+nzb)),
 // stores it for training and/or applies the learned correction to psi.

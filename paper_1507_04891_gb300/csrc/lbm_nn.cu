@@ -48,6 +48,12 @@ struct NNet {
   float* pool = nullptr;
   int cap = 0, count = 0, next = 0;
   bool collect = false, use = false;
+  // inference on channel pairs: input packed per cell as (x0, fluid mask),
+  // hidden activations stored per cell ([N][C] halves), and a host copy of
+  // the parameters for the kernels' arguments (stale after training)
+  __half2* xin = nullptr;
+  std::vector<float> hp;
+  bool hp_stale = true;
   // statistics of the guesses applied by the solver
   long long tried = 0, accepted = 0;
   double sum_ratio = 0.0;    // sum of residual ratio after/before over accepted guesses
@@ -117,15 +123,19 @@ __device__ float apply_A(const float* v, const Geo& G, int64_t i, int x, int y, 
 
 // x0 = r / sigma (fluid), 0 at wall nodes.  The residual of a trimmed
 // multigrid box covers planes [zlo, zlo + nzb).
+// When xin is given, the same input packed for inference: (x0, fluid mask)
+// as one FP16 pair per cell.
 __global__ void k_nn_input(const float* __restrict__ r, int zlo, int nzb, float inv_sigma, Geo G,
-                           float* __restrict__ x0) {
+                           float* __restrict__ x0, __half2* __restrict__ xin) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= G.N) return;
   const int64_t nxy = (int64_t)G.nx * G.ny;
   const int z = (int)(i / nxy);
+  const bool fl = fluid_at(G, i);
   float v = 0.f;
-  if (z >= zlo && z < zlo + nzb && fluid_at(G, i)) v = r[i - (int64_t)zlo * nxy] * inv_sigma;
+  if (z >= zlo && z < zlo + nzb && fl) v = r[i - (int64_t)zlo * nxy] * inv_sigma;
   x0[i] = v;
+  if (xin) xin[i] = __floats2half2_rn(v, fl ? 1.f : 0.f);
 }
 
 __global__ void k_sum_sq(const float* __restrict__ a, int64_t n, double* out) {
@@ -225,6 +235,115 @@ __global__ void __launch_bounds__(256) k_nn_infer2(const __half* __restrict__ hi
     for (int c = 0; c < C; ++c) acc += __half2float(__hmul(W2[c * 27 + o], hid[(int64_t)c * G.N + j]));
   }
   dpsi[i] = sigma * acc;
+}
+
+// Inference on channel pairs (C even, up to 16): the weights are kernel
+// arguments (constant-bank operands of the FP16 pair FMAs, no loads), the
+// input is one (x0, mask) pair per cell, the hidden activations one vector
+// of C halves per cell.  Same network as k_nn_infer1/2: layer 1 with bias
+// and tanh (the hardware's approximate tanh of FP16 pairs), layer 2
+// accumulated per channel pair in FP16 and over pairs in FP32.
+template <int C>
+struct InferW {
+  __half2 w1x[27][C / 2];  // W1[c][0][o] for c = 2k, 2k + 1
+  __half2 w1m[27][C / 2];  // W1[c][1][o]
+  __half2 b1[C / 2];
+  __half2 w2[27][C / 2];   // W2[c][o]
+};
+
+template <int C>
+struct HidVec {  // the C hidden halves of one cell
+  __half2 v[C / 2];
+};
+
+__device__ __forceinline__ __half2 tanh_approx_h2(__half2 x) {
+  uint32_t r;
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(r) : "r"(*reinterpret_cast<const uint32_t*>(&x)));
+  return *reinterpret_cast<const __half2*>(&r);
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) k_nn_fast1(const __half2* __restrict__ xin, const InferW<C> w,
+                                                  Geo G, HidVec<C>* __restrict__ hid) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= G.N) return;
+  int x, y, z;
+  xyz(i, G, x, y, z);
+  const Taps T = taps_of(G, x, y, z);
+  __half2 acc[C / 2];
+#pragma unroll
+  for (int k = 0; k < C / 2; ++k) acc[k] = w.b1[k];
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    const __half2 v = xin[i + T.ox[o % 3] + T.oy[(o / 3) % 3] + T.oz[o / 9]];
+    const __half2 xx = __low2half2(v), mm = __high2half2(v);
+#pragma unroll
+    for (int k = 0; k < C / 2; ++k) acc[k] = __hfma2(w.w1m[o][k], mm, __hfma2(w.w1x[o][k], xx, acc[k]));
+  }
+  HidVec<C> out;
+#pragma unroll
+  for (int k = 0; k < C / 2; ++k) out.v[k] = tanh_approx_h2(acc[k]);
+  hid[i] = out;
+}
+
+// Layer 2 and the correction: dpsi = sigma y on fluid cells (kept for a
+// revert), psi += round(dpsi) in fixed point.
+template <int C>
+__global__ void __launch_bounds__(256) k_nn_fast2(const HidVec<C>* __restrict__ hid, const InferW<C> w,
+                                                  Geo G, float sigma, float* __restrict__ dpsi,
+                                                  int64_t* __restrict__ psi) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= G.N) return;
+  if (!fluid_at(G, i)) {
+    dpsi[i] = 0.f;
+    return;
+  }
+  int x, y, z;
+  xyz(i, G, x, y, z);
+  const Taps T = taps_of(G, x, y, z);
+  __half2 acc[C / 2];
+#pragma unroll
+  for (int k = 0; k < C / 2; ++k) acc[k] = __float2half2_rn(0.f);
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    const HidVec<C> h = hid[i + T.ox[o % 3] + T.oy[(o / 3) % 3] + T.oz[o / 9]];
+#pragma unroll
+    for (int k = 0; k < C / 2; ++k) acc[k] = __hfma2(w.w2[o][k], h.v[k], acc[k]);
+  }
+  float yv = 0.f;
+#pragma unroll
+  for (int k = 0; k < C / 2; ++k) {
+    const float2 f = __half22float2(acc[k]);
+    yv += f.x + f.y;
+  }
+  const float d = sigma * yv;
+  dpsi[i] = d;
+  psi[i] += f32_to_i64_rn(d * PSI_SCALE_F);
+}
+
+template <int C>
+InferW<C> infer_weights(const std::vector<float>& p) {
+  InferW<C> w;
+  const int b1 = C * 2 * 27, w2 = b1 + C;
+  for (int o = 0; o < 27; ++o)
+    for (int k = 0; k < C / 2; ++k) {
+      const int c0 = 2 * k, c1 = 2 * k + 1;
+      w.w1x[o][k] = __floats2half2_rn(p[(c0 * 2 + 0) * 27 + o], p[(c1 * 2 + 0) * 27 + o]);
+      w.w1m[o][k] = __floats2half2_rn(p[(c0 * 2 + 1) * 27 + o], p[(c1 * 2 + 1) * 27 + o]);
+      w.w2[o][k] = __floats2half2_rn(p[w2 + c0 * 27 + o], p[w2 + c1 * 27 + o]);
+    }
+  for (int k = 0; k < C / 2; ++k) w.b1[k] = __floats2half2_rn(p[b1 + 2 * k], p[b1 + 2 * k + 1]);
+  return w;
+}
+
+template <int C>
+cudaError_t fast_infer(NNet* n, const Geo& G, float sigma, int64_t* psi, cudaStream_t st) {
+  const InferW<C> w = infer_weights<C>(n->hp);
+  const unsigned b = nb(G.N, 256);
+  HidVec<C>* hid = reinterpret_cast<HidVec<C>*>(n->hid16);
+  k_nn_fast1<C><<<b, 256, 0, st>>>(n->xin, w, G, hid);
+  k_nn_fast2<C><<<b, 256, 0, st>>>(hid, w, G, sigma, n->y, psi);
+  return cudaGetLastError();
 }
 
 // res = x0 - A y and its squared sum.
@@ -428,6 +547,7 @@ void nn_free(lbm_t* h) {
   cudaFree(n->x0);
   cudaFree(n->hid);
   cudaFree(n->hid16);
+  cudaFree(n->xin);
   cudaFree(n->y);
   cudaFree(n->res);
   cudaFree(n->gy);
@@ -458,6 +578,7 @@ lbm_status nn_init(lbm_t* h, int hidden, uint64_t seed) {
             cudaMalloc(&n->x0, N * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->hid, (size_t)hidden * N * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->hid16, (size_t)hidden * N * sizeof(__half)) == cudaSuccess &&
+            cudaMalloc(&n->xin, N * sizeof(__half2)) == cudaSuccess &&
             cudaMalloc(&n->y, N * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->res, N * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->gy, N * sizeof(float)) == cudaSuccess &&
@@ -523,8 +644,10 @@ lbm_status nn_before_solve(lbm_t* h, const float* r, int zlo, int nzb, double rm
   if (!n || rms <= 0.0 || !isfinite(rms)) return LBM_OK;
   const Geo G = geo_of(h);
   const unsigned b = nb(G.N, 256);
+  const bool fast = n->C == 2 || n->C == 4 || n->C == 8 || n->C == 16;
   if (n->collect || n->use) {
-    k_nn_input<<<b, 256, 0, h->st>>>(r, zlo, nzb, (float)(1.0 / rms), G, n->x0);
+    k_nn_input<<<b, 256, 0, h->st>>>(r, zlo, nzb, (float)(1.0 / rms), G, n->x0,
+                                      n->use && fast ? n->xin : nullptr);
     ++h->launches;
   }
   if (n->collect && n->cap > 0) {
@@ -534,10 +657,27 @@ lbm_status nn_before_solve(lbm_t* h, const float* r, int zlo, int nzb, double rm
     n->count = std::min(n->count + 1, n->cap);
   }
   if (n->use) {
-    k_nn_infer1<<<b, 256, 0, h->st>>>(n->x0, n->ph, n->C, G, n->hid16);
-    k_nn_infer2<<<b, 256, 0, h->st>>>(n->hid16, n->ph, n->C, G, (float)rms, n->y);
-    k_nn_apply<<<b, 256, 0, h->st>>>(h->ps.psi[h->ps.cur], n->y, G.N, +1);
-    h->launches += 3;
+    if (fast) {
+      if (n->hp_stale) {
+        n->hp.resize(n->np);
+        LBM_CUDA_TRY(h, cudaMemcpyAsync(n->hp.data(), n->p, n->np * sizeof(float), cudaMemcpyDeviceToHost,
+                                        h->st));
+        LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+        n->hp_stale = false;
+      }
+      int64_t* psi = h->ps.psi[h->ps.cur];
+      cudaError_t e = n->C == 2   ? fast_infer<2>(n, G, (float)rms, psi, h->st)
+                      : n->C == 4 ? fast_infer<4>(n, G, (float)rms, psi, h->st)
+                      : n->C == 8 ? fast_infer<8>(n, G, (float)rms, psi, h->st)
+                                  : fast_infer<16>(n, G, (float)rms, psi, h->st);
+      LBM_CUDA_TRY(h, e);
+      h->launches += 2;
+    } else {
+      k_nn_infer1<<<b, 256, 0, h->st>>>(n->x0, n->ph, n->C, G, n->hid16);
+      k_nn_infer2<<<b, 256, 0, h->st>>>(n->hid16, n->ph, n->C, G, (float)rms, n->y);
+      k_nn_apply<<<b, 256, 0, h->st>>>(h->ps.psi[h->ps.cur], n->y, G.N, +1);
+      h->launches += 3;
+    }
     LBM_CUDA_TRY(h, cudaGetLastError());
     *applied = true;
     *dpsi_out = n->y;
@@ -597,6 +737,7 @@ lbm_status nn_train(lbm_t* h, int epochs, double lr, double* losses) {
       ++n->adam_t;
       k_adam<<<nb(n->np, 256), 256, 0, h->st>>>(n->p, n->g, n->m, n->v, n->np, (float)lr, 0.9f,
                                                 0.999f, 1e-8f, n->adam_t, n->ph);
+      n->hp_stale = true;
       ++h->launches;
       LBM_CUDA_TRY(h, cudaGetLastError());
     }
@@ -621,6 +762,48 @@ lbm_status nn_loss_grad_host(lbm_t* h, const float* x0_host, double* loss, float
   return LBM_OK;
 }
 
+lbm_status nn_infer_host(lbm_t* h, const float* x0_host, float* y_host) {
+  NNet* n = h->nn;
+  if (!n) {
+    h->err = "network not initialised";
+    return LBM_EINVAL;
+  }
+  const Geo G = geo_of(h);
+  const unsigned b = nb(G.N, 256);
+  const bool fast = n->C == 2 || n->C == 4 || n->C == 8 || n->C == 16;
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(n->x0, x0_host, h->N * sizeof(float), cudaMemcpyHostToDevice, h->st));
+  // the same packing as for a solver residual (sigma 1, every plane)
+  k_nn_input<<<b, 256, 0, h->st>>>(n->x0, 0, h->cfg.nz, 1.0f, G, n->x0, fast ? n->xin : nullptr);
+  ++h->launches;
+  if (fast) {
+    int64_t* scratch = nullptr;
+    LBM_CUDA_TRY(h, cudaMalloc(&scratch, h->N * sizeof(int64_t)));
+    cudaMemsetAsync(scratch, 0, h->N * sizeof(int64_t), h->st);
+    if (n->hp_stale) {
+      n->hp.resize(n->np);
+      cudaMemcpyAsync(n->hp.data(), n->p, n->np * sizeof(float), cudaMemcpyDeviceToHost, h->st);
+      cudaStreamSynchronize(h->st);
+      n->hp_stale = false;
+    }
+    cudaError_t e = n->C == 2   ? fast_infer<2>(n, G, 1.0f, scratch, h->st)
+                    : n->C == 4 ? fast_infer<4>(n, G, 1.0f, scratch, h->st)
+                    : n->C == 8 ? fast_infer<8>(n, G, 1.0f, scratch, h->st)
+                                : fast_infer<16>(n, G, 1.0f, scratch, h->st);
+    cudaStreamSynchronize(h->st);
+    cudaFree(scratch);
+    LBM_CUDA_TRY(h, e);
+    h->launches += 2;
+  } else {
+    k_nn_infer1<<<b, 256, 0, h->st>>>(n->x0, n->ph, n->C, G, n->hid16);
+    k_nn_infer2<<<b, 256, 0, h->st>>>(n->hid16, n->ph, n->C, G, 1.0f, n->y);
+    h->launches += 2;
+    LBM_CUDA_TRY(h, cudaGetLastError());
+  }
+  LBM_CUDA_TRY(h, cudaMemcpyAsync(y_host, n->y, h->N * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+  LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return LBM_OK;
+}
+
 lbm_status nn_params(lbm_t* h, float* get, const float* set, int* np) {
   NNet* n = h->nn;
   if (!n) {
@@ -631,6 +814,7 @@ lbm_status nn_params(lbm_t* h, float* get, const float* set, int* np) {
   if (get) LBM_CUDA_TRY(h, cudaMemcpy(get, n->p, n->np * sizeof(float), cudaMemcpyDeviceToHost));
   if (set) {
     LBM_CUDA_TRY(h, cudaMemcpy(n->p, set, n->np * sizeof(float), cudaMemcpyHostToDevice));
+    n->hp_stale = true;
     k_to_half<<<nb(n->np, 256), 256, 0, h->st>>>(n->p, n->ph, n->np);
     LBM_CUDA_TRY(h, cudaGetLastError());
     LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));

@@ -1097,6 +1097,7 @@ lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
     }
   }
   rel0 = rel;
+  note_start_residual(h, rel0);
   int it = 0;
   if (h->cfg.poisson == LBM_POISSON_MG) {
     // Queue the predicted number of cycles (from the initial residual and

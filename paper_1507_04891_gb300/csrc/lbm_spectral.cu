@@ -1165,6 +1165,7 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
     LBM_CUDA_TRY(h, spec_residual(h, 0, true));
     LBM_CUDA_TRY(h, read_slots(h, 1));
     slot_norms(h, 0, &rn, &sn);
+    note_start_residual(h, sn > 0.0 ? rn / sn : 0.0);
     known = true;
     if (!conv_of(rn, sn)) {
       bool applied = false;
@@ -1199,6 +1200,8 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
     LBM_CUDA_TRY(h, spec_residual(h, k, false));
     LBM_CUDA_TRY(h, read_slots(h, k + 1));
     int need = k;
+    slot_norms(h, 0, &rn, &sn);
+    note_start_residual(h, sn > 0.0 ? rn / sn : 0.0);
     for (int i = 0; i <= k; ++i) {
       slot_norms(h, i, &rn, &sn);
       if (conv_of(rn, sn)) {
@@ -1266,6 +1269,8 @@ struct GraphStatus {
   int need[4];         // steps that needed 1, 2, 3, >= 4 applications since the host reset it
   int needf[4];        // the same, counting only steps whose start had the full history
   int full;            // the current step's start had the full history
+  double start_log;    // sum of log10 of the steps' start residuals
+  long long starts;    // steps counted in start_log
 };
 
 // Convergence test (one warp).  first: after the k applications queued
@@ -1303,6 +1308,12 @@ __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, do
   if (first) {
     st->full = !start_terms || *start_terms >= START_FULL_TERMS;
     st->iters = k;
+    // slot 0 holds the residual the first application transformed (the
+    // start), lane 0 read it
+    if (rn2 >= 0.0 && sn2 > 0.0) {
+      st->start_log += 0.5 * log10(fmax(rn2 / sn2, 1e-300));
+      st->starts += 1;
+    }
   } else {
     st->iters += 1;
   }
@@ -1561,6 +1572,8 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
   }
   const long long total0 = hs->total;
   const int fails0 = hs->fails;
+  const double slog0 = hs->start_log;
+  const long long starts0 = hs->starts;
   // Steps are replayed in chunks.  With the start from the solve history k
   // is one.  Otherwise the distribution of the applications the steps
   // needed (accumulated over at least CHUNK steps) sets the number k baked
@@ -1645,6 +1658,15 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     }
   }
   const long long iters = hs->total - total0;
+  if (hs->starts > starts0) {
+    // start residuals of the replayed steps (their geometric mean stands
+    // for the last one)
+    const double dl = hs->start_log - slog0;
+    const long long dn = hs->starts - starts0;
+    h->start_log_sum += dl;
+    h->start_count += dn;
+    h->last_start = pow(10.0, dl / (double)dn);
+  }
   h->t_cnt[1] += iters;
   h->t_cnt[0] += done;
   h->t_cnt[2] += done;

@@ -342,7 +342,7 @@ void start_free(lbm_t* h) {
 }
 
 bool start_enabled(const lbm_t* h) {
-  return h->start.state && !(h->cfg.flags & LBM_FLAG_NO_EXTRAPOLATION) && !nn_active(h);
+  return h->start.state && !(h->cfg.flags & LBM_FLAG_NO_EXTRAPOLATION);
 }
 
 cudaError_t start_apply(lbm_t* h, bool last) {

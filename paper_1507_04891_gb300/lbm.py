@@ -34,7 +34,7 @@ EXPORTED = [
     "lbm_nn_init", "lbm_nn_collect", "lbm_nn_train", "lbm_nn_use", "lbm_nn_params",
     "lbm_nn_loss_grad", "lbm_nn_stats", "lbm_get_moments_noalloc", "lbm_state_len", "lbm_stream", "lbm_last_error",
     "lbm_set_species_dev", "lbm_get_moments_dev", "lbm_plane_fluxes", "lbm_omega_drag_for_schmidt",
-    "lbm_set_drag_matrix",
+    "lbm_set_drag_matrix", "lbm_poisson_stats", "lbm_nn_infer",
 ]
 
 
@@ -144,6 +144,10 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_omega_drag_for_schmidt.restype = D
     lib.lbm_set_drag_matrix.argtypes = [P, P]
     lib.lbm_set_drag_matrix.restype = I
+    lib.lbm_poisson_stats.argtypes = [P, P]
+    lib.lbm_poisson_stats.restype = I
+    lib.lbm_nn_infer.argtypes = [P, P, P]
+    lib.lbm_nn_infer.restype = I
     _lib = lib
     return lib
 
@@ -273,6 +277,16 @@ class Lattice:
         g = np.zeros(n.value, dtype=np.float32) if grad else None
         self._check(self._lib.lbm_nn_loss_grad(self.h, _ptr(x0), ctypes.byref(loss), _ptr(g)))
         return loss.value, g
+
+    def nn_infer(self, x0):
+        """lbm_nn_infer: the solver's FP16 inference pass on x0 (lattice
+        shape); returns y, the correction in units of the residual rms."""
+        x0 = np.ascontiguousarray(x0, dtype=np.float32)
+        if x0.shape != self.shape:
+            raise ValueError("x0 must have the lattice shape")
+        y = np.empty(self.shape, dtype=np.float32)
+        self._check(self._lib.lbm_nn_infer(self.h, _ptr(x0), _ptr(y)))
+        return y
 
     def nn_stats(self):
         out = np.zeros(5)
@@ -407,6 +421,15 @@ class Lattice:
         return {"charge_ms": out[0], "poisson_ms": out[1], "collide_ms": out[2],
                 "charge_launches": int(out[3]), "poisson_iters": int(out[4]),
                 "collide_launches": int(out[5]), "kernel_launches": int(out[6])}
+
+    def poisson_stats(self):
+        """lbm_poisson_stats: iterations, start and end relative residuals of
+        the last solve, and the geometric-mean start residual since
+        set_timing."""
+        out = np.zeros(5)
+        self._check(self._lib.lbm_poisson_stats(self.h, _ptr(out)))
+        return {"iters": int(out[0]), "start_residual": out[1], "final_residual": out[2],
+                "solves": int(out[3]), "start_residual_geomean": 10.0 ** out[4] if out[3] else None}
 
     @property
     def stream(self):

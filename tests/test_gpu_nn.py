@@ -47,18 +47,46 @@ def test_gradient_matches_fp64_finite_differences(walls):
         assert abs(grad[k] - fd) <= 1e-3 * np.abs(grad).max() + 1e-4 * abs(fd), (k, grad[k], fd)
 
 
-def _charged_lattice(n, seed, poisson="mg"):
-    wl = WL.ternary_bulk(shape=(n, n, n), seed=seed, schmidt=1.0)
-    # both arms of the comparison start each solve from the previous potential
-    lat = lbm.Lattice(n, n, n, 3, omega_drag=1.0, bjerrum=0.7, poisson=poisson, poisson_maxit=100,
-                      extrapolate=False)
+@pytest.mark.parametrize("hidden,walls", [(8, False), (8, True), (3, True)])
+def test_inference_matches_fp64_forward(hidden, walls):
+    """The solver's inference pass (FP16 weights and activations, channel
+    pairs for even widths, the generic kernels for odd ones) against the
+    FP64 forward pass of the oracle network, on random parameters and a
+    random normalised residual.  FP16 keeps about three digits: the bound is
+    3% of the largest output, far below what matters for an initial guess
+    whose solve iterates to the same tolerance."""
+    shape = (6, 8, 10)
+    lat = lbm.Lattice(10, 8, 6, 1, bjerrum=0.7, poisson="mg")
+    fluid = np.ones(shape, bool)
+    if walls:
+        solid, sigma = WL.random_solid(shape, seed=13, fraction=0.15)
+        lat.set_walls(solid, sigma)
+        fluid = ~solid
+    lat.nn_init(hidden=hidden, seed=14)
+    g = np.random.Generator(np.random.PCG64(15))
+    params = g.uniform(-0.3, 0.3, size=lat.nn_params().size).astype(np.float32)
+    lat.nn_params(params)
+    x0 = np.where(fluid, g.standard_normal(shape), 0.0).astype(np.float32)
+    y = lat.nn_infer(x0)
+    ref = nn_oracle.forward(params.astype(np.float64), x0.astype(np.float64), fluid, hidden)
+    assert np.all(y[~fluid] == 0.0)
+    assert np.abs(y - ref).max() <= 3e-2 * np.abs(ref).max(), np.abs(y - ref).max()
+    assert np.corrcoef(y[fluid], ref[fluid])[0, 1] > 0.999
+
+
+def _porous_lattice(n, extrapolate=True):
+    wl = WL.porous_spheres(n=n, seed=1238)
+    lat = lbm.Lattice(n, n, n, 3, omega_drag=1.0, bjerrum=0.7, poisson="mg", poisson_maxit=200,
+                      extrapolate=extrapolate)
+    lat.set_walls(wl.solid, wl.sigma)
     for s in range(3):
-        lat.set_species(s, 1.0, wl.valence[s], wl.n0[s])
+        lat.set_species(s, 1.0, wl.valence[s], np.where(wl.solid, 1.0, wl.n0[s]))
     return lat
 
 
 def test_training_on_solver_residuals_lowers_the_loss():
-    lat = _charged_lattice(24, 41)
+    lat = _porous_lattice(32)
+    lat.step(4)
     lat.nn_init(hidden=8, seed=5)
     lat.nn_collect(16)
     lat.step(16)
@@ -68,35 +96,36 @@ def test_training_on_solver_residuals_lowers_the_loss():
     assert losses[-1] < 0.8 * losses[0]
 
 
-def test_learned_guess_cuts_multigrid_cycles_on_held_out_steps():
-    """Train on the first steps of a run, then compare the held-out steps
-    from the same state with and without the guess: every solve still ends
-    at the 1e-8 residual, the guess lowers the initial residual and the
-    number of V-cycles."""
-    base = _charged_lattice(32, 42)
-    base.nn_init(hidden=8, seed=7)
-    base.nn_collect(24)
-    base.step(24)
-    base.nn_train(epochs=60, lr=5e-3)
+def test_learned_guess_gains_over_the_history_start():
+    """The network, trained on the residuals the history start leaves (16
+    steps of a training run), then used on the same trajectory from the
+    same initial state as a run without it: every solve still ends at 1e-8;
+    the network lowers the start residual by more than a third and takes
+    strictly fewer V-cycles in total over the held-out steps."""
+    base = _porous_lattice(64)
+    base.step(4)
+    base.nn_init(hidden=8, seed=3)
+    base.nn_collect(16)
+    base.step(16)
+    base.nn_train(epochs=40, lr=5e-3)
     params = base.nn_params()
-    state, step = base.get_state()
-    psi = base.get_potential()
-    cycles = {}
+    base.destroy()
+    cycles, starts = {}, {}
     for use in (False, True):
-        lat = _charged_lattice(32, 42)
-        lat.set_state(state, step)
-        # warm start from the same potential
-        rho = sum(z * lat.get_moments(s)[0] for s, z in ((1, 1.0), (2, -1.0)))
-        lat.solve_poisson(rho, psi, tol=1e-12)
+        lat = _porous_lattice(64)
         if use:
-            lat.nn_init(hidden=8, seed=7)
+            lat.nn_init(hidden=8, seed=3)
             lat.nn_params(params)
             lat.nn_use(True)
+        lat.step(20)
         lat.set_timing(True)
-        lat.step(12)
+        lat.step(32)
         cycles[use] = lat.get_timing()["poisson_iters"]
+        starts[use] = lat.poisson_stats()["start_residual_geomean"]
         assert lat.diagnostics()["poisson_residual"] <= 1e-8
         if use:
             st = lat.nn_stats()
-            assert st["tried"] == 12 and st["kept"] >= 6 and st["mean_ratio"] < 0.9
-    assert cycles[True] <= cycles[False]
+            assert st["tried"] >= 40 and st["kept"] >= 0.8 * st["tried"] and st["mean_ratio"] < 0.66
+        lat.destroy()
+    assert starts[True] < 0.66 * starts[False], starts
+    assert cycles[True] < cycles[False], cycles
