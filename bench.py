@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--poisson", default="fft", choices=["mg", "sor", "fft"])
     ap.add_argument("--no-alt", action="store_true", help="skip the multigrid comparison run")
-    ap.add_argument("--only", choices=["batched", "learned", "slit", "conductivity", "slit_transport"], default=None,
+    ap.add_argument("--only", choices=["batched", "learned", "slit", "conductivity", "slit_transport",
+                                       "multigrid"], default=None,
                     help="run one extra measurement alone and print it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-slit and learned-guess measurements")
@@ -618,6 +619,61 @@ def run_porous(lbm, WL, steps=20, warm=5, local=0, n=256, params=None):
     return out
 
 
+# Fine-box bytes of one V(2,2) cycle per fine cell, in units of N (cells):
+# pre-smoothing 4 half-sweeps of 6.5 (other colour 2 + own residual 2 + own
+# mask 0.5 + own correction 2; the first one writes zeros to the other colour
+# instead of reading it), restriction 9.5 (e 4, r 4, mask 1, coarse 0.5),
+# prolongation 10 (e read and write 8, mask 1, coarse 1), post-smoothing 26
+# plus the potential update of the last half-sweep 16.5 (psi in 8, psi out 8,
+# mask 0.5), residual 25 (psi 8, source 8, component label 4, mask 1,
+# residual 4).
+MG_BYTES_PER_CELL = 26 + 9.5 + 10 + 26 + 16.5 + 25
+
+
+def run_multigrid(lbm, WL, n=256, steps=20, warm=5, local=0):
+    """Standalone measure of the multigrid V-cycle on the porous box (n^3,
+    seeded spheres, charged walls) with one weakly charged species (the
+    solvent of the porous workload with valence 0.01, so that the lattice
+    itself stays small and the run stable): each step solves from the
+    previous potential to 1e-8.  Reports the solve time per V-cycle and the
+    fine-box bytes of a cycle over that time (every coarse level's time
+    included)."""
+    import torch
+    wl = WL.porous_spheres(n=n, seed=1238)
+    lat = lbm.Lattice(n, n, n, 1, bjerrum=wl.bjerrum, poisson="mg", poisson_tol=1e-8,
+                      poisson_maxit=200, device=local, extrapolate=False)
+    lat.set_walls(wl.solid, wl.sigma)
+    lat.set_species(0, 1.0, 0.01, np.where(wl.solid, 1.0, wl.n0[0]))
+    lat.step(warm)
+    lat.synchronize()
+    lat.set_timing(True)
+    stream = torch.cuda.ExternalStream(lat.stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    lat.synchronize()
+    tm = lat.get_timing()
+    lat.set_timing(False)
+    d = lat.diagnostics()
+    lat.destroy()
+    cycles = tm["poisson_iters"]
+    ms_cycle = tm["poisson_ms"] / max(1, cycles)
+    nb = wl.sites  # fine cells (the box is periodic in z: no planes trimmed)
+    gbs = MG_BYTES_PER_CELL * nb / (ms_cycle * 1e-3) / 1e9
+    peak, src = measured_peaks()
+    return {"workload": "porous_%d^3, one species of valence 0.01, charged walls, multigrid from "
+                        "the previous potential to 1e-8" % n,
+            "steps": steps, "warmup": warm, "vcycles_per_step": cycles / steps,
+            "poisson_ms_per_step": tm["poisson_ms"] / steps, "ms_per_vcycle": ms_cycle,
+            "step_ms": e0.elapsed_time(e1) / steps,
+            "fine_bytes_per_vcycle": MG_BYTES_PER_CELL * nb,
+            "fine_bytes_per_cell": MG_BYTES_PER_CELL,
+            "achieved_gbs": gbs, "peak_gbs": peak, "peak_source": src, "frac": gbs / peak,
+            "poisson_residual_last": d["poisson_residual"]}
+
+
 def run_conductivity(lbm, WL, n=64, local=0):
     """Bulk conductivity (Sec. 4, current against D; Eq. Drude): a uniform
     neutral ternary electrolyte (ion fractions 0.01) in a field 1e-3 along
@@ -1029,6 +1085,9 @@ def main():
             res = run_slit_transport(lbm, WL)
         elif args.only == "conductivity":
             res = run_conductivity(lbm, WL, n=args.n if args.n != 128 else 64)
+        elif args.only == "multigrid":
+            res = run_multigrid(lbm, WL, n=args.n if args.n != 128 else 256,
+                                steps=min(max(1, args.steps), 50), warm=max(1, args.warmup))
         else:
             res = run_learned(lbm, WL)
             res["porous_256"] = run_porous(lbm, WL, params=res.pop("params"))

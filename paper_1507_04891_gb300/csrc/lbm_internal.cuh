@@ -133,6 +133,11 @@ struct Poisson {
   int64_t* src = nullptr; // 4 pi l_B (rho_e + w) per lattice node (fixed point), no mean removed
   double* dsum = nullptr; // [0] sum of src over fluid, [1 + 2k] sum r^2, [2 + 2k] sum s^2 (fixed-point units), k < NSLOT
   double* hsum = nullptr; // pinned mirror of dsum
+  uint8_t* face = nullptr; // face mask of the fine box (colour-split), walls only
+  float* nacc = nullptr;   // norm slots of the multigrid residual (|r|^2, then |s|^2)
+  float* hacc = nullptr;   // pinned mirror of nacc
+  double snorm = 0.0;      // ||s - <s>|| of the current solve (fixed-point units)
+  bool snorm_pending = false;  // the queued residual also carries the source norm
   long long* part = nullptr; // per-CTA partial sums of the charge kernel
   // connected fluid components (face neighbours): label per lattice node
   // (0 = largest component), allocated only when there is more than one
@@ -362,9 +367,10 @@ lbm_status nn_train(lbm_t* h, int epochs, double lr, double* losses);
 lbm_status nn_loss_grad_host(lbm_t* h, const float* x0, double* loss, float* grad);
 lbm_status nn_infer_host(lbm_t* h, const float* x0, float* y);
 lbm_status nn_params(lbm_t* h, float* get, const float* set, int* np);
-// Solver hooks: given the initial FP32 residual (planes [zlo, zlo+nzb)),
-// stores it for training and/or applies the learned correction to psi.
-lbm_status nn_before_solve(lbm_t* h, const float* r, int zlo, int nzb, double rms,
+// Solver hooks: given the initial FP32 residual (planes [zlo, zlo+nzb);
+// natural order when hx = 0, else colour-split with hx cells of a colour per
+// x row), stores it for training and/or applies the learned correction.
+lbm_status nn_before_solve(lbm_t* h, const float* r, int zlo, int nzb, int hx, double rms,
                            bool* applied, float** dpsi);
 lbm_status nn_revert(lbm_t* h, const float* dpsi);
 void nn_record(lbm_t* h, double ratio);

@@ -122,18 +122,30 @@ __device__ float apply_A(const float* v, const Geo& G, int64_t i, int x, int y, 
 }
 
 // x0 = r / sigma (fluid), 0 at wall nodes.  The residual of a trimmed
-// multigrid box covers planes [zlo, zlo + nzb).
+// multigrid box covers planes [zlo, zlo + nzb); with hx > 0 it is stored
+// colour-split: cell (x, y, zb) of colour q = (x + y + zb) mod 2 at
+// q H + (zb ny + y) hx + floor(x / 2), H = nzb ny hx.
 // When xin is given, the same input packed for inference: (x0, fluid mask)
 // as one FP16 pair per cell.
-__global__ void k_nn_input(const float* __restrict__ r, int zlo, int nzb, float inv_sigma, Geo G,
-                           float* __restrict__ x0, __half2* __restrict__ xin) {
+__global__ void k_nn_input(const float* __restrict__ r, int zlo, int nzb, int hx, float inv_sigma,
+                           Geo G, float* __restrict__ x0, __half2* __restrict__ xin) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= G.N) return;
   const int64_t nxy = (int64_t)G.nx * G.ny;
   const int z = (int)(i / nxy);
   const bool fl = fluid_at(G, i);
   float v = 0.f;
-  if (z >= zlo && z < zlo + nzb && fl) v = r[i - (int64_t)zlo * nxy] * inv_sigma;
+  if (z >= zlo && z < zlo + nzb && fl) {
+    int64_t j = i - (int64_t)zlo * nxy;
+    if (hx > 0) {
+      const int zb = z - zlo;
+      const int64_t rem = i - (int64_t)z * nxy;
+      const int y = (int)(rem / G.nx), x = (int)(rem - (int64_t)y * G.nx);
+      const int64_t H = (int64_t)nzb * G.ny * hx;
+      j = (((x + y + zb) & 1) ? H : 0) + ((int64_t)zb * G.ny + y) * hx + (x >> 1);
+    }
+    v = r[j] * inv_sigma;
+  }
   x0[i] = v;
   if (xin) xin[i] = __floats2half2_rn(v, fl ? 1.f : 0.f);
 }
@@ -634,11 +646,11 @@ lbm_status nn_collect(lbm_t* h, int capacity) {
 }
 
 // Called by the solver with the initial residual (FP32, box-indexed: planes
-// [zlo, zlo + nzb)) and its rms.  Stores it when collecting; applies the
+// [zlo, zlo + nzb); colour-split when hx > 0) and its rms.  Stores it when collecting; applies the
 // learned correction when in use.  Returns the relative change of the
 // residual norm the caller must verify (the caller reverts on failure).
-lbm_status nn_before_solve(lbm_t* h, const float* r, int zlo, int nzb, double rms, bool* applied,
-                           float** dpsi_out) {
+lbm_status nn_before_solve(lbm_t* h, const float* r, int zlo, int nzb, int hx, double rms,
+                           bool* applied, float** dpsi_out) {
   *applied = false;
   NNet* n = h->nn;
   if (!n || rms <= 0.0 || !isfinite(rms)) return LBM_OK;
@@ -646,7 +658,7 @@ lbm_status nn_before_solve(lbm_t* h, const float* r, int zlo, int nzb, double rm
   const unsigned b = nb(G.N, 256);
   const bool fast = n->C == 2 || n->C == 4 || n->C == 8 || n->C == 16;
   if (n->collect || n->use) {
-    k_nn_input<<<b, 256, 0, h->st>>>(r, zlo, nzb, (float)(1.0 / rms), G, n->x0,
+    k_nn_input<<<b, 256, 0, h->st>>>(r, zlo, nzb, hx, (float)(1.0 / rms), G, n->x0,
                                       n->use && fast ? n->xin : nullptr);
     ++h->launches;
   }
@@ -773,7 +785,7 @@ lbm_status nn_infer_host(lbm_t* h, const float* x0_host, float* y_host) {
   const bool fast = n->C == 2 || n->C == 4 || n->C == 8 || n->C == 16;
   LBM_CUDA_TRY(h, cudaMemcpyAsync(n->x0, x0_host, h->N * sizeof(float), cudaMemcpyHostToDevice, h->st));
   // the same packing as for a solver residual (sigma 1, every plane)
-  k_nn_input<<<b, 256, 0, h->st>>>(n->x0, 0, h->cfg.nz, 1.0f, G, n->x0, fast ? n->xin : nullptr);
+  k_nn_input<<<b, 256, 0, h->st>>>(n->x0, 0, h->cfg.nz, 0, 1.0f, G, n->x0, fast ? n->xin : nullptr);
   ++h->launches;
   if (fast) {
     int64_t* scratch = nullptr;

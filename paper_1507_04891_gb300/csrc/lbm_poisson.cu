@@ -28,20 +28,33 @@
 namespace lbm_gb300 {
 namespace {
 
+// Fine box of the multigrid: the lattice planes [zlo, zlo + nzb).  Its FP32
+// correction e and residual r are stored colour-split: cell (x, y, z) of
+// colour q = (x + y + z) mod 2 sits at q H + (z ny + y) hx + floor(x / 2),
+// hx = ceil(nx / 2), H = nzb ny hx.  A red-black half-sweep then reads the
+// other colour's array and whole sectors of its own instead of every line of
+// both colours interleaved.  The one-byte face mask uses the same layout.
 struct Box {
   int nx, ny, nzb, zlo, perz;
-  int64_t nxy;
+  int hx;        // cells of one colour per x row (with one pad cell if nx is odd)
+  uint32_t H;    // cells of one colour array
+  int64_t nxy;   // lattice plane
 };
+
+// Face mask of a fine-box cell: bit f set when face f (0 +x, 1 -x, 2 +y,
+// 3 -y, 4 +z, 5 -z) joins two fluid cells; FACE_SOLID for a wall cell.
+constexpr uint32_t FACE_SOLID = 0x80u;
+constexpr uint32_t FACES_OPEN = 0x3fu;
 
 // open-face bits from the link word: bit 2 of the link word = +x neighbour
 // is a wall node, 1 = -x, 4 = +y, 3 = -y, 6 = +z, 5 = -z.
 __device__ __forceinline__ bool open_face(uint32_t lk, int face) {
-  // face: 0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z
   const int bit = (face & 1) ? face : face + 2;  // 0->2, 1->1, 2->4, 3->3, 4->6, 5->5
   return !((lk >> bit) & 1u);
 }
 
-// box-cell neighbour offsets (periodic x, y; z periodic only if perz)
+// box-cell neighbour offsets in natural order (periodic x, y; z periodic
+// only if perz, else the cell itself at the ends, where the face is closed)
 __device__ __forceinline__ void box_nbr(const Box& b, int x, int y, int z,
                                         int (&d)[6]) {
   d[0] = (x == b.nx - 1) ? -(b.nx - 1) : 1;
@@ -66,52 +79,106 @@ __device__ __forceinline__ void box_xyz(uint32_t c, const Box& b, int& x,
   y = (int)(t - (uint32_t)z * (uint32_t)b.ny);
 }
 
+// colour-split index of box cell (x, y, z)
+__device__ __forceinline__ uint32_t sp_idx(const Box& b, int x, int y, int z) {
+  return (((x + y + z) & 1) ? b.H : 0u) + ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.hx +
+         (uint32_t)(x >> 1);
+}
+
+// colour-split indices of the six face neighbours (order of the mask bits)
+__device__ __forceinline__ void sp_nbrs(const Box& b, int x, int y, int z, uint32_t (&j)[6]) {
+  const int xp = (x == b.nx - 1) ? 0 : x + 1, xm = (x == 0) ? b.nx - 1 : x - 1;
+  const int yp = (y == b.ny - 1) ? 0 : y + 1, ym = (y == 0) ? b.ny - 1 : y - 1;
+  int zp, zm;
+  if (b.perz) {
+    zp = (z == b.nzb - 1) ? 0 : z + 1;
+    zm = (z == 0) ? b.nzb - 1 : z - 1;
+  } else {
+    zp = (z == b.nzb - 1) ? z : z + 1;
+    zm = (z == 0) ? z : z - 1;
+  }
+  j[0] = sp_idx(b, xp, y, z);
+  j[1] = sp_idx(b, xm, y, z);
+  j[2] = sp_idx(b, x, yp, z);
+  j[3] = sp_idx(b, x, ym, z);
+  j[4] = sp_idx(b, x, y, zp);
+  j[5] = sp_idx(b, x, y, zm);
+}
+
 __device__ __forceinline__ int64_t fx_of(float e) {
   return f32_to_i64_rn(e * PSI_SCALE_F);
 }
 
-// Residual on the fine box, r = s - <s> - A psi, exact in 64-bit integers.
-// Writes r (FP32) to rhs and block sums of r^2 and (s - <s>)^2 (fixed-point
-// units) to dsum[1], dsum[2].
-template <bool WALLS>
+// Face mask of the fine box from the lattice link words.
+__global__ void __launch_bounds__(256) k_face_mask(const uint32_t* __restrict__ links, Box b,
+                                                   uint32_t nbox, uint8_t* __restrict__ mask) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nbox) return;
+  int x, y, z;
+  box_xyz(c, b, x, y, z);
+  const uint32_t lk = links[(int64_t)c + (int64_t)b.zlo * b.nxy];
+  uint32_t m = 0;
+  if (lk & LINK_SOLID) {
+    m = FACE_SOLID;
+  } else {
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+      if (open_face(lk, f)) m |= 1u << f;
+  }
+  mask[sp_idx(b, x, y, z)] = (uint8_t)m;
+}
+
+// Norm partials of the fine residual: CTA k adds its sums into slot
+// k mod MG_NACC (FP32 atomics spread over addresses; FP64 atomics are slow
+// on this GPU).  Values are scaled by 2^-20 before squaring so that sums of
+// squared fixed-point values stay inside the FP32 range; the reader adds the
+// slots in FP64 and scales by 2^40.  The norms only decide convergence, so
+// FP32 partials are ample.
+constexpr int MG_NACC = 64;
+constexpr float MG_NORM_PRE = 1.0f / 1048576.0f;  // 2^-20
+
+// Residual on the fine box, r = s - <s> - A psi, exact in 64-bit integers;
+// one cell per thread.  Writes r (FP32, colour-split) and adds |r|^2 and,
+// with SNORM (the first residual of a solve: the source does not change
+// during one), |s - <s>|^2 (fixed-point units, scaled) to the norm slots.
+template <bool WALLS, bool SNORM>
 __global__ void __launch_bounds__(256) k_res0(
     const int64_t* __restrict__ psi, const int64_t* __restrict__ src,
-    const uint32_t* __restrict__ links, float* __restrict__ r, double* dsum,
-    Box b, int64_t nbox, double inv_nfluid, const int* __restrict__ label,
-    const long long* __restrict__ comp_mean) {
+    const uint8_t* __restrict__ mask, float* __restrict__ r, const double* __restrict__ dsum,
+    float* __restrict__ acc, Box b, uint32_t nbox, double inv_nfluid,
+    const int* __restrict__ label, const long long* __restrict__ comp_mean) {
   __shared__ long long s_mean;
   __shared__ float red_r[8], red_s[8];
   if (threadIdx.x == 0) s_mean = llrint(dsum[0] * inv_nfluid);
   __syncthreads();
   float rr = 0.f, ss = 0.f;
-  // grid-stride loop over a grid capped at a few CTAs per SM: one pair of
-  // FP64 atomics per CTA instead of per 256 cells
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < (uint32_t)nbox;
-       c += gridDim.x * blockDim.x) {
-    const int64_t i = (int64_t)c + (int64_t)b.zlo * b.nxy;  // lattice node
-    uint32_t lk = 0;
-    if (WALLS) lk = links[i];
-    if (WALLS && (lk & LINK_SOLID)) {
-      r[c] = 0.f;
-      continue;
-    }
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nbox) {
     int x, y, z;
     box_xyz(c, b, x, y, z);
-    int d[6];
-    box_nbr(b, x, y, z, d);
-    const int64_t pc = psi[i];
-    int64_t Ap = 0;
+    const uint32_t q = sp_idx(b, x, y, z);
+    const uint32_t m = WALLS ? (uint32_t)mask[q] : FACES_OPEN;
+    if (m & FACE_SOLID) {
+      r[q] = 0.f;
+    } else {
+      const int64_t i = (int64_t)c + (int64_t)b.zlo * b.nxy;  // lattice node
+      int d[6];
+      box_nbr(b, x, y, z, d);
+      const int64_t pc = psi[i];
+      int64_t Ap = 0;
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-      if (WALLS && !open_face(lk, f)) continue;
-      Ap += pc - psi[i + d[f]];
+      for (int f = 0; f < 6; ++f)
+        if ((m >> f) & 1u) Ap += pc - psi[i + d[f]];
+      const int64_t sfx = src[i] - (label ? comp_mean[label[i]] : (int64_t)s_mean);
+      const float rf = i64_to_f32(sfx - Ap);
+      r[q] = rf * PSI_INV_SCALE_F;
+      const float rs = rf * MG_NORM_PRE;
+      rr = rs * rs;
+      if (SNORM) {
+        const float sf = i64_to_f32(sfx) * MG_NORM_PRE;
+        ss = sf * sf;
+      }
     }
-    const int64_t sfx = src[i] - (label ? comp_mean[label[i]] : (int64_t)s_mean);
-    const float rf = i64_to_f32(sfx - Ap);
-    r[c] = rf * PSI_INV_SCALE_F;
-    rr += rf * rf;
-    const float sf = i64_to_f32(sfx);
-    ss += sf * sf;
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -124,19 +191,89 @@ __global__ void __launch_bounds__(256) k_res0(
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tr = 0.0, ts = 0.0;
+    float tr = 0.f, ts = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      tr += (double)red_r[w];
-      ts += (double)red_s[w];
+      tr += red_r[w];
+      ts += red_s[w];
     }
-    atomicAdd(dsum + 1, tr);
-    atomicAdd(dsum + 2, ts);
+    const int k = blockIdx.x & (MG_NACC - 1);
+    atomicAdd(acc + k, tr);
+    if (SNORM) atomicAdd(acc + MG_NACC + k, ts);
   }
 }
 
-// Cell of colour `color` handled by thread t when the x extent is even:
-// every x row holds nx/2 cells of each colour.  With an odd x extent every
-// thread takes one cell and skips the other colour.
+// Red-black Gauss-Seidel half-sweep on the fine box for A e = r (FP32), one
+// cell of colour `color` per thread (colour index t).  MODE 1, the first
+// half-sweep of a cycle: starts from e = 0, so no neighbour is read and the
+// thread clears the other colour's cell at the same index.  MODE 2, the last
+// half-sweep of a cycle: also writes the corrected potential
+// psi_out = psi_in + round(e) for the x pair (2k, 2k + 1) its cell shares
+// with the other colour's cell t, whose sweep has finished; wall cells keep
+// psi_in.
+template <bool WALLS, int MODE>
+__global__ void __launch_bounds__(256) k_smooth0(
+    float* __restrict__ e, const float* __restrict__ r, const uint8_t* __restrict__ mask,
+    Box b, int color, const int64_t* __restrict__ psi_in, int64_t* __restrict__ psi_out) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b.H) return;
+  const uint32_t row = t / (uint32_t)b.hx;
+  const uint32_t k = t - row * (uint32_t)b.hx;
+  const int z = (int)(row / (uint32_t)b.ny);
+  const int y = (int)(row - (uint32_t)z * (uint32_t)b.ny);
+  const int x = 2 * (int)k + ((y + z + color) & 1);
+  const uint32_t self = (color ? b.H : 0u) + t;
+  const uint32_t other = (color ? 0u : b.H) + t;
+  if (MODE == 1) e[other] = 0.f;
+  float ev = 0.f;
+  if (x < b.nx) {
+    const uint32_t m = WALLS ? (uint32_t)mask[self] : FACES_OPEN;
+    if (!(m & FACE_SOLID)) {
+      float sum = r[self];
+      if (MODE != 1) {
+        uint32_t j[6];
+        sp_nbrs(b, x, y, z, j);
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+          if ((m >> f) & 1u) sum += e[j[f]];
+      }
+      const int cnt = __popc(m & FACES_OPEN);
+      if (cnt > 0) {
+        ev = __fdividef(sum, (float)cnt);
+        e[self] = ev;
+      } else if (MODE == 1) {
+        e[self] = 0.f;
+      } else {
+        ev = e[self];
+      }
+    }
+  }
+  if (MODE == 2) {
+    const int xo = x ^ 1;  // the other colour's cell of the pair
+    float eo = 0.f;
+    if (xo < b.nx) {
+      const uint32_t mo = WALLS ? (uint32_t)mask[other] : FACES_OPEN;
+      if (!(mo & FACE_SOLID)) eo = e[other];
+    }
+    const int x0 = 2 * (int)k;
+    const float e0 = (x == x0) ? ev : eo, e1 = (x == x0) ? eo : ev;
+    const int64_t base = ((int64_t)(z + b.zlo) * b.ny + y) * b.nx + x0;
+    if ((b.nx & 1) == 0) {
+      const longlong2 pin = *reinterpret_cast<const longlong2*>(psi_in + base);
+      longlong2 po;
+      po.x = pin.x + fx_of(e0);
+      po.y = pin.y + fx_of(e1);
+      *reinterpret_cast<longlong2*>(psi_out + base) = po;
+    } else {
+      if (x0 < b.nx) psi_out[base] = psi_in[base] + fx_of(e0);
+      if (x0 + 1 < b.nx) psi_out[base + 1] = psi_in[base + 1] + fx_of(e1);
+    }
+  }
+}
+
+// Red-black cell of colour `color` handled by thread t on a coarse level in
+// natural order: with an even x extent every x row holds nx/2 cells of each
+// colour; with an odd one every thread takes one cell and skips the other
+// colour.
 __device__ __forceinline__ bool rb_cell(uint32_t t, int nx, int ny, int64_t n,
                                         int color, bool compact, uint32_t& c,
                                         int& x, int& y, int& z) {
@@ -160,40 +297,384 @@ __device__ __forceinline__ bool rb_cell(uint32_t t, int nx, int ny, int64_t n,
   return ((x + y + z) & 1) == color;
 }
 
-// Red-black Gauss-Seidel on the fine box for A e = r (FP32).  With APPLY
-// (the last sweep of a V-cycle) each cell also writes its final correction
-// into the other potential buffer: psi_out = psi_in + round(e).
-template <bool WALLS, bool APPLY>
-__global__ void __launch_bounds__(256) k_smooth0(
-    float* __restrict__ e, const float* __restrict__ r,
-    const uint32_t* __restrict__ links, Box b, int64_t nbox, int color,
-    int compact, const int64_t* __restrict__ psi_in, int64_t* __restrict__ psi_out) {
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t c;
-  int x, y, z;
-  if (!rb_cell(t, b.nx, b.ny, nbox, color, compact, c, x, y, z)) return;
-  const int64_t i = (int64_t)c + (int64_t)b.zlo * b.nxy;
-  uint32_t lk = 0;
-  if (WALLS) {
-    lk = links[i];
-    if (lk & LINK_SOLID) return;
+// ---------------------------------------------------------------------------
+// z-marching fine-box kernels.  Used when the red-black ordering is a true
+// two-colouring (nx, ny even; nzb even or z not periodic): every face
+// neighbour of a cell then has the other colour, and the other colour's
+// entry at the same pair index k in a neighbouring row or plane is the
+// cell's own y or z neighbour.  A thread owns the x pair (2k, 2k + 1) of row
+// y and walks a run of zc planes, keeping the column below, here and above
+// in registers; 2-D thread blocks over (k, y) need no integer division.
+// ---------------------------------------------------------------------------
+
+// Half-sweep of colour `color` (MODE as k_smooth0).  The planes are taken
+// ZM_BATCH at a time: every load of a batch is issued before the first is
+// used (the mask only selects among loaded values), so a thread keeps
+// several DRAM requests in flight instead of waiting on the mask first.
+constexpr int ZM_BATCH = 4;
+
+template <bool WALLS, int MODE>
+__global__ void __launch_bounds__(256) k_smooth0_zm(
+    float* __restrict__ e, const float* __restrict__ r, const uint8_t* __restrict__ mask,
+    Box b, int color, int zc, const int64_t* __restrict__ psi_in, int64_t* __restrict__ psi_out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (k >= b.hx || y >= b.ny) return;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, b.nzb);
+  const uint32_t own = color ? b.H : 0u, oth = color ? 0u : b.H;
+  float* __restrict__ eo = e + oth;
+  float* __restrict__ ec = e + own;
+  const float* __restrict__ rc = r + own;
+  const uint32_t plane = (uint32_t)b.ny * (uint32_t)b.hx;
+  const int yp = (y == b.ny - 1) ? 0 : y + 1, ym = (y == 0) ? b.ny - 1 : y - 1;
+  const int kp = (k == b.hx - 1) ? 0 : k + 1, km = (k == 0) ? b.hx - 1 : k - 1;
+  const uint32_t oc = (uint32_t)y * b.hx + k;
+  const uint32_t oyp = (uint32_t)yp * b.hx + k, oym = (uint32_t)ym * b.hx + k;
+  const uint32_t oxp = (uint32_t)y * b.hx + kp, oxm = (uint32_t)y * b.hx + km;
+  // other colour of this pair column: plane below, here (rolling)
+  float ob = 0.f, oh = 0.f;
+  if (MODE != 1) {
+    const int zb = (z0 > 0) ? z0 - 1 : (b.perz ? b.nzb - 1 : 0);
+    ob = eo[(uint32_t)zb * plane + oc];
+    oh = eo[(uint32_t)z0 * plane + oc];
   }
-  int d[6];
-  box_nbr(b, x, y, z, d);
-  float sum = r[c];
-  int cnt = 0;
+  for (int zs = z0; zs < z1; zs += ZM_BATCH) {
+    float OA[ZM_BATCH], RC[ZM_BATCH], EX[ZM_BATCH], EYP[ZM_BATCH], EYM[ZM_BATCH];
+    uint32_t M[ZM_BATCH], MO[ZM_BATCH];
+    longlong2 PIN[ZM_BATCH];
 #pragma unroll
-  for (int f = 0; f < 6; ++f) {
-    if (WALLS && !open_face(lk, f)) continue;
-    sum += e[(int64_t)c + d[f]];
-    ++cnt;
+    for (int u = 0; u < ZM_BATCH; ++u) {
+      const int z = min(zs + u, z1 - 1);  // past the run: a repeat, unused
+      const uint32_t pz = (uint32_t)z * plane;
+      RC[u] = rc[pz + oc];
+      M[u] = WALLS ? (uint32_t)mask[own + pz + oc] : FACES_OPEN;
+      if (MODE != 1) {
+        const int za = (z < b.nzb - 1) ? z + 1 : (b.perz ? 0 : z);
+        OA[u] = eo[(uint32_t)za * plane + oc];
+        const int p = (y + z + color) & 1;
+        EX[u] = eo[pz + (p ? oxp : oxm)];
+        EYP[u] = eo[pz + oyp];
+        EYM[u] = eo[pz + oym];
+      }
+      if (MODE == 2) {
+        MO[u] = WALLS ? (uint32_t)mask[oth + pz + oc] : FACES_OPEN;
+        PIN[u] = *reinterpret_cast<const longlong2*>(
+            psi_in + ((int64_t)(z + b.zlo) * b.ny + y) * b.nx + 2 * k);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < ZM_BATCH; ++u) {
+      const int z = zs + u;
+      if (z >= z1) break;
+      const uint32_t pz = (uint32_t)z * plane;
+      if (MODE == 1) eo[pz + oc] = 0.f;
+      const int p = (y + z + color) & 1;  // own cell at x = 2k + p
+      const uint32_t m = M[u];
+      float ev = 0.f;
+      if (!(m & FACE_SOLID)) {
+        float sum = RC[u];
+        if (MODE != 1) {
+          // the x neighbour outside the pair: 2k + 2 (pair k + 1) when the
+          // own cell is 2k + 1, else 2k - 1 (pair k - 1)
+          const float exp1 = p ? EX[u] : oh, exm1 = p ? oh : EX[u];
+          if (m & 1u) sum += exp1;
+          if (m & 2u) sum += exm1;
+          if (m & 4u) sum += EYP[u];
+          if (m & 8u) sum += EYM[u];
+          if (m & 16u) sum += OA[u];
+          if (m & 32u) sum += ob;
+        }
+        const int cnt = __popc(m & FACES_OPEN);
+        if (cnt > 0) {
+          ev = __fdividef(sum, (float)cnt);
+          ec[pz + oc] = ev;
+        } else if (MODE == 1) {
+          ec[pz + oc] = 0.f;
+        } else {
+          ev = ec[pz + oc];
+        }
+      }
+      if (MODE == 2) {
+        // pair update: the other colour's cell (x ^ 1) has its final value oh
+        const float eo_v = (MO[u] & FACE_SOLID) ? 0.f : oh;
+        const float e0 = p ? eo_v : ev, e1 = p ? ev : eo_v;
+        longlong2 po;
+        po.x = PIN[u].x + fx_of(e0);
+        po.y = PIN[u].y + fx_of(e1);
+        *reinterpret_cast<longlong2*>(psi_out + ((int64_t)(z + b.zlo) * b.ny + y) * b.nx + 2 * k) = po;
+      }
+      if (MODE != 1) {
+        ob = oh;
+        oh = OA[u];
+      }
+    }
   }
-  float ev = e[c];
-  if (cnt > 0) {
-    ev = sum / (float)cnt;
-    e[c] = ev;
+}
+
+// Half-sweep (MODE as k_smooth0) with two x pairs per thread: cells
+// 4j .. 4j + 3 of row y (pairs 2j and 2j + 1), colour arrays read as float2.
+// Needs nx a multiple of 4.  Batches of planes as k_smooth0_zm.  Wall cells
+// get e = 0 written (their correction is never read, and stays 0).
+template <bool WALLS, int MODE>
+__global__ void __launch_bounds__(256) k_smooth0_zq(
+    float* __restrict__ e, const float* __restrict__ r, const uint8_t* __restrict__ mask,
+    Box b, int color, int zc, const int64_t* __restrict__ psi_in, int64_t* __restrict__ psi_out) {
+  constexpr int NB = (MODE == 2) ? 2 : ZM_BATCH;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (j >= (b.hx >> 1) || y >= b.ny) return;
+  const int k0 = 2 * j;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, b.nzb);
+  const uint32_t own = color ? b.H : 0u, oth = color ? 0u : b.H;
+  float* __restrict__ eo = e + oth;
+  float* __restrict__ ec = e + own;
+  const float* __restrict__ rc = r + own;
+  const uint32_t plane = (uint32_t)b.ny * (uint32_t)b.hx;
+  const int yp = (y == b.ny - 1) ? 0 : y + 1, ym = (y == 0) ? b.ny - 1 : y - 1;
+  const int kl = (k0 == 0) ? b.hx - 1 : k0 - 1;       // pair left of the two
+  const int kr = (k0 + 2 == b.hx) ? 0 : k0 + 2;        // pair right of the two
+  const uint32_t oc = (uint32_t)y * b.hx + k0;
+  const uint32_t oyp = (uint32_t)yp * b.hx + k0, oym = (uint32_t)ym * b.hx + k0;
+  const uint32_t oxl = (uint32_t)y * b.hx + kl, oxr = (uint32_t)y * b.hx + kr;
+  auto ld2 = [](const float* p) { return *reinterpret_cast<const float2*>(p); };
+  float2 ob = make_float2(0.f, 0.f), oh = make_float2(0.f, 0.f);
+  if (MODE != 1) {
+    const int zb = (z0 > 0) ? z0 - 1 : (b.perz ? b.nzb - 1 : 0);
+    ob = ld2(eo + (uint32_t)zb * plane + oc);
+    oh = ld2(eo + (uint32_t)z0 * plane + oc);
   }
-  if (APPLY) psi_out[i] = psi_in[i] + fx_of(ev);
+  for (int zs = z0; zs < z1; zs += NB) {
+    float2 OA[NB], RC[NB], EYP[NB], EYM[NB];
+    float EX[NB];
+    uint32_t M[NB], MO[NB];
+    longlong2 P0[NB], P1[NB];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int z = min(zs + u, z1 - 1);  // past the run: a repeat, unused
+      const uint32_t pz = (uint32_t)z * plane;
+      RC[u] = ld2(rc + pz + oc);
+      M[u] = WALLS ? (uint32_t)*reinterpret_cast<const uint16_t*>(mask + own + pz + oc)
+                   : (FACES_OPEN | (FACES_OPEN << 8));
+      if (MODE != 1) {
+        const int za = (z < b.nzb - 1) ? z + 1 : (b.perz ? 0 : z);
+        OA[u] = ld2(eo + (uint32_t)za * plane + oc);
+        const int p = (y + z + color) & 1;
+        EX[u] = eo[pz + (p ? oxr : oxl)];
+        EYP[u] = ld2(eo + pz + oyp);
+        EYM[u] = ld2(eo + pz + oym);
+      }
+      if (MODE == 2) {
+        MO[u] = WALLS ? (uint32_t)*reinterpret_cast<const uint16_t*>(mask + oth + pz + oc)
+                      : (FACES_OPEN | (FACES_OPEN << 8));
+        const int64_t base = ((int64_t)(z + b.zlo) * b.ny + y) * b.nx + 4 * j;
+        P0[u] = *reinterpret_cast<const longlong2*>(psi_in + base);
+        P1[u] = *reinterpret_cast<const longlong2*>(psi_in + base + 2);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int z = zs + u;
+      if (z >= z1) break;
+      const uint32_t pz = (uint32_t)z * plane;
+      const int p = (y + z + color) & 1;  // own cells at 4j + p and 4j + 2 + p
+      if (MODE == 1) *reinterpret_cast<float2*>(eo + pz + oc) = make_float2(0.f, 0.f);
+      float val[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t m = (M[u] >> (8 * h)) & 0xffu;
+        float v = 0.f;
+        if (!(m & FACE_SOLID)) {
+          float sum = h ? RC[u].y : RC[u].x;
+          if (MODE != 1) {
+            // x neighbours: A (h = 0) at 4j + p, B (h = 1) at 4j + 2 + p;
+            // the other colour's cells of the two pairs are oh.x, oh.y
+            float xp, xm;
+            if (h == 0) {
+              xp = p ? oh.y : oh.x;
+              xm = p ? oh.x : EX[u];
+            } else {
+              xp = p ? EX[u] : oh.y;
+              xm = p ? oh.y : oh.x;
+            }
+            if (m & 1u) sum += xp;
+            if (m & 2u) sum += xm;
+            if (m & 4u) sum += h ? EYP[u].y : EYP[u].x;
+            if (m & 8u) sum += h ? EYM[u].y : EYM[u].x;
+            if (m & 16u) sum += h ? OA[u].y : OA[u].x;
+            if (m & 32u) sum += h ? ob.y : ob.x;
+          }
+          const int cnt = __popc(m & FACES_OPEN);
+          if (cnt > 0) v = __fdividef(sum, (float)cnt);
+          else if (MODE != 1) v = ec[pz + oc + h];  // isolated cell: unchanged
+        }
+        val[h] = v;
+      }
+      *reinterpret_cast<float2*>(ec + pz + oc) = make_float2(val[0], val[1]);
+      if (MODE == 2) {
+        const float ox = (MO[u] & FACE_SOLID) ? 0.f : oh.x;
+        const float oy = ((MO[u] >> 8) & FACE_SOLID) ? 0.f : oh.y;
+        const float e0 = p ? ox : val[0], e1 = p ? val[0] : ox;
+        const float e2 = p ? oy : val[1], e3 = p ? val[1] : oy;
+        const int64_t base = ((int64_t)(z + b.zlo) * b.ny + y) * b.nx + 4 * j;
+        longlong2 q0, q1;
+        q0.x = P0[u].x + fx_of(e0);
+        q0.y = P0[u].y + fx_of(e1);
+        q1.x = P1[u].x + fx_of(e2);
+        q1.y = P1[u].y + fx_of(e3);
+        *reinterpret_cast<longlong2*>(psi_out + base) = q0;
+        *reinterpret_cast<longlong2*>(psi_out + base + 2) = q1;
+      }
+      if (MODE != 1) {
+        ob = oh;
+        oh = OA[u];
+      }
+    }
+  }
+}
+
+// Fine-box residual r = s - <s> - A psi (exact integers), pair per thread
+// and plane, planes ZM_RES_BATCH at a time with every load of a batch issued
+// first; norms as in k_res0.
+constexpr int ZM_RES_BATCH = 2;
+
+template <bool WALLS, bool SNORM>
+__global__ void __launch_bounds__(256, 3) k_res0_zm(
+    const int64_t* __restrict__ psi, const int64_t* __restrict__ src,
+    const uint8_t* __restrict__ mask, float* __restrict__ r, const double* __restrict__ dsum,
+    float* __restrict__ acc, Box b, int zc, double inv_nfluid, const int* __restrict__ label,
+    const long long* __restrict__ comp_mean) {
+  __shared__ long long s_mean;
+  __shared__ float red_r[8], red_s[8];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid == 0) s_mean = llrint(dsum[0] * inv_nfluid);
+  __syncthreads();
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  float rr = 0.f, ss = 0.f;
+  if (k < b.hx && y < b.ny) {
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(z0 + zc, b.nzb);
+    const int x0 = 2 * k;
+    const int yp = (y == b.ny - 1) ? 0 : y + 1, ym = (y == 0) ? b.ny - 1 : y - 1;
+    const int64_t oc = (int64_t)y * b.nx + x0;
+    const int64_t oyp = (int64_t)yp * b.nx + x0, oym = (int64_t)ym * b.nx + x0;
+    const int64_t oxm = (int64_t)y * b.nx + (x0 == 0 ? b.nx - 1 : x0 - 1);
+    const int64_t oxp = (int64_t)y * b.nx + (x0 + 2 == b.nx ? 0 : x0 + 2);
+    const uint32_t plane = (uint32_t)b.ny * (uint32_t)b.hx;
+    const uint32_t sc = (uint32_t)y * b.hx + k;
+    const int zb0 = (z0 > 0) ? z0 - 1 : (b.perz ? b.nzb - 1 : 0);
+    longlong2 pb = *reinterpret_cast<const longlong2*>(psi + (int64_t)(zb0 + b.zlo) * b.nxy + oc);
+    longlong2 ph = *reinterpret_cast<const longlong2*>(psi + (int64_t)(z0 + b.zlo) * b.nxy + oc);
+    const int64_t mean0 = label ? (int64_t)comp_mean[0] : 0;
+    for (int zs = z0; zs < z1; zs += ZM_RES_BATCH) {
+      longlong2 PA[ZM_RES_BATCH], PYP[ZM_RES_BATCH], PYM[ZM_RES_BATCH], SV[ZM_RES_BATCH];
+      int64_t PXM[ZM_RES_BATCH], PXP[ZM_RES_BATCH];
+      int2 LB[ZM_RES_BATCH];
+      uint32_t M0[ZM_RES_BATCH], M1[ZM_RES_BATCH];
+#pragma unroll
+      for (int u = 0; u < ZM_RES_BATCH; ++u) {
+        const int z = min(zs + u, z1 - 1);  // past the run: a repeat, unused
+        const int za = (z < b.nzb - 1) ? z + 1 : (b.perz ? 0 : z);
+        const int64_t pl = (int64_t)(z + b.zlo) * b.nxy;
+        PA[u] = *reinterpret_cast<const longlong2*>(psi + (int64_t)(za + b.zlo) * b.nxy + oc);
+        PYP[u] = *reinterpret_cast<const longlong2*>(psi + pl + oyp);
+        PYM[u] = *reinterpret_cast<const longlong2*>(psi + pl + oym);
+        PXM[u] = psi[pl + oxm];
+        PXP[u] = psi[pl + oxp];
+        SV[u] = *reinterpret_cast<const longlong2*>(src + pl + oc);
+        if (label) LB[u] = *reinterpret_cast<const int2*>(label + pl + oc);
+        const uint32_t q0 = ((y + z) & 1) ? b.H : 0u, q1 = b.H - q0;
+        const uint32_t si = (uint32_t)z * plane + sc;
+        M0[u] = WALLS ? (uint32_t)mask[q0 + si] : FACES_OPEN;
+        M1[u] = WALLS ? (uint32_t)mask[q1 + si] : FACES_OPEN;
+      }
+#pragma unroll
+      for (int u = 0; u < ZM_RES_BATCH; ++u) {
+        const int z = zs + u;
+        if (z >= z1) break;
+        int64_t s0, s1;
+        if (label) {
+          // component 0 (the largest) from a register: the gather is only
+          // issued for cells of the other components
+          s0 = SV[u].x - (LB[u].x ? comp_mean[LB[u].x] : mean0);
+          s1 = SV[u].y - (LB[u].y ? comp_mean[LB[u].y] : mean0);
+        } else {
+          s0 = SV[u].x - (int64_t)s_mean;
+          s1 = SV[u].y - (int64_t)s_mean;
+        }
+        const uint32_t q0 = ((y + z) & 1) ? b.H : 0u, q1 = b.H - q0;  // colour arrays of x0, x0 + 1
+        const uint32_t si = (uint32_t)z * plane + sc;
+        const longlong2 pa = PA[u], pyp = PYP[u], pym = PYM[u];
+        const uint32_t m0 = M0[u], m1 = M1[u];
+        // cell x0: +x = x0 + 1, -x = x0 - 1; cell x0 + 1: +x = x0 + 2, -x = x0
+        if (!(m0 & FACE_SOLID)) {
+          int64_t Ap = 0;
+          const int64_t c = ph.x;
+          if (m0 & 1u) Ap += c - ph.y;
+          if (m0 & 2u) Ap += c - PXM[u];
+          if (m0 & 4u) Ap += c - pyp.x;
+          if (m0 & 8u) Ap += c - pym.x;
+          if (m0 & 16u) Ap += c - pa.x;
+          if (m0 & 32u) Ap += c - pb.x;
+          const float rf = i64_to_f32(s0 - Ap);
+          r[q0 + si] = rf * PSI_INV_SCALE_F;
+          const float rs = rf * MG_NORM_PRE;
+          rr = fmaf(rs, rs, rr);
+          if (SNORM) {
+            const float sf = i64_to_f32(s0) * MG_NORM_PRE;
+            ss = fmaf(sf, sf, ss);
+          }
+        } else {
+          r[q0 + si] = 0.f;
+        }
+        if (!(m1 & FACE_SOLID)) {
+          int64_t Ap = 0;
+          const int64_t c = ph.y;
+          if (m1 & 1u) Ap += c - PXP[u];
+          if (m1 & 2u) Ap += c - ph.x;
+          if (m1 & 4u) Ap += c - pyp.y;
+          if (m1 & 8u) Ap += c - pym.y;
+          if (m1 & 16u) Ap += c - pa.y;
+          if (m1 & 32u) Ap += c - pb.y;
+          const float rf = i64_to_f32(s1 - Ap);
+          r[q1 + si] = rf * PSI_INV_SCALE_F;
+          const float rs = rf * MG_NORM_PRE;
+          rr = fmaf(rs, rs, rr);
+          if (SNORM) {
+            const float sf = i64_to_f32(s1) * MG_NORM_PRE;
+            ss = fmaf(sf, sf, ss);
+          }
+        } else {
+          r[q1 + si] = 0.f;
+        }
+        pb = ph;
+        ph = pa;
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    rr += __shfl_down_sync(0xffffffffu, rr, off);
+    ss += __shfl_down_sync(0xffffffffu, ss, off);
+  }
+  if ((tid & 31) == 0) {
+    red_r[tid >> 5] = rr;
+    red_s[tid >> 5] = ss;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float tr = 0.f, ts = 0.f;
+    const int nw = (int)(blockDim.x * blockDim.y) >> 5;
+    for (int w = 0; w < nw; ++w) {
+      tr += red_r[w];
+      ts += red_s[w];
+    }
+    const int kk = (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)) & (MG_NACC - 1);
+    atomicAdd(acc + kk, tr);
+    if (SNORM) atomicAdd(acc + MG_NACC + kk, ts);
+  }
 }
 
 // Red-black SOR directly on the fixed-point psi (in place).
@@ -300,34 +781,12 @@ __global__ void __launch_bounds__(256) k_smooth(float* __restrict__ x,
   gs_cell(x, rhs, K, Dinv, l, c, xx, yy, zz);
 }
 
-// One CTA: many red-black sweeps over the whole coarsest level.
-__global__ void __launch_bounds__(1024) k_coarse_solve(
-    float* __restrict__ x, const float* __restrict__ rhs,
-    const float* __restrict__ K, const float* __restrict__ Dinv, CL l,
-    int sweeps) {
-  for (int it = 0; it < sweeps; ++it) {
-    for (int color = 0; color < 2; ++color) {
-      for (uint32_t c = threadIdx.x; c < (uint32_t)l.n; c += blockDim.x) {
-        int xx, yy, zz;
-        cl_xyz(c, l, xx, yy, zz);
-        if (((xx + yy + zz) & 1) != color) continue;
-        const float di = Dinv[c];
-        if (di == 0.f) continue;
-        int d[6];
-        cl_nbr(l, xx, yy, zz, d);
-        x[c] = di * (rhs[c] + cl_nsum(x, K, l, c, xx, yy, zz, d));
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// Restriction from the fine box: rhs_c(J) = sum over children i of
+// Restriction from the fine box: rhs_c(J) = sum over the children i of J of
 // (r_i - (A e)_i).
 template <bool WALLS>
 __global__ void __launch_bounds__(256) k_restrict0(
     const float* __restrict__ e, const float* __restrict__ r,
-    const uint32_t* __restrict__ links, Box b, CL cl, int cxs, int cys,
+    const uint8_t* __restrict__ mask, Box b, CL cl, int cxs, int cys,
     int czs, float* __restrict__ rhs_c) {
   const uint32_t J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= (uint32_t)cl.n) return;
@@ -338,22 +797,17 @@ __global__ void __launch_bounds__(256) k_restrict0(
     for (int ky = 0; ky <= cys; ++ky)
       for (int kx = 0; kx <= cxs; ++kx) {
         const int x = (X << cxs) + kx, y = (Y << cys) + ky, z = (Z << czs) + kz;
-        const uint32_t c = ((uint32_t)z * b.ny + y) * b.nx + x;
-        uint32_t lk = 0;
-        if (WALLS) {
-          lk = links[(int64_t)c + (int64_t)b.zlo * b.nxy];
-          if (lk & LINK_SOLID) continue;
-        }
-        int d[6];
-        box_nbr(b, x, y, z, d);
-        const float ec = e[c];
+        const uint32_t q = sp_idx(b, x, y, z);
+        const uint32_t m = WALLS ? (uint32_t)mask[q] : FACES_OPEN;
+        if (m & FACE_SOLID) continue;
+        uint32_t j[6];
+        sp_nbrs(b, x, y, z, j);
+        const float ec = e[q];
         float Ae = 0.f;
 #pragma unroll
-        for (int f = 0; f < 6; ++f) {
-          if (WALLS && !open_face(lk, f)) continue;
-          Ae += ec - e[(int64_t)c + d[f]];
-        }
-        acc += r[c] - Ae;
+        for (int f = 0; f < 6; ++f)
+          if ((m >> f) & 1u) Ae += ec - e[j[f]];
+        acc += r[q] - Ae;
       }
   rhs_c[J] = acc;
 }
@@ -382,63 +836,84 @@ __global__ void __launch_bounds__(256) k_restrict(
   rhs_c[J] = acc;
 }
 
-// Trilinear (cell-centred) prolongation of the coarse correction, added to
-// the fine correction.  A coarse cell outside a non-periodic boundary or
-// inactive is replaced by the parent cell.
-__device__ __forceinline__ void prol_axis(int i, int n_c, int per, int coarsened,
-                                          int& p0, int& p1, float& w0) {
-  if (!coarsened) {
-    p0 = p1 = i;
-    w0 = 1.f;
-    return;
-  }
-  p0 = i >> 1;
-  int q = (i & 1) ? p0 + 1 : p0 - 1;
-  if (q < 0 || q >= n_c) {
-    if (per) q = (q + n_c) % n_c;
-    else q = p0;
-  }
-  p1 = q;
-  w0 = 0.75f;
+// Coarse coordinates along one axis for the prolongation: [0] the neighbour
+// below, [1] the parent, [2] the neighbour above; a neighbour outside a
+// non-periodic boundary, or along an axis the coarse level does not halve,
+// is the parent's coordinate.
+__device__ __forceinline__ void prol_axis(int X, int n_c, int per, int coarsened, int (&c)[3]) {
+  c[0] = c[1] = c[2] = X;
+  if (!coarsened) return;
+  if (X > 0) c[0] = X - 1;
+  else if (per) c[0] = n_c - 1;
+  if (X < n_c - 1) c[2] = X + 1;
+  else if (per) c[2] = 0;
 }
 
+// Trilinear (cell-centred) prolongation of the coarse correction, added to
+// the fine correction; one thread per coarse cell J writes its children.
+// Along an axis the coarse level halves, child k of J takes 3/4 of J's
+// coordinate and 1/4 of the neighbour on its side (k = 0 below, k = 1
+// above); an inactive coarse cell contributes the parent's value instead.
+// FINE0: the fine level is the fine box (colour-split, face mask);
+// otherwise a level in natural order, Dinv_f = 0 marking inactive cells.
 template <bool FINE0, bool WALLS>
 __global__ void __launch_bounds__(256) k_prolong(
     float* __restrict__ ef, const float* __restrict__ Dinv_f,
-    const uint32_t* __restrict__ links, Box b, CL f, const float* __restrict__ xc,
+    const uint8_t* __restrict__ mask, Box b, CL f, const float* __restrict__ xc,
     const float* __restrict__ Dinv_c, CL cl, int cxs, int cys, int czs) {
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= (uint32_t)f.n) return;
-  int x, y, z;
-  cl_xyz(c, f, x, y, z);
-  if (FINE0) {
-    if (WALLS && (links[(int64_t)c + (int64_t)b.zlo * b.nxy] & LINK_SOLID)) return;
-  } else {
-    if (Dinv_f[c] == 0.f) return;
-  }
-  int ax[2], ay[2], az[2];
-  float wx0, wy0, wz0;
-  prol_axis(x, cl.nx, cl.px, cxs, ax[0], ax[1], wx0);
-  prol_axis(y, cl.ny, cl.py, cys, ay[0], ay[1], wy0);
-  prol_axis(z, cl.nz, cl.pz, czs, az[0], az[1], wz0);
-  const float wx[2] = {wx0, 1.f - wx0}, wy[2] = {wy0, 1.f - wy0},
-              wz[2] = {wz0, 1.f - wz0};
-  const int64_t parent = ((int64_t)az[0] * cl.ny + ay[0]) * cl.nx + ax[0];
-  const float vp = xc[parent];
-  float acc = 0.f;
+  const uint32_t J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= (uint32_t)cl.n) return;
+  int X, Y, Z;
+  cl_xyz(J, cl, X, Y, Z);
+  int ax[3], ay[3], az[3];
+  prol_axis(X, cl.nx, cl.px, cxs, ax);
+  prol_axis(Y, cl.ny, cl.py, cys, ay);
+  prol_axis(Z, cl.nz, cl.pz, czs, az);
+  const float vp = xc[J];
+  float v[3][3][3];
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const uint32_t Jn = ((uint32_t)az[dz] * (uint32_t)cl.ny + (uint32_t)ay[dy]) * (uint32_t)cl.nx +
+                            (uint32_t)ax[dx];
+        v[dz][dy][dx] = (Dinv_c[Jn] != 0.f) ? xc[Jn] : vp;
+      }
+  // weight of the parent's coordinate and of the side neighbour per axis
+  const float wx[2] = {cxs ? 0.75f : 1.f, cxs ? 0.25f : 0.f};
+  const float wy[2] = {cys ? 0.75f : 1.f, cys ? 0.25f : 0.f};
+  const float wz[2] = {czs ? 0.75f : 1.f, czs ? 0.25f : 0.f};
 #pragma unroll
   for (int kz = 0; kz < 2; ++kz)
 #pragma unroll
     for (int ky = 0; ky < 2; ++ky)
 #pragma unroll
       for (int kx = 0; kx < 2; ++kx) {
-        const float w = wx[kx] * wy[ky] * wz[kz];
-        if (w == 0.f) continue;
-        const int64_t J = ((int64_t)az[kz] * cl.ny + ay[ky]) * cl.nx + ax[kx];
-        const float v = (Dinv_c[J] != 0.f) ? xc[J] : vp;
-        acc += w * v;
+        if (kx > cxs || ky > cys || kz > czs) continue;
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+              const int sz = c ? (kz ? 2 : 0) : 1, sy = bb ? (ky ? 2 : 0) : 1,
+                        sx = a ? (kx ? 2 : 0) : 1;
+              acc = fmaf(wx[a] * wy[bb] * wz[c], v[sz][sy][sx], acc);
+            }
+        const int x = (X << cxs) + kx, y = (Y << cys) + ky, z = (Z << czs) + kz;
+        if (FINE0) {
+          const uint32_t q = sp_idx(b, x, y, z);
+          if (WALLS && (mask[q] & FACE_SOLID)) continue;
+          ef[q] += acc;
+        } else {
+          const uint32_t c = ((uint32_t)z * (uint32_t)f.ny + (uint32_t)y) * (uint32_t)f.nx + (uint32_t)x;
+          if (Dinv_f[c] == 0.f) continue;
+          ef[c] += acc;
+        }
       }
-  ef[c] += acc;
 }
 
 // Restricted residual of one coarse cell J: sum over its children i of
@@ -462,15 +937,224 @@ __device__ __forceinline__ float restrict_cell(const float* x, const float* rhs,
   return acc;
 }
 
+// Restriction from the fine box when the coarse level halves every axis
+// (z-marching form of k_restrict0): one thread per coarse (X, Y) walks zc
+// coarse planes.  Faces between two children of one coarse cell cancel in
+// the sum of (A e)_i over the children, so rhs_c = sum over fluid children of
+// r_i minus (e_i - e_out) over the open faces leaving the block.  The e of
+// fine planes 2Z - 1 .. 2Z + 2 of the pair column are kept in registers.
+template <bool WALLS>
+__global__ void __launch_bounds__(256) k_restrict0_zm(
+    const float* __restrict__ e, const float* __restrict__ r,
+    const uint8_t* __restrict__ mask, Box b, CL cl, int zc, float* __restrict__ rhs_c) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= cl.nx || Y >= cl.ny) return;
+  const int Z0 = blockIdx.z * zc;
+  const int Z1 = min(Z0 + zc, cl.nz);
+  const uint32_t plane = (uint32_t)b.ny * (uint32_t)b.hx;
+  const int Xm = (X == 0) ? b.hx - 1 : X - 1, Xp = (X == b.hx - 1) ? 0 : X + 1;
+  const int y0 = 2 * Y;
+  const int ym = (y0 == 0) ? b.ny - 1 : y0 - 1, yp = (y0 + 2 == b.ny) ? 0 : y0 + 2;
+  // fine plane index with wrap (periodic) or clamp (the face is closed)
+  auto zf = [&](int z) -> int {
+    if (z < 0) return b.perz ? z + b.nzb : 0;
+    if (z >= b.nzb) return b.perz ? z - b.nzb : b.nzb - 1;
+    return z;
+  };
+  // e of fine cell (2X + kx, y0 + ky, z) of the pair column
+  auto ecol = [&](int z, int ky, int kx) -> float {
+    const uint32_t q = ((kx + ky + z) & 1) ? b.H : 0u;
+    return e[q + (uint32_t)z * plane + (uint32_t)(y0 + ky) * b.hx + X];
+  };
+  float E[4][2][2];  // fine planes 2Z - 1, 2Z, 2Z + 1, 2Z + 2
+  {
+    const int za = zf(2 * Z0 - 1), zb = 2 * Z0;
+#pragma unroll
+    for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 2; ++kx) {
+        E[0][ky][kx] = ecol(za, ky, kx);
+        E[1][ky][kx] = ecol(zb, ky, kx);
+      }
+  }
+  for (int Z = Z0; Z < Z1; ++Z) {
+    const int z2 = 2 * Z + 1, z3 = zf(2 * Z + 2);
+#pragma unroll
+    for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 2; ++kx) {
+        E[2][ky][kx] = ecol(z2, ky, kx);
+        E[3][ky][kx] = ecol(z3, ky, kx);
+      }
+    // every load first (the masks only select among loaded values)
+    uint32_t M[2][2][2];
+    float RI[2][2][2], EXO[2][2][2], EYO[2][2][2];
+#pragma unroll
+    for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+      for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 2; ++kx) {
+          const int z = 2 * Z + kz, y = y0 + ky;
+          const uint32_t q = ((kx + ky + kz) & 1) ? b.H : 0u;  // colour of the child
+          const uint32_t qo = b.H - q;                          // its face neighbours
+          const uint32_t row = (uint32_t)z * plane + (uint32_t)y * b.hx;
+          M[kz][ky][kx] = WALLS ? (uint32_t)mask[q + row + X] : FACES_OPEN;
+          RI[kz][ky][kx] = r[q + row + X];
+          // x face leaving the block: -x for kx = 0 (pair X - 1), +x for kx = 1
+          EXO[kz][ky][kx] = e[qo + row + (kx ? Xp : Xm)];
+          // y face leaving the block: row y0 - 1 or y0 + 2, same pair
+          EYO[kz][ky][kx] = e[qo + (uint32_t)z * plane + (uint32_t)(ky ? yp : ym) * b.hx + X];
+        }
+    float acc = 0.f;
+#pragma unroll
+    for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+      for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 2; ++kx) {
+          const uint32_t m = M[kz][ky][kx];
+          if (m & FACE_SOLID) continue;
+          const float ei = E[1 + kz][ky][kx];
+          float Ae = 0.f;
+          if (m & (kx ? 1u : 2u)) Ae += ei - EXO[kz][ky][kx];
+          if (m & (ky ? 4u : 8u)) Ae += ei - EYO[kz][ky][kx];
+          // z face leaving the block: planes 2Z - 1 or 2Z + 2 (registers)
+          if (m & (kz ? 16u : 32u)) Ae += ei - (kz ? E[3][ky][kx] : E[0][ky][kx]);
+          acc += RI[kz][ky][kx] - Ae;
+        }
+    rhs_c[((uint32_t)Z * cl.ny + Y) * cl.nx + X] = acc;
+#pragma unroll
+    for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 2; ++kx) {
+        E[0][ky][kx] = E[2][ky][kx];
+        E[1][ky][kx] = E[3][ky][kx];
+      }
+  }
+}
+
+// Prolongation to the fine box when the coarse level halves every axis
+// (z-marching form of k_prolong<true, WALLS>): one thread per coarse (X, Y)
+// walks zc coarse planes, keeping the 3 x 3 coarse neighbourhood of the
+// planes below, here and above in registers (values, and a bit per cell for
+// "active").  The eight children of a plane are loaded before any is
+// stored, so that their loads overlap.
+template <bool WALLS>
+__global__ void __launch_bounds__(256) k_prolong0_zm(
+    float* __restrict__ ef, const uint8_t* __restrict__ mask, Box b,
+    const float* __restrict__ xc, const float* __restrict__ Dinv_c, CL cl, int zc) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= cl.nx || Y >= cl.ny) return;
+  const int Z0 = blockIdx.z * zc;
+  const int Z1 = min(Z0 + zc, cl.nz);
+  int ax[3], ay[3];
+  prol_axis(X, cl.nx, cl.px, 1, ax);
+  prol_axis(Y, cl.ny, cl.py, 1, ay);
+  const uint32_t cplane = (uint32_t)cl.nx * (uint32_t)cl.ny;
+  const uint32_t plane = (uint32_t)b.ny * (uint32_t)b.hx;
+  float R[3][3][3];
+  uint32_t act = 0;  // bit (dz * 9 + dy * 3 + dx): coarse cell active
+  auto load_plane = [&](int Zp, int dz) {
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const uint32_t j = (uint32_t)Zp * cplane + (uint32_t)ay[dy] * cl.nx + (uint32_t)ax[dx];
+        R[dz][dy][dx] = xc[j];
+        if (Dinv_c[j] != 0.f) act |= 1u << (dz * 9 + dy * 3 + dx);
+      }
+  };
+  auto zcl = [&](int Zq) -> int {  // coarse plane: wrap (periodic) or the parent's
+    if (Zq < 0) return cl.pz ? Zq + cl.nz : Zq + 1;
+    if (Zq >= cl.nz) return cl.pz ? Zq - cl.nz : Zq - 1;
+    return Zq;
+  };
+  load_plane(zcl(Z0 - 1), 0);
+  load_plane(Z0, 1);
+  for (int Z = Z0; Z < Z1; ++Z) {
+    act &= (1u << 18) - 1u;
+    load_plane(zcl(Z + 1), 2);
+    float EF[2][2][2];
+    uint32_t MK[2][2][2];
+#pragma unroll
+    for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+      for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 2; ++kx) {
+          const uint32_t q = ((kx + ky + kz) & 1) ? b.H : 0u;
+          const uint32_t i = q + (uint32_t)(2 * Z + kz) * plane + (uint32_t)(2 * Y + ky) * b.hx + X;
+          EF[kz][ky][kx] = ef[i];
+          MK[kz][ky][kx] = WALLS ? (uint32_t)mask[i] : FACES_OPEN;
+        }
+    const float vp = R[1][1][1];
+#pragma unroll
+    for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+      for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 2; ++kx) {
+          float acc = 0.f;
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+              for (int a = 0; a < 2; ++a) {
+                const int sz = c ? (kz ? 2 : 0) : 1, sy = bb ? (ky ? 2 : 0) : 1,
+                          sx = a ? (kx ? 2 : 0) : 1;
+                const float w = (a ? 0.25f : 0.75f) * (bb ? 0.25f : 0.75f) * (c ? 0.25f : 0.75f);
+                const float v = ((act >> (sz * 9 + sy * 3 + sx)) & 1u) ? R[sz][sy][sx] : vp;
+                acc = fmaf(w, v, acc);
+              }
+          if (MK[kz][ky][kx] & FACE_SOLID) continue;
+          const uint32_t q = ((kx + ky + kz) & 1) ? b.H : 0u;
+          const uint32_t i = q + (uint32_t)(2 * Z + kz) * plane + (uint32_t)(2 * Y + ky) * b.hx + X;
+          ef[i] = EF[kz][ky][kx] + acc;
+        }
+    act >>= 9;
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        R[0][dy][dx] = R[1][dy][dx];
+        R[1][dy][dx] = R[2][dy][dx];
+      }
+  }
+}
+
+// Coarse pair interpolated at fine coordinate i along one axis: p0 the
+// parent, p1 the neighbour on the child's side (the parent outside a
+// non-periodic boundary), w0 the parent's weight.
+__device__ __forceinline__ void prol_pair(int i, int n_c, int per, int coarsened,
+                                          int& p0, int& p1, float& w0) {
+  if (!coarsened) {
+    p0 = p1 = i;
+    w0 = 1.f;
+    return;
+  }
+  p0 = i >> 1;
+  int q = (i & 1) ? p0 + 1 : p0 - 1;
+  if (q < 0 || q >= n_c) {
+    if (per) q = (q + n_c) % n_c;
+    else q = p0;
+  }
+  p1 = q;
+  w0 = 0.75f;
+}
+
 // Trilinear interpolation of the coarse correction at fine cell (x, y, z).
 __device__ __forceinline__ float prolong_cell(const float* xc, const float* Dinv_c,
                                              const CL& cl, int x, int y, int z,
                                              int cxs, int cys, int czs) {
   int ax[2], ay[2], az[2];
   float wx0, wy0, wz0;
-  prol_axis(x, cl.nx, cl.px, cxs, ax[0], ax[1], wx0);
-  prol_axis(y, cl.ny, cl.py, cys, ay[0], ay[1], wy0);
-  prol_axis(z, cl.nz, cl.pz, czs, az[0], az[1], wz0);
+  prol_pair(x, cl.nx, cl.px, cxs, ax[0], ax[1], wx0);
+  prol_pair(y, cl.ny, cl.py, cys, ay[0], ay[1], wy0);
+  prol_pair(z, cl.nz, cl.pz, czs, az[0], az[1], wz0);
   const float wx[2] = {wx0, 1.f - wx0}, wy[2] = {wy0, 1.f - wy0},
               wz[2] = {wz0, 1.f - wz0};
   const int parent = (az[0] * cl.ny + ay[0]) * cl.nx + ax[0];
@@ -604,6 +1288,8 @@ Box make_box(lbm_t* h) {
   b.zlo = h->ps.zlo;
   b.perz = h->ps.perz;
   b.nxy = (int64_t)b.nx * b.ny;
+  b.hx = (b.nx + 1) / 2;
+  b.H = (uint32_t)((int64_t)b.nzb * b.ny * b.hx);
   return b;
 }
 
@@ -645,6 +1331,12 @@ void poisson_free(lbm_t* h) {
   cudaFree(P.psi[1]);
   cudaFree(P.src);
   cudaFree(P.dsum);
+  cudaFree(P.face);
+  cudaFree(P.nacc);
+  if (P.hacc) cudaFreeHost(P.hacc);
+  P.face = nullptr;
+  P.nacc = nullptr;
+  P.hacc = nullptr;
   cudaFree(P.part);
   P.part = nullptr;
   cudaFree(P.label);
@@ -728,12 +1420,37 @@ lbm_status poisson_setup(lbm_t* h, const uint8_t* solid) {
           if (fl0(x, y, (z + 1) % P.nzb)) Kh[2 * L0.n + c] = 1.f;
         }
       }
-  if (cudaMalloc(&L0.e, L0.n * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&L0.rhs, L0.n * sizeof(float)) != cudaSuccess) {
+  // level 0 fields are colour-split: two arrays of nzb ny ceil(nx / 2)
+  const size_t split = 2 * (size_t)P.nzb * ny * ((nx + 1) / 2);
+  if (cudaMalloc(&L0.e, split * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&L0.rhs, split * sizeof(float)) != cudaSuccess) {
     h->err = "Poisson level 0 allocation failed";
     return LBM_ENOMEM;
   }
+  // wall cells and pad cells are never read; cleared once so that no
+  // uninitialised value is ever visible
+  cudaMemset(L0.e, 0, split * sizeof(float));
+  cudaMemset(L0.rhs, 0, split * sizeof(float));
   P.lev.push_back(L0);
+  cudaFree(P.face);
+  P.face = nullptr;
+  if (h->has_walls) {
+    if (cudaMalloc(&P.face, split) != cudaSuccess) {
+      h->err = "Poisson face mask allocation failed";
+      return LBM_ENOMEM;
+    }
+    cudaMemset(P.face, (int)FACE_SOLID, split);
+    const Box b = make_box(h);
+    k_face_mask<<<nblocks(L0.n, 256), 256, 0, h->st>>>(h->links, b, (uint32_t)L0.n, P.face);
+    LBM_CUDA_TRY(h, cudaGetLastError());
+  }
+  if (!P.nacc) {
+    if (cudaMalloc(&P.nacc, 2 * MG_NACC * sizeof(float)) != cudaSuccess ||
+        cudaMallocHost(&P.hacc, 2 * MG_NACC * sizeof(float)) != cudaSuccess) {
+      h->err = "Poisson norm slot allocation failed";
+      return LBM_ENOMEM;
+    }
+  }
 
   // Coarsen while the level has more than 64 cells and an axis can halve.
   int lx = nx, ly = ny, lz = P.nzb;
@@ -831,25 +1548,98 @@ lbm_status poisson_setup(lbm_t* h, const uint8_t* solid) {
 
 namespace {
 
+// The z-marching fine-box kernels need a true red-black two-colouring: x
+// and y extents even, z extent even unless z is not periodic.
+bool zm_fine(const Box& b) {
+  return (b.nx % 2 == 0) && (b.ny % 2 == 0) && (!b.perz || b.nzb % 2 == 0);
+}
+
+// ... and, for the restriction and prolongation, a first coarse level that
+// halves every axis.
+bool zm_coarse(const Poisson& P, const Box& b) {
+  return zm_fine(b) && P.lev.size() > 1 && P.lev[1].coarsened[0] && P.lev[1].coarsened[1] &&
+         P.lev[1].coarsened[2];
+}
+
+constexpr int ZM_PLANES = 8;         // fine planes per thread
+constexpr int ZM_COARSE_PLANES = 4;  // coarse planes per thread (restriction, prolongation)
+
+// Launch shape of a z-marching kernel over nxp x nyp columns and nz planes:
+// 256 threads as TX x TY with TX (up to 32) along x, runs of zc planes.
+struct ZmShape {
+  dim3 grid, block;
+  int zc;
+};
+ZmShape zm_shape(int nxp, int nyp, int nz, int zc) {
+  int tx = 1;
+  while (tx < nxp && tx < 32) tx <<= 1;
+  const int ty = 256 / tx;
+  ZmShape z;
+  z.block = dim3((unsigned)tx, (unsigned)ty, 1);
+  z.zc = std::max(1, std::min(zc, nz));
+  z.grid = dim3((unsigned)((nxp + tx - 1) / tx), (unsigned)((nyp + ty - 1) / ty),
+                (unsigned)((nz + z.zc - 1) / z.zc));
+  return z;
+}
+
 // Queues the fine-box residual of the current potential and the
-// device-to-host copy of its norms; does not wait.
-cudaError_t residual_launch(lbm_t* h) {
+// device-to-host copy of its norm slots; does not wait.  snorm: also the
+// source norm (the first residual of a solve; later ones reuse it).
+template <bool SNORM>
+void residual_kernel(lbm_t* h, const Box& b) {
   Poisson& P = h->ps;
-  const Box b = make_box(h);
   const int64_t nbox = P.lev[0].n;
   const double inv_nf = 1.0 / (double)h->nfluid;
-  cudaError_t e = cudaMemsetAsync(P.dsum + 1, 0, 2 * sizeof(double), h->st);
+  const unsigned nb = nblocks(nbox, 256);
+  if (zm_fine(b)) {
+    const ZmShape z = zm_shape(b.hx, b.ny, b.nzb, ZM_PLANES);
+    if (h->has_walls)
+      k_res0_zm<true, SNORM><<<z.grid, z.block, 0, h->st>>>(P.psi[P.cur], P.src, P.face,
+                                                            P.lev[0].rhs, P.dsum, P.nacc, b, z.zc,
+                                                            inv_nf, P.label, P.comp_mean);
+    else
+      k_res0_zm<false, SNORM><<<z.grid, z.block, 0, h->st>>>(P.psi[P.cur], P.src, nullptr,
+                                                             P.lev[0].rhs, P.dsum, P.nacc, b, z.zc,
+                                                             inv_nf, nullptr, nullptr);
+  } else if (h->has_walls) {
+    k_res0<true, SNORM><<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, P.face, P.lev[0].rhs, P.dsum,
+                                               P.nacc, b, (uint32_t)nbox, inv_nf, P.label,
+                                               P.comp_mean);
+  } else {
+    k_res0<false, SNORM><<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, nullptr, P.lev[0].rhs,
+                                                P.dsum, P.nacc, b, (uint32_t)nbox, inv_nf, nullptr,
+                                                nullptr);
+  }
+}
+
+cudaError_t residual_launch(lbm_t* h, bool snorm = false) {
+  Poisson& P = h->ps;
+  const Box b = make_box(h);
+  cudaError_t e = cudaMemsetAsync(P.nacc, 0, 2 * MG_NACC * sizeof(float), h->st);
   if (e != cudaSuccess) return e;
-  const unsigned nb = (unsigned)std::min<int64_t>(nblocks(nbox, 256), h->grid_cap);
-  if (h->has_walls)
-    k_res0<true><<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, h->links, P.lev[0].rhs, P.dsum,
-                                        b, nbox, inv_nf, P.label, P.comp_mean);
-  else
-    k_res0<false><<<nb, 256, 0, h->st>>>(P.psi[P.cur], P.src, nullptr, P.lev[0].rhs, P.dsum,
-                                         b, nbox, inv_nf, nullptr, nullptr);
+  if (snorm) residual_kernel<true>(h, b);
+  else residual_kernel<false>(h, b);
+  P.snorm_pending = snorm;
   ++h->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return cudaMemcpyAsync(P.hsum, P.dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+  return cudaMemcpyAsync(P.hacc, P.nacc, 2 * MG_NACC * sizeof(float), cudaMemcpyDeviceToHost,
+                         h->st);
+}
+
+// Norms ||r||_2 and ||s - <s>||_2 (fixed-point units) of the last residual
+// read back.
+void residual_norms(Poisson& P, double* rn, double* sn) {
+  double a = 0.0, c = 0.0;
+  for (int k = 0; k < MG_NACC; ++k) {
+    a += (double)P.hacc[k];
+    c += (double)P.hacc[MG_NACC + k];
+  }
+  *rn = sqrt(a) * 1048576.0;
+  if (P.snorm_pending) {
+    P.snorm = sqrt(c) * 1048576.0;
+    P.snorm_pending = false;
+  }
+  *sn = P.snorm;
 }
 
 // Waits for the last queued residual.  Returns ||r|| / ||s|| in *rel and
@@ -859,7 +1649,8 @@ cudaError_t residual_launch(lbm_t* h) {
 lbm_status residual_read(lbm_t* h, double tol, double* rel, bool* done) {
   Poisson& P = h->ps;
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
-  const double rn = sqrt(P.hsum[1]), sn = sqrt(P.hsum[2]);
+  double rn, sn;
+  residual_norms(P, &rn, &sn);
   *rel = sn > 0.0 ? rn / sn : (rn > 0.0 ? INFINITY : 0.0);
   if (!isfinite(rn) || !isfinite(sn)) {
     h->err = "Poisson residual is not finite";
@@ -869,37 +1660,56 @@ lbm_status residual_read(lbm_t* h, double tol, double* rel, bool* done) {
   return LBM_OK;
 }
 
-cudaError_t smooth_level(lbm_t* h, int l, int sweeps, bool apply = false) {
+template <int MODE>
+void smooth0_launch(lbm_t* h, const Box& b, unsigned nb, int color) {
+  Poisson& P = h->ps;
+  PoissonLevel& L = P.lev[0];
+  const int64_t* pin = P.psi[P.cur];
+  int64_t* pout = P.psi[P.cur ^ 1];
+  if (zm_fine(b) && b.nx % 4 == 0) {
+    const ZmShape z = zm_shape(b.hx / 2, b.ny, b.nzb, ZM_PLANES);
+    if (h->has_walls)
+      k_smooth0_zq<true, MODE><<<z.grid, z.block, 0, h->st>>>(L.e, L.rhs, P.face, b, color, z.zc,
+                                                              pin, pout);
+    else
+      k_smooth0_zq<false, MODE><<<z.grid, z.block, 0, h->st>>>(L.e, L.rhs, nullptr, b, color,
+                                                               z.zc, pin, pout);
+  } else if (zm_fine(b)) {
+    const ZmShape z = zm_shape(b.hx, b.ny, b.nzb, ZM_PLANES);
+    if (h->has_walls)
+      k_smooth0_zm<true, MODE><<<z.grid, z.block, 0, h->st>>>(L.e, L.rhs, P.face, b, color, z.zc,
+                                                              pin, pout);
+    else
+      k_smooth0_zm<false, MODE><<<z.grid, z.block, 0, h->st>>>(L.e, L.rhs, nullptr, b, color,
+                                                               z.zc, pin, pout);
+  } else if (h->has_walls) {
+    k_smooth0<true, MODE><<<nb, 256, 0, h->st>>>(L.e, L.rhs, P.face, b, color, pin, pout);
+  } else {
+    k_smooth0<false, MODE><<<nb, 256, 0, h->st>>>(L.e, L.rhs, nullptr, b, color, pin, pout);
+  }
+  ++h->launches;
+}
+
+// `sweeps` red-black sweeps on level l.  On the fine box: zero_start, the
+// first half-sweep starts from e = 0; apply, the last half-sweep writes the
+// corrected potential into the other buffer, which becomes current.
+cudaError_t smooth_level(lbm_t* h, int l, int sweeps, bool apply = false,
+                         bool zero_start = false) {
   Poisson& P = h->ps;
   PoissonLevel& L = P.lev[l];
-  const int compact = (L.nx % 2 == 0) ? 1 : 0;
-  const unsigned nb = nblocks(compact ? L.n / 2 : L.n, 256);
   if (l == 0) {
     const Box b = make_box(h);
-    const int64_t* pin = P.psi[P.cur];
-    int64_t* pout = P.psi[P.cur ^ 1];
+    const unsigned nb = nblocks(b.H, 256);
     for (int k = 0; k < sweeps; ++k)
       for (int color = 0; color < 2; ++color) {
-        const bool last = apply && k == sweeps - 1;
-        if (h->has_walls) {
-          if (last)
-            k_smooth0<true, true><<<nb, 256, 0, h->st>>>(L.e, L.rhs, h->links, b, L.n, color,
-                                                         compact, pin, pout);
-          else
-            k_smooth0<true, false><<<nb, 256, 0, h->st>>>(L.e, L.rhs, h->links, b, L.n, color,
-                                                          compact, pin, pout);
-        } else {
-          if (last)
-            k_smooth0<false, true><<<nb, 256, 0, h->st>>>(L.e, L.rhs, nullptr, b, L.n, color,
-                                                          compact, pin, pout);
-          else
-            k_smooth0<false, false><<<nb, 256, 0, h->st>>>(L.e, L.rhs, nullptr, b, L.n, color,
-                                                           compact, pin, pout);
-        }
-        ++h->launches;
+        if (zero_start && k == 0 && color == 0) smooth0_launch<1>(h, b, nb, color);
+        else if (apply && k == sweeps - 1 && color == 1) smooth0_launch<2>(h, b, nb, color);
+        else smooth0_launch<0>(h, b, nb, color);
       }
     if (apply) P.cur ^= 1;
   } else {
+    const int compact = (L.nx % 2 == 0) ? 1 : 0;
+    const unsigned nb = nblocks(compact ? L.n / 2 : L.n, 256);
     const CL c = make_cl(L);
     for (int k = 0; k < sweeps; ++k)
       for (int color = 0; color < 2; ++color) {
@@ -949,17 +1759,29 @@ cudaError_t vcycle(lbm_t* h) {
   Poisson& P = h->ps;
   const int nl = (int)P.lev.size();
   const Box b = make_box(h);
-  cudaError_t e = cudaMemsetAsync(P.lev[0].e, 0, P.lev[0].n * sizeof(float), h->st);
-  if (e != cudaSuccess) return e;
-  if (nl == 1) return smooth_level(h, 0, 8, true);
+  cudaError_t e = cudaSuccess;
+  // the first half-sweep starts from e = 0 (no clearing pass)
+  if (nl == 1) return smooth_level(h, 0, 8, true, true);
   const int lc = sub_level(P);
-  if ((e = smooth_level(h, 0, P.nu1)) != cudaSuccess) return e;
+  if (P.nu1 > 0) {
+    if ((e = smooth_level(h, 0, P.nu1, false, true)) != cudaSuccess) return e;
+  } else if ((e = cudaMemsetAsync(P.lev[0].e, 0, 2 * (size_t)b.H * sizeof(float), h->st)) !=
+             cudaSuccess) {
+    return e;
+  }
   {
     PoissonLevel& C = P.lev[1];
     const CL cl = make_cl(C);
-    if (h->has_walls)
+    const ZmShape zs = zm_shape(cl.nx, cl.ny, cl.nz, ZM_COARSE_PLANES);
+    if (zm_coarse(P, b) && h->has_walls)
+      k_restrict0_zm<true><<<zs.grid, zs.block, 0, h->st>>>(P.lev[0].e, P.lev[0].rhs, P.face, b,
+                                                            cl, zs.zc, C.rhs);
+    else if (zm_coarse(P, b))
+      k_restrict0_zm<false><<<zs.grid, zs.block, 0, h->st>>>(P.lev[0].e, P.lev[0].rhs, nullptr, b,
+                                                             cl, zs.zc, C.rhs);
+    else if (h->has_walls)
       k_restrict0<true><<<nblocks(C.n, 256), 256, 0, h->st>>>(
-          P.lev[0].e, P.lev[0].rhs, h->links, b, cl, C.coarsened[0], C.coarsened[1],
+          P.lev[0].e, P.lev[0].rhs, P.face, b, cl, C.coarsened[0], C.coarsened[1],
           C.coarsened[2], C.rhs);
     else
       k_restrict0<false><<<nblocks(C.n, 256), 256, 0, h->st>>>(
@@ -988,10 +1810,19 @@ cudaError_t vcycle(lbm_t* h) {
   for (int l = last - 1; l >= 0; --l) {
     PoissonLevel& F = P.lev[l];
     PoissonLevel& C = P.lev[l + 1];
-    const unsigned nb = nblocks(F.n, 256);
-    if (l == 0) {
+    const unsigned nb = nblocks(C.n, 256);  // one thread per coarse cell
+    if (l == 0 && zm_coarse(P, b)) {
+      const CL cl = make_cl(C);
+      const ZmShape zs = zm_shape(cl.nx, cl.ny, cl.nz, ZM_COARSE_PLANES);
       if (h->has_walls)
-        k_prolong<true, true><<<nb, 256, 0, h->st>>>(F.e, nullptr, h->links, b, make_cl(F),
+        k_prolong0_zm<true><<<zs.grid, zs.block, 0, h->st>>>(F.e, P.face, b, C.e, C.Dinv, cl,
+                                                             zs.zc);
+      else
+        k_prolong0_zm<false><<<zs.grid, zs.block, 0, h->st>>>(F.e, nullptr, b, C.e, C.Dinv, cl,
+                                                              zs.zc);
+    } else if (l == 0) {
+      if (h->has_walls)
+        k_prolong<true, true><<<nb, 256, 0, h->st>>>(F.e, nullptr, P.face, b, make_cl(F),
                                                      C.e, C.Dinv, make_cl(C), C.coarsened[0],
                                                      C.coarsened[1], C.coarsened[2]);
       else
@@ -1004,7 +1835,7 @@ cudaError_t vcycle(lbm_t* h) {
                                                      C.coarsened[1], C.coarsened[2]);
     }
     ++h->launches;
-    if ((e = smooth_level(h, l, P.nu2, l == 0)) != cudaSuccess) return e;
+    if ((e = smooth_level(h, l, std::max(P.nu2, l == 0 ? 1 : 0), l == 0)) != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -1067,15 +1898,18 @@ lbm_status poisson_solve(lbm_t* h, double tol, int maxit, int* iters,
   Poisson& P = h->ps;
   double rel = 0.0, rel0 = 0.0;
   bool done = false;
-  LBM_CUDA_TRY(h, residual_launch(h));
+  LBM_CUDA_TRY(h, residual_launch(h, true));
   lbm_status s = residual_read(h, tol, &rel, &done);
   if (s != LBM_OK) return s;
   if (!done && nn_active(h)) {
     // learned initial guess: apply, keep it only if the residual drops
-    const double rn = sqrt(P.hsum[1]) * PSI_INV_SCALE;
+    double rn, sn;
+    residual_norms(P, &rn, &sn);
+    rn *= PSI_INV_SCALE;
     bool applied = false;
     float* dpsi = nullptr;
-    s = nn_before_solve(h, P.lev[0].rhs, P.zlo, P.nzb, rn / sqrt((double)h->nfluid), &applied, &dpsi);
+    s = nn_before_solve(h, P.lev[0].rhs, P.zlo, P.nzb, (h->cfg.nx + 1) / 2,
+                        rn / sqrt((double)h->nfluid), &applied, &dpsi);
     if (s != LBM_OK) return s;
     if (applied) {
       double rel_nn = 0.0;

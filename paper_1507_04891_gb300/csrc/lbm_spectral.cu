@@ -1170,7 +1170,7 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters, double* r
     if (!conv_of(rn, sn)) {
       bool applied = false;
       float* dpsi = nullptr;
-      lbm_status st = nn_before_solve(h, s->r, 0, s->nz, rn * PSI_INV_SCALE / sqrt((double)h->nfluid),
+      lbm_status st = nn_before_solve(h, s->r, 0, s->nz, 0, rn * PSI_INV_SCALE / sqrt((double)h->nfluid),
                                       &applied, &dpsi);
       if (st != LBM_OK) return st;
       if (applied) {
