@@ -38,6 +38,9 @@ namespace {
 template <int S, bool WALLS, bool CHARGED, int ST, bool DIAG, bool PAIR>
 __global__ void __launch_bounds__(256, S >= 4 ? 1 : 2) k_stream_collide(const StepArgs a) {
   using T = typename Fmt<ST>::T;
+  // a speculative launch the step has decided against (same for every
+  // thread of the grid)
+  if (a.skip && *a.skip) return;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   // deviation sums of the state after the step: masses, momentum, charge
   float qm[S], qjx = 0.f, qjy = 0.f, qjz = 0.f, qbad = 0.f;

@@ -106,6 +106,7 @@ struct StepArgs {
   uint32_t step;            // time step (seeds the stochastic rounding)
   const uint32_t* step_dev; // device copy of the step (graph replays) or NULL
   double* diag;             // per-CTA diagnostics partials (DIAG_NQ per CTA) or NULL
+  const int* skip;          // device flag: nonzero makes the launch return at once (or NULL)
   // matrix of pair drag frequencies omega^{ab} (Sec. 2, general gamma^{ab}
   // for equal masses; zero diagonal), used instead of omega_drag when pair_on
   int pair_on;
@@ -223,6 +224,7 @@ struct lbm {
   bool charge_means_ready = false;
   // step counter advanced by the charge path while graph steps are captured
   uint32_t* charge_step = nullptr;
+  const int* collide_skip = nullptr;  // skip flag of the stream/collide being captured
   double* hred = nullptr;   // pinned mirror
   int* dflag = nullptr;
   int last_iters = 0;

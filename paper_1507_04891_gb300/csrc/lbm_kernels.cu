@@ -536,6 +536,7 @@ StepArgs step_args(lbm_t* h) {
   a.step_dev = nullptr;
   if (h->gstatus) a.step_dev = reinterpret_cast<const uint32_t*>(h->gstatus);
   a.diag = h->dpart;
+  a.skip = h->collide_skip;
   a.pair_on = h->pair_on ? 1 : 0;
   for (int i = 0; i < MAX_SPECIES; ++i)
     for (int j = 0; j < MAX_SPECIES; ++j) a.pair[i][j] = h->pair[i][j];

@@ -1271,7 +1271,18 @@ struct GraphStatus {
   int full;            // the current step's start had the full history
   double start_log;    // sum of log10 of the steps' start residuals
   long long starts;    // steps counted in start_log
+  int spec_skip;       // the current step does not speculate (start from a short history)
+  long long redos;     // steps that ran the stream/collide after the loop
 };
+
+// Whether the step runs its stream/collide speculatively, beside the test
+// after the k baked applications: only when the start used the full
+// history.  A start from a short history (the first steps after a restart)
+// usually needs more applications, and the speculative stream/collide would
+// be discarded; then the stream/collide runs once, after the loop.
+__global__ void k_spec_decide(const int* __restrict__ start_terms, GraphStatus* st) {
+  st->spec_skip = (start_terms && *start_terms < START_FULL_TERMS) ? 1 : 0;
+}
 
 // Convergence test (one warp).  first: after the k applications queued
 // unconditionally (norm slots 0..k hold the residual before each and after
@@ -1320,8 +1331,13 @@ __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, do
   const bool more = !conv && st->iters < maxit;
   cudaGraphSetConditional(cond, more ? 1u : 0u);
   // the stream/collide ran beside this test on the potential after k
-  // applications: it runs again after the loop when the loop runs
-  if (first) cudaGraphSetConditional(redo, more ? 1u : 0u);
+  // applications: it runs again after the loop when the loop runs, or when
+  // the step did not speculate
+  if (first) {
+    const bool again = more || st->spec_skip;
+    cudaGraphSetConditional(redo, again ? 1u : 0u);
+    if (again) st->redos += 1;
+  }
   st->rel = snk > 0.0 ? sqrt(rnk / snk) : 0.0;
   // applications this step needed, recorded once per step: at the first
   // test when slot k converged (the earliest converged slot), else when the
@@ -1415,13 +1431,20 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
     if (ec == cudaSuccess && fit) ec = start_fit(h, side2, true);
     if (ec == cudaSuccess && fit) ec = cudaEventRecord(join2, side2);
     if (ec == cudaSuccess) ec = spec_means(h);
+    if (ec == cudaSuccess) {
+      k_spec_decide<<<1, 1, 0, main>>>(terms, gs);
+      ++h->launches;
+      ec = cudaGetLastError();
+    }
     for (int i = 0; i < k && ec == cudaSuccess; ++i) ec = spec_apply(h, i);
     if (ec == cudaSuccess) ec = cudaEventRecord(fork, main);
     if (ec == cudaSuccess) ec = cudaStreamWaitEvent(side, fork, 0);
     if (ec == cudaSuccess) {
       const int64_t a = h->launches;
       h->st = side;
+      h->collide_skip = &gs->spec_skip;
       ec = launch_stream_collide(h, diag);
+      h->collide_skip = nullptr;
       h->st = main;
       lc = h->launches - a;
     }
@@ -1492,6 +1515,9 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
     if (e == cudaSuccess) {
       e = cudaStreamBeginCaptureToGraph(main, ibody, nullptr, nullptr, 0, mode);
       if (e == cudaSuccess) {
+        // from the step's input populations again, into the same output as
+        // the speculative launch (which flipped the parity while capturing)
+        h->cur = parity;
         cudaError_t eb = launch_stream_collide(h, diag);
         cudaGraph_t gg = nullptr;
         e = cudaStreamEndCapture(main, &gg);
@@ -1603,6 +1629,7 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     }
     const int n = std::min(CHUNK, nsteps - done);
     const long long tot_before = hs->total;
+    const long long redos_before = hs->redos;
     LBM_CUDA_TRY(h, cudaMemsetAsync(ds->need, 0, 8 * sizeof(int), h->st));  // need, needf
     // the call's last step replays the variant that sums the state it
     // stores (diagnostics)
@@ -1616,10 +1643,9 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     LBM_CUDA_TRY(h, cudaMemcpyAsync(hs, ds, sizeof(GraphStatus), cudaMemcpyDeviceToHost, h->st));
     LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
     // the body of the while node ran once per application beyond the k
-    // baked into every step
-    // steps that needed more than k ran the while loop and the stream/collide again
-    int redo_steps = 0;
-    for (int j = sp->graph_k; j < 4; ++j) redo_steps += hs->need[j];
+    // baked into every step; steps that needed more than k, or did not
+    // speculate, ran the stream/collide again
+    const long long redo_steps = hs->redos - redos_before;
     h->launches += (int64_t)n * h->graph_kernels_fixed +
                    (hs->total - tot_before - (long long)n * sp->graph_k) * h->graph_kernels_iter +
                    (int64_t)redo_steps * h->graph_kernels_redo;
