@@ -217,7 +217,8 @@ lbm_status lbm_set_species(lbm_t* h, int s, double mass, double valence,
  * work on the legacy default stream.  The checks of lbm_set_species (n0
  * finite and > 0, u0 finite at every fluid node) run on the device; the
  * call returns after they were read back and the initialisation was
- * queued.  LBM_EINVAL as for lbm_set_species.                             */
+ * queued.  LBM_EINVAL as for lbm_set_species, and for a pointer the device
+ * cannot reach (pinned host memory is accepted and read in place).        */
 lbm_status lbm_set_species_dev(lbm_t* h, int s, double mass, double valence,
                                const double* n0_dev, const double* u0_dev, void* stream);
 
@@ -242,12 +243,15 @@ lbm_status lbm_synchronize(lbm_t* h);
  * pointer may be NULL.  Zero at wall nodes.  Host buffers.                */
 lbm_status lbm_get_moments(lbm_t* h, int s, double* n, double* u);
 
-/* As lbm_get_moments, into device memory of the handle's device: n_dev
+/* As lbm_get_moments, into memory the handle's device can write: n_dev
  * (N doubles) and u_dev (3N doubles, [3][N]), either may be NULL,
- * caller-owned and never retained.  The gather is queued on `stream` (a
- * cudaStream_t, or NULL for the library's stream) after the last step and
- * the call returns without waiting for it; the caller orders its reads of
- * the buffers on that stream.                                              */
+ * caller-owned and never retained.  Device (or managed) memory, or pinned
+ * host memory, which the gather kernel then writes directly (no separate
+ * copy); any other pointer is refused with LBM_EINVAL before a kernel runs.
+ * The gather is queued on `stream` (a cudaStream_t, or NULL for the
+ * library's stream) after the last step and the call returns without
+ * waiting for it; the caller orders its reads of the buffers on that
+ * stream.                                                                  */
 lbm_status lbm_get_moments_dev(lbm_t* h, int s, double* n_dev, double* u_dev, void* stream);
 
 /* Plane sums of the current state, for the slit currents of Sec. 4 (mass
@@ -315,6 +319,20 @@ lbm_status lbm_solve_poisson(lbm_t* h, const double* rho_e, double* psi,
  * density entering the last step; the values are still written).        */
 #define LBM_DIAG_LEN(S) ((S) + 7)
 lbm_status lbm_diagnostics(lbm_t* h, double* out);
+
+/* nsteps time steps as lbm_step, each followed by the read-back of its
+ * diagnostics: row k of out (LBM_DIAG_LEN(S) doubles per row, host memory,
+ * nsteps rows) holds what lbm_diagnostics would return right after step k,
+ * with that step's Poisson applications and final residual.  Every step
+ * sums the state it stores in the stream/collide kernel (no pass over the
+ * lattice); its sums are reduced on the device and copied to pinned
+ * library memory with an asynchronous copy queued behind the step, so the
+ * steps are not serialised by host waits: the call waits once per chunk
+ * of up to 4096 steps and converts the rows.  stream as in lbm_step.
+ * Returns as lbm_step; on an error the rows of the steps taken are
+ * written.  LBM_EUNSTABLE when a row would make lbm_diagnostics return it
+ * (all rows written).                                                     */
+lbm_status lbm_step_record(lbm_t* h, int nsteps, double* out, void* stream);
 
 /* Raw state for checkpointing (FP32 storage): the stored values of all
  * species, S*19*N floats in the library's internal order and form (post-

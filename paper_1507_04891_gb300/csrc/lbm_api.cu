@@ -131,6 +131,30 @@ struct CallStream {
 };
 
 // Argument checks shared by lbm_set_species and lbm_set_species_dev.
+// The address under which the handle's device reaches caller memory p:
+// device or managed memory of any device as is, pinned host memory through
+// its mapped device address.  Anything else (pageable host memory, an
+// unknown pointer) is refused here, before a kernel could touch it.
+lbm_status device_view(lbm_t* h, const void* p, void** out, const char* what) {
+  *out = nullptr;
+  if (!p) return LBM_OK;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, LBM_EINVAL, std::string(what) + " is not memory the device can reach");
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    *out = const_cast<void*>(p);
+    return LBM_OK;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    *out = at.devicePointer;
+    return LBM_OK;
+  }
+  return fail(h, LBM_EINVAL,
+              std::string(what) + " must be device memory or pinned (mapped) host memory");
+}
+
 lbm_status species_args(lbm_t* h, int s, double mass, double valence, const void* n0) {
   if (!h) return LBM_EINVAL;
   if (s < 0 || s >= h->S) return fail(h, LBM_EINVAL, "species index out of range");
@@ -306,6 +330,7 @@ void lbm_destroy(lbm_t* h) {
   cudaFree(h->wallq);
   cudaFree(h->wsrc);
   cudaFree(h->dred);
+  if (h->hrec) cudaFreeHost(h->hrec);
   cudaFree(h->dpart);
   cudaFree(h->dflag);
   if (h->hred) cudaFreeHost(h->hred);
@@ -505,10 +530,15 @@ lbm_status lbm_set_species(lbm_t* h, int s, double mass, double valence,
 }
 
 lbm_status lbm_set_species_dev(lbm_t* h, int s, double mass, double valence,
-                               const double* n0_dev, const double* u0_dev, void* stream) {
-  lbm_status st = species_args(h, s, mass, valence, n0_dev);
+                               const double* n0_arg, const double* u0_arg, void* stream) {
+  lbm_status st = species_args(h, s, mass, valence, n0_arg);
   if (st != LBM_OK) return st;
   cudaSetDevice(h->dev);
+  void *n0v = nullptr, *u0v = nullptr;
+  if ((st = device_view(h, n0_arg, &n0v, "n0_dev")) != LBM_OK) return st;
+  if ((st = device_view(h, u0_arg, &u0v, "u0_dev")) != LBM_OK) return st;
+  const double* n0_dev = static_cast<const double*>(n0v);
+  const double* u0_dev = static_cast<const double*>(u0v);
   CallStream cs(h, stream);
   LBM_CUDA_TRY(h, cs.err);
   // fluid-node sum of n0 (the reference density) and a count of invalid
@@ -530,12 +560,18 @@ lbm_status lbm_set_species_dev(lbm_t* h, int s, double mass, double valence,
   return species_done(h, s, mass, valence);
 }
 
-lbm_status lbm_get_moments_dev(lbm_t* h, int s, double* n_dev, double* u_dev, void* stream) {
+lbm_status lbm_get_moments_dev(lbm_t* h, int s, double* n_arg, double* u_arg, void* stream) {
   if (!h) return LBM_EINVAL;
   if (s < 0 || s >= h->S) return fail(h, LBM_EINVAL, "species index out of range");
   if (!(h->species_set >> s & 1u)) return fail(h, LBM_EINVAL, "species not set");
-  if (!n_dev && !u_dev) return LBM_OK;
+  if (!n_arg && !u_arg) return LBM_OK;
   cudaSetDevice(h->dev);
+  void *nv = nullptr, *uv = nullptr;
+  lbm_status st = device_view(h, n_arg, &nv, "n_dev");
+  if (st == LBM_OK) st = device_view(h, u_arg, &uv, "u_dev");
+  if (st != LBM_OK) return st;
+  double* n_dev = static_cast<double*>(nv);
+  double* u_dev = static_cast<double*>(uv);
   CallStream cs(h, stream);
   LBM_CUDA_TRY(h, cs.err);
   LBM_CUDA_TRY(h, launch_gather(h, s, n_dev, u_dev, nullptr));
@@ -549,13 +585,15 @@ double lbm_omega_drag_for_schmidt(double omega_visc, double schmidt) {
   return 1.0 / (0.5 + (1.0 / omega_visc - 0.5) / schmidt);
 }
 
-lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
-  if (!h) return LBM_EINVAL;
-  if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
-  if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set before stepping");
-  cudaSetDevice(h->dev);
-  CallStream cs(h, stream);
-  LBM_CUDA_TRY(h, cs.err);
+}  // extern "C"
+
+namespace {
+
+// The steps of lbm_step / lbm_step_record on the library's stream (the
+// caller's stream is ordered by the entry point).  While a recording call
+// steps (h->rec_dev set), every step sums the state it stores and its
+// record goes to slot k of the call's chunk.
+lbm_status step_impl(lbm_t* h, int nsteps) {
   const bool charged = h->cfg.bjerrum > 0.0;
   if (h->cfg.flags & LBM_FLAG_STEP_GRAPH) {
     Phase pg(h, 1);
@@ -592,14 +630,109 @@ lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
     }
     Phase ps(h, 2);
     // the last step of the call also sums the state it stores (diagnostics)
-    LBM_CUDA_TRY(h, launch_stream_collide(h, k == nsteps - 1));
+    LBM_CUDA_TRY(h, launch_stream_collide(h, h->rec_dev != nullptr || k == nsteps - 1));
     LBM_CUDA_TRY(h, ps.stop());
     LBM_CUDA_TRY(h, start_join(h));
     h->t_cnt[2] += 1;
     ++h->tstep;
+    if (h->rec_dev) {
+      // the sums straight into the host slot; the Poisson figures are known
+      // here
+      LBM_CUDA_TRY(h, launch_diag_reduce(h, h->rec_dev + (size_t)k * REC_LEN));
+      double* hslot = h->rec_host + (size_t)k * REC_LEN;
+      hslot[DIAG_NQ] = charged ? (double)h->last_iters : 0.0;
+      hslot[DIAG_NQ + 1] = charged ? h->last_res : 0.0;
+    }
     if (s == LBM_ENOCONV) return s;
   }
   if (h->timing && h->ev_used > 4096) LBM_CUDA_TRY(h, drain_timing(h));
+  return LBM_OK;
+}
+
+// The diagnostics of lbm_diagnostics from the deviation sums (DIAG_NQ
+// layout: species, momentum x y z, charge, bad flag).  Returns whether a
+// value is not finite or the flag is set.
+bool diag_from_sums(const lbm_t* h, const double* sums, double iters, double rel, double steps,
+                    double* out) {
+  const int S = h->S;
+  const double nf = (double)h->nfluid;
+  double zref = 0.0;
+  bool bad = sums[MAX_SPECIES + 4] != 0.0;
+  for (int s = 0; s < S; ++s) {
+    out[s] = nf * (double)h->nref[s] + sums[s];
+    zref += (double)h->valence[s] * (double)h->nref[s];
+  }
+  for (int d = 0; d < 3; ++d) out[S + d] = h->mass0 * sums[MAX_SPECIES + d];
+  out[S + 3] = nf * zref + sums[MAX_SPECIES + 3];
+  out[S + 4] = iters;
+  out[S + 5] = rel;
+  out[S + 6] = steps;
+  for (int k = 0; k < S + 4; ++k) bad = bad || !isfinite(out[k]);
+  return bad;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_step(lbm_t* h, int nsteps, void* stream) {
+  if (!h) return LBM_EINVAL;
+  if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
+  if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set before stepping");
+  cudaSetDevice(h->dev);
+  CallStream cs(h, stream);
+  LBM_CUDA_TRY(h, cs.err);
+  return step_impl(h, nsteps);
+}
+
+lbm_status lbm_step_record(lbm_t* h, int nsteps, double* out, void* stream) {
+  if (!h) return LBM_EINVAL;
+  if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
+  if (nsteps > 0 && !out) return fail(h, LBM_EINVAL, "out is NULL");
+  if (!species_complete(h)) return fail(h, LBM_EINVAL, "every species must be set before stepping");
+  cudaSetDevice(h->dev);
+  CallStream cs(h, stream);
+  LBM_CUDA_TRY(h, cs.err);
+  const int want = std::min(nsteps, REC_CHUNK);
+  if (want > h->rec_cap) {
+    if (h->hrec) cudaFreeHost(h->hrec);
+    h->hrec = nullptr;
+    h->hrec_dev = nullptr;
+    h->rec_cap = 0;
+    void* dp = nullptr;
+    if (cudaHostAlloc(&h->hrec, (size_t)want * REC_LEN * sizeof(double), cudaHostAllocMapped) !=
+            cudaSuccess ||
+        cudaHostGetDevicePointer(&dp, h->hrec, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, LBM_ENOMEM, "record buffer allocation failed");
+    }
+    h->hrec_dev = static_cast<double*>(dp);
+    h->rec_cap = want;
+  }
+  const int L = LBM_DIAG_LEN(h->S);
+  bool bad = false;
+  int done = 0;
+  while (done < nsteps) {
+    const int n = std::min(h->rec_cap, nsteps - done);
+    const int64_t t0 = h->tstep;
+    h->rec_dev = h->hrec_dev;
+    h->rec_host = h->hrec;
+    const lbm_status s = step_impl(h, n);
+    h->rec_dev = nullptr;
+    h->rec_host = nullptr;
+    // the steps taken (all n unless one failed) and their records
+    const int m = (int)(h->tstep - t0);
+    LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    for (int k = 0; k < m; ++k) {
+      const double* r = h->hrec + (size_t)k * REC_LEN;
+      bad = diag_from_sums(h, r, r[DIAG_NQ], r[DIAG_NQ + 1], (double)(t0 + k + 1),
+                           out + (size_t)(done + k) * L) || bad;
+    }
+    done += m;
+    if (s != LBM_OK) return s;
+    if (m < n) break;
+  }
+  if (bad) return fail(h, LBM_EUNSTABLE, "non-finite or non-positive density detected");
   return LBM_OK;
 }
 
@@ -751,19 +884,10 @@ lbm_status lbm_diagnostics(lbm_t* h, double* out) {
     bad = flag != 0;
   }
   // the reference parts n_ref x fluid nodes are exact
-  const int S = h->S;
-  const double nf = (double)h->nfluid;
-  double zref = 0.0;
-  for (int s = 0; s < S; ++s) {
-    out[s] = nf * (double)h->nref[s] + sums[s];
-    zref += (double)h->valence[s] * (double)h->nref[s];
-  }
-  for (int d = 0; d < 3; ++d) out[S + d] = h->mass0 * sums[MAX_SPECIES + d];
-  out[S + 3] = nf * zref + sums[MAX_SPECIES + 3];
-  out[S + 4] = (double)h->last_iters;
-  out[S + 5] = h->last_res;
-  out[S + 6] = (double)h->tstep;
-  for (int k = 0; k < S + 4; ++k) bad = bad || !isfinite(out[k]);
+  double full[DIAG_NQ];
+  for (int k = 0; k < MAX_SPECIES + 4; ++k) full[k] = sums[k];
+  full[MAX_SPECIES + 4] = bad ? 1.0 : 0.0;
+  bad = diag_from_sums(h, full, (double)h->last_iters, h->last_res, (double)h->tstep, out);
   if (bad) return fail(h, LBM_EUNSTABLE, "non-finite or non-positive density detected");
   return LBM_OK;
 }

@@ -20,6 +20,10 @@ constexpr int DIAG_SPREAD = 64;
 // kernel: MAX_SPECIES mass deviations, momentum x, y, z, charge, count of
 // non-finite or non-positive densities
 constexpr int DIAG_NQ = MAX_SPECIES + 5;
+// per-step record of lbm_step_record: the DIAG_NQ diagnostics sums, the
+// step's Poisson applications and final relative residual
+constexpr int REC_LEN = DIAG_NQ + 2;
+constexpr int REC_CHUNK = 4096;  // steps recorded between two host waits
 
 // Potential psi is held on the device as a signed 64-bit fixed-point number
 // with 52 fractional bits: psi = k * 2^-52 (|psi| < 2^11 = 2048, far beyond
@@ -52,6 +56,17 @@ constexpr int START_FULL_TERMS = START_K;
 // pipes: the instructions for 64-bit conversions issue on the FP64 pipe,
 // which is narrow on this GPU (ncu shows the residual kernels bound by it).
 //
+// Compensated FP32 accumulation (Knuth's two-sum): hi + lo carries the sum
+// to about twice the FP32 precision without FP64 arithmetic, which is slow
+// on this GPU.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
+}
+
 // i64_to_f32: |v| = hi 2^32 + lo; hi, lo >> 16 and lo & 0xffff (each below
 // 2^23) become floats exactly by placing them in the mantissa of 2^23 and
 // subtracting 2^23; two FMAs join them (two roundings: within about one ulp
@@ -226,6 +241,15 @@ struct lbm {
   uint32_t* charge_step = nullptr;
   const int* collide_skip = nullptr;  // skip flag of the stream/collide being captured
   double* hred = nullptr;   // pinned mirror
+  // per-step records (lbm_step_record): mapped pinned host slots (hrec,
+  // its device address hrec_dev), written by the reduce kernel behind each
+  // step; rec_dev / rec_host are set while a recording call steps (else
+  // NULL)
+  double* hrec = nullptr;
+  double* hrec_dev = nullptr;
+  int rec_cap = 0;
+  double* rec_dev = nullptr;
+  double* rec_host = nullptr;
   int* dflag = nullptr;
   int last_iters = 0;
   double last_res = 0.0;
@@ -313,7 +337,11 @@ cudaError_t launch_species_check(lbm_t* h, const double* n0_dev, const double* u
                                  int* nblk);
 // Sums the stream/collide kernel's per-CTA diagnostics partials into out
 // (DIAG_NQ doubles, device).
-cudaError_t launch_diag_reduce(lbm_t* h, double* out);
+// Reduces the stream/collide's per-CTA diagnostics partials into out (may
+// be mapped pinned host memory); iters / rel (device, or NULL) are copied
+// behind them.
+cudaError_t launch_diag_reduce(lbm_t* h, double* out, const int* iters = nullptr,
+                               const double* rel = nullptr);
 cudaError_t launch_links(lbm_t* h, const uint8_t* solid_dev);
 cudaError_t launch_psi_to_double(lbm_t* h, const int64_t* psi, double* out);
 cudaError_t launch_psi_from_double(lbm_t* h, const double* in, int64_t* psi);
@@ -334,6 +362,9 @@ lbm_status spectral_solve(lbm_t* h, double tol, int maxit, int* iters,
 // Whole-step graphs: build (if needed) and replay nsteps steps; reads the
 // device status once at the end.
 lbm_status spectral_graph_steps(lbm_t* h, int nsteps);
+// Device addresses of the current step's Poisson applications and final
+// relative residual in the graph status.
+void graph_status_ptrs(lbm_t* h, const int** iters, const double** rel);
 void spectral_graph_free(lbm_t* h);
 // Restarts the potential history of every solver (psi was set from outside
 // the steps).

@@ -167,7 +167,11 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const long long* part, in
 }
 
 // Gathers f(t) of species s and its moments n, u = sum c f / n (doubles,
-// from the deviations: n = n_ref + sum d, j = sum c d).
+// from the deviations: n = n_ref + sum d, j = sum c d).  The deviation sums
+// are compensated FP32 sums (about twice FP32 precision), 1/n an FP32
+// reciprocal refined by one Newton step r (2 - n r) in FP64: FP64-grade
+// moments with a handful of FP64 operations per node (FP64 arithmetic is
+// slow on this GPU).
 template <bool WALLS, int ST>
 __global__ void k_gather(const void* fin_v, const uint32_t* links, int s,
                          int nx, int ny, int nz, int64_t N, float nref,
@@ -188,21 +192,24 @@ __global__ void k_gather(const void* fin_v, const uint32_t* links, int s,
   site_xyz(i, nx, ny, x, y, z);
   const Nbr o = neighbours(x, y, z, nx, ny, nz);
   const T* fin = static_cast<const T*>(fin_v);
-  double m0 = nref, mx = 0, my = 0, mz = 0;
+  float m0h = 0.f, m0l = 0.f, mxh = 0.f, mxl = 0.f, myh = 0.f, myl = 0.f, mzh = 0.f, mzl = 0.f;
 #pragma unroll
   for (int p = 0; p < Q; ++p) {
     const float v = pull<ST, WALLS>(fin, N, s, p, i, upstream(o, p), lk, nref);
     if (f_out) f_out[(int64_t)p * N + i] = (double)WT(p) * nref + (double)v;
-    m0 += v;
-    mx += CX(p) * (double)v;
-    my += CY(p) * (double)v;
-    mz += CZ(p) * (double)v;
+    two_sum_add(m0h, m0l, v);
+    if (CX(p)) two_sum_add(mxh, mxl, CX(p) * v);
+    if (CY(p)) two_sum_add(myh, myl, CY(p) * v);
+    if (CZ(p)) two_sum_add(mzh, mzl, CZ(p) * v);
   }
-  if (n_out) n_out[i] = m0;
+  const double n = (double)nref + ((double)m0h + (double)m0l);
+  if (n_out) n_out[i] = n;
   if (u_out) {
-    u_out[i] = mx / m0;
-    u_out[N + i] = my / m0;
-    u_out[2 * N + i] = mz / m0;
+    double r = (double)__frcp_rn((float)n);
+    r = r * fma(-n, r, 2.0);
+    u_out[i] = ((double)mxh + (double)mxl) * r;
+    u_out[N + i] = ((double)myh + (double)myl) * r;
+    u_out[2 * N + i] = ((double)mzh + (double)mzl) * r;
   }
 }
 
@@ -429,10 +436,18 @@ __global__ void __launch_bounds__(256) k_species_check(const double* __restrict_
 
 // Sums the per-CTA diagnostics partials of the stream/collide kernel: one
 // CTA per quantity, FP64, in a fixed order (the result does not depend on
-// scheduling).
+// scheduling).  out may be mapped pinned host memory (a per-step record).
+// With iters / rel given (device), CTA 0 also copies them to out[DIAG_NQ],
+// out[DIAG_NQ + 1].
 __global__ void __launch_bounds__(256) k_diag_reduce(const double* __restrict__ part,
-                                                     int64_t nctas, double* __restrict__ out) {
+                                                     int64_t nctas, double* __restrict__ out,
+                                                     const int* __restrict__ iters,
+                                                     const double* __restrict__ rel) {
   const int k = blockIdx.x;
+  if (k == 0 && threadIdx.x == 0 && iters) {
+    out[DIAG_NQ] = (double)*iters;
+    out[DIAG_NQ + 1] = *rel;
+  }
   double v = 0.0;
   for (int64_t c = threadIdx.x; c < nctas; c += blockDim.x) v += part[c * DIAG_NQ + k];
   __shared__ double red[8];
@@ -582,8 +597,8 @@ cudaError_t launch_species_check(lbm_t* h, const double* n0_dev, const double* u
   return cudaGetLastError();
 }
 
-cudaError_t launch_diag_reduce(lbm_t* h, double* out) {
-  k_diag_reduce<<<DIAG_NQ, 256, 0, h->st>>>(h->dpart, h->dpart_ctas, out);
+cudaError_t launch_diag_reduce(lbm_t* h, double* out, const int* iters, const double* rel) {
+  k_diag_reduce<<<DIAG_NQ, 256, 0, h->st>>>(h->dpart, h->dpart_ctas, out, iters, rel);
   ++h->launches;
   return cudaGetLastError();
 }

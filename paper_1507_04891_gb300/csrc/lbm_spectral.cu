@@ -1564,6 +1564,12 @@ lbm_status build_step_graphs(lbm_t* h) {
 
 }  // namespace
 
+void graph_status_ptrs(lbm_t* h, const int** iters, const double** rel) {
+  GraphStatus* g = reinterpret_cast<GraphStatus*>(h->gstatus);
+  *iters = g ? &g->iters : nullptr;
+  *rel = g ? &g->rel : nullptr;
+}
+
 lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
   if (!h->spec->runs_fit) {
     h->err = "spectral Poisson solver: fluid run along z too long for shared memory";
@@ -1632,13 +1638,18 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     const long long redos_before = hs->redos;
     LBM_CUDA_TRY(h, cudaMemsetAsync(ds->need, 0, 8 * sizeof(int), h->st));  // need, needf
     // the call's last step replays the variant that sums the state it
-    // stores (diagnostics)
+    // stores (diagnostics); every step does when the call records them,
+    // and its record (the sums, applications and residual) is reduced and
+    // copied to the host slot right after the step
     for (int k = 0; k < n; ++k) {
-      const int d = (done + k == nsteps - 1) ? 1 : 0;
+      const int d = (h->rec_dev || done + k == nsteps - 1) ? 1 : 0;
       LBM_CUDA_TRY(h, cudaGraphLaunch(h->step_graph[h->cur][d], h->st));
       h->cur ^= 1;
       ++h->tstep;
       h->diag_valid = d == 1;
+      if (h->rec_dev)
+        LBM_CUDA_TRY(h, launch_diag_reduce(h, h->rec_dev + (size_t)(done + k) * REC_LEN,
+                                           &ds->iters, &ds->rel));
     }
     LBM_CUDA_TRY(h, cudaMemcpyAsync(hs, ds, sizeof(GraphStatus), cudaMemcpyDeviceToHost, h->st));
     LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));

@@ -108,17 +108,6 @@ __device__ bool solve_gram(const double* __restrict__ G, const double* __restric
   return ok;
 }
 
-// Compensated FP32 accumulation (Knuth's two-sum): hi + lo carries the sum
-// to about twice the FP32 precision without FP64 arithmetic, which is slow
-// on this GPU.
-__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
-  const float s = hi + x;
-  const float bp = s - hi;
-  const float e = (hi - (s - bp)) + (x - bp);
-  hi = s;
-  lo += e;
-}
-
 // Pass 1 (one cell per thread): D_0 = s(t) - s(t-1) against D_0 and the
 // stored D_1 .. D_K (ring slot of age j: (r - j) mod K); s(t) becomes the
 // previous source and D_0 replaces D_K (slot r mod K).  Products in FP32

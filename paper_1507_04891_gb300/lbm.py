@@ -34,7 +34,7 @@ EXPORTED = [
     "lbm_nn_init", "lbm_nn_collect", "lbm_nn_train", "lbm_nn_use", "lbm_nn_params",
     "lbm_nn_loss_grad", "lbm_nn_stats", "lbm_get_moments_noalloc", "lbm_state_len", "lbm_stream", "lbm_last_error",
     "lbm_set_species_dev", "lbm_get_moments_dev", "lbm_plane_fluxes", "lbm_omega_drag_for_schmidt",
-    "lbm_set_drag_matrix", "lbm_poisson_stats", "lbm_nn_infer",
+    "lbm_set_drag_matrix", "lbm_poisson_stats", "lbm_nn_infer", "lbm_step_record",
 ]
 
 
@@ -82,6 +82,8 @@ def load_library(path: str = LIB_PATH):
     lib.lbm_set_species.restype = I
     lib.lbm_step.argtypes = [P, I, V]
     lib.lbm_step.restype = I
+    lib.lbm_step_record.argtypes = [P, I, P, V]
+    lib.lbm_step_record.restype = I
     lib.lbm_synchronize.argtypes = [P]
     lib.lbm_synchronize.restype = I
     lib.lbm_get_moments.argtypes = [P, I, P, P]
@@ -398,6 +400,14 @@ class Lattice:
         return {"mass": out[:S].copy(), "momentum": out[S:S + 3].copy(), "charge": out[S + 3],
                 "poisson_iters": int(out[S + 4]), "poisson_residual": out[S + 5],
                 "steps": int(out[S + 6]), "unstable": st == LBM_EUNSTABLE, "raw": out}
+
+    def step_record(self, nsteps, stream=None):
+        """nsteps steps, each with its diagnostics read back (lbm_step_record):
+        an array of nsteps rows in the layout of diagnostics()["raw"]."""
+        out = np.empty((max(0, int(nsteps)), self.S + 7))
+        self._check(self._lib.lbm_step_record(self.h, int(nsteps), _ptr(out),
+                                              ctypes.c_void_p(stream) if stream else None))
+        return out
 
     def get_state(self):
         n = int(self._lib.lbm_state_len(self.h))

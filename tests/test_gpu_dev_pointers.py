@@ -91,3 +91,33 @@ def test_set_species_dev_rejects_invalid_fields():
     lat.set_species_dev(1, 1.0, 0.0, ok.data_ptr())
     d = lat.diagnostics()
     assert abs(d["mass"][0] - 256.0) < 1e-9 and not d["unstable"]
+
+
+def test_moments_into_pinned_host_memory_and_refusals():
+    """lbm_get_moments_dev writes pinned host buffers directly (the same
+    values as through device buffers); pageable host memory is refused before
+    any kernel runs."""
+    torch = pytest.importorskip("torch")
+    wl = WL.ternary_bulk(shape=(10, 8, 16), seed=61, spread=3e-3)
+    lat = lbm.Lattice(16, 8, 10, 3, omega_drag=1.0, bjerrum=0.7, poisson="fft")
+    for s in range(3):
+        lat.set_species(s, 1.0, wl.valence[s], wl.n0[s])
+    lat.step(3)
+    N = 16 * 8 * 10
+    dn = torch.empty(N, dtype=torch.float64, device="cuda")
+    du = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+    pn = torch.empty(N, dtype=torch.float64).pin_memory()
+    pu = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+    lat.get_moments_dev(1, dn.data_ptr(), du.data_ptr())
+    lat.get_moments_dev(1, pn.data_ptr(), pu.data_ptr())
+    lat.synchronize()
+    torch.cuda.synchronize()
+    assert np.array_equal(dn.cpu().numpy(), pn.numpy())
+    assert np.array_equal(du.cpu().numpy(), pu.numpy())
+    n_ref, u_ref = lat.get_moments(1)
+    assert np.array_equal(n_ref.ravel(), pn.numpy())
+    pageable = np.empty(N)
+    with pytest.raises(lbm.LBMError):
+        lat.get_moments_dev(1, pageable.ctypes.data, None)
+    with pytest.raises(lbm.LBMError):
+        lat.set_species_dev(0, 1.0, 0.0, pageable.ctypes.data)
