@@ -1606,11 +1606,12 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
   const int fails0 = hs->fails;
   const double slog0 = hs->start_log;
   const long long starts0 = hs->starts;
-  // Steps are replayed in chunks.  With the start from the solve history k
-  // is one.  Otherwise the distribution of the applications the steps
-  // needed (accumulated over at least CHUNK steps) sets the number k baked
-  // into the graphs (rebuilt only when k changes): the k of least expected
-  // cost per step.  A step costs its k applications; one that
+  // Steps are replayed in chunks.  The distribution of the applications
+  // the steps needed (accumulated over at least CHUNK steps whose start had
+  // the full history) sets the number k baked into the graphs (rebuilt only
+  // when k changes): the k of least expected cost per step.  With the start
+  // from the history that is one in FP32; 16-bit storage, whose rounding
+  // noise in the charge the history cannot predict, often needs two.  A step costs its k applications; one that
   // needs m > k also runs the while loop, m - k applications and residuals,
   // and the stream/collide again.  In units of a residual an application
   // costs about 4 and the stream/collide about 3.3 per FP32 species (3 per
@@ -1620,10 +1621,10 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
   const double costC = (h->cfg.storage == LBM_FP32 ? 3.3 : 3.0) * h->S;
   int done = 0;
   while (done < nsteps) {
-    // with the start from the history the steady state needs one
-    // application (the device-side loop adds what a step needs beyond
-    // it); otherwise the choice from the steps seen so far
-    const int pred = start_enabled(h) ? 1 : (sp->graph_pred > 0 ? sp->graph_pred : sp->last_iters);
+    // the choice from the steps seen so far; before any, one application
+    // with the start from the history (its steady state), else the last
+    // solve's count
+    const int pred = sp->graph_pred > 0 ? sp->graph_pred : (start_enabled(h) ? 1 : sp->last_iters);
     const int want = std::max(1, std::min(std::min(pred, h->cfg.poisson_maxit), Poisson::NSLOT - 1));
     if (sp->graph_k != want) {
       spectral_graph_free(h);
@@ -1665,7 +1666,9 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     // chunks and calls), or at the first chance
     for (int j = 0; j < 4; ++j) sp->need_acc[j] += hs->needf[j];
     const int tot = sp->need_acc[0] + sp->need_acc[1] + sp->need_acc[2] + sp->need_acc[3];
-    if (tot >= CHUNK || (sp->graph_pred == 0 && tot > 0)) {
+    // (with the start from the history the first decision also waits for
+    // CHUNK such steps: the first ones after a restart are not typical)
+    if (tot >= CHUNK || (sp->graph_pred == 0 && tot > 0 && !start_enabled(h))) {
       int best = 1;
       double best_cost = 0.0;
       for (int k = 1; k <= 4; ++k) {
@@ -1684,7 +1687,7 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
   }
   // a new choice of k is built now, so that the next call starts replaying
   // at once
-  if (sp->graph_pred > 0 && !start_enabled(h)) {
+  if (sp->graph_pred > 0) {
     const int want = std::max(1, std::min(std::min(sp->graph_pred, h->cfg.poisson_maxit),
                                           Poisson::NSLOT - 1));
     if (sp->graph_k != want) {
