@@ -159,7 +159,11 @@ struct Fmt<LBM_BF16_SHIFT> {
 
 // Counter-based random bits for stochastic rounding: one 32-bit mix of the
 // node index and the step per node, then one LCG step per stored value
-// (only the high bits of the LCG state are used).
+// (only the high bits of the LCG state are used).  The mix is the
+// low-bias 32-bit integer hash (xor-shift 16, multiply 0x7feb352d,
+// xor-shift 15, multiply 0x846ca68b, xor-shift 16) published by
+// C. Wellons' "hash prospector" search (2018); the LCG multiplier and
+// increment are the Numerical Recipes pair (Press et al.).
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   x ^= x >> 16;
   x *= 0x7feb352dU;
