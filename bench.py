@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--poisson", default="fft", choices=["mg", "sor", "fft"])
     ap.add_argument("--no-alt", action="store_true", help="skip the multigrid comparison run")
     ap.add_argument("--only", choices=["batched", "learned", "slit", "conductivity", "slit_transport",
-                                       "multigrid"], default=None,
+                                       "multigrid", "porous"], default=None,
                     help="run one extra measurement alone and print it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-slit and learned-guess measurements")
@@ -578,6 +578,7 @@ def run_porous(lbm, WL, steps=20, warm=5, local=0, n=256, params=None):
     wl = WL.porous_spheres(n=n, seed=1238)
     gen_s = time.perf_counter() - t0
     od = lbm.omega_drag_for_schmidt(1.0, 1.0)
+    nfluid = int((~wl.solid).sum())
     out = {"workload": "porous_%d^3 ternary, solid %.3f, multigrid, Sc 1" % (n, wl.meta["solid_fraction"]),
            "steps": steps, "warmup": warm, "input_seconds": gen_s}
     arms = ("plain", "history") + (("learned",) if params is not None else ())
@@ -618,6 +619,9 @@ def run_porous(lbm, WL, steps=20, warm=5, local=0, n=256, params=None):
                     "poisson_ms_per_step": tm["poisson_ms"] / steps,
                     "charge_ms_per_step": tm["charge_ms"] / steps,
                     "collide_ms_per_step": tm["collide_ms"] / steps,
+                    # stream/collide roofline: 152 B per fluid species-node
+                    "collide_frac_of_measured_hbm": 152.0 * 3 * nfluid / (tm["collide_ms"] / steps * 1e-3)
+                    / 1e9 / measured_peaks()[0],
                     "poisson_residual_last": d["poisson_residual"], "setup_seconds": setup_s}
         lat.destroy()
     return out
@@ -1094,6 +1098,8 @@ def main():
             res = run_slit_transport(lbm, WL)
         elif args.only == "conductivity":
             res = run_conductivity(lbm, WL, n=args.n if args.n != 128 else 64)
+        elif args.only == "porous":
+            res = run_porous(lbm, WL, steps=max(1, args.steps), warm=max(1, args.warmup), n=args.n)
         elif args.only == "multigrid":
             res = run_multigrid(lbm, WL, n=args.n,
                                 steps=min(max(1, args.steps), 50), warm=max(1, args.warmup))

@@ -1793,7 +1793,7 @@ cudaError_t vcycle(lbm_t* h) {
   for (int l = 1; l < last; ++l) {
     PoissonLevel& L = P.lev[l];
     if ((e = cudaMemsetAsync(L.e, 0, L.n * sizeof(float), h->st)) != cudaSuccess) return e;
-    if ((e = smooth_level(h, l, P.nu1)) != cudaSuccess) return e;
+    if ((e = smooth_level(h, l, P.nuc1)) != cudaSuccess) return e;
     PoissonLevel& C = P.lev[l + 1];
     k_restrict<<<nblocks(C.n, 256), 256, 0, h->st>>>(L.e, L.rhs, L.K, L.Dinv, make_cl(L),
                                                      make_cl(C), C.coarsened[0],
@@ -1835,7 +1835,7 @@ cudaError_t vcycle(lbm_t* h) {
                                                      C.coarsened[1], C.coarsened[2]);
     }
     ++h->launches;
-    if ((e = smooth_level(h, l, std::max(P.nu2, l == 0 ? 1 : 0), l == 0)) != cudaSuccess) return e;
+    if ((e = smooth_level(h, l, l == 0 ? std::max(P.nu2, 1) : P.nuc2, l == 0)) != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
