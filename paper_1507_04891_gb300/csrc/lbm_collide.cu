@@ -47,12 +47,21 @@ __global__ void __launch_bounds__(256, S >= 4 ? 1 : 2) k_stream_collide(const St
 #pragma unroll
   for (int s = 0; s < S; ++s) qm[s] = 0.f;
   uint32_t lk = 0;
-  bool active = i < (uint32_t)a.N;
-  if (WALLS && active) {
+  const bool inrange = i < (uint32_t)a.N;
+  bool active = inrange;
+  if (WALLS && inrange) {
     lk = a.links[i];
     active = !(lk & LINK_SOLID);
   }
-  if (active) {
+  // Wall nodes in a warp with fluid nodes run the same instructions with
+  // their loads switched off and store what they computed from zeros into
+  // their own slots (which no pull reads): every store of the warp then
+  // covers whole sectors, so the L2 need not fetch the rest of a sector a
+  // partial write leaves (measured on the porous box: about 130 MB of DRAM
+  // reads per launch at 128^3).  A warp of wall nodes only does nothing.
+  const bool any_fluid = WALLS ? __any_sync(0xffffffffu, active) : true;  // every lane votes
+  const bool work = inrange && any_fluid;
+  if (work) {
     int x, y, z;
     site_xyz(i, a.nx, a.ny, x, y, z);
     const Nbr o = neighbours(x, y, z, a.nx, a.ny, a.nz);
@@ -60,14 +69,33 @@ __global__ void __launch_bounds__(256, S >= 4 ? 1 : 2) k_stream_collide(const St
     T* __restrict__ fout = static_cast<T*>(a.fout);
     const int64_t N = a.N;
 
-    // stored h_p = (f_p - w_p n_ref) / (w_p n_ref) of every species
+    // stored h_p = (f_p - w_p n_ref) / (w_p n_ref) of every species, pulled
+    // from r - c_p.  The addresses do not wait for the link word: every
+    // lane loads from its upstream nodes at once; then, in a warp with a
+    // fluid node next to a wall, the directions whose upstream node is a
+    // wall node take the node's own reversed value (halfway bounce-back).
+    // Wall lanes compute from zeros.
     float f[S][Q];
 #pragma unroll
     for (int p = 0; p < Q; ++p) {
       const int d = upstream(o, p);
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        f[s][p] = pull_h<ST, WALLS>(fin, N, s, p, i, d, lk);
+      for (int s = 0; s < S; ++s) f[s][p] = pull_h<ST, false>(fin, N, s, p, i, d, 0u);
+    }
+    if (WALLS) {
+      const uint32_t wb = active ? (lk & ~LINK_SOLID) : 0u;
+      if (__any_sync(__activemask(), wb != 0u)) {
+#pragma unroll
+        for (int p = 1; p < Q; ++p)
+#pragma unroll
+          for (int s = 0; s < S; ++s)
+            if ((wb >> p) & 1u) f[s][p] = Fmt<ST>::ldh(fin + (int64_t)(s * Q + OPP(p)) * N + i);
+      }
+      if (!active) {
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+          for (int p = 0; p < Q; ++p) f[s][p] = 0.f;
       }
     }
 
@@ -104,7 +132,7 @@ __global__ void __launch_bounds__(256, S >= 4 ? 1 : 2) k_stream_collide(const St
       jx[s] = r * mx;
       jy[s] = r * my;
       jz[s] = r * mz;
-      if (DIAG && (!(n[s] > 0.f) || !isfinite(n[s]))) qbad = 1.f;
+      if (DIAG && active && (!(n[s] > 0.f) || !isfinite(n[s]))) qbad = 1.f;
     }
 
     float ntot = 0.f, Jx = 0.f, Jy = 0.f, Jz = 0.f;
@@ -215,7 +243,7 @@ __global__ void __launch_bounds__(256, S >= 4 ? 1 : 2) k_stream_collide(const St
       }
       const float h0 = Fmt<ST>::sth_sr(fout + (int64_t)(s * Q) * N + i, (mh[s] - moved) * INV_WT(0),
                                        lcg_next(rnd));
-      if (DIAG) {
+      if (DIAG && active) {
         const float r = a.nref[s];
         qm[s] = r * (WT(0) * h0 + moved);
         qjx += r * mjx;
