@@ -171,12 +171,14 @@ struct Poisson {
   int cyc_kernels = 0;
   bool cyc_failed = false;
   // smoothing sweeps before / after the coarse correction: fine box and the
-  // shared-memory sub-cycle 2 / 2; the grid-kernel coarse levels between
-  // them 1 / 1 (measured at 256^3: 0.61 ms per V-cycle against 0.65 for
-  // 2 / 2, 13.9 V-cycles per step against 13.5, 4% less Poisson time; the
-  // sub-cycle at 1 / 1 added cycles and time)
+  // shared-memory sub-cycle (nu), the grid-kernel coarse levels between them
+  // (nuc).  1 / 1 on the grid coarse levels saved 7% per V-cycle at 256^3
+  // but cost cycles: less Poisson time for long solves from the previous
+  // potential (13.9 cycles a step), more for the ~2-cycle solves from the
+  // history start (porous 256^3: 1.78 against 1.74 ms a step; bulk 128^3:
+  // 3.35 against 2.82 cycles), so all levels keep 2 / 2.
   int nu1 = 2, nu2 = 2;
-  int nuc1 = 1, nuc2 = 1;
+  int nuc1 = 2, nuc2 = 2;
 };
 
 // History of the start of the Poisson solves (lbm_start.cu), device memory.
