@@ -1273,7 +1273,15 @@ struct GraphStatus {
   long long starts;    // steps counted in start_log
   int spec_skip;       // the current step does not speculate (start from a short history)
   long long redos;     // steps that ran the stream/collide after the loop
+  int more;            // the first test of the step asks for more applications
 };
+
+// First node of the rerun branch: the loop runs when the step's first test
+// asked for more applications (it reruns the stream/collide also when the
+// step did not speculate and the baked applications were enough).
+__global__ void k_loop_seed(const GraphStatus* st, cudaGraphConditionalHandle cond) {
+  cudaGraphSetConditional(cond, st->more ? 1u : 0u);
+}
 
 // Whether the step runs its stream/collide speculatively, beside the test
 // after the k baked applications: only when the start used the full
@@ -1329,14 +1337,18 @@ __global__ void k_graph_check(const float* __restrict__ acc, GraphStatus* st, do
     st->iters += 1;
   }
   const bool more = !conv && st->iters < maxit;
-  cudaGraphSetConditional(cond, more ? 1u : 0u);
   // the stream/collide ran beside this test on the potential after k
   // applications: it runs again after the loop when the loop runs, or when
-  // the step did not speculate
+  // the step did not speculate.  The first test opens that branch (its loop
+  // condition is seeded from `more` inside it); the tests in the loop
+  // continue it.
   if (first) {
+    st->more = more ? 1 : 0;
     const bool again = more || st->spec_skip;
     cudaGraphSetConditional(redo, again ? 1u : 0u);
     if (again) st->redos += 1;
+  } else {
+    cudaGraphSetConditional(cond, more ? 1u : 0u);
   }
   st->rel = snk > 0.0 ? sqrt(rnk / snk) : 0.0;
   // applications this step needed, recorded once per step: at the first
@@ -1389,8 +1401,9 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
   const int* terms = start_enabled(h) ? start_terms_dev(h) : nullptr;
   cudaGraph_t G = nullptr;
   LBM_CUDA_TRY(h, cudaGraphCreate(&G, 0));
-  cudaGraphConditionalHandle cond, redo;
-  LBM_CUDA_TRY(h, cudaGraphConditionalHandleCreate(&cond, G, 0, cudaGraphCondAssignDefault));
+  // redo: the if node of the rerun branch (in G); cond: the loop inside it
+  // (created on the branch's body graph below)
+  cudaGraphConditionalHandle cond = 0, redo;
   LBM_CUDA_TRY(h, cudaGraphConditionalHandleCreate(&redo, G, 0, cudaGraphCondAssignDefault));
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
   cudaStream_t main = h->st, side = nullptr, side2 = nullptr;
@@ -1469,7 +1482,44 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
     cudaGraph_t Gc = nullptr;
     e = cudaStreamEndCapture(main, &Gc);
     if (e == cudaSuccess) e = ec;
-    // the conditional while node: one more application, its residual, the test
+    // The rerun branch, an if node after the speculative stream/collide and
+    // the fit: a kernel that seeds the loop condition from the first test,
+    // the while loop of [application, residual, test], then the
+    // stream/collide again on the refined potential.  A step that converged
+    // after its baked applications evaluates this one conditional node only.
+    const int64_t l1 = h->launches;
+    cudaGraphNode_t inode = nullptr;
+    cudaGraph_t ibody = nullptr;
+    if (e == cudaSuccess) {
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = redo;
+      cp.conditional.type = cudaGraphCondTypeIf;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&inode, G, deps.data(), nullptr, deps.size(), &cp);
+      if (e == cudaSuccess) ibody = cp.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess)
+      e = cudaGraphConditionalHandleCreate(&cond, ibody, 0, cudaGraphCondAssignDefault);
+    std::vector<cudaGraphNode_t> sdeps;
+    if (e == cudaSuccess) {
+      e = cudaStreamBeginCaptureToGraph(main, ibody, nullptr, nullptr, 0, mode);
+      if (e == cudaSuccess) {
+        k_loop_seed<<<1, 1, 0, main>>>(gs, cond);
+        ++h->launches;
+        cudaError_t eb = cudaGetLastError();
+        if (eb == cudaSuccess) {
+          cudaStreamCaptureStatus cs;
+          const cudaGraphNode_t* d = nullptr;
+          size_t nd = 0;
+          eb = cudaStreamGetCaptureInfo(main, &cs, nullptr, nullptr, &d, nullptr, &nd);
+          if (eb == cudaSuccess) sdeps.assign(d, d + nd);
+        }
+        cudaGraph_t sg = nullptr;
+        e = cudaStreamEndCapture(main, &sg);
+        if (e == cudaSuccess) e = eb;
+      }
+    }
     cudaGraphNode_t cnode = nullptr;
     cudaGraph_t body = nullptr;
     if (e == cudaSuccess) {
@@ -1478,10 +1528,10 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
       cp.conditional.handle = cond;
       cp.conditional.type = cudaGraphCondTypeWhile;
       cp.conditional.size = 1;
-      e = cudaGraphAddNode(&cnode, G, deps.data(), nullptr, deps.size(), &cp);
+      e = cudaGraphAddNode(&cnode, ibody, sdeps.data(), nullptr, sdeps.size(), &cp);
       if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
     }
-    const int64_t l1 = h->launches;
+    const int64_t l2 = h->launches;
     if (e == cudaSuccess) {
       e = cudaStreamBeginCaptureToGraph(main, body, nullptr, nullptr, 0, mode);
       if (e == cudaSuccess) {
@@ -1498,22 +1548,9 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
         if (e == cudaSuccess) e = eb;
       }
     }
-    const int64_t l2 = h->launches;
-    // the conditional if node: the stream/collide again, on the potential
-    // the loop refined
-    cudaGraphNode_t inode = nullptr;
-    cudaGraph_t ibody = nullptr;
+    const int64_t l3 = h->launches;
     if (e == cudaSuccess) {
-      cudaGraphNodeParams cp = {};
-      cp.type = cudaGraphNodeTypeConditional;
-      cp.conditional.handle = redo;
-      cp.conditional.type = cudaGraphCondTypeIf;
-      cp.conditional.size = 1;
-      e = cudaGraphAddNode(&inode, G, &cnode, nullptr, 1, &cp);
-      if (e == cudaSuccess) ibody = cp.conditional.phGraph_out[0];
-    }
-    if (e == cudaSuccess) {
-      e = cudaStreamBeginCaptureToGraph(main, ibody, nullptr, nullptr, 0, mode);
+      e = cudaStreamBeginCaptureToGraph(main, ibody, &cnode, nullptr, 1, mode);
       if (e == cudaSuccess) {
         // from the step's input populations again, into the same output as
         // the speculative launch (which flipped the parity while capturing)
@@ -1525,8 +1562,8 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
       }
     }
     h->graph_kernels_fixed = (int)(l1 - l0);
-    h->graph_kernels_iter = (int)(l2 - l1);
-    h->graph_kernels_redo = (int)lc;
+    h->graph_kernels_iter = (int)(l3 - l2);
+    h->graph_kernels_redo = (int)lc + 1;  // the seed and the stream/collide
   }
   h->launches = l0;
   h->cur = saved_cur;
