@@ -248,6 +248,12 @@ struct lbm {
   // step counter advanced by the charge path while graph steps are captured
   uint32_t* charge_step = nullptr;
   const int* collide_skip = nullptr;  // skip flag of the stream/collide being captured
+  // extra duties of the start's bookkeeping kernel while a step graph is
+  // captured: the speculation flag and the first norm slot to clear
+  int* mark_skip_out = nullptr;
+  float* mark_clear = nullptr;
+  int mark_nclear = 0;
+  bool slot0_cleared = false;  // the start's kernel cleared norm slot 0 (spec_fwd skips it)
   double* hred = nullptr;   // pinned mirror
   // per-step records (lbm_step_record): mapped pinned host slots (hrec,
   // its device address hrec_dev), written by the reduce kernel behind each

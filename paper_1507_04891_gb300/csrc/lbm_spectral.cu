@@ -1104,7 +1104,9 @@ cudaError_t spec_fwd(lbm_t* h, int slot) {
   Poisson& P = h->ps;
   const SpecArgs a = args_of(s);
   float* out = norm_slot(h, slot);
-  cudaError_t e = clear_slot(h, slot);
+  cudaError_t e = cudaSuccess;
+  if (slot == 0 && h->slot0_cleared) h->slot0_cleared = false;  // cleared with the start
+  else e = clear_slot(h, slot);
   if (e != cudaSuccess) return e;
   const unsigned gp = (unsigned)((s->nplanes + s->ppc - 1) / s->ppc);
   k_plane_fwd<<<gp, s->ppc << s->lgtp, s->plane_smem, h->st>>>(
@@ -1437,14 +1439,23 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
     h->charge_step = nullptr;
     // the start from the history, then the fit for the next step on the
     // second side stream, beside the applications
-    if (ec == cudaSuccess) ec = start_apply(h, false);
+    // the start's bookkeeping kernel also decides the speculation and
+    // clears the first norm slot (when the start is on)
     const bool fit = start_enabled(h);
+    if (fit) {
+      h->mark_skip_out = &gs->spec_skip;
+      h->mark_clear = norm_slot(h, 0);
+      h->mark_nclear = 2 * NACC;
+    }
+    if (ec == cudaSuccess) ec = start_apply(h, false);
+    h->mark_skip_out = nullptr;
+    h->mark_clear = nullptr;
     if (ec == cudaSuccess && fit) ec = cudaEventRecord(fork2, main);
     if (ec == cudaSuccess && fit) ec = cudaStreamWaitEvent(side2, fork2, 0);
     if (ec == cudaSuccess && fit) ec = start_fit(h, side2, true);
     if (ec == cudaSuccess && fit) ec = cudaEventRecord(join2, side2);
     if (ec == cudaSuccess) ec = spec_means(h);
-    if (ec == cudaSuccess) {
+    if (ec == cudaSuccess && !fit) {
       k_spec_decide<<<1, 1, 0, main>>>(terms, gs);
       ++h->launches;
       ec = cudaGetLastError();
@@ -1568,6 +1579,9 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
   h->launches = l0;
   h->cur = saved_cur;
   h->diag_valid = saved_diag;
+  h->slot0_cleared = false;
+  h->mark_skip_out = nullptr;
+  h->mark_clear = nullptr;
   h->st = main;
   cudaGraphExec_t ex = nullptr;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, G, cudaGraphInstantiateFlagUseNodePriority);
