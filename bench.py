@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--no-extrapolation", action="store_true",
                     help="spectral solves start from the previous potential, not its "
                          "extrapolation in time")
+    ap.add_argument("--charge-pass", action="store_true",
+                    help="charge density by a separate pass over the charged populations "
+                         "(LBM_FLAG_CHARGE_PASS), not scattered by the previous stream/collide")
     return ap.parse_args()
 
 
@@ -100,10 +103,10 @@ def collide_source_hash():
     return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
-def kernel_traffic(storage="fp32"):
+def kernel_traffic(storage="fp32", variant=""):
     """DRAM bytes per stream/collide launch from the committed ncu summary,
     valid only while the kernel source is unchanged (hash recorded there)."""
-    path = os.path.join(ROOT, "profiles", "stream_collide_ternary_128_%s.md" % storage)
+    path = os.path.join(ROOT, "profiles", "stream_collide_ternary_128_%s%s.md" % (storage, variant))
     try:
         h = collide_source_hash()
         rec = {}
@@ -860,12 +863,13 @@ def run_ours(args, rank, world, local):
     warm = max(3, args.warmup)
     K = args.steps
 
-    def make(poisson, graph=False, omega_drag=None, storage=None):
+    def make(poisson, graph=False, omega_drag=None, storage=None, charge_pass=False):
         return lbm.Lattice(n, n, n, S, omega_visc=wl.omega_visc,
                            omega_drag=od if omega_drag is None else omega_drag, bjerrum=wl.bjerrum,
                            storage=storage or args.storage, poisson=poisson, poisson_tol=1e-8,
                            poisson_maxit=500, device=local, step_graph=graph,
-                           extrapolate=not args.no_extrapolation)
+                           extrapolate=not args.no_extrapolation,
+                           charge_pass=charge_pass or args.charge_pass)
 
     def barrier():
         replicas.barrier(world)
@@ -874,10 +878,11 @@ def run_ours(args, rank, world, local):
     def max_over_ranks(x):
         return replicas.max_over_ranks(x, world, device="cuda")
 
-    def timed(poisson, sample_clocks, graph=False, omega_drag=None, storage=None, keep=False):
+    def timed(poisson, sample_clocks, graph=False, omega_drag=None, storage=None, keep=False,
+              charge_pass=False):
         """W warm-up steps, then K steps timed with CUDA events on the
         library's stream; phase times from the library's own events."""
-        lat = make(poisson, graph, omega_drag, storage)
+        lat = make(poisson, graph, omega_drag, storage, charge_pass)
         for s in range(S):
             lat.set_species(s, 1.0, wl.valence[s], wl.n0[s])
         stream = torch.cuda.ExternalStream(lat.stream, device=dev)
@@ -925,9 +930,13 @@ def run_ours(args, rank, world, local):
         tm, host_run = tm_head, None
     collide_ms = tm["collide_ms"] / max(1, tm["collide_launches"])
     bpl = BYTES_PER_SPECIES_SITE[args.storage] * S * N
+    # with the charge scatter (FP32, x rows of whole warps, no walls) the
+    # stream/collide also adds the next step's 8-byte source per node
+    scatter = args.storage == "fp32" and n % 32 == 0 and not args.charge_pass
+    bpl_head = bpl + (8 * N if scatter else 0)
     peak, peak_kind = measured_peaks()
-    achieved = bpl / (collide_ms / 1e3) / 1e9
-    traffic = kernel_traffic(args.storage) if n == 128 else None
+    achieved = bpl_head / (collide_ms / 1e3) / 1e9
+    traffic = kernel_traffic(args.storage, "" if scatter else "_charge_pass") if n == 128 else None
 
     # the same workload with 16-bit shifted storage (FP32 arithmetic), graph
     # steps for the rate and host steps for the kernel time; the fields after
@@ -960,6 +969,25 @@ def run_ours(args, rank, world, local):
                              "algorithmic_bytes_per_launch": b16, "collide_ms": cms,
                              "traffic": kernel_traffic(st) if n == 128 else None}}
     lat_head.destroy()
+
+    # the same workload with the charge density from a separate pass over
+    # the charged populations (LBM_FLAG_CHARGE_PASS) instead of the
+    # previous stream/collide's scatter: whole steps, and the stream/collide
+    # without the scatter against its roofline
+    charge_pass = None
+    if scatter and not args.no_alt:
+        tc, tmc, _, _ = timed(args.poisson, False, graph=graph_head, charge_pass=True)
+        th, tmh, _, _ = timed(args.poisson, False, graph=False, charge_pass=True)
+        cms = tmh["collide_ms"] / max(1, tmh["collide_launches"])
+        charge_pass = {
+            "value": rate(tc), "ms_per_step": tc / K, "poisson_iters_per_step": tmc["poisson_iters"] / K,
+            "phase_ms_per_step": {"charge": tmh["charge_ms"] / K, "poisson": tmh["poisson_ms"] / K,
+                                  "stream_collide": tmh["collide_ms"] / K},
+            "roofline": {"kernel": "k_stream_collide (no scatter)", "bound": "hbm",
+                         "achieved": bpl / (cms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": bpl / (cms / 1e3) / 1e9 / peak, "peak_source": peak_kind,
+                         "algorithmic_bytes_per_launch": bpl, "collide_ms": cms,
+                         "traffic": kernel_traffic("fp32", "_charge_pass") if n == 128 else None}}
 
     # the same workload with the multigrid solver, for comparison
     alt = None
@@ -1042,6 +1070,8 @@ def run_ours(args, rank, world, local):
                        "poisson": args.poisson, "poisson_tol": 1e-8, "storage": args.storage,
                        "poisson_start": ("previous psi" if args.no_extrapolation
                                          else "history projection (5 source differences)"),
+                       "charge_density": ("scattered by the previous stream/collide" if scatter
+                                          else "separate pass over the charged populations"),
                        "l2": "not flushed: inputs larger than L2 (2 x %.0f MB population lattices)"
                              % (BYTES_PER_SPECIES_SITE[args.storage] / 2 * S * N / 1e6),
                        "steps": "cuda_graph" if graph_head else "host",
@@ -1050,10 +1080,11 @@ def run_ours(args, rank, world, local):
             "phase_ms_per_step": {"charge": tm["charge_ms"] / K,
                                   "poisson": tm["poisson_ms"] / K,
                                   "stream_collide": tm["collide_ms"] / K},
-            "roofline": {"kernel": "k_stream_collide", "bound": "hbm", "achieved": achieved,
+            "roofline": {"kernel": "k_stream_collide" + (" (with the charge scatter)" if scatter else ""),
+                         "bound": "hbm", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_kind,
-                         "algorithmic_bytes_per_launch": bpl, "collide_ms": collide_ms,
+                         "algorithmic_bytes_per_launch": bpl_head, "collide_ms": collide_ms,
                          "traffic": traffic},
             "clocks": clk,
             "gpu_launches": tm_head["kernel_launches"],
@@ -1067,6 +1098,7 @@ def run_ours(args, rank, world, local):
                     "steps_recorded": int(e2e_rows.shape[0]),
                     "final_cation_mass": e2e_mass},
             "storage_variants": storage_lines or None,
+            "charge_pass": charge_pass,
             "poisson_alternative": alt,
             "sc100": sc100,
             "host_steps": host_run,

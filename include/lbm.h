@@ -105,6 +105,17 @@ typedef struct {
  * this library's solver.                                                  */
 #define LBM_FLAG_NO_EXTRAPOLATION 2
 
+/* LBM_FLAG_CHARGE_PASS: the charge density rho_e(t) of Eq. (Poisson) is
+ * computed at the start of every step by a pass that pulls the charged
+ * species' populations f(t).  Without the flag, on periodic FP32 lattices
+ * without walls whose nx is a multiple of 32, the stream/collide of step
+ * t - 1 adds each stored charged population to the node it streams to
+ * (rho_e(r, t) = sum_a z_a sum_p f*_p^a(r - c_p, t - 1)), in 64-bit fixed
+ * point, so the step reads those populations once; the results agree with
+ * the pass up to FP32 rounding of the per-node sums.  The paper has no
+ * counterpart: a property of this library's step.                        */
+#define LBM_FLAG_CHARGE_PASS 4
+
 /* Fills *cfg with defaults: omega_visc = 1, omega_drag = 1, l_B = 0,
  * FP32 storage, multigrid Poisson, tol 1e-8, maxit 200, device 0.        */
 void lbm_config_default(lbm_config* cfg);

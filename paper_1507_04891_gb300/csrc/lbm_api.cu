@@ -297,6 +297,19 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
     s = dev_alloc(h, &h->ps.psi[0], N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.psi[1], N);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.src, N);
+    // the charge scatter: FP32 storage (for 16-bit storage the pass is
+    // faster: its stream/collide is bound by instruction issue, and the
+    // scatter's instructions cost more than the pass), periodic (walls may
+    // still come, lbm_set_walls turns it off), x rows of whole warps
+    h->scat_on = !(c.flags & LBM_FLAG_CHARGE_PASS) && c.storage == LBM_FP32 && c.nx % 32 == 0;
+    if (s == LBM_OK && h->scat_on) {
+      s = dev_alloc(h, &h->scat_acc, N);
+      if (s == LBM_OK) s = dev_alloc(h, &h->scat_tot, 3);
+      if (s == LBM_OK) {
+        cudaMemset(h->scat_acc, 0, N * sizeof(int64_t));
+        cudaMemset(h->scat_tot, 0, 3 * sizeof(unsigned long long));
+      }
+    }
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.dsum, 1 + 2 * Poisson::NSLOT);
     if (s == LBM_OK) s = dev_alloc(h, &h->ps.part, (size_t)((N + 63) / 64));
     if (s == LBM_OK && cudaMallocHost(&h->ps.hsum, (1 + 2 * Poisson::NSLOT) * sizeof(double)) != cudaSuccess)
@@ -326,6 +339,8 @@ void lbm_destroy(lbm_t* h) {
   if (h->own) cudaStreamSynchronize(h->own);
   cudaFree(h->f[0]);
   cudaFree(h->f[1]);
+  cudaFree(h->scat_acc);
+  cudaFree(h->scat_tot);
   cudaFree(h->links);
   cudaFree(h->wallq);
   cudaFree(h->wsrc);
@@ -406,6 +421,8 @@ lbm_status lbm_set_walls(lbm_t* h, const uint8_t* solid, const double* sigma) {
   if (s != LBM_OK) return s;
   LBM_CUDA_TRY(h, cudaMemcpy(sc.p, solid, N, cudaMemcpyHostToDevice));
   h->has_walls = true;
+  h->scat_on = false;  // the charge pass handles walls
+  h->scat_valid = false;
   LBM_CUDA_TRY(h, launch_links(h, (const uint8_t*)sc.p));
   if (charged_walls) {
     if (!h->wallq && (s = dev_alloc(h, &h->wallq, N)) != LBM_OK) return s;
@@ -917,6 +934,7 @@ lbm_status lbm_set_state(lbm_t* h, const float* state, int64_t step) {
   LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
   h->tstep = step;
   h->diag_valid = false;
+  h->scat_valid = false;
   return potential_history_reset(h);
 }
 
@@ -1085,6 +1103,7 @@ lbm_status lbm_autotune(lbm_t* h, double* out) {
   h->charge_threads = tq;
   spectral_graph_free(h);  // graphs baked the old sizes
   h->psi_valid = false;
+  h->scat_valid = false;  // the timed charge launches took the scattered source
   if (out) {
     out[0] = tc;
     out[1] = best_c;

@@ -35,7 +35,77 @@ namespace {
 //      and a count of nodes whose density entering the step was not finite
 //      and positive, written to a[blockIdx.x * DIAG_NQ + k].
 // ---------------------------------------------------------------------------
-template <int S, bool WALLS, bool CHARGED, int ST, bool DIAG, bool PAIR>
+// Charge scatter: the target of a stored population h*_p(r) is r + c_p
+// (it is pulled there at the next step).  Targets are grouped by their row
+// offset (dy, dz) = (c_y, c_z), nine groups; GRP numbers them.  Five groups
+// also hold directions with an x component (dy = 0 or dz = 0); XGRP numbers
+// those.  Per node: q0[GRP] sums the contributions to (x, y + dy, z + dz),
+// qp[XGRP] those to x + 1, qm[XGRP] those to x - 1.
+__host__ __device__ __forceinline__ constexpr int GRP(int p) { return (CZ(p) + 1) * 3 + (CY(p) + 1); }
+__host__ __device__ __forceinline__ constexpr int XGRP_OF(int dy, int dz) {
+  return dz == 0 ? (dy == 0 ? 0 : (dy == 1 ? 1 : 2)) : (dz == 1 ? 3 : 4);
+}
+__host__ __device__ __forceinline__ constexpr int XGRP(int p) { return XGRP_OF(CY(p), CZ(p)); }
+
+// (p is a constant once the direction loops are unrolled, so the sums stay
+// in registers)
+__device__ __forceinline__ void scat_add(int p, float (&q0)[9], float (&qp)[5], float (&qm)[5],
+                                         float v) {
+  if (CX(p) == 0) q0[GRP(p)] += v;
+  else if (CX(p) == 1) qp[XGRP(p)] += v;
+  else qm[XGRP(p)] += v;
+}
+
+// A warp holds 32 consecutive nodes of one x row (nx is a multiple of 32).
+// Per target group (dy, dz) a lane adds the contributions that reach its own
+// x: its own ones with c_x = 0, those of lane - 1 with c_x = +1 and of
+// lane + 1 with c_x = -1 (register shuffles); rows of one warp wrap inside
+// the warp, and for wider rows the first and last lane send the
+// contributions that cross into the neighbouring warp themselves.  Each
+// sum goes to the next step's source with one 64-bit integer atomic per
+// target (exact, so the order in which warps add does not matter; the
+// FP32 sums are formed in a fixed order, so every run gives the same
+// source).  The node's own target also receives the reference part of the
+// source, once per node.  (x, y, z): the lane's node.
+__device__ __forceinline__ void scatter_charge(const StepArgs& a, int x, int y, int z,
+                                               float (&c0)[9], const float (&cp)[5],
+                                               const float (&cm)[5]) {
+  const int lane = threadIdx.x & 31;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const bool one = nx == 32;  // the row is this warp: the shuffles wrap it
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const float fl = __shfl_sync(0xffffffffu, cp[j], (lane + 31) & 31);  // lane - 1 sends to x
+    const float fr = __shfl_sync(0xffffffffu, cm[j], (lane + 1) & 31);   // lane + 1 sends to x
+    const int g = j == 0 ? 4 : (j == 1 ? 5 : (j == 2 ? 3 : (j == 3 ? 7 : 1)));  // GRP of XGRP j
+    if (one || lane != 0) c0[g] += fl;
+    if (one || lane != 31) c0[g] += fr;
+  }
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(a.scat_acc);
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+  const int64_t nxy = (int64_t)nx * ny;
+  const int64_t rowz[3] = {(int64_t)zm * nxy, (int64_t)z * nxy, (int64_t)zp * nxy};
+  const int rowy[3] = {ym * nx, y * nx, yp * nx};
+#pragma unroll
+  for (int g = 0; g < 9; ++g) {
+    long long q = (long long)f32_to_i64_rn(c0[g]);
+    if (g == 4) q += a.src_ref;
+    atomicAdd(acc + rowz[g / 3] + rowy[g % 3] + x, (unsigned long long)q);
+  }
+  if (!one && (lane == 0 || lane == 31)) {
+    // the contributions that cross into the neighbouring warp of the row
+    const int xt = lane == 0 ? (x == 0 ? nx - 1 : x - 1) : (x == nx - 1 ? 0 : x + 1);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const int g = j == 0 ? 4 : (j == 1 ? 5 : (j == 2 ? 3 : (j == 3 ? 7 : 1)));
+      const float v = lane == 0 ? cm[j] : cp[j];
+      atomicAdd(acc + rowz[g / 3] + rowy[g % 3] + xt, (unsigned long long)(long long)f32_to_i64_rn(v));
+    }
+  }
+}
+
+template <int S, bool WALLS, bool CHARGED, int ST, bool DIAG, bool PAIR, bool SCAT>
 __global__ void __launch_bounds__(256, S >= 4 ? 1 : 2) k_stream_collide(const StepArgs a) {
   using T = typename Fmt<ST>::T;
   // a speculative launch the step has decided against (same for every
@@ -46,6 +116,12 @@ __global__ void __launch_bounds__(256, S >= 4 ? 1 : 2) k_stream_collide(const St
   float qm[S], qjx = 0.f, qjy = 0.f, qjz = 0.f, qbad = 0.f;
 #pragma unroll
   for (int s = 0; s < S; ++s) qm[s] = 0.f;
+  // (SCAT) charge sent to the next step's source, per target group
+  float c0[9], cp[5], cm[5];
+#pragma unroll
+  for (int g = 0; g < 9; ++g) c0[g] = 0.f;
+#pragma unroll
+  for (int g = 0; g < 5; ++g) cp[g] = cm[g] = 0.f;
   uint32_t lk = 0;
   const bool inrange = i < (uint32_t)a.N;
   bool active = inrange;
@@ -230,6 +306,13 @@ __global__ void __launch_bounds__(256, S >= 4 ? 1 : 2) k_stream_collide(const St
                                            fout + (int64_t)(s * Q + p + 1) * N + i,
                                            omm * f[s][p + 1] + (even - odd), lcg_next(rnd));
         moved += WT(p) * (hs.x + hs.y);  // same weight for p and p+1
+        if constexpr (SCAT) {
+          // charge these two stored values carry to r + c_p and r - c_p
+          // (zero for a neutral species)
+          const float kw = a.scat_k[s] * WT(p);
+          scat_add(p, c0, cp, cm, kw * hs.x);
+          scat_add(p + 1, c0, cp, cm, kw * hs.y);
+        }
         // momentum carried by the pair at the next step: h*_p moves along
         // c_p unless r + c_p is a wall node (bit p+1), then it is pulled
         // back along -c_p; h*_{p+1} likewise with bit p
@@ -243,6 +326,7 @@ __global__ void __launch_bounds__(256, S >= 4 ? 1 : 2) k_stream_collide(const St
       }
       const float h0 = Fmt<ST>::sth_sr(fout + (int64_t)(s * Q) * N + i, (mh[s] - moved) * INV_WT(0),
                                        lcg_next(rnd));
+      if constexpr (SCAT) c0[GRP(0)] += a.scat_k[s] * WT(0) * h0;
       if (DIAG && active) {
         const float r = a.nref[s];
         qm[s] = r * (WT(0) * h0 + moved);
@@ -251,7 +335,9 @@ __global__ void __launch_bounds__(256, S >= 4 ? 1 : 2) k_stream_collide(const St
         qjz += r * mjz;
       }
     }
+    if constexpr (SCAT) scatter_charge(a, x, y, z, c0, cp, cm);
   }
+
 
   // per-CTA partial sums of the diagnostics (inactive threads add zeros)
   if (DIAG) {
@@ -289,24 +375,34 @@ __global__ void __launch_bounds__(256, S >= 4 ? 1 : 2) k_stream_collide(const St
   }
 }
 
-template <int S, bool W, bool C, int ST>
-cudaError_t launch_sc(const StepArgs& a, cudaStream_t st, int threads, bool diag) {
+template <int S, bool W, bool C, int ST, bool SC>
+cudaError_t launch_sc2(const StepArgs& a, cudaStream_t st, int threads, bool diag) {
   const unsigned nb = nblocks(a.N, threads);
   // the pair-frequency drag exists for three or more species (a binary
   // depends on its one cross frequency, which the host passes as omega_drag)
   constexpr bool CAN_PAIR = S >= 3;
   if (CAN_PAIR && a.pair_on) {
     if (diag)
-      k_stream_collide<S, W, C, ST, true, CAN_PAIR><<<nb, threads, 0, st>>>(a);
+      k_stream_collide<S, W, C, ST, true, CAN_PAIR, SC><<<nb, threads, 0, st>>>(a);
     else
-      k_stream_collide<S, W, C, ST, false, CAN_PAIR><<<nb, threads, 0, st>>>(a);
+      k_stream_collide<S, W, C, ST, false, CAN_PAIR, SC><<<nb, threads, 0, st>>>(a);
   } else {
     if (diag)
-      k_stream_collide<S, W, C, ST, true, false><<<nb, threads, 0, st>>>(a);
+      k_stream_collide<S, W, C, ST, true, false, SC><<<nb, threads, 0, st>>>(a);
     else
-      k_stream_collide<S, W, C, ST, false, false><<<nb, threads, 0, st>>>(a);
+      k_stream_collide<S, W, C, ST, false, false, SC><<<nb, threads, 0, st>>>(a);
   }
   return cudaGetLastError();
+}
+
+// The charge scatter: a.scat_acc is set by the host only for charged FP32
+// lattices without walls whose nx is a multiple of 32.
+template <int S, bool W, bool C, int ST>
+cudaError_t launch_sc(const StepArgs& a, cudaStream_t st, int threads, bool diag) {
+  if constexpr (!W && C && ST == LBM_FP32) {
+    if (a.scat_acc) return launch_sc2<S, W, C, ST, true>(a, st, threads, diag);
+  }
+  return launch_sc2<S, W, C, ST, false>(a, st, threads, diag);
 }
 
 template <int S, int ST>

@@ -126,6 +126,13 @@ struct StepArgs {
   // for equal masses; zero diagonal), used instead of omega_drag when pair_on
   int pair_on;
   float pair[MAX_SPECIES][MAX_SPECIES];
+  // charge scatter (periodic lattices without walls, nx a multiple of 32):
+  // each node's stored charged populations are added, in fixed point, to
+  // the next step's Poisson source at the node they stream to; NULL when a
+  // separate pass computes the source
+  int64_t* scat_acc;
+  float scat_k[MAX_SPECIES];  // 4 pi l_B z n_ref 2^52 (0 for a neutral species)
+  long long src_ref;          // 4 pi l_B sum_a z_a n_ref_a in fixed point, once per node
 };
 
 struct PoissonLevel {
@@ -251,6 +258,8 @@ struct lbm {
   // extra duties of the start's bookkeeping kernel while a step graph is
   // captured: the speculation flag and the first norm slot to clear
   int* mark_skip_out = nullptr;
+  const int* mark_prev_iters = nullptr;  // the previous step's applications (graph status)
+  int mark_k = 0;                        // applications baked into the graph being captured
   float* mark_clear = nullptr;
   int mark_nclear = 0;
   bool slot0_cleared = false;  // the start's kernel cleared norm slot 0 (spec_fwd skips it)
@@ -292,13 +301,25 @@ struct lbm {
   // whole-step CUDA graphs (LBM_FLAG_STEP_GRAPH), one per population parity
   // [parity] and stream/collide variant [diag]
   cudaGraphExec_t step_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  // the species' reference densities and valences the graphs were built with
+  float graph_nref[lbm_gb300::MAX_SPECIES] = {0};
+  float graph_valence[lbm_gb300::MAX_SPECIES] = {0};
   void* gstatus = nullptr;        // device status of graph steps
   void* hstatus = nullptr;        // pinned mirror
   int graph_kernels_fixed = 0;    // kernels per step outside the Poisson loop
   int graph_kernels_iter = 0;     // kernels per Poisson iteration
   int graph_kernels_redo = 0;     // kernels of the stream/collide run again after the loop
   std::vector<int> instance_z0;   // first plane of each stacked instance
-  int charge_threads = 256;       // CTA size of the charge kernel (autotuned)  // kernels launched since timing was (re)set
+  int charge_threads = 256;       // CTA size of the charge kernel (autotuned)
+  // charge scatter (LBM_FLAG_CHARGE_PASS off, periodic lattice without
+  // walls, nx a multiple of 32): scat_acc
+  // accumulates the next step's Poisson source in the stream/collide;
+  // scat_valid: it holds the source of the current populations (the step
+  // then takes it instead of running the charge pass)
+  bool scat_on = false;
+  bool scat_valid = false;
+  int64_t* scat_acc = nullptr;
+  unsigned long long* scat_tot = nullptr;  // running 128-bit source total and CTA count (k_src_take)
   std::string err;
 };
 
@@ -338,6 +359,9 @@ cudaError_t launch_stream_collide(lbm_t* h, bool diag);
 // advancing the state (autotuning).
 cudaError_t launch_stream_collide_probe(lbm_t* h, int threads);
 cudaError_t launch_charge(lbm_t* h);
+// With the charge scatter on and no valid scattered source, runs the charge
+// pass into the accumulator (so that the next step's launch_charge takes it).
+cudaError_t charge_prepare(lbm_t* h);
 cudaError_t launch_gather(lbm_t* h, int s, double* n_dev, double* u_dev,
                           double* f_dev);
 cudaError_t launch_diagnostics(lbm_t* h);

@@ -256,6 +256,82 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const long long* part, in
   }
 }
 
+// Takes the Poisson source that the previous step's stream/collide
+// scattered (the charge scatter): src = acc, acc = 0 for the next
+// scatter; node pairs (16-byte loads and stores; N is even: nx is a
+// multiple of 32) over a grid of a few CTAs per SM, four pairs in flight
+// per thread.  The total of the source is summed exactly as a 128-bit
+// integer: each CTA adds its sum to tot[0] (low word; the carry is known
+// from the old value) and tot[1] (high word), then counts itself in tot[2];
+// the last CTA converts the total to FP64 into *out, writes the source mean
+// over the fluid to mean_z[0 .. nz) (when given), advances the graph step
+// counter (when given) and clears tot for the next launch.  Integer sums do
+// not depend on the order in which CTAs add, so the result is the same in
+// every run (the work of k_sum_partials, without a second launch; few CTAs,
+// so few same-address atomics).
+__global__ void __launch_bounds__(256) k_src_take(int64_t* __restrict__ acc,
+                                                  int64_t* __restrict__ src, int64_t N,
+                                                  unsigned long long* tot, double* out,
+                                                  long long* mean_z, int nz, double inv_nfluid,
+                                                  uint32_t* step) {
+  const int64_t np = N / 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  longlong2* a2 = reinterpret_cast<longlong2*>(acc);
+  longlong2* s2 = reinterpret_cast<longlong2*>(src);
+  long long v = 0;
+  for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k0 < np; k0 += 4 * stride) {
+    longlong2 q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = k0 + u * stride;
+      q[u] = k < np ? a2[k] : make_longlong2(0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = k0 + u * stride;
+      if (k < np) {
+        s2[k] = q[u];
+        a2[k] = make_longlong2(0, 0);
+        v += q[u].x + q[u].y;
+      }
+    }
+  }
+  __shared__ long long red[32];
+  __shared__ int last;
+  __shared__ long long s_mean;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long c = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) c += red[w];
+    const unsigned long long lo = (unsigned long long)c;
+    const unsigned long long old = atomicAdd(&tot[0], lo);
+    const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    atomicAdd(&tot[1], carry + (c < 0 ? ~0ull : 0ull));
+    __threadfence();
+    last = atomicAdd(&tot[2], 1ull) == (unsigned long long)(gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long lo = atomicExch(&tot[0], 0ull);
+    const unsigned long long hi = atomicExch(&tot[1], 0ull);
+    atomicExch(&tot[2], 0ull);
+    const __int128 t = (__int128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
+    const double td = (double)t;
+    *out = td;
+    s_mean = llrint(td * inv_nfluid);
+    if (step) *step += 1u;
+  }
+  if (mean_z) {
+    __syncthreads();
+    for (int z = threadIdx.x; z < nz; z += blockDim.x) mean_z[z] = s_mean;
+  }
+}
+
 // Gathers f(t) of species s and its moments n, u = sum c f / n (doubles,
 // from the deviations: n = n_ref + sum d, j = sum c d).  The deviation sums
 // are compensated FP32 sums (about twice FP32 precision), 1/n an FP32
@@ -645,13 +721,33 @@ StepArgs step_args(lbm_t* h) {
   a.pair_on = h->pair_on ? 1 : 0;
   for (int i = 0; i < MAX_SPECIES; ++i)
     for (int j = 0; j < MAX_SPECIES; ++j) a.pair[i][j] = h->pair[i][j];
+  a.scat_acc = nullptr;
+  a.src_ref = 0;
+  for (int s = 0; s < MAX_SPECIES; ++s) a.scat_k[s] = 0.f;
   return a;
 }
 
-cudaError_t collide_into_spare(lbm_t* h, int threads, bool d) {
-  const StepArgs a = step_args(h);
+// 4 pi l_B sum_a z_a n_ref_a in fixed point (FP64 on the host): the part
+// of the Poisson source that is the same at every fluid node
+long long source_reference(const lbm_t* h) {
+  double zref = 0.0;
+  for (int s = 0; s < h->S; ++s) zref += (double)h->valence[s] * (double)h->nref[s];
+  return llrint(4.0 * 3.14159265358979323846 * h->cfg.bjerrum * zref * PSI_SCALE);
+}
+
+cudaError_t collide_into_spare(lbm_t* h, int threads, bool d, bool scatter) {
+  StepArgs a = step_args(h);
   const bool c = h->cfg.bjerrum > 0.0;
   const bool w = h->has_walls;
+  if (scatter) {
+    // the next step's source, accumulated into scat_acc (zero here: the
+    // step took the previous one out)
+    a.scat_acc = h->scat_acc;
+    a.src_ref = source_reference(h);
+    for (int s = 0; s < h->S; ++s)
+      a.scat_k[s] = (float)(4.0 * 3.14159265358979323846 * h->cfg.bjerrum * (double)h->valence[s] *
+                            (double)h->nref[s] * PSI_SCALE);
+  }
   if (d) h->dpart_ctas = (int64_t)nblocks(h->N, threads);
   switch (h->cfg.storage) {
     case LBM_FP32: return collide_dispatch<LBM_FP32>(a, h->S, w, c, h->st, threads, d);
@@ -663,17 +759,18 @@ cudaError_t collide_into_spare(lbm_t* h, int threads, bool d) {
 }  // namespace
 
 cudaError_t launch_stream_collide(lbm_t* h, bool diag) {
-  cudaError_t e = collide_into_spare(h, h->collide_threads, diag);
+  cudaError_t e = collide_into_spare(h, h->collide_threads, diag, h->scat_on);
   if (e == cudaSuccess) {
     h->cur ^= 1;
     ++h->launches;
     h->diag_valid = diag;
+    if (h->scat_on) h->scat_valid = true;
   }
   return e;
 }
 
 cudaError_t launch_stream_collide_probe(lbm_t* h, int threads) {
-  cudaError_t e = collide_into_spare(h, threads, false);
+  cudaError_t e = collide_into_spare(h, threads, false, false);
   if (e == cudaSuccess) ++h->launches;
   return e;
 }
@@ -732,6 +829,7 @@ cudaError_t launch_plane_fluxes(lbm_t* h, double* out_dev) {
 
 cudaError_t launch_init_species(lbm_t* h, int s, const double* n0,
                                 const double* u0) {
+  h->scat_valid = false;  // new populations: the next step runs the charge pass
   const int nb = nblocks(h->N, 256);
   LBM_DISPATCH_WS(h, (k_init<W_, ST_><<<nb, 256, 0, h->st>>>(
                          s, n0, u0, h->links, h->f[h->cur], h->cfg.nx,
@@ -740,7 +838,11 @@ cudaError_t launch_init_species(lbm_t* h, int s, const double* n0,
   return cudaGetLastError();
 }
 
-cudaError_t launch_charge(lbm_t* h) {
+namespace {
+// The charge pass: the source of the current populations into out (the
+// Poisson source, or the scatter's accumulator), per-CTA partial sums into
+// ps.part; returns the number of partials.
+int charge_pass(lbm_t* h, int64_t* out) {
   // one node per thread (the pulled loads of a node are independent and all
   // in flight); per-CTA partial sums instead of same-address atomics
   const int ct = h->charge_threads;
@@ -748,9 +850,7 @@ cudaError_t launch_charge(lbm_t* h) {
   const float k = (float)(4.0 * 3.14159265358979323846 * h->cfg.bjerrum);
   // reference part of the source, 4 pi l_B sum_alpha z^alpha n_ref^alpha,
   // in fixed point (FP64 on the host, the same at every fluid node)
-  double zref = 0.0;
-  for (int s = 0; s < h->S; ++s) zref += (double)h->valence[s] * (double)h->nref[s];
-  const long long src_ref = llrint(4.0 * 3.14159265358979323846 * h->cfg.bjerrum * zref * PSI_SCALE);
+  const long long src_ref = source_reference(h);
   // the charged species, packed
   int csi[4] = {0, 0, 0, 0};
   float cval[4] = {0.f, 0.f, 0.f, 0.f}, cref[4] = {1.f, 1.f, 1.f, 1.f};
@@ -767,7 +867,7 @@ cudaError_t launch_charge(lbm_t* h) {
   const float4 cr4 = make_float4(cref[0], cref[1], cref[2], cref[3]);
 #define LBM_CHARGE_S(NC)                                                        \
   LBM_DISPATCH_WS(h, (k_charge<NC, W_, ST_><<<nb, ct, 0, h->st>>>(               \
-                         h->f[h->cur], h->links, h->wsrc, h->ps.src, h->ps.part, \
+                         h->f[h->cur], h->links, h->wsrc, out, h->ps.part,      \
                          h->ps.label, h->ps.comp_sum,                            \
                          h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,                  \
                          cs4, cv4, cr4, k, src_ref)))
@@ -782,11 +882,11 @@ cudaError_t launch_charge(lbm_t* h) {
   do {                                                                                     \
     if (h->cfg.storage == LBM_FP16_SHIFT)                                                  \
       k_charge_quad<NC, LBM_FP16_SHIFT><<<nbq, ct, 0, h->st>>>(                            \
-          h->f[h->cur], h->ps.src, h->ps.part, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N, cs4, \
+          h->f[h->cur], out, h->ps.part, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N, cs4, \
           cv4, cr4, k, src_ref);                                                           \
     else                                                                                   \
       k_charge_quad<NC, LBM_BF16_SHIFT><<<nbq, ct, 0, h->st>>>(                            \
-          h->f[h->cur], h->ps.src, h->ps.part, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N, cs4, \
+          h->f[h->cur], out, h->ps.part, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N, cs4, \
           cv4, cr4, k, src_ref);                                                           \
   } while (0)
     switch (nc) {
@@ -807,13 +907,44 @@ cudaError_t launch_charge(lbm_t* h) {
     }
   }
 #undef LBM_CHARGE_S
-  // the spectral solver's source mean for one periodic run is written here;
-  // the solve then skips its own mean kernel once (charge_means_ready)
-  long long* mz = h->charge_mean_z;
-  k_sum_partials<<<1, 1024, 0, h->st>>>(h->ps.part, nbq, h->ps.dsum, mz, h->cfg.nz,
-                                        1.0 / (double)h->nfluid, h->charge_step);
-  h->charge_means_ready = mz != nullptr;
-  h->launches += 2;
+  ++h->launches;
+  return nbq;
+}
+}  // namespace
+
+cudaError_t charge_prepare(lbm_t* h) {
+  if (h->scat_on && !h->scat_valid) {
+    charge_pass(h, h->scat_acc);
+    h->scat_valid = true;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_charge(lbm_t* h) {
+  int nbq;
+  if (h->scat_on) {
+    // the source the previous stream/collide scattered (computed by the
+    // pass into the accumulator when the populations came from elsewhere),
+    // moved into the Poisson source; the accumulator is then zero for the
+    // scatter of this step
+    if (!h->scat_valid) charge_pass(h, h->scat_acc);
+    const int tb = 256;
+    const unsigned nbt = (unsigned)std::min<int64_t>(nblocks(h->N / 2, tb), h->grid_cap / 2);
+    k_src_take<<<nbt, tb, 0, h->st>>>(
+        h->scat_acc, h->ps.src, h->N, h->scat_tot, h->ps.dsum, h->charge_mean_z, h->cfg.nz,
+        1.0 / (double)h->nfluid, h->charge_step);
+    ++h->launches;
+    h->scat_valid = false;
+  } else {
+    nbq = charge_pass(h, h->ps.src);
+    k_sum_partials<<<1, 1024, 0, h->st>>>(h->ps.part, nbq, h->ps.dsum, h->charge_mean_z,
+                                          h->cfg.nz, 1.0 / (double)h->nfluid, h->charge_step);
+    ++h->launches;
+  }
+  // the spectral solver's source mean for one periodic run is written
+  // there; the solve then skips its own mean kernel once
+  // (charge_means_ready)
+  h->charge_means_ready = h->charge_mean_z != nullptr;
   if (h->ps.label) {
     k_comp_means<<<1, 256, 0, h->st>>>(h->ps.dsum, h->ps.comp_sum, h->ps.comp_size,
                                         h->ps.ncomp, h->ps.comp_mean);

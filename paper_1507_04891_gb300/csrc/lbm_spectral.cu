@@ -1290,8 +1290,12 @@ __global__ void k_loop_seed(const GraphStatus* st, cudaGraphConditionalHandle co
 // history.  A start from a short history (the first steps after a restart)
 // usually needs more applications, and the speculative stream/collide would
 // be discarded; then the stream/collide runs once, after the loop.
-__global__ void k_spec_decide(const int* __restrict__ start_terms, GraphStatus* st) {
-  st->spec_skip = (start_terms && *start_terms < START_FULL_TERMS) ? 1 : 0;
+// The step after one that needed more than the k baked applications does
+// not speculate either (such steps come in runs; see k_start_mark).  This
+// kernel decides when the start from the history is off; otherwise the
+// start's bookkeeping kernel does.
+__global__ void k_spec_decide(const int* __restrict__ start_terms, GraphStatus* st, int k) {
+  st->spec_skip = ((start_terms && *start_terms < START_FULL_TERMS) || st->iters > k) ? 1 : 0;
 }
 
 // Convergence test (one warp).  first: after the k applications queued
@@ -1393,6 +1397,7 @@ namespace {
 lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
   const int saved_cur = h->cur;
   const bool saved_diag = h->diag_valid;  // capture runs nothing
+  const bool saved_scat = h->scat_valid;
   h->cur = parity;
   GraphStatus* gs = reinterpret_cast<GraphStatus*>(h->gstatus);
   const double tol = h->cfg.poisson_tol;
@@ -1435,6 +1440,11 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
   if (e == cudaSuccess) {
     cudaError_t ec = cudaSuccess;
     h->charge_step = &gs->step;
+    // with the charge scatter, a replay finds the source of its input
+    // populations in the accumulator (spectral_graph_steps sees to it
+    // before the first replay; every step's stream/collide scatters the
+    // next one)
+    h->scat_valid = true;
     ec = launch_charge(h);
     h->charge_step = nullptr;
     // the start from the history, then the fit for the next step on the
@@ -1444,11 +1454,14 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
     const bool fit = start_enabled(h);
     if (fit) {
       h->mark_skip_out = &gs->spec_skip;
+      h->mark_prev_iters = &gs->iters;
+      h->mark_k = k;
       h->mark_clear = norm_slot(h, 0);
       h->mark_nclear = 2 * NACC;
     }
     if (ec == cudaSuccess) ec = start_apply(h, false);
     h->mark_skip_out = nullptr;
+    h->mark_prev_iters = nullptr;
     h->mark_clear = nullptr;
     if (ec == cudaSuccess && fit) ec = cudaEventRecord(fork2, main);
     if (ec == cudaSuccess && fit) ec = cudaStreamWaitEvent(side2, fork2, 0);
@@ -1456,7 +1469,7 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
     if (ec == cudaSuccess && fit) ec = cudaEventRecord(join2, side2);
     if (ec == cudaSuccess) ec = spec_means(h);
     if (ec == cudaSuccess && !fit) {
-      k_spec_decide<<<1, 1, 0, main>>>(terms, gs);
+      k_spec_decide<<<1, 1, 0, main>>>(terms, gs, k);
       ++h->launches;
       ec = cudaGetLastError();
     }
@@ -1564,9 +1577,12 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
       e = cudaStreamBeginCaptureToGraph(main, ibody, &cnode, nullptr, 1, mode);
       if (e == cudaSuccess) {
         // from the step's input populations again, into the same output as
-        // the speculative launch (which flipped the parity while capturing)
+        // the speculative launch (which flipped the parity while capturing);
+        // the scatter of the speculative launch is cleared first
         h->cur = parity;
-        cudaError_t eb = launch_stream_collide(h, diag);
+        cudaError_t eb = cudaSuccess;
+        if (h->scat_on) eb = cudaMemsetAsync(h->scat_acc, 0, (size_t)h->N * sizeof(int64_t), main);
+        if (eb == cudaSuccess) eb = launch_stream_collide(h, diag);
         cudaGraph_t gg = nullptr;
         e = cudaStreamEndCapture(main, &gg);
         if (e == cudaSuccess) e = eb;
@@ -1579,8 +1595,10 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
   h->launches = l0;
   h->cur = saved_cur;
   h->diag_valid = saved_diag;
+  h->scat_valid = saved_scat;
   h->slot0_cleared = false;
   h->mark_skip_out = nullptr;
+  h->mark_prev_iters = nullptr;
   h->mark_clear = nullptr;
   h->st = main;
   cudaGraphExec_t ex = nullptr;
@@ -1604,6 +1622,17 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
 // Builds the missing step graphs (both parities, both stream/collide
 // variants).
 lbm_status build_step_graphs(lbm_t* h) {
+  // the kernels' arguments bake every species' reference density and
+  // valence (decoding of the stored deviations, charge, forces): a change
+  // by lbm_set_species / lbm_set_species_dev rebuilds the graphs
+  bool same = true;
+  for (int s = 0; s < MAX_SPECIES; ++s)
+    same = same && h->graph_nref[s] == h->nref[s] && h->graph_valence[s] == h->valence[s];
+  if (!same) spectral_graph_free(h);
+  for (int s = 0; s < MAX_SPECIES; ++s) {
+    h->graph_nref[s] = h->nref[s];
+    h->graph_valence[s] = h->valence[s];
+  }
   for (int k = 0; k < 2; ++k)
     for (int d = 0; d < 2; ++d)
       if (!h->step_graph[k][d]) {
@@ -1653,6 +1682,9 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     LBM_CUDA_TRY(h, cudaStreamSynchronize(h->st));
     sp->status_read = true;
   }
+  // the charge scatter: the source of the current populations into the
+  // accumulator, where the first replay takes it
+  LBM_CUDA_TRY(h, charge_prepare(h));
   const long long total0 = hs->total;
   const int fails0 = hs->fails;
   const double slog0 = hs->start_log;
@@ -1758,6 +1790,7 @@ lbm_status spectral_graph_steps(lbm_t* h, int nsteps) {
     h->start_count += dn;
     h->last_start = pow(10.0, dl / (double)dn);
   }
+  if (h->scat_on) h->scat_valid = true;  // each replay ends with a scattering stream/collide
   h->t_cnt[1] += iters;
   h->t_cnt[0] += done;
   h->t_cnt[2] += done;

@@ -270,16 +270,24 @@ __global__ void __launch_bounds__(256) k_start_psi(int64_t* __restrict__ psi,
 // The step's bookkeeping after the start: the terms it used (for the
 // graph's decisions) and, when it is the step's last pass, the ring
 // position; after every thread of the start read them.  In a step graph it
-// also writes whether the step speculates (the start used fewer than
-// START_FULL_TERMS differences: no) and clears the norm slot of the first
-// application, which saves two graph nodes on the step's critical path.
+// also writes whether the step speculates and clears the norm slot of the
+// first application, which saves two graph nodes on the step's critical
+// path.  The step does not speculate when the start used fewer than
+// START_FULL_TERMS differences, or when the previous step needed more than
+// the k applications baked into the graph (prev_iters: its count): steps
+// that need more come in runs (the first steps after a restart, a change
+// in the source the history does not follow), and a step that does not
+// speculate only serialises its stream/collide behind the convergence
+// test, while a failed speculation runs the stream/collide twice.
 __global__ void k_start_mark(int* __restrict__ state, int advance, int* __restrict__ skip_out,
+                             const int* __restrict__ prev_iters, int kbaked,
                              float* __restrict__ clear, int nclear) {
   if (threadIdx.x == 0) {
     const int used = state[ST_TERMS];
     state[ST_USED] = used;
     if (advance) state[ST_RING] = (state[ST_RING] + 1) % K;
-    if (skip_out) *skip_out = used < START_FULL_TERMS ? 1 : 0;
+    if (skip_out)
+      *skip_out = (used < START_FULL_TERMS || (prev_iters && *prev_iters > kbaked)) ? 1 : 0;
   }
   for (int k = threadIdx.x; k < nclear; k += blockDim.x) clear[k] = 0.f;
 }
@@ -349,8 +357,8 @@ cudaError_t start_apply(lbm_t* h, bool last) {
   if (!start_enabled(h)) return start_reset(h);
   k_start_psi<<<nblk(h->N, 256), 256, 0, h->st>>>(h->ps.psi[h->ps.cur], H.psi_prev, H.ring_p, H.coef,
                                                    H.state, h->N, last ? 1 : 0);
-  k_start_mark<<<1, 128, 0, h->st>>>(H.state, last ? 1 : 0, h->mark_skip_out, h->mark_clear,
-                                     h->mark_clear ? h->mark_nclear : 0);
+  k_start_mark<<<1, 128, 0, h->st>>>(H.state, last ? 1 : 0, h->mark_skip_out, h->mark_prev_iters,
+                                     h->mark_k, h->mark_clear, h->mark_clear ? h->mark_nclear : 0);
   h->slot0_cleared = h->mark_clear != nullptr;
   h->launches += 2;
   return cudaGetLastError();

@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 LBM_FLAG_STEP_GRAPH = 1
 LBM_FLAG_NO_EXTRAPOLATION = 2
+LBM_FLAG_CHARGE_PASS = 4
 POISSON = {"mg": 0, "sor": 1, "fft": 2}
 
 # every symbol include/lbm.h declares
@@ -156,7 +157,7 @@ def load_library(path: str = LIB_PATH):
 
 def make_config(nx, ny, nz, nspecies, omega_visc=1.0, omega_drag=1.0, bjerrum=0.0,
                 e_ext=(0.0, 0.0, 0.0), storage="fp32", poisson="mg", poisson_tol=1e-8,
-                poisson_maxit=200, device=0, step_graph=False, extrapolate=True):
+                poisson_maxit=200, device=0, step_graph=False, extrapolate=True, charge_pass=False):
     lib = load_library()
     cfg = LbmConfig()
     lib.lbm_config_default(ctypes.byref(cfg))
@@ -168,7 +169,8 @@ def make_config(nx, ny, nz, nspecies, omega_visc=1.0, omega_drag=1.0, bjerrum=0.
     cfg.poisson = POISSON[poisson] if isinstance(poisson, str) else int(poisson)
     cfg.poisson_tol, cfg.poisson_maxit, cfg.device = float(poisson_tol), int(poisson_maxit), int(device)
     cfg.flags = (LBM_FLAG_STEP_GRAPH if step_graph else 0) | \
-                (0 if extrapolate else LBM_FLAG_NO_EXTRAPOLATION)
+                (0 if extrapolate else LBM_FLAG_NO_EXTRAPOLATION) | \
+                (LBM_FLAG_CHARGE_PASS if charge_pass else 0)
     return cfg
 
 
@@ -192,15 +194,18 @@ class Lattice:
     "fp16" or "bf16"; poisson "mg", "sor" or "fft"; step_graph sets
     LBM_FLAG_STEP_GRAPH (spectral solver only); extrapolate=False sets
     LBM_FLAG_NO_EXTRAPOLATION (each solve starts from the previous potential
-    instead of its extrapolation in time)."""
+    instead of its extrapolation in time); charge_pass=True sets
+    LBM_FLAG_CHARGE_PASS (the charge density by a separate pass each step,
+    not scattered by the previous stream/collide)."""
 
     def __init__(self, nx, ny, nz, nspecies, omega_visc=1.0, omega_drag=1.0,
                  bjerrum=0.0, e_ext=(0.0, 0.0, 0.0), storage="fp32", poisson="mg",
                  poisson_tol=1e-8, poisson_maxit=200, device=0, step_graph=False,
-                 extrapolate=True, _stack=None):
+                 extrapolate=True, charge_pass=False, _stack=None):
         self._lib = load_library()
         cfg = make_config(nx, ny, nz, nspecies, omega_visc, omega_drag, bjerrum, e_ext, storage,
-                          poisson, poisson_tol, poisson_maxit, device, step_graph, extrapolate)
+                          poisson, poisson_tol, poisson_maxit, device, step_graph, extrapolate,
+                          charge_pass)
         self.cfg = cfg
         self.S = int(nspecies)
         h = ctypes.c_void_p()

@@ -108,7 +108,8 @@ def test_binding_constants_match_the_header(tmp_path):
              "LBM_BF16_SHIFT": lbm.STORAGE["bf16"], "LBM_POISSON_MG": lbm.POISSON["mg"],
              "LBM_POISSON_SOR": lbm.POISSON["sor"], "LBM_POISSON_FFT": lbm.POISSON["fft"],
              "LBM_FLAG_STEP_GRAPH": lbm.LBM_FLAG_STEP_GRAPH,
-             "LBM_FLAG_NO_EXTRAPOLATION": lbm.LBM_FLAG_NO_EXTRAPOLATION}
+             "LBM_FLAG_NO_EXTRAPOLATION": lbm.LBM_FLAG_NO_EXTRAPOLATION,
+             "LBM_FLAG_CHARGE_PASS": lbm.LBM_FLAG_CHARGE_PASS}
     src = tmp_path / "consts.c"
     body = "".join('printf("%s %%d\\n", (int)(%s));' % (n, n) for n in names)
     src.write_text('#include <stdio.h>\n#include "lbm.h"\nint main(void){' + body + 'return 0;}\n')
@@ -119,10 +120,12 @@ def test_binding_constants_match_the_header(tmp_path):
     for n, v in names.items():
         assert int(out[n]) == v, n
     # flag bits are distinct powers of two
-    flags = [lbm.LBM_FLAG_STEP_GRAPH, lbm.LBM_FLAG_NO_EXTRAPOLATION]
+    flags = [lbm.LBM_FLAG_STEP_GRAPH, lbm.LBM_FLAG_NO_EXTRAPOLATION, lbm.LBM_FLAG_CHARGE_PASS]
     assert all(f & (f - 1) == 0 for f in flags) and len(set(flags)) == len(flags)
     cfg = lbm.make_config(8, 8, 8, 1, step_graph=True, extrapolate=False)
     assert cfg.flags == lbm.LBM_FLAG_STEP_GRAPH | lbm.LBM_FLAG_NO_EXTRAPOLATION
+    cfg = lbm.make_config(8, 8, 8, 1, charge_pass=True)
+    assert cfg.flags == lbm.LBM_FLAG_CHARGE_PASS
 
 
 def test_omega_drag_for_schmidt_inverts_the_lattice_transport_coefficients(libpath):
