@@ -1104,6 +1104,11 @@ lbm_status lbm_autotune(lbm_t* h, double* out) {
   spectral_graph_free(h);  // graphs baked the old sizes
   h->psi_valid = false;
   h->scat_valid = false;  // the timed charge launches took the scattered source
+  // (and, with the scatter, wrote source differences into the history)
+  {
+    lbm_status sr = potential_history_reset(h);
+    if (sr != LBM_OK) return sr;
+  }
   if (out) {
     out[0] = tc;
     out[1] = best_c;

@@ -105,8 +105,19 @@ __device__ __forceinline__ void scatter_charge(const StepArgs& a, int x, int y, 
   }
 }
 
+// Registers: up to 128 per thread (two 256-thread CTAs per SM), 255 for four
+// species.  The 16-bit ternary kernel without walls is capped at 96: it is
+// bound by instruction issue, and 20 warps per SM (128-thread CTAs) instead
+// of 16 issue more often than the few spilled registers cost (measured at
+// 128^3: 133 -> 127 us per launch; 88 registers: 130 us).
+template <int S, bool WALLS, int ST>
+constexpr int collide_maxnreg() {
+  return S >= 4 ? 255 : ((ST != LBM_FP32 && !WALLS && S == 3) ? 96 : 128);
+}
+
 template <int S, bool WALLS, bool CHARGED, int ST, bool DIAG, bool PAIR, bool SCAT>
-__global__ void __launch_bounds__(256, S >= 4 ? 1 : 2) k_stream_collide(const StepArgs a) {
+__global__ void __launch_bounds__(256) __maxnreg__((collide_maxnreg<S, WALLS, ST>()))
+    k_stream_collide(const StepArgs a) {
   using T = typename Fmt<ST>::T;
   // a speculative launch the step has decided against (same for every
   // thread of the grid)

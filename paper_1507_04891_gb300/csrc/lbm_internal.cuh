@@ -199,6 +199,10 @@ struct StartHistory {
   float* coef = nullptr;        // START_K coefficients of the current step
   int* state = nullptr;         // valid steps, ring position, terms of coef, terms used
   int ctas = 0;
+  // the charge scatter's source take also ran the fit's first pass (the
+  // differences and inner products) for this step, with dots_ctas partials
+  bool dots_done = false;
+  int dots_ctas = 0;
   cudaStream_t side = nullptr;  // the fit runs here, beside the solve (lowest priority)
   cudaEvent_t fork = nullptr, join = nullptr;
   bool pending = false;         // a fit was queued on side and not yet joined
@@ -362,6 +366,14 @@ cudaError_t launch_charge(lbm_t* h);
 // With the charge scatter on and no valid scattered source, runs the charge
 // pass into the accumulator (so that the next step's launch_charge takes it).
 cudaError_t charge_prepare(lbm_t* h);
+
+// ---- lbm_start.cu: the source take fused with the fit's first pass ----
+// With the start from the history on, moves the scattered source into the
+// Poisson source (as k_src_take: accumulator cleared, exact total, mean,
+// step counter) and forms the step's source difference and its inner
+// products in the same pass; returns false (launching nothing) when the
+// start is off.
+bool launch_take_dots(lbm_t* h, unsigned ctas, double inv_nfluid);
 cudaError_t launch_gather(lbm_t* h, int s, double* n_dev, double* u_dev,
                           double* f_dev);
 cudaError_t launch_diagnostics(lbm_t* h);

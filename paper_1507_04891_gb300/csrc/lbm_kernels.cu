@@ -930,7 +930,10 @@ cudaError_t launch_charge(lbm_t* h) {
     if (!h->scat_valid) charge_pass(h, h->scat_acc);
     const int tb = 256;
     const unsigned nbt = (unsigned)std::min<int64_t>(nblocks(h->N / 2, tb), h->grid_cap / 2);
-    k_src_take<<<nbt, tb, 0, h->st>>>(
+    // with the start from the history on, the take also forms the fit's
+    // source difference and its inner products (one pass over the source)
+    if (!launch_take_dots(h, nbt, 1.0 / (double)h->nfluid))
+      k_src_take<<<nbt, tb, 0, h->st>>>(
         h->scat_acc, h->ps.src, h->N, h->scat_tot, h->ps.dsum, h->charge_mean_z, h->cfg.nz,
         1.0 / (double)h->nfluid, h->charge_step);
     ++h->launches;

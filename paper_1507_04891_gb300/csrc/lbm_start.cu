@@ -292,7 +292,112 @@ __global__ void k_start_mark(int* __restrict__ state, int advance, int* __restri
   for (int k = threadIdx.x; k < nclear; k += blockDim.x) clear[k] = 0.f;
 }
 
+// The charge scatter's source take fused with pass 1 (the step's source
+// s(t) is the accumulator, and the source buffer still holds s(t-1), so the
+// stored previous source is not needed: in a lattice with the scatter,
+// k_start_dots never runs, and the first difference after a restart of the
+// history is never used).  Node pairs over a grid of a few CTAs per SM:
+// src = acc, acc = 0, D_0 = s(t) - s(t-1) into the ring slot r mod K, its
+// products with D_0 .. D_K per CTA into part, and the exact 128-bit source
+// total with the last CTA's work of k_src_take (FP64 total, mean over the
+// fluid into mean_z, graph step counter, tot cleared).
+__global__ void __launch_bounds__(256) k_take_dots(int64_t* __restrict__ acc,
+                                                   int64_t* __restrict__ src,
+                                                   float* __restrict__ ring_d,
+                                                   const int* __restrict__ state, int64_t N,
+                                                   float* __restrict__ part,
+                                                   unsigned long long* tot, double* out,
+                                                   long long* mean_z, int nz, double inv_nfluid,
+                                                   uint32_t* step) {
+  const int r = state[ST_RING];
+  const int64_t np = N / 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  longlong2* a2 = reinterpret_cast<longlong2*>(acc);
+  longlong2* s2 = reinterpret_cast<longlong2*>(src);
+  float2* rw = reinterpret_cast<float2*>(ring_d + (int64_t)(r % K) * N);
+  float dp[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) dp[j] = 0.f;
+  long long v = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) {
+    const longlong2 q = a2[k];
+    const longlong2 o = s2[k];
+    float2 dj[K + 1];
+#pragma unroll
+    for (int j = 1; j <= K; ++j)
+      dj[j] = reinterpret_cast<const float2*>(ring_d + (int64_t)((r - j + 2 * K) % K) * N)[k];
+    s2[k] = q;
+    a2[k] = make_longlong2(0, 0);
+    v += q.x + q.y;
+    const float d0x = i64_to_f32(q.x - o.x), d0y = i64_to_f32(q.y - o.y);
+    rw[k] = make_float2(d0x, d0y);
+    dp[0] += d0x * d0x + d0y * d0y;
+#pragma unroll
+    for (int j = 1; j <= K; ++j) dp[j] += d0x * dj[j].x + d0y * dj[j].y;
+  }
+  __shared__ float red[8][K + 1];
+  __shared__ long long redv[8];
+  __shared__ int last;
+  __shared__ long long s_mean;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    float t = dp[j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][j] = t;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) redv[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x <= K) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
+    part[(int64_t)blockIdx.x * (K + 1) + threadIdx.x] = t;
+  }
+  if (threadIdx.x == 0) {
+    long long c = 0;
+    for (int w = 0; w < 8; ++w) c += redv[w];
+    const unsigned long long lo = (unsigned long long)c;
+    const unsigned long long old = atomicAdd(&tot[0], lo);
+    const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    atomicAdd(&tot[1], carry + (c < 0 ? ~0ull : 0ull));
+    __threadfence();
+    last = atomicAdd(&tot[2], 1ull) == (unsigned long long)(gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long lo = atomicExch(&tot[0], 0ull);
+    const unsigned long long hi = atomicExch(&tot[1], 0ull);
+    atomicExch(&tot[2], 0ull);
+    const __int128 t = (__int128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
+    const double td = (double)t;
+    *out = td;
+    s_mean = llrint(td * inv_nfluid);
+    if (step) *step += 1u;
+  }
+  if (mean_z) {
+    __syncthreads();
+    for (int z = threadIdx.x; z < nz; z += blockDim.x) mean_z[z] = s_mean;
+  }
+}
+
 }  // namespace
+
+bool launch_take_dots(lbm_t* h, unsigned ctas, double inv_nfluid) {
+  StartHistory& H = h->start;
+  if (!start_enabled(h)) return false;
+  ctas = std::min<unsigned>(ctas, (unsigned)H.ctas);
+  k_take_dots<<<ctas, 256, 0, h->st>>>(h->scat_acc, h->ps.src, H.ring_d, H.state, h->N, H.part,
+                                      h->scat_tot, h->ps.dsum, h->charge_mean_z, h->cfg.nz,
+                                      inv_nfluid, h->charge_step);
+  H.dots_done = true;
+  H.dots_ctas = (int)ctas;
+  return true;
+}
 
 lbm_status start_setup(lbm_t* h) {
   start_free(h);
@@ -367,9 +472,18 @@ cudaError_t start_apply(lbm_t* h, bool last) {
 cudaError_t start_fit(lbm_t* h, cudaStream_t st, bool last) {
   StartHistory& H = h->start;
   if (!start_enabled(h)) return cudaSuccess;
-  k_start_dots<<<H.ctas, DOT_THREADS, 0, st>>>(h->ps.src, H.s_prev, H.ring_d, H.state, h->N, H.part);
-  k_start_solve<<<1, 256, 0, st>>>(H.part, H.ctas, H.gram, H.coef, H.state, last ? 1 : 0);
-  h->launches += 2;
+  int nparts = H.ctas;
+  if (H.dots_done) {
+    // the source take of this step formed the differences and products
+    nparts = H.dots_ctas;
+    H.dots_done = false;
+  } else {
+    k_start_dots<<<H.ctas, DOT_THREADS, 0, st>>>(h->ps.src, H.s_prev, H.ring_d, H.state, h->N,
+                                                 H.part);
+    ++h->launches;
+  }
+  k_start_solve<<<1, 256, 0, st>>>(H.part, nparts, H.gram, H.coef, H.state, last ? 1 : 0);
+  ++h->launches;
   return cudaGetLastError();
 }
 
