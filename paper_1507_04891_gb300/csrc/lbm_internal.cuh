@@ -47,6 +47,8 @@ constexpr double RES_FLOOR_RMS = 4.0;
 // Differences of the source and potential history kept for the start of
 // each step's Poisson solve (lbm_start.cu).
 constexpr int START_K = 5;
+// index of the ring position in the history's device state
+constexpr int START_RING_IDX = 1;
 // starts fitted on at least this many differences count as steady-state
 // steps for the graph steps' choice of the number of applications
 constexpr int START_FULL_TERMS = START_K;
@@ -135,6 +137,16 @@ struct StepArgs {
   long long src_ref;          // 4 pi l_B sum_a z_a n_ref_a in fixed point, once per node
 };
 
+// The start's first pass fused into the charge pass: the source difference
+// D_0 = s(t) - s(t-1) (s(t-1): what the source buffer holds before the pass
+// overwrites it) into the ring slot of the current position, and its
+// products with D_0 and the stored D_1 .. D_K per CTA into part.
+struct DotsArgs {
+  float* ring_d;       // START_K x N differences of consecutive sources
+  const int* state;    // history state (ring position at START_RING_IDX)
+  float* part;         // (START_K + 1) floats per CTA
+};
+
 struct PoissonLevel {
   int nx, ny, nz;
   int64_t n;
@@ -203,6 +215,7 @@ struct StartHistory {
   // differences and inner products) for this step, with dots_ctas partials
   bool dots_done = false;
   int dots_ctas = 0;
+  int part_ctas = 0;            // CTAs part has room for
   cudaStream_t side = nullptr;  // the fit runs here, beside the solve (lowest priority)
   cudaEvent_t fork = nullptr, join = nullptr;
   bool pending = false;         // a fit was queued on side and not yet joined
@@ -374,6 +387,10 @@ cudaError_t charge_prepare(lbm_t* h);
 // products in the same pass; returns false (launching nothing) when the
 // start is off.
 bool launch_take_dots(lbm_t* h, unsigned ctas, double inv_nfluid);
+// The arguments for fusing the start's first pass into a charge pass of
+// `ctas` CTAs that writes the Poisson source; marks the step's pass as done.
+// False when the start is off.
+bool charge_dots_args(lbm_t* h, int ctas, DotsArgs* out);
 cudaError_t launch_gather(lbm_t* h, int s, double* n_dev, double* u_dev,
                           double* f_dev);
 cudaError_t launch_diagnostics(lbm_t* h);

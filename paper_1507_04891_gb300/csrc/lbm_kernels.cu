@@ -62,19 +62,90 @@ __global__ void k_init(int s, const double* __restrict__ n0,
 // rho_e = sum_alpha z^alpha n^alpha(r, t) from the pulled populations of the
 // charged species; per-CTA sums of s over fluid nodes (exact, int64).
 // ---------------------------------------------------------------------------
+// The start's first pass fused into the charge pass (DotsArgs): for this
+// thread's NV consecutive nodes from i0 (i0 a multiple of NV), the source
+// differences d0 against the stored D_1 .. D_K (ring slot of age j:
+// (r - j) mod K, read before d0 replaces the oldest, slot r mod K), summed
+// per CTA in FP32 into part (K + 1 values per CTA), as k_start_dots does.
+// The stored differences of this thread's nodes, loaded before the pulls
+// so that they are in flight with them.
+template <int NV>
+__device__ __forceinline__ void dots_load(const DotsArgs& dk, int64_t N, int64_t i0, int r,
+                                          float (&dj)[START_K + 1][NV]) {
+  constexpr int K = START_K;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const float* rs = dk.ring_d + (int64_t)((r - j + 2 * K) % K) * N + i0;
+    if (NV == 4) {
+      const float4 w = *reinterpret_cast<const float4*>(rs);
+      dj[j][0] = w.x; dj[j][NV > 1 ? 1 : 0] = w.y; dj[j][NV > 2 ? 2 : 0] = w.z;
+      dj[j][NV > 3 ? 3 : 0] = w.w;
+    } else {
+#pragma unroll
+      for (int u = 0; u < NV; ++u) dj[j][u] = rs[u];
+    }
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void fused_dots(const DotsArgs& dk, int64_t N, int64_t i0, int r,
+                                           const float (&dj)[START_K + 1][NV],
+                                           const float (&d0)[NV], bool valid) {
+  constexpr int K = START_K;
+  float acc[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) acc[j] = 0.f;
+  if (valid) {
+#pragma unroll
+    for (int u = 0; u < NV; ++u) acc[0] += d0[u] * d0[u];
+#pragma unroll
+    for (int j = 1; j <= K; ++j)
+#pragma unroll
+      for (int u = 0; u < NV; ++u) acc[j] += d0[u] * dj[j][u];
+    float* rw = dk.ring_d + (int64_t)(r % K) * N + i0;
+    if (NV == 4) {
+      *reinterpret_cast<float4*>(rw) = make_float4(d0[0], d0[NV > 1 ? 1 : 0], d0[NV > 2 ? 2 : 0],
+                                                   d0[NV > 3 ? 3 : 0]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < NV; ++u) rw[u] = d0[u];
+    }
+  }
+  __shared__ float red[8][K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    float t = acc[j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][j] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x <= K) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+    dk.part[(int64_t)blockIdx.x * (K + 1) + threadIdx.x] = t;
+  }
+}
+
 // NC charged species, species indices cs, valences val, reference densities
-// nref (the neutral species are not read).
-template <int NC, bool WALLS, int ST>
+// nref (the neutral species are not read).  DOTS: the start's first pass in
+// the same kernel (the source buffer holds s(t-1) until this pass writes
+// s(t)).
+template <int NC, bool WALLS, int ST, bool DOTS>
 __global__ void __launch_bounds__(256) k_charge(
     const void* fin_v, const uint32_t* links, const int64_t* wsrc, int64_t* src,
     long long* part, const int* label, unsigned long long* comp_sum, int nx, int ny,
-    int nz, int64_t N, int4 cs, float4 val, float4 nref, float fourpi_lb, long long src_ref) {
+    int nz, int64_t N, int4 cs, float4 val, float4 nref, float fourpi_lb, long long src_ref,
+    DotsArgs dk) {
   using T = typename Fmt<ST>::T;
   const T* fin = static_cast<const T*>(fin_v);
   const int sp[4] = {cs.x, cs.y, cs.z, cs.w};
   const float vz[4] = {val.x, val.y, val.z, val.w};
   const float nr[4] = {nref.x, nref.y, nref.z, nref.w};
   long long acc = 0;
+  float d0[1] = {0.f};
+  float dj[START_K + 1][1];
+  const int r = DOTS ? dk.state[START_RING_IDX] : 0;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < (uint32_t)N) {
     uint32_t lk = 0;
@@ -84,6 +155,11 @@ __global__ void __launch_bounds__(256) k_charge(
       fluid = !(lk & LINK_SOLID);
     }
     long long sv = 0;
+    long long old = 0;
+    if (DOTS) {
+      old = src[i];
+      dots_load<1>(dk, N, i, r, dj);
+    }
     if (fluid) {
       int x, y, z;
       site_xyz(i, nx, ny, x, y, z);
@@ -114,6 +190,7 @@ __global__ void __launch_bounds__(256) k_charge(
       if (wsrc) sv += wsrc[i];
     }
     src[i] = sv;
+    if (DOTS) d0[0] = i64_to_f32(sv - old);
     // the largest fluid component (label 0) is summed per CTA; the cells of
     // other components (rare: pockets closed off by walls) add to their own
     // sum (two's-complement wrap-around keeps the 64-bit sum exact)
@@ -123,6 +200,7 @@ __global__ void __launch_bounds__(256) k_charge(
       acc = sv;
   }
   block_partial(acc, part);
+  if (DOTS) fused_dots<1>(dk, N, i, r, dj, d0, i < (uint32_t)N);
 }
 
 // Four consecutive stored values of one direction plane starting at an
@@ -154,19 +232,30 @@ __device__ __forceinline__ void ld4h(const typename Fmt<ST>::T* p, float (&v)[4]
 // four upstream values of a direction are one aligned vector load when the
 // direction has no x component, two when it has (the row's wrap included).
 // The same sums in the same order as k_charge, so the source is the same.
-template <int NC, int ST>
+template <int NC, int ST, bool DOTS>
 __global__ void __launch_bounds__(256) k_charge_quad(
     const void* fin_v, int64_t* src, long long* part, int nx, int ny, int nz, int64_t N, int4 cs,
-    float4 val, float4 nref, float fourpi_lb, long long src_ref) {
+    float4 val, float4 nref, float fourpi_lb, long long src_ref, DotsArgs dk) {
   using T = typename Fmt<ST>::T;
   const T* fin = static_cast<const T*>(fin_v);
   const int sp[4] = {cs.x, cs.y, cs.z, cs.w};
   const float vz[4] = {val.x, val.y, val.z, val.w};
   const float nr[4] = {nref.x, nref.y, nref.z, nref.w};
   long long acc = 0;
+  float d0[4] = {0.f, 0.f, 0.f, 0.f};
+  float dj[START_K + 1][4];
+  longlong2 o0 = make_longlong2(0, 0), o1 = make_longlong2(0, 0);
+  const int r = DOTS ? dk.state[START_RING_IDX] : 0;
   const uint32_t qd = blockIdx.x * blockDim.x + threadIdx.x;
   if (qd < (uint32_t)(N >> 2)) {
     const uint32_t i0 = 4u * qd;
+    if (DOTS) {
+      // s(t-1) and the stored differences, in flight with the pulls
+      const longlong2* so = reinterpret_cast<const longlong2*>(src + i0);
+      o0 = so[0];
+      o1 = so[1];
+      dots_load<4>(dk, N, i0, r, dj);
+    }
     int x0, y, z;
     site_xyz(i0, nx, ny, x0, y, z);
     const Nbr o = neighbours(x0, y, z, nx, ny, nz);
@@ -209,10 +298,17 @@ __global__ void __launch_bounds__(256) k_charge_quad(
       acc += sv[j];
     }
     longlong2* d = reinterpret_cast<longlong2*>(src + i0);
+    if (DOTS) {
+      d0[0] = i64_to_f32(sv[0] - o0.x);
+      d0[1] = i64_to_f32(sv[1] - o0.y);
+      d0[2] = i64_to_f32(sv[2] - o1.x);
+      d0[3] = i64_to_f32(sv[3] - o1.y);
+    }
     d[0] = make_longlong2(sv[0], sv[1]);
     d[1] = make_longlong2(sv[2], sv[3]);
   }
   block_partial(acc, part);
+  if (DOTS) fused_dots<4>(dk, N, 4 * (int64_t)qd, r, dj, d0, qd < (uint32_t)(N >> 2));
 }
 
 // Sums the per-CTA partials of k_charge into *out exactly in 128-bit
@@ -865,29 +961,39 @@ int charge_pass(lbm_t* h, int64_t* out) {
   const int4 cs4 = make_int4(csi[0], csi[1], csi[2], csi[3]);
   const float4 cv4 = make_float4(cval[0], cval[1], cval[2], cval[3]);
   const float4 cr4 = make_float4(cref[0], cref[1], cref[2], cref[3]);
-#define LBM_CHARGE_S(NC)                                                        \
-  LBM_DISPATCH_WS(h, (k_charge<NC, W_, ST_><<<nb, ct, 0, h->st>>>(               \
-                         h->f[h->cur], h->links, h->wsrc, out, h->ps.part,      \
-                         h->ps.label, h->ps.comp_sum,                            \
-                         h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N,                  \
-                         cs4, cv4, cr4, k, src_ref)))
+  // the start's first pass rides along when the pass writes the Poisson
+  // source (not the scatter's accumulator)
+  DotsArgs dk{};
+#define LBM_CHARGE_S(NC)                                                                    \
+  LBM_DISPATCH_WS(h, (dots ? k_charge<NC, W_, ST_, true><<<nb, ct, 0, h->st>>>(             \
+                                 h->f[h->cur], h->links, h->wsrc, out, h->ps.part,           \
+                                 h->ps.label, h->ps.comp_sum, h->cfg.nx, h->cfg.ny,          \
+                                 h->cfg.nz, h->N, cs4, cv4, cr4, k, src_ref, dk)             \
+                           : k_charge<NC, W_, ST_, false><<<nb, ct, 0, h->st>>>(            \
+                                 h->f[h->cur], h->links, h->wsrc, out, h->ps.part,           \
+                                 h->ps.label, h->ps.comp_sum, h->cfg.nx, h->cfg.ny,          \
+                                 h->cfg.nz, h->N, cs4, cv4, cr4, k, src_ref, dk)))
   // 16-bit storage without walls: four nodes per thread (the two-byte
   // loads of one node per thread made the pass request-bound; in FP32 the
   // one-node pass is faster, 53 against 61 us at 128^3)
   const bool quad = !h->has_walls && h->cfg.storage != LBM_FP32 && h->cfg.nx % 4 == 0;
   int nbq = nb;
+  if (quad) nbq = (int)nblocks(h->N / 4, ct);
+  const bool dots = out == h->ps.src && charge_dots_args(h, nbq, &dk);
   if (quad) {
-    nbq = (int)nblocks(h->N / 4, ct);
+#define LBM_CHARGE_Q1(NC, ST, D)                                                            \
+  k_charge_quad<NC, ST, D><<<nbq, ct, 0, h->st>>>(h->f[h->cur], out, h->ps.part, h->cfg.nx, \
+                                                  h->cfg.ny, h->cfg.nz, h->N, cs4, cv4, cr4,  \
+                                                  k, src_ref, dk)
 #define LBM_CHARGE_Q(NC)                                                                   \
   do {                                                                                     \
-    if (h->cfg.storage == LBM_FP16_SHIFT)                                                  \
-      k_charge_quad<NC, LBM_FP16_SHIFT><<<nbq, ct, 0, h->st>>>(                            \
-          h->f[h->cur], out, h->ps.part, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N, cs4, \
-          cv4, cr4, k, src_ref);                                                           \
-    else                                                                                   \
-      k_charge_quad<NC, LBM_BF16_SHIFT><<<nbq, ct, 0, h->st>>>(                            \
-          h->f[h->cur], out, h->ps.part, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->N, cs4, \
-          cv4, cr4, k, src_ref);                                                           \
+    if (h->cfg.storage == LBM_FP16_SHIFT) {                                                \
+      if (dots) LBM_CHARGE_Q1(NC, LBM_FP16_SHIFT, true);                                   \
+      else LBM_CHARGE_Q1(NC, LBM_FP16_SHIFT, false);                                       \
+    } else {                                                                               \
+      if (dots) LBM_CHARGE_Q1(NC, LBM_BF16_SHIFT, true);                                   \
+      else LBM_CHARGE_Q1(NC, LBM_BF16_SHIFT, false);                                       \
+    }                                                                                      \
   } while (0)
     switch (nc) {
       case 0: LBM_CHARGE_Q(0); break;
@@ -897,6 +1003,7 @@ int charge_pass(lbm_t* h, int64_t* out) {
       default: LBM_CHARGE_Q(4); break;
     }
 #undef LBM_CHARGE_Q
+#undef LBM_CHARGE_Q1
   } else {
     switch (nc) {
       case 0: LBM_CHARGE_S(0); break;

@@ -56,6 +56,7 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 //          next start uses this many
 // state[3] terms the current step's start used (for the graph's decisions)
 enum { ST_VALID = 0, ST_RING = 1, ST_TERMS = 2, ST_USED = 3 };
+static_assert(ST_RING == START_RING_IDX, "ring position index shared with the charge pass");
 
 // Least-squares coefficients over the first m stored differences:
 // Cholesky of the Gram matrix G (K x K, row-major) with a relative diagonal
@@ -387,6 +388,17 @@ __global__ void __launch_bounds__(256) k_take_dots(int64_t* __restrict__ acc,
 
 }  // namespace
 
+bool charge_dots_args(lbm_t* h, int ctas, DotsArgs* out) {
+  StartHistory& H = h->start;
+  if (!start_enabled(h) || ctas > H.part_ctas) return false;
+  out->ring_d = H.ring_d;
+  out->state = H.state;
+  out->part = H.part;
+  H.dots_done = true;
+  H.dots_ctas = ctas;
+  return true;
+}
+
 bool launch_take_dots(lbm_t* h, unsigned ctas, double inv_nfluid) {
   StartHistory& H = h->start;
   if (!start_enabled(h)) return false;
@@ -404,6 +416,8 @@ lbm_status start_setup(lbm_t* h) {
   StartHistory& H = h->start;
   const int64_t N = h->N;
   H.ctas = (int)nblk(N, DOT_THREADS);
+  // partials for the largest grid that forms them: a charge pass of 64-thread CTAs
+  H.part_ctas = std::max<int>(H.ctas, (int)nblk(N, 64));
   auto al = [&](void** p, size_t bytes) {
     if (cudaMalloc(p, bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -415,7 +429,7 @@ lbm_status start_setup(lbm_t* h) {
                   al((void**)&H.psi_prev, N * sizeof(int64_t)) &&
                   al((void**)&H.ring_d, (size_t)K * N * sizeof(float)) &&
                   al((void**)&H.ring_p, (size_t)K * N * sizeof(float)) &&
-                  al((void**)&H.part, (size_t)H.ctas * (K + 1) * sizeof(float)) &&
+                  al((void**)&H.part, (size_t)H.part_ctas * (K + 1) * sizeof(float)) &&
                   al((void**)&H.gram, K * K * sizeof(double)) &&
                   al((void**)&H.coef, K * sizeof(float)) && al((void**)&H.state, 4 * sizeof(int));
   if (!ok) {
