@@ -78,6 +78,28 @@ def test_binary_sinusoid_fields_within_1e3(storage):
 
 
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_charged_periodic_spectral_graph_fields_within_1e3(storage):
+    """Charged ternary, periodic 32 x 16 x 8, spectral Poisson in graph
+    steps: the charge pass of four nodes per thread, with the Poisson
+    start's first pass in it, against the oracle after 200 steps."""
+    wl = WL.ternary_bulk(shape=(8, 16, 32), seed=93, spread=2e-3)
+    wl.e_ext = (1e-4, 0.0, 0.0)
+    od = lbm.omega_drag_for_schmidt(1.0, 10.0)
+    nz, ny, nx = wl.shape
+    lat = lbm.Lattice(nx, ny, nz, 3, omega_visc=wl.omega_visc, omega_drag=od, bjerrum=wl.bjerrum,
+                      e_ext=wl.e_ext, storage=storage, poisson="fft", step_graph=True)
+    for s in range(3):
+        lat.set_species(s, wl.mass[s], wl.valence[s], wl.n0[s])
+    p = O.Params(wl.omega_visc, od, wl.mass, wl.valence, bjerrum=wl.bjerrum, e_ext=wl.e_ext)
+    o = O.Oracle(p, wl.shape)
+    o.initialise(wl.n0)
+    lat.step(200)
+    o.run(200)
+    assert lat.diagnostics()["poisson_residual"] <= 1e-8
+    _check(storage, _field_error(lat, o, np.ones(wl.shape, bool)))
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
 def test_charged_walls_fields_within_1e3(storage):
     wl = WL.ternary_bulk(shape=(8, 10, 12), seed=91, spread=2e-3)
     wl.e_ext = (1e-4, 0.0, 0.0)
