@@ -1079,7 +1079,10 @@ lbm_status lbm_autotune(lbm_t* h, double* out) {
       tc = sizes[k];
     }
   }
-  if (h->cfg.bjerrum > 0.0) {
+  // (with the charge scatter the pass runs only after a restart, and the
+  // step's source take would apply the potential's start on every timed
+  // launch: nothing to time)
+  if (h->cfg.bjerrum > 0.0 && !h->scat_on) {
     const int saved = h->charge_threads;
     for (int k = 0; k < 3; ++k) {
       h->charge_threads = sizes[k];

@@ -215,6 +215,10 @@ struct StartHistory {
   // differences and inner products) for this step, with dots_ctas partials
   bool dots_done = false;
   int dots_ctas = 0;
+  // it also applied the start of the potential (and cleared the first norm
+  // slot when psi_cleared), which start_apply then skips
+  bool psi_done = false;
+  bool psi_cleared = false;
   int part_ctas = 0;            // CTAs part has room for
   cudaStream_t side = nullptr;  // the fit runs here, beside the solve (lowest priority)
   cudaEvent_t fork = nullptr, join = nullptr;

@@ -1440,17 +1440,11 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
   if (e == cudaSuccess) {
     cudaError_t ec = cudaSuccess;
     h->charge_step = &gs->step;
-    // with the charge scatter, a replay finds the source of its input
-    // populations in the accumulator (spectral_graph_steps sees to it
-    // before the first replay; every step's stream/collide scatters the
-    // next one)
-    h->scat_valid = true;
-    ec = launch_charge(h);
-    h->charge_step = nullptr;
     // the start from the history, then the fit for the next step on the
-    // second side stream, beside the applications
-    // the start's bookkeeping kernel also decides the speculation and
-    // clears the first norm slot (when the start is on)
+    // second side stream, beside the applications; the start's
+    // bookkeeping (its own kernel, or the last CTA of the source take when
+    // that applies the start) also decides the speculation and clears the
+    // first norm slot (when the start is on)
     const bool fit = start_enabled(h);
     if (fit) {
       h->mark_skip_out = &gs->spec_skip;
@@ -1459,6 +1453,13 @@ lbm_status build_step_graph(lbm_t* h, int parity, bool diag) {
       h->mark_clear = norm_slot(h, 0);
       h->mark_nclear = 2 * NACC;
     }
+    // with the charge scatter, a replay finds the source of its input
+    // populations in the accumulator (spectral_graph_steps sees to it
+    // before the first replay; every step's stream/collide scatters the
+    // next one)
+    h->scat_valid = true;
+    ec = launch_charge(h);
+    h->charge_step = nullptr;
     if (ec == cudaSuccess) ec = start_apply(h, false);
     h->mark_skip_out = nullptr;
     h->mark_prev_iters = nullptr;

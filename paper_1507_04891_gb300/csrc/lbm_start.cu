@@ -302,15 +302,34 @@ __global__ void k_start_mark(int* __restrict__ state, int advance, int* __restri
 // products with D_0 .. D_K per CTA into part, and the exact 128-bit source
 // total with the last CTA's work of k_src_take (FP64 total, mean over the
 // fluid into mean_z, graph step counter, tot cleared).
+// PSI (the spectral solver, whose start uses the previous step's fit): the
+// start of the potential in the same pass (pass 3, as k_start_psi: the
+// coefficients are known at the step's start), and the last CTA does
+// k_start_mark's bookkeeping (terms used, the speculation flag, the first
+// norm slot cleared; no ring advance: the fit advances it).
+struct PsiArgs {
+  int64_t* psi;
+  int64_t* psi_prev;
+  float* ring_p;
+  const float* coef;
+  int* skip_out;          // speculation flag of a step graph, or NULL
+  const int* prev_iters;  // the previous step's applications (with skip_out)
+  int kbaked;
+  float* clear;           // norm slot to clear, or NULL
+  int nclear;
+};
+
+template <bool PSI>
 __global__ void __launch_bounds__(256) k_take_dots(int64_t* __restrict__ acc,
                                                    int64_t* __restrict__ src,
                                                    float* __restrict__ ring_d,
-                                                   const int* __restrict__ state, int64_t N,
+                                                   int* __restrict__ state, int64_t N,
                                                    float* __restrict__ part,
                                                    unsigned long long* tot, double* out,
                                                    long long* mean_z, int nz, double inv_nfluid,
-                                                   uint32_t* step) {
+                                                   uint32_t* step, const PsiArgs pa) {
   const int r = state[ST_RING];
+  const int m = PSI ? state[ST_TERMS] : 0;
   const int64_t np = N / 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   longlong2* a2 = reinterpret_cast<longlong2*>(acc);
@@ -327,6 +346,17 @@ __global__ void __launch_bounds__(256) k_take_dots(int64_t* __restrict__ acc,
 #pragma unroll
     for (int j = 1; j <= K; ++j)
       dj[j] = reinterpret_cast<const float2*>(ring_d + (int64_t)((r - j + 2 * K) % K) * N)[k];
+    longlong2 pv = make_longlong2(0, 0), pp = make_longlong2(0, 0);
+    float2 pj[K + 1];
+    if (PSI) {
+      pv = reinterpret_cast<const longlong2*>(pa.psi)[k];
+      pp = reinterpret_cast<const longlong2*>(pa.psi_prev)[k];
+#pragma unroll
+      for (int j = 2; j <= K; ++j)
+        pj[j] = j <= m ? reinterpret_cast<const float2*>(
+                             pa.ring_p + (int64_t)((r - j + 1 + K) % K) * N)[k]
+                       : make_float2(0.f, 0.f);
+    }
     s2[k] = q;
     a2[k] = make_longlong2(0, 0);
     v += q.x + q.y;
@@ -335,6 +365,24 @@ __global__ void __launch_bounds__(256) k_take_dots(int64_t* __restrict__ acc,
     dp[0] += d0x * d0x + d0y * d0y;
 #pragma unroll
     for (int j = 1; j <= K; ++j) dp[j] += d0x * dj[j].x + d0y * dj[j].y;
+    if (PSI) {
+      const float p1x = i64_to_f32(pv.x - pp.x), p1y = i64_to_f32(pv.y - pp.y);
+      longlong2 nv = pv;
+      if (m > 0) {
+        float cx = pa.coef[0] * p1x, cy = pa.coef[0] * p1y;
+#pragma unroll
+        for (int j = 2; j <= K; ++j)
+          if (j <= m) {
+            cx += pa.coef[j - 1] * pj[j].x;
+            cy += pa.coef[j - 1] * pj[j].y;
+          }
+        if (fabsf(cx) < 2.3e18f) nv.x = pv.x + f32_to_i64_rn(cx);
+        if (fabsf(cy) < 2.3e18f) nv.y = pv.y + f32_to_i64_rn(cy);
+      }
+      reinterpret_cast<longlong2*>(pa.psi)[k] = nv;
+      reinterpret_cast<longlong2*>(pa.psi_prev)[k] = pv;
+      reinterpret_cast<float2*>(pa.ring_p + (int64_t)(r % K) * N)[k] = make_float2(p1x, p1y);
+    }
   }
   __shared__ float red[8][K + 1];
   __shared__ long long redv[8];
@@ -379,7 +427,16 @@ __global__ void __launch_bounds__(256) k_take_dots(int64_t* __restrict__ acc,
     *out = td;
     s_mean = llrint(td * inv_nfluid);
     if (step) *step += 1u;
+    if (PSI) {
+      // every CTA read the terms and the ring position before counting itself
+      const int used = state[ST_TERMS];
+      state[ST_USED] = used;
+      if (pa.skip_out)
+        *pa.skip_out = (used < START_FULL_TERMS || (pa.prev_iters && *pa.prev_iters > pa.kbaked)) ? 1 : 0;
+    }
   }
+  if (PSI)
+    for (int k = threadIdx.x; k < pa.nclear; k += blockDim.x) pa.clear[k] = 0.f;
   if (mean_z) {
     __syncthreads();
     for (int z = threadIdx.x; z < nz; z += blockDim.x) mean_z[z] = s_mean;
@@ -403,11 +460,32 @@ bool launch_take_dots(lbm_t* h, unsigned ctas, double inv_nfluid) {
   StartHistory& H = h->start;
   if (!start_enabled(h)) return false;
   ctas = std::min<unsigned>(ctas, (unsigned)H.ctas);
-  k_take_dots<<<ctas, 256, 0, h->st>>>(h->scat_acc, h->ps.src, H.ring_d, H.state, h->N, H.part,
-                                      h->scat_tot, h->ps.dsum, h->charge_mean_z, h->cfg.nz,
-                                      inv_nfluid, h->charge_step);
+  // the spectral solver's start uses the previous step's fit, so the
+  // start of the potential comes along (its bookkeeping in the last CTA)
+  const bool psi = h->spec != nullptr;
+  PsiArgs pa{};
+  if (psi) {
+    pa.psi = h->ps.psi[h->ps.cur];
+    pa.psi_prev = H.psi_prev;
+    pa.ring_p = H.ring_p;
+    pa.coef = H.coef;
+    pa.skip_out = h->mark_skip_out;
+    pa.prev_iters = h->mark_prev_iters;
+    pa.kbaked = h->mark_k;
+    pa.clear = h->mark_clear;
+    pa.nclear = h->mark_clear ? h->mark_nclear : 0;
+    k_take_dots<true><<<ctas, 256, 0, h->st>>>(h->scat_acc, h->ps.src, H.ring_d, H.state, h->N,
+                                               H.part, h->scat_tot, h->ps.dsum, h->charge_mean_z,
+                                               h->cfg.nz, inv_nfluid, h->charge_step, pa);
+  } else {
+    k_take_dots<false><<<ctas, 256, 0, h->st>>>(h->scat_acc, h->ps.src, H.ring_d, H.state, h->N,
+                                                H.part, h->scat_tot, h->ps.dsum, h->charge_mean_z,
+                                                h->cfg.nz, inv_nfluid, h->charge_step, pa);
+  }
   H.dots_done = true;
   H.dots_ctas = (int)ctas;
+  H.psi_done = psi;
+  H.psi_cleared = psi && h->mark_clear != nullptr;
   return true;
 }
 
@@ -474,6 +552,13 @@ cudaError_t start_apply(lbm_t* h, bool last) {
   StartHistory& H = h->start;
   // without the start the history goes stale: it restarts when enabled again
   if (!start_enabled(h)) return start_reset(h);
+  if (H.psi_done && !last) {
+    // the step's source take applied the start (k_take_dots)
+    H.psi_done = false;
+    h->slot0_cleared = H.psi_cleared;
+    return cudaSuccess;
+  }
+  H.psi_done = false;
   k_start_psi<<<nblk(h->N, 256), 256, 0, h->st>>>(h->ps.psi[h->ps.cur], H.psi_prev, H.ring_p, H.coef,
                                                    H.state, h->N, last ? 1 : 0);
   k_start_mark<<<1, 128, 0, h->st>>>(H.state, last ? 1 : 0, h->mark_skip_out, h->mark_prev_iters,
