@@ -290,6 +290,9 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_t** out) {
   if (s == LBM_OK) s = dev_alloc(h, &h->dred, (MAX_SPECIES + 4) * DIAG_SPREAD);
   // diagnostics partials for the smallest CTA size the stream/collide uses (64)
   if (s == LBM_OK) s = dev_alloc(h, &h->dpart, (size_t)((N + 63) / 64) * DIAG_NQ);
+  if (s == LBM_OK) s = dev_alloc(h, &h->dmid, (size_t)DIAG_NQ * 64);
+  if (s == LBM_OK) s = dev_alloc(h, &h->ddone, 1);
+  if (s == LBM_OK) cudaMemset(h->ddone, 0, sizeof(unsigned));
   if (s == LBM_OK) s = dev_alloc(h, &h->dflag, 1);
   if (s == LBM_OK && cudaMallocHost(&h->hred, (MAX_SPECIES + 4) * DIAG_SPREAD * sizeof(double)) != cudaSuccess)
     s = LBM_ENOMEM;
@@ -347,6 +350,8 @@ void lbm_destroy(lbm_t* h) {
   cudaFree(h->dred);
   if (h->hrec) cudaFreeHost(h->hrec);
   cudaFree(h->dpart);
+  cudaFree(h->dmid);
+  cudaFree(h->ddone);
   cudaFree(h->dflag);
   if (h->hred) cudaFreeHost(h->hred);
   spectral_graph_free(h);

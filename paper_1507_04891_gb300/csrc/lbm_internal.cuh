@@ -267,6 +267,8 @@ struct lbm {
   // (DIAG_NQ doubles per CTA); diag_valid: they describe the current state
   double* dpart = nullptr;
   int64_t dpart_ctas = 0;   // CTAs of the last stream/collide launch
+  double* dmid = nullptr;   // second level of the partials' reduction (k_diag_reduce)
+  unsigned* ddone = nullptr;  // CTAs of k_diag_reduce done (reset by its last CTA)
   bool diag_valid = false;
   // set by the spectral plan when the fluid is one periodic run: the charge
   // kernel's partial sum writes the source mean of every plane there, and

@@ -696,23 +696,27 @@ __global__ void __launch_bounds__(256) k_species_check(const double* __restrict_
   }
 }
 
-// Sums the per-CTA diagnostics partials of the stream/collide kernel: one
-// CTA per quantity, FP64, in a fixed order (the result does not depend on
-// scheduling).  out may be mapped pinned host memory (a per-step record).
-// With iters / rel given (device), CTA 0 also copies them to out[DIAG_NQ],
+// Sums the per-CTA diagnostics partials of the stream/collide kernel in
+// FP64, in a fixed order (the result does not depend on scheduling):
+// DIAG_REDUCE_G CTAs per quantity each sum a contiguous share of the
+// partials into mid, and the CTA that finishes last (counted in *done,
+// which it resets) adds the DIAG_REDUCE_G values of each quantity in order.
+// out may be mapped pinned host memory (a per-step record).  With iters /
+// rel given (device), the last CTA also copies them to out[DIAG_NQ],
 // out[DIAG_NQ + 1].
+constexpr int DIAG_REDUCE_G = 8;
 __global__ void __launch_bounds__(256) k_diag_reduce(const double* __restrict__ part,
-                                                     int64_t nctas, double* __restrict__ out,
+                                                     int64_t nctas, double* __restrict__ mid,
+                                                     unsigned* done, double* __restrict__ out,
                                                      const int* __restrict__ iters,
                                                      const double* __restrict__ rel) {
-  const int k = blockIdx.x;
-  if (k == 0 && threadIdx.x == 0 && iters) {
-    out[DIAG_NQ] = (double)*iters;
-    out[DIAG_NQ + 1] = *rel;
-  }
+  const int k = blockIdx.x / DIAG_REDUCE_G, g = blockIdx.x % DIAG_REDUCE_G;
+  const int64_t chunk = (nctas + DIAG_REDUCE_G - 1) / DIAG_REDUCE_G;
+  const int64_t c0 = g * chunk, c1 = min(nctas, c0 + chunk);
   double v = 0.0;
-  for (int64_t c = threadIdx.x; c < nctas; c += blockDim.x) v += part[c * DIAG_NQ + k];
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) v += part[c * DIAG_NQ + k];
   __shared__ double red[8];
+  __shared__ int last;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -720,7 +724,25 @@ __global__ void __launch_bounds__(256) k_diag_reduce(const double* __restrict__ 
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    out[k] = t;
+    mid[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < DIAG_NQ) {
+    double t = 0.0;
+    for (int q = 0; q < DIAG_REDUCE_G; ++q)
+      t += __ldcg(mid + threadIdx.x * DIAG_REDUCE_G + q);  // other CTAs' sums, from the L2
+    out[threadIdx.x] = t;
+  }
+  if (threadIdx.x == 0) {
+    if (iters) {
+      out[DIAG_NQ] = (double)*iters;
+      out[DIAG_NQ + 1] = *rel;
+    }
+    *done = 0u;
   }
 }
 
@@ -881,7 +903,8 @@ cudaError_t launch_species_check(lbm_t* h, const double* n0_dev, const double* u
 }
 
 cudaError_t launch_diag_reduce(lbm_t* h, double* out, const int* iters, const double* rel) {
-  k_diag_reduce<<<DIAG_NQ, 256, 0, h->st>>>(h->dpart, h->dpart_ctas, out, iters, rel);
+  k_diag_reduce<<<DIAG_NQ * DIAG_REDUCE_G, 256, 0, h->st>>>(h->dpart, h->dpart_ctas, h->dmid,
+                                                            h->ddone, out, iters, rel);
   ++h->launches;
   return cudaGetLastError();
 }
