@@ -158,9 +158,13 @@ lbm_status lbm_set_plane_omega_drag(lbm_t* h, const double* omega);
 lbm_status lbm_set_drag_matrix(lbm_t* h, const double* omega);
 
 /* Autotuner: times the stream/collide and charge kernels of the current
- * state at several CTA sizes (64, 128, 256) and keeps the fastest; the state
- * does not advance.  out (may be NULL) receives the chosen sizes and their
- * times in ms: [collide_threads, collide_ms, charge_threads, charge_ms].  */
+ * state at several CTA sizes (64, 128, 256) and keeps the fastest; the
+ * populations do not advance, and the Poisson start's history restarts.
+ * out (may be NULL) receives the chosen sizes and their times in ms:
+ * [collide_threads, collide_ms, charge_threads, charge_ms]; with the charge
+ * scatter (LBM_FLAG_CHARGE_PASS off, see there) the charge pass runs only
+ * after new populations and is not timed (charge_ms 0, charge_threads
+ * unchanged).                                                             */
 lbm_status lbm_autotune(lbm_t* h, double* out);
 
 /* Learned initial guess of the Poisson solve.  The paper has no
