@@ -70,8 +70,9 @@ def _against_oracle(lat, o, S):
 @pytest.mark.parametrize("solver,graph", [("fft", False), ("fft", True), ("mg", False)])
 def test_scattered_charge_matches_oracle_200_steps(solver, graph):
     """Charged ternary, 32 x 16 x 12 periodic (a row is one warp, its x wrap
-    stays inside the warp), Sc 3 and an applied field: per node within 1e-5 of the oracle after 200
-    steps, and within 1e-7 of the same lattice with the charge pass."""
+    stays inside the warp), Sc 3 and an applied field: per node within 1e-5
+    of the oracle after 200 steps, and within 1e-7 of the same lattice with
+    the charge pass."""
     wl = WL.ternary_bulk(shape=(12, 16, 32), seed=52, spread=3e-3)
     wl.e_ext = (1e-4, -5e-5, 0.0)
     od = lbm.omega_drag_for_schmidt(1.0, 3.0)
